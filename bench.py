@@ -1,0 +1,298 @@
+"""Benchmark of the MPR gap fill on GB300 (one JSON line on stdout, rank 0).
+
+A step is one whole gap fill of a 4096 x 4096 Whittle-Matern grid (nu = 1, correlation
+length 32, half of the sites missing as random disks of radius 8-64 plus random sites):
+Eq. 1 map and lattice set-up, Eq. 4 sample energy, T-hat from the e(T, L) table, the
+Algorithm 2 relaxation with the slope test, M = 100 equilibrium sweeps and the averaging /
+back-transform.  The metric is gap-site updates per second (one update = over-relaxation +
+Metropolis step of one gap site).
+
+  value : inputs and output already in device memory (torch tensors)
+  e2e   : the same call with pinned host buffers, host<->device copies inside the step
+The e(T, L) table depends only on the lattice shape and the sampler parameters; it is
+built once per shape during warm-up (its build time is reported) and reused by every step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mpr|reference]
+With N > 1 (torchrun) every rank fills its own map (independent seeds): weak scaling,
+no collective on the data path; the reported time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "mpr-fill-4096x4096-wm-nu1-xi32-p0.5-disks"
+METRIC = "MPR site-updates/s"
+UNIT = "site-updates/s"
+L = 4096
+M = 100
+
+
+def make_inputs(seed_offset: int):
+    from paper_1811_01604_gb300 import synth
+    z = synth.wm_field(L, 1.0, 32.0, seed=3 + seed_offset)
+    mask = synth.mask_disks(L, L, 0.5, seed=1_000_003 + seed_offset)
+    return z, mask
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for name, v in zip(names, r[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def cpu_baseline(z, mask, T):
+    """The FP64 oracle, single-threaded, on a 512 x 512 crop of the same workload."""
+    import oracle.oracle as orc
+    c = 512
+    zc = np.ascontiguousarray(z[:c, :c])
+    mc = np.ascontiguousarray(mask[:c, :c])
+    prm = orc.params(seed=0, M=M)
+    t0 = time.perf_counter()
+    _, _, out = orc.fill(zc, mc, prm, T_fixed=T)
+    dt = time.perf_counter() - t0
+    updates = out.n_gap * (out.eq.sweeps + M)
+    return {"value": updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"512x512 crop of the step's grid, fixed T-hat, slope-test relaxation "
+                      f"({out.eq.sweeps} sweeps) + M={M}, {updates} site-updates in {dt:.1f} s"}
+
+
+def run_reference(args, rank):
+    """--impl reference: the oracle as it stands, each step a 256 x 256 crop fill."""
+    if rank != 0:
+        return
+    import oracle.oracle as orc
+    orc.build()
+    z, mask = make_inputs(0)
+    c = 256
+    zc = np.ascontiguousarray(z[:c, :c])
+    mc = np.ascontiguousarray(mask[:c, :c])
+    prm = orc.params(seed=0, M=M, KT=8, T_W=32, T_H=32, M_T=50)
+    _, _, out0 = orc.fill(zc, mc, prm)                      # T-hat of the crop
+    T = out0.T_hat
+    for _ in range(args.warmup):
+        orc.fill(zc, mc, prm, T_fixed=T)
+    t0 = time.perf_counter()
+    updates = 0
+    for _ in range(args.steps):
+        _, _, out = orc.fill(zc, mc, prm, T_fixed=T)
+        updates += out.n_gap * (out.eq.sweeps + M)
+    dt = time.perf_counter() - t0
+    v = updates / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "256x256 crop",
+                                              "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"256x256 crop of the 4096^2 step grid, fixed T-hat "
+                                       f"{T:.4f}, slope-test relaxation + M={M} per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mpr", choices=["mpr", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    from paper_1811_01604_gb300 import mpr
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    z_np, m_np = make_inputs(rank)
+    H, W = z_np.shape
+    z = torch.from_numpy(z_np).to(dev)
+    mask = torch.from_numpy(m_np).to(dev)
+    zhat = torch.empty_like(z)
+    z_h = torch.from_numpy(z_np).pin_memory()
+    m_h = torch.from_numpy(m_np).pin_memory()
+    zhat_h = torch.empty_like(z_h).pin_memory()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
+    prm = mpr.mpr_default_params(seed=1 + rank, M=M)
+    stream = torch.cuda.current_stream(dev)
+
+    def one_fill(zi, mi, out):
+        ctx = mpr.mpr_init(zi, mi, W, H, prm, stream.cuda_stream)
+        try:
+            T, _ = mpr.mpr_estimate_T(ctx)
+            st = mpr.mpr_equilibrate(ctx)
+            mpr.mpr_predict(ctx, M, out)
+            P = int(m_np.size - m_np.sum())
+        finally:
+            mpr.mpr_free(ctx)
+        return P * (st.sweeps + M), st, T
+
+    # warm-up (the first one builds and caches the e(T, L) table)
+    t_tab = time.perf_counter()
+    one_fill(z, mask, zhat)
+    torch.cuda.synchronize()
+    table_s = time.perf_counter() - t_tab
+    for _ in range(max(0, args.warmup - 1)):
+        one_fill(z, mask, zhat)
+
+    def timed(zi, mi, out):
+        total_ms, updates, launches, sweeps = 0.0, 0, 0, []
+        for _ in range(args.steps):
+            flush.zero_()                                  # L2 flush between steps
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            l0 = mpr.mpr_kernel_launches()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            u, st, T = one_fill(zi, mi, out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            launches += mpr.mpr_kernel_launches() - l0
+            total_ms += e0.elapsed_time(e1)
+            updates += u
+            sweeps.append(st.sweeps)
+        return total_ms, updates, launches, sweeps, T
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    dev_ms, dev_updates, launches, sweeps, T = timed(z, mask, zhat)
+    e2e_ms, e2e_updates, _, _, _ = timed(z_h, m_h, zhat_h)
+    clk = clocks.stop()
+
+    # dominant kernel: half-sweep launches timed with CUDA events on the context stream
+    ctx = mpr.mpr_init(z, mask, W, H, prm, stream.cuda_stream)
+    try:
+        mpr.mpr_set_T(ctx, T)
+        mpr.mpr_sweep(ctx, 50, 8.0)
+        half_ms = mpr.mpr_time_half_sweeps(ctx, 20, 8.0)
+    finally:
+        mpr.mpr_free(ctx)
+    N = H * W
+    P = int(m_np.size - m_np.sum())
+    bytes_per_launch = (8 * N + 20 * P) / 2.0        # other-colour plane + own gaps r/w + list
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = bytes_per_launch / (half_ms * 1e-3) / 1e9
+
+    times = torch.tensor([dev_ms, e2e_ms], dtype=torch.float64, device=dev)
+    ups = torch.tensor([float(dev_updates), float(e2e_updates)], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+        dist.all_reduce(ups, op=dist.ReduceOp.SUM)
+    dev_ms, e2e_ms = times.tolist()
+    dev_updates, e2e_updates = ups.tolist()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": dev_updates / (dev_ms * 1e-3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dev_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "W": W, "H": H, "gap_sites": P, "M": M,
+                       "relax_sweeps": sweeps, "T_hat": T,
+                       "s_per_map": dev_ms * 1e-3 / args.steps,
+                       "T_table": f"built once per shape during warm-up ({table_s:.2f} s incl. one fill)",
+                       "l2": "512 MB buffer written between steps (L2 flush)",
+                       "parallelism": f"replicas{world}"},
+            "e2e": {"value": e2e_updates / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": N * 5, "d2h_bytes_per_step": N * 4},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None,
+                         "kernel": "k_half_sweep", "ms_per_launch": half_ms,
+                         "peak_source": f"{peak_src} hbm_gbs",
+                         "bytes_per_launch": bytes_per_launch},
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(z_np, m_np, T)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * mpr.h -- C ABI of the GB300 MPR gap-filling library (libmpr.so).
+ *
+ * Method: Zukovic, Borovsky, Lach, Hristopulos, "GPU-accelerated Simulation of
+ * Massive Spatial Data based on the Modified Planar Rotator Model".  A grid
+ * G = G_S u G_P holds sample values Z_s at the sample sites G_S; the library
+ * returns estimates Z_p at the prediction (gap) sites G_P (Sect. 2.1) by
+ * conditional hybrid Monte Carlo of the MPR model (Eq. 2, q = 1/2), following
+ * Algorithm 2: data-to-angle map (Eq. 1), temperature inference by specific
+ * energy matching (Eqs. 4-5), relaxation with the hybrid update of Algorithm 1
+ * until the energy slope test passes, M equilibrium sweeps and the inverse map.
+ *
+ * Conventions shared by every entry point
+ *  - Grids are row-major [H][W] (x fastest).  mask[i] = 1 marks a sample site,
+ *    0 a gap site.  z values at gap sites are ignored.
+ *  - Pointers may be host or device memory (CUDA unified addressing decides);
+ *    inputs are copied at the call, outputs are written before the call returns.
+ *    The caller owns every buffer it passes; the context owns all others.
+ *  - All device work is enqueued on the stream given to mpr_init (a
+ *    cudaStream_t passed as void*, NULL = legacy default stream).  A call that
+ *    returns a value to the host synchronises that stream first.
+ *  - Errors are returned as mpr_status; nothing is thrown across the ABI.
+ *    mpr_last_error(ctx) gives a one-line description of the last failure.
+ *  - A context is not thread-safe: use one context per host thread / stream.
+ *  - Only q = 1/2 (the paper's value) is implemented by the kernels.
+ */
+#ifndef MPR_H_
+#define MPR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpr_ctx mpr_ctx;
+
+typedef enum {
+    MPR_OK = 0,
+    MPR_EINVAL = 1,      /* invalid argument (sizes, NULL pointer, parameter out of range) */
+    MPR_ENOMEM = 2,      /* a device or pinned-host allocation failed */
+    MPR_ECUDA = 3,       /* a CUDA runtime call failed */
+    MPR_ENODATA = 4,     /* fewer than two samples, or z_max == z_min: Eq. 1 is undefined */
+    MPR_ENOPAIRS = 5,    /* no nearest-neighbour sample pair: Eq. 4 is undefined */
+    MPR_ETIMEOUT = 6,    /* a bounded device-side wait expired; the device state is unreliable */
+    MPR_ENOTEQUIL = 7,   /* i_max reached with slope k < 0; results are valid but flagged */
+    MPR_ESTATE = 8       /* call out of order (e.g. sweeps before a temperature is set) */
+} mpr_status;
+
+/* over-relaxation (Eq. 6) variants */
+enum { MPR_OR_CONSERVING = 0, MPR_OR_NONE = 2 };
+/* transcendental functions of the sweep kernel (Sect. 3.3.2, precision study) */
+enum { MPR_TRIG_ACCURATE = 0, MPR_TRIG_FAST = 1 };
+/* how sweeps are driven */
+enum { MPR_EXEC_AUTO = 0, MPR_EXEC_GRAPH = 1, MPR_EXEC_PERSISTENT = 2 };
+
+/*
+ * Simulation parameters (Algorithm 2, step 1.1) and the readings of what the
+ * paper leaves open.  Fill with mpr_default_params() and override.
+ */
+typedef struct {
+    uint64_t seed;     /* Philox4x32-10 key; counter = {site, sweep, chain, 0} */
+    double q;          /* coupling of Eq. 2; must be 0.5 */
+    double A_targ;     /* target Metropolis acceptance ratio (default 0.3) */
+    double k_a;        /* a(i+1) = 1 + (i+1)/k_a when A < A_targ (default 3) */
+    int n_f;           /* slope test every n_f sweeps (default 5) */
+    int n_fit;         /* energies in the slope fit (default 20, >= 2) */
+    int i_max;         /* cap on relaxation sweeps (default 10000) */
+    int M;             /* equilibrium realizations for mpr_predict's default (default 100) */
+    int or_mode;       /* MPR_OR_CONSERVING (default) or MPR_OR_NONE */
+    int trig_mode;     /* MPR_TRIG_ACCURATE (default) or MPR_TRIG_FAST */
+    double a_eq;       /* window factor in the equilibrium phase (paper: 1) */
+    int KT;            /* temperatures in the e(T,L) table (default 16, >= 2) */
+    double T_min;      /* table range (default 1e-4 .. 1) */
+    double T_max;
+    int T_cap;         /* table lattice side = min(W, T_cap) x min(H, T_cap); 0 = W x H (default 1024) */
+    int M_T;           /* sweeps averaged per table temperature (default 100) */
+    int exec_mode;     /* MPR_EXEC_* (default AUTO) */
+    uint32_t chain;    /* realization id of this context's chain (default 0) */
+} mpr_params;
+
+typedef struct {
+    int sweeps;          /* sweeps performed by the call */
+    double acceptance;   /* Metropolis acceptance ratio of the last sweep */
+    double e;            /* specific energy H/N_GP after the last sweep (Eq. 5 normalisation) */
+} mpr_sweep_stats;
+
+typedef struct {
+    int sweeps;          /* relaxation sweeps i at exit (Algorithm 2 step 5) */
+    double a;            /* window factor at exit */
+    double k;            /* last energy slope */
+    double A_last;       /* acceptance ratio of the last sweep */
+    double e_last;       /* specific energy after the last sweep */
+    int converged;       /* 1 if the loop ended on k >= 0, 0 if on i > i_max */
+} mpr_equil_stats;
+
+/* Fills *p with the defaults listed above. */
+void mpr_default_params(mpr_params* p);
+
+/* Returns a static string naming a status code. */
+const char* mpr_status_string(mpr_status s);
+
+/*
+ * Algorithm 2 steps 2-3 and the set-up of the device lattice.
+ * z: float[H][W] data, mask: uint8[H][W] (1 = sample).  W, H >= 1, W/2 < 65536,
+ * H < 65536.  Maps samples to angles by Eq. 1, draws the gap angles from
+ * U(0, 2pi) (step 2.2) and builds the red/black lattice and gap lists.
+ * On success *ctx owns all device state; release it with mpr_free.
+ * Errors: MPR_EINVAL, MPR_ENODATA, MPR_ENOMEM, MPR_ECUDA (no context is returned).
+ */
+mpr_status mpr_init(mpr_ctx** ctx, const float* z, const uint8_t* mask, int W, int H,
+                    const mpr_params* params, void* cuda_stream);
+
+/*
+ * Algorithm 2 step 4: sample specific energy e_s (Eq. 4, each sample pair once),
+ * the table e(T_k, L) of Eq. 5 from unconditional simulations of all-free
+ * lattices (one chain per temperature, all in one batched run, cached per
+ * lattice shape and parameters in the process), and T-hat = argmin |e_s - e(T,L)|
+ * by piecewise-linear interpolation in T.  Sets the context temperature.
+ * T_hat and e_s may be NULL.  Errors: MPR_ENOPAIRS, MPR_ECUDA, MPR_ETIMEOUT.
+ */
+mpr_status mpr_estimate_T(mpr_ctx* ctx, double* T_hat, double* e_s);
+
+/* Sets the temperature directly (T > 0), skipping mpr_estimate_T. */
+mpr_status mpr_set_T(mpr_ctx* ctx, double T);
+
+/*
+ * n >= 0 hybrid sweeps (Algorithm 1 on sub-grid A, then on sub-grid B) at a
+ * fixed window factor a >= 1, advancing the sweep counter.  out may be NULL.
+ */
+mpr_status mpr_sweep(mpr_ctx* ctx, int n, double a, mpr_sweep_stats* out);
+
+/*
+ * Algorithm 2 step 5 from the current state: i = 0, k = -1, a = 1; sweep while
+ * k < 0 and i <= i_max, with the window update of step 5.2 and the slope test of
+ * step 5.4 (least-squares slope of the last n_fit specific energies, every n_f
+ * sweeps once i >= n_fit).  Returns MPR_ENOTEQUIL if it stopped on i_max.
+ */
+mpr_status mpr_equilibrate(mpr_ctx* ctx, mpr_equil_stats* out);
+
+/*
+ * Algorithm 2 steps 6-7: M >= 1 sweeps at window a_eq, accumulating every gap
+ * angle, then zhat = G^-1(mean angle) at gaps and zhat = z at samples.
+ * zhat: float[H][W] (host or device).
+ */
+mpr_status mpr_predict(mpr_ctx* ctx, int M, float* zhat);
+
+/*
+ * Algorithm 2 end to end: mpr_estimate_T (unless a temperature was set),
+ * mpr_equilibrate, mpr_predict(params.M).  stats may be NULL.
+ * Returns MPR_OK or MPR_ENOTEQUIL on success.
+ */
+mpr_status mpr_fill(mpr_ctx* ctx, float* zhat, mpr_equil_stats* stats);
+
+/* Releases the context and everything it owns.  NULL is allowed. */
+void mpr_free(mpr_ctx* ctx);
+
+/* Text of the last error recorded on ctx (never NULL). */
+const char* mpr_last_error(const mpr_ctx* ctx);
+
+/*
+ * State access (checkpoint / resume and per-sweep parity checks).
+ * phi: float[H][W] angles in [0, 2pi] (sample sites hold their mapped angle);
+ * sweep: the global sweep counter used by the Philox streams.
+ * mpr_set_state writes only gap sites.
+ */
+mpr_status mpr_get_state(mpr_ctx* ctx, float* phi, uint32_t* sweep);
+mpr_status mpr_set_state(mpr_ctx* ctx, const float* phi, uint32_t sweep);
+
+/*
+ * Energy bookkeeping: H_exact recomputes Eq. 2 over all bonds; H_tracked is the
+ * value carried incrementally by the sweeps (sum of accepted energy changes).
+ * zmin/zmax/T/e_s report the context's map and temperature (any may be NULL).
+ */
+mpr_status mpr_get_info(mpr_ctx* ctx, double* H_exact, double* H_tracked, double* zmin,
+                        double* zmax, double* T, double* e_s);
+
+/*
+ * Benchmark support: enqueues n sweeps at window a >= 1 as 2n back-to-back half-sweep
+ * launches (no control kernel), timed with CUDA events on the context stream, and
+ * returns the mean duration of one half-sweep launch in milliseconds.  Advances the
+ * state and the sweep counter like mpr_sweep.
+ */
+mpr_status mpr_time_half_sweeps(mpr_ctx* ctx, int n, double a, double* ms_per_launch);
+
+/*
+ * Diagnostics: number of kernels this library has enqueued in the process so far
+ * (direct launches plus the kernels of every replayed CUDA graph).
+ */
+uint64_t mpr_kernel_launches(void);
+
+/*
+ * Test support: Philox4x32-10 on the device.  ctr: uint32[n][4], out: uint32[n][4]
+ * (host or device), key = (seed lo, seed hi).
+ */
+mpr_status mpr_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, size_t n,
+                      void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPR_H_ */

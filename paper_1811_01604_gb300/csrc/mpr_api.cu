@@ -1,0 +1,781 @@
+// mpr_api.cu -- host side of the C ABI declared in include/mpr.h.
+//
+// A context owns a Batch: one or more grids ("entries") laid out as red/black planes
+// (see mpr_internal.cuh) plus their gap lists, per-entry control state and the sweep
+// work lists.  The main fill is a batch of one entry; the e(T, L) table of Eq. 5 is a
+// batch of KT all-free lattices that run together.  Sweeps are driven by CUDA graphs
+// of S sweeps (half-sweep A, half-sweep B, control) replayed until every entry of the
+// relaxation has stopped.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/mpr.h"
+#include "mpr_internal.cuh"
+
+using namespace mpr;
+
+namespace {
+extern std::atomic<unsigned long long> g_launches;
+}
+void mpr::count_launches(unsigned long long n, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (st && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+        return;
+    g_launches += n;
+}
+
+namespace {
+
+constexpr int kGraphSweeps = 8;           // sweeps per captured relaxation graph
+constexpr int kScratch = 2048;            // doubles of reduction scratch
+
+struct GridIn {
+    int W, H;
+    const float* z;       // device, may be null for all-free lattices
+    const uint8_t* mask;  // device, may be null for all-free lattices
+    uint32_t chain;
+    double T;
+    double zmin, scale;
+};
+
+struct Batch {
+    int n_ent = 0;
+    std::vector<EntryDesc> ents;
+    EntryDesc* d_ents = nullptr;
+    float2* d_lat = nullptr;
+    size_t lat_elems = 0;
+    uint32_t* d_gaps = nullptr;
+    float* d_acc = nullptr;
+    size_t n_gaps = 0;
+    BlockWork* d_work[2] = {nullptr, nullptr};
+    int nblk[2] = {0, 0};
+    Part* d_part[2] = {nullptr, nullptr};
+    Ctl* d_ctl = nullptr;
+    double* d_ehist = nullptr;
+    int ehist_stride = 0;
+    int* d_active = nullptr;               // kGraphSweeps counters
+    double* d_scratch = nullptr;
+    double* d_H = nullptr;                 // one exact energy per entry
+    std::map<std::tuple<int, int, int, int, float>, cudaGraphExec_t> graphs;
+};
+
+}  // namespace
+
+struct mpr_ctx {
+    cudaStream_t st = nullptr;
+    cudaStream_t cap = nullptr;            // private stream for graph capture
+    mpr_params prm{};
+    int W = 0, H = 0;
+    float* d_z = nullptr;
+    uint8_t* d_mask = nullptr;
+    float* d_out = nullptr;                // [H][W] staging for outputs
+    double zmin = 0, zmax = 0, scale = 0;
+    long long n_samples = 0;
+    double e_s = 0;
+    long long n_sp = 0;
+    double T = 0;
+    bool T_set = false;
+    Batch b;
+    int* h_active = nullptr;               // pinned
+    std::string err;
+};
+
+namespace {
+
+std::atomic<unsigned long long> g_launches{0};
+std::mutex g_table_mu;
+std::map<std::string, std::pair<std::vector<double>, std::vector<double>>> g_tables;
+
+mpr_status fail(mpr_ctx* c, mpr_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+#define CU(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? MPR_ENOMEM : MPR_ECUDA,  \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));            \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    return cudaMalloc((void**)p, n * sizeof(T));
+}
+
+void batch_free(Batch& b) {
+    for (auto& kv : b.graphs) cudaGraphExecDestroy(kv.second);
+    b.graphs.clear();
+    cudaFree(b.d_ents);
+    cudaFree(b.d_lat);
+    cudaFree(b.d_gaps);
+    cudaFree(b.d_acc);
+    for (int c = 0; c < 2; ++c) {
+        cudaFree(b.d_work[c]);
+        cudaFree(b.d_part[c]);
+    }
+    cudaFree(b.d_ctl);
+    cudaFree(b.d_ehist);
+    cudaFree(b.d_active);
+    cudaFree(b.d_scratch);
+    cudaFree(b.d_H);
+    b = Batch();
+}
+
+// Lays out, packs and indexes a batch of grids.  all_free: every site is a gap.
+mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids, int all_free) {
+    cudaStream_t st = ctx->st;
+    const uint32_t k0 = (uint32_t)ctx->prm.seed, k1 = (uint32_t)(ctx->prm.seed >> 32);
+    b.n_ent = (int)grids.size();
+    b.ents.assign(b.n_ent, EntryDesc{});
+    size_t lat = 0;
+    long long site0 = 0;
+    int maxH = 1;
+    for (int e = 0; e < b.n_ent; ++e) {
+        EntryDesc& E = b.ents[e];
+        E.W = grids[e].W;
+        E.H = grids[e].H;
+        E.pitch = ((E.W / 2 + 2) + 31) & ~31;
+        const size_t plane = (size_t)(E.H + 2) * E.pitch;
+        E.plane[0] = (long long)lat;
+        E.plane[1] = (long long)(lat + plane);
+        lat += 2 * plane;
+        E.chain = grids[e].chain;
+        E.ngp = (double)E.W * (E.H - 1) + (double)E.H * (E.W - 1);
+        E.site0 = site0;
+        site0 += (long long)E.W * E.H;
+        maxH = std::max(maxH, E.H);
+    }
+    b.lat_elems = lat;
+    CU(dalloc(&b.d_lat, lat));
+    CU(cudaMemsetAsync(b.d_lat, 0, lat * sizeof(float2), st));
+    for (int e = 0; e < b.n_ent; ++e)
+        CU(launch_pack(&b.ents[e], grids[e].z, grids[e].mask, grids[e].zmin, grids[e].scale, b.d_lat,
+                       k0, k1, all_free, st));
+    // gap lists: per-row counts, scan, scatter
+    int* d_rows = nullptr;
+    int* d_tot = nullptr;
+    CU(dalloc(&d_rows, (size_t)2 * maxH));
+    CU(dalloc(&d_tot, 2));
+    std::vector<std::vector<int>> row_off(b.n_ent);
+    size_t ng = 0;
+    std::vector<int> tot(2);
+    // counts first (so the gap buffer can be sized), one entry at a time
+    std::vector<std::vector<int>> offs(b.n_ent);
+    for (int e = 0; e < b.n_ent; ++e) {
+        EntryDesc& E = b.ents[e];
+        CU(launch_gap_count(&E, grids[e].mask, all_free, d_rows, st));
+        CU(launch_scan_rows(d_rows, E.H, 2, d_tot, st));
+        offs[e].resize((size_t)2 * E.H);
+        CU(cudaMemcpyAsync(offs[e].data(), d_rows, sizeof(int) * 2 * E.H, cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(tot.data(), d_tot, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        E.ngap[0] = tot[0];
+        E.ngap[1] = tot[1];
+        E.P = tot[0] + tot[1];
+        E.gbase[0] = (long long)ng;
+        E.gbase[1] = (long long)(ng + tot[0]);
+        ng += (size_t)E.P;
+    }
+    b.n_gaps = ng;
+    CU(dalloc(&b.d_gaps, ng));
+    CU(dalloc(&b.d_acc, ng));
+    for (int e = 0; e < b.n_ent; ++e) {
+        EntryDesc& E = b.ents[e];
+        CU(cudaMemcpyAsync(d_rows, offs[e].data(), sizeof(int) * 2 * E.H, cudaMemcpyHostToDevice, st));
+        CU(launch_gap_scatter(&E, grids[e].mask, all_free, d_rows, b.d_gaps, st));
+        CU(cudaStreamSynchronize(st));
+    }
+    cudaFree(d_rows);
+    cudaFree(d_tot);
+    // sweep work lists
+    const int chunk = kSweepThreads * kSweepItems;
+    for (int c = 0; c < 2; ++c) {
+        std::vector<BlockWork> w;
+        for (int e = 0; e < b.n_ent; ++e) {
+            EntryDesc& E = b.ents[e];
+            E.blk0[c] = (int)w.size();
+            const int nb = (E.ngap[c] + chunk - 1) / chunk;
+            E.nblk[c] = nb;
+            for (int i = 0; i < nb; ++i) w.push_back(BlockWork{e, i * chunk});
+        }
+        b.nblk[c] = (int)w.size();
+        CU(dalloc(&b.d_work[c], w.size()));
+        CU(dalloc(&b.d_part[c], w.size()));
+        if (!w.empty())
+            CU(cudaMemcpyAsync(b.d_work[c], w.data(), w.size() * sizeof(BlockWork),
+                               cudaMemcpyHostToDevice, st));
+    }
+    CU(dalloc(&b.d_ents, b.n_ent));
+    CU(cudaMemcpyAsync(b.d_ents, b.ents.data(), b.n_ent * sizeof(EntryDesc), cudaMemcpyHostToDevice, st));
+    std::vector<Ctl> ctl(b.n_ent);
+    for (int e = 0; e < b.n_ent; ++e) {
+        std::memset(&ctl[e], 0, sizeof(Ctl));
+        ctl[e].T = grids[e].T;
+        ctl[e].a = 1.0;
+        ctl[e].k = -1.0;
+    }
+    CU(dalloc(&b.d_ctl, b.n_ent));
+    CU(cudaMemcpyAsync(b.d_ctl, ctl.data(), b.n_ent * sizeof(Ctl), cudaMemcpyHostToDevice, st));
+    b.ehist_stride = ctx->prm.i_max + 2;
+    CU(dalloc(&b.d_ehist, (size_t)b.n_ent * b.ehist_stride));
+    CU(cudaMemsetAsync(b.d_ehist, 0, sizeof(double) * (size_t)b.n_ent * b.ehist_stride, st));
+    CU(dalloc(&b.d_active, kGraphSweeps));
+    CU(dalloc(&b.d_scratch, kScratch + 8));
+    CU(dalloc(&b.d_H, (size_t)b.n_ent));
+    CU(cudaStreamSynchronize(st));
+    return MPR_OK;
+}
+
+SweepArgs sweep_args(const mpr_ctx* ctx, const Batch& b, bool use_ctl_a, double a_fixed,
+                     bool skip_stopped, bool acc) {
+    SweepArgs A;
+    std::memset(&A, 0, sizeof A);
+    A.ents = b.d_ents;
+    A.lat = b.d_lat;
+    A.gaps = b.d_gaps;
+    A.acc = acc ? b.d_acc : nullptr;
+    A.ctl = b.d_ctl;
+    for (int c = 0; c < 2; ++c) {
+        A.part[c] = b.d_part[c];
+        A.work[c] = b.d_work[c];
+        A.nblk[c] = b.nblk[c];
+    }
+    A.use_ctl_a = use_ctl_a ? 1 : 0;
+    A.half_qd_fixed = (float)(0.5 * kTwoPi * ctx->prm.q / a_fixed);
+    A.skip_stopped = skip_stopped ? 1 : 0;
+    A.or_on = ctx->prm.or_mode == MPR_OR_CONSERVING ? 1 : 0;
+    A.key0 = (uint32_t)ctx->prm.seed;
+    A.key1 = (uint32_t)(ctx->prm.seed >> 32);
+    return A;
+}
+
+// Enqueues n sweeps (A, B, control) on stream s.
+mpr_status enqueue_sweeps(mpr_ctx* ctx, Batch& b, cudaStream_t s, int n, int mode, double a_fixed,
+                          bool acc, bool count_active) {
+    const bool relax = mode == CTL_RELAX;
+    const SweepArgs A = sweep_args(ctx, b, relax, a_fixed, relax, acc);
+    const mpr_params& p = ctx->prm;
+    if (count_active) CU(cudaMemsetAsync(b.d_active, 0, sizeof(int) * kGraphSweeps, s));
+    for (int i = 0; i < n; ++i) {
+        CU(launch_half_sweep(A, 0, p.trig_mode, s));
+        CU(launch_half_sweep(A, 1, p.trig_mode, s));
+        CU(launch_control(b.d_ctl, b.d_part, b.d_ents, b.n_ent, mode, p.A_targ, p.k_a, p.n_f,
+                          p.n_fit, p.i_max, b.d_ehist, b.ehist_stride,
+                          count_active ? b.d_active + (i % kGraphSweeps) : nullptr, s));
+    }
+    return MPR_OK;
+}
+
+// Runs n sweeps through a cached CUDA graph of kGraphSweeps sweeps (plus a tail).
+mpr_status run_sweeps(mpr_ctx* ctx, Batch& b, int n, int mode, double a_fixed, bool acc) {
+    if (n <= 0) return MPR_OK;
+    const int S = kGraphSweeps;
+    const bool relax = mode == CTL_RELAX;
+    auto key = std::make_tuple(mode, acc ? 1 : 0, S, ctx->prm.trig_mode, (float)a_fixed);
+    cudaGraphExec_t exec = nullptr;
+    if (n >= S || relax) {
+        auto it = b.graphs.find(key);
+        if (it == b.graphs.end()) {
+            CU(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+            mpr_status s = enqueue_sweeps(ctx, b, ctx->cap, S, mode, a_fixed, acc, relax);
+            cudaGraph_t g = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(ctx->cap, &g);
+            if (s != MPR_OK) {
+                if (g) cudaGraphDestroy(g);
+                return s;
+            }
+            CU(ce);
+            cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
+            cudaGraphDestroy(g);
+            CU(ie);
+            b.graphs[key] = exec;
+        } else {
+            exec = it->second;
+        }
+    }
+    if (relax) {
+        // replay until no entry is still relaxing (each entry stops itself on the slope
+        // test or on i_max; the cap below only guards against a logic error)
+        const long long cap_chunks = (long long)ctx->prm.i_max / S + 4;
+        for (long long ch = 0;; ++ch) {
+            if (ch > cap_chunks)
+                return fail(ctx, MPR_ETIMEOUT, "relaxation did not stop within i_max sweeps");
+            CU(cudaGraphLaunch(exec, ctx->st));
+            count_launches(3ull * S, nullptr);
+            CU(cudaMemcpyAsync(ctx->h_active, b.d_active + (S - 1), sizeof(int),
+                               cudaMemcpyDeviceToHost, ctx->st));
+            CU(cudaStreamSynchronize(ctx->st));
+            if (*ctx->h_active == 0) break;
+        }
+        return MPR_OK;
+    }
+    int done = 0;
+    for (; exec && done + S <= n; done += S) {
+        CU(cudaGraphLaunch(exec, ctx->st));
+        count_launches(3ull * S, nullptr);
+    }
+    return enqueue_sweeps(ctx, b, ctx->st, n - done, mode, a_fixed, acc, false);
+}
+
+// Recomputes Eq. 2 for every entry and makes it the tracked energy.
+mpr_status reset_tracked_energy(mpr_ctx* ctx, Batch& b) {
+    for (int e = 0; e < b.n_ent; ++e)
+        CU(launch_energy(&b.ents[e], b.d_lat, b.d_scratch, kScratch, b.d_H + e, ctx->st));
+    CU(launch_set_tracked_energy(b.d_ctl, b.d_H, b.n_ent, ctx->st));
+    return MPR_OK;
+}
+
+mpr_status read_ctl(mpr_ctx* ctx, Batch& b, std::vector<Ctl>& out) {
+    out.resize(b.n_ent);
+    CU(cudaMemcpyAsync(out.data(), b.d_ctl, sizeof(Ctl) * b.n_ent, cudaMemcpyDeviceToHost, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    return MPR_OK;
+}
+
+// Resets the relaxation state of every entry (Algorithm 2 steps 2.1, 2.3, 2.4).
+mpr_status reset_relax(mpr_ctx* ctx, Batch& b) {
+    std::vector<Ctl> c;
+    mpr_status s = read_ctl(ctx, b, c);
+    if (s != MPR_OK) return s;
+    for (int e = 0; e < b.n_ent; ++e) {
+        c[e].i = 0;
+        c[e].k = -1.0;
+        c[e].a = 1.0;
+        c[e].stop = b.ents[e].P == 0 ? 1 : 0;
+        c[e].converged = 0;
+        c[e].esum = 0.0;
+        c[e].nsamp = 0;
+    }
+    CU(cudaMemcpyAsync(b.d_ctl, c.data(), sizeof(Ctl) * b.n_ent, cudaMemcpyHostToDevice, ctx->st));
+    return reset_tracked_energy(ctx, b);
+}
+
+std::string table_key(const mpr_params& p, int W, int H) {
+    char buf[512];
+    std::snprintf(buf, sizeof buf, "%d|%d|%llu|%.17g|%.17g|%.17g|%d|%d|%d|%d|%d|%.17g|%d|%.17g|%.17g|%d",
+                  W, H, (unsigned long long)p.seed, p.q, p.A_targ, p.k_a, p.n_f, p.n_fit, p.i_max,
+                  p.or_mode, p.trig_mode, p.a_eq, p.KT, p.T_min, p.T_max, p.M_T);
+    return buf;
+}
+
+// Eq. 5 table: KT all-free lattices, relaxed by Algorithm 2 step 5 at their own T_k,
+// then M_T sweeps at a_eq averaging the specific energy.
+mpr_status build_table(mpr_ctx* ctx, int Wt, int Ht, std::vector<double>& Tk,
+                       std::vector<double>& ek) {
+    const mpr_params& p = ctx->prm;
+    Tk.resize(p.KT);
+    ek.resize(p.KT);
+    std::vector<GridIn> g(p.KT);
+    for (int k = 0; k < p.KT; ++k) {
+        Tk[k] = p.T_min * std::pow(p.T_max / p.T_min, (double)k / (double)(p.KT - 1));
+        g[k] = GridIn{Wt, Ht, nullptr, nullptr, 0x80000000u + (uint32_t)k, Tk[k], 0.0, 0.0};
+    }
+    Batch tb;
+    mpr_status s = batch_build(ctx, tb, g, 1);
+    if (s == MPR_OK) s = reset_relax(ctx, tb);
+    if (s == MPR_OK) s = run_sweeps(ctx, tb, 0, CTL_RELAX, 1.0, false);
+    if (s == MPR_OK) s = run_sweeps(ctx, tb, p.M_T, CTL_SAMPLE, p.a_eq, false);
+    std::vector<Ctl> c;
+    if (s == MPR_OK) s = read_ctl(ctx, tb, c);
+    if (s == MPR_OK)
+        for (int k = 0; k < p.KT; ++k) ek[k] = c[k].nsamp ? c[k].esum / c[k].nsamp : 0.0;
+    batch_free(tb);
+    return s;
+}
+
+// T-hat = argmin_T |e_s - e(T, L)|: first bracketing interval from the lowest T,
+// linear in T inside it; otherwise the closest table point.
+double invert_T(const std::vector<double>& Tk, const std::vector<double>& ek, double e_s) {
+    const int K = (int)Tk.size();
+    if (e_s <= ek[0]) return Tk[0];
+    for (int k = 0; k + 1 < K; ++k)
+        if (ek[k] <= e_s && e_s < ek[k + 1])
+            return Tk[k] + (e_s - ek[k]) * (Tk[k + 1] - Tk[k]) / (ek[k + 1] - ek[k]);
+    int best = 0;
+    for (int k = 1; k < K; ++k)
+        if (std::fabs(e_s - ek[k]) < std::fabs(e_s - ek[best])) best = k;
+    return Tk[best];
+}
+
+}  // namespace
+
+extern "C" {
+
+void mpr_default_params(mpr_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->seed = 0;
+    p->q = 0.5;
+    p->A_targ = 0.3;
+    p->k_a = 3.0;
+    p->n_f = 5;
+    p->n_fit = 20;
+    p->i_max = 10000;
+    p->M = 100;
+    p->or_mode = MPR_OR_CONSERVING;
+    p->trig_mode = MPR_TRIG_ACCURATE;
+    p->a_eq = 1.0;
+    p->KT = 16;
+    p->T_min = 1e-4;
+    p->T_max = 1.0;
+    p->T_cap = 1024;
+    p->M_T = 100;
+    p->exec_mode = MPR_EXEC_AUTO;
+    p->chain = 0;
+}
+
+const char* mpr_status_string(mpr_status s) {
+    switch (s) {
+        case MPR_OK: return "MPR_OK";
+        case MPR_EINVAL: return "MPR_EINVAL";
+        case MPR_ENOMEM: return "MPR_ENOMEM";
+        case MPR_ECUDA: return "MPR_ECUDA";
+        case MPR_ENODATA: return "MPR_ENODATA";
+        case MPR_ENOPAIRS: return "MPR_ENOPAIRS";
+        case MPR_ETIMEOUT: return "MPR_ETIMEOUT";
+        case MPR_ENOTEQUIL: return "MPR_ENOTEQUIL";
+        case MPR_ESTATE: return "MPR_ESTATE";
+    }
+    return "MPR_UNKNOWN";
+}
+
+const char* mpr_last_error(const mpr_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void mpr_free(mpr_ctx* ctx) {
+    if (!ctx) return;
+    batch_free(ctx->b);
+    cudaFree(ctx->d_z);
+    cudaFree(ctx->d_mask);
+    cudaFree(ctx->d_out);
+    if (ctx->h_active) cudaFreeHost(ctx->h_active);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    delete ctx;
+}
+
+static mpr_status check_params(const mpr_params* p, std::string& why) {
+    if (!(p->q == 0.5)) { why = "only q = 0.5 is implemented"; return MPR_EINVAL; }
+    if (!(p->A_targ >= 0.0 && p->A_targ <= 1.0)) { why = "A_targ must lie in [0, 1]"; return MPR_EINVAL; }
+    if (!(p->k_a > 0.0)) { why = "k_a must be > 0"; return MPR_EINVAL; }
+    if (p->n_f < 1 || p->n_fit < 2 || p->i_max < 0 || p->M < 1) { why = "n_f >= 1, n_fit >= 2, i_max >= 0, M >= 1"; return MPR_EINVAL; }
+    if (p->i_max > 100000000) { why = "i_max too large"; return MPR_EINVAL; }
+    if (p->or_mode != MPR_OR_CONSERVING && p->or_mode != MPR_OR_NONE) { why = "or_mode"; return MPR_EINVAL; }
+    if (p->trig_mode != MPR_TRIG_ACCURATE && p->trig_mode != MPR_TRIG_FAST) { why = "trig_mode"; return MPR_EINVAL; }
+    if (!(p->a_eq >= 1.0)) { why = "a_eq must be >= 1"; return MPR_EINVAL; }
+    if (p->KT < 2 || !(p->T_min > 0.0) || !(p->T_max > p->T_min) || p->M_T < 1 || p->T_cap < 0) { why = "table parameters"; return MPR_EINVAL; }
+    return MPR_OK;
+}
+
+mpr_status mpr_init(mpr_ctx** out, const float* z, const uint8_t* mask, int W, int H,
+                    const mpr_params* params, void* cuda_stream) {
+    if (!out) return MPR_EINVAL;
+    *out = nullptr;
+    if (!z || !mask || W < 1 || H < 1 || H > 65535 || (W + 1) / 2 > 65535) return MPR_EINVAL;
+    mpr_ctx* ctx = new mpr_ctx();
+    if (params) ctx->prm = *params; else mpr_default_params(&ctx->prm);
+    std::string why;
+    if (check_params(&ctx->prm, why) != MPR_OK) { delete ctx; return MPR_EINVAL; }
+    ctx->st = (cudaStream_t)cuda_stream;
+    ctx->W = W;
+    ctx->H = H;
+    auto bail = [&](mpr_status s) { mpr_free(ctx); return s; };
+    const size_t n = (size_t)W * H;
+#define CUI(call) do { if ((call) != cudaSuccess) { cudaGetLastError(); return bail(MPR_ECUDA); } } while (0)
+    CUI(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
+    CUI(cudaMallocHost((void**)&ctx->h_active, sizeof(int) * 4));
+    if (dalloc(&ctx->d_z, n) != cudaSuccess || dalloc(&ctx->d_mask, n) != cudaSuccess ||
+        dalloc(&ctx->d_out, n) != cudaSuccess) { cudaGetLastError(); return bail(MPR_ENOMEM); }
+    CUI(cudaMemcpyAsync(ctx->d_z, z, n * sizeof(float), cudaMemcpyDefault, ctx->st));
+    CUI(cudaMemcpyAsync(ctx->d_mask, mask, n, cudaMemcpyDefault, ctx->st));
+    // Eq. 1 extremes
+    unsigned* d_keys = nullptr;
+    unsigned long long* d_ns = nullptr;
+    CUI(dalloc(&d_keys, 2));
+    CUI(dalloc(&d_ns, 1));
+    CUI(cudaMemsetAsync(d_keys, 0xFF, sizeof(unsigned), ctx->st));
+    CUI(cudaMemsetAsync(d_keys + 1, 0, sizeof(unsigned), ctx->st));
+    CUI(cudaMemsetAsync(d_ns, 0, sizeof(unsigned long long), ctx->st));
+    CUI(launch_minmax(ctx->d_z, ctx->d_mask, (long long)n, d_keys, d_ns, ctx->st));
+    unsigned keys[2];
+    unsigned long long ns = 0;
+    CUI(cudaMemcpyAsync(keys, d_keys, sizeof keys, cudaMemcpyDeviceToHost, ctx->st));
+    CUI(cudaMemcpyAsync(&ns, d_ns, sizeof ns, cudaMemcpyDeviceToHost, ctx->st));
+    CUI(cudaStreamSynchronize(ctx->st));
+    cudaFree(d_keys);
+    cudaFree(d_ns);
+    auto unkey = [](unsigned k) {
+        const unsigned b = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+        float f;
+        std::memcpy(&f, &b, sizeof f);
+        return (double)f;
+    };
+    ctx->n_samples = (long long)ns;
+    if (ns < 2) return bail(MPR_ENODATA);
+    ctx->zmin = unkey(keys[0]);
+    ctx->zmax = unkey(keys[1]);
+    if (!(ctx->zmax > ctx->zmin) || !std::isfinite(ctx->zmin) || !std::isfinite(ctx->zmax))
+        return bail(MPR_ENODATA);
+    ctx->scale = kTwoPi / (ctx->zmax - ctx->zmin);
+    std::vector<GridIn> g{GridIn{W, H, ctx->d_z, ctx->d_mask, ctx->prm.chain, 0.0, ctx->zmin, ctx->scale}};
+    {
+        const mpr_status bs = batch_build(ctx, ctx->b, g, 0);
+        if (bs != MPR_OK) return bail(bs);
+    }
+    // Eq. 4
+    double* d_ps = nullptr;
+    unsigned long long* d_pc = nullptr;
+    CUI(dalloc(&d_ps, 1024));
+    CUI(dalloc(&d_pc, 1024));
+    int np = 0;
+    CUI(launch_sample_energy(&ctx->b.ents[0], ctx->d_z, ctx->d_mask, ctx->scale, ctx->prm.q, d_ps,
+                             d_pc, &np, ctx->st));
+    std::vector<double> ps(np);
+    std::vector<unsigned long long> pc(np);
+    CUI(cudaMemcpyAsync(ps.data(), d_ps, sizeof(double) * np, cudaMemcpyDeviceToHost, ctx->st));
+    CUI(cudaMemcpyAsync(pc.data(), d_pc, sizeof(unsigned long long) * np, cudaMemcpyDeviceToHost, ctx->st));
+    CUI(cudaStreamSynchronize(ctx->st));
+    cudaFree(d_ps);
+    cudaFree(d_pc);
+    double sum = 0.0;
+    unsigned long long cnt = 0;
+    for (int i = 0; i < np; ++i) { sum += ps[i]; cnt += pc[i]; }
+    ctx->n_sp = (long long)cnt;
+    ctx->e_s = cnt ? -sum / (double)cnt : 0.0;
+#undef CUI
+    *out = ctx;
+    return MPR_OK;
+}
+
+mpr_status mpr_set_T(mpr_ctx* ctx, double T) {
+    if (!ctx) return MPR_EINVAL;
+    if (!(T > 0.0) || !std::isfinite(T)) return fail(ctx, MPR_EINVAL, "T must be positive");
+    std::vector<Ctl> c;
+    mpr_status s = read_ctl(ctx, ctx->b, c);
+    if (s != MPR_OK) return s;
+    for (auto& x : c) x.T = T;
+    CU(cudaMemcpyAsync(ctx->b.d_ctl, c.data(), sizeof(Ctl) * c.size(), cudaMemcpyHostToDevice, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    ctx->T = T;
+    ctx->T_set = true;
+    return MPR_OK;
+}
+
+mpr_status mpr_estimate_T(mpr_ctx* ctx, double* T_hat, double* e_s) {
+    if (!ctx) return MPR_EINVAL;
+    if (ctx->n_sp == 0) return fail(ctx, MPR_ENOPAIRS, "no nearest-neighbour sample pairs");
+    const mpr_params& p = ctx->prm;
+    const int Wt = p.T_cap > 0 ? std::min(ctx->W, p.T_cap) : ctx->W;
+    const int Ht = p.T_cap > 0 ? std::min(ctx->H, p.T_cap) : ctx->H;
+    std::vector<double> Tk, ek;
+    const std::string key = table_key(p, Wt, Ht);
+    {
+        std::lock_guard<std::mutex> lk(g_table_mu);
+        auto it = g_tables.find(key);
+        if (it != g_tables.end()) {
+            Tk = it->second.first;
+            ek = it->second.second;
+        }
+    }
+    if (Tk.empty()) {
+        mpr_status s = build_table(ctx, Wt, Ht, Tk, ek);
+        if (s != MPR_OK) return s;
+        std::lock_guard<std::mutex> lk(g_table_mu);
+        g_tables[key] = std::make_pair(Tk, ek);
+    }
+    const double T = invert_T(Tk, ek, ctx->e_s);
+    mpr_status s = mpr_set_T(ctx, T);
+    if (s != MPR_OK) return s;
+    if (T_hat) *T_hat = T;
+    if (e_s) *e_s = ctx->e_s;
+    return MPR_OK;
+}
+
+mpr_status mpr_sweep(mpr_ctx* ctx, int n, double a, mpr_sweep_stats* out) {
+    if (!ctx) return MPR_EINVAL;
+    if (n < 0 || !(a >= 1.0)) return fail(ctx, MPR_EINVAL, "n >= 0 and a >= 1 required");
+    if (!ctx->T_set) return fail(ctx, MPR_ESTATE, "temperature not set");
+    mpr_status s = reset_tracked_energy(ctx, ctx->b);
+    if (s == MPR_OK) s = run_sweeps(ctx, ctx->b, n, CTL_FIXED, a, false);
+    std::vector<Ctl> c;
+    if (s == MPR_OK) s = read_ctl(ctx, ctx->b, c);
+    if (s != MPR_OK) return s;
+    if (out) {
+        out->sweeps = n;
+        out->acceptance = c[0].A_last;
+        out->e = c[0].e_last;
+    }
+    return MPR_OK;
+}
+
+mpr_status mpr_equilibrate(mpr_ctx* ctx, mpr_equil_stats* out) {
+    if (!ctx) return MPR_EINVAL;
+    if (!ctx->T_set) return fail(ctx, MPR_ESTATE, "temperature not set");
+    mpr_status s = reset_relax(ctx, ctx->b);
+    if (s == MPR_OK) s = run_sweeps(ctx, ctx->b, 0, CTL_RELAX, 1.0, false);
+    std::vector<Ctl> c;
+    if (s == MPR_OK) s = read_ctl(ctx, ctx->b, c);
+    if (s != MPR_OK) return s;
+    if (out) {
+        out->sweeps = c[0].i;
+        out->a = c[0].a;
+        out->k = c[0].k;
+        out->A_last = c[0].A_last;
+        out->e_last = c[0].e_last;
+        out->converged = c[0].converged;
+    }
+    return (c[0].converged || ctx->b.ents[0].P == 0) ? MPR_OK : MPR_ENOTEQUIL;
+}
+
+mpr_status mpr_predict(mpr_ctx* ctx, int M, float* zhat) {
+    if (!ctx || !zhat) return MPR_EINVAL;
+    if (M < 1) return fail(ctx, MPR_EINVAL, "M >= 1 required");
+    if (!ctx->T_set) return fail(ctx, MPR_ESTATE, "temperature not set");
+    Batch& b = ctx->b;
+    const size_t n = (size_t)ctx->W * ctx->H;
+    CU(cudaMemsetAsync(b.d_acc, 0, sizeof(float) * std::max<size_t>(b.n_gaps, 1), ctx->st));
+    mpr_status s = run_sweeps(ctx, b, M, CTL_FIXED, ctx->prm.a_eq, true);
+    if (s != MPR_OK) return s;
+    CU(cudaMemcpyAsync(ctx->d_out, ctx->d_z, n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->st));
+    CU(launch_predict_out(&b.ents[0], b.d_lat, b.d_gaps, b.d_acc, M, ctx->prm.q, ctx->zmin, ctx->zmax,
+                          ctx->d_out, ctx->st));
+    CU(cudaMemcpyAsync(zhat, ctx->d_out, n * sizeof(float), cudaMemcpyDefault, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    return MPR_OK;
+}
+
+mpr_status mpr_fill(mpr_ctx* ctx, float* zhat, mpr_equil_stats* stats) {
+    if (!ctx || !zhat) return MPR_EINVAL;
+    mpr_status s = MPR_OK;
+    if (!ctx->T_set) s = mpr_estimate_T(ctx, nullptr, nullptr);
+    if (s != MPR_OK) return s;
+    mpr_status eq = mpr_equilibrate(ctx, stats);
+    if (eq != MPR_OK && eq != MPR_ENOTEQUIL) return eq;
+    s = mpr_predict(ctx, ctx->prm.M, zhat);
+    return s != MPR_OK ? s : eq;
+}
+
+mpr_status mpr_get_state(mpr_ctx* ctx, float* phi, uint32_t* sweep) {
+    if (!ctx || !phi) return MPR_EINVAL;
+    const size_t n = (size_t)ctx->W * ctx->H;
+    CU(launch_get_state(&ctx->b.ents[0], ctx->b.d_lat, ctx->d_out, ctx->st));
+    CU(cudaMemcpyAsync(phi, ctx->d_out, n * sizeof(float), cudaMemcpyDefault, ctx->st));
+    std::vector<Ctl> c;
+    mpr_status s = read_ctl(ctx, ctx->b, c);
+    if (s != MPR_OK) return s;
+    if (sweep) *sweep = c[0].sweep;
+    return MPR_OK;
+}
+
+mpr_status mpr_set_state(mpr_ctx* ctx, const float* phi, uint32_t sweep) {
+    if (!ctx || !phi) return MPR_EINVAL;
+    const size_t n = (size_t)ctx->W * ctx->H;
+    CU(cudaMemcpyAsync(ctx->d_out, phi, n * sizeof(float), cudaMemcpyDefault, ctx->st));
+    CU(launch_set_state(&ctx->b.ents[0], ctx->b.d_lat, ctx->b.d_gaps, ctx->d_out, ctx->st));
+    std::vector<Ctl> c;
+    mpr_status s = read_ctl(ctx, ctx->b, c);
+    if (s != MPR_OK) return s;
+    c[0].sweep = sweep;
+    CU(cudaMemcpyAsync(ctx->b.d_ctl, c.data(), sizeof(Ctl), cudaMemcpyHostToDevice, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    return MPR_OK;
+}
+
+mpr_status mpr_get_info(mpr_ctx* ctx, double* H_exact, double* H_tracked, double* zmin,
+                        double* zmax, double* T, double* e_s) {
+    if (!ctx) return MPR_EINVAL;
+    if (H_exact) {
+        double* d = ctx->b.d_scratch + kScratch;
+        CU(launch_energy(&ctx->b.ents[0], ctx->b.d_lat, ctx->b.d_scratch, kScratch, d, ctx->st));
+        CU(cudaMemcpyAsync(H_exact, d, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    }
+    std::vector<Ctl> c;
+    mpr_status s = read_ctl(ctx, ctx->b, c);
+    if (s != MPR_OK) return s;
+    if (H_tracked) *H_tracked = c[0].H;
+    if (zmin) *zmin = ctx->zmin;
+    if (zmax) *zmax = ctx->zmax;
+    if (T) *T = ctx->T;
+    if (e_s) *e_s = ctx->e_s;
+    return MPR_OK;
+}
+
+uint64_t mpr_kernel_launches(void) { return (uint64_t)g_launches.load(); }
+
+mpr_status mpr_time_half_sweeps(mpr_ctx* ctx, int n, double a, double* ms_per_launch) {
+    if (!ctx || n < 1 || !(a >= 1.0) || !ms_per_launch) return MPR_EINVAL;
+    if (!ctx->T_set) return fail(ctx, MPR_ESTATE, "temperature not set");
+    Batch& b = ctx->b;
+    const SweepArgs A = sweep_args(ctx, b, false, a, false, false);
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    CU(cudaEventRecord(e0, ctx->st));
+    for (int i = 0; i < n; ++i) {
+        CU(launch_half_sweep(A, 0, ctx->prm.trig_mode, ctx->st));
+        CU(launch_half_sweep(A, 1, ctx->prm.trig_mode, ctx->st));
+        // advance the sweep counter (and fold the partials) between sweeps
+        CU(launch_control(b.d_ctl, b.d_part, b.d_ents, b.n_ent, CTL_FIXED, ctx->prm.A_targ,
+                          ctx->prm.k_a, ctx->prm.n_f, ctx->prm.n_fit, ctx->prm.i_max, b.d_ehist,
+                          b.ehist_stride, nullptr, ctx->st));
+    }
+    CU(cudaEventRecord(e1, ctx->st));
+    CU(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, e0, e1));
+    // time of the small control kernels, measured the same way, is subtracted
+    CU(cudaEventRecord(e0, ctx->st));
+    for (int i = 0; i < n; ++i)
+        CU(launch_control(b.d_ctl, b.d_part, b.d_ents, b.n_ent, CTL_FIXED, ctx->prm.A_targ,
+                          ctx->prm.k_a, ctx->prm.n_f, ctx->prm.n_fit, ctx->prm.i_max, b.d_ehist,
+                          b.ehist_stride, nullptr, ctx->st));
+    CU(cudaEventRecord(e1, ctx->st));
+    CU(cudaEventSynchronize(e1));
+    float ms_ctl = 0.f;
+    CU(cudaEventElapsedTime(&ms_ctl, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the extra control launches advanced the counter: step it back
+    std::vector<Ctl> c;
+    mpr_status s = read_ctl(ctx, b, c);
+    if (s != MPR_OK) return s;
+    for (auto& x : c) x.sweep -= (uint32_t)n;
+    CU(cudaMemcpyAsync(b.d_ctl, c.data(), sizeof(Ctl) * c.size(), cudaMemcpyHostToDevice, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    *ms_per_launch = (double)(ms - ms_ctl) / (2.0 * n);
+    return MPR_OK;
+}
+
+mpr_status mpr_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, size_t n,
+                      void* cuda_stream) {
+    if ((!ctr || !out) && n) return MPR_EINVAL;
+    if (n == 0) return MPR_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    uint4* d_in = nullptr;
+    uint4* d_out = nullptr;
+    if (cudaMalloc((void**)&d_in, n * sizeof(uint4)) != cudaSuccess) return MPR_ENOMEM;
+    if (cudaMalloc((void**)&d_out, n * sizeof(uint4)) != cudaSuccess) { cudaFree(d_in); return MPR_ENOMEM; }
+    mpr_status s = MPR_OK;
+    if (cudaMemcpyAsync(d_in, ctr, n * sizeof(uint4), cudaMemcpyDefault, st) != cudaSuccess ||
+        launch_philox(d_in, (uint32_t)seed, (uint32_t)(seed >> 32), d_out, n, st) != cudaSuccess ||
+        cudaMemcpyAsync(out, d_out, n * sizeof(uint4), cudaMemcpyDefault, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        s = MPR_ECUDA;
+    cudaFree(d_in);
+    cudaFree(d_out);
+    return s;
+}
+
+}  // extern "C"

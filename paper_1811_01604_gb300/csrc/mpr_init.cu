@@ -1,0 +1,258 @@
+// mpr_init.cu -- set-up kernels: Eq. 1 map, lattice packing, gap lists, Eq. 4.
+//
+// These run once per grid (Algorithm 2, steps 2-4.1); the hot path is in mpr_sweep.cu.
+#include "mpr_internal.cuh"
+
+namespace mpr {
+namespace {
+
+constexpr int kThreads = 256;
+
+// Order-preserving map of a float to an unsigned key (for atomicMin/atomicMax).
+__device__ __forceinline__ unsigned float_key(float f) {
+    const unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// z_min, z_max and the number of samples over one grid (Eq. 1 needs the extremes).
+__global__ void k_minmax(const float* __restrict__ z, const uint8_t* __restrict__ mask,
+                         long long n, unsigned* keys, unsigned long long* nsamples) {
+    unsigned kmin = 0xFFFFFFFFu, kmax = 0u, cnt = 0u;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (mask[i]) {
+            const unsigned k = float_key(z[i]);
+            kmin = min(kmin, k);
+            kmax = max(kmax, k);
+            ++cnt;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+        kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+    }
+    cnt = warp_sum(cnt);
+    if ((threadIdx.x & 31) == 0) {
+        if (cnt) {
+            atomicMin(&keys[0], kmin);
+            atomicMax(&keys[1], kmax);
+            atomicAdd(nsamples, (unsigned long long)cnt);
+        }
+    }
+}
+
+// Packs one grid into its two colour planes.  Samples get the Eq. 1 angle; gap sites
+// get phi = 2 pi u with u from the Philox stream {site, 0xFFFFFFFF, chain, 0}
+// (Algorithm 2, step 2.2).  Stored as (cos(phi/2), sin(phi/2)).
+__global__ void k_pack(EntryDesc e, const float* __restrict__ z, const uint8_t* __restrict__ mask,
+                       double zmin, double scale, float2* __restrict__ lat, uint32_t key0,
+                       uint32_t key1, int all_free) {
+    const long long n = (long long)e.W * e.H;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(i / e.W), x = (int)(i - (long long)y * e.W);
+        const int c = (x + y) & 1;
+        float theta;
+        if (!all_free && mask[i]) {
+            const double phi = ((double)z[i] - zmin) * scale;          // Eq. 1
+            theta = (float)(0.5 * phi);
+        } else {
+            const uint4 r = philox10(make_uint4((uint32_t)i, kInitSweep, e.chain, 0u), key0, key1);
+            theta = (float)(3.141592653589793 * (double)u24f(r.x));    // q * 2 pi u
+        }
+        float s, co;
+        sincosf(theta, &s, &co);
+        const long long base = c ? e.plane[1] : e.plane[0];
+        lat[base + (long long)(y + 1) * e.pitch + (x >> 1) + 1] = make_float2(co, s);
+    }
+}
+
+// Number of gap sites of each colour in each row: row_counts[c * H + y].  One warp per row.
+__global__ void k_gap_count(EntryDesc e, const uint8_t* __restrict__ mask, int all_free,
+                            int* __restrict__ row_counts) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= e.H) return;
+    const int y = warp;
+    int cnt[2] = {0, 0};
+    for (int x0 = 0; x0 < e.W; x0 += 32) {
+        const int x = x0 + lane;
+        const bool gap = x < e.W && (all_free || !mask[(long long)y * e.W + x]);
+        const unsigned b = __ballot_sync(0xffffffffu, gap);
+        // lanes with (x + y) even are colour 0
+        const unsigned even = ((x0 + y) & 1) ? 0xAAAAAAAAu : 0x55555555u;
+        cnt[0] += __popc(b & even);
+        cnt[1] += __popc(b & ~even);
+    }
+    if (lane == 0) {
+        row_counts[y] = cnt[0];
+        row_counts[e.H + y] = cnt[1];
+    }
+}
+
+// In-place exclusive scan of narrays consecutive arrays of nrows ints (one block each);
+// totals[a] receives the sum of array a.
+__global__ void k_scan_rows(int* __restrict__ v, int nrows, int* __restrict__ totals) {
+    __shared__ int part[1024];
+    int* a = v + (long long)blockIdx.x * nrows;
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int chunk = (nrows + nt - 1) / nt;
+    const int b = min(nrows, t * chunk), e = min(nrows, b + chunk);
+    int s = 0;
+    for (int i = b; i < e; ++i) s += a[i];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < nt; o <<= 1) {            // Hillis-Steele inclusive scan
+        const int add = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += add;
+        __syncthreads();
+    }
+    int run = t ? part[t - 1] : 0;
+    for (int i = b; i < e; ++i) {
+        const int c = a[i];
+        a[i] = run;
+        run += c;
+    }
+    if (t == nt - 1) totals[blockIdx.x] = part[t];
+}
+
+// Writes the gap lists, row-major, as (y << 16) | j.  One warp per row.
+__global__ void k_gap_scatter(EntryDesc e, const uint8_t* __restrict__ mask, int all_free,
+                              const int* __restrict__ row_off, uint32_t* __restrict__ gaps) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= e.H) return;
+    const int y = warp;
+    int pos0 = row_off[y], pos1 = row_off[e.H + y];
+    const unsigned lt = (1u << lane) - 1u;
+    for (int x0 = 0; x0 < e.W; x0 += 32) {
+        const int x = x0 + lane;
+        const bool gap = x < e.W && (all_free || !mask[(long long)y * e.W + x]);
+        const unsigned b = __ballot_sync(0xffffffffu, gap);
+        const unsigned even = ((x0 + y) & 1) ? 0xAAAAAAAAu : 0x55555555u;
+        const int c = (x + y) & 1;
+        const unsigned mine = c ? (b & ~even) : (b & even);
+        if (gap) {
+            const long long at = c ? e.gbase[1] + pos1 : e.gbase[0] + pos0;
+            gaps[at + __popc(mine & lt)] = ((uint32_t)y << 16) | (uint32_t)(x >> 1);
+        }
+        pos0 += __popc(b & even);
+        pos1 += __popc(b & ~even);
+    }
+}
+
+// Eq. 4: sum over nearest-neighbour sample pairs (each once: right and down partner) of
+// cos(q (phi_i - phi_j)), with phi_i - phi_j = (z_i - z_j) * 2pi / (z_max - z_min).
+// Each block writes its partial sums; they are added in block order afterwards.
+__global__ void k_sample_energy(EntryDesc e, const float* __restrict__ z,
+                                const uint8_t* __restrict__ mask, double scale, double q,
+                                double* part_sum, unsigned long long* part_cnt) {
+    __shared__ double ssum[kThreads / 32];
+    __shared__ unsigned scnt[kThreads / 32];
+    const long long n = (long long)e.W * e.H;
+    double acc = 0.0;
+    unsigned cnt = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (!mask[i]) continue;
+        const int y = (int)(i / e.W), x = (int)(i - (long long)y * e.W);
+        const double zi = (double)z[i];
+        if (x + 1 < e.W && mask[i + 1]) {
+            acc += (double)cosf((float)(q * ((zi - (double)z[i + 1]) * scale)));
+            ++cnt;
+        }
+        if (y + 1 < e.H && mask[i + e.W]) {
+            acc += (double)cosf((float)(q * ((zi - (double)z[i + e.W]) * scale)));
+            ++cnt;
+        }
+    }
+    acc = warp_sum(acc);
+    cnt = warp_sum(cnt);
+    if ((threadIdx.x & 31) == 0) {
+        ssum[threadIdx.x >> 5] = acc;
+        scnt[threadIdx.x >> 5] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        unsigned long long c = 0;
+        for (int w = 0; w < kThreads / 32; ++w) { t += ssum[w]; c += scnt[w]; }
+        part_sum[blockIdx.x] = t;
+        part_cnt[blockIdx.x] = c;
+    }
+}
+
+__global__ void k_philox(const uint4* __restrict__ ctr, uint32_t k0, uint32_t k1,
+                         uint4* __restrict__ out, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = philox10(ctr[i], k0, k1);
+}
+
+int grid_for(long long n) {
+    long long b = (n + kThreads - 1) / kThreads;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_minmax(const float* z, const uint8_t* mask, long long n, unsigned* keys,
+                          unsigned long long* nsamples, cudaStream_t st) {
+    count_launches(1, st);
+    k_minmax<<<grid_for(n), kThreads, 0, st>>>(z, mask, n, keys, nsamples);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const EntryDesc* e, const float* z, const uint8_t* mask, double zmin,
+                        double scale, float2* lat, uint32_t key0, uint32_t key1, int all_free,
+                        cudaStream_t st) {
+    count_launches(1, st);
+    k_pack<<<grid_for((long long)e->W * e->H), kThreads, 0, st>>>(*e, z, mask, zmin, scale, lat,
+                                                                   key0, key1, all_free);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gap_count(const EntryDesc* e, const uint8_t* mask, int all_free,
+                             int* row_counts, cudaStream_t st) {
+    const int blocks = (e->H * 32 + kThreads - 1) / kThreads;
+    count_launches(1, st);
+    k_gap_count<<<blocks, kThreads, 0, st>>>(*e, mask, all_free, row_counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_rows(int* row_counts, int nrows, int narrays, int* totals,
+                             cudaStream_t st) {
+    count_launches(1, st);
+    k_scan_rows<<<narrays, 1024, 0, st>>>(row_counts, nrows, totals);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gap_scatter(const EntryDesc* e, const uint8_t* mask, int all_free,
+                               const int* row_offsets, uint32_t* gaps, cudaStream_t st) {
+    const int blocks = (e->H * 32 + kThreads - 1) / kThreads;
+    count_launches(1, st);
+    k_gap_scatter<<<blocks, kThreads, 0, st>>>(*e, mask, all_free, row_offsets, gaps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_energy(const EntryDesc* e, const float* z, const uint8_t* mask,
+                                 double scale, double q, double* part_sum,
+                                 unsigned long long* part_cnt, int* nparts, cudaStream_t st) {
+    int g = grid_for((long long)e->W * e->H);
+    if (g > 1024) g = 1024;
+    *nparts = g;
+    count_launches(1, st);
+    k_sample_energy<<<g, kThreads, 0, st>>>(*e, z, mask, scale, q, part_sum, part_cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, size_t n,
+                          cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    count_launches(1, st);
+    k_philox<<<grid_for((long long)n), kThreads, 0, st>>>(ctr, k0, k1, out, n);
+    return cudaGetLastError();
+}
+
+}  // namespace mpr

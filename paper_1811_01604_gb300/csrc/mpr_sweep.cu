@@ -1,0 +1,400 @@
+// mpr_sweep.cu -- the hot path: checkerboard half-sweeps of the hybrid update
+// (Algorithm 1 with the over-relaxation of Eq. 6), the per-sweep control of
+// Algorithm 2 step 5, the energy (Eq. 2), and the equilibrium averaging with the
+// inverse of Eq. 1 (Algorithm 2 steps 6-7).
+#include "mpr_internal.cuh"
+
+namespace mpr {
+namespace {
+
+enum { TRIG_ACCURATE = 0, TRIG_FAST = 1 };
+
+// One gap-site update (Algorithm 1) in unit-vector form, q = 1/2, theta = phi/2 in [0, pi).
+//   v        current (cos theta, sin theta) of the site
+//   C, S     local field: sums of the neighbours' cos/sin
+//   hq       half the proposal rotation, q * 2 pi (u - 1/2) / a / 2
+//   r        acceptance uniform
+// Returns the accepted energy change (0 if rejected) and writes the new vector.
+template <int TRIG>
+__device__ __forceinline__ float hybrid_update(float2& v, float C, float S, float hq, float r,
+                                               float neg_inv_T, int or_on, bool& accepted) {
+    float c = v.x, s = v.y;
+    // R cos(theta - psi) and R sin(theta - psi), psi the direction of the field
+    const float along = fmaf(c, C, s * S);
+    float perp = fmaf(s, C, -(c * S));
+    // Eq. 6 (energy-conserving reading): reflect theta about psi; keep it only if the
+    // image stays in [0, pi), i.e. sin >= 0 (the point theta = pi is excluded).
+    const float R2 = fmaf(C, C, S * S);
+    if (or_on && R2 > 1e-12f) {
+        const float f = (TRIG == TRIG_FAST) ? __fdividef(2.0f * along, R2) : (2.0f * along) / R2;
+        const float cr = fmaf(f, C, -c), sr = fmaf(f, S, -s);
+        if (sr > 0.0f || (sr == 0.0f && cr > 0.0f)) {
+            c = cr;
+            s = sr;
+            perp = -perp;          // the reflection keeps `along` and flips `perp`
+        }
+    }
+    // proposal: rotate by 2*hq (steps 2-3); 1 - cos and sin of the rotation from the half angle
+    float sh, ch;
+    if (TRIG == TRIG_FAST) {
+        __sincosf(hq, &sh, &ch);
+    } else {
+        sincos_quarter(hq, &sh, &ch);
+    }
+    const float sn = 2.0f * sh * ch;
+    const float hh = 2.0f * sh * sh;
+    // step 4: dH = R [cos(theta - psi) - cos(theta + 2hq - psi)]
+    float dH = fmaf(hh, along, sn * perp);
+    float c2 = c - fmaf(c, hh, s * sn);
+    float s2 = s - fmaf(s, hh, -(c * sn));
+    // modulo 2 pi in phi is a half turn in theta: negate the vector, dH -> 2 along - dH
+    if (s2 < 0.0f || (s2 == 0.0f && c2 < 0.0f)) {
+        c2 = -c2;
+        s2 = -s2;
+        dH = 2.0f * along - dH;
+    }
+    // steps 5-6: accept if min(1, exp(-dH/T)) > r
+    const float x = dH * neg_inv_T;
+    const float ap = (TRIG == TRIG_FAST) ? __expf(x) : expf(x);
+    accepted = (dH <= 0.0f) || (ap > r);
+    if (accepted) {
+        c = c2;
+        s = s2;
+    }
+    // one Newton step back to unit length (rounding drift of reflections and rotations)
+    const float g = fmaf(-0.5f, fmaf(c, c, s * s), 1.5f);
+    v = make_float2(c * g, s * g);
+    return accepted ? dH : 0.0f;
+}
+
+// Half-sweep: every gap site of one colour (all entries), Algorithm 1.
+// Blocks come from a work list (entry, first gap) so that grids of any size share a launch.
+template <int TRIG, bool ACC>
+__global__ void __launch_bounds__(kSweepThreads)
+k_half_sweep(const SweepArgs A, const int color) {
+    const BlockWork w = (color ? A.work[1] : A.work[0])[blockIdx.x];
+    const EntryDesc* __restrict__ E = A.ents + w.entry;
+    const Ctl* ctl = A.ctl + w.entry;
+    if (A.skip_stopped && ctl->stop) return;
+    const float half_qd = A.use_ctl_a ? (float)(0.5 * kTwoPi * 0.5 / ctl->a) : A.half_qd_fixed;
+    const float neg_inv_T = (float)(-1.0 / ctl->T);
+    const uint32_t sweep = ctl->sweep;
+    const int n = color ? E->ngap[1] : E->ngap[0], pitch = E->pitch, W = E->W;
+    const uint32_t chain = E->chain;
+    const long long gb = color ? E->gbase[1] : E->gbase[0];
+    const uint32_t* __restrict__ gl = A.gaps + gb;
+    float2* __restrict__ own = A.lat + (color ? E->plane[1] : E->plane[0]);
+    const float2* __restrict__ oth = A.lat + (color ? E->plane[0] : E->plane[1]);
+    float* __restrict__ acc = ACC ? A.acc + gb : nullptr;
+
+    float dE = 0.0f;
+    unsigned nacc = 0;
+#pragma unroll
+    for (int it = 0; it < kSweepItems; ++it) {
+        const int g = w.first + it * kSweepThreads + (int)threadIdx.x;
+        if (g < n) {
+            const uint32_t ent = __ldg(gl + g);
+            const int y = (int)(ent >> 16), j = (int)(ent & 0xFFFFu);
+            const int s = color ^ (y & 1);
+            const long long k = (long long)(y + 1) * pitch + j + 1;
+            const float2 nu = oth[k - pitch], nd = oth[k + pitch];
+            const float2 nl = oth[k - 1 + s], nr = oth[k + s];
+            const float C = (nu.x + nd.x) + (nl.x + nr.x);
+            const float S = (nu.y + nd.y) + (nl.y + nr.y);
+            float2 v = own[k];
+            const uint32_t site = (uint32_t)y * (uint32_t)W + (uint32_t)(2 * j + s);
+            const uint4 rnd = philox10(make_uint4(site, sweep, chain, 0u), A.key0, A.key1);
+            const float hq = (u24f(rnd.x) - 0.5f) * half_qd;
+            bool accepted;
+            dE += hybrid_update<TRIG>(v, C, S, hq, u24f(rnd.y), neg_inv_T, A.or_on, accepted);
+            nacc += accepted ? 1u : 0u;
+            own[k] = v;
+            if (ACC) acc[g] += atan2f(v.y, v.x);
+        }
+    }
+    // energy change and acceptance count: warp shuffle, then a fixed-order block sum
+    __shared__ float s_dE[kSweepThreads / 32];
+    __shared__ unsigned s_na[kSweepThreads / 32];
+    dE = warp_sum(dE);
+    nacc = warp_sum(nacc);
+    if ((threadIdx.x & 31) == 0) {
+        s_dE[threadIdx.x >> 5] = dE;
+        s_na[threadIdx.x >> 5] = nacc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        unsigned na = 0;
+#pragma unroll
+        for (int i = 0; i < kSweepThreads / 32; ++i) { t += (double)s_dE[i]; na += s_na[i]; }
+        Part p;
+        p.dH = t;
+        p.nacc = na;
+        p._pad = 0;
+        (color ? A.part[1] : A.part[0])[blockIdx.x] = p;
+    }
+}
+
+// Per-sweep control, one block per entry.  The block first adds the sweep blocks'
+// partials of this entry in a fixed order (bitwise reproducible), then thread 0 runs
+//   CTL_RELAX : Algorithm 2 step 5 after one sweep (window 5.2, energy 5.3, slope 5.4, 5.5)
+//   CTL_FIXED : bookkeeping of a fixed-window sweep (energy, acceptance, counter)
+//   CTL_SAMPLE: as FIXED, and accumulate e for the e(T, L) table average
+constexpr int kCtlThreads = 128;
+__global__ void __launch_bounds__(kCtlThreads)
+k_control(Ctl* ctl, Part* part0, Part* part1, const EntryDesc* __restrict__ ents, int mode,
+          double A_targ, double k_a, int n_f, int n_fit, int i_max, double* ehist,
+          int ehist_stride, int* active) {
+    __shared__ double s_dH[kCtlThreads];
+    __shared__ unsigned long long s_na[kCtlThreads];
+    const int e = blockIdx.x;
+    const EntryDesc E = ents[e];
+    double dH = 0.0;
+    unsigned long long na = 0;
+    for (int c = 0; c < 2; ++c) {
+        const Part* p = c ? part1 + E.blk0[1] : part0 + E.blk0[0];
+        const int nb = c ? E.nblk[1] : E.nblk[0];
+        for (int b = threadIdx.x; b < nb; b += kCtlThreads) {
+            dH += p[b].dH;
+            na += p[b].nacc;
+        }
+    }
+    s_dH[threadIdx.x] = dH;
+    s_na[threadIdx.x] = na;
+    __syncthreads();
+    for (int o = kCtlThreads / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            s_dH[threadIdx.x] += s_dH[threadIdx.x + o];
+            s_na[threadIdx.x] += s_na[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    dH = s_dH[0];
+    na = s_na[0];
+    Ctl c = ctl[e];
+    if (mode == CTL_RELAX) {
+        if (!c.stop) {
+            c.H += dH;
+            const double A = E.P ? (double)na / (double)E.P : 0.0;
+            if (A < A_targ) c.a = 1.0 + (double)(c.i + 1) / k_a;          // 5.2
+            const double en = c.H / E.ngp;                                 // 5.3
+            double* eh = ehist + (long long)e * ehist_stride;
+            eh[c.i + 1] = en;
+            if (c.i >= n_fit && c.i % n_f == 0) {                          // 5.4
+                const double* w = eh + (c.i + 2 - n_fit);
+                const double tbar = 0.5 * (double)(n_fit - 1);
+                double ebar = 0.0;
+                for (int t = 0; t < n_fit; ++t) ebar += w[t];
+                ebar /= (double)n_fit;
+                double num = 0.0, den = 0.0;
+                for (int t = 0; t < n_fit; ++t) {
+                    const double dt = (double)t - tbar;
+                    num += dt * (w[t] - ebar);
+                    den += dt * dt;
+                }
+                c.k = num / den;
+            }
+            c.i += 1;                                                      // 5.5
+            c.sweep += 1u;
+            c.A_last = A;
+            c.e_last = en;
+            if (!(c.k < 0.0 && c.i <= i_max)) {
+                c.stop = 1;
+                c.converged = c.k >= 0.0 ? 1 : 0;
+            }
+        }
+    } else {
+        c.H += dH;
+        c.A_last = E.P ? (double)na / (double)E.P : 0.0;
+        c.e_last = c.H / E.ngp;
+        if (mode == CTL_SAMPLE) {
+            c.esum += c.e_last;
+            c.nsamp += 1;
+        }
+        c.sweep += 1u;
+    }
+    ctl[e] = c;
+    if (active && !c.stop) atomicAdd(active, 1);
+}
+
+// Eq. 2 over all bonds of one grid: each colour-0 site with its four colour-1 neighbours
+// (padding contributes 0).  cos(theta_i - theta_j) = c_i c_j + s_i s_j.  One partial per block.
+__global__ void k_energy(EntryDesc e, const float2* __restrict__ lat, double* part) {
+    __shared__ double sw[8];
+    const int Wc = (e.W + 1) >> 1;
+    const long long n = (long long)e.H * Wc;
+    const float2* p0 = lat + e.plane[0];
+    const float2* p1 = lat + e.plane[1];
+    double acc = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(t / Wc), j = (int)(t - (long long)y * Wc);
+        const int s = y & 1;                                     // colour 0: s = y & 1
+        if (2 * j + s >= e.W) continue;
+        const long long k = (long long)(y + 1) * e.pitch + j + 1;
+        const float2 v = p0[k];
+        const float2 a = p1[k - e.pitch], b = p1[k + e.pitch], l = p1[k - 1 + s], r = p1[k + s];
+        acc -= (double)fmaf(v.x, a.x, v.y * a.y) + (double)fmaf(v.x, b.x, v.y * b.y) +
+               (double)fmaf(v.x, l.x, v.y * l.y) + (double)fmaf(v.x, r.x, v.y * r.y);
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sw[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// Fixed-order sum of n doubles (one block).
+__global__ void k_sum(const double* __restrict__ v, int n, double* out) {
+    __shared__ double s[256];
+    double t = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) t += v[i];
+    s[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0];
+}
+
+__global__ void k_set_tracked_energy(Ctl* ctl, const double* H, int n_ent) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n_ent) ctl[e].H = H[e];
+}
+
+// Algorithm 2 step 7: zhat = G^-1(mean phi) at gap sites (G affine, so this equals the
+// mean of the back-transformed realizations).  Sample sites are copied beforehand.
+__global__ void k_predict_out(EntryDesc e, const uint32_t* __restrict__ gaps,
+                              const float* __restrict__ acc, int M, double q, double zmin,
+                              double zmax, float* __restrict__ zhat) {
+    const int P = e.ngap[0] + e.ngap[1];
+    const double f = (zmax - zmin) / (kTwoPi * q * (double)M);
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < P; g += gridDim.x * blockDim.x) {
+        const int c = g < e.ngap[0] ? 0 : 1;
+        const long long gi = c ? e.gbase[1] + (g - e.ngap[0]) : e.gbase[0] + g;
+        const uint32_t ent = gaps[gi];
+        const int y = (int)(ent >> 16), j = (int)(ent & 0xFFFFu);
+        const int x = 2 * j + (c ^ (y & 1));
+        double v = zmin + (double)acc[gi] * f;
+        v = v < zmin ? zmin : (v > zmax ? zmax : v);
+        zhat[(long long)y * e.W + x] = (float)v;
+    }
+}
+
+// phi = 2 atan2(sin, cos) for every site of one grid.
+__global__ void k_get_state(EntryDesc e, const float2* __restrict__ lat, float* __restrict__ phi) {
+    const long long n = (long long)e.W * e.H;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(i / e.W), x = (int)(i - (long long)y * e.W);
+        const long long base = ((x + y) & 1) ? e.plane[1] : e.plane[0];
+        const float2 v = lat[base + (long long)(y + 1) * e.pitch + (x >> 1) + 1];
+        phi[i] = 2.0f * atan2f(v.y, v.x);
+    }
+}
+
+// Writes gap sites from phi (samples untouched).
+__global__ void k_set_state(EntryDesc e, float2* __restrict__ lat, const uint32_t* __restrict__ gaps,
+                            const float* __restrict__ phi) {
+    const int P = e.ngap[0] + e.ngap[1];
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < P; g += gridDim.x * blockDim.x) {
+        const int c = g < e.ngap[0] ? 0 : 1;
+        const long long gi = c ? e.gbase[1] + (g - e.ngap[0]) : e.gbase[0] + g;
+        const uint32_t ent = gaps[gi];
+        const int y = (int)(ent >> 16), j = (int)(ent & 0xFFFFu);
+        const int x = 2 * j + (c ^ (y & 1));
+        float s, co;
+        sincosf(0.5f * phi[(long long)y * e.W + x], &s, &co);
+        const long long base = c ? e.plane[1] : e.plane[0];
+        lat[base + (long long)(y + 1) * e.pitch + j + 1] = make_float2(co, s);
+    }
+}
+
+int grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_half_sweep(const SweepArgs& a, int color, int trig, cudaStream_t st) {
+    const int nb = a.nblk[color];
+    if (nb == 0) return cudaSuccess;
+    const bool acc = a.acc != nullptr;
+    count_launches(1, st);
+    if (trig == TRIG_FAST) {
+        if (acc) k_half_sweep<TRIG_FAST, true><<<nb, kSweepThreads, 0, st>>>(a, color);
+        else k_half_sweep<TRIG_FAST, false><<<nb, kSweepThreads, 0, st>>>(a, color);
+    } else {
+        if (acc) k_half_sweep<TRIG_ACCURATE, true><<<nb, kSweepThreads, 0, st>>>(a, color);
+        else k_half_sweep<TRIG_ACCURATE, false><<<nb, kSweepThreads, 0, st>>>(a, color);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_control(Ctl* ctl, Part* const part[2], const EntryDesc* ents, int n_ent,
+                           int mode, double A_targ, double k_a, int n_f, int n_fit, int i_max,
+                           double* ehist, int ehist_stride, int* active, cudaStream_t st) {
+    count_launches(1, st);
+    k_control<<<n_ent, kCtlThreads, 0, st>>>(ctl, part[0], part[1], ents, mode, A_targ, k_a, n_f,
+                                             n_fit, i_max, ehist, ehist_stride, active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy(const EntryDesc* e_host, const float2* lat, double* scratch,
+                          int scratch_len, double* out, cudaStream_t st) {
+    const long long n = (long long)e_host->H * ((e_host->W + 1) >> 1);
+    int g = grid_for(n, 256);
+    if (g > scratch_len) g = scratch_len;
+    count_launches(1, st);
+    k_energy<<<g, 256, 0, st>>>(*e_host, lat, scratch);
+    count_launches(1, st);
+    k_sum<<<1, 256, 0, st>>>(scratch, g, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum(const double* v, int n, double* out, cudaStream_t st) {
+    count_launches(1, st);
+    k_sum<<<1, 256, 0, st>>>(v, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_tracked_energy(Ctl* ctl, const double* H, int n_ent, cudaStream_t st) {
+    count_launches(1, st);
+    k_set_tracked_energy<<<(n_ent + 255) / 256, 256, 0, st>>>(ctl, H, n_ent);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_predict_out(const EntryDesc* e_host, const float2*, const uint32_t* gaps,
+                               const float* acc, int M, double q, double zmin, double zmax,
+                               float* zhat, cudaStream_t st) {
+    const long long P = (long long)e_host->ngap[0] + e_host->ngap[1];
+    if (P == 0) return cudaSuccess;
+    count_launches(1, st);
+    k_predict_out<<<grid_for(P, 256), 256, 0, st>>>(*e_host, gaps, acc, M, q, zmin, zmax, zhat);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_state(const EntryDesc* e_host, const float2* lat, float* phi,
+                             cudaStream_t st) {
+    count_launches(1, st);
+    k_get_state<<<grid_for((long long)e_host->W * e_host->H, 256), 256, 0, st>>>(*e_host, lat, phi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_state(const EntryDesc* e_host, float2* lat, const uint32_t* gaps,
+                             const float* phi, cudaStream_t st) {
+    const long long P = (long long)e_host->ngap[0] + e_host->ngap[1];
+    if (P == 0) return cudaSuccess;
+    count_launches(1, st);
+    k_set_state<<<grid_for(P, 256), 256, 0, st>>>(*e_host, lat, gaps, phi);
+    return cudaGetLastError();
+}
+
+}  // namespace mpr

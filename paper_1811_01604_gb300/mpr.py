@@ -1,0 +1,220 @@
+"""Thin Python binding of the C ABI in include/mpr.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  Arrays may be
+torch tensors (CUDA or CPU) or numpy arrays; they are passed as raw pointers and
+the library decides host or device from the pointer.  A non-zero status raises
+MprError.  There is no fallback: if libmpr.so is missing the import of the
+library fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MPR_OK, MPR_EINVAL, MPR_ENOMEM, MPR_ECUDA, MPR_ENODATA, MPR_ENOPAIRS, MPR_ETIMEOUT, \
+    MPR_ENOTEQUIL, MPR_ESTATE = range(9)
+MPR_OR_CONSERVING, MPR_OR_NONE = 0, 2
+MPR_TRIG_ACCURATE, MPR_TRIG_FAST = 0, 1
+MPR_EXEC_AUTO, MPR_EXEC_GRAPH, MPR_EXEC_PERSISTENT = 0, 1, 2
+
+
+class MprError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class mpr_params(ctypes.Structure):
+    _fields_ = [
+        ("seed", ctypes.c_uint64), ("q", ctypes.c_double), ("A_targ", ctypes.c_double),
+        ("k_a", ctypes.c_double), ("n_f", ctypes.c_int), ("n_fit", ctypes.c_int),
+        ("i_max", ctypes.c_int), ("M", ctypes.c_int), ("or_mode", ctypes.c_int),
+        ("trig_mode", ctypes.c_int), ("a_eq", ctypes.c_double), ("KT", ctypes.c_int),
+        ("T_min", ctypes.c_double), ("T_max", ctypes.c_double), ("T_cap", ctypes.c_int),
+        ("M_T", ctypes.c_int), ("exec_mode", ctypes.c_int), ("chain", ctypes.c_uint32),
+    ]
+
+
+class mpr_sweep_stats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int), ("acceptance", ctypes.c_double), ("e", ctypes.c_double)]
+
+
+class mpr_equil_stats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int), ("a", ctypes.c_double), ("k", ctypes.c_double),
+                ("A_last", ctypes.c_double), ("e_last", ctypes.c_double),
+                ("converged", ctypes.c_int)]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/mpr.h
+_VP, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+_SIGS = [
+    ("mpr_default_params", None, [ctypes.POINTER(mpr_params)]),
+    ("mpr_status_string", ctypes.c_char_p, [_I]),
+    ("mpr_init", _I, [ctypes.POINTER(_VP), _VP, _VP, _I, _I, ctypes.POINTER(mpr_params), _VP]),
+    ("mpr_estimate_T", _I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    ("mpr_set_T", _I, [_VP, _D]),
+    ("mpr_sweep", _I, [_VP, _I, _D, ctypes.POINTER(mpr_sweep_stats)]),
+    ("mpr_equilibrate", _I, [_VP, ctypes.POINTER(mpr_equil_stats)]),
+    ("mpr_predict", _I, [_VP, _I, _VP]),
+    ("mpr_fill", _I, [_VP, _VP, ctypes.POINTER(mpr_equil_stats)]),
+    ("mpr_free", None, [_VP]),
+    ("mpr_last_error", ctypes.c_char_p, [_VP]),
+    ("mpr_get_state", _I, [_VP, _VP, ctypes.POINTER(ctypes.c_uint32)]),
+    ("mpr_set_state", _I, [_VP, _VP, ctypes.c_uint32]),
+    ("mpr_get_info", _I, [_VP] + [ctypes.POINTER(_D)] * 6),
+    ("mpr_time_half_sweeps", _I, [_VP, _I, _D, ctypes.POINTER(_D)]),
+    ("mpr_kernel_launches", ctypes.c_uint64, []),
+    ("mpr_philox", _I, [_VP, ctypes.c_uint64, _VP, ctypes.c_size_t, _VP]),
+]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Loads libmpr.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"MPR CUDA library not found at {path}")
+        L = ctypes.CDLL(path)
+        for name, res, args in _SIGS:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data_as(ctypes.c_void_p)
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return None
+
+
+def _check(ctx, st, ok=(MPR_OK,)):
+    if st not in ok:
+        msg = lib().mpr_last_error(ctx).decode() if ctx else ""
+        name = lib().mpr_status_string(st).decode()
+        raise MprError(st, f"{name}: {msg}")
+    return st
+
+
+def mpr_default_params(**overrides) -> mpr_params:
+    p = mpr_params()
+    lib().mpr_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def mpr_init(z, mask, W: int, H: int, params: mpr_params | None = None, stream=None):
+    ctx = ctypes.c_void_p()
+    st = lib().mpr_init(ctypes.byref(ctx), _ptr(z), _ptr(mask), int(W), int(H),
+                        ctypes.byref(params) if params is not None else None, _stream(stream))
+    if st != MPR_OK:
+        raise MprError(st, lib().mpr_status_string(st).decode())
+    return ctx
+
+
+def mpr_estimate_T(ctx):
+    T, es = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().mpr_estimate_T(ctx, ctypes.byref(T), ctypes.byref(es)))
+    return T.value, es.value
+
+
+def mpr_set_T(ctx, T: float):
+    _check(ctx, lib().mpr_set_T(ctx, float(T)))
+
+
+def mpr_sweep(ctx, n: int, a: float) -> mpr_sweep_stats:
+    out = mpr_sweep_stats()
+    _check(ctx, lib().mpr_sweep(ctx, int(n), float(a), ctypes.byref(out)))
+    return out
+
+
+def mpr_equilibrate(ctx) -> mpr_equil_stats:
+    out = mpr_equil_stats()
+    _check(ctx, lib().mpr_equilibrate(ctx, ctypes.byref(out)), ok=(MPR_OK, MPR_ENOTEQUIL))
+    return out
+
+
+def mpr_predict(ctx, M: int, zhat):
+    _check(ctx, lib().mpr_predict(ctx, int(M), _ptr(zhat)))
+
+
+def mpr_fill(ctx, zhat) -> mpr_equil_stats:
+    out = mpr_equil_stats()
+    _check(ctx, lib().mpr_fill(ctx, _ptr(zhat), ctypes.byref(out)), ok=(MPR_OK, MPR_ENOTEQUIL))
+    return out
+
+
+def mpr_free(ctx):
+    if ctx:
+        lib().mpr_free(ctx)
+
+
+def mpr_last_error(ctx) -> str:
+    return lib().mpr_last_error(ctx).decode()
+
+
+def mpr_get_state(ctx, phi) -> int:
+    sw = ctypes.c_uint32()
+    _check(ctx, lib().mpr_get_state(ctx, _ptr(phi), ctypes.byref(sw)))
+    return sw.value
+
+
+def mpr_set_state(ctx, phi, sweep: int):
+    _check(ctx, lib().mpr_set_state(ctx, _ptr(phi), int(sweep)))
+
+
+def mpr_get_info(ctx) -> dict:
+    v = [ctypes.c_double() for _ in range(6)]
+    _check(ctx, lib().mpr_get_info(ctx, *[ctypes.byref(x) for x in v]))
+    keys = ("H_exact", "H_tracked", "zmin", "zmax", "T", "e_s")
+    return {k: x.value for k, x in zip(keys, v)}
+
+
+def mpr_time_half_sweeps(ctx, n: int, a: float) -> float:
+    ms = ctypes.c_double()
+    _check(ctx, lib().mpr_time_half_sweeps(ctx, int(n), float(a), ctypes.byref(ms)))
+    return ms.value
+
+
+def mpr_kernel_launches() -> int:
+    return int(lib().mpr_kernel_launches())
+
+
+def mpr_philox(ctr, seed: int, out, stream=None):
+    n = (ctr.numel() if hasattr(ctr, "numel") else ctr.size) // 4
+    st = lib().mpr_philox(_ptr(ctr), ctypes.c_uint64(seed), _ptr(out), n, _stream(stream))
+    if st != MPR_OK:
+        raise MprError(st, lib().mpr_status_string(st).decode())
