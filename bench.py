@@ -158,6 +158,24 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(name):
+    """4096^2 bench grid, T = 0.05, 24 sweeps at a = 8: about 50 half-sweep launches."""
+    import torch
+    from paper_1811_01604_gb300 import mpr
+    z_np, m_np = make_inputs(0)
+    H, W = z_np.shape
+    z = torch.from_numpy(z_np).cuda()
+    mask = torch.from_numpy(m_np).cuda()
+    ctx = mpr.mpr_init(z, mask, W, H, mpr.mpr_default_params(seed=1))
+    try:
+        mpr.mpr_set_T(ctx, 0.05)
+        st = mpr.mpr_sweep(ctx, 24, 8.0)
+        torch.cuda.synchronize()
+    finally:
+        mpr.mpr_free(ctx)
+    print(f"profile case {name}: acceptance {st.acceptance:.3f} e {st.e:.6f}")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -165,6 +183,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mpr", choices=["mpr", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", default=None, choices=["sweep4096"],
+                    help="run a small fixed sweep workload for ncu instead of the benchmark")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -172,6 +192,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.profile_case:
+        profile_case(args.profile_case)
         return
 
     import torch
@@ -237,7 +260,9 @@ def main():
 
     clocks = ClockSampler(local)
     clocks.start()
+    torch.cuda.profiler.start()        # an ncu run with --profile-from-start off sees these steps
     dev_ms, dev_updates, launches, sweeps, T = timed(z, mask, zhat)
+    torch.cuda.profiler.stop()
     e2e_ms, e2e_updates, _, _, _ = timed(z_h, m_h, zhat_h)
     clk = clocks.stop()
 

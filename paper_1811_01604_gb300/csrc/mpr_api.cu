@@ -282,9 +282,9 @@ mpr_status enqueue_sweeps(mpr_ctx* ctx, Batch& b, cudaStream_t s, int n, int mod
 
 // Runs n sweeps through a cached CUDA graph of kGraphSweeps sweeps (plus a tail).
 mpr_status run_sweeps(mpr_ctx* ctx, Batch& b, int n, int mode, double a_fixed, bool acc) {
-    if (n <= 0) return MPR_OK;
     const int S = kGraphSweeps;
     const bool relax = mode == CTL_RELAX;
+    if (n <= 0 && !relax) return MPR_OK;
     auto key = std::make_tuple(mode, acc ? 1 : 0, S, ctx->prm.trig_mode, (float)a_fixed);
     cudaGraphExec_t exec = nullptr;
     if (n >= S || relax) {

@@ -294,7 +294,7 @@ __global__ void k_get_state(EntryDesc e, const float2* __restrict__ lat, float* 
         const int y = (int)(i / e.W), x = (int)(i - (long long)y * e.W);
         const long long base = ((x + y) & 1) ? e.plane[1] : e.plane[0];
         const float2 v = lat[base + (long long)(y + 1) * e.pitch + (x >> 1) + 1];
-        phi[i] = 2.0f * atan2f(v.y, v.x);
+        phi[i] = 2.0f * atan2f(fmaxf(v.y, 0.0f), v.x);
     }
 }
 
@@ -310,6 +310,7 @@ __global__ void k_set_state(EntryDesc e, float2* __restrict__ lat, const uint32_
         const int x = 2 * j + (c ^ (y & 1));
         float s, co;
         sincosf(0.5f * phi[(long long)y * e.W + x], &s, &co);
+        s = fmaxf(s, 0.0f);
         const long long base = c ? e.plane[1] : e.plane[0];
         lat[base + (long long)(y + 1) * e.pitch + j + 1] = make_float2(co, s);
     }
