@@ -191,6 +191,34 @@ mpr_status mpr_time_half_sweeps(mpr_ctx* ctx, int n, double a, double* ms_per_la
 uint64_t mpr_kernel_launches(void);
 
 /*
+ * Allocation-free sample energy.  The paper has no counterpart to this entry point: it
+ * exists for callers that are not allowed to allocate device memory, such as a host
+ * application that owns the GPU's memory through its own pool or budget and forbids
+ * cudaMalloc/cudaFree inside libraries, or a latency-critical loop where an allocation
+ * would stall or synchronise the device.
+ *
+ * Computes what mpr_init computes before any sweep: e_s of Eq. 4 (each nearest-neighbour
+ * sample pair once) over the samples mapped by Eq. 1, and the number of sample pairs.
+ * z: float[H][W] and mask: uint8[H][W] (1 = sample) must be device-accessible memory;
+ * e_s and n_pairs are host pointers, written before the call returns (the call
+ * synchronises the stream).  H may not exceed MPR_STATIC_MAX_ROWS (MPR_EINVAL otherwise).
+ *
+ * It allocates nothing and calls no allocating routine.  Its scratch is one fixed
+ * device array of about 256 KB (16 bytes per row plus a 256-byte header), reserved on
+ * every GPU where the library is loaded and held until the process exits.  The first
+ * call on each device looks up that array's device address (cudaGetSymbolAddress, with
+ * the device current); make that first call before any stream capture.  Every call
+ * shares the one array: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  Each call clears the fields it
+ * accumulates into before use, so one call's leftovers never reach the next.
+ * Returns MPR_OK, MPR_EINVAL, MPR_ENODATA (fewer than two samples or constant data),
+ * MPR_ENOPAIRS (no sample pair; e_s = 0) or MPR_ECUDA.
+ */
+#define MPR_STATIC_MAX_ROWS 16384
+mpr_status mpr_sample_energy_static(const float* z, const uint8_t* mask, int W, int H, double q,
+                                    double* e_s, long long* n_pairs, void* cuda_stream);
+
+/*
  * Test support: Philox4x32-10 on the device.  ctr: uint32[n][4], out: uint32[n][4]
  * (host or device), key = (seed lo, seed hi).
  */

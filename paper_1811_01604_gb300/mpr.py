@@ -70,6 +70,8 @@ _SIGS = [
     ("mpr_get_info", _I, [_VP] + [ctypes.POINTER(_D)] * 6),
     ("mpr_time_half_sweeps", _I, [_VP, _I, _D, ctypes.POINTER(_D)]),
     ("mpr_kernel_launches", ctypes.c_uint64, []),
+    ("mpr_sample_energy_static", _I, [_VP, _VP, _I, _I, _D, ctypes.POINTER(_D),
+                                      ctypes.POINTER(ctypes.c_longlong), _VP]),
     ("mpr_philox", _I, [_VP, ctypes.c_uint64, _VP, ctypes.c_size_t, _VP]),
 ]
 
@@ -207,6 +209,17 @@ def mpr_time_half_sweeps(ctx, n: int, a: float) -> float:
     ms = ctypes.c_double()
     _check(ctx, lib().mpr_time_half_sweeps(ctx, int(n), float(a), ctypes.byref(ms)))
     return ms.value
+
+
+def mpr_sample_energy_static(z, mask, W: int, H: int, q: float = 0.5, stream=None):
+    """Allocation-free e_s (Eq. 4) of device-resident data; returns (e_s, n_pairs)."""
+    e = ctypes.c_double()
+    n = ctypes.c_longlong()
+    st = lib().mpr_sample_energy_static(_ptr(z), _ptr(mask), int(W), int(H), float(q),
+                                        ctypes.byref(e), ctypes.byref(n), _stream(stream))
+    if st != MPR_OK:
+        raise MprError(st, lib().mpr_status_string(st).decode())
+    return e.value, n.value
 
 
 def mpr_kernel_launches() -> int:
