@@ -52,8 +52,10 @@ typedef enum {
 enum { MPR_OR_CONSERVING = 0, MPR_OR_NONE = 2 };
 /* transcendental functions of the sweep kernel (Sect. 3.3.2, precision study) */
 enum { MPR_TRIG_ACCURATE = 0, MPR_TRIG_FAST = 1 };
-/* how sweeps are driven */
-enum { MPR_EXEC_AUTO = 0, MPR_EXEC_GRAPH = 1, MPR_EXEC_PERSISTENT = 2 };
+/* sweep kernels: AUTO (= TILE), LIST (one launch per half-sweep over gap lists, in place),
+   TILE (one fused launch per sweep over shared-memory tiles, two lattice buffers).
+   Both are replayed as CUDA graphs and give bitwise identical lattices. */
+enum { MPR_EXEC_AUTO = 0, MPR_EXEC_LIST = 1, MPR_EXEC_TILE = 2 };
 
 /*
  * Simulation parameters (Algorithm 2, step 1.1) and the readings of what the
@@ -177,12 +179,12 @@ mpr_status mpr_get_info(mpr_ctx* ctx, double* H_exact, double* H_tracked, double
                         double* zmax, double* T, double* e_s);
 
 /*
- * Benchmark support: enqueues n sweeps at window a >= 1 as 2n back-to-back half-sweep
- * launches (no control kernel), timed with CUDA events on the context stream, and
- * returns the mean duration of one half-sweep launch in milliseconds.  Advances the
- * state and the sweep counter like mpr_sweep.
+ * Benchmark support: enqueues n sweeps at window a >= 1 (the kernels of the context's
+ * exec_mode, launched directly, no graph), times them with CUDA events on the context
+ * stream and returns the mean duration of one sweep in milliseconds.  Advances the state
+ * and the sweep counter like mpr_sweep.
  */
-mpr_status mpr_time_half_sweeps(mpr_ctx* ctx, int n, double a, double* ms_per_launch);
+mpr_status mpr_time_sweeps(mpr_ctx* ctx, int n, double a, double* ms_per_sweep);
 
 /*
  * Diagnostics: number of kernels this library has enqueued in the process so far

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmpr.so")
-SOURCES = ["mpr_init.cu", "mpr_sweep.cu", "mpr_api.cu", "mpr_static.cu"]
+SOURCES = ["mpr_init.cu", "mpr_sweep.cu", "mpr_tile.cu", "mpr_api.cu", "mpr_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]
@@ -42,6 +42,8 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compiles libmpr.so if it is missing or older than its sources.  Extra nvcc flags
+    (e.g. -DMPR_TILE_THREADS=256 -DMPR_TILE_STAGES=2) can be passed in MPR_NVCC_FLAGS."""
     if not force and not _stale():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
@@ -50,7 +52,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, "-I", os.path.join(HERE, "..", "include"), "-c",
+        extra = os.environ.get("MPR_NVCC_FLAGS", "").split()
+        cmd = [cc, *ARCH, *FLAGS, *extra, "-I", os.path.join(HERE, "..", "include"), "-c",
                os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")

@@ -66,6 +66,19 @@ struct Batch {
     int* d_active = nullptr;               // kGraphSweeps counters
     double* d_scratch = nullptr;
     double* d_H = nullptr;                 // one exact energy per entry
+    // tile path (fused sweeps over shared-memory tiles, two lattice buffers)
+    bool tiled = false;
+    float2* d_lat2 = nullptr;
+    TileDesc* d_tiles = nullptr;
+    int ntiles = 0;
+    TileCnt* d_cnts = nullptr;
+    uint16_t* d_lists = nullptr;
+    float* d_tacc = nullptr;
+    double* d_tpart_dH = nullptr;
+    unsigned* d_tpart_na = nullptr;
+    unsigned* d_ticket = nullptr;
+    CUtensorMap* d_maps = nullptr;
+    int* d_err = nullptr;
     std::map<std::tuple<int, int, int, int, float>, cudaGraphExec_t> graphs;
 };
 
@@ -132,12 +145,24 @@ void batch_free(Batch& b) {
     cudaFree(b.d_active);
     cudaFree(b.d_scratch);
     cudaFree(b.d_H);
+    cudaFree(b.d_lat2);
+    cudaFree(b.d_tiles);
+    cudaFree(b.d_cnts);
+    cudaFree(b.d_lists);
+    cudaFree(b.d_tacc);
+    cudaFree(b.d_tpart_dH);
+    cudaFree(b.d_tpart_na);
+    cudaFree(b.d_ticket);
+    cudaFree(b.d_maps);
+    cudaFree(b.d_err);
     b = Batch();
 }
 
 // Lays out, packs and indexes a batch of grids.  all_free: every site is a gap.
-mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids, int all_free) {
+mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids, int all_free,
+                       const uint8_t* mask_base) {
     cudaStream_t st = ctx->st;
+    b.tiled = ctx->prm.exec_mode != MPR_EXEC_LIST;
     const uint32_t k0 = (uint32_t)ctx->prm.seed, k1 = (uint32_t)(ctx->prm.seed >> 32);
     b.n_ent = (int)grids.size();
     b.ents.assign(b.n_ent, EntryDesc{});
@@ -148,8 +173,10 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
         EntryDesc& E = b.ents[e];
         E.W = grids[e].W;
         E.H = grids[e].H;
-        E.pitch = ((E.W / 2 + 2) + 31) & ~31;
-        const size_t plane = (size_t)(E.H + 2) * E.pitch;
+        // >= W/2 + 3 columns, and at least one TMA box wide and high
+        E.pitch = (std::max(E.W / 2 + 4, kTileRW) + 31) & ~31;
+        E.prows = std::max(E.H + 2, kTileRH);
+        const size_t plane = (size_t)E.prows * E.pitch;
         E.plane[0] = (long long)lat;
         E.plane[1] = (long long)(lat + plane);
         lat += 2 * plane;
@@ -219,14 +246,47 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
             CU(cudaMemcpyAsync(b.d_work[c], w.data(), w.size() * sizeof(BlockWork),
                                cudaMemcpyHostToDevice, st));
     }
+    // tiles (tile path): per grid ceil(H/kTileH) x ceil(W/kTileW), row-major
+    std::vector<TileDesc> tiles;
+    for (int e = 0; e < b.n_ent; ++e) {
+        EntryDesc& E = b.ents[e];
+        E.tile0 = (int)tiles.size();
+        for (int y0 = 0; y0 < E.H; y0 += kTileH)
+            for (int x0 = 0; x0 < E.W; x0 += kTileW) tiles.push_back(TileDesc{e, y0, x0, 0});
+        E.ntiles = (int)tiles.size() - E.tile0;
+    }
     CU(dalloc(&b.d_ents, b.n_ent));
     CU(cudaMemcpyAsync(b.d_ents, b.ents.data(), b.n_ent * sizeof(EntryDesc), cudaMemcpyHostToDevice, st));
+    if (b.tiled) {
+        b.ntiles = (int)tiles.size();
+        CU(dalloc(&b.d_lat2, lat));
+        CU(cudaMemcpyAsync(b.d_lat2, b.d_lat, lat * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+        CU(dalloc(&b.d_tiles, tiles.size()));
+        CU(cudaMemcpyAsync(b.d_tiles, tiles.data(), tiles.size() * sizeof(TileDesc),
+                           cudaMemcpyHostToDevice, st));
+        CU(dalloc(&b.d_cnts, tiles.size()));
+        CU(dalloc(&b.d_lists, tiles.size() * (size_t)tile_list_len()));
+        CU(dalloc(&b.d_tacc, tiles.size() * (size_t)tile_acc_len()));
+        CU(dalloc(&b.d_tpart_dH, tiles.size()));
+        CU(dalloc(&b.d_tpart_na, tiles.size()));
+        CU(dalloc(&b.d_ticket, (size_t)b.n_ent));
+        CU(cudaMemsetAsync(b.d_ticket, 0, sizeof(unsigned) * b.n_ent, st));
+        CU(launch_tile_lists(b.d_tiles, b.ntiles, b.d_ents, mask_base, all_free, b.d_lists, b.d_cnts, st));
+        CU(dalloc(&b.d_maps, (size_t)2 * b.n_ent));
+        CU(make_tile_maps(b.ents.data(), b.n_ent, b.d_lat, b.d_lat2, b.d_maps, st));
+        CU(dalloc(&b.d_err, 1));
+        CU(cudaMemsetAsync(b.d_err, 0, sizeof(int), st));
+        tile_sweep_blocks();                  // kernel attributes are set outside any capture
+        CU(cudaGetLastError());
+    }
     std::vector<Ctl> ctl(b.n_ent);
     for (int e = 0; e < b.n_ent; ++e) {
         std::memset(&ctl[e], 0, sizeof(Ctl));
         ctl[e].T = grids[e].T;
         ctl[e].a = 1.0;
         ctl[e].k = -1.0;
+        ctl[e].half_qd = (float)(0.5 * kTwoPi * 0.5 / 1.0);
+        ctl[e].neg_inv_T = grids[e].T > 0.0 ? (float)(-1.0 / grids[e].T) : 0.0f;
     }
     CU(dalloc(&b.d_ctl, b.n_ent));
     CU(cudaMemcpyAsync(b.d_ctl, ctl.data(), b.n_ent * sizeof(Ctl), cudaMemcpyHostToDevice, st));
@@ -264,12 +324,57 @@ SweepArgs sweep_args(const mpr_ctx* ctx, const Batch& b, bool use_ctl_a, double 
 }
 
 // Enqueues n sweeps (A, B, control) on stream s.
+TileArgs tile_args(const mpr_ctx* ctx, const Batch& b, int mode, double a_fixed, bool acc) {
+    const mpr_params& p = ctx->prm;
+    const bool relax = mode == CTL_RELAX;
+    TileArgs T;
+    std::memset(&T, 0, sizeof T);
+    T.ents = b.d_ents;
+    T.lat[0] = b.d_lat;
+    T.lat[1] = b.d_lat2;
+    T.maps = b.d_maps;
+    T.err = b.d_err;
+    T.tiles = b.d_tiles;
+    T.cnts = b.d_cnts;
+    T.lists = b.d_lists;
+    T.acc = acc ? b.d_tacc : nullptr;
+    T.ctl = b.d_ctl;
+    T.part_dH = b.d_tpart_dH;
+    T.part_na = b.d_tpart_na;
+    T.ticket = b.d_ticket;
+    T.ehist = b.d_ehist;
+    T.ehist_stride = b.ehist_stride;
+    T.ntiles = b.ntiles;
+    T.use_ctl_a = relax ? 1 : 0;
+    T.half_qd_fixed = (float)(0.5 * kTwoPi * p.q / a_fixed);
+    T.skip_stopped = relax ? 1 : 0;
+    T.or_on = p.or_mode == MPR_OR_CONSERVING ? 1 : 0;
+    T.key0 = (uint32_t)p.seed;
+    T.key1 = (uint32_t)(p.seed >> 32);
+    T.mode = mode;
+    T.A_targ = p.A_targ;
+    T.k_a = p.k_a;
+    T.n_f = p.n_f;
+    T.n_fit = p.n_fit;
+    T.i_max = p.i_max;
+    T.active = nullptr;
+    return T;
+}
+
 mpr_status enqueue_sweeps(mpr_ctx* ctx, Batch& b, cudaStream_t s, int n, int mode, double a_fixed,
                           bool acc, bool count_active) {
     const bool relax = mode == CTL_RELAX;
     const SweepArgs A = sweep_args(ctx, b, relax, a_fixed, relax, acc);
     const mpr_params& p = ctx->prm;
     if (count_active) CU(cudaMemsetAsync(b.d_active, 0, sizeof(int) * kGraphSweeps, s));
+    if (b.tiled) {
+        TileArgs T = tile_args(ctx, b, mode, a_fixed, acc);
+        for (int i = 0; i < n; ++i) {
+            T.active = count_active ? b.d_active + (i % kGraphSweeps) : nullptr;
+            CU(launch_tile_sweep(T, p.trig_mode, s));
+        }
+        return MPR_OK;
+    }
     for (int i = 0; i < n; ++i) {
         CU(launch_half_sweep(A, 0, p.trig_mode, s));
         CU(launch_half_sweep(A, 1, p.trig_mode, s));
@@ -315,7 +420,7 @@ mpr_status run_sweeps(mpr_ctx* ctx, Batch& b, int n, int mode, double a_fixed, b
             if (ch > cap_chunks)
                 return fail(ctx, MPR_ETIMEOUT, "relaxation did not stop within i_max sweeps");
             CU(cudaGraphLaunch(exec, ctx->st));
-            count_launches(3ull * S, nullptr);
+            count_launches((b.tiled ? 1ull : 3ull) * S, nullptr);
             CU(cudaMemcpyAsync(ctx->h_active, b.d_active + (S - 1), sizeof(int),
                                cudaMemcpyDeviceToHost, ctx->st));
             CU(cudaStreamSynchronize(ctx->st));
@@ -326,15 +431,23 @@ mpr_status run_sweeps(mpr_ctx* ctx, Batch& b, int n, int mode, double a_fixed, b
     int done = 0;
     for (; exec && done + S <= n; done += S) {
         CU(cudaGraphLaunch(exec, ctx->st));
-        count_launches(3ull * S, nullptr);
+        count_launches((b.tiled ? 1ull : 3ull) * S, nullptr);
     }
     return enqueue_sweeps(ctx, b, ctx->st, n - done, mode, a_fixed, acc, false);
 }
 
 // Recomputes Eq. 2 for every entry and makes it the tracked energy.
+mpr_status read_ctl(mpr_ctx* ctx, Batch& b, std::vector<Ctl>& out);
+
+// Lattice buffer that holds entry e's current state (the tile path alternates buffers).
+float2* lat_cur(const Batch& b, const Ctl& c) { return (b.tiled && c.cur) ? b.d_lat2 : b.d_lat; }
+
 mpr_status reset_tracked_energy(mpr_ctx* ctx, Batch& b) {
+    std::vector<Ctl> c;
+    mpr_status s = read_ctl(ctx, b, c);
+    if (s != MPR_OK) return s;
     for (int e = 0; e < b.n_ent; ++e)
-        CU(launch_energy(&b.ents[e], b.d_lat, b.d_scratch, kScratch, b.d_H + e, ctx->st));
+        CU(launch_energy(&b.ents[e], lat_cur(b, c[e]), b.d_scratch, kScratch, b.d_H + e, ctx->st));
     CU(launch_set_tracked_energy(b.d_ctl, b.d_H, b.n_ent, ctx->st));
     return MPR_OK;
 }
@@ -359,6 +472,7 @@ mpr_status reset_relax(mpr_ctx* ctx, Batch& b) {
         c[e].converged = 0;
         c[e].esum = 0.0;
         c[e].nsamp = 0;
+        c[e].half_qd = (float)(0.5 * kTwoPi * 0.5 / 1.0);
     }
     CU(cudaMemcpyAsync(b.d_ctl, c.data(), sizeof(Ctl) * b.n_ent, cudaMemcpyHostToDevice, ctx->st));
     return reset_tracked_energy(ctx, b);
@@ -385,7 +499,7 @@ mpr_status build_table(mpr_ctx* ctx, int Wt, int Ht, std::vector<double>& Tk,
         g[k] = GridIn{Wt, Ht, nullptr, nullptr, 0x80000000u + (uint32_t)k, Tk[k], 0.0, 0.0};
     }
     Batch tb;
-    mpr_status s = batch_build(ctx, tb, g, 1);
+    mpr_status s = batch_build(ctx, tb, g, 1, nullptr);
     if (s == MPR_OK) s = reset_relax(ctx, tb);
     if (s == MPR_OK) s = run_sweeps(ctx, tb, 0, CTL_RELAX, 1.0, false);
     if (s == MPR_OK) s = run_sweeps(ctx, tb, p.M_T, CTL_SAMPLE, p.a_eq, false);
@@ -475,6 +589,7 @@ static mpr_status check_params(const mpr_params* p, std::string& why) {
     if (p->or_mode != MPR_OR_CONSERVING && p->or_mode != MPR_OR_NONE) { why = "or_mode"; return MPR_EINVAL; }
     if (p->trig_mode != MPR_TRIG_ACCURATE && p->trig_mode != MPR_TRIG_FAST) { why = "trig_mode"; return MPR_EINVAL; }
     if (!(p->a_eq >= 1.0)) { why = "a_eq must be >= 1"; return MPR_EINVAL; }
+    if (p->exec_mode != MPR_EXEC_AUTO && p->exec_mode != MPR_EXEC_LIST && p->exec_mode != MPR_EXEC_TILE) { why = "exec_mode"; return MPR_EINVAL; }
     if (p->KT < 2 || !(p->T_min > 0.0) || !(p->T_max > p->T_min) || p->M_T < 1 || p->T_cap < 0) { why = "table parameters"; return MPR_EINVAL; }
     return MPR_OK;
 }
@@ -531,7 +646,7 @@ mpr_status mpr_init(mpr_ctx** out, const float* z, const uint8_t* mask, int W, i
     ctx->scale = kTwoPi / (ctx->zmax - ctx->zmin);
     std::vector<GridIn> g{GridIn{W, H, ctx->d_z, ctx->d_mask, ctx->prm.chain, 0.0, ctx->zmin, ctx->scale}};
     {
-        const mpr_status bs = batch_build(ctx, ctx->b, g, 0);
+        const mpr_status bs = batch_build(ctx, ctx->b, g, 0, ctx->d_mask);
         if (bs != MPR_OK) return bail(bs);
     }
     // Eq. 4
@@ -565,7 +680,10 @@ mpr_status mpr_set_T(mpr_ctx* ctx, double T) {
     std::vector<Ctl> c;
     mpr_status s = read_ctl(ctx, ctx->b, c);
     if (s != MPR_OK) return s;
-    for (auto& x : c) x.T = T;
+    for (auto& x : c) {
+        x.T = T;
+        x.neg_inv_T = (float)(-1.0 / T);
+    }
     CU(cudaMemcpyAsync(ctx->b.d_ctl, c.data(), sizeof(Ctl) * c.size(), cudaMemcpyHostToDevice, ctx->st));
     CU(cudaStreamSynchronize(ctx->st));
     ctx->T = T;
@@ -645,12 +763,20 @@ mpr_status mpr_predict(mpr_ctx* ctx, int M, float* zhat) {
     if (!ctx->T_set) return fail(ctx, MPR_ESTATE, "temperature not set");
     Batch& b = ctx->b;
     const size_t n = (size_t)ctx->W * ctx->H;
-    CU(cudaMemsetAsync(b.d_acc, 0, sizeof(float) * std::max<size_t>(b.n_gaps, 1), ctx->st));
+    if (b.tiled)
+        CU(cudaMemsetAsync(b.d_tacc, 0, sizeof(float) * (size_t)b.ntiles * tile_acc_len(), ctx->st));
+    else
+        CU(cudaMemsetAsync(b.d_acc, 0, sizeof(float) * std::max<size_t>(b.n_gaps, 1), ctx->st));
     mpr_status s = run_sweeps(ctx, b, M, CTL_FIXED, ctx->prm.a_eq, true);
     if (s != MPR_OK) return s;
     CU(cudaMemcpyAsync(ctx->d_out, ctx->d_z, n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->st));
-    CU(launch_predict_out(&b.ents[0], b.d_lat, b.d_gaps, b.d_acc, M, ctx->prm.q, ctx->zmin, ctx->zmax,
-                          ctx->d_out, ctx->st));
+    if (b.tiled)
+        CU(launch_tile_predict_out(b.d_tiles, b.d_cnts, b.d_lists, b.d_tacc, b.d_ents, b.ents[0].tile0,
+                                   b.ents[0].ntiles, M, ctx->prm.q, ctx->zmin, ctx->zmax, ctx->d_out,
+                                   ctx->st));
+    else
+        CU(launch_predict_out(&b.ents[0], b.d_lat, b.d_gaps, b.d_acc, M, ctx->prm.q, ctx->zmin,
+                              ctx->zmax, ctx->d_out, ctx->st));
     CU(cudaMemcpyAsync(zhat, ctx->d_out, n * sizeof(float), cudaMemcpyDefault, ctx->st));
     CU(cudaStreamSynchronize(ctx->st));
     return MPR_OK;
@@ -670,11 +796,12 @@ mpr_status mpr_fill(mpr_ctx* ctx, float* zhat, mpr_equil_stats* stats) {
 mpr_status mpr_get_state(mpr_ctx* ctx, float* phi, uint32_t* sweep) {
     if (!ctx || !phi) return MPR_EINVAL;
     const size_t n = (size_t)ctx->W * ctx->H;
-    CU(launch_get_state(&ctx->b.ents[0], ctx->b.d_lat, ctx->d_out, ctx->st));
-    CU(cudaMemcpyAsync(phi, ctx->d_out, n * sizeof(float), cudaMemcpyDefault, ctx->st));
     std::vector<Ctl> c;
     mpr_status s = read_ctl(ctx, ctx->b, c);
     if (s != MPR_OK) return s;
+    CU(launch_get_state(&ctx->b.ents[0], lat_cur(ctx->b, c[0]), ctx->d_out, ctx->st));
+    CU(cudaMemcpyAsync(phi, ctx->d_out, n * sizeof(float), cudaMemcpyDefault, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
     if (sweep) *sweep = c[0].sweep;
     return MPR_OK;
 }
@@ -682,11 +809,11 @@ mpr_status mpr_get_state(mpr_ctx* ctx, float* phi, uint32_t* sweep) {
 mpr_status mpr_set_state(mpr_ctx* ctx, const float* phi, uint32_t sweep) {
     if (!ctx || !phi) return MPR_EINVAL;
     const size_t n = (size_t)ctx->W * ctx->H;
-    CU(cudaMemcpyAsync(ctx->d_out, phi, n * sizeof(float), cudaMemcpyDefault, ctx->st));
-    CU(launch_set_state(&ctx->b.ents[0], ctx->b.d_lat, ctx->b.d_gaps, ctx->d_out, ctx->st));
     std::vector<Ctl> c;
     mpr_status s = read_ctl(ctx, ctx->b, c);
     if (s != MPR_OK) return s;
+    CU(cudaMemcpyAsync(ctx->d_out, phi, n * sizeof(float), cudaMemcpyDefault, ctx->st));
+    CU(launch_set_state(&ctx->b.ents[0], lat_cur(ctx->b, c[0]), ctx->b.d_gaps, ctx->d_out, ctx->st));
     c[0].sweep = sweep;
     CU(cudaMemcpyAsync(ctx->b.d_ctl, c.data(), sizeof(Ctl), cudaMemcpyHostToDevice, ctx->st));
     CU(cudaStreamSynchronize(ctx->st));
@@ -696,14 +823,15 @@ mpr_status mpr_set_state(mpr_ctx* ctx, const float* phi, uint32_t sweep) {
 mpr_status mpr_get_info(mpr_ctx* ctx, double* H_exact, double* H_tracked, double* zmin,
                         double* zmax, double* T, double* e_s) {
     if (!ctx) return MPR_EINVAL;
-    if (H_exact) {
-        double* d = ctx->b.d_scratch + kScratch;
-        CU(launch_energy(&ctx->b.ents[0], ctx->b.d_lat, ctx->b.d_scratch, kScratch, d, ctx->st));
-        CU(cudaMemcpyAsync(H_exact, d, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
-    }
     std::vector<Ctl> c;
     mpr_status s = read_ctl(ctx, ctx->b, c);
     if (s != MPR_OK) return s;
+    if (H_exact) {
+        double* d = ctx->b.d_scratch + kScratch;
+        CU(launch_energy(&ctx->b.ents[0], lat_cur(ctx->b, c[0]), ctx->b.d_scratch, kScratch, d, ctx->st));
+        CU(cudaMemcpyAsync(H_exact, d, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+        CU(cudaStreamSynchronize(ctx->st));
+    }
     if (H_tracked) *H_tracked = c[0].H;
     if (zmin) *zmin = ctx->zmin;
     if (zmax) *zmax = ctx->zmax;
@@ -714,47 +842,22 @@ mpr_status mpr_get_info(mpr_ctx* ctx, double* H_exact, double* H_tracked, double
 
 uint64_t mpr_kernel_launches(void) { return (uint64_t)g_launches.load(); }
 
-mpr_status mpr_time_half_sweeps(mpr_ctx* ctx, int n, double a, double* ms_per_launch) {
-    if (!ctx || n < 1 || !(a >= 1.0) || !ms_per_launch) return MPR_EINVAL;
+mpr_status mpr_time_sweeps(mpr_ctx* ctx, int n, double a, double* ms_per_sweep) {
+    if (!ctx || n < 1 || !(a >= 1.0) || !ms_per_sweep) return MPR_EINVAL;
     if (!ctx->T_set) return fail(ctx, MPR_ESTATE, "temperature not set");
-    Batch& b = ctx->b;
-    const SweepArgs A = sweep_args(ctx, b, false, a, false, false);
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     CU(cudaEventRecord(e0, ctx->st));
-    for (int i = 0; i < n; ++i) {
-        CU(launch_half_sweep(A, 0, ctx->prm.trig_mode, ctx->st));
-        CU(launch_half_sweep(A, 1, ctx->prm.trig_mode, ctx->st));
-        // advance the sweep counter (and fold the partials) between sweeps
-        CU(launch_control(b.d_ctl, b.d_part, b.d_ents, b.n_ent, CTL_FIXED, ctx->prm.A_targ,
-                          ctx->prm.k_a, ctx->prm.n_f, ctx->prm.n_fit, ctx->prm.i_max, b.d_ehist,
-                          b.ehist_stride, nullptr, ctx->st));
-    }
+    mpr_status s = enqueue_sweeps(ctx, ctx->b, ctx->st, n, CTL_FIXED, a, false, false);
+    if (s != MPR_OK) return s;
     CU(cudaEventRecord(e1, ctx->st));
     CU(cudaEventSynchronize(e1));
     float ms = 0.f;
     CU(cudaEventElapsedTime(&ms, e0, e1));
-    // time of the small control kernels, measured the same way, is subtracted
-    CU(cudaEventRecord(e0, ctx->st));
-    for (int i = 0; i < n; ++i)
-        CU(launch_control(b.d_ctl, b.d_part, b.d_ents, b.n_ent, CTL_FIXED, ctx->prm.A_targ,
-                          ctx->prm.k_a, ctx->prm.n_f, ctx->prm.n_fit, ctx->prm.i_max, b.d_ehist,
-                          b.ehist_stride, nullptr, ctx->st));
-    CU(cudaEventRecord(e1, ctx->st));
-    CU(cudaEventSynchronize(e1));
-    float ms_ctl = 0.f;
-    CU(cudaEventElapsedTime(&ms_ctl, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    // the extra control launches advanced the counter: step it back
-    std::vector<Ctl> c;
-    mpr_status s = read_ctl(ctx, b, c);
-    if (s != MPR_OK) return s;
-    for (auto& x : c) x.sweep -= (uint32_t)n;
-    CU(cudaMemcpyAsync(b.d_ctl, c.data(), sizeof(Ctl) * c.size(), cudaMemcpyHostToDevice, ctx->st));
-    CU(cudaStreamSynchronize(ctx->st));
-    *ms_per_launch = (double)(ms - ms_ctl) / (2.0 * n);
+    *ms_per_sweep = (double)ms / (double)n;
     return MPR_OK;
 }
 

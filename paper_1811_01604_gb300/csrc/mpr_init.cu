@@ -65,7 +65,7 @@ __global__ void k_pack(EntryDesc e, const float* __restrict__ z, const uint8_t* 
         sincosf(theta, &s, &co);
         s = fmaxf(s, 0.0f);     // theta = pi rounds above pi in FP32: stay on the upper half circle
         const long long base = c ? e.plane[1] : e.plane[0];
-        lat[base + (long long)(y + 1) * e.pitch + (x >> 1) + 1] = make_float2(co, s);
+        lat[base + (long long)(y + 1) * e.pitch + (x >> 1) + kPadL] = make_float2(co, s);
     }
 }
 

@@ -4,25 +4,32 @@
 //   The checkerboard of Sect. 3.3 splits the grid into colour 0 ((x+y) even) and
 //   colour 1.  Each colour is packed into a plane of float2 unit vectors
 //   (cos(q phi), sin(q phi)), row y, column j = x >> 1, with one padding row above
-//   and below and a padding column on the left.  Padding slots hold (0, 0), so an
-//   out-of-grid neighbour contributes nothing to the local field: no boundary
-//   branches in the sweep.  For q = 1/2 the state space phi in [0, 2pi) is the
-//   upper half circle sin(q phi) >= 0.
-//   Padded index of (y, j): (y + 1) * pitch + (j + 1).  For a site of colour c in
+//   and below and kPadL padding columns on the left (two, so that tiles whose first
+//   grid column is a multiple of 4 start on a 16-byte boundary).  Padding slots hold
+//   (0, 0), so an out-of-grid neighbour contributes nothing to the local field: no
+//   boundary branches in the sweep.  For q = 1/2 the state space phi in [0, 2pi) is
+//   the upper half circle sin(q phi) >= 0.
+//   Padded index of (y, j): (y + 1) * pitch + (j + kPadL).  For a site of colour c in
 //   row y, s = c ^ (y & 1) gives x = 2j + s and its neighbours in the other plane at
 //   k - pitch, k + pitch, k - 1 + s, k + s.
 //   Gap sites of each colour are listed row-major as (y << 16) | j.
 #pragma once
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace mpr {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr int kPadL = 2;                          // zero columns left of column j = 0
 constexpr int kSweepThreads = 256;
 constexpr int kSweepItems = 2;                    // gap sites per thread per launch chunk
 constexpr uint32_t kInitSweep = 0xFFFFFFFFu;      // Philox sweep word of the initial state
+
+// Control modes (Algorithm 2 step 5 / fixed window / table sampling).
+enum { CTL_RELAX = 0, CTL_FIXED = 1, CTL_SAMPLE = 2 };
 
 struct EntryDesc {            // immutable during a run
     int W, H, pitch, _pad0;
@@ -35,6 +42,10 @@ struct EntryDesc {            // immutable during a run
     long long site0;          // offset of the grid in concatenated [H][W] buffers
     int blk0[2];              // first sweep block of this entry in colour c's work list
     int nblk[2];              // number of sweep blocks of this entry per colour
+    int tile0;                // first tile of this entry (tile path)
+    int ntiles;               // number of tiles of this entry
+    int prows;                // rows allocated per plane: max(H + 2, kTileRH)
+    int _pad2;
 };
 
 struct Ctl {                  // mutable per-entry control state (Algorithm 2)
@@ -50,12 +61,62 @@ struct Ctl {                  // mutable per-entry control state (Algorithm 2)
     uint32_t sweep;           // global sweep counter (Philox counter word 1)
     int nsamp;
     int status;               // 0, or a device-side error code
+    int cur;                  // tile path: which of the two lattice buffers holds the state
+    float half_qd;            // q * pi / a as float (proposal half-angle scale)
+    float neg_inv_T;          // -1/T as float
+    int _pad1;
 };
 
 struct Part {                 // one sweep block's energy change and acceptance count
     double dH;
     unsigned nacc;
     unsigned _pad;
+};
+
+// Tile path (mpr_tile.cu): tiles of kTileH x kTileW grid sites.
+constexpr int kTileH = 32;
+constexpr int kTileW = 64;
+constexpr int kTileRH = kTileH + 4;           // rows of a tile's TMA box (halo 2)
+constexpr int kTileRW = kTileW / 2 + 4;       // plane columns of a tile's TMA box
+
+struct TileDesc {             // one tile: its grid and the grid coordinates of its origin
+    int entry;
+    int y0, x0;
+    int _pad;
+};
+
+struct TileCnt {              // gap sites listed for one tile
+    uint16_t nA_int;          // colour A inside the tile
+    uint16_t nA_ring;         // colour A on the one-site ring around it
+    uint16_t nB;              // colour B inside the tile
+    uint16_t _pad;
+};
+
+struct TileArgs {
+    const EntryDesc* ents;
+    float2* lat[2];           // the two lattice buffers (Ctl::cur selects the source)
+    const CUtensorMap* maps;  // per entry: maps of buffer 0 and buffer 1 (64-byte aligned)
+    int* err;                 // set to 1 if a bounded wait gave up
+    const TileDesc* tiles;
+    const TileCnt* cnts;
+    const uint16_t* lists;
+    float* acc;               // per-tile accumulators, or nullptr
+    Ctl* ctl;
+    double* part_dH;          // one per tile
+    unsigned* part_na;
+    unsigned* ticket;         // one per grid, zero between sweeps
+    double* ehist;
+    int ehist_stride;
+    int ntiles;
+    int use_ctl_a;
+    float half_qd_fixed;
+    int skip_stopped;
+    int or_on;
+    uint32_t key0, key1;
+    int mode;
+    double A_targ, k_a;
+    int n_f, n_fit, i_max;
+    int* active;
 };
 
 struct BlockWork {            // one sweep block: entry and first gap index of its chunk
@@ -79,17 +140,17 @@ struct SweepArgs {
     uint32_t key0, key1;      // Philox key
 };
 
-// Control-kernel modes.
-enum { CTL_RELAX = 0, CTL_FIXED = 1, CTL_SAMPLE = 2 };
 
 // ---------------------------------------------------------------- device helpers
 __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
     // Philox4x32-10, Salmon et al. (SC'11): 10 rounds, Weyl key schedule.
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        // one 32x32 -> 64-bit product per multiplier gives both halves
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
@@ -135,6 +196,124 @@ __device__ __forceinline__ unsigned warp_sum(unsigned v) {
 // recorded into a graph under capture are counted when the graph is replayed instead.
 void count_launches(unsigned long long n, cudaStream_t st);
 
+// ---------------------------------------------------------------- the site update
+enum { TRIG_ACCURATE = 0, TRIG_FAST = 1 };
+
+// One gap-site update (Algorithm 1) in unit-vector form, q = 1/2, theta = phi/2 in [0, pi).
+//   v        current (cos theta, sin theta) of the site
+//   C, S     local field: sums of the neighbours' cos/sin
+//   hq       half the proposal rotation, q * 2 pi (u - 1/2) / a / 2
+//   r        acceptance uniform
+// Returns the accepted energy change (0 if rejected) and writes the new vector.
+template <int TRIG>
+__device__ __forceinline__ float hybrid_update(float2& v, float C, float S, float hq, float r,
+                                               float neg_inv_T, int or_on, bool& accepted) {
+    float c = v.x, s = v.y;
+    // R cos(theta - psi) and R sin(theta - psi), psi the direction of the field
+    const float along = fmaf(c, C, s * S);
+    float perp = fmaf(s, C, -(c * S));
+    // Eq. 6 (energy-conserving reading): reflect theta about psi; keep it only if the
+    // image stays in [0, pi), i.e. sin >= 0 (the point theta = pi is excluded).
+    const float R2 = fmaf(C, C, S * S);
+    if (or_on && R2 > 1e-12f) {
+        // reflection factor 2 (v.n)/|n|^2; a 2-ulp quotient moves the image by ~2e-7 rad
+        const float f = __fdividef(2.0f * along, R2);
+        const float cr = fmaf(f, C, -c), sr = fmaf(f, S, -s);
+        if (sr > 0.0f || (sr == 0.0f && cr > 0.0f)) {
+            c = cr;
+            s = sr;
+            perp = -perp;          // the reflection keeps `along` and flips `perp`
+        }
+    }
+    // proposal: rotate by 2*hq (steps 2-3); 1 - cos and sin of the rotation from the half angle
+    float sh, ch;
+    if (TRIG == TRIG_FAST) {
+        __sincosf(hq, &sh, &ch);
+    } else {
+        sincos_quarter(hq, &sh, &ch);
+    }
+    const float sn = 2.0f * sh * ch;
+    const float hh = 2.0f * sh * sh;
+    // step 4: dH = R [cos(theta - psi) - cos(theta + 2hq - psi)]
+    float dH = fmaf(hh, along, sn * perp);
+    float c2 = c - fmaf(c, hh, s * sn);
+    float s2 = s - fmaf(s, hh, -(c * sn));
+    // modulo 2 pi in phi is a half turn in theta: negate the vector, dH -> 2 along - dH
+    if (s2 < 0.0f || (s2 == 0.0f && c2 < 0.0f)) {
+        c2 = -c2;
+        s2 = -s2;
+        dH = 2.0f * along - dH;
+    }
+    // steps 5-6: accept if min(1, exp(-dH/T)) > r
+    const float x = dH * neg_inv_T;
+    const float ap = (TRIG == TRIG_FAST) ? __expf(x) : expf(x);
+    accepted = (dH <= 0.0f) || (ap > r);
+    if (accepted) {
+        c = c2;
+        s = s2;
+    }
+    // one Newton step back to unit length (rounding drift of reflections and rotations)
+    const float g = fmaf(-0.5f, fmaf(c, c, s * s), 1.5f);
+    v = make_float2(c * g, s * g);
+    return accepted ? dH : 0.0f;
+}
+
+// ---------------------------------------------------------------- Algorithm 2 control
+// One sweep's bookkeeping for one grid, given the sweep's accepted energy change dH and
+// acceptance count na.  flip_cur: the sweep wrote the other lattice buffer (tile path).
+//   CTL_RELAX : step 5 (window 5.2, energy 5.3, slope 5.4 every n_f sweeps, counter 5.5)
+//   CTL_FIXED : energy, acceptance and sweep counter of a fixed-window sweep
+//   CTL_SAMPLE: as FIXED, and e accumulated for the e(T, L) table average
+__device__ __forceinline__ void control_step(Ctl& c, const EntryDesc& E, double dH,
+                                             unsigned long long na, int mode, double A_targ,
+                                             double k_a, int n_f, int n_fit, int i_max,
+                                             double* eh, int flip_cur) {
+    if (mode == CTL_RELAX) {
+        if (c.stop) return;
+        c.H += dH;
+        const double A = E.P ? (double)na / (double)E.P : 0.0;
+        if (A < A_targ) {                                                  // 5.2
+            c.a = 1.0 + (double)(c.i + 1) / k_a;
+            c.half_qd = (float)(0.5 * kTwoPi * 0.5 / c.a);
+        }
+        const double en = c.H / E.ngp;                                     // 5.3
+        eh[c.i + 1] = en;
+        if (c.i >= n_fit && c.i % n_f == 0) {                              // 5.4
+            const double* w = eh + (c.i + 2 - n_fit);
+            const double tbar = 0.5 * (double)(n_fit - 1);
+            double ebar = 0.0;
+            for (int t = 0; t < n_fit; ++t) ebar += w[t];
+            ebar /= (double)n_fit;
+            double num = 0.0, den = 0.0;
+            for (int t = 0; t < n_fit; ++t) {
+                const double dt = (double)t - tbar;
+                num += dt * (w[t] - ebar);
+                den += dt * dt;
+            }
+            c.k = num / den;
+        }
+        c.i += 1;                                                          // 5.5
+        c.sweep += 1u;
+        c.A_last = A;
+        c.e_last = en;
+        if (flip_cur) c.cur ^= 1;
+        if (!(c.k < 0.0 && c.i <= i_max)) {
+            c.stop = 1;
+            c.converged = c.k >= 0.0 ? 1 : 0;
+        }
+        return;
+    }
+    c.H += dH;
+    c.A_last = E.P ? (double)na / (double)E.P : 0.0;
+    c.e_last = c.H / E.ngp;
+    if (mode == CTL_SAMPLE) {
+        c.esum += c.e_last;
+        c.nsamp += 1;
+    }
+    c.sweep += 1u;
+    if (flip_cur) c.cur ^= 1;
+}
+
 // ---------------------------------------------------------------- launchers
 // init (mpr_init.cu)
 cudaError_t launch_minmax(const float* z, const uint8_t* mask, long long n, unsigned* keys,
@@ -154,6 +333,21 @@ cudaError_t launch_sample_energy(const EntryDesc* e_host, const float* z, const 
                                  unsigned long long* part_cnt, int* nparts, cudaStream_t st);
 cudaError_t launch_philox(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, size_t n,
                           cudaStream_t st);
+
+// tile path (mpr_tile.cu)
+int tile_list_len();
+int tile_acc_len();
+int tile_sweep_blocks();
+cudaError_t make_tile_maps(const EntryDesc* ents, int n_ent, float2* lat0, float2* lat1,
+                           CUtensorMap* d_maps, cudaStream_t st);
+cudaError_t launch_tile_lists(const TileDesc* tiles, int ntiles, const EntryDesc* ents,
+                              const uint8_t* mask, int all_free, uint16_t* lists, TileCnt* cnts,
+                              cudaStream_t st);
+cudaError_t launch_tile_sweep(const TileArgs& a, int trig, cudaStream_t st);
+cudaError_t launch_tile_predict_out(const TileDesc* tiles, const TileCnt* cnts, const uint16_t* lists,
+                                    const float* acc, const EntryDesc* ents, int tile0, int ntiles,
+                                    int M, double q, double zmin, double zmax, float* zhat,
+                                    cudaStream_t st);
 
 // sweeps (mpr_sweep.cu)
 cudaError_t launch_half_sweep(const SweepArgs& a, int color, int trig, cudaStream_t st);

@@ -7,66 +7,6 @@
 namespace mpr {
 namespace {
 
-enum { TRIG_ACCURATE = 0, TRIG_FAST = 1 };
-
-// One gap-site update (Algorithm 1) in unit-vector form, q = 1/2, theta = phi/2 in [0, pi).
-//   v        current (cos theta, sin theta) of the site
-//   C, S     local field: sums of the neighbours' cos/sin
-//   hq       half the proposal rotation, q * 2 pi (u - 1/2) / a / 2
-//   r        acceptance uniform
-// Returns the accepted energy change (0 if rejected) and writes the new vector.
-template <int TRIG>
-__device__ __forceinline__ float hybrid_update(float2& v, float C, float S, float hq, float r,
-                                               float neg_inv_T, int or_on, bool& accepted) {
-    float c = v.x, s = v.y;
-    // R cos(theta - psi) and R sin(theta - psi), psi the direction of the field
-    const float along = fmaf(c, C, s * S);
-    float perp = fmaf(s, C, -(c * S));
-    // Eq. 6 (energy-conserving reading): reflect theta about psi; keep it only if the
-    // image stays in [0, pi), i.e. sin >= 0 (the point theta = pi is excluded).
-    const float R2 = fmaf(C, C, S * S);
-    if (or_on && R2 > 1e-12f) {
-        const float f = (TRIG == TRIG_FAST) ? __fdividef(2.0f * along, R2) : (2.0f * along) / R2;
-        const float cr = fmaf(f, C, -c), sr = fmaf(f, S, -s);
-        if (sr > 0.0f || (sr == 0.0f && cr > 0.0f)) {
-            c = cr;
-            s = sr;
-            perp = -perp;          // the reflection keeps `along` and flips `perp`
-        }
-    }
-    // proposal: rotate by 2*hq (steps 2-3); 1 - cos and sin of the rotation from the half angle
-    float sh, ch;
-    if (TRIG == TRIG_FAST) {
-        __sincosf(hq, &sh, &ch);
-    } else {
-        sincos_quarter(hq, &sh, &ch);
-    }
-    const float sn = 2.0f * sh * ch;
-    const float hh = 2.0f * sh * sh;
-    // step 4: dH = R [cos(theta - psi) - cos(theta + 2hq - psi)]
-    float dH = fmaf(hh, along, sn * perp);
-    float c2 = c - fmaf(c, hh, s * sn);
-    float s2 = s - fmaf(s, hh, -(c * sn));
-    // modulo 2 pi in phi is a half turn in theta: negate the vector, dH -> 2 along - dH
-    if (s2 < 0.0f || (s2 == 0.0f && c2 < 0.0f)) {
-        c2 = -c2;
-        s2 = -s2;
-        dH = 2.0f * along - dH;
-    }
-    // steps 5-6: accept if min(1, exp(-dH/T)) > r
-    const float x = dH * neg_inv_T;
-    const float ap = (TRIG == TRIG_FAST) ? __expf(x) : expf(x);
-    accepted = (dH <= 0.0f) || (ap > r);
-    if (accepted) {
-        c = c2;
-        s = s2;
-    }
-    // one Newton step back to unit length (rounding drift of reflections and rotations)
-    const float g = fmaf(-0.5f, fmaf(c, c, s * s), 1.5f);
-    v = make_float2(c * g, s * g);
-    return accepted ? dH : 0.0f;
-}
-
 // Half-sweep: every gap site of one colour (all entries), Algorithm 1.
 // Blocks come from a work list (entry, first gap) so that grids of any size share a launch.
 template <int TRIG, bool ACC>
@@ -96,7 +36,7 @@ k_half_sweep(const SweepArgs A, const int color) {
             const uint32_t ent = __ldg(gl + g);
             const int y = (int)(ent >> 16), j = (int)(ent & 0xFFFFu);
             const int s = color ^ (y & 1);
-            const long long k = (long long)(y + 1) * pitch + j + 1;
+            const long long k = (long long)(y + 1) * pitch + j + kPadL;
             const float2 nu = oth[k - pitch], nd = oth[k + pitch];
             const float2 nl = oth[k - 1 + s], nr = oth[k + s];
             const float C = (nu.x + nd.x) + (nl.x + nr.x);
@@ -173,47 +113,8 @@ k_control(Ctl* ctl, Part* part0, Part* part1, const EntryDesc* __restrict__ ents
     dH = s_dH[0];
     na = s_na[0];
     Ctl c = ctl[e];
-    if (mode == CTL_RELAX) {
-        if (!c.stop) {
-            c.H += dH;
-            const double A = E.P ? (double)na / (double)E.P : 0.0;
-            if (A < A_targ) c.a = 1.0 + (double)(c.i + 1) / k_a;          // 5.2
-            const double en = c.H / E.ngp;                                 // 5.3
-            double* eh = ehist + (long long)e * ehist_stride;
-            eh[c.i + 1] = en;
-            if (c.i >= n_fit && c.i % n_f == 0) {                          // 5.4
-                const double* w = eh + (c.i + 2 - n_fit);
-                const double tbar = 0.5 * (double)(n_fit - 1);
-                double ebar = 0.0;
-                for (int t = 0; t < n_fit; ++t) ebar += w[t];
-                ebar /= (double)n_fit;
-                double num = 0.0, den = 0.0;
-                for (int t = 0; t < n_fit; ++t) {
-                    const double dt = (double)t - tbar;
-                    num += dt * (w[t] - ebar);
-                    den += dt * dt;
-                }
-                c.k = num / den;
-            }
-            c.i += 1;                                                      // 5.5
-            c.sweep += 1u;
-            c.A_last = A;
-            c.e_last = en;
-            if (!(c.k < 0.0 && c.i <= i_max)) {
-                c.stop = 1;
-                c.converged = c.k >= 0.0 ? 1 : 0;
-            }
-        }
-    } else {
-        c.H += dH;
-        c.A_last = E.P ? (double)na / (double)E.P : 0.0;
-        c.e_last = c.H / E.ngp;
-        if (mode == CTL_SAMPLE) {
-            c.esum += c.e_last;
-            c.nsamp += 1;
-        }
-        c.sweep += 1u;
-    }
+    control_step(c, E, dH, na, mode, A_targ, k_a, n_f, n_fit, i_max,
+                 ehist + (long long)e * ehist_stride, 0);
     ctl[e] = c;
     if (active && !c.stop) atomicAdd(active, 1);
 }
@@ -232,7 +133,7 @@ __global__ void k_energy(EntryDesc e, const float2* __restrict__ lat, double* pa
         const int y = (int)(t / Wc), j = (int)(t - (long long)y * Wc);
         const int s = y & 1;                                     // colour 0: s = y & 1
         if (2 * j + s >= e.W) continue;
-        const long long k = (long long)(y + 1) * e.pitch + j + 1;
+        const long long k = (long long)(y + 1) * e.pitch + j + kPadL;
         const float2 v = p0[k];
         const float2 a = p1[k - e.pitch], b = p1[k + e.pitch], l = p1[k - 1 + s], r = p1[k + s];
         acc -= (double)fmaf(v.x, a.x, v.y * a.y) + (double)fmaf(v.x, b.x, v.y * b.y) +
@@ -293,7 +194,7 @@ __global__ void k_get_state(EntryDesc e, const float2* __restrict__ lat, float* 
          i += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(i / e.W), x = (int)(i - (long long)y * e.W);
         const long long base = ((x + y) & 1) ? e.plane[1] : e.plane[0];
-        const float2 v = lat[base + (long long)(y + 1) * e.pitch + (x >> 1) + 1];
+        const float2 v = lat[base + (long long)(y + 1) * e.pitch + (x >> 1) + kPadL];
         phi[i] = 2.0f * atan2f(fmaxf(v.y, 0.0f), v.x);
     }
 }
@@ -312,7 +213,7 @@ __global__ void k_set_state(EntryDesc e, float2* __restrict__ lat, const uint32_
         sincosf(0.5f * phi[(long long)y * e.W + x], &s, &co);
         s = fmaxf(s, 0.0f);
         const long long base = c ? e.plane[1] : e.plane[0];
-        lat[base + (long long)(y + 1) * e.pitch + j + 1] = make_float2(co, s);
+        lat[base + (long long)(y + 1) * e.pitch + j + kPadL] = make_float2(co, s);
     }
 }
 

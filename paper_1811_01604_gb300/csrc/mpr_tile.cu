@@ -1,0 +1,513 @@
+// mpr_tile.cu -- fused full sweep over shared-memory tiles with halos.
+//
+// One block owns a TH x TW tile of one grid.  It copies the tile plus a halo of two
+// sites of both colour planes from the current lattice buffer into shared memory,
+// updates colour A (Algorithm 1) on the tile and on a one-site ring around it, then
+// colour B on the tile, and writes the tile's interior to the other lattice buffer.
+// The ring updates duplicate what the neighbouring tiles compute for their own interior:
+// every update is a deterministic function of its neighbours and of its Philox counter
+// {site, sweep, chain, 0}, so the duplicates are bitwise identical and each tile's B
+// pass sees exactly the post-A values of a whole-grid half-sweep.  Reading one buffer
+// and writing the other keeps every tile's halo at the pre-sweep state.
+//
+// Per tile, the gap sites are listed once at set-up (u16 (r << 7) | q in the tile's
+// local region coordinates): colour-A sites inside the tile, then colour-A sites on the
+// ring, then colour-B sites inside the tile, contiguous in a 16-byte aligned slot that is
+// copied into shared memory together with the region.  Accumulators for the equilibrium average
+// use the same order (A interior, then B).
+//
+// The sweep's accepted energy change and acceptance count are reduced per tile; the
+// last tile of a grid to finish (atomic ticket) adds the tiles' partials in tile order
+// and runs the Algorithm 2 control step for that grid in place, so no separate control
+// launch is needed and the sums are bitwise reproducible.
+#include <algorithm>
+#include <vector>
+
+#include "mpr_internal.cuh"
+
+#ifndef MPR_TILE_THREADS
+#define MPR_TILE_THREADS 128
+#endif
+#ifndef MPR_TILE_STAGES
+#define MPR_TILE_STAGES 1
+#endif
+
+namespace mpr {
+
+namespace {
+
+
+template <int TH, int TW>
+struct Geo {
+    static constexpr int RH = TH + 4;                 // region rows (halo 2)
+    static constexpr int RW = TW / 2 + 4;             // region plane columns
+    static constexpr int CAPA = ((TH + 2) * (TW + 2) + 1) / 2;
+    static constexpr int CAPB = TH * TW / 2;
+    static constexpr int LIST = (CAPA + CAPB + 7) / 8 * 8;   // u16 entries per tile (16-byte slots)
+    static constexpr int ACC = TH * TW;               // accumulator floats per tile
+    static_assert(TH % 2 == 0 && TW % 4 == 0, "tile origin parity and 16-byte alignment");
+    static_assert(RW <= 128 && RH <= 512, "entry encoding");
+    static_assert(RW * 8 % 16 == 0, "TMA box rows must be a multiple of 16 bytes");
+    static_assert((2 * RH * RW * 8) % 128 == 0, "list slots stay 16-byte aligned");
+};
+
+// Lists the gap sites of each tile (one warp per tile), row-major in region coordinates.
+template <int TH, int TW>
+__global__ void k_tile_lists(const TileDesc* __restrict__ tiles, int ntiles,
+                             const EntryDesc* __restrict__ ents, const uint8_t* __restrict__ mask,
+                             int all_free, uint16_t* __restrict__ lists, TileCnt* __restrict__ cnts) {
+    using G = Geo<TH, TW>;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (t >= ntiles) return;
+    const TileDesc td = tiles[t];
+    const EntryDesc E = ents[td.entry];
+    const uint8_t* m = mask ? mask + E.site0 : nullptr;
+    uint16_t* out = lists + (long long)t * G::LIST;
+    const unsigned lt = (1u << lane) - 1u;
+    int counts[3] = {0, 0, 0};
+    // list 0: colour A, interior; list 1: colour A, ring; list 2: colour B, interior
+    for (int which = 0; which < 3; ++which) {
+        const int c = which == 2 ? 1 : 0;
+        int n = 0;
+        uint16_t* dst = out + (which == 0 ? 0 : which == 1 ? counts[0] : counts[0] + counts[1]);
+        for (int base = 0; base < G::RH * G::RW; base += 32) {
+            const int idx = base + lane;
+            bool take = false;
+            int r = 0, q = 0;
+            if (idx < G::RH * G::RW) {
+                r = idx / G::RW;
+                q = idx - r * G::RW;
+                const int y = td.y0 - 2 + r;
+                const int s = c ^ (r & 1);
+                const int x = td.x0 + 2 * q - 4 + s;
+                const bool in_grid = y >= 0 && y < E.H && x >= 0 && x < E.W;
+                const bool interior = y >= td.y0 && y < td.y0 + TH && x >= td.x0 && x < td.x0 + TW;
+                const bool ring = !interior && y >= td.y0 - 1 && y <= td.y0 + TH && x >= td.x0 - 1 &&
+                                  x <= td.x0 + TW;
+                const bool gap = in_grid && (all_free || !m[(long long)y * E.W + x]);
+                take = gap && (which == 1 ? ring : interior);
+            }
+            const unsigned b = __ballot_sync(0xffffffffu, take);
+            if (take) dst[n + __popc(b & lt)] = (uint16_t)((r << 7) | q);
+            n += __popc(b);
+        }
+        counts[which] = n;
+    }
+    if (lane == 0) {
+        TileCnt c;
+        c.nA_int = (uint16_t)counts[0];
+        c.nA_ring = (uint16_t)counts[1];
+        c.nB = (uint16_t)counts[2];
+        c._pad = 0;
+        cnts[t] = c;
+    }
+}
+
+// ---------------------------------------------------------------- TMA and mbarrier
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes) : "memory");
+}
+// Tiled bulk copy of a 3-D box (x = plane column, y = padded row, z = colour plane).
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+// Bulk copy of `bytes` (a multiple of 16) from global to shared memory.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_addr(dst)), "l"((unsigned long long)src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after ~0.3 s (2^24 polls with a 20 ns pause) and reports false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < (1u << 24); ++i) {
+        if (mbar_test(bar, parity)) return true;
+        __nanosleep(20);
+    }
+    return false;
+}
+
+// Next tile of this block's strided sequence whose grid is still relaxing (or any tile
+// when stopped grids are not skipped).  Stop flags do not change during a launch: a grid's
+// control step runs after its last tile.
+__device__ __forceinline__ int next_tile(const TileArgs& A, int t) {
+    while (t < A.ntiles && A.skip_stopped && A.ctl[A.tiles[t].entry].stop) t += gridDim.x;
+    return t;
+}
+
+// Per-tile parameters staged in shared memory by the issuing thread.
+struct TileParams {
+    long long pl0, pl1;
+    int y0, x0, W, H, pitch, e, cur, tile0, ntiles, t;
+    uint32_t chain, sweep;
+    float half_qd, neg_inv_T;
+    TileCnt cnt;
+};
+
+// Persistent fused sweep: each block walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// through STAGES shared-memory stages.  Thread 0 issues the TMA copies (region box of
+// both planes plus the tile's gap list, one mbarrier per stage) up to STAGES - 1 tiles
+// ahead of the tile being updated.
+template <int TH, int TW, int TRIG, bool ACC, int NT, int STAGES>
+__global__ void __launch_bounds__(NT)
+k_tile_sweep(const TileArgs A) {
+    using G = Geo<TH, TW>;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    float2(*stage)[2][G::RH][G::RW] = reinterpret_cast<float2(*)[2][G::RH][G::RW]>(dsm);
+    uint16_t(*slist)[G::LIST] =
+        reinterpret_cast<uint16_t(*)[G::LIST]>(dsm + STAGES * 2 * G::RH * G::RW * sizeof(float2));
+    __shared__ TileParams sp[STAGES];
+    __shared__ __align__(8) uint64_t bar[STAGES];
+    __shared__ float s_dE[NT / 32];
+    __shared__ unsigned s_na[NT / 32];
+    __shared__ int s_last;
+    __shared__ int s_fail;
+    __shared__ double s_sum[NT];
+    __shared__ unsigned long long s_cnt[NT];
+    constexpr uint32_t kBytes = 2u * G::RH * G::RW * sizeof(float2);
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < STAGES; ++i) mbar_init(&bar[i], 1);
+        fence_barrier_init();
+        s_fail = 0;
+    }
+    __syncthreads();
+
+    // thread 0 only: stage the parameters of tile t and start its copies into stage st
+    auto issue = [&](int t, int st) {
+        TileParams& P = sp[st];
+        P.t = t;
+        if (t >= A.ntiles) return;
+        const TileDesc td = A.tiles[t];
+        const EntryDesc& E = A.ents[td.entry];
+        const Ctl& c = A.ctl[td.entry];
+        P.pl0 = E.plane[0];
+        P.pl1 = E.plane[1];
+        P.y0 = td.y0;
+        P.x0 = td.x0;
+        P.W = E.W;
+        P.H = E.H;
+        P.pitch = E.pitch;
+        P.e = td.entry;
+        P.cur = c.cur;
+        P.tile0 = E.tile0;
+        P.ntiles = E.ntiles;
+        P.chain = E.chain;
+        P.sweep = c.sweep;
+        P.half_qd = A.use_ctl_a ? c.half_qd : A.half_qd_fixed;
+        P.neg_inv_T = c.neg_inv_T;
+        const TileCnt n = A.cnts[t];
+        P.cnt = n;
+        const uint32_t lbytes = ((uint32_t)(n.nA_int + n.nA_ring + n.nB) * 2u + 15u) & ~15u;
+        mbar_expect_tx(&bar[st], kBytes + lbytes);
+        tma_load_3d(&stage[st][0][0][0], A.maps + 2 * td.entry + c.cur, &bar[st], td.x0 >> 1,
+                    td.y0 - 1, 0);
+        if (lbytes) bulk_load(&slist[st][0], A.lists + (long long)t * G::LIST, lbytes, &bar[st]);
+    };
+
+    int next = next_tile(A, blockIdx.x);                       // thread 0's issue cursor
+    if (threadIdx.x == 0)
+        for (int i = 0; i < STAGES - 1; ++i) {
+            issue(next, i);
+            if (next < A.ntiles) next = next_tile(A, next + gridDim.x);
+        }
+    for (int it = 0;; ++it) {
+        const int st = it % STAGES;
+        if (threadIdx.x == 0) {
+            const int ahead = (it + STAGES - 1) % STAGES;       // the stage freed last iteration
+            issue(next, ahead);
+            if (next < A.ntiles) next = next_tile(A, next + gridDim.x);
+        }
+        __syncthreads();                                        // sp[st].t visible
+        const int t = sp[st].t;
+        if (t >= A.ntiles) break;
+        if (!mbar_wait(&bar[st], (uint32_t)(it / STAGES) & 1u)) {
+            if (threadIdx.x == 0) atomicExch(A.err, 1);
+            s_fail = 1;
+        }
+        __syncthreads();
+        if (s_fail) {
+            // let copies still in flight land before the block's shared memory goes away
+            for (int k = 1; k < STAGES; ++k) {
+                const int j = it + k;
+                if (sp[j % STAGES].t < A.ntiles) mbar_wait(&bar[j % STAGES], (uint32_t)(j / STAGES) & 1u);
+            }
+            return;
+        }
+        float2(*sm)[G::RH][G::RW] = stage[st];
+        const TileParams& P = sp[st];
+        const int W = P.W, H = P.H, pitch = P.pitch;
+        const int y0 = P.y0, x0 = P.x0;
+        const uint32_t chain = P.chain, sweep = P.sweep;
+        const float half_qd = P.half_qd, neg_inv_T = P.neg_inv_T;
+        float2* __restrict__ dst = P.cur ? A.lat[0] : A.lat[1];
+        const TileCnt cnt = P.cnt;
+        const uint16_t* list = slist[st];
+        float* __restrict__ acc = ACC ? A.acc + (long long)t * G::ACC : nullptr;
+        float dE = 0.0f;
+        unsigned nacc = 0;
+
+        // colour A on the tile and its ring
+        const int nA = cnt.nA_int + cnt.nA_ring;
+        for (int k = threadIdx.x; k < nA; k += NT) {
+            const int ent = list[k];
+            const int r = ent >> 7, q = ent & 127;
+            const int s = r & 1;
+            const float2 nu = sm[1][r - 1][q], nd = sm[1][r + 1][q];
+            const float2 nl = sm[1][r][q - 1 + s], nr = sm[1][r][q + s];
+            const float C = (nu.x + nd.x) + (nl.x + nr.x);
+            const float S = (nu.y + nd.y) + (nl.y + nr.y);
+            float2 v = sm[0][r][q];
+            const int y = y0 - 2 + r, x = x0 + 2 * q - 4 + s;
+            const uint32_t site = (uint32_t)y * (uint32_t)W + (uint32_t)x;
+            const uint4 rnd = philox10(make_uint4(site, sweep, chain, 0u), A.key0, A.key1);
+            const float hq = (u24f(rnd.x) - 0.5f) * half_qd;
+            bool accepted;
+            const float d = hybrid_update<TRIG>(v, C, S, hq, u24f(rnd.y), neg_inv_T, A.or_on, accepted);
+            sm[0][r][q] = v;
+            if (k < cnt.nA_int) {
+                dE += d;
+                nacc += accepted ? 1u : 0u;
+                if (ACC) acc[k] += atan2f(v.y, v.x);
+            }
+        }
+        __syncthreads();
+        // colour B on the tile
+        for (int k = threadIdx.x; k < cnt.nB; k += NT) {
+            const int ent = list[nA + k];
+            const int r = ent >> 7, q = ent & 127;
+            const int s = 1 ^ (r & 1);
+            const float2 nu = sm[0][r - 1][q], nd = sm[0][r + 1][q];
+            const float2 nl = sm[0][r][q - 1 + s], nr = sm[0][r][q + s];
+            const float C = (nu.x + nd.x) + (nl.x + nr.x);
+            const float S = (nu.y + nd.y) + (nl.y + nr.y);
+            float2 v = sm[1][r][q];
+            const int y = y0 - 2 + r, x = x0 + 2 * q - 4 + s;
+            const uint32_t site = (uint32_t)y * (uint32_t)W + (uint32_t)x;
+            const uint4 rnd = philox10(make_uint4(site, sweep, chain, 0u), A.key0, A.key1);
+            const float hq = (u24f(rnd.x) - 0.5f) * half_qd;
+            bool accepted;
+            dE += hybrid_update<TRIG>(v, C, S, hq, u24f(rnd.y), neg_inv_T, A.or_on, accepted);
+            nacc += accepted ? 1u : 0u;
+            sm[1][r][q] = v;
+            if (ACC) acc[cnt.nA_int + k] += atan2f(v.y, v.x);
+        }
+        __syncthreads();
+        // interior rows of both colours to the other buffer (samples included)
+        constexpr int I2 = TW / 4;                    // float4 per interior row
+        for (int idx = threadIdx.x; idx < 2 * TH * I2; idx += NT) {
+            const int c = idx / (TH * I2);
+            const int rem = idx - c * (TH * I2);
+            const int ri = rem / I2, q2 = rem - ri * I2;
+            const int y = y0 + ri;
+            const int pc = (x0 >> 1) + 2 + 2 * q2;
+            if (y < H && pc < pitch) {
+                const float4 v = *reinterpret_cast<const float4*>(&sm[c][ri + 2][2 + 2 * q2]);
+                *reinterpret_cast<float4*>(dst + (c ? P.pl1 : P.pl0) + (long long)(y + 1) * pitch + pc) = v;
+            }
+        }
+        // tile partials; the grid's last tile runs the control step
+        dE = warp_sum(dE);
+        nacc = warp_sum(nacc);
+        if ((threadIdx.x & 31) == 0) {
+            s_dE[threadIdx.x >> 5] = dE;
+            s_na[threadIdx.x >> 5] = nacc;
+        }
+        __syncthreads();                              // also: stage st and its list are free
+        if (threadIdx.x == 0) {
+            double tt = 0.0;
+            unsigned na = 0;
+            for (int i = 0; i < NT / 32; ++i) { tt += (double)s_dE[i]; na += s_na[i]; }
+            A.part_dH[t] = tt;
+            A.part_na[t] = na;
+            __threadfence();
+            const unsigned prev = atomicAdd(A.ticket + P.e, 1u);
+            s_last = prev == (unsigned)(P.ntiles - 1);
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            double tt = 0.0;
+            unsigned long long na = 0;
+            for (int i = threadIdx.x; i < P.ntiles; i += NT) {
+                tt += *((volatile double*)A.part_dH + P.tile0 + i);
+                na += *((volatile unsigned*)A.part_na + P.tile0 + i);
+            }
+            s_sum[threadIdx.x] = tt;
+            s_cnt[threadIdx.x] = na;
+            __syncthreads();
+            for (int o = NT / 2; o > 0; o >>= 1) {
+                if ((int)threadIdx.x < o) {
+                    s_sum[threadIdx.x] += s_sum[threadIdx.x + o];
+                    s_cnt[threadIdx.x] += s_cnt[threadIdx.x + o];
+                }
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) {
+                Ctl c = A.ctl[P.e];
+                control_step(c, A.ents[P.e], s_sum[0], s_cnt[0], A.mode, A.A_targ, A.k_a, A.n_f,
+                             A.n_fit, A.i_max, A.ehist + (long long)P.e * A.ehist_stride, 1);
+                A.ctl[P.e] = c;
+                A.ticket[P.e] = 0u;
+                if (A.active && !c.stop) atomicAdd(A.active, 1);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// zhat at the gap sites of every tile (same mean and inverse map as the list path).
+template <int TH, int TW>
+__global__ void k_tile_predict_out(const TileDesc* __restrict__ tiles, const TileCnt* __restrict__ cnts,
+                                   const uint16_t* __restrict__ lists, const float* __restrict__ acc,
+                                   const EntryDesc* __restrict__ ents, int M, double q, double zmin,
+                                   double zmax, float* __restrict__ zhat) {
+    using G = Geo<TH, TW>;
+    const int tile = blockIdx.x;
+    const TileDesc td = tiles[tile];
+    const EntryDesc E = ents[td.entry];
+    const TileCnt cnt = cnts[tile];
+    const uint16_t* list = lists + (long long)tile * G::LIST;
+    const float* a = acc + (long long)tile * G::ACC;
+    const int nA = cnt.nA_int + cnt.nA_ring;
+    const double f = (zmax - zmin) / (kTwoPi * q * (double)M);
+    for (int k = threadIdx.x; k < cnt.nA_int + cnt.nB; k += blockDim.x) {
+        const bool isA = k < cnt.nA_int;
+        const int ent = isA ? list[k] : list[nA + (k - cnt.nA_int)];
+        const int r = ent >> 7, qq = ent & 127;
+        const int s = (isA ? 0 : 1) ^ (r & 1);
+        const int y = td.y0 - 2 + r, x = td.x0 + 2 * qq - 4 + s;
+        double v = zmin + (double)a[k] * f;
+        v = v < zmin ? zmin : (v > zmax ? zmax : v);
+        zhat[E.site0 + (long long)y * E.W + x] = (float)v;
+    }
+}
+
+}  // namespace
+
+// Tensor maps of every entry's two lattice buffers, viewed as 3-D boxes
+// {plane column, padded row, colour}: 8-byte elements, zero fill out of bounds.
+cudaError_t make_tile_maps(const EntryDesc* ents, int n_ent, float2* lat0, float2* lat1,
+                           CUtensorMap* d_maps, cudaStream_t st) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    using G = Geo<kTileH, kTileW>;
+    std::vector<CUtensorMap> maps((size_t)2 * n_ent);
+    for (int e = 0; e < n_ent; ++e) {
+        const EntryDesc& E = ents[e];
+        for (int b = 0; b < 2; ++b) {
+            float2* base = (b ? lat1 : lat0) + E.plane[0];
+            const cuuint64_t dims[3] = {(cuuint64_t)E.pitch, (cuuint64_t)E.prows, 2};
+            const cuuint64_t strides[2] = {(cuuint64_t)E.pitch * 8, (cuuint64_t)E.prows * E.pitch * 8};
+            const cuuint32_t box[3] = {(cuuint32_t)G::RW, (cuuint32_t)G::RH, 2};
+            const cuuint32_t estr[3] = {1, 1, 1};
+            CUresult r = encode(&maps[2 * e + b], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, base, dims,
+                                strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        }
+    }
+    return cudaMemcpyAsync(d_maps, maps.data(), maps.size() * sizeof(CUtensorMap),
+                           cudaMemcpyHostToDevice, st);
+}
+
+constexpr int kNT = MPR_TILE_THREADS;           // threads per tile block
+constexpr int kST = MPR_TILE_STAGES;            // shared-memory stages per block
+constexpr int kSmem = kST * 2 * Geo<kTileH, kTileW>::RH * Geo<kTileH, kTileW>::RW * 8 +
+                      kST * Geo<kTileH, kTileW>::LIST * 2;
+
+// Opts the sweep kernels into their dynamic shared memory (more than the default 48 KB)
+// and returns the persistent grid size: blocks per SM at that footprint times the SMs.
+// Called from set-up code, never under stream capture.
+int tile_sweep_blocks() {
+    static int blocks = 0;
+    if (!blocks) {
+        cudaFuncSetAttribute(k_tile_sweep<kTileH, kTileW, TRIG_ACCURATE, true, kNT, kST>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        cudaFuncSetAttribute(k_tile_sweep<kTileH, kTileW, TRIG_ACCURATE, false, kNT, kST>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        cudaFuncSetAttribute(k_tile_sweep<kTileH, kTileW, TRIG_FAST, true, kNT, kST>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        cudaFuncSetAttribute(k_tile_sweep<kTileH, kTileW, TRIG_FAST, false, kNT, kST>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per, k_tile_sweep<kTileH, kTileW, TRIG_ACCURATE, true, kNT, kST>, kNT, kSmem);
+        blocks = std::max(1, sms * std::max(1, per));
+    }
+    return blocks;
+}
+
+int tile_list_len() { return Geo<kTileH, kTileW>::LIST; }
+int tile_acc_len() { return Geo<kTileH, kTileW>::ACC; }
+
+cudaError_t launch_tile_lists(const TileDesc* tiles, int ntiles, const EntryDesc* ents,
+                              const uint8_t* mask, int all_free, uint16_t* lists, TileCnt* cnts,
+                              cudaStream_t st) {
+    if (ntiles == 0) return cudaSuccess;
+    count_launches(1, st);
+    k_tile_lists<kTileH, kTileW><<<(ntiles * 32 + 127) / 128, 128, 0, st>>>(tiles, ntiles, ents, mask,
+                                                                            all_free, lists, cnts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_sweep(const TileArgs& a, int trig, cudaStream_t st) {
+    if (a.ntiles == 0) return cudaSuccess;
+    count_launches(1, st);
+    const bool acc = a.acc != nullptr;
+    const int nb = std::min(a.ntiles, tile_sweep_blocks());
+    if (trig == TRIG_FAST) {
+        if (acc) k_tile_sweep<kTileH, kTileW, TRIG_FAST, true, kNT, kST><<<nb, kNT, kSmem, st>>>(a);
+        else k_tile_sweep<kTileH, kTileW, TRIG_FAST, false, kNT, kST><<<nb, kNT, kSmem, st>>>(a);
+    } else {
+        if (acc) k_tile_sweep<kTileH, kTileW, TRIG_ACCURATE, true, kNT, kST><<<nb, kNT, kSmem, st>>>(a);
+        else k_tile_sweep<kTileH, kTileW, TRIG_ACCURATE, false, kNT, kST><<<nb, kNT, kSmem, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_predict_out(const TileDesc* tiles, const TileCnt* cnts, const uint16_t* lists,
+                                    const float* acc, const EntryDesc* ents, int tile0, int ntiles,
+                                    int M, double q, double zmin, double zmax, float* zhat,
+                                    cudaStream_t st) {
+    if (ntiles == 0) return cudaSuccess;
+    count_launches(1, st);
+    k_tile_predict_out<kTileH, kTileW><<<ntiles, 256, 0, st>>>(
+        tiles + tile0, cnts + tile0, lists + (long long)tile0 * tile_list_len(),
+        acc + (long long)tile0 * tile_acc_len(), ents, M, q, zmin, zmax, zhat);
+    return cudaGetLastError();
+}
+
+}  // namespace mpr

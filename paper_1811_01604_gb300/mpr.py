@@ -19,7 +19,7 @@ MPR_OK, MPR_EINVAL, MPR_ENOMEM, MPR_ECUDA, MPR_ENODATA, MPR_ENOPAIRS, MPR_ETIMEO
     MPR_ENOTEQUIL, MPR_ESTATE = range(9)
 MPR_OR_CONSERVING, MPR_OR_NONE = 0, 2
 MPR_TRIG_ACCURATE, MPR_TRIG_FAST = 0, 1
-MPR_EXEC_AUTO, MPR_EXEC_GRAPH, MPR_EXEC_PERSISTENT = 0, 1, 2
+MPR_EXEC_AUTO, MPR_EXEC_LIST, MPR_EXEC_TILE = 0, 1, 2
 
 
 class MprError(RuntimeError):
@@ -68,7 +68,7 @@ _SIGS = [
     ("mpr_get_state", _I, [_VP, _VP, ctypes.POINTER(ctypes.c_uint32)]),
     ("mpr_set_state", _I, [_VP, _VP, ctypes.c_uint32]),
     ("mpr_get_info", _I, [_VP] + [ctypes.POINTER(_D)] * 6),
-    ("mpr_time_half_sweeps", _I, [_VP, _I, _D, ctypes.POINTER(_D)]),
+    ("mpr_time_sweeps", _I, [_VP, _I, _D, ctypes.POINTER(_D)]),
     ("mpr_kernel_launches", ctypes.c_uint64, []),
     ("mpr_sample_energy_static", _I, [_VP, _VP, _I, _I, _D, ctypes.POINTER(_D),
                                       ctypes.POINTER(ctypes.c_longlong), _VP]),
@@ -205,9 +205,9 @@ def mpr_get_info(ctx) -> dict:
     return {k: x.value for k, x in zip(keys, v)}
 
 
-def mpr_time_half_sweeps(ctx, n: int, a: float) -> float:
+def mpr_time_sweeps(ctx, n: int, a: float) -> float:
     ms = ctypes.c_double()
-    _check(ctx, lib().mpr_time_half_sweeps(ctx, int(n), float(a), ctypes.byref(ms)))
+    _check(ctx, lib().mpr_time_sweeps(ctx, int(n), float(a), ctypes.byref(ms)))
     return ms.value
 
 

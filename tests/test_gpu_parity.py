@@ -70,8 +70,12 @@ def test_map_sample_energy_and_energy(name):
         mpr.mpr_free(ctx)
 
 
-def _sweep_parity(z, mask, T, a_list, sweeps, trig=mpr.MPR_TRIG_ACCURATE, seed=11):
-    ctx = make_ctx(z, mask, seed=seed, trig_mode=trig)
+EXEC = [mpr.MPR_EXEC_TILE, mpr.MPR_EXEC_LIST]
+
+
+def _sweep_parity(z, mask, T, a_list, sweeps, trig=mpr.MPR_TRIG_ACCURATE, seed=11,
+                  exec_mode=mpr.MPR_EXEC_TILE):
+    ctx = make_ctx(z, mask, seed=seed, trig_mode=trig, exec_mode=exec_mode)
     flips = decisions = 0
     worst = 0.0
     try:
@@ -98,21 +102,54 @@ def _sweep_parity(z, mask, T, a_list, sweeps, trig=mpr.MPR_TRIG_ACCURATE, seed=1
     return flips, decisions, worst
 
 
-def test_single_sweep_parity_grid64():
+@pytest.mark.parametrize("exec_mode", EXEC)
+def test_single_sweep_parity_grid64(exec_mode):
     c = synth.config("grid64")
     flips, n, worst = _sweep_parity(c["z"], c["mask"], T=0.12, a_list=[1.0, 2.5, 6.0, 20.0],
-                                    sweeps=120)
+                                    sweeps=120, exec_mode=exec_mode)
     assert worst <= 1e-5
     assert flips <= 1e-6 * n + 1, (flips, n)
 
 
-def test_single_sweep_parity_256_ragged_gaps():
+@pytest.mark.parametrize("exec_mode", EXEC)
+def test_single_sweep_parity_256_ragged_gaps(exec_mode):
     z = synth.wm_field(256, 0.5, 5.0, seed=21, W=250)
     mask = synth.mask_uniform(256, 250, 0.5, seed=22)
-    flips, n, worst = _sweep_parity(z, mask, T=0.1, a_list=[1.0, 4.0, 9.0], sweeps=40)
+    flips, n, worst = _sweep_parity(z, mask, T=0.1, a_list=[1.0, 4.0, 9.0], sweeps=40,
+                                    exec_mode=exec_mode)
     assert n > 1_000_000
     assert worst <= 1e-5
     assert flips <= 1e-6 * n + 1, (flips, n)
+
+
+@pytest.mark.parametrize("shape", [(64, 64), (37, 601), (200, 130), (1, 9), (3, 1)])
+def test_tile_and_list_paths_are_bitwise_identical(shape):
+    # same arithmetic and the same Philox counters: the fused tile sweep (with its
+    # duplicated ring updates) must reproduce the two half-sweep launches bit for bit
+    H, W = shape
+    z = synth.wm_field(H, 0.5, 4.0, seed=13, W=W) if H > 1 and W > 1 else \
+        np.arange(H * W, dtype=np.float32).reshape(H, W)
+    mask = synth.mask_uniform(H, W, 0.45, seed=14)
+    mask.flat[0] = 1; mask.flat[-1] = 1
+    states = []
+    for mode in (mpr.MPR_EXEC_LIST, mpr.MPR_EXEC_TILE):
+        ctx = make_ctx(z, mask, seed=17, exec_mode=mode)
+        try:
+            mpr.mpr_set_T(ctx, 0.08)
+            for a in (1.0, 3.0, 7.5, 1.0, 12.0):
+                mpr.mpr_sweep(ctx, 3, a)
+            mpr.mpr_sweep(ctx, 9, 2.0)                  # one graph of 8 plus one direct sweep
+            phi = np.zeros((H, W), np.float32)
+            sw = mpr.mpr_get_state(ctx, phi)
+            states.append((phi, sw, mpr.mpr_get_info(ctx)))
+        finally:
+            mpr.mpr_free(ctx)
+    (p0, s0, i0), (p1, s1, i1) = states
+    assert s0 == s1 == 24
+    assert np.array_equal(p0.view(np.uint32), p1.view(np.uint32))
+    assert i0["H_exact"] == i1["H_exact"]
+    # tracked energies add the same changes grouped differently (FP32 partial sums)
+    assert abs(i0["H_tracked"] - i1["H_tracked"]) <= 1e-8 * max(1.0, abs(i1["H_exact"]))
 
 
 def test_tracked_energy_matches_exact_energy():
@@ -229,6 +266,22 @@ def test_degenerate_inputs():
             assert zh.flat[0] == 0 and zh.flat[-1] == H * W - 1
         finally:
             mpr.mpr_free(ctx)
+
+
+def test_tile_path_fill_matches_list_path_fill():
+    c = synth.config("grid64")
+    out = []
+    for mode in (mpr.MPR_EXEC_LIST, mpr.MPR_EXEC_TILE):
+        ctx = make_ctx(c["z"], c["mask"], seed=9, KT=6, T_cap=32, M_T=30, M=20, exec_mode=mode)
+        try:
+            zh = np.zeros_like(c["z"])
+            st = mpr.mpr_fill(ctx, zh)
+            out.append((zh, st.sweeps, mpr.mpr_get_info(ctx)["T"]))
+        finally:
+            mpr.mpr_free(ctx)
+    (z0, n0, T0), (z1, n1, T1) = out
+    assert T0 == T1 and n0 == n1
+    assert np.abs(z0.astype(np.float64) - z1).max() < 1e-3     # same chain; sums differ in order
 
 
 def test_runs_are_bitwise_reproducible():
