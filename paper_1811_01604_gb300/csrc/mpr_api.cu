@@ -252,7 +252,7 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
         EntryDesc& E = b.ents[e];
         E.tile0 = (int)tiles.size();
         for (int y0 = 0; y0 < E.H; y0 += kTileH)
-            for (int x0 = 0; x0 < E.W; x0 += kTileW) tiles.push_back(TileDesc{e, y0, x0, 0});
+            for (int x0 = 0; x0 < E.W; x0 += kTileW) tiles.push_back(TileDesc{e, y0, x0, 0, 0, 0, {0, 0}});
         E.ntiles = (int)tiles.size() - E.tile0;
     }
     CU(dalloc(&b.d_ents, b.n_ent));
@@ -269,6 +269,8 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
         CU(dalloc(&b.d_tacc, tiles.size() * (size_t)tile_acc_len()));
         CU(dalloc(&b.d_tpart_dH, tiles.size()));
         CU(dalloc(&b.d_tpart_na, tiles.size()));
+        CU(cudaMemsetAsync(b.d_tpart_dH, 0, sizeof(double) * tiles.size(), st));   // slots that
+        CU(cudaMemsetAsync(b.d_tpart_na, 0, sizeof(unsigned) * tiles.size(), st)); // never end a run stay 0
         CU(dalloc(&b.d_ticket, (size_t)b.n_ent));
         CU(cudaMemsetAsync(b.d_ticket, 0, sizeof(unsigned) * b.n_ent, st));
         CU(launch_tile_lists(b.d_tiles, b.ntiles, b.d_ents, mask_base, all_free, b.d_lists, b.d_cnts, st));

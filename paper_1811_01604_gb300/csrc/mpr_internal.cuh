@@ -74,15 +74,24 @@ struct Part {                 // one sweep block's energy change and acceptance 
 };
 
 // Tile path (mpr_tile.cu): tiles of kTileH x kTileW grid sites.
-constexpr int kTileH = 32;
-constexpr int kTileW = 64;
+#ifndef MPR_TILE_H
+#define MPR_TILE_H 16
+#endif
+#ifndef MPR_TILE_W
+#define MPR_TILE_W 128
+#endif
+constexpr int kTileH = MPR_TILE_H;
+constexpr int kTileW = MPR_TILE_W;
 constexpr int kTileRH = kTileH + 4;           // rows of a tile's TMA box (halo 2)
 constexpr int kTileRW = kTileW / 2 + 4;       // plane columns of a tile's TMA box
 
-struct TileDesc {             // one tile: its grid and the grid coordinates of its origin
+struct TileDesc {             // one tile: its grid, origin, and gap-list counts (set-up)
     int entry;
     int y0, x0;
-    int _pad;
+    int nA_int;               // colour A inside the tile
+    int nA_ring;              // colour A on the one-site ring
+    int nB;                   // colour B inside the tile
+    int _pad[2];
 };
 
 struct TileCnt {              // gap sites listed for one tile
@@ -340,7 +349,7 @@ int tile_acc_len();
 int tile_sweep_blocks();
 cudaError_t make_tile_maps(const EntryDesc* ents, int n_ent, float2* lat0, float2* lat1,
                            CUtensorMap* d_maps, cudaStream_t st);
-cudaError_t launch_tile_lists(const TileDesc* tiles, int ntiles, const EntryDesc* ents,
+cudaError_t launch_tile_lists(TileDesc* tiles, int ntiles, const EntryDesc* ents,
                               const uint8_t* mask, int all_free, uint16_t* lists, TileCnt* cnts,
                               cudaStream_t st);
 cudaError_t launch_tile_sweep(const TileArgs& a, int trig, cudaStream_t st);

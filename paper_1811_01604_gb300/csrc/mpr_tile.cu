@@ -31,6 +31,9 @@
 #ifndef MPR_TILE_STAGES
 #define MPR_TILE_STAGES 1
 #endif
+#ifndef MPR_TILE_MINB
+#define MPR_TILE_MINB 8                         // blocks per SM the register budget must allow
+#endif
 
 namespace mpr {
 
@@ -47,13 +50,14 @@ struct Geo {
     static constexpr int ACC = TH * TW;               // accumulator floats per tile
     static_assert(TH % 2 == 0 && TW % 4 == 0, "tile origin parity and 16-byte alignment");
     static_assert(RW <= 128 && RH <= 512, "entry encoding");
+
     static_assert(RW * 8 % 16 == 0, "TMA box rows must be a multiple of 16 bytes");
     static_assert((2 * RH * RW * 8) % 128 == 0, "list slots stay 16-byte aligned");
 };
 
 // Lists the gap sites of each tile (one warp per tile), row-major in region coordinates.
 template <int TH, int TW>
-__global__ void k_tile_lists(const TileDesc* __restrict__ tiles, int ntiles,
+__global__ void k_tile_lists(TileDesc* __restrict__ tiles, int ntiles,
                              const EntryDesc* __restrict__ ents, const uint8_t* __restrict__ mask,
                              int all_free, uint16_t* __restrict__ lists, TileCnt* __restrict__ cnts) {
     using G = Geo<TH, TW>;
@@ -100,6 +104,9 @@ __global__ void k_tile_lists(const TileDesc* __restrict__ tiles, int ntiles,
         c.nB = (uint16_t)counts[2];
         c._pad = 0;
         cnts[t] = c;
+        tiles[t].nA_int = counts[0];
+        tiles[t].nA_ring = counts[1];
+        tiles[t].nB = counts[2];
     }
 }
 
@@ -133,6 +140,23 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         ::"r"(smem_addr(dst)), "l"((unsigned long long)src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
 }
+// Bulk copy of `bytes` (a multiple of 16) from shared to global memory, tracked by the
+// issuing thread's bulk-async group.
+__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                 ::"l"((unsigned long long)gdst), "r"(smem_addr(ssrc)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Waits until this thread's bulk stores have read their shared-memory source.
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// Waits until this thread's bulk stores are complete.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Orders this thread's generic-proxy shared-memory writes before later async-proxy reads.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -141,20 +165,13 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 // Bounded wait: gives up after ~0.3 s (2^24 polls with a 20 ns pause) and reports false.
+// (Polling measured faster here than the hardware-suspended try_wait.)
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     for (uint32_t i = 0; i < (1u << 24); ++i) {
         if (mbar_test(bar, parity)) return true;
         __nanosleep(20);
     }
     return false;
-}
-
-// Next tile of this block's strided sequence whose grid is still relaxing (or any tile
-// when stopped grids are not skipped).  Stop flags do not change during a launch: a grid's
-// control step runs after its last tile.
-__device__ __forceinline__ int next_tile(const TileArgs& A, int t) {
-    while (t < A.ntiles && A.skip_stopped && A.ctl[A.tiles[t].entry].stop) t += gridDim.x;
-    return t;
 }
 
 // Per-tile parameters staged in shared memory by the issuing thread.
@@ -171,7 +188,7 @@ struct TileParams {
 // both planes plus the tile's gap list, one mbarrier per stage) up to STAGES - 1 tiles
 // ahead of the tile being updated.
 template <int TH, int TW, int TRIG, bool ACC, int NT, int STAGES>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, MPR_TILE_MINB)
 k_tile_sweep(const TileArgs A) {
     using G = Geo<TH, TW>;
     extern __shared__ __align__(128) unsigned char dsm[];
@@ -182,7 +199,9 @@ k_tile_sweep(const TileArgs A) {
     __shared__ __align__(8) uint64_t bar[STAGES];
     __shared__ float s_dE[NT / 32];
     __shared__ unsigned s_na[NT / 32];
-    __shared__ int s_last;
+    __shared__ int s_last;                                     // this tile ends a run
+    __shared__ int s_runlen;                                   // tiles in the current run
+    __shared__ int s_grid_done;                                // this block completed the grid
     __shared__ int s_fail;
     __shared__ double s_sum[NT];
     __shared__ unsigned long long s_cnt[NT];
@@ -192,57 +211,90 @@ k_tile_sweep(const TileArgs A) {
         for (int i = 0; i < STAGES; ++i) mbar_init(&bar[i], 1);
         fence_barrier_init();
         s_fail = 0;
+        s_runlen = 0;
     }
     __syncthreads();
 
-    // thread 0 only: stage the parameters of tile t and start its copies into stage st
-    auto issue = [&](int t, int st) {
+    // Thread 0 only.  Tile descriptors are one 16-byte load; a grid's parameters do not
+    // change during a launch, so they are reloaded only when the grid changes.
+    __shared__ TileParams cp_;                                 // thread 0's cache
+    __shared__ const CUtensorMap* cmap;
+    __shared__ int cstop;
+    int ce = -1;
+    auto load_entry = [&](int e) {
+        const EntryDesc& E = A.ents[e];
+        const Ctl& c = A.ctl[e];
+        cp_.pl0 = E.plane[0];
+        cp_.pl1 = E.plane[1];
+        cp_.W = E.W;
+        cp_.H = E.H;
+        cp_.pitch = E.pitch;
+        cp_.e = e;
+        cp_.cur = c.cur;
+        cp_.tile0 = E.tile0;
+        cp_.ntiles = E.ntiles;
+        cp_.chain = E.chain;
+        cp_.sweep = c.sweep;
+        cp_.half_qd = A.use_ctl_a ? c.half_qd : A.half_qd_fixed;
+        cp_.neg_inv_T = c.neg_inv_T;
+        cstop = A.skip_stopped ? c.stop : 0;
+        cmap = A.maps + 2 * e + c.cur;
+        ce = e;
+    };
+    // thread 0's issue cursor and the descriptor of the tile at the cursor (prefetched, so
+    // that staging a tile never waits on a global load)
+    int next = blockIdx.x;
+    TileDesc dnext;
+    if (threadIdx.x == 0 && next < A.ntiles) dnext = A.tiles[next];
+    // stages the next tile of this block whose grid is still relaxing into stage st
+    auto issue = [&](int st) {
         TileParams& P = sp[st];
-        P.t = t;
-        if (t >= A.ntiles) return;
-        const TileDesc td = A.tiles[t];
-        const EntryDesc& E = A.ents[td.entry];
-        const Ctl& c = A.ctl[td.entry];
-        P.pl0 = E.plane[0];
-        P.pl1 = E.plane[1];
-        P.y0 = td.y0;
-        P.x0 = td.x0;
-        P.W = E.W;
-        P.H = E.H;
-        P.pitch = E.pitch;
-        P.e = td.entry;
-        P.cur = c.cur;
-        P.tile0 = E.tile0;
-        P.ntiles = E.ntiles;
-        P.chain = E.chain;
-        P.sweep = c.sweep;
-        P.half_qd = A.use_ctl_a ? c.half_qd : A.half_qd_fixed;
-        P.neg_inv_T = c.neg_inv_T;
-        const TileCnt n = A.cnts[t];
-        P.cnt = n;
-        const uint32_t lbytes = ((uint32_t)(n.nA_int + n.nA_ring + n.nB) * 2u + 15u) & ~15u;
-        mbar_expect_tx(&bar[st], kBytes + lbytes);
-        tma_load_3d(&stage[st][0][0][0], A.maps + 2 * td.entry + c.cur, &bar[st], td.x0 >> 1,
-                    td.y0 - 1, 0);
-        if (lbytes) bulk_load(&slist[st][0], A.lists + (long long)t * G::LIST, lbytes, &bar[st]);
+        for (;;) {
+            if (next >= A.ntiles) { P.t = A.ntiles; return; }
+            const TileDesc d = dnext;
+            const int cur_t = next;
+            next += gridDim.x;
+            if (next < A.ntiles) dnext = A.tiles[next];
+            if (d.entry != ce) load_entry(d.entry);
+            if (!cstop) {
+                P = cp_;
+                P.t = cur_t;
+                P.y0 = d.y0;
+                P.x0 = d.x0;
+                TileCnt n;
+                n.nA_int = (uint16_t)d.nA_int;
+                n.nA_ring = (uint16_t)d.nA_ring;
+                n.nB = (uint16_t)d.nB;
+                n._pad = 0;
+                P.cnt = n;
+                const uint32_t lbytes = ((uint32_t)(d.nA_int + d.nA_ring + d.nB) * 2u + 15u) & ~15u;
+                mbar_expect_tx(&bar[st], kBytes + lbytes);
+                tma_load_3d(&stage[st][0][0][0], cmap, &bar[st], d.x0 >> 1, d.y0 - 1, 0);
+                if (lbytes)
+                    bulk_load(&slist[st][0], A.lists + (long long)cur_t * G::LIST, lbytes, &bar[st]);
+                return;
+            }
+        }
     };
 
-    int next = next_tile(A, blockIdx.x);                       // thread 0's issue cursor
     if (threadIdx.x == 0)
-        for (int i = 0; i < STAGES - 1; ++i) {
-            issue(next, i);
-            if (next < A.ntiles) next = next_tile(A, next + gridDim.x);
-        }
+        for (int i = 0; i < STAGES - 1; ++i) issue(i);
+    // energy change and acceptance count of the block's current run of tiles of one grid
+    float dE = 0.0f;
+    unsigned nacc = 0;
     for (int it = 0;; ++it) {
         const int st = it % STAGES;
-        if (threadIdx.x == 0) {
-            const int ahead = (it + STAGES - 1) % STAGES;       // the stage freed last iteration
-            issue(next, ahead);
-            if (next < A.ntiles) next = next_tile(A, next + gridDim.x);
+        if (threadIdx.x < 32) {
+            bulk_wait_read();                           // stores of the freed stage have read it
+            __syncwarp();
+            if (threadIdx.x == 0) issue((it + STAGES - 1) % STAGES);   // the stage freed last iteration
         }
         __syncthreads();                                        // sp[st].t visible
         const int t = sp[st].t;
-        if (t >= A.ntiles) break;
+        if (t >= A.ntiles) {
+            if (threadIdx.x < 32) bulk_wait_all();
+            break;
+        }
         if (!mbar_wait(&bar[st], (uint32_t)(it / STAGES) & 1u)) {
             if (threadIdx.x == 0) atomicExch(A.err, 1);
             s_fail = 1;
@@ -266,114 +318,124 @@ k_tile_sweep(const TileArgs A) {
         const TileCnt cnt = P.cnt;
         const uint16_t* list = slist[st];
         float* __restrict__ acc = ACC ? A.acc + (long long)t * G::ACC : nullptr;
-        float dE = 0.0f;
-        unsigned nacc = 0;
 
-        // colour A on the tile and its ring
+        // colour A on the tile and its ring, then colour B on the tile
         const int nA = cnt.nA_int + cnt.nA_ring;
-        for (int k = threadIdx.x; k < nA; k += NT) {
-            const int ent = list[k];
-            const int r = ent >> 7, q = ent & 127;
-            const int s = r & 1;
-            const float2 nu = sm[1][r - 1][q], nd = sm[1][r + 1][q];
-            const float2 nl = sm[1][r][q - 1 + s], nr = sm[1][r][q + s];
-            const float C = (nu.x + nd.x) + (nl.x + nr.x);
-            const float S = (nu.y + nd.y) + (nl.y + nr.y);
-            float2 v = sm[0][r][q];
-            const int y = y0 - 2 + r, x = x0 + 2 * q - 4 + s;
-            const uint32_t site = (uint32_t)y * (uint32_t)W + (uint32_t)x;
-            const uint4 rnd = philox10(make_uint4(site, sweep, chain, 0u), A.key0, A.key1);
-            const float hq = (u24f(rnd.x) - 0.5f) * half_qd;
-            bool accepted;
-            const float d = hybrid_update<TRIG>(v, C, S, hq, u24f(rnd.y), neg_inv_T, A.or_on, accepted);
-            sm[0][r][q] = v;
-            if (k < cnt.nA_int) {
-                dE += d;
-                nacc += accepted ? 1u : 0u;
-                if (ACC) acc[k] += atan2f(v.y, v.x);
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+            const int c = pass;                           // colour being updated
+            const int n = pass ? cnt.nB : nA;
+            const uint16_t* lst = pass ? list + nA : list;
+            float2(*own)[G::RW] = sm[c];
+            float2(*oth)[G::RW] = sm[c ^ 1];
+            for (int k = threadIdx.x; k < n; k += NT) {
+                const int ent = lst[k];
+                const int r = ent >> 7, q = ent & 127;
+                const int s = c ^ (r & 1);
+                const float2 nu = oth[r - 1][q], nd = oth[r + 1][q];
+                const float2 nl = oth[r][q - 1 + s], nr = oth[r][q + s];
+                const float C = (nu.x + nd.x) + (nl.x + nr.x);
+                const float S = (nu.y + nd.y) + (nl.y + nr.y);
+                float2 v = own[r][q];
+                const int y = y0 - 2 + r, x = x0 + 2 * q - 4 + s;
+                const uint32_t site = (uint32_t)y * (uint32_t)W + (uint32_t)x;
+                const uint4 rnd = philox10(make_uint4(site, sweep, chain, 0u), A.key0, A.key1);
+                const float hq = (u24f(rnd.x) - 0.5f) * half_qd;
+                bool accepted;
+                const float d = hybrid_update<TRIG>(v, C, S, hq, u24f(rnd.y), neg_inv_T, A.or_on, accepted);
+                own[r][q] = v;
+                if (pass || k < cnt.nA_int) {             // the ring belongs to other tiles
+                    dE += d;
+                    nacc += accepted ? 1u : 0u;
+                    if (ACC) acc[pass ? cnt.nA_int + k : k] += atan2f(v.y, v.x);
+                }
             }
+            if (pass == 0) __syncthreads();
         }
+        fence_proxy_async_smem();                     // every writer orders its stores for the bulk copies
         __syncthreads();
-        // colour B on the tile
-        for (int k = threadIdx.x; k < cnt.nB; k += NT) {
-            const int ent = list[nA + k];
-            const int r = ent >> 7, q = ent & 127;
-            const int s = 1 ^ (r & 1);
-            const float2 nu = sm[0][r - 1][q], nd = sm[0][r + 1][q];
-            const float2 nl = sm[0][r][q - 1 + s], nr = sm[0][r][q + s];
-            const float C = (nu.x + nd.x) + (nl.x + nr.x);
-            const float S = (nu.y + nd.y) + (nl.y + nr.y);
-            float2 v = sm[1][r][q];
-            const int y = y0 - 2 + r, x = x0 + 2 * q - 4 + s;
-            const uint32_t site = (uint32_t)y * (uint32_t)W + (uint32_t)x;
-            const uint4 rnd = philox10(make_uint4(site, sweep, chain, 0u), A.key0, A.key1);
-            const float hq = (u24f(rnd.x) - 0.5f) * half_qd;
-            bool accepted;
-            dE += hybrid_update<TRIG>(v, C, S, hq, u24f(rnd.y), neg_inv_T, A.or_on, accepted);
-            nacc += accepted ? 1u : 0u;
-            sm[1][r][q] = v;
-            if (ACC) acc[cnt.nA_int + k] += atan2f(v.y, v.x);
-        }
-        __syncthreads();
-        // interior rows of both colours to the other buffer (samples included)
-        constexpr int I2 = TW / 4;                    // float4 per interior row
-        for (int idx = threadIdx.x; idx < 2 * TH * I2; idx += NT) {
-            const int c = idx / (TH * I2);
-            const int rem = idx - c * (TH * I2);
-            const int ri = rem / I2, q2 = rem - ri * I2;
-            const int y = y0 + ri;
-            const int pc = (x0 >> 1) + 2 + 2 * q2;
-            if (y < H && pc < pitch) {
-                const float4 v = *reinterpret_cast<const float4*>(&sm[c][ri + 2][2 + 2 * q2]);
-                *reinterpret_cast<float4*>(dst + (c ? P.pl1 : P.pl0) + (long long)(y + 1) * pitch + pc) = v;
+        // interior rows of both colours to the other buffer (samples included): one bulk
+        // copy per row, issued by the lanes of warp 0 (rows beyond the grid are skipped)
+        if (threadIdx.x < 32) {
+            const int rows = min(TH, H - y0);
+            for (int i = threadIdx.x; i < 2 * rows; i += 32) {
+                const int c = i / rows, ri = i - c * rows;
+                const int pc = (x0 >> 1) + 2;
+                const int ncol = min(TW / 2, pitch - pc) & ~1;          // whole 16-byte pairs
+                if (ncol > 0)
+                    bulk_store(dst + (c ? P.pl1 : P.pl0) + (long long)(y0 + ri + 1) * pitch + pc,
+                               &sm[c][ri + 2][2], (uint32_t)ncol * 8u);
             }
+            bulk_commit();
         }
-        // tile partials; the grid's last tile runs the control step
-        dE = warp_sum(dE);
-        nacc = warp_sum(nacc);
-        if ((threadIdx.x & 31) == 0) {
-            s_dE[threadIdx.x >> 5] = dE;
-            s_na[threadIdx.x >> 5] = nacc;
-        }
-        __syncthreads();                              // also: stage st and its list are free
+        // Partials are flushed once per run of consecutive tiles of one grid: at the end of
+        // the run the block writes its sums into the slot of the run's last tile (the other
+        // slots of the grid stay zero) and takes one ticket per tile of the run; the block
+        // that completes the grid's count adds the slots in tile order and runs the grid's
+        // control step.
         if (threadIdx.x == 0) {
-            double tt = 0.0;
-            unsigned na = 0;
-            for (int i = 0; i < NT / 32; ++i) { tt += (double)s_dE[i]; na += s_na[i]; }
-            A.part_dH[t] = tt;
-            A.part_na[t] = na;
-            __threadfence();
-            const unsigned prev = atomicAdd(A.ticket + P.e, 1u);
-            s_last = prev == (unsigned)(P.ntiles - 1);
+            // the next tile this block updates: already staged (STAGES > 1) or at the cursor
+            int ne;
+            if (STAGES > 1) {
+                const int nt = sp[(it + 1) % STAGES].t;
+                ne = nt >= A.ntiles ? -1 : sp[(it + 1) % STAGES].e;
+            } else {
+                ne = next >= A.ntiles ? -1 : dnext.entry;
+            }
+            s_last = ne != P.e ? 1 : 0;
+            s_runlen += 1;
         }
         __syncthreads();
         if (s_last) {
-            __threadfence();
-            double tt = 0.0;
-            unsigned long long na = 0;
-            for (int i = threadIdx.x; i < P.ntiles; i += NT) {
-                tt += *((volatile double*)A.part_dH + P.tile0 + i);
-                na += *((volatile unsigned*)A.part_na + P.tile0 + i);
+            dE = warp_sum(dE);
+            nacc = warp_sum(nacc);
+            if ((threadIdx.x & 31) == 0) {
+                s_dE[threadIdx.x >> 5] = dE;
+                s_na[threadIdx.x >> 5] = nacc;
             }
-            s_sum[threadIdx.x] = tt;
-            s_cnt[threadIdx.x] = na;
+            dE = 0.0f;
+            nacc = 0;
             __syncthreads();
-            for (int o = NT / 2; o > 0; o >>= 1) {
-                if ((int)threadIdx.x < o) {
-                    s_sum[threadIdx.x] += s_sum[threadIdx.x + o];
-                    s_cnt[threadIdx.x] += s_cnt[threadIdx.x + o];
+            if (threadIdx.x == 0) {
+                double tt = 0.0;
+                unsigned na = 0;
+                for (int i = 0; i < NT / 32; ++i) { tt += (double)s_dE[i]; na += s_na[i]; }
+                A.part_dH[t] = tt;
+                A.part_na[t] = na;
+                __threadfence();
+                const unsigned prev = atomicAdd(A.ticket + P.e, (unsigned)s_runlen);
+                s_grid_done = (prev + (unsigned)s_runlen == (unsigned)P.ntiles) ? 1 : 0;
+                s_runlen = 0;
+            }
+            __syncthreads();
+            if (s_grid_done) {
+                __threadfence();
+                double tt = 0.0;
+                unsigned long long na = 0;
+                for (int i = threadIdx.x; i < P.ntiles; i += NT) {
+                    tt += *((volatile double*)A.part_dH + P.tile0 + i);
+                    na += *((volatile unsigned*)A.part_na + P.tile0 + i);
+                }
+                s_sum[threadIdx.x] = tt;
+                s_cnt[threadIdx.x] = na;
+                __syncthreads();
+                for (int o = NT / 2; o > 0; o >>= 1) {
+                    if ((int)threadIdx.x < o) {
+                        s_sum[threadIdx.x] += s_sum[threadIdx.x + o];
+                        s_cnt[threadIdx.x] += s_cnt[threadIdx.x + o];
+                    }
+                    __syncthreads();
+                }
+                if (threadIdx.x == 0) {
+                    Ctl c = A.ctl[P.e];
+                    control_step(c, A.ents[P.e], s_sum[0], s_cnt[0], A.mode, A.A_targ, A.k_a, A.n_f,
+                                 A.n_fit, A.i_max, A.ehist + (long long)P.e * A.ehist_stride, 1);
+                    A.ctl[P.e] = c;
+                    A.ticket[P.e] = 0u;
+                    if (A.active && !c.stop) atomicAdd(A.active, 1);
                 }
                 __syncthreads();
             }
-            if (threadIdx.x == 0) {
-                Ctl c = A.ctl[P.e];
-                control_step(c, A.ents[P.e], s_sum[0], s_cnt[0], A.mode, A.A_targ, A.k_a, A.n_f,
-                             A.n_fit, A.i_max, A.ehist + (long long)P.e * A.ehist_stride, 1);
-                A.ctl[P.e] = c;
-                A.ticket[P.e] = 0u;
-                if (A.active && !c.stop) atomicAdd(A.active, 1);
-            }
-            __syncthreads();
         }
     }
 }
@@ -473,7 +535,7 @@ int tile_sweep_blocks() {
 int tile_list_len() { return Geo<kTileH, kTileW>::LIST; }
 int tile_acc_len() { return Geo<kTileH, kTileW>::ACC; }
 
-cudaError_t launch_tile_lists(const TileDesc* tiles, int ntiles, const EntryDesc* ents,
+cudaError_t launch_tile_lists(TileDesc* tiles, int ntiles, const EntryDesc* ents,
                               const uint8_t* mask, int all_free, uint16_t* lists, TileCnt* cnts,
                               cudaStream_t st) {
     if (ntiles == 0) return cudaSuccess;
