@@ -80,6 +80,7 @@ typedef struct {
     int M_T;           /* sweeps averaged per table temperature (default 100) */
     int exec_mode;     /* MPR_EXEC_* (default AUTO) */
     uint32_t chain;    /* realization id of this context's chain (default 0) */
+    int tile_cfg;      /* compiled tile shape of the TILE kernels, 0 .. 2 (default 0; see mpr_autotune) */
 } mpr_params;
 
 typedef struct {
@@ -154,6 +155,44 @@ mpr_status mpr_predict(mpr_ctx* ctx, int M, float* zhat);
  * Returns MPR_OK or MPR_ENOTEQUIL on success.
  */
 mpr_status mpr_fill(mpr_ctx* ctx, float* zhat, mpr_equil_stats* stats);
+
+/*
+ * Batched form: n >= 1 grids of their own sizes in one context.  Every grid gets its own
+ * map (Eq. 1), e_s (Eq. 4), temperature, window factor and slope test (Algorithm 2), and
+ * its own Philox chain id (params.chain + g); the sweeps of all grids run in the same
+ * kernel launches.  z[g], mask[g]: float/uint8 [H[g]][W[g]] (host or device).
+ * mpr_estimate_T, mpr_set_T, mpr_sweep and mpr_equilibrate act on every grid (their
+ * returned statistics describe grid 0); in a batch of several grids the e(T, L) table of a
+ * grid is built on a lattice whose sides are the grid's, capped at T_cap and rounded down
+ * to a power of two, so that grids of similar size share one table.
+ */
+mpr_status mpr_init_batch(mpr_ctx** ctx, int n, const float* const* z, const uint8_t* const* mask,
+                          const int* W, const int* H, const mpr_params* params, void* cuda_stream);
+
+/* Number of grids of the context. */
+int mpr_batch_size(const mpr_ctx* ctx);
+
+/* Algorithm 2 steps 6-7 for every grid: M sweeps, zhat[g] = float[H[g]][W[g]]. */
+mpr_status mpr_predict_batch(mpr_ctx* ctx, int M, float* const* zhat);
+
+/* mpr_fill for every grid (estimate_T unless set, equilibrate, predict_batch(params.M)).
+   Returns MPR_ENOTEQUIL if any grid stopped on i_max. */
+mpr_status mpr_fill_batch(mpr_ctx* ctx, float* const* zhat);
+
+/* Per-grid results: temperature, e_s, relaxation sweeps, converged flag, map extremes
+   (any pointer may be NULL). */
+mpr_status mpr_batch_info(mpr_ctx* ctx, int g, double* T, double* e_s, int* sweeps, int* converged,
+                          double* zmin, double* zmax);
+
+/*
+ * Autotuner of the TILE kernels: times a few sweeps of every compiled tile shape on the
+ * context's own grids (starting from a snapshot of the state, which is restored, so the
+ * chains are not advanced), keeps the fastest, and sets the number of sweeps per captured
+ * CUDA graph so that the host's once-per-graph check costs about a quarter of the sweeping
+ * time.  Needs a temperature.  Outputs (may be NULL): chosen tile configuration, sweeps
+ * per graph, time of one sweep in ms.
+ */
+mpr_status mpr_autotune(mpr_ctx* ctx, int* tile_cfg, int* graph_sweeps, double* ms_per_sweep);
 
 /* Releases the context and everything it owns.  NULL is allowed. */
 void mpr_free(mpr_ctx* ctx);

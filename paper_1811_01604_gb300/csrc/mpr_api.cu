@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -36,7 +37,8 @@ void mpr::count_launches(unsigned long long n, cudaStream_t st) {
 
 namespace {
 
-constexpr int kGraphSweeps = 8;           // sweeps per captured relaxation graph
+constexpr int kMaxGraphSweeps = 64;       // longest captured chunk of sweeps
+constexpr int kDefaultGraphSweeps = 8;    // sweeps per captured chunk unless autotuned
 constexpr int kScratch = 2048;            // doubles of reduction scratch
 
 struct GridIn {
@@ -63,7 +65,8 @@ struct Batch {
     Ctl* d_ctl = nullptr;
     double* d_ehist = nullptr;
     int ehist_stride = 0;
-    int* d_active = nullptr;               // kGraphSweeps counters
+    int* d_active = nullptr;               // one counter per sweep of a captured chunk
+    int gsweeps = kDefaultGraphSweeps;     // sweeps per captured chunk (host checks once per chunk)
     double* d_scratch = nullptr;
     double* d_H = nullptr;                 // one exact energy per entry
     // tile path (fused sweeps over shared-memory tiles, two lattice buffers)
@@ -79,24 +82,33 @@ struct Batch {
     unsigned* d_ticket = nullptr;
     CUtensorMap* d_maps = nullptr;
     int* d_err = nullptr;
+    int tcfg = 0;                          // compiled tile configuration in use
+    const uint8_t* mask_base = nullptr;    // masks of the grids (concatenated), or null
+    int all_free = 0;
     std::map<std::tuple<int, int, int, int, float>, cudaGraphExec_t> graphs;
 };
 
 }  // namespace
 
+struct GridInfo {                          // host view of one grid of a context
+    int W = 0, H = 0;
+    long long site0 = 0;                   // offset in the concatenated [H][W] buffers
+    double zmin = 0, zmax = 0, scale = 0;  // Eq. 1
+    long long n_samples = 0;
+    double e_s = 0;                        // Eq. 4
+    long long n_sp = 0;
+    double T = 0;
+};
+
 struct mpr_ctx {
     cudaStream_t st = nullptr;
     cudaStream_t cap = nullptr;            // private stream for graph capture
     mpr_params prm{};
-    int W = 0, H = 0;
-    float* d_z = nullptr;
+    std::vector<GridInfo> g;               // one per grid
+    long long n_sites = 0;                 // total sites of all grids
+    float* d_z = nullptr;                  // concatenated inputs
     uint8_t* d_mask = nullptr;
-    float* d_out = nullptr;                // [H][W] staging for outputs
-    double zmin = 0, zmax = 0, scale = 0;
-    long long n_samples = 0;
-    double e_s = 0;
-    long long n_sp = 0;
-    double T = 0;
+    float* d_out = nullptr;                // concatenated staging for outputs
     bool T_set = false;
     Batch b;
     int* h_active = nullptr;               // pinned
@@ -158,7 +170,59 @@ void batch_free(Batch& b) {
     b = Batch();
 }
 
+// (Re)builds the tile tables of a batch for compiled configuration cfg: tile
+// descriptors, gap lists, per-tile accumulators and partials, tickets, tensor maps.
+mpr_status build_tiles(mpr_ctx* ctx, Batch& b, int cfg) {
+    cudaStream_t st = ctx->st;
+    if (cfg < 0 || cfg >= tile_config_count()) return fail(ctx, MPR_EINVAL, "tile configuration");
+    const TileGeom g = tile_geom(cfg);
+    cudaFree(b.d_tiles);
+    cudaFree(b.d_cnts);
+    cudaFree(b.d_lists);
+    cudaFree(b.d_tacc);
+    cudaFree(b.d_tpart_dH);
+    cudaFree(b.d_tpart_na);
+    cudaFree(b.d_ticket);
+    b.d_tiles = nullptr; b.d_cnts = nullptr; b.d_lists = nullptr; b.d_tacc = nullptr;
+    b.d_tpart_dH = nullptr; b.d_tpart_na = nullptr; b.d_ticket = nullptr;
+    for (auto& kv : b.graphs) cudaGraphExecDestroy(kv.second);
+    b.graphs.clear();
+    std::vector<TileDesc> tiles;          // per grid ceil(H/th) x ceil(W/tw), row-major
+    for (int e = 0; e < b.n_ent; ++e) {
+        EntryDesc& E = b.ents[e];
+        E.tile0 = (int)tiles.size();
+        for (int y0 = 0; y0 < E.H; y0 += g.th)
+            for (int x0 = 0; x0 < E.W; x0 += g.tw) tiles.push_back(TileDesc{e, y0, x0, 0, 0, 0, {0, 0}});
+        E.ntiles = (int)tiles.size() - E.tile0;
+    }
+    CU(cudaMemcpyAsync(b.d_ents, b.ents.data(), b.n_ent * sizeof(EntryDesc), cudaMemcpyHostToDevice, st));
+    b.ntiles = (int)tiles.size();
+    CU(dalloc(&b.d_tiles, tiles.size()));
+    CU(cudaMemcpyAsync(b.d_tiles, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, st));
+    CU(dalloc(&b.d_cnts, tiles.size()));
+    CU(dalloc(&b.d_lists, tiles.size() * (size_t)g.list));
+    CU(dalloc(&b.d_tacc, tiles.size() * (size_t)g.acc));
+    CU(dalloc(&b.d_tpart_dH, tiles.size()));
+    CU(dalloc(&b.d_tpart_na, tiles.size()));
+    CU(cudaMemsetAsync(b.d_tpart_dH, 0, sizeof(double) * tiles.size(), st));   // slots that never
+    CU(cudaMemsetAsync(b.d_tpart_na, 0, sizeof(unsigned) * tiles.size(), st)); // end a run stay 0
+    CU(dalloc(&b.d_ticket, (size_t)b.n_ent));
+    CU(cudaMemsetAsync(b.d_ticket, 0, sizeof(unsigned) * b.n_ent, st));
+    CU(launch_tile_lists(cfg, b.d_tiles, b.ntiles, b.d_ents, b.mask_base, b.all_free, b.d_lists,
+                         b.d_cnts, st));
+    CU(make_tile_maps(cfg, b.ents.data(), b.n_ent, b.d_lat, b.d_lat2, b.d_maps, st));
+    tile_sweep_blocks(cfg);               // kernel attributes are set outside any capture
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(st));
+    b.tcfg = cfg;
+    return MPR_OK;
+}
+
 // Lays out, packs and indexes a batch of grids.  all_free: every site is a gap.
+mpr_status reset_relax(mpr_ctx* ctx, Batch& b);
+mpr_status run_sweeps(mpr_ctx* ctx, Batch& b, int n, int mode, double a_fixed, bool acc);
+mpr_status read_ctl(mpr_ctx* ctx, Batch& b, std::vector<Ctl>& out);
+
 mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids, int all_free,
                        const uint8_t* mask_base) {
     cudaStream_t st = ctx->st;
@@ -174,8 +238,8 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
         E.W = grids[e].W;
         E.H = grids[e].H;
         // >= W/2 + 3 columns, and at least one TMA box wide and high
-        E.pitch = (std::max(E.W / 2 + 4, kTileRW) + 31) & ~31;
-        E.prows = std::max(E.H + 2, kTileRH);
+        E.pitch = (std::max(E.W / 2 + 4, tile_max_cols()) + 31) & ~31;
+        E.prows = std::max(E.H + 2, tile_max_rows());
         const size_t plane = (size_t)E.prows * E.pitch;
         E.plane[0] = (long long)lat;
         E.plane[1] = (long long)(lat + plane);
@@ -246,40 +310,18 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
             CU(cudaMemcpyAsync(b.d_work[c], w.data(), w.size() * sizeof(BlockWork),
                                cudaMemcpyHostToDevice, st));
     }
-    // tiles (tile path): per grid ceil(H/kTileH) x ceil(W/kTileW), row-major
-    std::vector<TileDesc> tiles;
-    for (int e = 0; e < b.n_ent; ++e) {
-        EntryDesc& E = b.ents[e];
-        E.tile0 = (int)tiles.size();
-        for (int y0 = 0; y0 < E.H; y0 += kTileH)
-            for (int x0 = 0; x0 < E.W; x0 += kTileW) tiles.push_back(TileDesc{e, y0, x0, 0, 0, 0, {0, 0}});
-        E.ntiles = (int)tiles.size() - E.tile0;
-    }
     CU(dalloc(&b.d_ents, b.n_ent));
     CU(cudaMemcpyAsync(b.d_ents, b.ents.data(), b.n_ent * sizeof(EntryDesc), cudaMemcpyHostToDevice, st));
     if (b.tiled) {
-        b.ntiles = (int)tiles.size();
         CU(dalloc(&b.d_lat2, lat));
         CU(cudaMemcpyAsync(b.d_lat2, b.d_lat, lat * sizeof(float2), cudaMemcpyDeviceToDevice, st));
-        CU(dalloc(&b.d_tiles, tiles.size()));
-        CU(cudaMemcpyAsync(b.d_tiles, tiles.data(), tiles.size() * sizeof(TileDesc),
-                           cudaMemcpyHostToDevice, st));
-        CU(dalloc(&b.d_cnts, tiles.size()));
-        CU(dalloc(&b.d_lists, tiles.size() * (size_t)tile_list_len()));
-        CU(dalloc(&b.d_tacc, tiles.size() * (size_t)tile_acc_len()));
-        CU(dalloc(&b.d_tpart_dH, tiles.size()));
-        CU(dalloc(&b.d_tpart_na, tiles.size()));
-        CU(cudaMemsetAsync(b.d_tpart_dH, 0, sizeof(double) * tiles.size(), st));   // slots that
-        CU(cudaMemsetAsync(b.d_tpart_na, 0, sizeof(unsigned) * tiles.size(), st)); // never end a run stay 0
-        CU(dalloc(&b.d_ticket, (size_t)b.n_ent));
-        CU(cudaMemsetAsync(b.d_ticket, 0, sizeof(unsigned) * b.n_ent, st));
-        CU(launch_tile_lists(b.d_tiles, b.ntiles, b.d_ents, mask_base, all_free, b.d_lists, b.d_cnts, st));
         CU(dalloc(&b.d_maps, (size_t)2 * b.n_ent));
-        CU(make_tile_maps(b.ents.data(), b.n_ent, b.d_lat, b.d_lat2, b.d_maps, st));
         CU(dalloc(&b.d_err, 1));
         CU(cudaMemsetAsync(b.d_err, 0, sizeof(int), st));
-        tile_sweep_blocks();                  // kernel attributes are set outside any capture
-        CU(cudaGetLastError());
+        b.mask_base = mask_base;
+        b.all_free = all_free;
+        const mpr_status ts = build_tiles(ctx, b, ctx->prm.tile_cfg);
+        if (ts != MPR_OK) return ts;
     }
     std::vector<Ctl> ctl(b.n_ent);
     for (int e = 0; e < b.n_ent; ++e) {
@@ -295,7 +337,7 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
     b.ehist_stride = ctx->prm.i_max + 2;
     CU(dalloc(&b.d_ehist, (size_t)b.n_ent * b.ehist_stride));
     CU(cudaMemsetAsync(b.d_ehist, 0, sizeof(double) * (size_t)b.n_ent * b.ehist_stride, st));
-    CU(dalloc(&b.d_active, kGraphSweeps));
+    CU(dalloc(&b.d_active, kMaxGraphSweeps));
     CU(dalloc(&b.d_scratch, kScratch + 8));
     CU(dalloc(&b.d_H, (size_t)b.n_ent));
     CU(cudaStreamSynchronize(st));
@@ -347,6 +389,7 @@ TileArgs tile_args(const mpr_ctx* ctx, const Batch& b, int mode, double a_fixed,
     T.ehist = b.d_ehist;
     T.ehist_stride = b.ehist_stride;
     T.ntiles = b.ntiles;
+    T.cfg = b.tcfg;
     T.use_ctl_a = relax ? 1 : 0;
     T.half_qd_fixed = (float)(0.5 * kTwoPi * p.q / a_fixed);
     T.skip_stopped = relax ? 1 : 0;
@@ -368,11 +411,11 @@ mpr_status enqueue_sweeps(mpr_ctx* ctx, Batch& b, cudaStream_t s, int n, int mod
     const bool relax = mode == CTL_RELAX;
     const SweepArgs A = sweep_args(ctx, b, relax, a_fixed, relax, acc);
     const mpr_params& p = ctx->prm;
-    if (count_active) CU(cudaMemsetAsync(b.d_active, 0, sizeof(int) * kGraphSweeps, s));
+    if (count_active) CU(cudaMemsetAsync(b.d_active, 0, sizeof(int) * b.gsweeps, s));
     if (b.tiled) {
         TileArgs T = tile_args(ctx, b, mode, a_fixed, acc);
         for (int i = 0; i < n; ++i) {
-            T.active = count_active ? b.d_active + (i % kGraphSweeps) : nullptr;
+            T.active = count_active ? b.d_active + (i % b.gsweeps) : nullptr;
             CU(launch_tile_sweep(T, p.trig_mode, s));
         }
         return MPR_OK;
@@ -382,14 +425,14 @@ mpr_status enqueue_sweeps(mpr_ctx* ctx, Batch& b, cudaStream_t s, int n, int mod
         CU(launch_half_sweep(A, 1, p.trig_mode, s));
         CU(launch_control(b.d_ctl, b.d_part, b.d_ents, b.n_ent, mode, p.A_targ, p.k_a, p.n_f,
                           p.n_fit, p.i_max, b.d_ehist, b.ehist_stride,
-                          count_active ? b.d_active + (i % kGraphSweeps) : nullptr, s));
+                          count_active ? b.d_active + (i % b.gsweeps) : nullptr, s));
     }
     return MPR_OK;
 }
 
-// Runs n sweeps through a cached CUDA graph of kGraphSweeps sweeps (plus a tail).
+// Runs n sweeps through a cached CUDA graph of b.gsweeps sweeps (plus a tail).
 mpr_status run_sweeps(mpr_ctx* ctx, Batch& b, int n, int mode, double a_fixed, bool acc) {
-    const int S = kGraphSweeps;
+    const int S = b.gsweeps;
     const bool relax = mode == CTL_RELAX;
     if (n <= 0 && !relax) return MPR_OK;
     auto key = std::make_tuple(mode, acc ? 1 : 0, S, ctx->prm.trig_mode, (float)a_fixed);
@@ -488,18 +531,20 @@ std::string table_key(const mpr_params& p, int W, int H) {
     return buf;
 }
 
-// Eq. 5 table: KT all-free lattices, relaxed by Algorithm 2 step 5 at their own T_k,
-// then M_T sweeps at a_eq averaging the specific energy.
-mpr_status build_table(mpr_ctx* ctx, int Wt, int Ht, std::vector<double>& Tk,
-                       std::vector<double>& ek) {
+// Eq. 5 tables: for each requested lattice shape, KT all-free lattices (one per T_k),
+// all shapes in one batch; relaxed by Algorithm 2 step 5 at their own T_k, then M_T
+// sweeps at a_eq averaging the specific energy.
+mpr_status build_tables(mpr_ctx* ctx, const std::vector<std::pair<int, int>>& shapes,
+                        std::vector<std::vector<double>>& Tk, std::vector<std::vector<double>>& ek) {
     const mpr_params& p = ctx->prm;
-    Tk.resize(p.KT);
-    ek.resize(p.KT);
-    std::vector<GridIn> g(p.KT);
-    for (int k = 0; k < p.KT; ++k) {
-        Tk[k] = p.T_min * std::pow(p.T_max / p.T_min, (double)k / (double)(p.KT - 1));
-        g[k] = GridIn{Wt, Ht, nullptr, nullptr, 0x80000000u + (uint32_t)k, Tk[k], 0.0, 0.0};
-    }
+    std::vector<double> T(p.KT);
+    for (int k = 0; k < p.KT; ++k)
+        T[k] = p.T_min * std::pow(p.T_max / p.T_min, (double)k / (double)(p.KT - 1));
+    std::vector<GridIn> g;
+    for (size_t sh = 0; sh < shapes.size(); ++sh)
+        for (int k = 0; k < p.KT; ++k)
+            g.push_back(GridIn{shapes[sh].first, shapes[sh].second, nullptr, nullptr,
+                               0x80000000u + (uint32_t)(sh * p.KT + k), T[k], 0.0, 0.0});
     Batch tb;
     mpr_status s = batch_build(ctx, tb, g, 1, nullptr);
     if (s == MPR_OK) s = reset_relax(ctx, tb);
@@ -507,10 +552,33 @@ mpr_status build_table(mpr_ctx* ctx, int Wt, int Ht, std::vector<double>& Tk,
     if (s == MPR_OK) s = run_sweeps(ctx, tb, p.M_T, CTL_SAMPLE, p.a_eq, false);
     std::vector<Ctl> c;
     if (s == MPR_OK) s = read_ctl(ctx, tb, c);
-    if (s == MPR_OK)
-        for (int k = 0; k < p.KT; ++k) ek[k] = c[k].nsamp ? c[k].esum / c[k].nsamp : 0.0;
+    if (s == MPR_OK) {
+        Tk.assign(shapes.size(), T);
+        ek.assign(shapes.size(), std::vector<double>(p.KT));
+        for (size_t sh = 0; sh < shapes.size(); ++sh)
+            for (int k = 0; k < p.KT; ++k) {
+                const Ctl& x = c[sh * p.KT + k];
+                ek[sh][k] = x.nsamp ? x.esum / x.nsamp : 0.0;
+            }
+    }
     batch_free(tb);
     return s;
+}
+
+// Shape of the unconditional lattices used for a grid's table: the grid's sides capped
+// at T_cap; in batches of several grids also rounded down to a power of two (at least
+// 32) so that grids of similar size share one table.
+std::pair<int, int> table_shape(const mpr_params& p, int W, int H, bool batch) {
+    auto side = [&](int v) {
+        int t = p.T_cap > 0 ? std::min(v, p.T_cap) : v;
+        if (batch && t >= 32) {
+            int q = 32;
+            while (q * 2 <= t) q *= 2;
+            t = q;
+        }
+        return t;
+    };
+    return {side(W), side(H)};
 }
 
 // T-hat = argmin_T |e_s - e(T, L)|: first bracketing interval from the lowest T,
@@ -552,6 +620,7 @@ void mpr_default_params(mpr_params* p) {
     p->M_T = 100;
     p->exec_mode = MPR_EXEC_AUTO;
     p->chain = 0;
+    p->tile_cfg = 0;
 }
 
 const char* mpr_status_string(mpr_status s) {
@@ -591,45 +660,64 @@ static mpr_status check_params(const mpr_params* p, std::string& why) {
     if (p->or_mode != MPR_OR_CONSERVING && p->or_mode != MPR_OR_NONE) { why = "or_mode"; return MPR_EINVAL; }
     if (p->trig_mode != MPR_TRIG_ACCURATE && p->trig_mode != MPR_TRIG_FAST) { why = "trig_mode"; return MPR_EINVAL; }
     if (!(p->a_eq >= 1.0)) { why = "a_eq must be >= 1"; return MPR_EINVAL; }
+    if (p->tile_cfg < 0 || p->tile_cfg >= tile_config_count()) { why = "tile_cfg"; return MPR_EINVAL; }
     if (p->exec_mode != MPR_EXEC_AUTO && p->exec_mode != MPR_EXEC_LIST && p->exec_mode != MPR_EXEC_TILE) { why = "exec_mode"; return MPR_EINVAL; }
     if (p->KT < 2 || !(p->T_min > 0.0) || !(p->T_max > p->T_min) || p->M_T < 1 || p->T_cap < 0) { why = "table parameters"; return MPR_EINVAL; }
     return MPR_OK;
 }
 
-mpr_status mpr_init(mpr_ctx** out, const float* z, const uint8_t* mask, int W, int H,
-                    const mpr_params* params, void* cuda_stream) {
+// Copies the grids in, maps them (Eq. 1), builds the lattice batch and computes Eq. 4.
+static mpr_status init_grids(mpr_ctx** out, int n, const float* const* z, const uint8_t* const* mask,
+                             const int* W, const int* H, const mpr_params* params, void* stream) {
     if (!out) return MPR_EINVAL;
     *out = nullptr;
-    if (!z || !mask || W < 1 || H < 1 || H > 65535 || (W + 1) / 2 > 65535) return MPR_EINVAL;
+    if (n < 1 || !z || !mask || !W || !H) return MPR_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!z[i] || !mask[i] || W[i] < 1 || H[i] < 1 || H[i] > 65535 || (W[i] + 1) / 2 > 65535)
+            return MPR_EINVAL;
     mpr_ctx* ctx = new mpr_ctx();
     if (params) ctx->prm = *params; else mpr_default_params(&ctx->prm);
     std::string why;
     if (check_params(&ctx->prm, why) != MPR_OK) { delete ctx; return MPR_EINVAL; }
-    ctx->st = (cudaStream_t)cuda_stream;
-    ctx->W = W;
-    ctx->H = H;
+    ctx->st = (cudaStream_t)stream;
+    ctx->g.resize(n);
+    long long site0 = 0;
+    for (int i = 0; i < n; ++i) {
+        ctx->g[i].W = W[i];
+        ctx->g[i].H = H[i];
+        ctx->g[i].site0 = site0;
+        site0 += (long long)W[i] * H[i];
+    }
+    ctx->n_sites = site0;
     auto bail = [&](mpr_status s) { mpr_free(ctx); return s; };
-    const size_t n = (size_t)W * H;
 #define CUI(call) do { if ((call) != cudaSuccess) { cudaGetLastError(); return bail(MPR_ECUDA); } } while (0)
     CUI(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
     CUI(cudaMallocHost((void**)&ctx->h_active, sizeof(int) * 4));
-    if (dalloc(&ctx->d_z, n) != cudaSuccess || dalloc(&ctx->d_mask, n) != cudaSuccess ||
-        dalloc(&ctx->d_out, n) != cudaSuccess) { cudaGetLastError(); return bail(MPR_ENOMEM); }
-    CUI(cudaMemcpyAsync(ctx->d_z, z, n * sizeof(float), cudaMemcpyDefault, ctx->st));
-    CUI(cudaMemcpyAsync(ctx->d_mask, mask, n, cudaMemcpyDefault, ctx->st));
-    // Eq. 1 extremes
+    const size_t N = (size_t)site0;
+    if (dalloc(&ctx->d_z, N) != cudaSuccess || dalloc(&ctx->d_mask, N) != cudaSuccess ||
+        dalloc(&ctx->d_out, N) != cudaSuccess) { cudaGetLastError(); return bail(MPR_ENOMEM); }
+    for (int i = 0; i < n; ++i) {
+        const size_t ni = (size_t)W[i] * H[i];
+        CUI(cudaMemcpyAsync(ctx->d_z + ctx->g[i].site0, z[i], ni * sizeof(float), cudaMemcpyDefault, ctx->st));
+        CUI(cudaMemcpyAsync(ctx->d_mask + ctx->g[i].site0, mask[i], ni, cudaMemcpyDefault, ctx->st));
+    }
+    // Eq. 1 extremes, per grid
     unsigned* d_keys = nullptr;
     unsigned long long* d_ns = nullptr;
-    CUI(dalloc(&d_keys, 2));
-    CUI(dalloc(&d_ns, 1));
-    CUI(cudaMemsetAsync(d_keys, 0xFF, sizeof(unsigned), ctx->st));
-    CUI(cudaMemsetAsync(d_keys + 1, 0, sizeof(unsigned), ctx->st));
-    CUI(cudaMemsetAsync(d_ns, 0, sizeof(unsigned long long), ctx->st));
-    CUI(launch_minmax(ctx->d_z, ctx->d_mask, (long long)n, d_keys, d_ns, ctx->st));
-    unsigned keys[2];
-    unsigned long long ns = 0;
-    CUI(cudaMemcpyAsync(keys, d_keys, sizeof keys, cudaMemcpyDeviceToHost, ctx->st));
-    CUI(cudaMemcpyAsync(&ns, d_ns, sizeof ns, cudaMemcpyDeviceToHost, ctx->st));
+    CUI(dalloc(&d_keys, (size_t)2 * n));
+    CUI(dalloc(&d_ns, (size_t)n));
+    for (int i = 0; i < n; ++i) {
+        CUI(cudaMemsetAsync(d_keys + 2 * i, 0xFF, sizeof(unsigned), ctx->st));
+        CUI(cudaMemsetAsync(d_keys + 2 * i + 1, 0, sizeof(unsigned), ctx->st));
+    }
+    CUI(cudaMemsetAsync(d_ns, 0, sizeof(unsigned long long) * n, ctx->st));
+    for (int i = 0; i < n; ++i)
+        CUI(launch_minmax(ctx->d_z + ctx->g[i].site0, ctx->d_mask + ctx->g[i].site0,
+                          (long long)W[i] * H[i], d_keys + 2 * i, d_ns + i, ctx->st));
+    std::vector<unsigned> keys((size_t)2 * n);
+    std::vector<unsigned long long> ns((size_t)n);
+    CUI(cudaMemcpyAsync(keys.data(), d_keys, sizeof(unsigned) * 2 * n, cudaMemcpyDeviceToHost, ctx->st));
+    CUI(cudaMemcpyAsync(ns.data(), d_ns, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, ctx->st));
     CUI(cudaStreamSynchronize(ctx->st));
     cudaFree(d_keys);
     cudaFree(d_ns);
@@ -639,87 +727,120 @@ mpr_status mpr_init(mpr_ctx** out, const float* z, const uint8_t* mask, int W, i
         std::memcpy(&f, &b, sizeof f);
         return (double)f;
     };
-    ctx->n_samples = (long long)ns;
-    if (ns < 2) return bail(MPR_ENODATA);
-    ctx->zmin = unkey(keys[0]);
-    ctx->zmax = unkey(keys[1]);
-    if (!(ctx->zmax > ctx->zmin) || !std::isfinite(ctx->zmin) || !std::isfinite(ctx->zmax))
-        return bail(MPR_ENODATA);
-    ctx->scale = kTwoPi / (ctx->zmax - ctx->zmin);
-    std::vector<GridIn> g{GridIn{W, H, ctx->d_z, ctx->d_mask, ctx->prm.chain, 0.0, ctx->zmin, ctx->scale}};
+    std::vector<GridIn> gi(n);
+    for (int i = 0; i < n; ++i) {
+        GridInfo& G = ctx->g[i];
+        G.n_samples = (long long)ns[i];
+        if (ns[i] < 2) return bail(MPR_ENODATA);
+        G.zmin = unkey(keys[2 * i]);
+        G.zmax = unkey(keys[2 * i + 1]);
+        if (!(G.zmax > G.zmin) || !std::isfinite(G.zmin) || !std::isfinite(G.zmax)) return bail(MPR_ENODATA);
+        G.scale = kTwoPi / (G.zmax - G.zmin);
+        gi[i] = GridIn{W[i], H[i], ctx->d_z + G.site0, ctx->d_mask + G.site0,
+                       ctx->prm.chain + (uint32_t)i, 0.0, G.zmin, G.scale};
+    }
     {
-        const mpr_status bs = batch_build(ctx, ctx->b, g, 0, ctx->d_mask);
+        const mpr_status bs = batch_build(ctx, ctx->b, gi, 0, ctx->d_mask);
         if (bs != MPR_OK) return bail(bs);
     }
-    // Eq. 4
+    // Eq. 4, per grid (per-block partials added in block order on the host)
     double* d_ps = nullptr;
     unsigned long long* d_pc = nullptr;
     CUI(dalloc(&d_ps, 1024));
     CUI(dalloc(&d_pc, 1024));
-    int np = 0;
-    CUI(launch_sample_energy(&ctx->b.ents[0], ctx->d_z, ctx->d_mask, ctx->scale, ctx->prm.q, d_ps,
-                             d_pc, &np, ctx->st));
-    std::vector<double> ps(np);
-    std::vector<unsigned long long> pc(np);
-    CUI(cudaMemcpyAsync(ps.data(), d_ps, sizeof(double) * np, cudaMemcpyDeviceToHost, ctx->st));
-    CUI(cudaMemcpyAsync(pc.data(), d_pc, sizeof(unsigned long long) * np, cudaMemcpyDeviceToHost, ctx->st));
-    CUI(cudaStreamSynchronize(ctx->st));
+    for (int i = 0; i < n; ++i) {
+        GridInfo& G = ctx->g[i];
+        int np = 0;
+        CUI(launch_sample_energy(&ctx->b.ents[i], ctx->d_z + G.site0, ctx->d_mask + G.site0, G.scale,
+                                 ctx->prm.q, d_ps, d_pc, &np, ctx->st));
+        std::vector<double> ps(np);
+        std::vector<unsigned long long> pc(np);
+        CUI(cudaMemcpyAsync(ps.data(), d_ps, sizeof(double) * np, cudaMemcpyDeviceToHost, ctx->st));
+        CUI(cudaMemcpyAsync(pc.data(), d_pc, sizeof(unsigned long long) * np, cudaMemcpyDeviceToHost, ctx->st));
+        CUI(cudaStreamSynchronize(ctx->st));
+        double sum = 0.0;
+        unsigned long long cnt = 0;
+        for (int k = 0; k < np; ++k) { sum += ps[k]; cnt += pc[k]; }
+        G.n_sp = (long long)cnt;
+        G.e_s = cnt ? -sum / (double)cnt : 0.0;
+    }
     cudaFree(d_ps);
     cudaFree(d_pc);
-    double sum = 0.0;
-    unsigned long long cnt = 0;
-    for (int i = 0; i < np; ++i) { sum += ps[i]; cnt += pc[i]; }
-    ctx->n_sp = (long long)cnt;
-    ctx->e_s = cnt ? -sum / (double)cnt : 0.0;
 #undef CUI
     *out = ctx;
+    return MPR_OK;
+}
+
+mpr_status mpr_init(mpr_ctx** out, const float* z, const uint8_t* mask, int W, int H,
+                    const mpr_params* params, void* cuda_stream) {
+    return init_grids(out, 1, &z, &mask, &W, &H, params, cuda_stream);
+}
+
+mpr_status mpr_init_batch(mpr_ctx** out, int n, const float* const* z, const uint8_t* const* mask,
+                          const int* W, const int* H, const mpr_params* params, void* cuda_stream) {
+    return init_grids(out, n, z, mask, W, H, params, cuda_stream);
+}
+
+int mpr_batch_size(const mpr_ctx* ctx) { return ctx ? (int)ctx->g.size() : 0; }
+
+static mpr_status set_T_all(mpr_ctx* ctx, const std::vector<double>& T) {
+    std::vector<Ctl> c;
+    mpr_status s = read_ctl(ctx, ctx->b, c);
+    if (s != MPR_OK) return s;
+    for (size_t i = 0; i < c.size(); ++i) {
+        c[i].T = T[i];
+        c[i].neg_inv_T = (float)(-1.0 / T[i]);
+        ctx->g[i].T = T[i];
+    }
+    CU(cudaMemcpyAsync(ctx->b.d_ctl, c.data(), sizeof(Ctl) * c.size(), cudaMemcpyHostToDevice, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    ctx->T_set = true;
     return MPR_OK;
 }
 
 mpr_status mpr_set_T(mpr_ctx* ctx, double T) {
     if (!ctx) return MPR_EINVAL;
     if (!(T > 0.0) || !std::isfinite(T)) return fail(ctx, MPR_EINVAL, "T must be positive");
-    std::vector<Ctl> c;
-    mpr_status s = read_ctl(ctx, ctx->b, c);
-    if (s != MPR_OK) return s;
-    for (auto& x : c) {
-        x.T = T;
-        x.neg_inv_T = (float)(-1.0 / T);
-    }
-    CU(cudaMemcpyAsync(ctx->b.d_ctl, c.data(), sizeof(Ctl) * c.size(), cudaMemcpyHostToDevice, ctx->st));
-    CU(cudaStreamSynchronize(ctx->st));
-    ctx->T = T;
-    ctx->T_set = true;
-    return MPR_OK;
+    return set_T_all(ctx, std::vector<double>(ctx->g.size(), T));
 }
 
 mpr_status mpr_estimate_T(mpr_ctx* ctx, double* T_hat, double* e_s) {
     if (!ctx) return MPR_EINVAL;
-    if (ctx->n_sp == 0) return fail(ctx, MPR_ENOPAIRS, "no nearest-neighbour sample pairs");
     const mpr_params& p = ctx->prm;
-    const int Wt = p.T_cap > 0 ? std::min(ctx->W, p.T_cap) : ctx->W;
-    const int Ht = p.T_cap > 0 ? std::min(ctx->H, p.T_cap) : ctx->H;
-    std::vector<double> Tk, ek;
-    const std::string key = table_key(p, Wt, Ht);
-    {
+    const bool batch = ctx->g.size() > 1;
+    for (const GridInfo& G : ctx->g)
+        if (G.n_sp == 0) return fail(ctx, MPR_ENOPAIRS, "no nearest-neighbour sample pairs");
+    // tables for every lattice shape not cached yet, built together
+    std::vector<std::pair<int, int>> need;
+    for (const GridInfo& G : ctx->g) {
+        const auto sh = table_shape(p, G.W, G.H, batch);
         std::lock_guard<std::mutex> lk(g_table_mu);
-        auto it = g_tables.find(key);
-        if (it != g_tables.end()) {
-            Tk = it->second.first;
-            ek = it->second.second;
-        }
+        if (!g_tables.count(table_key(p, sh.first, sh.second)) &&
+            std::find(need.begin(), need.end(), sh) == need.end())
+            need.push_back(sh);
     }
-    if (Tk.empty()) {
-        mpr_status s = build_table(ctx, Wt, Ht, Tk, ek);
+    if (!need.empty()) {
+        std::vector<std::vector<double>> Tk, ek;
+        mpr_status s = build_tables(ctx, need, Tk, ek);
         if (s != MPR_OK) return s;
         std::lock_guard<std::mutex> lk(g_table_mu);
-        g_tables[key] = std::make_pair(Tk, ek);
+        for (size_t i = 0; i < need.size(); ++i)
+            g_tables[table_key(p, need[i].first, need[i].second)] = std::make_pair(Tk[i], ek[i]);
     }
-    const double T = invert_T(Tk, ek, ctx->e_s);
-    mpr_status s = mpr_set_T(ctx, T);
+    std::vector<double> T(ctx->g.size());
+    for (size_t i = 0; i < ctx->g.size(); ++i) {
+        const auto sh = table_shape(p, ctx->g[i].W, ctx->g[i].H, batch);
+        std::pair<std::vector<double>, std::vector<double>> tab;
+        {
+            std::lock_guard<std::mutex> lk(g_table_mu);
+            tab = g_tables[table_key(p, sh.first, sh.second)];
+        }
+        T[i] = invert_T(tab.first, tab.second, ctx->g[i].e_s);
+    }
+    mpr_status s = set_T_all(ctx, T);
     if (s != MPR_OK) return s;
-    if (T_hat) *T_hat = T;
-    if (e_s) *e_s = ctx->e_s;
+    if (T_hat) *T_hat = T[0];
+    if (e_s) *e_s = ctx->g[0].e_s;
     return MPR_OK;
 }
 
@@ -756,48 +877,100 @@ mpr_status mpr_equilibrate(mpr_ctx* ctx, mpr_equil_stats* out) {
         out->e_last = c[0].e_last;
         out->converged = c[0].converged;
     }
-    return (c[0].converged || ctx->b.ents[0].P == 0) ? MPR_OK : MPR_ENOTEQUIL;
+    for (size_t i = 0; i < c.size(); ++i)
+        if (!c[i].converged && ctx->b.ents[i].P > 0) return MPR_ENOTEQUIL;
+    return MPR_OK;
 }
 
-mpr_status mpr_predict(mpr_ctx* ctx, int M, float* zhat) {
-    if (!ctx || !zhat) return MPR_EINVAL;
-    if (M < 1) return fail(ctx, MPR_EINVAL, "M >= 1 required");
-    if (!ctx->T_set) return fail(ctx, MPR_ESTATE, "temperature not set");
+// M equilibrium sweeps of every grid, then each grid's zhat into out[g] (host or device).
+static mpr_status predict_all(mpr_ctx* ctx, int M, float* const* out) {
     Batch& b = ctx->b;
-    const size_t n = (size_t)ctx->W * ctx->H;
     if (b.tiled)
-        CU(cudaMemsetAsync(b.d_tacc, 0, sizeof(float) * (size_t)b.ntiles * tile_acc_len(), ctx->st));
+        CU(cudaMemsetAsync(b.d_tacc, 0, sizeof(float) * (size_t)b.ntiles * tile_geom(b.tcfg).acc, ctx->st));
     else
         CU(cudaMemsetAsync(b.d_acc, 0, sizeof(float) * std::max<size_t>(b.n_gaps, 1), ctx->st));
     mpr_status s = run_sweeps(ctx, b, M, CTL_FIXED, ctx->prm.a_eq, true);
     if (s != MPR_OK) return s;
-    CU(cudaMemcpyAsync(ctx->d_out, ctx->d_z, n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->st));
-    if (b.tiled)
-        CU(launch_tile_predict_out(b.d_tiles, b.d_cnts, b.d_lists, b.d_tacc, b.d_ents, b.ents[0].tile0,
-                                   b.ents[0].ntiles, M, ctx->prm.q, ctx->zmin, ctx->zmax, ctx->d_out,
-                                   ctx->st));
-    else
-        CU(launch_predict_out(&b.ents[0], b.d_lat, b.d_gaps, b.d_acc, M, ctx->prm.q, ctx->zmin,
-                              ctx->zmax, ctx->d_out, ctx->st));
-    CU(cudaMemcpyAsync(zhat, ctx->d_out, n * sizeof(float), cudaMemcpyDefault, ctx->st));
+    CU(cudaMemcpyAsync(ctx->d_out, ctx->d_z, (size_t)ctx->n_sites * sizeof(float),
+                       cudaMemcpyDeviceToDevice, ctx->st));
+    for (size_t i = 0; i < ctx->g.size(); ++i) {
+        const GridInfo& G = ctx->g[i];
+        if (b.tiled)
+            CU(launch_tile_predict_out(b.tcfg, b.d_tiles, b.d_cnts, b.d_lists, b.d_tacc, b.d_ents,
+                                       b.ents[i].tile0, b.ents[i].ntiles, M, ctx->prm.q, G.zmin,
+                                       G.zmax, ctx->d_out, ctx->st));
+        else
+            CU(launch_predict_out(&b.ents[i], b.d_lat, b.d_gaps, b.d_acc, M, ctx->prm.q, G.zmin,
+                                  G.zmax, ctx->d_out + G.site0, ctx->st));
+    }
+    for (size_t i = 0; i < ctx->g.size(); ++i) {
+        const GridInfo& G = ctx->g[i];
+        CU(cudaMemcpyAsync(out[i], ctx->d_out + G.site0, (size_t)G.W * G.H * sizeof(float),
+                           cudaMemcpyDefault, ctx->st));
+    }
     CU(cudaStreamSynchronize(ctx->st));
     return MPR_OK;
 }
 
+mpr_status mpr_predict(mpr_ctx* ctx, int M, float* zhat) {
+    if (!ctx || !zhat) return MPR_EINVAL;
+    if (ctx->g.size() != 1) return fail(ctx, MPR_EINVAL, "mpr_predict serves one grid; use mpr_predict_batch");
+    if (M < 1) return fail(ctx, MPR_EINVAL, "M >= 1 required");
+    if (!ctx->T_set) return fail(ctx, MPR_ESTATE, "temperature not set");
+    return predict_all(ctx, M, &zhat);
+}
+
+mpr_status mpr_predict_batch(mpr_ctx* ctx, int M, float* const* zhat) {
+    if (!ctx || !zhat) return MPR_EINVAL;
+    for (size_t i = 0; i < ctx->g.size(); ++i)
+        if (!zhat[i]) return MPR_EINVAL;
+    if (M < 1) return fail(ctx, MPR_EINVAL, "M >= 1 required");
+    if (!ctx->T_set) return fail(ctx, MPR_ESTATE, "temperature not set");
+    return predict_all(ctx, M, zhat);
+}
+
 mpr_status mpr_fill(mpr_ctx* ctx, float* zhat, mpr_equil_stats* stats) {
     if (!ctx || !zhat) return MPR_EINVAL;
+    if (ctx->g.size() != 1) return fail(ctx, MPR_EINVAL, "mpr_fill serves one grid; use mpr_fill_batch");
     mpr_status s = MPR_OK;
     if (!ctx->T_set) s = mpr_estimate_T(ctx, nullptr, nullptr);
     if (s != MPR_OK) return s;
     mpr_status eq = mpr_equilibrate(ctx, stats);
     if (eq != MPR_OK && eq != MPR_ENOTEQUIL) return eq;
-    s = mpr_predict(ctx, ctx->prm.M, zhat);
+    s = predict_all(ctx, ctx->prm.M, &zhat);
     return s != MPR_OK ? s : eq;
+}
+
+mpr_status mpr_fill_batch(mpr_ctx* ctx, float* const* zhat) {
+    if (!ctx || !zhat) return MPR_EINVAL;
+    mpr_status s = MPR_OK;
+    if (!ctx->T_set) s = mpr_estimate_T(ctx, nullptr, nullptr);
+    if (s != MPR_OK) return s;
+    mpr_status eq = mpr_equilibrate(ctx, nullptr);
+    if (eq != MPR_OK && eq != MPR_ENOTEQUIL) return eq;
+    s = mpr_predict_batch(ctx, ctx->prm.M, zhat);
+    return s != MPR_OK ? s : eq;
+}
+
+mpr_status mpr_batch_info(mpr_ctx* ctx, int g, double* T, double* e_s, int* sweeps, int* converged,
+                          double* zmin, double* zmax) {
+    if (!ctx || g < 0 || g >= (int)ctx->g.size()) return MPR_EINVAL;
+    std::vector<Ctl> c;
+    mpr_status s = read_ctl(ctx, ctx->b, c);
+    if (s != MPR_OK) return s;
+    const GridInfo& G = ctx->g[g];
+    if (T) *T = G.T;
+    if (e_s) *e_s = G.e_s;
+    if (sweeps) *sweeps = c[g].i;
+    if (converged) *converged = c[g].converged;
+    if (zmin) *zmin = G.zmin;
+    if (zmax) *zmax = G.zmax;
+    return MPR_OK;
 }
 
 mpr_status mpr_get_state(mpr_ctx* ctx, float* phi, uint32_t* sweep) {
     if (!ctx || !phi) return MPR_EINVAL;
-    const size_t n = (size_t)ctx->W * ctx->H;
+    const size_t n = (size_t)ctx->g[0].W * ctx->g[0].H;
     std::vector<Ctl> c;
     mpr_status s = read_ctl(ctx, ctx->b, c);
     if (s != MPR_OK) return s;
@@ -810,7 +983,7 @@ mpr_status mpr_get_state(mpr_ctx* ctx, float* phi, uint32_t* sweep) {
 
 mpr_status mpr_set_state(mpr_ctx* ctx, const float* phi, uint32_t sweep) {
     if (!ctx || !phi) return MPR_EINVAL;
-    const size_t n = (size_t)ctx->W * ctx->H;
+    const size_t n = (size_t)ctx->g[0].W * ctx->g[0].H;
     std::vector<Ctl> c;
     mpr_status s = read_ctl(ctx, ctx->b, c);
     if (s != MPR_OK) return s;
@@ -835,10 +1008,81 @@ mpr_status mpr_get_info(mpr_ctx* ctx, double* H_exact, double* H_tracked, double
         CU(cudaStreamSynchronize(ctx->st));
     }
     if (H_tracked) *H_tracked = c[0].H;
-    if (zmin) *zmin = ctx->zmin;
-    if (zmax) *zmax = ctx->zmax;
-    if (T) *T = ctx->T;
-    if (e_s) *e_s = ctx->e_s;
+    if (zmin) *zmin = ctx->g[0].zmin;
+    if (zmax) *zmax = ctx->g[0].zmax;
+    if (T) *T = ctx->g[0].T;
+    if (e_s) *e_s = ctx->g[0].e_s;
+    return MPR_OK;
+}
+
+// Autotuner: times a few sweeps of every compiled tile configuration on the context's own
+// grids (from a snapshot of the state, restored afterwards, so the chain is unchanged),
+// keeps the fastest, and sizes the captured chunk of sweeps so that the host's once-per-
+// chunk check (a graph launch, a 4-byte read and a synchronisation, also measured) costs
+// about a quarter of the chunk's sweeping time.
+mpr_status mpr_autotune(mpr_ctx* ctx, int* tile_cfg, int* graph_sweeps, double* ms_per_sweep) {
+    if (!ctx) return MPR_EINVAL;
+    Batch& b = ctx->b;
+    if (!b.tiled) return fail(ctx, MPR_ESTATE, "autotuning applies to the tile kernels");
+    if (!ctx->T_set) return fail(ctx, MPR_ESTATE, "temperature not set");
+    // snapshot: both lattice buffers and the control state
+    const size_t bytes = b.lat_elems * sizeof(float2);
+    float2* snap0 = nullptr;
+    float2* snap1 = nullptr;
+    CU(dalloc(&snap0, b.lat_elems));
+    CU(dalloc(&snap1, b.lat_elems));
+    CU(cudaMemcpyAsync(snap0, b.d_lat, bytes, cudaMemcpyDeviceToDevice, ctx->st));
+    CU(cudaMemcpyAsync(snap1, b.d_lat2, bytes, cudaMemcpyDeviceToDevice, ctx->st));
+    std::vector<Ctl> c0;
+    mpr_status s = read_ctl(ctx, b, c0);
+    if (s != MPR_OK) return s;
+    const int n_try = 6;
+    int best = b.tcfg;
+    double best_ms = 1e30;
+    for (int cfg = 0; cfg < tile_config_count() && s == MPR_OK; ++cfg) {
+        s = build_tiles(ctx, b, cfg);
+        if (s != MPR_OK) break;
+        double ms = 0.0;
+        s = mpr_time_sweeps(ctx, 2, 4.0, &ms);                 // warm-up
+        if (s == MPR_OK) s = mpr_time_sweeps(ctx, n_try, 4.0, &ms);
+        if (s == MPR_OK && ms < best_ms) { best_ms = ms; best = cfg; }
+        CU(cudaMemcpyAsync(b.d_lat, snap0, bytes, cudaMemcpyDeviceToDevice, ctx->st));
+        CU(cudaMemcpyAsync(b.d_lat2, snap1, bytes, cudaMemcpyDeviceToDevice, ctx->st));
+        CU(cudaMemcpyAsync(b.d_ctl, c0.data(), sizeof(Ctl) * c0.size(), cudaMemcpyHostToDevice, ctx->st));
+        CU(cudaStreamSynchronize(ctx->st));
+    }
+    cudaFree(snap0);
+    cudaFree(snap1);
+    if (s != MPR_OK) return s;
+    if (best != b.tcfg) {
+        s = build_tiles(ctx, b, best);
+        if (s != MPR_OK) return s;
+    }
+    // cost of the host's check of one chunk: an empty graph launch, a 4-byte read, a sync
+    cudaGraph_t eg = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    CU(cudaGraphCreate(&eg, 0));
+    CU(cudaGraphInstantiate(&ex, eg, 0));
+    auto t0 = std::chrono::steady_clock::now();
+    for (int i = 0; i < 20; ++i) {
+        CU(cudaGraphLaunch(ex, ctx->st));
+        CU(cudaMemcpyAsync(ctx->h_active, b.d_active, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+        CU(cudaStreamSynchronize(ctx->st));
+    }
+    const double check_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() / 20.0;
+    cudaGraphExecDestroy(ex);
+    cudaGraphDestroy(eg);
+    int S = (int)std::lround(4.0 * check_ms / std::max(best_ms, 1e-6));
+    S = std::min(kMaxGraphSweeps, std::max(4, S));
+    if (S != b.gsweeps) {
+        for (auto& kv : b.graphs) cudaGraphExecDestroy(kv.second);
+        b.graphs.clear();
+        b.gsweeps = S;
+    }
+    if (tile_cfg) *tile_cfg = b.tcfg;
+    if (graph_sweeps) *graph_sweeps = b.gsweeps;
+    if (ms_per_sweep) *ms_per_sweep = best_ms;
     return MPR_OK;
 }
 

@@ -44,7 +44,7 @@ struct EntryDesc {            // immutable during a run
     int nblk[2];              // number of sweep blocks of this entry per colour
     int tile0;                // first tile of this entry (tile path)
     int ntiles;               // number of tiles of this entry
-    int prows;                // rows allocated per plane: max(H + 2, kTileRH)
+    int prows;                // rows allocated per plane: max(H + 2, tallest tile box)
     int _pad2;
 };
 
@@ -73,17 +73,15 @@ struct Part {                 // one sweep block's energy change and acceptance 
     unsigned _pad;
 };
 
-// Tile path (mpr_tile.cu): tiles of kTileH x kTileW grid sites.
-#ifndef MPR_TILE_H
-#define MPR_TILE_H 16
-#endif
-#ifndef MPR_TILE_W
-#define MPR_TILE_W 128
-#endif
-constexpr int kTileH = MPR_TILE_H;
-constexpr int kTileW = MPR_TILE_W;
-constexpr int kTileRH = kTileH + 4;           // rows of a tile's TMA box (halo 2)
-constexpr int kTileRW = kTileW / 2 + 4;       // plane columns of a tile's TMA box
+// Tile path (mpr_tile.cu): tiles of TH x TW grid sites in one of the compiled
+// configurations (tile_geom).
+struct TileGeom {
+    int th, tw;               // tile rows and columns (grid sites)
+    int rh, rw;               // TMA box: rows and plane columns of the region (halo 2)
+    int list;                 // u16 list entries per tile slot
+    int acc;                  // accumulator floats per tile
+    int nt;                   // threads per block
+};
 
 struct TileDesc {             // one tile: its grid, origin, and gap-list counts (set-up)
     int entry;
@@ -117,6 +115,7 @@ struct TileArgs {
     double* ehist;
     int ehist_stride;
     int ntiles;
+    int cfg;                  // compiled tile configuration
     int use_ctl_a;
     float half_qd_fixed;
     int skip_stopped;
@@ -344,19 +343,21 @@ cudaError_t launch_philox(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out
                           cudaStream_t st);
 
 // tile path (mpr_tile.cu)
-int tile_list_len();
-int tile_acc_len();
-int tile_sweep_blocks();
-cudaError_t make_tile_maps(const EntryDesc* ents, int n_ent, float2* lat0, float2* lat1,
+TileGeom tile_geom(int cfg);
+int tile_config_count();
+int tile_max_rows();
+int tile_max_cols();
+int tile_sweep_blocks(int cfg);
+cudaError_t make_tile_maps(int cfg, const EntryDesc* ents, int n_ent, float2* lat0, float2* lat1,
                            CUtensorMap* d_maps, cudaStream_t st);
-cudaError_t launch_tile_lists(TileDesc* tiles, int ntiles, const EntryDesc* ents,
+cudaError_t launch_tile_lists(int cfg, TileDesc* tiles, int ntiles, const EntryDesc* ents,
                               const uint8_t* mask, int all_free, uint16_t* lists, TileCnt* cnts,
                               cudaStream_t st);
 cudaError_t launch_tile_sweep(const TileArgs& a, int trig, cudaStream_t st);
-cudaError_t launch_tile_predict_out(const TileDesc* tiles, const TileCnt* cnts, const uint16_t* lists,
-                                    const float* acc, const EntryDesc* ents, int tile0, int ntiles,
-                                    int M, double q, double zmin, double zmax, float* zhat,
-                                    cudaStream_t st);
+cudaError_t launch_tile_predict_out(int cfg, const TileDesc* tiles, const TileCnt* cnts,
+                                    const uint16_t* lists, const float* acc, const EntryDesc* ents,
+                                    int tile0, int ntiles, int M, double q, double zmin, double zmax,
+                                    float* zhat, cudaStream_t st);
 
 // sweeps (mpr_sweep.cu)
 cudaError_t launch_half_sweep(const SweepArgs& a, int color, int trig, cudaStream_t st);

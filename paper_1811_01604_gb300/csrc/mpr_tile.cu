@@ -25,16 +25,6 @@
 
 #include "mpr_internal.cuh"
 
-#ifndef MPR_TILE_THREADS
-#define MPR_TILE_THREADS 128
-#endif
-#ifndef MPR_TILE_STAGES
-#define MPR_TILE_STAGES 1
-#endif
-#ifndef MPR_TILE_MINB
-#define MPR_TILE_MINB 8                         // blocks per SM the register budget must allow
-#endif
-
 namespace mpr {
 
 namespace {
@@ -187,8 +177,8 @@ struct TileParams {
 // through STAGES shared-memory stages.  Thread 0 issues the TMA copies (region box of
 // both planes plus the tile's gap list, one mbarrier per stage) up to STAGES - 1 tiles
 // ahead of the tile being updated.
-template <int TH, int TW, int TRIG, bool ACC, int NT, int STAGES>
-__global__ void __launch_bounds__(NT, MPR_TILE_MINB)
+template <int TH, int TW, int TRIG, bool ACC, int NT, int STAGES, int MB>
+__global__ void __launch_bounds__(NT, MB)
 k_tile_sweep(const TileArgs A) {
     using G = Geo<TH, TW>;
     extern __shared__ __align__(128) unsigned char dsm[];
@@ -469,9 +459,38 @@ __global__ void k_tile_predict_out(const TileDesc* __restrict__ tiles, const Til
 
 }  // namespace
 
+// ---------------------------------------------------------------- compiled configurations
+// The tile shapes the library is built with; the autotuner picks one per batch.
+//   id  TH  TW  threads  stages  blocks/SM register budget
+//    0  16 128     128       1    8
+//    1  32  64     128       1    8
+//    2  32 128     256       1    4
+#define MPR_TILE_CONFIGS(X) \
+    X(0, 16, 128, 128, 1, 8)  \
+    X(1, 32, 64, 128, 1, 8)   \
+    X(2, 32, 128, 256, 1, 4)
+
+template <int TH, int TW, int NT, int ST>
+struct Cfg {
+    using G = Geo<TH, TW>;
+    static constexpr int SMEM = ST * 2 * G::RH * G::RW * 8 + ST * G::LIST * 2;
+};
+
+#define MPR_CFG_GEOM(id, th, tw, nt, st, mb) \
+    case id: g = TileGeom{th, tw, Geo<th, tw>::RH, Geo<th, tw>::RW, Geo<th, tw>::LIST, Geo<th, tw>::ACC, nt}; break;
+TileGeom tile_geom(int cfg) {
+    TileGeom g{0, 0, 0, 0, 0, 0, 0};
+    switch (cfg) { MPR_TILE_CONFIGS(MPR_CFG_GEOM) default: break; }
+    return g;
+}
+int tile_config_count() { return 3; }
+int tile_max_rows() { return 32 + 4; }
+int tile_max_cols() { return 128 / 2 + 4; }
+
 // Tensor maps of every entry's two lattice buffers, viewed as 3-D boxes
-// {plane column, padded row, colour}: 8-byte elements, zero fill out of bounds.
-cudaError_t make_tile_maps(const EntryDesc* ents, int n_ent, float2* lat0, float2* lat1,
+// {plane column, padded row, colour} of the configuration's region size: 8-byte elements,
+// zero fill out of bounds.
+cudaError_t make_tile_maps(int cfg, const EntryDesc* ents, int n_ent, float2* lat0, float2* lat1,
                            CUtensorMap* d_maps, cudaStream_t st) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -482,7 +501,7 @@ cudaError_t make_tile_maps(const EntryDesc* ents, int n_ent, float2* lat0, float
         if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
-    using G = Geo<kTileH, kTileW>;
+    const TileGeom g = tile_geom(cfg);
     std::vector<CUtensorMap> maps((size_t)2 * n_ent);
     for (int e = 0; e < n_ent; ++e) {
         const EntryDesc& E = ents[e];
@@ -490,7 +509,7 @@ cudaError_t make_tile_maps(const EntryDesc* ents, int n_ent, float2* lat0, float
             float2* base = (b ? lat1 : lat0) + E.plane[0];
             const cuuint64_t dims[3] = {(cuuint64_t)E.pitch, (cuuint64_t)E.prows, 2};
             const cuuint64_t strides[2] = {(cuuint64_t)E.pitch * 8, (cuuint64_t)E.prows * E.pitch * 8};
-            const cuuint32_t box[3] = {(cuuint32_t)G::RW, (cuuint32_t)G::RH, 2};
+            const cuuint32_t box[3] = {(cuuint32_t)g.rw, (cuuint32_t)g.rh, 2};
             const cuuint32_t estr[3] = {1, 1, 1};
             CUresult r = encode(&maps[2 * e + b], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, base, dims,
                                 strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -503,72 +522,85 @@ cudaError_t make_tile_maps(const EntryDesc* ents, int n_ent, float2* lat0, float
                            cudaMemcpyHostToDevice, st);
 }
 
-constexpr int kNT = MPR_TILE_THREADS;           // threads per tile block
-constexpr int kST = MPR_TILE_STAGES;            // shared-memory stages per block
-constexpr int kSmem = kST * 2 * Geo<kTileH, kTileW>::RH * Geo<kTileH, kTileW>::RW * 8 +
-                      kST * Geo<kTileH, kTileW>::LIST * 2;
-
-// Opts the sweep kernels into their dynamic shared memory (more than the default 48 KB)
-// and returns the persistent grid size: blocks per SM at that footprint times the SMs.
-// Called from set-up code, never under stream capture.
-int tile_sweep_blocks() {
-    static int blocks = 0;
-    if (!blocks) {
-        cudaFuncSetAttribute(k_tile_sweep<kTileH, kTileW, TRIG_ACCURATE, true, kNT, kST>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-        cudaFuncSetAttribute(k_tile_sweep<kTileH, kTileW, TRIG_ACCURATE, false, kNT, kST>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-        cudaFuncSetAttribute(k_tile_sweep<kTileH, kTileW, TRIG_FAST, true, kNT, kST>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-        cudaFuncSetAttribute(k_tile_sweep<kTileH, kTileW, TRIG_FAST, false, kNT, kST>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per, k_tile_sweep<kTileH, kTileW, TRIG_ACCURATE, true, kNT, kST>, kNT, kSmem);
-        blocks = std::max(1, sms * std::max(1, per));
-    }
-    return blocks;
+// Opts the sweep kernels of every configuration into their dynamic shared memory (more
+// than the default 48 KB) and returns the persistent grid size of configuration cfg:
+// blocks per SM at its footprint times the SMs.  Called from set-up code, never under
+// stream capture.
+template <int TH, int TW, int NT, int ST, int MB>
+int blocks_for() {
+    constexpr int sm = Cfg<TH, TW, NT, ST>::SMEM;
+    cudaFuncSetAttribute(k_tile_sweep<TH, TW, TRIG_ACCURATE, true, NT, ST, MB>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_tile_sweep<TH, TW, TRIG_ACCURATE, false, NT, ST, MB>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_tile_sweep<TH, TW, TRIG_FAST, true, NT, ST, MB>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_tile_sweep<TH, TW, TRIG_FAST, false, NT, ST, MB>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per, k_tile_sweep<TH, TW, TRIG_ACCURATE, true, NT, ST, MB>, NT, sm);
+    return std::max(1, sms * std::max(1, per));
 }
 
-int tile_list_len() { return Geo<kTileH, kTileW>::LIST; }
-int tile_acc_len() { return Geo<kTileH, kTileW>::ACC; }
+#define MPR_CFG_BLOCKS(id, th, tw, nt, st, mb) \
+    case id: blocks[id] = blocks_for<th, tw, nt, st, mb>(); break;
+int tile_sweep_blocks(int cfg) {
+    static int blocks[8] = {0};
+    if (cfg < 0 || cfg >= tile_config_count()) return 0;
+    if (!blocks[cfg]) {
+        switch (cfg) { MPR_TILE_CONFIGS(MPR_CFG_BLOCKS) default: break; }
+    }
+    return blocks[cfg];
+}
 
-cudaError_t launch_tile_lists(TileDesc* tiles, int ntiles, const EntryDesc* ents,
+#define MPR_CFG_LISTS(id, th, tw, nt, st, mb) \
+    case id: k_tile_lists<th, tw><<<(ntiles * 32 + 127) / 128, 128, 0, st_>>>(tiles, ntiles, ents, mask, all_free, lists, cnts); break;
+cudaError_t launch_tile_lists(int cfg, TileDesc* tiles, int ntiles, const EntryDesc* ents,
                               const uint8_t* mask, int all_free, uint16_t* lists, TileCnt* cnts,
-                              cudaStream_t st) {
+                              cudaStream_t st_) {
     if (ntiles == 0) return cudaSuccess;
-    count_launches(1, st);
-    k_tile_lists<kTileH, kTileW><<<(ntiles * 32 + 127) / 128, 128, 0, st>>>(tiles, ntiles, ents, mask,
-                                                                            all_free, lists, cnts);
+    count_launches(1, st_);
+    switch (cfg) { MPR_TILE_CONFIGS(MPR_CFG_LISTS) default: return cudaErrorInvalidValue; }
     return cudaGetLastError();
 }
 
+template <int TH, int TW, int NT, int ST, int MB>
+void sweep_for(const TileArgs& a, int trig, cudaStream_t st) {
+    constexpr int sm = Cfg<TH, TW, NT, ST>::SMEM;
+    const int nb = std::min(a.ntiles, tile_sweep_blocks(a.cfg));
+    const bool acc = a.acc != nullptr;
+    if (trig == TRIG_FAST) {
+        if (acc) k_tile_sweep<TH, TW, TRIG_FAST, true, NT, ST, MB><<<nb, NT, sm, st>>>(a);
+        else k_tile_sweep<TH, TW, TRIG_FAST, false, NT, ST, MB><<<nb, NT, sm, st>>>(a);
+    } else {
+        if (acc) k_tile_sweep<TH, TW, TRIG_ACCURATE, true, NT, ST, MB><<<nb, NT, sm, st>>>(a);
+        else k_tile_sweep<TH, TW, TRIG_ACCURATE, false, NT, ST, MB><<<nb, NT, sm, st>>>(a);
+    }
+}
+#define MPR_CFG_SWEEP(id, th, tw, nt, st_, mb) \
+    case id: sweep_for<th, tw, nt, st_, mb>(a, trig, st); break;
 cudaError_t launch_tile_sweep(const TileArgs& a, int trig, cudaStream_t st) {
     if (a.ntiles == 0) return cudaSuccess;
     count_launches(1, st);
-    const bool acc = a.acc != nullptr;
-    const int nb = std::min(a.ntiles, tile_sweep_blocks());
-    if (trig == TRIG_FAST) {
-        if (acc) k_tile_sweep<kTileH, kTileW, TRIG_FAST, true, kNT, kST><<<nb, kNT, kSmem, st>>>(a);
-        else k_tile_sweep<kTileH, kTileW, TRIG_FAST, false, kNT, kST><<<nb, kNT, kSmem, st>>>(a);
-    } else {
-        if (acc) k_tile_sweep<kTileH, kTileW, TRIG_ACCURATE, true, kNT, kST><<<nb, kNT, kSmem, st>>>(a);
-        else k_tile_sweep<kTileH, kTileW, TRIG_ACCURATE, false, kNT, kST><<<nb, kNT, kSmem, st>>>(a);
-    }
+    switch (a.cfg) { MPR_TILE_CONFIGS(MPR_CFG_SWEEP) default: return cudaErrorInvalidValue; }
     return cudaGetLastError();
 }
 
-cudaError_t launch_tile_predict_out(const TileDesc* tiles, const TileCnt* cnts, const uint16_t* lists,
-                                    const float* acc, const EntryDesc* ents, int tile0, int ntiles,
-                                    int M, double q, double zmin, double zmax, float* zhat,
-                                    cudaStream_t st) {
+#define MPR_CFG_OUT(id, th, tw, nt, st_, mb) \
+    case id: k_tile_predict_out<th, tw><<<ntiles, 256, 0, st>>>( \
+        tiles + tile0, cnts + tile0, lists + (long long)tile0 * g.list, acc + (long long)tile0 * g.acc, \
+        ents, M, q, zmin, zmax, zhat); break;
+cudaError_t launch_tile_predict_out(int cfg, const TileDesc* tiles, const TileCnt* cnts,
+                                    const uint16_t* lists, const float* acc, const EntryDesc* ents,
+                                    int tile0, int ntiles, int M, double q, double zmin, double zmax,
+                                    float* zhat, cudaStream_t st) {
     if (ntiles == 0) return cudaSuccess;
     count_launches(1, st);
-    k_tile_predict_out<kTileH, kTileW><<<ntiles, 256, 0, st>>>(
-        tiles + tile0, cnts + tile0, lists + (long long)tile0 * tile_list_len(),
-        acc + (long long)tile0 * tile_acc_len(), ents, M, q, zmin, zmax, zhat);
+    const TileGeom g = tile_geom(cfg);
+    switch (cfg) { MPR_TILE_CONFIGS(MPR_CFG_OUT) default: return cudaErrorInvalidValue; }
     return cudaGetLastError();
 }
 

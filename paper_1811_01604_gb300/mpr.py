@@ -36,6 +36,7 @@ class mpr_params(ctypes.Structure):
         ("trig_mode", ctypes.c_int), ("a_eq", ctypes.c_double), ("KT", ctypes.c_int),
         ("T_min", ctypes.c_double), ("T_max", ctypes.c_double), ("T_cap", ctypes.c_int),
         ("M_T", ctypes.c_int), ("exec_mode", ctypes.c_int), ("chain", ctypes.c_uint32),
+        ("tile_cfg", ctypes.c_int),
     ]
 
 
@@ -63,6 +64,13 @@ _SIGS = [
     ("mpr_equilibrate", _I, [_VP, ctypes.POINTER(mpr_equil_stats)]),
     ("mpr_predict", _I, [_VP, _I, _VP]),
     ("mpr_fill", _I, [_VP, _VP, ctypes.POINTER(mpr_equil_stats)]),
+    ("mpr_init_batch", _I, [ctypes.POINTER(_VP), _I, _VP, _VP, _VP, _VP, ctypes.POINTER(mpr_params), _VP]),
+    ("mpr_batch_size", _I, [_VP]),
+    ("mpr_predict_batch", _I, [_VP, _I, _VP]),
+    ("mpr_fill_batch", _I, [_VP, _VP]),
+    ("mpr_batch_info", _I, [_VP, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I),
+                            ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    ("mpr_autotune", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     ("mpr_free", None, [_VP]),
     ("mpr_last_error", ctypes.c_char_p, [_VP]),
     ("mpr_get_state", _I, [_VP, _VP, ctypes.POINTER(ctypes.c_uint32)]),
@@ -177,6 +185,53 @@ def mpr_fill(ctx, zhat) -> mpr_equil_stats:
     out = mpr_equil_stats()
     _check(ctx, lib().mpr_fill(ctx, _ptr(zhat), ctypes.byref(out)), ok=(MPR_OK, MPR_ENOTEQUIL))
     return out
+
+
+def _ptr_array(bufs):
+    arr = (ctypes.c_void_p * len(bufs))()
+    for i, b in enumerate(bufs):
+        arr[i] = _ptr(b)
+    return arr
+
+
+def mpr_init_batch(zs, masks, params: mpr_params | None = None, stream=None):
+    """zs, masks: sequences of [H][W] arrays/tensors (sizes may differ)."""
+    n = len(zs)
+    W = (ctypes.c_int * n)(*[int(z.shape[1]) for z in zs])
+    H = (ctypes.c_int * n)(*[int(z.shape[0]) for z in zs])
+    ctx = ctypes.c_void_p()
+    st = lib().mpr_init_batch(ctypes.byref(ctx), n, _ptr_array(zs), _ptr_array(masks), W, H,
+                              ctypes.byref(params) if params is not None else None, _stream(stream))
+    if st != MPR_OK:
+        raise MprError(st, lib().mpr_status_string(st).decode())
+    return ctx
+
+
+def mpr_batch_size(ctx) -> int:
+    return int(lib().mpr_batch_size(ctx))
+
+
+def mpr_predict_batch(ctx, M: int, zhats):
+    _check(ctx, lib().mpr_predict_batch(ctx, int(M), _ptr_array(zhats)))
+
+
+def mpr_fill_batch(ctx, zhats) -> int:
+    return _check(ctx, lib().mpr_fill_batch(ctx, _ptr_array(zhats)), ok=(MPR_OK, MPR_ENOTEQUIL))
+
+
+def mpr_batch_info(ctx, g: int) -> dict:
+    T, es, zmin, zmax = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    sw, cv = ctypes.c_int(), ctypes.c_int()
+    _check(ctx, lib().mpr_batch_info(ctx, int(g), ctypes.byref(T), ctypes.byref(es), ctypes.byref(sw),
+                                     ctypes.byref(cv), ctypes.byref(zmin), ctypes.byref(zmax)))
+    return dict(T=T.value, e_s=es.value, sweeps=sw.value, converged=cv.value, zmin=zmin.value,
+                zmax=zmax.value)
+
+
+def mpr_autotune(ctx) -> dict:
+    cfg, gs, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(ctx, lib().mpr_autotune(ctx, ctypes.byref(cfg), ctypes.byref(gs), ctypes.byref(ms)))
+    return dict(tile_cfg=cfg.value, graph_sweeps=gs.value, ms_per_sweep=ms.value)
 
 
 def mpr_free(ctx):

@@ -47,6 +47,68 @@ def wm_field(L: int, nu: float, xi: float, seed: int, m: float = 50.0, sigma: fl
     return z.astype(np.float32)
 
 
+def wm_field_gpu(H: int, W: int, nu: float, xi: float, seed: int, m: float = 50.0,
+                 sigma: float = 10.0, device="cuda"):
+    """Same spectral method as wm_field, computed with torch on a GPU (for large batches of
+    inputs).  Eq. 7 in closed form for nu in {0.5, 1, 1.5, 2.5} (K_1 for nu = 1).  The white
+    noise comes from torch's generator, so fields differ from wm_field's for one seed."""
+    import torch
+    pad = int(max(32, 16 * xi))
+    ny, nx = H + pad, W + pad
+    ny += ny % 2
+    nx += nx % 2
+    dy = torch.arange(ny, device=device, dtype=torch.float64)
+    dx = torch.arange(nx, device=device, dtype=torch.float64)
+    dy = torch.minimum(dy, ny - dy)
+    dx = torch.minimum(dx, nx - dx)
+    kh = torch.sqrt(dy[:, None] ** 2 + dx[None, :] ** 2) / float(xi)
+    if nu == 0.5:
+        C = torch.exp(-kh)
+    elif nu == 1.5:
+        C = (1.0 + kh) * torch.exp(-kh)
+    elif nu == 2.5:
+        C = (1.0 + kh + kh * kh / 3.0) * torch.exp(-kh)
+    elif nu == 1.0:
+        C = torch.where(kh > 0, kh * torch.special.modified_bessel_k1(torch.clamp(kh, min=1e-300)),
+                        torch.ones_like(kh))
+    else:
+        raise ValueError("nu must be one of 0.5, 1, 1.5, 2.5")
+    lam = torch.clamp(torch.fft.rfft2(C).real, min=0.0)
+    del C, kh
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    w = torch.randn((ny, nx), generator=gen, device=device, dtype=torch.float64)
+    g = torch.fft.irfft2(torch.sqrt(lam) * torch.fft.rfft2(w), s=(ny, nx))
+    return (m + sigma * g[:H, :W]).to(torch.float32).contiguous()
+
+
+def batch_workload(n: int = 256, L_min: int = 128, L_max: int = 2048, seed: int = 4):
+    """Parameters of the batched workload: per grid g (seed + g) a side L log-uniform in
+    [L_min, L_max], nu in {0.5, 1, 2.5}, correlation length uniform in [4, 64], missing
+    fraction uniform in [0.2, 0.7]."""
+    out = []
+    for g in range(n):
+        rng = np.random.Generator(np.random.PCG64(seed + g))
+        L = int(round(float(np.exp(rng.uniform(np.log(L_min), np.log(L_max))))))
+        nu = float(rng.choice([0.5, 1.0, 2.5]))
+        xi = float(rng.uniform(4.0, 64.0))
+        p = float(rng.uniform(0.2, 0.7))
+        out.append(dict(L=L, nu=nu, xi=xi, p=p, seed=seed + g))
+    return out
+
+
+def mask_uniform_gpu(H: int, W: int, p: float, seed: int, device="cuda"):
+    """uint8 [H][W] with exactly round(p*H*W) gaps (0) placed uniformly, via torch."""
+    import torch
+    n = H * W
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    perm = torch.randperm(n, generator=gen, device=device)
+    m = torch.ones(n, dtype=torch.uint8, device=device)
+    m[perm[: int(round(p * n))]] = 0
+    return m.view(H, W)
+
+
 def wm_covariance(h, nu: float, xi: float, sigma: float = 10.0):
     """Eq. 7, the Whittle-Matern covariance at distance h (for generator checks)."""
     from scipy.special import gamma, kv
