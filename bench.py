@@ -100,6 +100,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
+# DRAM bytes per launch of k_tile_sweep on this grid from one ncu capture
+# (profiles/k_tile_sweep_4096.md), valid for the kernel sources with this hash only.
+TILE_TRAFFIC_BYTES = 243.8e6
+TILE_TRAFFIC_SOURCE_HASH = "f151b74d83f9cbc6"
+
+
+def tile_kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("mpr_tile.cu", "mpr_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1811_01604_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -392,7 +407,8 @@ def main():
                     "h2d_bytes_per_step": N * 5, "d2h_bytes_per_step": N * 4},
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None,
+                         "frac": achieved / hbm,
+                         "traffic": TILE_TRAFFIC_BYTES if tile_kernel_hash() == TILE_TRAFFIC_SOURCE_HASH else None,
                          "kernel": "k_tile_sweep", "ms_per_launch": sweep_ms,
                          "peak_source": f"{peak_src} hbm_gbs",
                          "bytes_per_launch": bytes_per_launch},
