@@ -174,15 +174,43 @@ def run_reference(args, rank):
 
 
 def profile_case(name):
-    """4096^2 bench grid, T = 0.05, 24 sweeps at a = 8: about 50 half-sweep launches."""
+    """sweep4096: 4096^2 bench grid, T = 0.05, 24 sweeps at a = 8 (about 50 sweep launches).
+    net4096: two warm-start forward passes (untrained network) on the 4096^2 bench grid.
+    net128: two training steps of the warm-start network on a batch of 32 128^2 grids."""
     import torch
     from paper_1811_01604_gb300 import mpr
+    if name == "net128":
+        B, S = 32, 128
+        g = torch.Generator(device="cuda")
+        g.manual_seed(0)
+        z = torch.rand((B, S, S), generator=g, device="cuda")
+        m = (torch.rand((B, S, S), generator=g, device="cuda") > 0.4).to(torch.uint8)
+        phi = 6.283 * torch.rand((B, S, S), generator=g, device="cuda")
+        net = mpr.mpr_net_create(0)
+        try:
+            for _ in range(2):
+                mpr.mpr_net_train_step(net, z, m, phi, np.zeros(B), np.ones(B), B, S, S, 1e-3)
+            torch.cuda.synchronize()
+        finally:
+            mpr.mpr_net_free(net)
+        print(f"profile case {name}: done")
+        return
     z_np, m_np = make_inputs(0)
     H, W = z_np.shape
     z = torch.from_numpy(z_np).cuda()
     mask = torch.from_numpy(m_np).cuda()
     ctx = mpr.mpr_init(z, mask, W, H, mpr.mpr_default_params(seed=1))
     try:
+        if name == "net4096":
+            net = mpr.mpr_net_create(0)
+            try:
+                for _ in range(2):
+                    mpr.mpr_warmstart_init(ctx, net)
+                torch.cuda.synchronize()
+            finally:
+                mpr.mpr_net_free(net)
+            print(f"profile case {name}: done")
+            return
         mpr.mpr_set_T(ctx, 0.05)
         st = mpr.mpr_sweep(ctx, 24, 8.0)
         torch.cuda.synchronize()
@@ -270,6 +298,133 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def net_flops_per_site():
+    """Useful multiply-adds x 2 of one forward pass per full-resolution site (the first
+    convolution counted with its 3 used input channels)."""
+    lev = [0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0]
+    cin = [3, 32, 32, 64, 64, 128, 128, 256, 384, 128, 192, 64, 96, 32]
+    cout = [32, 32, 64, 64, 128, 128, 256, 256, 128, 128, 64, 64, 32, 32]
+    return sum(2 * 9 * a * b / 4 ** l for a, b, l in zip(cin, cout, lev)) + 2 * 32 * 2
+
+
+def run_warm(args):
+    """Learned warm start against the plain random start on the same maps: a step fills one
+    map twice (plain, then warm-started), each timed with CUDA events; the network is
+    trained first (untimed) on equilibrium states of 64^2 grids and 128^2 crops of 1024^2
+    fields made by the library's own MCMC."""
+    import torch
+    from paper_1811_01604_gb300 import mpr, synth, warmstart
+    Lw = 1024 if args.workload == "warm1024" else 4096
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    groups = warmstart.training_grids(n64=args.train_n64, n128=args.train_n128, seed=10_000)
+    sets = [warmstart.equilibrium_states(z, m, states_per_grid=4, spacing=20, seed=20_000) for z, m in groups]
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = warmstart.WarmStartNet(seed=0)
+    t0 = time.perf_counter()
+    losses = warmstart.train(net, sets, steps=args.train_steps, batch=32, lr=1e-3, seed=0)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    if Lw == 1024:
+        z = synth.wm_field_gpu(1024, 1024, 0.5, 16.0, 1)
+        mask = synth.mask_uniform_gpu(1024, 1024, 0.33, 1_000_001)
+        wl = "mpr-warmstart-1024x1024-wm-nu0.5-xi16-p0.33"
+    else:
+        z_np, m_np = make_inputs(0)
+        z, mask = torch.from_numpy(z_np).cuda(), torch.from_numpy(m_np).cuda()
+        wl = "mpr-warmstart-4096x4096-wm-nu1-xi32-p0.5-disks"
+    H, W = z.shape
+    gap = mask == 0
+    P = int(gap.sum().item())
+    out = torch.empty_like(z)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    prm = mpr.mpr_default_params(seed=1, M=M)
+
+    def fill(use_net):
+        ctx = mpr.mpr_init(z, mask, W, H, prm, stream.cuda_stream)
+        try:
+            mpr.mpr_estimate_T(ctx)
+            if use_net:
+                net.warmstart(ctx)
+            st = mpr.mpr_equilibrate(ctx)
+            mpr.mpr_predict(ctx, M, out)
+        finally:
+            mpr.mpr_free(ctx)
+        return st.sweeps
+
+    def timed(use_net, n):
+        ms, sw = [], []
+        for _ in range(n):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sw.append(fill(use_net))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        mae = float((out - z)[gap].abs().mean())
+        return ms, sw, mae
+
+    for _ in range(args.warmup):
+        fill(False)
+        fill(True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = mpr.mpr_kernel_launches()
+    ms_w, sw_w, mae_w = timed(True, args.steps)
+    launches = mpr.mpr_kernel_launches() - l0
+    ms_p, sw_p, mae_p = timed(False, args.steps)
+    # inference alone: the warm start of a fresh context, timed on the context's stream
+    ctx = mpr.mpr_init(z, mask, W, H, prm, stream.cuda_stream)
+    try:
+        inf = []
+        for _ in range(3):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            net.warmstart(ctx)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            inf.append(e0.elapsed_time(e1))
+    finally:
+        mpr.mpr_free(ctx)
+    clk = clocks.stop()
+    inf_ms = statistics.median(inf)
+    Hp, Wp = (H + 7) // 8 * 8, (W + 7) // 8 * 8
+    flops = net_flops_per_site() * Hp * Wp
+    peaks, src = measured_peaks()
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    ach = flops / (inf_ms * 1e-3) / 1e12
+    n_states = sum(s.n for s in sets)
+    line = {"metric": "s per map (warm start)", "value": statistics.mean(ms_w) * 1e-3, "unit": "s/map",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.mean(ms_w), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 lattice, bf16 network", "data": "synthetic",
+            "config": {"workload": wl, "W": W, "H": H, "gap_sites": P, "M": M,
+                       "l2": "512 MB buffer written between steps (L2 flush)",
+                       "train": {"states": n_states, "steps": args.train_steps, "batch": 32,
+                                 "data_s": t_data, "train_s": t_train,
+                                 "loss_first20": float(np.mean(losses[:20])),
+                                 "loss_last20": float(np.mean(losses[-20:]))}},
+            "warm": {"s_per_map": statistics.mean(ms_w) * 1e-3, "relax_sweeps": sw_w, "mae": mae_w,
+                     "inference_ms": inf_ms},
+            "plain": {"s_per_map": statistics.mean(ms_p) * 1e-3, "relax_sweeps": sw_p, "mae": mae_p},
+            "speedup_vs_plain": statistics.mean(ms_p) / statistics.mean(ms_w),
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach / peak, "traffic": None,
+                         "kernel": "warm-start forward (14 x k_conv3x3 + 9 small kernels)",
+                         "flops_per_launch": flops, "ms_per_launch": inf_ms,
+                         "peak_source": f"{src} bf16_tflops"},
+            "clocks": clk}
+    net.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -277,11 +432,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mpr", choices=["mpr", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-case", default=None, choices=["sweep4096"],
+    ap.add_argument("--profile-case", default=None, choices=["sweep4096", "net4096", "net128"],
                     help="run a small fixed sweep workload for ncu instead of the benchmark")
-    ap.add_argument("--workload", default="fill4096", choices=["fill4096", "batch256"],
+    ap.add_argument("--workload", default="fill4096", choices=["fill4096", "batch256", "warm1024", "warm4096"],
                     help="fill4096: one 4096^2 map per step (default); batch256: 256 grids of "
-                         "sides 128-2048 filled in one batch, against the same grids one at a time")
+                         "sides 128-2048 filled in one batch, against the same grids one at a time; "
+                         "warm1024 / warm4096: learned warm start against the plain random start")
+    ap.add_argument("--train-steps", type=int, default=2000, help="warm start: Adam steps")
+    ap.add_argument("--train-n64", type=int, default=1024, help="warm start: 64^2 training grids")
+    ap.add_argument("--train-n128", type=int, default=4096, help="warm start: 128^2 training crops")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -295,6 +454,9 @@ def main():
         return
     if args.workload == "batch256":
         run_batch(args)
+        return
+    if args.workload in ("warm1024", "warm4096"):
+        run_warm(args)
         return
 
     import torch

@@ -208,6 +208,8 @@ const char* mpr_last_error(const mpr_ctx* ctx);
  */
 mpr_status mpr_get_state(mpr_ctx* ctx, float* phi, uint32_t* sweep);
 mpr_status mpr_set_state(mpr_ctx* ctx, const float* phi, uint32_t sweep);
+/* Grid g of a batch context: its current angles phi (float[H_g][W_g], as above). */
+mpr_status mpr_get_state_batch(mpr_ctx* ctx, int g, float* phi);
 
 /*
  * Energy bookkeeping: H_exact recomputes Eq. 2 over all bonds; H_tracked is the

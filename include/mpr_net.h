@@ -1,0 +1,103 @@
+/*
+ * mpr_net.h -- C ABI of the learned warm start of libmpr.so.
+ *
+ * The warm start replaces the uniform random initial state of the gap sites in
+ * Algorithm 2 (the conditional hybrid Monte Carlo then runs unchanged: the same
+ * relaxation with the energy-slope stopping test, the same M equilibrium sweeps).
+ * It is not part of the paper's method; a good initial state only shortens the
+ * relaxation.
+ *
+ * Network: a 4-level convolutional encoder-decoder (U-Net style) on the grid.
+ *  - Input per site (NHWC, 32 channels, 3 used): (cos theta, sin theta, 1) at
+ *    sample sites and (0, 0, 0) at gap sites, with theta = q phi, q = 1/2, and phi
+ *    the data-to-angle map of Eq. 1 (zmin, zmax of the grid's samples).
+ *  - Encoder: two 3x3 convolutions + ReLU per level, channels 32, 64, 128, 256;
+ *    2x2 average pooling between levels.  Decoder: nearest 2x upsampling,
+ *    concatenation with the encoder output of the same level, two 3x3
+ *    convolutions + ReLU (128, 64, 32); a 1x1 head to (u, v).
+ *  - Prediction: theta_0 = direction of (u, max(v, 0)) in [0, pi), phi_0 = 2 theta_0.
+ *  - Loss (training), mean over the batch's gap sites: 1 - cos(theta_0 - theta_t)
+ *    with theta_t = phi_t / 2 of an equilibrium state of the MCMC.
+ *  - Precision: bf16 weights and activations, fp32 accumulation (tensor cores),
+ *    fp32 master weights, gradients, head and loss.  Adam (beta 0.9, 0.999, eps 1e-8).
+ *  - Parameters: one fp32 vector; per convolution (order e0a e0b e1a e1b e2a e2b
+ *    e3a e3b d2a d2b d1a d1b d0a d0b) W[9][C_in][C_out] (tap = 3 dy + dx) then
+ *    b[C_out]; then the head Wh[32][2], bh[2].
+ *
+ * Conventions: as in mpr.h.  z (float), mask (uint8, 1 = sample) and phi_target
+ * (float, radians in [0, 2 pi)) are [B][H][W] device arrays (B images of one
+ * shape, contiguous); zmin, zmax are B doubles (host or device).  H and W are
+ * positive multiples of 8, 1 <= B <= 4096.  All work is enqueued on the stream
+ * given at creation; calls that return host values synchronise it.  A network is
+ * not thread-safe.  Its activation workspace is sized for the last (B, H, W)
+ * and reallocated when that changes.
+ */
+#ifndef MPR_NET_H_
+#define MPR_NET_H_
+
+#include <stdint.h>
+
+#include "mpr.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpr_net mpr_net;
+
+/* A new network with He-initialised weights drawn from seed (host PRNG).
+   ENOMEM / ECUDA on device failure; *net is NULL then. */
+mpr_status mpr_net_create(mpr_net** net, uint64_t seed, void* cuda_stream);
+void mpr_net_free(mpr_net* net);
+const char* mpr_net_last_error(const mpr_net* net);
+
+/* Number of fp32 parameters (the layout above). */
+long long mpr_net_num_params(const mpr_net* net);
+/* Copy the fp32 parameters out / in (host or device, num_params floats).  set
+   also refreshes the bf16 copy and resets the Adam state. */
+mpr_status mpr_net_get_params(mpr_net* net, float* params);
+mpr_status mpr_net_set_params(mpr_net* net, const float* params);
+/* Accumulated gradient (num_params floats) and its reset. */
+mpr_status mpr_net_get_grads(mpr_net* net, float* grads);
+mpr_status mpr_net_zero_grads(mpr_net* net);
+
+/* Forward pass, loss and backward pass on a batch; the gradient is ADDED to the
+   network's gradient buffer.  *loss (host, may be NULL: no synchronisation) is the
+   mean loss over the batch's gap sites (0 if there are none). */
+mpr_status mpr_net_loss_grad(mpr_net* net, const float* z, const uint8_t* mask, const float* phi_target,
+                             const double* zmin, const double* zmax, int B, int H, int W, double* loss);
+/* One Adam step with learning rate lr on the accumulated gradient, which it clears. */
+mpr_status mpr_net_adam_step(mpr_net* net, float lr);
+/* mpr_net_loss_grad followed by mpr_net_adam_step. */
+mpr_status mpr_net_train_step(mpr_net* net, const float* z, const uint8_t* mask, const float* phi_target,
+                              const double* zmin, const double* zmax, int B, int H, int W, float lr,
+                              double* loss);
+/* Network output (u, v) per site: uv is float [B][H][W][2] (host or device). */
+mpr_status mpr_net_forward(mpr_net* net, const float* z, const uint8_t* mask, const double* zmin,
+                           const double* zmax, int B, int H, int W, float* uv);
+
+/* Writes the warm-start state theta_0 into the gap sites of every grid of a
+   context (replacing their random initial state; samples are untouched).  Grids of
+   any shape (the network runs on the grid padded to multiples of 8, padding read
+   as gaps).  Call after mpr_init / mpr_init_batch and before mpr_equilibrate or
+   mpr_fill.  EINVAL for NULL arguments. */
+mpr_status mpr_warmstart_init(mpr_ctx* ctx, mpr_net* net);
+
+/* Test support: one 3x3 convolution (zero padding 1) of the network on caller
+   device buffers.  in: bf16 [B][H][W][Cin], w: bf16 [9][Cin][Cout], bias: fp32
+   [Cout] or NULL, out: bf16 [B][H][W][Cout] = relu?(conv(in) + bias).  Cin, Cout
+   positive multiples of 32. */
+mpr_status mpr_net_conv3x3(const uint16_t* in, int B, int H, int W, int Cin, const uint16_t* w,
+                           const float* bias, int Cout, int relu, uint16_t* out, void* cuda_stream);
+/* Its two gradients for an output gradient gout (bf16 [B][H][W][Cout]):
+   din = fp32 [B][H][W][Cin] (overwritten), dw = fp32 [9][Cin][Cout] (added to);
+   w_scratch: bf16 [9][Cin][Cout] device scratch. */
+mpr_status mpr_net_conv3x3_bwd(const uint16_t* in, const uint16_t* gout, int B, int H, int W, int Cin,
+                               const uint16_t* w, int Cout, float* din, float* dw, uint16_t* w_scratch,
+                               void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPR_NET_H_ */

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmpr.so")
-SOURCES = ["mpr_init.cu", "mpr_sweep.cu", "mpr_tile.cu", "mpr_api.cu", "mpr_static.cu"]
+SOURCES = ["mpr_init.cu", "mpr_sweep.cu", "mpr_tile.cu", "mpr_api.cu", "mpr_static.cu", "mpr_net.cu",
+           "mpr_net_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]
@@ -37,7 +38,8 @@ def _stale() -> bool:
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [
-        os.path.join(HERE, "..", "include", "mpr.h"), os.path.abspath(__file__)]
+        os.path.join(HERE, "..", "include", "mpr.h"), os.path.join(HERE, "..", "include", "mpr_net.h"),
+        os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 

@@ -22,6 +22,7 @@
 
 #include "../../include/mpr.h"
 #include "mpr_internal.cuh"
+#include "mpr_net_internal.cuh"
 
 using namespace mpr;
 
@@ -952,6 +953,31 @@ mpr_status mpr_fill_batch(mpr_ctx* ctx, float* const* zhat) {
     return s != MPR_OK ? s : eq;
 }
 
+// Warm start: the network's initial gap state for every grid, run on runs of consecutive
+// grids of one shape (contiguous in the concatenated buffers) as one batch.
+mpr_status mpr_warmstart_init(mpr_ctx* ctx, mpr_net* net) {
+    if (!ctx || !net) return MPR_EINVAL;
+    Batch& b = ctx->b;
+    float2* lat1 = b.tiled ? b.d_lat2 : nullptr;
+    const int n = (int)ctx->g.size();
+    for (int i = 0; i < n;) {
+        int j = i + 1;
+        while (j < n && j - i < 4096 && ctx->g[j].W == ctx->g[i].W && ctx->g[j].H == ctx->g[i].H) ++j;
+        std::vector<double> zmin, zmax;
+        for (int k = i; k < j; ++k) {
+            zmin.push_back(ctx->g[k].zmin);
+            zmax.push_back(ctx->g[k].zmax);
+        }
+        const GridInfo& G = ctx->g[i];
+        const mpr_status s = mprnet_warmstart(net, ctx->d_z + G.site0, ctx->d_mask + G.site0, j - i, G.H, G.W,
+                                              zmin.data(), zmax.data(), b.d_ents + i, b.d_lat, lat1, ctx->st);
+        if (s != MPR_OK) return fail(ctx, s, std::string("warm start: ") + mprnet_error(net));
+        i = j;
+    }
+    CU(cudaStreamSynchronize(ctx->st));
+    return MPR_OK;
+}
+
 mpr_status mpr_batch_info(mpr_ctx* ctx, int g, double* T, double* e_s, int* sweeps, int* converged,
                           double* zmin, double* zmax) {
     if (!ctx || g < 0 || g >= (int)ctx->g.size()) return MPR_EINVAL;
@@ -978,6 +1004,18 @@ mpr_status mpr_get_state(mpr_ctx* ctx, float* phi, uint32_t* sweep) {
     CU(cudaMemcpyAsync(phi, ctx->d_out, n * sizeof(float), cudaMemcpyDefault, ctx->st));
     CU(cudaStreamSynchronize(ctx->st));
     if (sweep) *sweep = c[0].sweep;
+    return MPR_OK;
+}
+
+mpr_status mpr_get_state_batch(mpr_ctx* ctx, int g, float* phi) {
+    if (!ctx || !phi || g < 0 || g >= (int)ctx->g.size()) return MPR_EINVAL;
+    const GridInfo& G = ctx->g[g];
+    std::vector<Ctl> c;
+    mpr_status s = read_ctl(ctx, ctx->b, c);
+    if (s != MPR_OK) return s;
+    CU(launch_get_state(&ctx->b.ents[g], lat_cur(ctx->b, c[g]), ctx->d_out + G.site0, ctx->st));
+    CU(cudaMemcpyAsync(phi, ctx->d_out + G.site0, (size_t)G.W * G.H * sizeof(float), cudaMemcpyDefault, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
     return MPR_OK;
 }
 

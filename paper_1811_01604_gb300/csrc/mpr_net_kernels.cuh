@@ -1,0 +1,57 @@
+// mpr_net_kernels.cuh -- BF16 tensor-core kernels of the warm-start network.
+//
+// Activations are NHWC bf16, weights [tap = 3 ky + kx][C_in][C_out] bf16 (C_out contiguous),
+// gradients fp32.  Every 3x3 convolution (stride 1, zero padding 1) is an implicit GEMM
+// over M = pixels, N = output channels, K = 9 C_in, computed with mma.sync m16n8k16
+// (bf16 x bf16 -> fp32) on fragments loaded by ldmatrix from cp.async-filled shared memory.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mprnet {
+
+typedef __nv_bfloat16 bf16;
+
+// A convolution input: the channel-wise concatenation of src0 (C0 channels, full
+// resolution) and src1 (C1 channels, at half resolution and upsampled by nearest
+// neighbour if up1, else full resolution).  C0 and C1 are multiples of 32 (C1 may be 0).
+struct ConvIn {
+    const bf16* src0;
+    int C0;
+    const bf16* src1;
+    int C1;
+    int up1;
+};
+
+// An fp32 output split by channel ranges: channels [0, C0) to dst0, [C0, C0 + C1) to dst1
+// (each NHWC with its own channel count); accumulate adds to the destination.
+struct ConvOutF32 {
+    float* dst0;
+    int C0;
+    float* dst1;
+    int C1;
+    int accumulate;
+};
+
+struct ConvArgs {
+    ConvIn in;
+    int B, H, W;                 // spatial size of input and output
+    int Cin;                     // C0 + C1
+    const bf16* w;               // [9 * Cin][Cout]
+    int Cout;
+    const float* bias;           // forward: [Cout] or null
+    int relu;                    // forward: apply ReLU
+    bf16* out_bf16;              // forward output [B][H][W][Cout]
+    ConvOutF32 out_f32;          // backward output (used when out_bf16 is null)
+};
+
+cudaError_t conv3x3(const ConvArgs& a, cudaStream_t st);
+
+// dW[tap][ci][co] += sum_p in(p + tap)[ci] * g[p][co] over all pixels (in: ConvIn with the
+// forward layer's input, g: bf16 [B][H][W][Cout]).  dW fp32, accumulated with atomics.
+cudaError_t conv3x3_wgrad(const ConvIn& in, int B, int H, int W, int Cin, const bf16* g, int Cout,
+                          float* dW, cudaStream_t st);
+
+}  // namespace mprnet

@@ -81,6 +81,24 @@ _SIGS = [
     ("mpr_sample_energy_static", _I, [_VP, _VP, _I, _I, _D, ctypes.POINTER(_D),
                                       ctypes.POINTER(ctypes.c_longlong), _VP]),
     ("mpr_philox", _I, [_VP, ctypes.c_uint64, _VP, ctypes.c_size_t, _VP]),
+    ("mpr_get_state_batch", _I, [_VP, _I, _VP]),
+    # include/mpr_net.h
+    ("mpr_net_create", _I, [ctypes.POINTER(_VP), ctypes.c_uint64, _VP]),
+    ("mpr_net_free", None, [_VP]),
+    ("mpr_net_last_error", ctypes.c_char_p, [_VP]),
+    ("mpr_net_num_params", ctypes.c_longlong, [_VP]),
+    ("mpr_net_get_params", _I, [_VP, _VP]),
+    ("mpr_net_set_params", _I, [_VP, _VP]),
+    ("mpr_net_get_grads", _I, [_VP, _VP]),
+    ("mpr_net_zero_grads", _I, [_VP]),
+    ("mpr_net_loss_grad", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _I, ctypes.POINTER(_D)]),
+    ("mpr_net_adam_step", _I, [_VP, ctypes.c_float]),
+    ("mpr_net_train_step", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _I, ctypes.c_float,
+                                ctypes.POINTER(_D)]),
+    ("mpr_net_forward", _I, [_VP, _VP, _VP, _VP, _VP, _I, _I, _I, _VP]),
+    ("mpr_warmstart_init", _I, [_VP, _VP]),
+    ("mpr_net_conv3x3", _I, [_VP, _I, _I, _I, _I, _VP, _VP, _I, _I, _VP, _VP]),
+    ("mpr_net_conv3x3_bwd", _I, [_VP, _VP, _I, _I, _I, _I, _VP, _I, _VP, _VP, _VP, _VP]),
 ]
 
 
@@ -286,3 +304,94 @@ def mpr_philox(ctr, seed: int, out, stream=None):
     st = lib().mpr_philox(_ptr(ctr), ctypes.c_uint64(seed), _ptr(out), n, _stream(stream))
     if st != MPR_OK:
         raise MprError(st, lib().mpr_status_string(st).decode())
+
+
+def mpr_get_state_batch(ctx, g: int, phi):
+    _check(ctx, lib().mpr_get_state_batch(ctx, int(g), _ptr(phi)))
+
+
+# ---------------------------------------------------------------- warm-start network
+def _ncheck(net, st):
+    if st != MPR_OK:
+        msg = lib().mpr_net_last_error(net).decode() if net else ""
+        raise MprError(st, f"{lib().mpr_status_string(st).decode()}: {msg}")
+    return st
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+
+
+def mpr_net_create(seed: int = 0, stream=None):
+    net = ctypes.c_void_p()
+    _ncheck(None, lib().mpr_net_create(ctypes.byref(net), ctypes.c_uint64(seed), _stream(stream)))
+    return net
+
+
+def mpr_net_free(net):
+    if net:
+        lib().mpr_net_free(net)
+
+
+def mpr_net_num_params(net) -> int:
+    return int(lib().mpr_net_num_params(net))
+
+
+def mpr_net_get_params(net, out):
+    _ncheck(net, lib().mpr_net_get_params(net, _ptr(out)))
+
+
+def mpr_net_set_params(net, params):
+    _ncheck(net, lib().mpr_net_set_params(net, _ptr(params)))
+
+
+def mpr_net_get_grads(net, out):
+    _ncheck(net, lib().mpr_net_get_grads(net, _ptr(out)))
+
+
+def mpr_net_zero_grads(net):
+    _ncheck(net, lib().mpr_net_zero_grads(net))
+
+
+def mpr_net_loss_grad(net, z, mask, phi_t, zmin, zmax, B: int, H: int, W: int, want_loss=True):
+    lo = ctypes.c_double()
+    zmin, zmax = _f64(zmin), _f64(zmax)
+    _ncheck(net, lib().mpr_net_loss_grad(net, _ptr(z), _ptr(mask), _ptr(phi_t), _ptr(zmin), _ptr(zmax),
+                                         int(B), int(H), int(W), ctypes.byref(lo) if want_loss else None))
+    return lo.value if want_loss else None
+
+
+def mpr_net_adam_step(net, lr: float):
+    _ncheck(net, lib().mpr_net_adam_step(net, float(lr)))
+
+
+def mpr_net_train_step(net, z, mask, phi_t, zmin, zmax, B: int, H: int, W: int, lr: float,
+                       want_loss=True):
+    lo = ctypes.c_double()
+    zmin, zmax = _f64(zmin), _f64(zmax)
+    _ncheck(net, lib().mpr_net_train_step(net, _ptr(z), _ptr(mask), _ptr(phi_t), _ptr(zmin), _ptr(zmax),
+                                          int(B), int(H), int(W), float(lr),
+                                          ctypes.byref(lo) if want_loss else None))
+    return lo.value if want_loss else None
+
+
+def mpr_net_forward(net, z, mask, zmin, zmax, B: int, H: int, W: int, uv):
+    zmin, zmax = _f64(zmin), _f64(zmax)
+    _ncheck(net, lib().mpr_net_forward(net, _ptr(z), _ptr(mask), _ptr(zmin), _ptr(zmax), int(B), int(H),
+                                       int(W), _ptr(uv)))
+
+
+def mpr_warmstart_init(ctx, net):
+    _check(ctx, lib().mpr_warmstart_init(ctx, net))
+
+
+def mpr_net_conv3x3(x, B, H, W, Cin, w, bias, Cout, relu, out, stream=None):
+    st = lib().mpr_net_conv3x3(_ptr(x), int(B), int(H), int(W), int(Cin), _ptr(w), _ptr(bias), int(Cout),
+                               int(relu), _ptr(out), _stream(stream))
+    _ncheck(None, st)
+
+
+def mpr_net_conv3x3_bwd(x, gout, B, H, W, Cin, w, Cout, din, dw, w_scratch, stream=None):
+    st = lib().mpr_net_conv3x3_bwd(_ptr(x), _ptr(gout), int(B), int(H), int(W), int(Cin), _ptr(w),
+                                   int(Cout), _ptr(din), _ptr(dw), _ptr(w_scratch), _stream(stream))
+    _ncheck(None, st)
