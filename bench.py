@@ -176,7 +176,8 @@ def run_reference(args, rank):
 def profile_case(name):
     """sweep4096: 4096^2 bench grid, T = 0.05, 24 sweeps at a = 8 (about 50 sweep launches).
     net4096: two warm-start forward passes (untrained network) on the 4096^2 bench grid.
-    net128: two training steps of the warm-start network on a batch of 32 128^2 grids."""
+    net128: two training steps of the warm-start network on a batch of 32 128^2 grids.
+    net1024: two warm-start forward passes (untrained network) on a 1024^2 grid."""
     import torch
     from paper_1811_01604_gb300 import mpr
     if name == "net128":
@@ -195,13 +196,19 @@ def profile_case(name):
             mpr.mpr_net_free(net)
         print(f"profile case {name}: done")
         return
-    z_np, m_np = make_inputs(0)
-    H, W = z_np.shape
-    z = torch.from_numpy(z_np).cuda()
-    mask = torch.from_numpy(m_np).cuda()
+    if name == "net1024":
+        from paper_1811_01604_gb300 import synth
+        z = synth.wm_field_gpu(1024, 1024, 0.5, 16.0, 1)
+        mask = synth.mask_uniform_gpu(1024, 1024, 0.33, 1_000_001)
+        H, W = 1024, 1024
+    else:
+        z_np, m_np = make_inputs(0)
+        H, W = z_np.shape
+        z = torch.from_numpy(z_np).cuda()
+        mask = torch.from_numpy(m_np).cuda()
     ctx = mpr.mpr_init(z, mask, W, H, mpr.mpr_default_params(seed=1))
     try:
-        if name == "net4096":
+        if name in ("net4096", "net1024"):
             net = mpr.mpr_net_create(0)
             try:
                 for _ in range(2):
@@ -317,7 +324,8 @@ def run_warm(args):
     Lw = 1024 if args.workload == "warm1024" else 4096
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    groups = warmstart.training_grids(n64=args.train_n64, n128=args.train_n128, seed=10_000)
+    groups = warmstart.training_grids(n64=args.train_n64, n128=args.train_n128, seed=10_000,
+                                      n256=args.train_n256)
     sets = [warmstart.equilibrium_states(z, m, states_per_grid=4, spacing=20, seed=20_000) for z, m in groups]
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
@@ -406,7 +414,8 @@ def run_warm(args):
             "vs_baseline": None, "dtype": "f32 lattice, bf16 network", "data": "synthetic",
             "config": {"workload": wl, "W": W, "H": H, "gap_sites": P, "M": M,
                        "l2": "512 MB buffer written between steps (L2 flush)",
-                       "train": {"states": n_states, "steps": args.train_steps, "batch": 32,
+                       "train": {"states": n_states, "steps": args.train_steps, "batch": "32 x 128^2 sites",
+                                 "groups": [list(st.z.shape) for st in sets],
                                  "data_s": t_data, "train_s": t_train,
                                  "loss_first20": float(np.mean(losses[:20])),
                                  "loss_last20": float(np.mean(losses[-20:]))}},
@@ -432,7 +441,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mpr", choices=["mpr", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-case", default=None, choices=["sweep4096", "net4096", "net128"],
+    ap.add_argument("--profile-case", default=None, choices=["sweep4096", "net4096", "net1024", "net128"],
                     help="run a small fixed sweep workload for ncu instead of the benchmark")
     ap.add_argument("--workload", default="fill4096", choices=["fill4096", "batch256", "warm1024", "warm4096"],
                     help="fill4096: one 4096^2 map per step (default); batch256: 256 grids of "
@@ -441,6 +450,8 @@ def main():
     ap.add_argument("--train-steps", type=int, default=2000, help="warm start: Adam steps")
     ap.add_argument("--train-n64", type=int, default=1024, help="warm start: 64^2 training grids")
     ap.add_argument("--train-n128", type=int, default=4096, help="warm start: 128^2 training crops")
+    ap.add_argument("--train-n256", type=int, default=1024,
+                    help="warm start: 256^2 training crops with the 4096^2 workload's disk gaps")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))

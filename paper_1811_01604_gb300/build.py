@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmpr.so")
 SOURCES = ["mpr_init.cu", "mpr_sweep.cu", "mpr_tile.cu", "mpr_api.cu", "mpr_static.cu", "mpr_net.cu",
-           "mpr_net_kernels.cu"]
+           "mpr_net_kernels.cu", "mpr_net_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

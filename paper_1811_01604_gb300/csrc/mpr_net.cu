@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <random>
 #include <string>
@@ -292,6 +293,7 @@ int grid1(long long n) {
 const int kLevel[14] = {0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0};
 const int kCin[14] = {kIn, 32, 32, 64, 64, 128, 128, 256, 128 + 256, 128, 64 + 128, 64, 32 + 64, 32};
 const int kCout[14] = {32, 32, 64, 64, 128, 128, 256, 256, 128, 128, 64, 64, 32, 32};
+const int kCatC[3] = {32 + 64, 64 + 128, 128 + 256};
 
 }  // namespace
 
@@ -305,7 +307,12 @@ struct mpr_net {
     float* m = nullptr;                // Adam moments
     float* v = nullptr;
     bf16* wb = nullptr;                // bf16 copy of the parameters (conv weights are read from it)
-    bf16* wflip = nullptr;             // flipped weights of one layer (backward)
+    bf16* wflip = nullptr;             // flipped weights of one layer (backward, legacy kernel)
+    bf16* wt = nullptr;                // K-major weights of the tensor-core kernels: forward
+    bf16* wtb = nullptr;               //   and data-gradient, per layer at wt_off / wtb_off
+    long long wt_off[14] = {0}, wtb_off[14] = {0};
+    bool legacy = false;               // MPR_NET_CONV=mma: all convolutions on mma.sync
+    int* d_err = nullptr;              // set by a tensor-core kernel whose barrier wait expired
     int adam_t = 0;
     double* d_zr = nullptr;            // zmin[kMaxB], zmax[kMaxB]
     double* d_loss = nullptr;
@@ -322,6 +329,8 @@ struct mpr_net {
     float* dact[14] = {nullptr};
     float* dpool[3] = {nullptr};
     float* dup = nullptr;              // gradient w.r.t. an upsampled tensor
+    bf16* cat[3] = {nullptr};          // decoder inputs [A_l, up(lower)] of levels 0-2, written by
+                                       //   the producing layers (tensor-core path)
     bf16* gb = nullptr;                // gated bf16 gradient of one layer
     std::string err;
 };
@@ -372,6 +381,8 @@ mpr_status ensure_ws(mpr_net* net, int B, int H, int W, bool train) {
         if (train) NCU(nalloc(net, &net->dpool[i], P * kCout[2 * i + 1]));
     }
     NCU(nalloc(net, &net->out2, P0 * 2));
+    if (!net->legacy)
+        for (int i = 0; i < 3; ++i) NCU(nalloc(net, &net->cat[i], (P0 >> (2 * i)) * kCatC[i]));
     if (train) {
         NCU(nalloc(net, &net->dout2, P0 * 2));
         NCU(nalloc(net, &net->dup, P0 * 64));       // largest: level 0, 64 upsampled channels
@@ -381,6 +392,75 @@ mpr_status ensure_ws(mpr_net* net, int B, int H, int W, bool train) {
     net->H = H;
     net->W = W;
     net->train = train;
+    return MPR_OK;
+}
+
+// K-major copies of the current bf16 weights for the tensor-core kernels
+mpr_status refresh_wt(mpr_net* net) {
+    if (net->legacy) return MPR_OK;
+    for (int l = 0; l < 14; ++l) {
+        NCU(mprnet::tc_weights(net->wb + net->off_w[l], kCin[l], kCout[l], 0, net->wt + net->wt_off[l], net->st));
+        NCU(mprnet::tc_weights(net->wb + net->off_w[l], kCin[l], kCout[l], 1, net->wtb + net->wtb_off[l], net->st));
+    }
+    mpr::count_launches(28, net->st);
+    return MPR_OK;
+}
+
+// One convolution: tensor cores (TMA-fed, weights from the K-major copy) or the legacy
+// kernel.  On the tensor-core path the decoder inputs are the concatenation buffers, which
+// the layers producing their parts also write (A_l as is, the lower level upsampled).
+mpr_status conv(mpr_net* net, ConvArgs& a, int l, bool dgrad) {
+    if (net->legacy) {
+        NCU(mprnet::conv3x3(a, net->st));
+        mpr::count_launches(1, net->st);
+        return MPR_OK;
+    }
+    mprnet::TcConv c;
+    std::memset(&c, 0, sizeof c);
+    c.B = a.B; c.H = a.H; c.W = a.W;
+    c.N = a.Cout;
+    if (dgrad) {
+        c.in = a.in.src0;
+        c.C = a.Cin;
+        c.wt = net->wtb + net->wtb_off[l];
+        c.of = a.out_f32;
+    } else {
+        if (l == 8 || l == 10 || l == 12) {
+            const int lev = kLevel[l];
+            c.in = net->cat[lev];
+            c.C = kCatC[lev];
+        } else {
+            c.in = a.in.src0;
+            c.C = a.Cin;
+        }
+        c.wt = net->wt + net->wt_off[l];
+        c.bias = a.bias;
+        c.relu = a.relu;
+        c.out = a.out_bf16;
+        switch (l) {                       // parts of the concatenation buffers
+            case 1: c.out2 = net->cat[0]; c.ld2 = kCatC[0]; c.off2 = 0; c.pool = net->pool[0]; break;
+            case 3: c.out2 = net->cat[1]; c.ld2 = kCatC[1]; c.off2 = 0; c.pool = net->pool[1]; break;
+            case 5: c.out2 = net->cat[2]; c.ld2 = kCatC[2]; c.off2 = 0; c.pool = net->pool[2]; break;
+            case 7: c.out2 = net->cat[2]; c.ld2 = kCatC[2]; c.off2 = 128; c.up2 = 1; break;
+            case 9: c.out2 = net->cat[1]; c.ld2 = kCatC[1]; c.off2 = 64; c.up2 = 1; break;
+            case 11: c.out2 = net->cat[0]; c.ld2 = kCatC[0]; c.off2 = 32; c.up2 = 1; break;
+            default: break;
+        }
+    }
+    NCU(mprnet::conv3x3_tma(c, net->d_err, net->st));
+    mpr::count_launches(1, net->st);
+    return MPR_OK;
+}
+
+// Reads and clears the kernels' error flag (synchronises the stream).
+mpr_status check_err(mpr_net* net) {
+    int h = 0;
+    NCU(cudaMemcpyAsync(&h, net->d_err, sizeof(int), cudaMemcpyDeviceToHost, net->st));
+    NCU(cudaStreamSynchronize(net->st));
+    if (h) {
+        NCU(cudaMemsetAsync(net->d_err, 0, sizeof(int), net->st));
+        return nfail(net, MPR_ETIMEOUT, "a tensor-core convolution's barrier wait expired");
+    }
     return MPR_OK;
 }
 
@@ -425,9 +505,9 @@ mpr_status forward(mpr_net* net) {
         a.bias = net->w + net->off_b[l];
         a.relu = 1;
         a.out_bf16 = net->act[l];
-        NCU(mprnet::conv3x3(a, st));
-        mpr::count_launches(1, st);
-        if (l == 1 || l == 3 || l == 5) {
+        const mpr_status cs = conv(net, a, l, false);
+        if (cs != MPR_OK) return cs;
+        if (net->legacy && (l == 1 || l == 3 || l == 5)) {   // fused into the convolution otherwise
             k_pool<<<grid1((long long)B * (Hl / 2) * (Wl / 2) * kCout[l]), 256, 0, st>>>(net->act[l], B, Hl, Wl,
                                                                                      kCout[l], net->pool[l / 2]);
             mpr::count_launches(1, st);
@@ -456,7 +536,10 @@ mpr_status backward(mpr_net* net) {
         NCU(mprnet::conv3x3_wgrad(layer_in(net, l), B, Hl, Wl, Cin, net->gb, Cout, net->g + net->off_w[l], st));
         mpr::count_launches(3, st);
         if (l == 0) break;                                    // no gradient w.r.t. the network input
-        k_flip<<<grid1(9LL * Cin * Cout), 256, 0, st>>>(net->wb + net->off_w[l], Cin, Cout, net->wflip);
+        if (net->legacy) {
+            k_flip<<<grid1(9LL * Cin * Cout), 256, 0, st>>>(net->wb + net->off_w[l], Cin, Cout, net->wflip);
+            mpr::count_launches(1, st);
+        }
         ConvArgs a;
         std::memset(&a, 0, sizeof a);
         a.in = ConvIn{net->gb, Cout, nullptr, 0, 0};
@@ -472,8 +555,8 @@ mpr_status backward(mpr_net* net) {
         } else {
             a.out_f32 = {net->dact[l - 1], Cin, nullptr, 0, 0};
         }
-        NCU(mprnet::conv3x3(a, st));
-        mpr::count_launches(2, st);
+        const mpr_status cs = conv(net, a, l, true);
+        if (cs != MPR_OK) return cs;
         if (l == 8 || l == 10 || l == 12) {
             const int low = l - 1;
             const int Cl = kCout[low];
@@ -516,6 +599,7 @@ mpr_status mprnet_warmstart(mpr_net* net, const float* z, const uint8_t* mask, i
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = nfail(net, MPR_ECUDA, std::string("k_to_lattice: ") + cudaGetErrorString(e));
     }
+    if (s == MPR_OK) s = check_err(net);
     net->st = keep;
     return s;
 }
@@ -541,6 +625,17 @@ mpr_status mpr_net_create(mpr_net** out, uint64_t seed, void* cuda_stream) {
     net->off_bh = off;
     off += 2;
     net->n_params = off;
+    long long owt = 0, owtb = 0;
+    for (int l = 0; l < 14; ++l) {
+        net->wt_off[l] = owt;
+        owt += (long long)kCout[l] * 9 * mprnet::tc_layer_kt(kCin[l], kCout[l]);
+        net->wtb_off[l] = owtb;
+        owtb += (long long)kCin[l] * 9 * mprnet::tc_layer_kt(kCout[l], kCin[l]);
+    }
+    {
+        const char* env = std::getenv("MPR_NET_CONV");
+        net->legacy = env && std::string(env) == "mma";
+    }
     std::vector<float> h((size_t)off, 0.f);
     std::mt19937_64 rng(seed);
     for (int l = 0; l < 14; ++l) {                 // He initialisation (3 used input channels at l = 0)
@@ -563,7 +658,10 @@ mpr_status mpr_net_create(mpr_net** out, uint64_t seed, void* cuda_stream) {
               cudaMalloc((void**)&net->wflip, sizeof(bf16) * 9 * 256 * 256) == cudaSuccess &&
               cudaMalloc((void**)&net->d_zr, sizeof(double) * 2 * kMaxB) == cudaSuccess &&
               cudaMalloc((void**)&net->d_loss, sizeof(double)) == cudaSuccess &&
-              cudaMalloc((void**)&net->d_cnt, sizeof(unsigned long long)) == cudaSuccess;
+              cudaMalloc((void**)&net->d_cnt, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc((void**)&net->wt, sizeof(bf16) * owt) == cudaSuccess &&
+              cudaMalloc((void**)&net->wtb, sizeof(bf16) * owtb) == cudaSuccess &&
+              cudaMalloc((void**)&net->d_err, sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         mpr_net_free(net);
@@ -573,10 +671,11 @@ mpr_status mpr_net_create(mpr_net** out, uint64_t seed, void* cuda_stream) {
          cudaMemsetAsync(net->g, 0, sizeof(float) * off, net->st) == cudaSuccess &&
          cudaMemsetAsync(net->m, 0, sizeof(float) * off, net->st) == cudaSuccess &&
          cudaMemsetAsync(net->v, 0, sizeof(float) * off, net->st) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(net->d_err, 0, sizeof(int), net->st) == cudaSuccess;
     if (ok) {
         k_to_bf16<<<grid1(off), 256, 0, net->st>>>(net->w, off, net->wb);
         mpr::count_launches(1, net->st);
-        ok = cudaStreamSynchronize(net->st) == cudaSuccess;
+        ok = refresh_wt(net) == MPR_OK && cudaStreamSynchronize(net->st) == cudaSuccess;
     }
     if (!ok) {
         mpr_net_free(net);
@@ -599,6 +698,9 @@ void mpr_net_free(mpr_net* net) {
     cudaFree(net->d_zr);
     cudaFree(net->d_loss);
     cudaFree(net->d_cnt);
+    cudaFree(net->wt);
+    cudaFree(net->wtb);
+    cudaFree(net->d_err);
     delete net;
 }
 
@@ -618,6 +720,10 @@ mpr_status mpr_net_set_params(mpr_net* net, const float* params) {
     NCU(cudaMemcpyAsync(net->w, params, sizeof(float) * net->n_params, cudaMemcpyDefault, net->st));
     k_to_bf16<<<grid1(net->n_params), 256, 0, net->st>>>(net->w, net->n_params, net->wb);
     mpr::count_launches(1, net->st);
+    {
+        const mpr_status rs = refresh_wt(net);
+        if (rs != MPR_OK) return rs;
+    }
     NCU(cudaMemsetAsync(net->m, 0, sizeof(float) * net->n_params, net->st));
     NCU(cudaMemsetAsync(net->v, 0, sizeof(float) * net->n_params, net->st));
     NCU(cudaStreamSynchronize(net->st));
@@ -628,8 +734,7 @@ mpr_status mpr_net_set_params(mpr_net* net, const float* params) {
 mpr_status mpr_net_get_grads(mpr_net* net, float* grads) {
     if (!net || !grads) return MPR_EINVAL;
     NCU(cudaMemcpyAsync(grads, net->g, sizeof(float) * net->n_params, cudaMemcpyDefault, net->st));
-    NCU(cudaStreamSynchronize(net->st));
-    return MPR_OK;
+    return check_err(net);
 }
 
 mpr_status mpr_net_zero_grads(mpr_net* net) {
@@ -656,7 +761,7 @@ mpr_status mpr_net_loss_grad(mpr_net* net, const float* z, const uint8_t* mask, 
     if (s != MPR_OK) return s;
     if (loss) {
         NCU(cudaMemcpyAsync(loss, net->d_loss, sizeof(double), cudaMemcpyDefault, net->st));
-        NCU(cudaStreamSynchronize(net->st));
+        return check_err(net);
     }
     return MPR_OK;
 }
@@ -670,7 +775,7 @@ mpr_status mpr_net_adam_step(mpr_net* net, float lr) {
                                                      1e-8f, c1, c2, net->wb);
     mpr::count_launches(1, net->st);
     NCU(cudaGetLastError());
-    return MPR_OK;
+    return refresh_wt(net);
 }
 
 mpr_status mpr_net_train_step(mpr_net* net, const float* z, const uint8_t* mask, const float* phi_target,
@@ -688,48 +793,73 @@ mpr_status mpr_net_forward(mpr_net* net, const float* z, const uint8_t* mask, co
     if (s == MPR_OK) s = forward(net);
     if (s != MPR_OK) return s;
     NCU(cudaMemcpyAsync(uv, net->out2, sizeof(float) * 2 * (size_t)B * H * W, cudaMemcpyDefault, net->st));
-    NCU(cudaStreamSynchronize(net->st));
-    return MPR_OK;
+    return check_err(net);
 }
 
+// Test support: the library's own convolution kernels on caller buffers.
 mpr_status mpr_net_conv3x3(const uint16_t* in, int B, int H, int W, int Cin, const uint16_t* w, const float* bias,
                            int Cout, int relu, uint16_t* out, void* cuda_stream) {
-    if (!in || !w || !out || B < 1 || H < 1 || W < 1 || Cin < 32 || Cout < 32 || Cin % 32 || Cout % 32)
+    if (!in || !w || !out || B < 1 || H < 1 || W < 1 || Cin < 32 || Cout < 32 || Cin % 32 || Cout % 32 ||
+        !mprnet::tc_supported(Cin, Cout))
         return MPR_EINVAL;
-    ConvArgs a;
-    std::memset(&a, 0, sizeof a);
-    a.in = ConvIn{(const bf16*)in, Cin, nullptr, 0, 0};
-    a.B = B; a.H = H; a.W = W;
-    a.Cin = Cin;
-    a.w = (const bf16*)w;
-    a.Cout = Cout;
-    a.bias = bias;
-    a.relu = relu;
-    a.out_bf16 = (bf16*)out;
-    mpr::count_launches(1, (cudaStream_t)cuda_stream);
-    return mprnet::conv3x3(a, (cudaStream_t)cuda_stream) == cudaSuccess ? MPR_OK : MPR_ECUDA;
+    const cudaStream_t st = (cudaStream_t)cuda_stream;
+    bf16* wt = nullptr;
+    int* err = nullptr;
+    int herr = 0;
+    mprnet::TcConv c;
+    std::memset(&c, 0, sizeof c);
+    c.in = (const bf16*)in;
+    c.C = Cin;
+    c.B = B; c.H = H; c.W = W;
+    c.N = Cout;
+    c.bias = bias;
+    c.relu = relu;
+    c.out = (bf16*)out;
+    cudaError_t e = cudaMalloc((void**)&wt, sizeof(bf16) * (size_t)Cout * 9 * mprnet::tc_layer_kt(Cin, Cout));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = mprnet::tc_weights((const bf16*)w, Cin, Cout, 0, wt, st);
+    c.wt = wt;
+    if (e == cudaSuccess) e = mprnet::conv3x3_tma(c, err, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    mpr::count_launches(2, st);
+    cudaFree(wt);
+    cudaFree(err);
+    return e != cudaSuccess ? MPR_ECUDA : herr ? MPR_ETIMEOUT : MPR_OK;
 }
 
 mpr_status mpr_net_conv3x3_bwd(const uint16_t* in, const uint16_t* gout, int B, int H, int W, int Cin,
                                const uint16_t* w, int Cout, float* din, float* dw, uint16_t* w_scratch,
                                void* cuda_stream) {
     if (!in || !gout || !w || !din || !dw || !w_scratch || B < 1 || H < 1 || W < 1 || Cin < 32 || Cout < 32 ||
-        Cin % 32 || Cout % 32)
+        Cin % 32 || Cout % 32 || !mprnet::tc_supported(Cout, Cin))
         return MPR_EINVAL;
     const cudaStream_t st = (cudaStream_t)cuda_stream;
     const ConvIn ci{(const bf16*)in, Cin, nullptr, 0, 0};
     if (mprnet::conv3x3_wgrad(ci, B, H, W, Cin, (const bf16*)gout, Cout, dw, st) != cudaSuccess) return MPR_ECUDA;
-    k_flip<<<grid1(9LL * Cin * Cout), 256, 0, st>>>((const bf16*)w, Cin, Cout, (bf16*)w_scratch);
-    ConvArgs a;
-    std::memset(&a, 0, sizeof a);
-    a.in = ConvIn{(const bf16*)gout, Cout, nullptr, 0, 0};
-    a.B = B; a.H = H; a.W = W;
-    a.Cin = Cout;
-    a.w = (const bf16*)w_scratch;
-    a.Cout = Cin;
-    a.out_f32 = {din, Cin, nullptr, 0, 0};
+    bf16* wt = nullptr;
+    int* err = nullptr;
+    int herr = 0;
+    mprnet::TcConv c;
+    std::memset(&c, 0, sizeof c);
+    c.in = (const bf16*)gout;
+    c.C = Cout;
+    c.B = B; c.H = H; c.W = W;
+    c.N = Cin;
+    c.of = {din, Cin, nullptr, 0, 0};
+    cudaError_t e = cudaMalloc((void**)&wt, sizeof(bf16) * (size_t)Cin * 9 * mprnet::tc_layer_kt(Cout, Cin));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = mprnet::tc_weights((const bf16*)w, Cin, Cout, 1, wt, st);
+    c.wt = wt;
+    if (e == cudaSuccess) e = mprnet::conv3x3_tma(c, err, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     mpr::count_launches(3, st);
-    return mprnet::conv3x3(a, st) == cudaSuccess ? MPR_OK : MPR_ECUDA;
+    cudaFree(wt);
+    cudaFree(err);
+    return e != cudaSuccess ? MPR_ECUDA : herr ? MPR_ETIMEOUT : MPR_OK;
 }
 
 }  // extern "C"

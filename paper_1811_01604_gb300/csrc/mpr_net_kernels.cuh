@@ -54,4 +54,39 @@ cudaError_t conv3x3(const ConvArgs& a, cudaStream_t st);
 cudaError_t conv3x3_wgrad(const ConvIn& in, int B, int H, int W, int Cin, const bf16* g, int Cout,
                           float* dW, cudaStream_t st);
 
+// ---- tensor-core (tcgen05 + TMA) path: forward and data-gradient convolutions ----
+// K-major weights: wt[n][k], k = tap * Kt + c, zero for c >= C, with C the input channels of
+// the convolution, N its output channels and Kt = tc_layer_kt(C, N) (C itself for the
+// halo-tile kernel, else C rounded up to 64).  flip = 0: forward weights of w[9][Cin][Cout]
+// (n = co, C = Cin); flip = 1: data-gradient weights (n = ci, C = Cout, tap reflected).
+int tc_kt(int C);
+int tc_layer_kt(int C, int N);
+cudaError_t tc_weights(const bf16* w, int Cin, int Cout, int flip, bf16* wt, cudaStream_t st);
+// Channel counts the kernel instantiates: C any multiple of 8; N in {32, 64, 96, 128, 192,
+// 256, 384}.
+bool tc_supported(int C, int N);
+
+// One tensor-core convolution.  in: NHWC bf16 [B][H][W][C] (16-byte aligned).  bf16 output
+// (out non-null): out[p][N] = relu?(conv + bias), and if out2: the same values also at
+// out2[p'][off2 + n] with channel stride ld2, where p' is p itself or, with up2, each of the
+// 2 x 2 pixels of a 2H x 2W image that p covers under nearest upsampling; if pool: the 2 x 2
+// average of the stored bf16 values, ((a + b) + c) + d then times 1/4, at [B][H/2][W/2][N]
+// (H, W even).  fp32 output (out null): `of` as in ConvOutF32.
+struct TcConv {
+    const bf16* in;
+    int C;
+    int B, H, W;
+    int N;
+    const bf16* wt;
+    const float* bias;
+    int relu;
+    bf16* out;
+    bf16* out2;
+    int ld2, off2, up2;
+    bf16* pool;
+    ConvOutF32 of;
+};
+// A barrier wait that expires sets *err (device int) to 1.
+cudaError_t conv3x3_tma(const TcConv& c, int* err, cudaStream_t st);
+
 }  // namespace mprnet

@@ -36,11 +36,15 @@ def _uniform_masks(n, H, W, p, seed, device):
     return m.view(n, H, W)
 
 
-def training_grids(n64: int, n128: int, seed: int = 10_000, device="cuda"):
-    """Input grids for the training set, as two shape groups of (z, mask) CUDA tensors:
+def training_grids(n64: int, n128: int, seed: int = 10_000, device="cuda", n256: int = 0):
+    """Input grids for the training set, as shape groups of (z, mask) CUDA tensors:
       * n64 grids 64 x 64: nu = 0.5, correlation length 4, 33 % uniform gaps;
       * n128 crops 128 x 128 of 1024 x 1024 fields: nu in {0.5, 2.5}, correlation
-        length 16, Gaussian or lognormal, 33 % or 66 % uniform gaps.
+        length 16, Gaussian or lognormal, 33 % or 66 % uniform gaps;
+      * n256 crops 256 x 256 of 4096 x 4096 fields with nu = 1, correlation length 32, and
+        half of the sites missing as disks of radius 8-64 (a quarter of the crop) plus
+        uniform gaps: the statistics of the 4096^2 workload, whose large holes the other
+        groups never show.
     Seeds start at `seed` (>= 10^4, disjoint from the evaluation workloads)."""
     import torch
     groups = []
@@ -65,6 +69,16 @@ def training_grids(n64: int, n128: int, seed: int = 10_000, device="cuda"):
             ms.append(_uniform_masks(per, 128, 128, p, seed + 200_000 + f, device))
             f += 1
         groups.append((torch.cat(zs)[:n128].contiguous(), torch.cat(ms)[:n128].contiguous()))
+    if n256:
+        zs, ms = [], []
+        f = 0
+        while sum(x.shape[0] for x in zs) < n256:
+            z = synth.wm_field_gpu(4096, 4096, 1.0, 32.0, seed + 300_000 + f, device=device)
+            zs.append(z.view(16, 256, 16, 256).permute(0, 2, 1, 3).reshape(256, 256, 256))
+            f += 1
+        z = torch.cat(zs)[:n256].contiguous()
+        m = np.stack([synth.mask_disks(256, 256, 0.5, seed + 400_000 + i) for i in range(n256)])
+        groups.append((z, torch.from_numpy(m).to(device).contiguous()))
     return groups
 
 
@@ -152,16 +166,19 @@ class WarmStartNet:
 def train(net: WarmStartNet, sets, steps: int, batch: int = 32, lr: float = 1e-3, seed: int = 0,
           log_every: int = 0, lr_final: float = 0.1):
     """Adam on random batches (drawn per step from one shape group, groups in proportion
-    to their size); cosine decay of the learning rate to lr * lr_final.  Returns the loss
-    of every step."""
+    to their number of sites; `batch` grids of 128^2 sites or the same number of sites in
+    other shapes); cosine decay of the learning rate to lr * lr_final.  Returns the loss of
+    every step."""
     import torch
     rng = np.random.Generator(np.random.PCG64(seed))
-    sizes = np.array([s.n for s in sets], np.float64)
+    sizes = np.array([s.n * s.z.shape[1] * s.z.shape[2] for s in sets], np.float64)
     prob = sizes / sizes.sum()
     losses = []
     for it in range(steps):
         s = sets[int(rng.choice(len(sets), p=prob))]
-        idx = np.sort(rng.choice(s.n, size=min(batch, s.n), replace=False))
+        # batches of about batch x 128^2 sites whatever the shape
+        bs = max(1, min(s.n, int(round(batch * 128 * 128 / (s.z.shape[1] * s.z.shape[2])))))
+        idx = np.sort(rng.choice(s.n, size=bs, replace=False))
         ti = torch.as_tensor(idx, device=s.z.device)
         z = s.z.index_select(0, ti).contiguous()
         m = s.mask.index_select(0, ti).contiguous()

@@ -38,12 +38,15 @@ def _from_bits(t):
     return no.from_bf16_bits(t.cpu().numpy().view(np.uint16))
 
 
-CONV_CASES = [  # B, H, W, Cin, Cout: ragged pixel tails, both N tile widths, several K chunks
-    (2, 20, 13, 32, 32),
-    (1, 9, 30, 96, 64),
-    (2, 16, 16, 64, 96),
-    (1, 7, 5, 32, 256),
-    (3, 1, 1, 32, 32),
+CONV_CASES = [  # B, H, W, Cin, Cout: ragged tile edges, every N tile width, both tile kinds
+    (2, 20, 13, 32, 32),     # halo tile (N <= 64, weights resident), one channel block
+    (2, 18, 20, 96, 32),     # halo tile, two channel blocks (the second half zero-padded)
+    (1, 16, 24, 64, 64),     # halo tile, N = 64
+    (1, 9, 30, 96, 64),      # general tile
+    (2, 16, 16, 64, 96),     # general tile, N = 96
+    (1, 7, 5, 32, 256),      # general tile, N = 256
+    (1, 6, 34, 128, 128),    # general tile, two channel blocks
+    (3, 1, 1, 32, 32),       # tiles mostly outside the image
 ]
 
 
