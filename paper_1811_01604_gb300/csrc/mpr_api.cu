@@ -363,8 +363,7 @@ SweepArgs sweep_args(const mpr_ctx* ctx, const Batch& b, bool use_ctl_a, double 
     A.half_qd_fixed = (float)(0.5 * kTwoPi * ctx->prm.q / a_fixed);
     A.skip_stopped = skip_stopped ? 1 : 0;
     A.or_on = ctx->prm.or_mode == MPR_OR_CONSERVING ? 1 : 0;
-    A.key0 = (uint32_t)ctx->prm.seed;
-    A.key1 = (uint32_t)(ctx->prm.seed >> 32);
+    A.rk = round_keys(ctx->prm.seed);
     return A;
 }
 
@@ -395,8 +394,7 @@ TileArgs tile_args(const mpr_ctx* ctx, const Batch& b, int mode, double a_fixed,
     T.half_qd_fixed = (float)(0.5 * kTwoPi * p.q / a_fixed);
     T.skip_stopped = relax ? 1 : 0;
     T.or_on = p.or_mode == MPR_OR_CONSERVING ? 1 : 0;
-    T.key0 = (uint32_t)p.seed;
-    T.key1 = (uint32_t)(p.seed >> 32);
+    T.rk = round_keys(p.seed);
     T.mode = mode;
     T.A_targ = p.A_targ;
     T.k_a = p.k_a;

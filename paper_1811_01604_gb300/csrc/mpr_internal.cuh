@@ -99,6 +99,24 @@ struct TileCnt {              // gap sites listed for one tile
     uint16_t _pad;
 };
 
+// Philox4x32-10 round keys (k + r * Weyl constant, r = 0..9) computed once on the host, so
+// the kernels XOR them in straight from the parameter bank instead of stepping the key
+// schedule for every site.
+struct RoundKeys {
+    uint32_t k0[10], k1[10];
+};
+inline RoundKeys round_keys(uint64_t seed) {
+    RoundKeys rk;
+    uint32_t a = (uint32_t)seed, b = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        rk.k0[r] = a;
+        rk.k1[r] = b;
+        a += 0x9E3779B9u;
+        b += 0xBB67AE85u;
+    }
+    return rk;
+}
+
 struct TileArgs {
     const EntryDesc* ents;
     float2* lat[2];           // the two lattice buffers (Ctl::cur selects the source)
@@ -120,7 +138,7 @@ struct TileArgs {
     float half_qd_fixed;
     int skip_stopped;
     int or_on;
-    uint32_t key0, key1;
+    RoundKeys rk;             // Philox round keys of the seed
     int mode;
     double A_targ, k_a;
     int n_f, n_fit, i_max;
@@ -145,7 +163,7 @@ struct SweepArgs {
     float half_qd_fixed;      // q * pi / a for the fixed window
     int skip_stopped;         // skip entries whose relaxation has ended
     int or_on;
-    uint32_t key0, key1;      // Philox key
+    RoundKeys rk;             // Philox round keys of the seed
 };
 
 
@@ -161,6 +179,18 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
                        (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// The same with precomputed round keys.
+__device__ __forceinline__ uint4 philox10(uint4 c, const RoundKeys& rk) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk.k0[r], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ rk.k1[r], (uint32_t)p0);
     }
     return c;
 }

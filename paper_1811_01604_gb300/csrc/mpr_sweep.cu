@@ -43,7 +43,7 @@ k_half_sweep(const SweepArgs A, const int color) {
             const float S = (nu.y + nd.y) + (nl.y + nr.y);
             float2 v = own[k];
             const uint32_t site = (uint32_t)y * (uint32_t)W + (uint32_t)(2 * j + s);
-            const uint4 rnd = philox10(make_uint4(site, sweep, chain, 0u), A.key0, A.key1);
+            const uint4 rnd = philox10(make_uint4(site, sweep, chain, 0u), A.rk);
             const float hq = (u24f(rnd.x) - 0.5f) * half_qd;
             bool accepted;
             dE += hybrid_update<TRIG>(v, C, S, hq, u24f(rnd.y), neg_inv_T, A.or_on, accepted);

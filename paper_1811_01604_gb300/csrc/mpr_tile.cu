@@ -329,7 +329,7 @@ k_tile_sweep(const TileArgs A) {
                 float2 v = own[r][q];
                 const int y = y0 - 2 + r, x = x0 + 2 * q - 4 + s;
                 const uint32_t site = (uint32_t)y * (uint32_t)W + (uint32_t)x;
-                const uint4 rnd = philox10(make_uint4(site, sweep, chain, 0u), A.key0, A.key1);
+                const uint4 rnd = philox10(make_uint4(site, sweep, chain, 0u), A.rk);
                 const float hq = (u24f(rnd.x) - 0.5f) * half_qd;
                 bool accepted;
                 const float d = hybrid_update<TRIG>(v, C, S, hq, u24f(rnd.y), neg_inv_T, A.or_on, accepted);
