@@ -151,12 +151,17 @@ constexpr int kHaloCopy = kHaloRows * 64;                  // 9216 B = 9 x 1024
 constexpr int kHaloStage = 3 * kHaloCopy;
 constexpr int kHaloStages = 5;
 constexpr int kHaloBmax = 80 * 1024;                       // resident weights at most
-template <int BN>
+// RES: the layer's weights resident (at most kHaloBmax); otherwise each stage also carries
+// the block's weights for the nine taps (9 x BN rows of 64 B).
+template <int BN, bool RES>
 struct Th {
     static constexpr int ACC_STRIDE = BN;
     static constexpr int TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;
-    static constexpr int A_OFF = kHaloBmax;
-    static constexpr int BAR_OFF = A_OFF + kHaloStages * kHaloStage;
+    static constexpr int B_STAGE = RES ? 0 : 9 * BN * 64;
+    static constexpr int STAGE = kHaloStage + B_STAGE;                 // multiple of 1024
+    static constexpr int STAGES = RES ? kHaloStages : (196 * 1024) / STAGE;
+    static constexpr int A_OFF = RES ? kHaloBmax : 0;
+    static constexpr int BAR_OFF = A_OFF + STAGES * STAGE;
     static constexpr int SMEM = BAR_OFF + 256 + 1024;
 };
 
@@ -417,16 +422,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tma(const __grid_constant_
     teardown(tmem, C::TMEM_COLS);
 }
 
-// Halo-tile convolution for N = BN in {32, 64} (maps: A box {64, 8, 18, 1}; B box {64, BN}).
-template <int BN>
+// Halo-tile convolution for N = BN in {32, 64} (maps: A box {32, 8, 18, 1}; B box {32, BN}).
+template <int BN, bool RES>
 __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant__ CUtensorMap mapA,
                                                            const __grid_constant__ CUtensorMap mapB,
                                                            const TcConv c, int* __restrict__ err) {
-    using C = Th<BN>;
+    using C = Th<BN, RES>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = saddr(smem);
-    const Bars B{sbase + C::BAR_OFF, kHaloStages};
+    const Bars B{sbase + C::BAR_OFF, C::STAGES};
     uint32_t* tmem_slot = B.slot(smem + C::BAR_OFF);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -440,8 +445,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
     if (warp == kProdWarp) {
         if (lane == 0) {
             // the layer's weights, once: chunk kc = tap * KB + cb (32 wide) at kc * BN * 64
-            mbar_expect_tx(B.bres(), (uint32_t)(9 * KB * BN * 64));
-            for (int kc = 0; kc < 9 * KB; ++kc) tma_load_2d(sbase + kc * BN * 64, &mapB, B.bres(), kc * 32, 0);
+            if (RES) {
+                mbar_expect_tx(B.bres(), (uint32_t)(9 * KB * BN * 64));
+                for (int kc = 0; kc < 9 * KB; ++kc) tma_load_2d(sbase + kc * BN * 64, &mapB, B.bres(), kc * 32, 0);
+            }
             long long it = 0;
             for (long long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
                 long long q = t;
@@ -450,17 +457,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
                 const int b = (int)(q / TYn);
                 bool ok = true;
                 for (int cb = 0; cb < KB; ++cb, ++it) {
-                    const int s = (int)(it % kHaloStages);
-                    if (it >= kHaloStages &&
-                        !mbar_wait(B.empty(s), (uint32_t)((it / kHaloStages) - 1) & 1u, err, abort_flag)) {
+                    const int s = (int)(it % C::STAGES);
+                    if (it >= C::STAGES &&
+                        !mbar_wait(B.empty(s), (uint32_t)((it / C::STAGES) - 1) & 1u, err, abort_flag)) {
                         ok = false;
                         break;
                     }
-                    const uint32_t sa = sbase + C::A_OFF + s * kHaloStage;
-                    mbar_expect_tx(B.full(s), kHaloStage);
+                    const uint32_t sa = sbase + C::A_OFF + s * C::STAGE;
+                    mbar_expect_tx(B.full(s), C::STAGE);
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx)
                         tma_load_4d(sa + dx * kHaloCopy, &mapA, B.full(s), cb * 32, x0 + dx - 1, y0 - 1, b);
+                    if (!RES)                              // this block's weights of the nine taps
+                        for (int tap = 0; tap < 9; ++tap)
+                            tma_load_2d(sa + kHaloStage + tap * BN * 64, &mapB, B.full(s), tap * c.C + cb * 32, 0);
                 }
                 if (!ok) break;
             }
@@ -470,25 +480,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_bf16(kBM, BN);
             long long it = 0, tc = 0;
-            bool ok = mbar_wait(B.bres(), 0, err, abort_flag);
+            bool ok = !RES || mbar_wait(B.bres(), 0, err, abort_flag);
             for (long long t = blockIdx.x; ok && t < ntiles && !*abort_flag; t += gridDim.x, ++tc) {
                 const int buf = (int)(tc & 1);
                 if (tc >= 2 && !mbar_wait(B.acce(buf), (uint32_t)((tc >> 1) - 1) & 1u, err, abort_flag)) break;
                 tc_fence_after();
                 const uint32_t d = tmem + buf * C::ACC_STRIDE;
                 for (int cb = 0; cb < KB; ++cb, ++it) {
-                    const int s = (int)(it % kHaloStages);
-                    if (!mbar_wait(B.full(s), (uint32_t)(it / kHaloStages) & 1u, err, abort_flag)) {
+                    const int s = (int)(it % C::STAGES);
+                    if (!mbar_wait(B.full(s), (uint32_t)(it / C::STAGES) & 1u, err, abort_flag)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sa = sbase + C::A_OFF + s * kHaloStage;
+                    const uint32_t sa = sbase + C::A_OFF + s * C::STAGE;
 #pragma unroll 1
                     for (int tap = 0; tap < 9; ++tap) {
                         const int dy = tap / 3, dx = tap - dy * 3;
                         const uint32_t a0 = sa + dx * kHaloCopy + dy * 512;
-                        const uint32_t b0 = sbase + (tap * KB + cb) * BN * 64;
+                        const uint32_t b0 = RES ? sbase + (tap * KB + cb) * BN * 64 : sa + kHaloStage + tap * BN * 64;
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk)
                             tc_mma(d, sdesc64(a0 + kk * 32), sdesc64(b0 + kk * 32), idesc, (cb | tap | kk) != 0);
@@ -584,11 +594,12 @@ cudaError_t launch_tma(const TcConv& c, int* err, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int BN>
+template <int BN, bool RES>
 cudaError_t launch_halo(const TcConv& c, int* err, cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv_halo<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Th<BN>::SMEM);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_conv_halo<BN, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize, Th<BN, RES>::SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -597,7 +608,7 @@ cudaError_t launch_halo(const TcConv& c, int* err, cudaStream_t st) {
     const long long tiles = (long long)c.B * ((c.H + kHY - 1) / kHY) * ((c.W + kHX - 1) / kHX);
     const int grid = (int)(tiles < num_sms() ? tiles : num_sms());
     if (grid <= 0) return cudaSuccess;
-    k_conv_halo<BN><<<grid, kThreads, Th<BN>::SMEM, st>>>(ma, mb, c, err);
+    k_conv_halo<BN, RES><<<grid, kThreads, Th<BN, RES>::SMEM, st>>>(ma, mb, c, err);
     return cudaGetLastError();
 }
 
@@ -605,9 +616,11 @@ cudaError_t launch_halo(const TcConv& c, int* err, cudaStream_t st) {
 
 int tc_kt(int C) { return (C + 63) / 64 * 64; }
 
-static bool halo_fits(int C, int N) { return (N == 32 || N == 64) && C % 32 == 0 && 9LL * C * N * 2 <= kHaloBmax; }
+// halo tiles: N in {32, 64} and whole 32-channel blocks; weights resident when they fit
+static bool halo_ok(int C, int N) { return (N == 32 || N == 64) && C % 32 == 0; }
+static bool halo_resident(int C, int N) { return halo_ok(C, N) && 9LL * C * N * 2 <= kHaloBmax; }
 
-int tc_layer_kt(int C, int N) { return halo_fits(C, N) ? C : tc_kt(C); }
+int tc_layer_kt(int C, int N) { return halo_ok(C, N) ? C : tc_kt(C); }
 
 cudaError_t tc_weights(const bf16* w, int Cin, int Cout, int flip, bf16* wt, cudaStream_t st) {
     const int Kt = flip ? tc_layer_kt(Cout, Cin) : tc_layer_kt(Cin, Cout);
@@ -626,7 +639,8 @@ cudaError_t conv3x3_tma(const TcConv& c, int* err, cudaStream_t st) {
     if (!tc_supported(c.C, c.N) || c.B < 1 || c.H < 1 || c.W < 1) return cudaErrorInvalidValue;
     if (c.out2 && (c.ld2 % 8 || c.off2 % 8)) return cudaErrorInvalidValue;
     if (c.pool && (!c.out || c.H % 2 || c.W % 2)) return cudaErrorInvalidValue;
-    if (halo_fits(c.C, c.N)) return c.N == 32 ? launch_halo<32>(c, err, st) : launch_halo<64>(c, err, st);
+    if (halo_resident(c.C, c.N)) return c.N == 32 ? launch_halo<32, true>(c, err, st) : launch_halo<64, true>(c, err, st);
+    if (halo_ok(c.C, c.N)) return c.N == 32 ? launch_halo<32, false>(c, err, st) : launch_halo<64, false>(c, err, st);
     switch (c.N) {
         case 32: return launch_tma<32>(c, err, st);
         case 64: return launch_tma<64>(c, err, st);

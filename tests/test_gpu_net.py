@@ -42,6 +42,8 @@ CONV_CASES = [  # B, H, W, Cin, Cout: ragged tile edges, every N tile width, bot
     (2, 20, 13, 32, 32),     # halo tile (N <= 64, weights resident), one channel block
     (2, 18, 20, 96, 32),     # halo tile, two channel blocks (the second half zero-padded)
     (1, 16, 24, 64, 64),     # halo tile, N = 64
+    (1, 12, 20, 192, 64),    # halo tile, weights streamed per channel block (N = 64)
+    (2, 10, 16, 192, 32),    # halo tile, weights streamed per channel block (N = 32)
     (1, 9, 30, 96, 64),      # general tile
     (2, 16, 16, 64, 96),     # general tile, N = 96
     (1, 7, 5, 32, 256),      # general tile, N = 256
