@@ -39,6 +39,19 @@ L = 4096
 M = 100
 
 
+def reduce_over_ranks(times_ms, updates, dist=None, device="cpu"):
+    """Whole-job numbers of a weak-scaling run: the slowest rank's times (every rank filled
+    its own map, so the job ends when the last one does) and the sum of the site updates of
+    all ranks.  dist: torch.distributed (initialised) or None for one process."""
+    import torch
+    t = torch.tensor([float(x) for x in times_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([float(x) for x in updates], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return t.tolist(), u.tolist()
+
+
 def make_inputs(seed_offset: int):
     from paper_1811_01604_gb300 import synth
     z = synth.wm_field(L, 1.0, 32.0, seed=3 + seed_offset)
@@ -565,13 +578,8 @@ def main():
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     achieved = bytes_per_launch / (sweep_ms * 1e-3) / 1e9
 
-    times = torch.tensor([dev_ms, e2e_ms], dtype=torch.float64, device=dev)
-    ups = torch.tensor([float(dev_updates), float(e2e_updates)], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(times, op=dist.ReduceOp.MAX)
-        dist.all_reduce(ups, op=dist.ReduceOp.SUM)
-    dev_ms, e2e_ms = times.tolist()
-    dev_updates, e2e_updates = ups.tolist()
+    (dev_ms, e2e_ms), (dev_updates, e2e_updates) = reduce_over_ranks(
+        [dev_ms, e2e_ms], [dev_updates, e2e_updates], dist, dev)
 
     if rank == 0:
         line = {
