@@ -78,8 +78,8 @@ struct Batch {
     TileCnt* d_cnts = nullptr;
     uint16_t* d_lists = nullptr;
     float* d_tacc = nullptr;
-    double* d_tpart_dH = nullptr;
-    unsigned* d_tpart_na = nullptr;
+    unsigned long long* d_gsum = nullptr;   // per grid: fixed-point energy change, acceptance count
+    unsigned* d_sched = nullptr;            // tile counter of the persistent sweep
     unsigned* d_ticket = nullptr;
     CUtensorMap* d_maps = nullptr;
     int* d_err = nullptr;
@@ -163,8 +163,8 @@ void batch_free(Batch& b) {
     cudaFree(b.d_cnts);
     cudaFree(b.d_lists);
     cudaFree(b.d_tacc);
-    cudaFree(b.d_tpart_dH);
-    cudaFree(b.d_tpart_na);
+    cudaFree(b.d_gsum);
+    cudaFree(b.d_sched);
     cudaFree(b.d_ticket);
     cudaFree(b.d_maps);
     cudaFree(b.d_err);
@@ -181,11 +181,11 @@ mpr_status build_tiles(mpr_ctx* ctx, Batch& b, int cfg) {
     cudaFree(b.d_cnts);
     cudaFree(b.d_lists);
     cudaFree(b.d_tacc);
-    cudaFree(b.d_tpart_dH);
-    cudaFree(b.d_tpart_na);
+    cudaFree(b.d_gsum);
+    cudaFree(b.d_sched);
     cudaFree(b.d_ticket);
     b.d_tiles = nullptr; b.d_cnts = nullptr; b.d_lists = nullptr; b.d_tacc = nullptr;
-    b.d_tpart_dH = nullptr; b.d_tpart_na = nullptr; b.d_ticket = nullptr;
+    b.d_gsum = nullptr; b.d_sched = nullptr; b.d_ticket = nullptr;
     for (auto& kv : b.graphs) cudaGraphExecDestroy(kv.second);
     b.graphs.clear();
     std::vector<TileDesc> tiles;          // per grid ceil(H/th) x ceil(W/tw), row-major
@@ -203,10 +203,10 @@ mpr_status build_tiles(mpr_ctx* ctx, Batch& b, int cfg) {
     CU(dalloc(&b.d_cnts, tiles.size()));
     CU(dalloc(&b.d_lists, tiles.size() * (size_t)g.list));
     CU(dalloc(&b.d_tacc, tiles.size() * (size_t)g.acc));
-    CU(dalloc(&b.d_tpart_dH, tiles.size()));
-    CU(dalloc(&b.d_tpart_na, tiles.size()));
-    CU(cudaMemsetAsync(b.d_tpart_dH, 0, sizeof(double) * tiles.size(), st));   // slots that never
-    CU(cudaMemsetAsync(b.d_tpart_na, 0, sizeof(unsigned) * tiles.size(), st)); // end a run stay 0
+    CU(dalloc(&b.d_gsum, (size_t)2 * b.n_ent));
+    CU(cudaMemsetAsync(b.d_gsum, 0, sizeof(unsigned long long) * 2 * b.n_ent, st));
+    CU(dalloc(&b.d_sched, 2));
+    CU(cudaMemsetAsync(b.d_sched, 0, sizeof(unsigned) * 2, st));
     CU(dalloc(&b.d_ticket, (size_t)b.n_ent));
     CU(cudaMemsetAsync(b.d_ticket, 0, sizeof(unsigned) * b.n_ent, st));
     CU(launch_tile_lists(cfg, b.d_tiles, b.ntiles, b.d_ents, b.mask_base, b.all_free, b.d_lists,
@@ -383,9 +383,9 @@ TileArgs tile_args(const mpr_ctx* ctx, const Batch& b, int mode, double a_fixed,
     T.lists = b.d_lists;
     T.acc = acc ? b.d_tacc : nullptr;
     T.ctl = b.d_ctl;
-    T.part_dH = b.d_tpart_dH;
-    T.part_na = b.d_tpart_na;
+    T.gsum = b.d_gsum;
     T.ticket = b.d_ticket;
+    T.sched = b.d_sched;
     T.ehist = b.d_ehist;
     T.ehist_stride = b.ehist_stride;
     T.ntiles = b.ntiles;

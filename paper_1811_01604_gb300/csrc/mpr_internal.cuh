@@ -127,9 +127,9 @@ struct TileArgs {
     const uint16_t* lists;
     float* acc;               // per-tile accumulators, or nullptr
     Ctl* ctl;
-    double* part_dH;          // one per tile
-    unsigned* part_na;
+    unsigned long long* gsum; // per grid: energy change (fixed point, 2^-28) and acceptance count
     unsigned* ticket;         // one per grid, zero between sweeps
+    unsigned* sched;          // tile counter and blocks-done counter, zero between launches
     double* ehist;
     int ehist_stride;
     int ntiles;
@@ -242,27 +242,32 @@ enum { TRIG_ACCURATE = 0, TRIG_FAST = 1 };
 //   C, S     local field: sums of the neighbours' cos/sin
 //   hq       half the proposal rotation, q * 2 pi (u - 1/2) / a / 2
 //   r        acceptance uniform
-// Returns the accepted energy change (0 if rejected) and writes the new vector.
+//   kx       -1/T (TRIG_ACCURATE: the test uses expf) or -log2(e)/T (TRIG_FAST: ex2.approx)
+// Returns the accepted energy change (0 if rejected) and writes the new vector.  Written
+// without branches: both outcomes of each test are computed and selected.
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 template <int TRIG>
 __device__ __forceinline__ float hybrid_update(float2& v, float C, float S, float hq, float r,
-                                               float neg_inv_T, int or_on, bool& accepted) {
+                                               float kx, int or_on, bool& accepted) {
     float c = v.x, s = v.y;
     // R cos(theta - psi) and R sin(theta - psi), psi the direction of the field
     const float along = fmaf(c, C, s * S);
-    float perp = fmaf(s, C, -(c * S));
+    const float perp0 = fmaf(s, C, -(c * S));
     // Eq. 6 (energy-conserving reading): reflect theta about psi; keep it only if the
-    // image stays in [0, pi), i.e. sin >= 0 (the point theta = pi is excluded).
+    // image stays in [0, pi), i.e. sin > 0 or theta = 0 (the point theta = pi is excluded).
+    // No reflection when the field vanishes (R^2 <= 1e-12).
     const float R2 = fmaf(C, C, S * S);
-    if (or_on && R2 > 1e-12f) {
-        // reflection factor 2 (v.n)/|n|^2; a 2-ulp quotient moves the image by ~2e-7 rad
-        const float f = __fdividef(2.0f * along, R2);
-        const float cr = fmaf(f, C, -c), sr = fmaf(f, S, -s);
-        if (sr > 0.0f || (sr == 0.0f && cr > 0.0f)) {
-            c = cr;
-            s = sr;
-            perp = -perp;          // the reflection keeps `along` and flips `perp`
-        }
-    }
+    // reflection factor 2 (v.n)/|n|^2; a 2-ulp quotient moves the image by ~2e-7 rad
+    const float f = __fdividef(2.0f * along, R2);
+    const float cr = fmaf(f, C, -c), sr = fmaf(f, S, -s);
+    const bool refl = or_on && R2 > 1e-12f && (sr > 0.0f || (sr == 0.0f && cr > 0.0f));
+    c = refl ? cr : c;
+    s = refl ? sr : s;
+    const float perp = refl ? -perp0 : perp0;     // the reflection keeps `along`, flips `perp`
     // proposal: rotate by 2*hq (steps 2-3); 1 - cos and sin of the rotation from the half angle
     float sh, ch;
     if (TRIG == TRIG_FAST) {
@@ -273,27 +278,29 @@ __device__ __forceinline__ float hybrid_update(float2& v, float C, float S, floa
     const float sn = 2.0f * sh * ch;
     const float hh = 2.0f * sh * sh;
     // step 4: dH = R [cos(theta - psi) - cos(theta + 2hq - psi)]
-    float dH = fmaf(hh, along, sn * perp);
-    float c2 = c - fmaf(c, hh, s * sn);
-    float s2 = s - fmaf(s, hh, -(c * sn));
+    const float dH0 = fmaf(hh, along, sn * perp);
+    const float c20 = c - fmaf(c, hh, s * sn);
+    const float s20 = s - fmaf(s, hh, -(c * sn));
     // modulo 2 pi in phi is a half turn in theta: negate the vector, dH -> 2 along - dH
-    if (s2 < 0.0f || (s2 == 0.0f && c2 < 0.0f)) {
-        c2 = -c2;
-        s2 = -s2;
-        dH = 2.0f * along - dH;
-    }
+    const bool wrap = s20 < 0.0f || (s20 == 0.0f && c20 < 0.0f);
+    const float c2 = wrap ? -c20 : c20;
+    const float s2 = wrap ? -s20 : s20;
+    const float dH = wrap ? 2.0f * along - dH0 : dH0;
     // steps 5-6: accept if min(1, exp(-dH/T)) > r
-    const float x = dH * neg_inv_T;
-    const float ap = (TRIG == TRIG_FAST) ? __expf(x) : expf(x);
+    const float ap = (TRIG == TRIG_FAST) ? ex2_approx(dH * kx) : expf(dH * kx);
     accepted = (dH <= 0.0f) || (ap > r);
-    if (accepted) {
-        c = c2;
-        s = s2;
-    }
+    c = accepted ? c2 : c;
+    s = accepted ? s2 : s;
     // one Newton step back to unit length (rounding drift of reflections and rotations)
     const float g = fmaf(-0.5f, fmaf(c, c, s * s), 1.5f);
     v = make_float2(c * g, s * g);
     return accepted ? dH : 0.0f;
+}
+
+// The exponent scale kx of hybrid_update for a temperature given as -1/T.
+template <int TRIG>
+__device__ __forceinline__ float accept_scale(float neg_inv_T) {
+    return TRIG == TRIG_FAST ? neg_inv_T * 1.4426950408889634f : neg_inv_T;
 }
 
 // ---------------------------------------------------------------- Algorithm 2 control

@@ -17,7 +17,7 @@ k_half_sweep(const SweepArgs A, const int color) {
     const Ctl* ctl = A.ctl + w.entry;
     if (A.skip_stopped && ctl->stop) return;
     const float half_qd = A.use_ctl_a ? (float)(0.5 * kTwoPi * 0.5 / ctl->a) : A.half_qd_fixed;
-    const float neg_inv_T = (float)(-1.0 / ctl->T);
+    const float kx = accept_scale<TRIG>((float)(-1.0 / ctl->T));
     const uint32_t sweep = ctl->sweep;
     const int n = color ? E->ngap[1] : E->ngap[0], pitch = E->pitch, W = E->W;
     const uint32_t chain = E->chain;
@@ -46,7 +46,7 @@ k_half_sweep(const SweepArgs A, const int color) {
             const uint4 rnd = philox10(make_uint4(site, sweep, chain, 0u), A.rk);
             const float hq = (u24f(rnd.x) - 0.5f) * half_qd;
             bool accepted;
-            dE += hybrid_update<TRIG>(v, C, S, hq, u24f(rnd.y), neg_inv_T, A.or_on, accepted);
+            dE += hybrid_update<TRIG>(v, C, S, hq, u24f(rnd.y), kx, A.or_on, accepted);
             nacc += accepted ? 1u : 0u;
             own[k] = v;
             if (ACC) acc[g] += atan2f(v.y, v.x);

@@ -154,6 +154,18 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
         " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity), "r"(100000u) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_try(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < 3000u; ++i)
+        if (mbar_try(bar, parity)) return true;
+    return false;
+}
 // Bounded wait: gives up after ~0.3 s (2^24 polls with a 20 ns pause) and reports false.
 // (Polling measured faster here than the hardware-suspended try_wait.)
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
@@ -164,22 +176,40 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
-// Per-tile parameters staged in shared memory by the issuing thread.
-struct TileParams {
-    long long pl0, pl1;
-    int y0, x0, W, H, pitch, e, cur, tile0, ntiles, t;
-    uint32_t chain, sweep;
-    float half_qd, neg_inv_T;
-    TileCnt cnt;
+// Per-tile parameters staged in shared memory by the issuing thread, in 16-byte groups
+// so that each thread picks up what it needs with a few vector loads.
+struct __align__(16) TileParams {
+    int t, y0, x0, W;                     // tile, origin, grid width
+    uint32_t chain, sweep;                // Philox counter words 2 and 1
+    float half_qd, neg_inv_T;             // proposal half-angle scale, -1/T
+    int nA_int, nA_ring, nB, e;           // list counts, grid
+    int ntiles, H, pitch, cur;            // grid's tile count and height, row pitch, source buffer
+    long long pl0, pl1;                   // plane offsets of the grid in the lattice buffers
 };
 
-// Persistent fused sweep: each block walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...
-// through STAGES shared-memory stages.  Thread 0 issues the TMA copies (region box of
-// both planes plus the tile's gap list, one mbarrier per stage) up to STAGES - 1 tiles
-// ahead of the tile being updated.
+// Energy changes are summed across the tiles of a grid in 64-bit fixed point (2^-28 units):
+// integer addition is associative, so the total does not depend on which block updated
+// which tile or in which order.  |dH| <= 8 per site keeps any grid of < 2^31 sites far
+// from overflow.
+constexpr float kFixScale = 268435456.0f;             // 2^28
+constexpr double kFixUnit = 1.0 / 268435456.0;
+
+// Persistent fused sweep.  Blocks take tiles from a global counter (the last block to
+// leave resets it for the next launch), so faster blocks take more tiles and no block
+// idles while others finish.  Thread 0 stages a tile: a TMA box of both colour planes
+// plus the bulk-copied gap list, completing on the stage's mbarrier.  With two stages the
+// next tile is staged as soon as the current one is in shared memory, a whole tile
+// ahead; with one stage, after the previous tile has been written back.
+// Per tile: every warp adds its energy change and acceptance count to the grid's
+// fixed-point totals; thread 0 then takes the grid's ticket, and the block that
+// completes a grid's tiles runs the grid's Algorithm 2 control step from the totals.
+// The interior rows of both planes go back to the other lattice buffer as 16-byte
+// stores, which frees the stage at once.
 template <int TH, int TW, int TRIG, bool ACC, int NT, int STAGES, int MB>
 __global__ void __launch_bounds__(NT, MB)
 k_tile_sweep(const TileArgs A) {
+    static_assert(STAGES == 1 || STAGES == 2, "one or two stages");
+    static_assert(TW % 8 == 0, "write-back in 16-byte vectors");
     using G = Geo<TH, TW>;
     extern __shared__ __align__(128) unsigned char dsm[];
     float2(*stage)[2][G::RH][G::RW] = reinterpret_cast<float2(*)[2][G::RH][G::RW]>(dsm);
@@ -187,76 +217,68 @@ k_tile_sweep(const TileArgs A) {
         reinterpret_cast<uint16_t(*)[G::LIST]>(dsm + STAGES * 2 * G::RH * G::RW * sizeof(float2));
     __shared__ TileParams sp[STAGES];
     __shared__ __align__(8) uint64_t bar[STAGES];
-    __shared__ float s_dE[NT / 32];
-    __shared__ unsigned s_na[NT / 32];
-    __shared__ int s_last;                                     // this tile ends a run
-    __shared__ int s_runlen;                                   // tiles in the current run
-    __shared__ int s_grid_done;                                // this block completed the grid
     __shared__ int s_fail;
-    __shared__ double s_sum[NT];
-    __shared__ unsigned long long s_cnt[NT];
+    __shared__ TileParams cp_;                                 // thread 0's grid cache
+    __shared__ const CUtensorMap* cmap;
+    __shared__ int cstop;
     constexpr uint32_t kBytes = 2u * G::RH * G::RW * sizeof(float2);
+    const int lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < STAGES; ++i) mbar_init(&bar[i], 1);
         fence_barrier_init();
         s_fail = 0;
-        s_runlen = 0;
     }
     __syncthreads();
 
-    // Thread 0 only.  Tile descriptors are one 16-byte load; a grid's parameters do not
-    // change during a launch, so they are reloaded only when the grid changes.
-    __shared__ TileParams cp_;                                 // thread 0's cache
-    __shared__ const CUtensorMap* cmap;
-    __shared__ int cstop;
-    int ce = -1;
+    // Thread 0 only: the next tile index taken from the counter and its descriptor
+    // (fetched a tile ahead, so that staging never waits on a global load), and the
+    // parameters of the grid being staged (constant during a launch; reloaded only when
+    // the grid changes -- tiles are taken in increasing order and a grid's are contiguous).
+    int ce = -1, nxt = A.ntiles;
+    __shared__ TileDesc dnext;
+    if (threadIdx.x == 0) {
+        nxt = (int)atomicAdd(A.sched, 1u);
+        if (nxt < A.ntiles) dnext = A.tiles[nxt];
+    }
     auto load_entry = [&](int e) {
         const EntryDesc& E = A.ents[e];
         const Ctl& c = A.ctl[e];
-        cp_.pl0 = E.plane[0];
-        cp_.pl1 = E.plane[1];
         cp_.W = E.W;
         cp_.H = E.H;
-        cp_.pitch = E.pitch;
-        cp_.e = e;
-        cp_.cur = c.cur;
-        cp_.tile0 = E.tile0;
-        cp_.ntiles = E.ntiles;
         cp_.chain = E.chain;
         cp_.sweep = c.sweep;
         cp_.half_qd = A.use_ctl_a ? c.half_qd : A.half_qd_fixed;
         cp_.neg_inv_T = c.neg_inv_T;
+        cp_.e = e;
+        cp_.ntiles = E.ntiles;
+        cp_.pl0 = E.plane[0];
+        cp_.pl1 = E.plane[1];
+        cp_.pitch = E.pitch;
+        cp_.cur = c.cur;
         cstop = A.skip_stopped ? c.stop : 0;
         cmap = A.maps + 2 * e + c.cur;
         ce = e;
     };
-    // thread 0's issue cursor and the descriptor of the tile at the cursor (prefetched, so
-    // that staging a tile never waits on a global load)
-    int next = blockIdx.x;
-    TileDesc dnext;
-    if (threadIdx.x == 0 && next < A.ntiles) dnext = A.tiles[next];
-    // stages the next tile of this block whose grid is still relaxing into stage st
+    // stages the next tile whose grid is still relaxing into stage st, or marks the stage
+    // empty (t = ntiles) when the counter is exhausted
     auto issue = [&](int st) {
         TileParams& P = sp[st];
         for (;;) {
-            if (next >= A.ntiles) { P.t = A.ntiles; return; }
+            if (nxt >= A.ntiles) { P.t = A.ntiles; return; }
             const TileDesc d = dnext;
-            const int cur_t = next;
-            next += gridDim.x;
-            if (next < A.ntiles) dnext = A.tiles[next];
+            const int cur_t = nxt;
+            nxt = (int)atomicAdd(A.sched, 1u);
+            if (nxt < A.ntiles) dnext = A.tiles[nxt];
             if (d.entry != ce) load_entry(d.entry);
             if (!cstop) {
+                cp_.t = cur_t;
+                cp_.y0 = d.y0;
+                cp_.x0 = d.x0;
+                cp_.nA_int = d.nA_int;
+                cp_.nA_ring = d.nA_ring;
+                cp_.nB = d.nB;
                 P = cp_;
-                P.t = cur_t;
-                P.y0 = d.y0;
-                P.x0 = d.x0;
-                TileCnt n;
-                n.nA_int = (uint16_t)d.nA_int;
-                n.nA_ring = (uint16_t)d.nA_ring;
-                n.nB = (uint16_t)d.nB;
-                n._pad = 0;
-                P.cnt = n;
                 const uint32_t lbytes = ((uint32_t)(d.nA_int + d.nA_ring + d.nB) * 2u + 15u) & ~15u;
                 mbar_expect_tx(&bar[st], kBytes + lbytes);
                 tma_load_3d(&stage[st][0][0][0], cmap, &bar[st], d.x0 >> 1, d.y0 - 1, 0);
@@ -267,54 +289,48 @@ k_tile_sweep(const TileArgs A) {
         }
     };
 
-    if (threadIdx.x == 0)
-        for (int i = 0; i < STAGES - 1; ++i) issue(i);
-    // energy change and acceptance count of the block's current run of tiles of one grid
-    float dE = 0.0f;
-    unsigned nacc = 0;
+    if (threadIdx.x == 0) issue(0);
     for (int it = 0;; ++it) {
-        const int st = it % STAGES;
-        if (threadIdx.x < 32) {
-            bulk_wait_read();                           // stores of the freed stage have read it
-            __syncwarp();
-            if (threadIdx.x == 0) issue((it + STAGES - 1) % STAGES);   // the stage freed last iteration
+        const int st = STAGES == 1 ? 0 : (it & 1);
+        const uint32_t parity = (uint32_t)(STAGES == 1 ? it : (it >> 1)) & 1u;
+        if (STAGES == 1 && it > 0) {
+            __syncthreads();                                      // B0: the write-back has read the stage
+            if (threadIdx.x == 0) issue(0);
         }
-        __syncthreads();                                        // sp[st].t visible
-        const int t = sp[st].t;
-        if (t >= A.ntiles) {
-            if (threadIdx.x < 32) bulk_wait_all();
-            break;
-        }
-        if (!mbar_wait(&bar[st], (uint32_t)(it / STAGES) & 1u)) {
-            if (threadIdx.x == 0) atomicExch(A.err, 1);
+        if (threadIdx.x == 0 && sp[st].t < A.ntiles && !mbar_wait_try(&bar[st], parity)) {
+            atomicExch(A.err, 1);
             s_fail = 1;
         }
-        __syncthreads();
+        __syncthreads();                                          // B1: the tile is in stage st
+        const int4 g0 = *reinterpret_cast<const int4*>(&sp[st].t);
+        const int t = g0.x;
+        if (t >= A.ntiles) break;
         if (s_fail) {
-            // let copies still in flight land before the block's shared memory goes away
-            for (int k = 1; k < STAGES; ++k) {
-                const int j = it + k;
-                if (sp[j % STAGES].t < A.ntiles) mbar_wait(&bar[j % STAGES], (uint32_t)(j / STAGES) & 1u);
-            }
-            return;
+            // give the late copy a second bounded wait to land before the block's shared
+            // memory goes away (no other copy is in flight at B1), then leave
+            if (threadIdx.x == 0) (void)mbar_wait_try(&bar[st], parity);
+            break;
         }
+        (void)mbar_test(&bar[st], parity);                        // each thread acquires the copy
+        // stage st ^ 1 was written back before B1: stage the next tile into it now
+        if (STAGES == 2 && threadIdx.x == 0) issue(st ^ 1);
+        const int y0 = g0.y, x0 = g0.z, W = g0.w;
+        const int4 g1 = *reinterpret_cast<const int4*>(&sp[st].chain);
+        const int4 g2 = *reinterpret_cast<const int4*>(&sp[st].nA_int);
+        const uint32_t chain = (uint32_t)g1.x, sweep = (uint32_t)g1.y;
+        const float half_qd = __int_as_float(g1.z), kx = accept_scale<TRIG>(__int_as_float(g1.w));
+        const int nA_int = g2.x, nA = g2.x + g2.y, nB = g2.z, e = g2.w;
         float2(*sm)[G::RH][G::RW] = stage[st];
-        const TileParams& P = sp[st];
-        const int W = P.W, H = P.H, pitch = P.pitch;
-        const int y0 = P.y0, x0 = P.x0;
-        const uint32_t chain = P.chain, sweep = P.sweep;
-        const float half_qd = P.half_qd, neg_inv_T = P.neg_inv_T;
-        float2* __restrict__ dst = P.cur ? A.lat[0] : A.lat[1];
-        const TileCnt cnt = P.cnt;
         const uint16_t* list = slist[st];
         float* __restrict__ acc = ACC ? A.acc + (long long)t * G::ACC : nullptr;
 
         // colour A on the tile and its ring, then colour B on the tile
-        const int nA = cnt.nA_int + cnt.nA_ring;
+        float dE = 0.0f;
+        unsigned nacc = 0;
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
             const int c = pass;                           // colour being updated
-            const int n = pass ? cnt.nB : nA;
+            const int n = pass ? nB : nA;
             const uint16_t* lst = pass ? list + nA : list;
             float2(*own)[G::RW] = sm[c];
             float2(*oth)[G::RW] = sm[c ^ 1];
@@ -332,100 +348,70 @@ k_tile_sweep(const TileArgs A) {
                 const uint4 rnd = philox10(make_uint4(site, sweep, chain, 0u), A.rk);
                 const float hq = (u24f(rnd.x) - 0.5f) * half_qd;
                 bool accepted;
-                const float d = hybrid_update<TRIG>(v, C, S, hq, u24f(rnd.y), neg_inv_T, A.or_on, accepted);
+                const float d = hybrid_update<TRIG>(v, C, S, hq, u24f(rnd.y), kx, A.or_on, accepted);
                 own[r][q] = v;
-                if (pass || k < cnt.nA_int) {             // the ring belongs to other tiles
+                if (pass || k < nA_int) {                 // the ring belongs to other tiles
                     dE += d;
                     nacc += accepted ? 1u : 0u;
-                    if (ACC) acc[pass ? cnt.nA_int + k : k] += atan2f(v.y, v.x);
+                    if (ACC) acc[pass ? nA_int + k : k] += atan2f(v.y, v.x);
                 }
             }
-            if (pass == 0) __syncthreads();
+            if (pass == 0) __syncthreads();               // B2: colour A done
         }
-        fence_proxy_async_smem();                     // every writer orders its stores for the bulk copies
-        __syncthreads();
-        // interior rows of both colours to the other buffer (samples included): one bulk
-        // copy per row, issued by the lanes of warp 0 (rows beyond the grid are skipped)
-        if (threadIdx.x < 32) {
-            const int rows = min(TH, H - y0);
-            for (int i = threadIdx.x; i < 2 * rows; i += 32) {
-                const int c = i / rows, ri = i - c * rows;
-                const int pc = (x0 >> 1) + 2;
-                const int ncol = min(TW / 2, pitch - pc) & ~1;          // whole 16-byte pairs
-                if (ncol > 0)
-                    bulk_store(dst + (c ? P.pl1 : P.pl0) + (long long)(y0 + ri + 1) * pitch + pc,
-                               &sm[c][ri + 2][2], (uint32_t)ncol * 8u);
-            }
-            bulk_commit();
+        // the warp's share of the tile's energy change and acceptance count
+        dE = warp_sum(dE);
+        nacc = warp_sum(nacc);
+        if (lane == 0) {
+            atomicAdd(A.gsum + 2 * e, (unsigned long long)__float2ll_rn(dE * kFixScale));
+            if (nacc) atomicAdd(A.gsum + 2 * e + 1, (unsigned long long)nacc);
         }
-        // Partials are flushed once per run of consecutive tiles of one grid: at the end of
-        // the run the block writes its sums into the slot of the run's last tile (the other
-        // slots of the grid stay zero) and takes one ticket per tile of the run; the block
-        // that completes the grid's count adds the slots in tile order and runs the grid's
-        // control step.
+        fence_proxy_async_smem();                     // this thread's stage writes before the next copy into it
+        __syncthreads();                              // B3: colour B done, partials issued
+        const int4 g3 = *reinterpret_cast<const int4*>(&sp[st].ntiles);
         if (threadIdx.x == 0) {
-            // the next tile this block updates: already staged (STAGES > 1) or at the cursor
-            int ne;
-            if (STAGES > 1) {
-                const int nt = sp[(it + 1) % STAGES].t;
-                ne = nt >= A.ntiles ? -1 : sp[(it + 1) % STAGES].e;
-            } else {
-                ne = next >= A.ntiles ? -1 : dnext.entry;
+            // the tile is done: take the grid's ticket; the block completing the grid runs
+            // its control step (release/acquire through the fences around the ticket)
+            __threadfence();
+            const unsigned prev = atomicAdd(A.ticket + e, 1u);
+            if (prev + 1u == (unsigned)g3.x) {
+                __threadfence();
+                const long long fx = (long long)atomicExch(A.gsum + 2 * e, 0ull);
+                const unsigned long long na = atomicExch(A.gsum + 2 * e + 1, 0ull);
+                Ctl c = A.ctl[e];
+                control_step(c, A.ents[e], (double)fx * kFixUnit, na, A.mode, A.A_targ, A.k_a, A.n_f,
+                             A.n_fit, A.i_max, A.ehist + (long long)e * A.ehist_stride, 1);
+                A.ctl[e] = c;
+                A.ticket[e] = 0u;
+                if (A.active && !c.stop) atomicAdd(A.active, 1);
             }
-            s_last = ne != P.e ? 1 : 0;
-            s_runlen += 1;
         }
-        __syncthreads();
-        if (s_last) {
-            dE = warp_sum(dE);
-            nacc = warp_sum(nacc);
-            if ((threadIdx.x & 31) == 0) {
-                s_dE[threadIdx.x >> 5] = dE;
-                s_na[threadIdx.x >> 5] = nacc;
-            }
-            dE = 0.0f;
-            nacc = 0;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double tt = 0.0;
-                unsigned na = 0;
-                for (int i = 0; i < NT / 32; ++i) { tt += (double)s_dE[i]; na += s_na[i]; }
-                A.part_dH[t] = tt;
-                A.part_na[t] = na;
-                __threadfence();
-                const unsigned prev = atomicAdd(A.ticket + P.e, (unsigned)s_runlen);
-                s_grid_done = (prev + (unsigned)s_runlen == (unsigned)P.ntiles) ? 1 : 0;
-                s_runlen = 0;
-            }
-            __syncthreads();
-            if (s_grid_done) {
-                __threadfence();
-                double tt = 0.0;
-                unsigned long long na = 0;
-                for (int i = threadIdx.x; i < P.ntiles; i += NT) {
-                    tt += *((volatile double*)A.part_dH + P.tile0 + i);
-                    na += *((volatile unsigned*)A.part_na + P.tile0 + i);
+        // interior rows of both colours to the other buffer (samples included), 16 bytes
+        // per thread and step, one warp per row; rows and columns beyond the grid skipped
+        {
+            const int rows = min(TH, g3.y - y0);
+            const int pc = (x0 >> 1) + 2;
+            const int nv = (min(TW / 2, g3.z - pc) & ~1) >> 1;        // 16-byte vectors per row
+            const long long pl0 = sp[st].pl0, pl1 = sp[st].pl1;
+            float2* __restrict__ dst = g3.w ? A.lat[0] : A.lat[1];
+            constexpr int V = TW / 4;
+#pragma unroll 2
+            for (int i = threadIdx.x; i < 2 * TH * V; i += NT) {
+                const int c = i / (TH * V), rr = (i / V) % TH, v = i % V;
+                if (rr < rows && v < nv) {
+                    const float4 val = *reinterpret_cast<const float4*>(&sm[c][rr + 2][2 + 2 * v]);
+                    *reinterpret_cast<float4*>(dst + (c ? pl1 : pl0) + (long long)(y0 + rr + 1) * g3.z +
+                                               pc + 2 * v) = val;
                 }
-                s_sum[threadIdx.x] = tt;
-                s_cnt[threadIdx.x] = na;
-                __syncthreads();
-                for (int o = NT / 2; o > 0; o >>= 1) {
-                    if ((int)threadIdx.x < o) {
-                        s_sum[threadIdx.x] += s_sum[threadIdx.x + o];
-                        s_cnt[threadIdx.x] += s_cnt[threadIdx.x + o];
-                    }
-                    __syncthreads();
-                }
-                if (threadIdx.x == 0) {
-                    Ctl c = A.ctl[P.e];
-                    control_step(c, A.ents[P.e], s_sum[0], s_cnt[0], A.mode, A.A_targ, A.k_a, A.n_f,
-                                 A.n_fit, A.i_max, A.ehist + (long long)P.e * A.ehist_stride, 1);
-                    A.ctl[P.e] = c;
-                    A.ticket[P.e] = 0u;
-                    if (A.active && !c.stop) atomicAdd(A.active, 1);
-                }
-                __syncthreads();
             }
+        }
+    }
+    // leave: the last block out resets the tile counter for the next launch (every block
+    // has stopped taking tiles by the time it counts itself out)
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(A.sched + 1, 1u) == gridDim.x - 1u) {
+            atomicExch(A.sched, 0u);
+            atomicExch(A.sched + 1, 0u);
         }
     }
 }
