@@ -194,15 +194,36 @@ struct __align__(16) TileParams {
 constexpr float kFixScale = 268435456.0f;             // 2^28
 constexpr double kFixUnit = 1.0 / 268435456.0;
 
+// Thread 0 of a block, after a barrier that follows every warp's flush for grid e: n more
+// tiles of e are done (release/acquire through the fences around the ticket).  The block
+// completing e's tiles runs e's control step from the fixed-point totals and clears them.
+__device__ __forceinline__ void tile_ticket(const TileArgs& A, int e, int n) {
+    __threadfence();
+    const unsigned prev = atomicAdd(A.ticket + e, (unsigned)n);
+    if (prev + (unsigned)n == (unsigned)A.ents[e].ntiles) {
+        __threadfence();
+        const long long f = (long long)atomicExch(A.gsum + 2 * e, 0ull);
+        const unsigned long long nacc_e = atomicExch(A.gsum + 2 * e + 1, 0ull);
+        Ctl c = A.ctl[e];
+        control_step(c, A.ents[e], (double)f * kFixUnit, nacc_e, A.mode, A.A_targ, A.k_a, A.n_f,
+                     A.n_fit, A.i_max, A.ehist + (long long)e * A.ehist_stride, 1);
+        A.ctl[e] = c;
+        A.ticket[e] = 0u;
+        if (A.active && !c.stop) atomicAdd(A.active, 1);
+    }
+}
+
 // Persistent fused sweep.  Blocks take tiles from a global counter (the last block to
 // leave resets it for the next launch), so faster blocks take more tiles and no block
 // idles while others finish.  Thread 0 stages a tile: a TMA box of both colour planes
 // plus the bulk-copied gap list, completing on the stage's mbarrier.  With two stages the
 // next tile is staged as soon as the current one is in shared memory, a whole tile
 // ahead; with one stage, after the previous tile has been written back.
-// Per tile: every warp adds its energy change and acceptance count to the grid's
-// fixed-point totals; thread 0 then takes the grid's ticket, and the block that
-// completes a grid's tiles runs the grid's Algorithm 2 control step from the totals.
+// Each thread keeps its energy change (fixed point) and acceptance count summed over the
+// block's tiles of one grid; when the block moves on to another grid or runs out of
+// tiles, the warps add them to the grid's totals and thread 0 adds the block's tile count
+// to the grid's ticket.  The block that completes a grid's tiles runs the grid's
+// Algorithm 2 control step from the totals.
 // The interior rows of both planes go back to the other lattice buffer as 16-byte
 // stores, which frees the stage at once.
 template <int TH, int TW, int TRIG, bool ACC, int NT, int STAGES, int MB>
@@ -231,15 +252,24 @@ k_tile_sweep(const TileArgs A) {
     }
     __syncthreads();
 
-    // Thread 0 only: the next tile index taken from the counter and its descriptor
-    // (fetched a tile ahead, so that staging never waits on a global load), and the
-    // parameters of the grid being staged (constant during a launch; reloaded only when
-    // the grid changes -- tiles are taken in increasing order and a grid's are contiguous).
-    int ce = -1, nxt = A.ntiles;
-    __shared__ TileDesc dnext;
+    // Thread 0 only: tile indices come from the counter two tiles ahead and descriptors
+    // one tile ahead (an asynchronous copy into shared memory), so that staging a tile
+    // never waits on the counter or on a global load; the parameters of the grid being
+    // staged are reloaded only when the grid changes (tiles are taken in increasing
+    // order and a grid's tiles are contiguous; they are constant during a launch).
+    int ce = -1, i0 = A.ntiles, i1 = A.ntiles;
+    __shared__ __align__(16) TileDesc dnext;
+    auto fetch_desc = [&](int i) {
+        const TileDesc* src = A.tiles + i;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(&dnext)), "l"(src) : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(&dnext) + 16u),
+                     "l"(reinterpret_cast<const char*>(src) + 16) : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
     if (threadIdx.x == 0) {
-        nxt = (int)atomicAdd(A.sched, 1u);
-        if (nxt < A.ntiles) dnext = A.tiles[nxt];
+        i0 = (int)atomicAdd(A.sched, 1u);
+        i1 = (int)atomicAdd(A.sched, 1u);
+        if (i0 < A.ntiles) fetch_desc(i0);
     }
     auto load_entry = [&](int e) {
         const EntryDesc& E = A.ents[e];
@@ -265,11 +295,13 @@ k_tile_sweep(const TileArgs A) {
     auto issue = [&](int st) {
         TileParams& P = sp[st];
         for (;;) {
-            if (nxt >= A.ntiles) { P.t = A.ntiles; return; }
+            if (i0 >= A.ntiles) { P.t = A.ntiles; return; }
+            asm volatile("cp.async.wait_all;" ::: "memory");          // the descriptor of i0
             const TileDesc d = dnext;
-            const int cur_t = nxt;
-            nxt = (int)atomicAdd(A.sched, 1u);
-            if (nxt < A.ntiles) dnext = A.tiles[nxt];
+            const int cur_t = i0;
+            i0 = i1;                                                  // taken a tile ago
+            if (i0 < A.ntiles) fetch_desc(i0);
+            i1 = (int)atomicAdd(A.sched, 1u);                         // needed two tiles from now
             if (d.entry != ce) load_entry(d.entry);
             if (!cstop) {
                 cp_.t = cur_t;
@@ -289,6 +321,38 @@ k_tile_sweep(const TileArgs A) {
         }
     };
 
+    // each thread's totals over the block's tiles of grid s_acc_e (kept in shared memory)
+    __shared__ long long s_fx[NT];
+    __shared__ unsigned s_nat[NT];
+    __shared__ int s_acc_e, ntile_e, pend_e, pend_n;         // thread 0 writes; ticket bookkeeping
+    s_fx[threadIdx.x] = 0;
+    s_nat[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) {
+        s_acc_e = -1;
+        ntile_e = 0;
+        pend_e = -1;
+        pend_n = 0;
+    }
+    __syncthreads();
+    auto flush_partials = [&](int e) {
+        long long w = s_fx[threadIdx.x];
+        unsigned long long wn = s_nat[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            w += __shfl_xor_sync(0xffffffffu, w, o);
+            wn += __shfl_xor_sync(0xffffffffu, wn, o);
+        }
+        if (lane == 0) {
+            if (w) atomicAdd(A.gsum + 2 * e, (unsigned long long)w);
+            if (wn) atomicAdd(A.gsum + 2 * e + 1, wn);
+        }
+        s_fx[threadIdx.x] = 0;
+        s_nat[threadIdx.x] = 0u;
+    };
+    // thread 0, after a barrier that follows every warp's flush for grid e: n more tiles of
+    // e are done; the block completing e's tiles runs e's control step
+    auto take_ticket = [&](int e, int n) { tile_ticket(A, e, n); };
+
     if (threadIdx.x == 0) issue(0);
     for (int it = 0;; ++it) {
         const int st = STAGES == 1 ? 0 : (it & 1);
@@ -296,6 +360,12 @@ k_tile_sweep(const TileArgs A) {
         if (STAGES == 1 && it > 0) {
             __syncthreads();                                      // B0: the write-back has read the stage
             if (threadIdx.x == 0) issue(0);
+        }
+        // the previous grid's ticket (its flushes were ordered by the last B2/B3), while the
+        // copy is in flight
+        if (threadIdx.x == 0 && pend_e >= 0) {
+            take_ticket(pend_e, pend_n);
+            pend_e = -1;
         }
         if (threadIdx.x == 0 && sp[st].t < A.ntiles && !mbar_wait_try(&bar[st], parity)) {
             atomicExch(A.err, 1);
@@ -323,6 +393,17 @@ k_tile_sweep(const TileArgs A) {
         float2(*sm)[G::RH][G::RW] = stage[st];
         const uint16_t* list = slist[st];
         float* __restrict__ acc = ACC ? A.acc + (long long)t * G::ACC : nullptr;
+        {
+            const int acc_e = s_acc_e;                        // rewritten only after B2
+            if (e != acc_e) {                                 // the block moves on to grid e
+                if (acc_e >= 0) flush_partials(acc_e);
+                if (threadIdx.x == 0) {
+                    pend_e = acc_e;
+                    pend_n = ntile_e;
+                    ntile_e = 0;
+                }
+            }
+        }
 
         // colour A on the tile and its ring, then colour B on the tile
         float dE = 0.0f;
@@ -356,35 +437,18 @@ k_tile_sweep(const TileArgs A) {
                     if (ACC) acc[pass ? nA_int + k : k] += atan2f(v.y, v.x);
                 }
             }
-            if (pass == 0) __syncthreads();               // B2: colour A done
-        }
-        // the warp's share of the tile's energy change and acceptance count
-        dE = warp_sum(dE);
-        nacc = warp_sum(nacc);
-        if (lane == 0) {
-            atomicAdd(A.gsum + 2 * e, (unsigned long long)__float2ll_rn(dE * kFixScale));
-            if (nacc) atomicAdd(A.gsum + 2 * e + 1, (unsigned long long)nacc);
-        }
-        fence_proxy_async_smem();                     // this thread's stage writes before the next copy into it
-        __syncthreads();                              // B3: colour B done, partials issued
-        const int4 g3 = *reinterpret_cast<const int4*>(&sp[st].ntiles);
-        if (threadIdx.x == 0) {
-            // the tile is done: take the grid's ticket; the block completing the grid runs
-            // its control step (release/acquire through the fences around the ticket)
-            __threadfence();
-            const unsigned prev = atomicAdd(A.ticket + e, 1u);
-            if (prev + 1u == (unsigned)g3.x) {
-                __threadfence();
-                const long long fx = (long long)atomicExch(A.gsum + 2 * e, 0ull);
-                const unsigned long long na = atomicExch(A.gsum + 2 * e + 1, 0ull);
-                Ctl c = A.ctl[e];
-                control_step(c, A.ents[e], (double)fx * kFixUnit, na, A.mode, A.A_targ, A.k_a, A.n_f,
-                             A.n_fit, A.i_max, A.ehist + (long long)e * A.ehist_stride, 1);
-                A.ctl[e] = c;
-                A.ticket[e] = 0u;
-                if (A.active && !c.stop) atomicAdd(A.active, 1);
+            if (pass == 0) {
+                __syncthreads();                          // B2: colour A done (and any flush)
+                if (threadIdx.x == 0) s_acc_e = e;
             }
         }
+        // the tile's energy change in fixed point: deterministic whatever the tile order
+        s_fx[threadIdx.x] += __float2ll_rn(dE * kFixScale);
+        s_nat[threadIdx.x] += nacc;
+        if (threadIdx.x == 0) ++ntile_e;
+        fence_proxy_async_smem();                     // this thread's stage writes before the next copy into it
+        __syncthreads();                              // B3: colour B done
+        const int4 g3 = *reinterpret_cast<const int4*>(&sp[st].ntiles);
         // interior rows of both colours to the other buffer (samples included), 16 bytes
         // per thread and step, one warp per row; rows and columns beyond the grid skipped
         {
@@ -405,9 +469,15 @@ k_tile_sweep(const TileArgs A) {
             }
         }
     }
-    // leave: the last block out resets the tile counter for the next launch (every block
-    // has stopped taking tiles by the time it counts itself out)
+    // leave: hand in the last grid's totals and tiles, then the last block out resets the
+    // tile counter for the next launch (every block has stopped taking tiles by the time
+    // it counts itself out)
+    const int acc_e = s_acc_e;
+    if (acc_e >= 0) flush_partials(acc_e);
+    __syncthreads();
+    if (threadIdx.x == 0 && acc_e >= 0) take_ticket(acc_e, ntile_e);
     if (threadIdx.x == 0) {
+        asm volatile("cp.async.wait_all;" ::: "memory");
         __threadfence();
         if (atomicAdd(A.sched + 1, 1u) == gridDim.x - 1u) {
             atomicExch(A.sched, 0u);
