@@ -7,10 +7,13 @@ Tolerances (written here, derived in the design notes):
   * one sweep from an identical state: |d phi| <= 1e-5 rad (circular) at every site
     whose decisions agree; sites beyond that are counted as flipped decisions and must be
     at most 1e-6 of all decisions (plus one, for sample sizes below 10^6).
-  * whole runs (chains diverge after the first flip): MAE and RMSE within 1% relative
-    of the oracle's at 256^2, and within 6% of the paper's Table 2-3 values at L = 1024.
+  * whole runs (chains diverge after the first flip): MAE and RMSE, averaged over
+    independent chains of each side, within 1% relative of the oracle's at 256^2, and
+    within 6% of the paper's Table 2-3 values at L = 1024.
 """
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 import pytest
@@ -167,26 +170,43 @@ def test_tracked_energy_matches_exact_energy():
 
 def test_fixed_length_run_matches_oracle_statistics():
     # 256^2, 33% gaps, fixed T, 200 relaxation sweeps (slope test disabled) then M = 100.
+    # Whole runs of the two sides diverge after the first flipped decision, so the fills
+    # are compared as estimators: MAE/RMSE averaged over independent chains (seeds) of
+    # each side within 1 %.  The C oracle runs outside the GIL, on parallel threads.
     L = 256
     z = synth.wm_field(L, 0.5, 5.0, seed=41)
     mask = synth.mask_uniform(L, L, 0.33, seed=1_000_041)
     T = 0.12
-    prm = orc.params(seed=3, i_max=199, n_fit=10**6, M=100)
-    zo, _, fo = orc.fill(z, mask, prm, T_fixed=T)
-    ctx = make_ctx(z, mask, seed=3, i_max=199, n_fit=10**6, M=100)
-    try:
-        mpr.mpr_set_T(ctx, T)
-        st = mpr.mpr_equilibrate(ctx)
-        assert st.sweeps == 200 and fo.eq.sweeps == 200
-        assert st.a >= 1.0 and abs(st.a / fo.eq.a - 1) < 0.5
-        zg = np.zeros_like(z)
-        mpr.mpr_predict(ctx, 100, zg)
-    finally:
-        mpr.mpr_free(ctx)
+    seeds = (3, 4, 5, 6, 7, 8)
     g = mask == 0
-    assert np.array_equal(zg[~g], z[~g])
-    mae_o = np.abs(zo[g] - z[g]).mean(); mae_g = np.abs(zg[g] - z[g]).mean()
-    rmse_o = np.sqrt(((zo[g] - z[g]) ** 2).mean()); rmse_g = np.sqrt(((zg[g] - z[g]) ** 2).mean())
+
+    def errors(zh):
+        e = zh[g].astype(np.float64) - z[g]
+        return np.abs(e).mean(), np.sqrt((e ** 2).mean())
+
+    def oracle_run(seed):
+        prm = orc.params(seed=seed, i_max=199, n_fit=10**6, M=100)
+        zo, _, fo = orc.fill(z, mask, prm, T_fixed=T)
+        return errors(zo), fo.eq.sweeps, fo.eq.a
+
+    with ThreadPoolExecutor(max_workers=min(len(seeds), os.cpu_count() or 1)) as ex:
+        oracle = list(ex.map(oracle_run, seeds))
+    gpu = []
+    for seed, (_, o_sweeps, o_a) in zip(seeds, oracle):
+        ctx = make_ctx(z, mask, seed=seed, i_max=199, n_fit=10**6, M=100)
+        try:
+            mpr.mpr_set_T(ctx, T)
+            st = mpr.mpr_equilibrate(ctx)
+            assert st.sweeps == 200 and o_sweeps == 200
+            assert st.a >= 1.0 and abs(st.a / o_a - 1) < 0.5
+            zg = np.zeros_like(z)
+            mpr.mpr_predict(ctx, 100, zg)
+        finally:
+            mpr.mpr_free(ctx)
+        assert np.array_equal(zg[~g], z[~g])
+        gpu.append(errors(zg))
+    mae_o, rmse_o = np.mean([o[0] for o in oracle], axis=0)
+    mae_g, rmse_g = np.mean(gpu, axis=0)
     assert abs(mae_g / mae_o - 1) < 0.01, (mae_g, mae_o)
     assert abs(rmse_g / rmse_o - 1) < 0.01, (rmse_g, rmse_o)
 

@@ -5,11 +5,16 @@ half of the sites missing as disks plus random sites).
 Run with -s to print the table; the bounds asserted here are the ones the design notes
 derive (|d phi| <= 1e-5 rad where decisions agree; flipped decisions <= 1e-6 of all in the
 accurate mode; MAE/RMSE within 1 % of the oracle's for both modes).
+
+Whole runs of the two sides diverge after the first flipped decision, so they are compared
+as estimators: one run's MAE on this crop moves by about +-1 % from seed to seed (on both
+sides), so the 1 % bound applies to the mean over SEEDS independent chains of each side.
 """
 import json
 import math
 import os
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 import pytest
@@ -64,9 +69,29 @@ def _single_sweeps(z, m, T, trig, sweeps=24):
                 p99_err=float(np.quantile(e, 0.99)))
 
 
-def _run(z, m, T, trig):
+SEEDS = (6, 7, 8, 9, 10, 11, 12, 13)
+
+
+def _errors(zh, z, m):
+    g = m == 0
+    err = zh[g].astype(np.float64) - z[g]
+    return float(np.abs(err).mean()), float(np.sqrt((err ** 2).mean()))
+
+
+def _oracle_runs(z, m, T):
+    """(MAE, RMSE) of the oracle's fill per seed; the C oracle runs outside the GIL, so
+    the seeds run on parallel threads."""
+    def one(seed):
+        prm = orc.params(seed=seed, i_max=199, n_fit=10**6, M=100)
+        zo, _, _ = orc.fill(z, m, prm, T_fixed=T)
+        return _errors(zo, z, m)
+    with ThreadPoolExecutor(max_workers=min(len(SEEDS), os.cpu_count() or 1)) as ex:
+        return list(ex.map(one, SEEDS))
+
+
+def _run(z, m, T, trig, seed):
     H, W = z.shape
-    ctx = mpr.mpr_init(z, m, W, H, mpr.mpr_default_params(seed=6, trig_mode=trig, i_max=199,
+    ctx = mpr.mpr_init(z, m, W, H, mpr.mpr_default_params(seed=seed, trig_mode=trig, i_max=199,
                                                           n_fit=10**6, M=100))
     try:
         mpr.mpr_set_T(ctx, T)
@@ -76,10 +101,8 @@ def _run(z, m, T, trig):
         info = mpr.mpr_get_info(ctx)
     finally:
         mpr.mpr_free(ctx)
-    g = m == 0
-    err = zh[g].astype(np.float64) - z[g]
-    return dict(mae=float(np.abs(err).mean()), rmse=float(np.sqrt((err ** 2).mean())),
-                energy_drift=abs(info["H_tracked"] / info["H_exact"] - 1))
+    mae, rmse = _errors(zh, z, m)
+    return dict(mae=mae, rmse=rmse, energy_drift=abs(info["H_tracked"] / info["H_exact"] - 1))
 
 
 def test_precision_accurate_vs_fast_against_oracle(crop):
@@ -90,20 +113,22 @@ def test_precision_accurate_vs_fast_against_oracle(crop):
         T, _ = mpr.mpr_estimate_T(ctx)
     finally:
         mpr.mpr_free(ctx)
-    prm = orc.params(seed=6, i_max=199, n_fit=10**6, M=100)
-    zo, _, _ = orc.fill(z, m, prm, T_fixed=T)
-    g = m == 0
-    eo = zo[g] - z[g]
-    ref = dict(mae=float(np.abs(eo).mean()), rmse=float(np.sqrt((eo ** 2).mean())))
-    report = {"T_hat": T, "oracle": ref}
+    oracle_runs = np.array(_oracle_runs(z, m, T))
+    ref = dict(mae=float(oracle_runs[:, 0].mean()), rmse=float(oracle_runs[:, 1].mean()),
+               mae_per_seed=oracle_runs[:, 0].tolist())
+    report = {"T_hat": T, "seeds": list(SEEDS), "oracle": ref}
     for name, trig in (("accurate", mpr.MPR_TRIG_ACCURATE), ("fast", mpr.MPR_TRIG_FAST)):
         one = _single_sweeps(z, m, T, trig)
-        run = _run(z, m, T, trig)
+        runs = [_run(z, m, T, trig, s) for s in SEEDS]
+        run = dict(mae=float(np.mean([r["mae"] for r in runs])),
+                   rmse=float(np.mean([r["rmse"] for r in runs])),
+                   mae_per_seed=[r["mae"] for r in runs],
+                   energy_drift=max(r["energy_drift"] for r in runs))
         run["mae_rel_to_oracle"] = run["mae"] / ref["mae"] - 1
         run["rmse_rel_to_oracle"] = run["rmse"] / ref["rmse"] - 1
         report[name] = dict(single_sweep=one, run=run)
         assert one["max_err"] <= 1e-5
-        assert abs(run["mae_rel_to_oracle"]) < 0.01 and abs(run["rmse_rel_to_oracle"]) < 0.01
+        assert abs(run["mae_rel_to_oracle"]) < 0.01 and abs(run["rmse_rel_to_oracle"]) < 0.01, run
         assert run["energy_drift"] < 1e-6
     acc = report["accurate"]["single_sweep"]
     assert acc["flips"] <= 1e-6 * acc["decisions"] + 1
