@@ -214,6 +214,30 @@ __device__ __forceinline__ void sincos_quarter(float x, float* s, float* c) {
     *c = fmaf(pc, x2, 1.0f);
 }
 
+// theta = atan2(s, c) for a point (c, s) of the closed upper half plane (s >= 0), in
+// [0, pi]: reduction to x = min(|c|, s) / max(|c|, s) in [0, 1]; atan(x) = x P(x^2) with P
+// of degree 7 fitted by csrc/fit_atan.py (least squares on Chebyshev nodes refined by
+// Lawson's iteration towards the minimax fit; the FP32 evaluation is within 1.8e-7 of
+// atan on [0, 1]); then pi/2 - a above the diagonal and pi - a for c < 0.  With the
+// 2-ulp quotient the result is within 4e-7 rad of the exact angle.  (0, 0) gives 0.
+__device__ __forceinline__ float angle_upper(float c, float s) {
+    const float ac = fabsf(c);
+    const float lo = fminf(ac, s), hi = fmaxf(ac, s);
+    const float x = hi > 0.0f ? __fdividef(lo, hi) : 0.0f;
+    const float t = x * x;
+    float p = -4.781315569e-03f;
+    p = fmaf(p, t, 2.456034347e-02f);
+    p = fmaf(p, t, -5.990952626e-02f);
+    p = fmaf(p, t, 9.943124652e-02f);
+    p = fmaf(p, t, -1.402956843e-01f);
+    p = fmaf(p, t, 1.997140646e-01f);
+    p = fmaf(p, t, -3.333209753e-01f);
+    p = fmaf(p, t, 9.999999404e-01f);
+    float a = p * x;
+    a = s > ac ? 1.5707963267948966f - a : a;
+    return c < 0.0f ? 3.1415926535897932f - a : a;
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -49,7 +49,7 @@ k_half_sweep(const SweepArgs A, const int color) {
             dE += hybrid_update<TRIG>(v, C, S, hq, u24f(rnd.y), kx, A.or_on, accepted);
             nacc += accepted ? 1u : 0u;
             own[k] = v;
-            if (ACC) acc[g] += atan2f(v.y, v.x);
+            if (ACC) acc[g] += angle_upper(v.x, v.y);
         }
     }
     // energy change and acceptance count: warp shuffle, then a fixed-order block sum
@@ -187,7 +187,7 @@ __global__ void k_predict_out(EntryDesc e, const uint32_t* __restrict__ gaps,
     }
 }
 
-// phi = 2 atan2(sin, cos) for every site of one grid.
+// phi = 2 theta, theta the angle of (cos, sin) in [0, pi], for every site of one grid.
 __global__ void k_get_state(EntryDesc e, const float2* __restrict__ lat, float* __restrict__ phi) {
     const long long n = (long long)e.W * e.H;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -195,7 +195,7 @@ __global__ void k_get_state(EntryDesc e, const float2* __restrict__ lat, float* 
         const int y = (int)(i / e.W), x = (int)(i - (long long)y * e.W);
         const long long base = ((x + y) & 1) ? e.plane[1] : e.plane[0];
         const float2 v = lat[base + (long long)(y + 1) * e.pitch + (x >> 1) + kPadL];
-        phi[i] = 2.0f * atan2f(fmaxf(v.y, 0.0f), v.x);
+        phi[i] = 2.0f * angle_upper(v.x, fmaxf(v.y, 0.0f));
     }
 }
 

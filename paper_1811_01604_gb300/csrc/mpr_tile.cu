@@ -416,6 +416,13 @@ k_tile_sweep(const TileArgs A) {
             float2(*own)[G::RW] = sm[c];
             float2(*oth)[G::RW] = sm[c ^ 1];
             for (int k = threadIdx.x; k < n; k += NT) {
+                // the ring belongs to other tiles: its sites count nowhere
+                const bool own_site = pass || k < nA_int;
+                const int aidx = pass ? nA_int + k : k;
+                // the running angle sum is loaded first, so that its latency hides behind
+                // the update
+                float acc_old = 0.0f;
+                if (ACC && own_site) acc_old = acc[aidx];
                 const int ent = lst[k];
                 const int r = ent >> 7, q = ent & 127;
                 const int s = c ^ (r & 1);
@@ -431,10 +438,10 @@ k_tile_sweep(const TileArgs A) {
                 bool accepted;
                 const float d = hybrid_update<TRIG>(v, C, S, hq, u24f(rnd.y), kx, A.or_on, accepted);
                 own[r][q] = v;
-                if (pass || k < nA_int) {                 // the ring belongs to other tiles
+                if (own_site) {
                     dE += d;
                     nacc += accepted ? 1u : 0u;
-                    if (ACC) acc[pass ? nA_int + k : k] += atan2f(v.y, v.x);
+                    if (ACC) acc[aidx] = acc_old + angle_upper(v.x, v.y);
                 }
             }
             if (pass == 0) {
