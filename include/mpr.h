@@ -234,6 +234,16 @@ mpr_status mpr_time_sweeps(mpr_ctx* ctx, int n, double a, double* ms_per_sweep);
 uint64_t mpr_kernel_launches(void);
 
 /*
+ * Memory of released contexts.  Contexts take their device memory from a stream-ordered
+ * pool per device owned by the library, which keeps what mpr_free releases so that the
+ * next context of a similar size allocates without going back to the driver (no
+ * counterpart in the paper; it serves repeated fills).  This call returns the kept,
+ * unused memory of the current device's pool to the driver; live contexts are not
+ * affected.  Returns MPR_OK (also when no pool exists yet) or MPR_ECUDA.
+ */
+mpr_status mpr_release_memory(void);
+
+/*
  * Allocation-free sample energy.  The paper has no counterpart to this entry point: it
  * exists for callers that are not allowed to allocate device memory, such as a host
  * application that owns the GPU's memory through its own pool or budget and forbids

@@ -135,39 +135,84 @@ mpr_status fail(mpr_ctx* c, mpr_status s, const std::string& msg) {
                         std::string(#call) + ": " + cudaGetErrorString(e_));            \
     } while (0)
 
-template <class T>
-cudaError_t dalloc(T** p, size_t n) {
-    *p = nullptr;
-    if (n == 0) n = 1;
-    return cudaMalloc((void**)p, n * sizeof(T));
+// Device memory of the library's contexts comes from a stream-ordered memory pool per
+// device owned by the library.  The pool keeps what is freed (release threshold:
+// unlimited), so building and releasing contexts of similar sizes -- a serving loop over
+// maps -- reuses that memory instead of going back to the driver; mpr_release_memory()
+// hands it back.
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+
+cudaError_t device_pool(cudaMemPool_t* pool) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof props);
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        e = cudaMemPoolCreate(&p, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = ~0ull;
+        e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return e;
+        }
+        g_pools[dev] = p;
+    }
+    *pool = g_pools[dev];
+    return cudaSuccess;
 }
 
-void batch_free(Batch& b) {
+// n elements of T from the pool, usable in the order of stream st
+template <class T>
+cudaError_t dalloc(T** p, size_t n, cudaStream_t st) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = device_pool(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync((void**)p, n * sizeof(T), pool, st);
+}
+
+// returns p to the pool in the order of stream st (null is ignored)
+void dfree(void* p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+
+void batch_free(Batch& b, cudaStream_t st) {
     for (auto& kv : b.graphs) cudaGraphExecDestroy(kv.second);
     b.graphs.clear();
-    cudaFree(b.d_ents);
-    cudaFree(b.d_lat);
-    cudaFree(b.d_gaps);
-    cudaFree(b.d_acc);
+    dfree(b.d_ents, st);
+    dfree(b.d_lat, st);
+    dfree(b.d_gaps, st);
+    dfree(b.d_acc, st);
     for (int c = 0; c < 2; ++c) {
-        cudaFree(b.d_work[c]);
-        cudaFree(b.d_part[c]);
+        dfree(b.d_work[c], st);
+        dfree(b.d_part[c], st);
     }
-    cudaFree(b.d_ctl);
-    cudaFree(b.d_ehist);
-    cudaFree(b.d_active);
-    cudaFree(b.d_scratch);
-    cudaFree(b.d_H);
-    cudaFree(b.d_lat2);
-    cudaFree(b.d_tiles);
-    cudaFree(b.d_cnts);
-    cudaFree(b.d_lists);
-    cudaFree(b.d_tacc);
-    cudaFree(b.d_gsum);
-    cudaFree(b.d_sched);
-    cudaFree(b.d_ticket);
-    cudaFree(b.d_maps);
-    cudaFree(b.d_err);
+    dfree(b.d_ctl, st);
+    dfree(b.d_ehist, st);
+    dfree(b.d_active, st);
+    dfree(b.d_scratch, st);
+    dfree(b.d_H, st);
+    dfree(b.d_lat2, st);
+    dfree(b.d_tiles, st);
+    dfree(b.d_cnts, st);
+    dfree(b.d_lists, st);
+    dfree(b.d_tacc, st);
+    dfree(b.d_gsum, st);
+    dfree(b.d_sched, st);
+    dfree(b.d_ticket, st);
+    dfree(b.d_maps, st);
+    dfree(b.d_err, st);
     b = Batch();
 }
 
@@ -177,13 +222,13 @@ mpr_status build_tiles(mpr_ctx* ctx, Batch& b, int cfg) {
     cudaStream_t st = ctx->st;
     if (cfg < 0 || cfg >= tile_config_count()) return fail(ctx, MPR_EINVAL, "tile configuration");
     const TileGeom g = tile_geom(cfg);
-    cudaFree(b.d_tiles);
-    cudaFree(b.d_cnts);
-    cudaFree(b.d_lists);
-    cudaFree(b.d_tacc);
-    cudaFree(b.d_gsum);
-    cudaFree(b.d_sched);
-    cudaFree(b.d_ticket);
+    dfree(b.d_tiles, st);
+    dfree(b.d_cnts, st);
+    dfree(b.d_lists, st);
+    dfree(b.d_tacc, st);
+    dfree(b.d_gsum, st);
+    dfree(b.d_sched, st);
+    dfree(b.d_ticket, st);
     b.d_tiles = nullptr; b.d_cnts = nullptr; b.d_lists = nullptr; b.d_tacc = nullptr;
     b.d_gsum = nullptr; b.d_sched = nullptr; b.d_ticket = nullptr;
     for (auto& kv : b.graphs) cudaGraphExecDestroy(kv.second);
@@ -198,16 +243,16 @@ mpr_status build_tiles(mpr_ctx* ctx, Batch& b, int cfg) {
     }
     CU(cudaMemcpyAsync(b.d_ents, b.ents.data(), b.n_ent * sizeof(EntryDesc), cudaMemcpyHostToDevice, st));
     b.ntiles = (int)tiles.size();
-    CU(dalloc(&b.d_tiles, tiles.size()));
+    CU(dalloc(&b.d_tiles, tiles.size(), st));
     CU(cudaMemcpyAsync(b.d_tiles, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, st));
-    CU(dalloc(&b.d_cnts, tiles.size()));
-    CU(dalloc(&b.d_lists, tiles.size() * (size_t)g.list));
-    CU(dalloc(&b.d_tacc, tiles.size() * (size_t)g.acc));
-    CU(dalloc(&b.d_gsum, (size_t)2 * b.n_ent));
+    CU(dalloc(&b.d_cnts, tiles.size(), st));
+    CU(dalloc(&b.d_lists, tiles.size() * (size_t)g.list, st));
+    CU(dalloc(&b.d_tacc, tiles.size() * (size_t)g.acc, st));
+    CU(dalloc(&b.d_gsum, (size_t)2 * b.n_ent, st));
     CU(cudaMemsetAsync(b.d_gsum, 0, sizeof(unsigned long long) * 2 * b.n_ent, st));
-    CU(dalloc(&b.d_sched, 2));
+    CU(dalloc(&b.d_sched, 2, st));
     CU(cudaMemsetAsync(b.d_sched, 0, sizeof(unsigned) * 2, st));
-    CU(dalloc(&b.d_ticket, (size_t)b.n_ent));
+    CU(dalloc(&b.d_ticket, (size_t)b.n_ent, st));
     CU(cudaMemsetAsync(b.d_ticket, 0, sizeof(unsigned) * b.n_ent, st));
     CU(launch_tile_lists(cfg, b.d_tiles, b.ntiles, b.d_ents, b.mask_base, b.all_free, b.d_lists,
                          b.d_cnts, st));
@@ -252,7 +297,7 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
         maxH = std::max(maxH, E.H);
     }
     b.lat_elems = lat;
-    CU(dalloc(&b.d_lat, lat));
+    CU(dalloc(&b.d_lat, lat, st));
     CU(cudaMemsetAsync(b.d_lat, 0, lat * sizeof(float2), st));
     for (int e = 0; e < b.n_ent; ++e)
         CU(launch_pack(&b.ents[e], grids[e].z, grids[e].mask, grids[e].zmin, grids[e].scale, b.d_lat,
@@ -260,8 +305,8 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
     // gap lists: per-row counts, scan, scatter
     int* d_rows = nullptr;
     int* d_tot = nullptr;
-    CU(dalloc(&d_rows, (size_t)2 * maxH));
-    CU(dalloc(&d_tot, 2));
+    CU(dalloc(&d_rows, (size_t)2 * maxH, st));
+    CU(dalloc(&d_tot, 2, st));
     std::vector<std::vector<int>> row_off(b.n_ent);
     size_t ng = 0;
     std::vector<int> tot(2);
@@ -283,16 +328,16 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
         ng += (size_t)E.P;
     }
     b.n_gaps = ng;
-    CU(dalloc(&b.d_gaps, ng));
-    CU(dalloc(&b.d_acc, ng));
+    CU(dalloc(&b.d_gaps, ng, st));
+    CU(dalloc(&b.d_acc, ng, st));
     for (int e = 0; e < b.n_ent; ++e) {
         EntryDesc& E = b.ents[e];
         CU(cudaMemcpyAsync(d_rows, offs[e].data(), sizeof(int) * 2 * E.H, cudaMemcpyHostToDevice, st));
         CU(launch_gap_scatter(&E, grids[e].mask, all_free, d_rows, b.d_gaps, st));
         CU(cudaStreamSynchronize(st));
     }
-    cudaFree(d_rows);
-    cudaFree(d_tot);
+    dfree(d_rows, st);
+    dfree(d_tot, st);
     // sweep work lists
     const int chunk = kSweepThreads * kSweepItems;
     for (int c = 0; c < 2; ++c) {
@@ -305,19 +350,19 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
             for (int i = 0; i < nb; ++i) w.push_back(BlockWork{e, i * chunk});
         }
         b.nblk[c] = (int)w.size();
-        CU(dalloc(&b.d_work[c], w.size()));
-        CU(dalloc(&b.d_part[c], w.size()));
+        CU(dalloc(&b.d_work[c], w.size(), st));
+        CU(dalloc(&b.d_part[c], w.size(), st));
         if (!w.empty())
             CU(cudaMemcpyAsync(b.d_work[c], w.data(), w.size() * sizeof(BlockWork),
                                cudaMemcpyHostToDevice, st));
     }
-    CU(dalloc(&b.d_ents, b.n_ent));
+    CU(dalloc(&b.d_ents, b.n_ent, st));
     CU(cudaMemcpyAsync(b.d_ents, b.ents.data(), b.n_ent * sizeof(EntryDesc), cudaMemcpyHostToDevice, st));
     if (b.tiled) {
-        CU(dalloc(&b.d_lat2, lat));
+        CU(dalloc(&b.d_lat2, lat, st));
         CU(cudaMemcpyAsync(b.d_lat2, b.d_lat, lat * sizeof(float2), cudaMemcpyDeviceToDevice, st));
-        CU(dalloc(&b.d_maps, (size_t)2 * b.n_ent));
-        CU(dalloc(&b.d_err, 1));
+        CU(dalloc(&b.d_maps, (size_t)2 * b.n_ent, st));
+        CU(dalloc(&b.d_err, 1, st));
         CU(cudaMemsetAsync(b.d_err, 0, sizeof(int), st));
         b.mask_base = mask_base;
         b.all_free = all_free;
@@ -333,14 +378,14 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
         ctl[e].half_qd = (float)(0.5 * kTwoPi * 0.5 / 1.0);
         ctl[e].neg_inv_T = grids[e].T > 0.0 ? (float)(-1.0 / grids[e].T) : 0.0f;
     }
-    CU(dalloc(&b.d_ctl, b.n_ent));
+    CU(dalloc(&b.d_ctl, b.n_ent, st));
     CU(cudaMemcpyAsync(b.d_ctl, ctl.data(), b.n_ent * sizeof(Ctl), cudaMemcpyHostToDevice, st));
     b.ehist_stride = ctx->prm.i_max + 2;
-    CU(dalloc(&b.d_ehist, (size_t)b.n_ent * b.ehist_stride));
+    CU(dalloc(&b.d_ehist, (size_t)b.n_ent * b.ehist_stride, st));
     CU(cudaMemsetAsync(b.d_ehist, 0, sizeof(double) * (size_t)b.n_ent * b.ehist_stride, st));
-    CU(dalloc(&b.d_active, kMaxGraphSweeps));
-    CU(dalloc(&b.d_scratch, kScratch + 8));
-    CU(dalloc(&b.d_H, (size_t)b.n_ent));
+    CU(dalloc(&b.d_active, kMaxGraphSweeps, st));
+    CU(dalloc(&b.d_scratch, kScratch + 8, st));
+    CU(dalloc(&b.d_H, (size_t)b.n_ent, st));
     CU(cudaStreamSynchronize(st));
     return MPR_OK;
 }
@@ -560,7 +605,7 @@ mpr_status build_tables(mpr_ctx* ctx, const std::vector<std::pair<int, int>>& sh
                 ek[sh][k] = x.nsamp ? x.esum / x.nsamp : 0.0;
             }
     }
-    batch_free(tb);
+    batch_free(tb, ctx->st);
     return s;
 }
 
@@ -641,10 +686,13 @@ const char* mpr_last_error(const mpr_ctx* ctx) { return ctx ? ctx->err.c_str() :
 
 void mpr_free(mpr_ctx* ctx) {
     if (!ctx) return;
-    batch_free(ctx->b);
-    cudaFree(ctx->d_z);
-    cudaFree(ctx->d_mask);
-    cudaFree(ctx->d_out);
+    // the work already enqueued finishes before its buffers and graphs go (the frees are
+    // stream-ordered on the caller's stream)
+    cudaStreamSynchronize(ctx->st);
+    batch_free(ctx->b, ctx->st);
+    dfree(ctx->d_z, ctx->st);
+    dfree(ctx->d_mask, ctx->st);
+    dfree(ctx->d_out, ctx->st);
     if (ctx->h_active) cudaFreeHost(ctx->h_active);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
     delete ctx;
@@ -693,8 +741,8 @@ static mpr_status init_grids(mpr_ctx** out, int n, const float* const* z, const 
     CUI(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
     CUI(cudaMallocHost((void**)&ctx->h_active, sizeof(int) * 4));
     const size_t N = (size_t)site0;
-    if (dalloc(&ctx->d_z, N) != cudaSuccess || dalloc(&ctx->d_mask, N) != cudaSuccess ||
-        dalloc(&ctx->d_out, N) != cudaSuccess) { cudaGetLastError(); return bail(MPR_ENOMEM); }
+    if (dalloc(&ctx->d_z, N, ctx->st) != cudaSuccess || dalloc(&ctx->d_mask, N, ctx->st) != cudaSuccess ||
+        dalloc(&ctx->d_out, N, ctx->st) != cudaSuccess) { cudaGetLastError(); return bail(MPR_ENOMEM); }
     for (int i = 0; i < n; ++i) {
         const size_t ni = (size_t)W[i] * H[i];
         CUI(cudaMemcpyAsync(ctx->d_z + ctx->g[i].site0, z[i], ni * sizeof(float), cudaMemcpyDefault, ctx->st));
@@ -703,8 +751,8 @@ static mpr_status init_grids(mpr_ctx** out, int n, const float* const* z, const 
     // Eq. 1 extremes, per grid
     unsigned* d_keys = nullptr;
     unsigned long long* d_ns = nullptr;
-    CUI(dalloc(&d_keys, (size_t)2 * n));
-    CUI(dalloc(&d_ns, (size_t)n));
+    CUI(dalloc(&d_keys, (size_t)2 * n, ctx->st));
+    CUI(dalloc(&d_ns, (size_t)n, ctx->st));
     for (int i = 0; i < n; ++i) {
         CUI(cudaMemsetAsync(d_keys + 2 * i, 0xFF, sizeof(unsigned), ctx->st));
         CUI(cudaMemsetAsync(d_keys + 2 * i + 1, 0, sizeof(unsigned), ctx->st));
@@ -718,8 +766,8 @@ static mpr_status init_grids(mpr_ctx** out, int n, const float* const* z, const 
     CUI(cudaMemcpyAsync(keys.data(), d_keys, sizeof(unsigned) * 2 * n, cudaMemcpyDeviceToHost, ctx->st));
     CUI(cudaMemcpyAsync(ns.data(), d_ns, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, ctx->st));
     CUI(cudaStreamSynchronize(ctx->st));
-    cudaFree(d_keys);
-    cudaFree(d_ns);
+    dfree(d_keys, ctx->st);
+    dfree(d_ns, ctx->st);
     auto unkey = [](unsigned k) {
         const unsigned b = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
         float f;
@@ -745,8 +793,8 @@ static mpr_status init_grids(mpr_ctx** out, int n, const float* const* z, const 
     // Eq. 4, per grid (per-block partials added in block order on the host)
     double* d_ps = nullptr;
     unsigned long long* d_pc = nullptr;
-    CUI(dalloc(&d_ps, 1024));
-    CUI(dalloc(&d_pc, 1024));
+    CUI(dalloc(&d_ps, 1024, ctx->st));
+    CUI(dalloc(&d_pc, 1024, ctx->st));
     for (int i = 0; i < n; ++i) {
         GridInfo& G = ctx->g[i];
         int np = 0;
@@ -763,8 +811,8 @@ static mpr_status init_grids(mpr_ctx** out, int n, const float* const* z, const 
         G.n_sp = (long long)cnt;
         G.e_s = cnt ? -sum / (double)cnt : 0.0;
     }
-    cudaFree(d_ps);
-    cudaFree(d_pc);
+    dfree(d_ps, ctx->st);
+    dfree(d_pc, ctx->st);
 #undef CUI
     *out = ctx;
     return MPR_OK;
@@ -1065,8 +1113,8 @@ mpr_status mpr_autotune(mpr_ctx* ctx, int* tile_cfg, int* graph_sweeps, double* 
     const size_t bytes = b.lat_elems * sizeof(float2);
     float2* snap0 = nullptr;
     float2* snap1 = nullptr;
-    CU(dalloc(&snap0, b.lat_elems));
-    CU(dalloc(&snap1, b.lat_elems));
+    CU(dalloc(&snap0, b.lat_elems, ctx->st));
+    CU(dalloc(&snap1, b.lat_elems, ctx->st));
     CU(cudaMemcpyAsync(snap0, b.d_lat, bytes, cudaMemcpyDeviceToDevice, ctx->st));
     CU(cudaMemcpyAsync(snap1, b.d_lat2, bytes, cudaMemcpyDeviceToDevice, ctx->st));
     std::vector<Ctl> c0;
@@ -1087,8 +1135,8 @@ mpr_status mpr_autotune(mpr_ctx* ctx, int* tile_cfg, int* graph_sweeps, double* 
         CU(cudaMemcpyAsync(b.d_ctl, c0.data(), sizeof(Ctl) * c0.size(), cudaMemcpyHostToDevice, ctx->st));
         CU(cudaStreamSynchronize(ctx->st));
     }
-    cudaFree(snap0);
-    cudaFree(snap1);
+    dfree(snap0, ctx->st);
+    dfree(snap1, ctx->st);
     if (s != MPR_OK) return s;
     if (best != b.tcfg) {
         s = build_tiles(ctx, b, best);
@@ -1143,6 +1191,14 @@ mpr_status mpr_time_sweeps(mpr_ctx* ctx, int n, double a, double* ms_per_sweep) 
     return MPR_OK;
 }
 
+mpr_status mpr_release_memory(void) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MPR_ECUDA;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) return MPR_OK;
+    return cudaMemPoolTrimTo(g_pools[dev], 0) == cudaSuccess ? MPR_OK : MPR_ECUDA;
+}
+
 mpr_status mpr_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, size_t n,
                       void* cuda_stream) {
     if ((!ctr || !out) && n) return MPR_EINVAL;
@@ -1150,16 +1206,16 @@ mpr_status mpr_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, size_t 
     cudaStream_t st = (cudaStream_t)cuda_stream;
     uint4* d_in = nullptr;
     uint4* d_out = nullptr;
-    if (cudaMalloc((void**)&d_in, n * sizeof(uint4)) != cudaSuccess) return MPR_ENOMEM;
-    if (cudaMalloc((void**)&d_out, n * sizeof(uint4)) != cudaSuccess) { cudaFree(d_in); return MPR_ENOMEM; }
+    if (dalloc(&d_in, n, st) != cudaSuccess) return MPR_ENOMEM;
+    if (dalloc(&d_out, n, st) != cudaSuccess) { dfree(d_in, st); return MPR_ENOMEM; }
     mpr_status s = MPR_OK;
     if (cudaMemcpyAsync(d_in, ctr, n * sizeof(uint4), cudaMemcpyDefault, st) != cudaSuccess ||
         launch_philox(d_in, (uint32_t)seed, (uint32_t)(seed >> 32), d_out, n, st) != cudaSuccess ||
         cudaMemcpyAsync(out, d_out, n * sizeof(uint4), cudaMemcpyDefault, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         s = MPR_ECUDA;
-    cudaFree(d_in);
-    cudaFree(d_out);
+    dfree(d_in, st);
+    dfree(d_out, st);
     return s;
 }
 

@@ -78,6 +78,7 @@ _SIGS = [
     ("mpr_get_info", _I, [_VP] + [ctypes.POINTER(_D)] * 6),
     ("mpr_time_sweeps", _I, [_VP, _I, _D, ctypes.POINTER(_D)]),
     ("mpr_kernel_launches", ctypes.c_uint64, []),
+    ("mpr_release_memory", _I, []),
     ("mpr_sample_energy_static", _I, [_VP, _VP, _I, _I, _D, ctypes.POINTER(_D),
                                       ctypes.POINTER(ctypes.c_longlong), _VP]),
     ("mpr_philox", _I, [_VP, ctypes.c_uint64, _VP, ctypes.c_size_t, _VP]),
@@ -297,6 +298,12 @@ def mpr_sample_energy_static(z, mask, W: int, H: int, q: float = 0.5, stream=Non
 
 def mpr_kernel_launches() -> int:
     return int(lib().mpr_kernel_launches())
+
+
+def mpr_release_memory():
+    """Hands the device memory kept by the library's pool (from released contexts) back
+    to the driver."""
+    _check(None, lib().mpr_release_memory())
 
 
 def mpr_philox(ctr, seed: int, out, stream=None):

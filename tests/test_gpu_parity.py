@@ -316,3 +316,28 @@ def test_runs_are_bitwise_reproducible():
         finally:
             mpr.mpr_free(ctx)
     assert np.array_equal(outs[0], outs[1])
+
+
+def test_pooled_memory_reuse_and_release():
+    # contexts take device memory from the library's pool: a context built on memory that
+    # a released context left behind, and one built after the pool was handed back to
+    # the driver, give bitwise the same states as the first one
+    c = synth.config("grid64")
+    H, W = c["z"].shape
+
+    def states():
+        ctx = make_ctx(c["z"], c["mask"], seed=9)
+        try:
+            mpr.mpr_set_T(ctx, 0.2)
+            mpr.mpr_sweep(ctx, 5, 3.0)
+            phi = np.zeros((H, W), np.float32)
+            mpr.mpr_get_state(ctx, phi)
+        finally:
+            mpr.mpr_free(ctx)
+        return phi
+
+    first = states()
+    assert np.array_equal(states(), first)
+    mpr.mpr_release_memory()
+    assert np.array_equal(states(), first)
+    mpr.mpr_release_memory()
