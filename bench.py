@@ -115,8 +115,8 @@ class ClockSampler:
 
 # DRAM bytes per launch of k_tile_sweep on this grid from one ncu capture
 # (profiles/k_tile_sweep_4096.md), valid for the kernel sources with this hash only.
-TILE_TRAFFIC_BYTES = 243.8e6
-TILE_TRAFFIC_SOURCE_HASH = "f151b74d83f9cbc6"
+TILE_TRAFFIC_BYTES = 253.8e6
+TILE_TRAFFIC_SOURCE_HASH = "5ef1a45cbc4665d7"
 
 
 def tile_kernel_hash():
@@ -137,9 +137,9 @@ def measured_peaks():
 
 
 def cpu_baseline(z, mask, T):
-    """The FP64 oracle, single-threaded, on a 512 x 512 crop of the same workload."""
+    """The FP64 oracle, single-threaded, on a 1024 x 1024 crop of the same workload."""
     import oracle.oracle as orc
-    c = 512
+    c = 1024
     zc = np.ascontiguousarray(z[:c, :c])
     mc = np.ascontiguousarray(mask[:c, :c])
     prm = orc.params(seed=0, M=M)
@@ -148,7 +148,7 @@ def cpu_baseline(z, mask, T):
     dt = time.perf_counter() - t0
     updates = out.n_gap * (out.eq.sweeps + M)
     return {"value": updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"512x512 crop of the step's grid, fixed T-hat, slope-test relaxation "
+            "sample": f"1024x1024 crop of the step's grid, fixed T-hat, slope-test relaxation "
                       f"({out.eq.sweeps} sweeps) + M={M}, {updates} site-updates in {dt:.1f} s"}
 
 
@@ -569,6 +569,15 @@ def main():
         sweep_ms = mpr.mpr_time_sweeps(ctx, 20, 8.0)
     finally:
         mpr.mpr_free(ctx)
+    # the same sweep with the fast transcendentals (__sincosf, ex2.approx), for reference
+    ctx = mpr.mpr_init(z, mask, W, H, mpr.mpr_default_params(seed=1 + rank, M=M, trig_mode=mpr.MPR_TRIG_FAST,
+                                                             tile_cfg=prm.tile_cfg), stream.cuda_stream)
+    try:
+        mpr.mpr_set_T(ctx, T)
+        mpr.mpr_sweep(ctx, 50, 8.0)
+        sweep_ms_fast = mpr.mpr_time_sweeps(ctx, 20, 8.0)
+    finally:
+        mpr.mpr_free(ctx)
     N = H * W
     P = int(m_np.size - m_np.sum())
     # algorithmic bytes of one sweep: read every site's vector once (8 B), write every gap
@@ -592,6 +601,7 @@ def main():
                        "s_per_map": dev_ms * 1e-3 / args.steps,
                        "T_table": f"built once per shape during warm-up ({table_s:.2f} s incl. one fill)",
                        "tile_cfg": tune["tile_cfg"], "autotune_ms_per_sweep": tune["ms_per_sweep"],
+                       "trig": "accurate (Taylor sincos, expf); fast-trig sweep in roofline.ms_per_launch_fast",
                        "l2": "512 MB buffer written between steps (L2 flush)",
                        "parallelism": f"replicas{world}"},
             "e2e": {"value": e2e_updates / (e2e_ms * 1e-3), "unit": UNIT,
@@ -601,6 +611,7 @@ def main():
                          "frac": achieved / hbm,
                          "traffic": TILE_TRAFFIC_BYTES if tile_kernel_hash() == TILE_TRAFFIC_SOURCE_HASH else None,
                          "kernel": "k_tile_sweep", "ms_per_launch": sweep_ms,
+                         "ms_per_launch_fast": sweep_ms_fast,
                          "peak_source": f"{peak_src} hbm_gbs",
                          "bytes_per_launch": bytes_per_launch},
             "clocks": clk,
