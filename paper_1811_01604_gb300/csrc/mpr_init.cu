@@ -146,29 +146,41 @@ __global__ void k_gap_scatter(EntryDesc e, const uint8_t* __restrict__ mask, int
 // cos(q (phi_i - phi_j)), with phi_i - phi_j = (z_i - z_j) * 2pi / (z_max - z_min).
 // Each block writes its partial sums; they are added in block order afterwards.
 __global__ void k_sample_energy(EntryDesc e, const float* __restrict__ z,
-                                const uint8_t* __restrict__ mask, double scale, double q,
+                                const uint8_t* __restrict__ mask, float qs,
                                 double* part_sum, unsigned long long* part_cnt) {
+    // Eq. 4 pairs (each unordered sample pair once: right and down neighbours), rows
+    // block-strided and columns thread-strided (no index division).  The cosine argument
+    // q (z_i - z_j) 2 pi / (z_max - z_min) is formed in FP32 (one rounding of the scale,
+    // one of the difference, one of the product: ~1e-7 rad), each row's terms are summed
+    // in FP32 and the rows in FP64.
     __shared__ double ssum[kThreads / 32];
-    __shared__ unsigned scnt[kThreads / 32];
-    const long long n = (long long)e.W * e.H;
+    __shared__ unsigned long long scnt[kThreads / 32];
     double acc = 0.0;
-    unsigned cnt = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        if (!mask[i]) continue;
-        const int y = (int)(i / e.W), x = (int)(i - (long long)y * e.W);
-        const double zi = (double)z[i];
-        if (x + 1 < e.W && mask[i + 1]) {
-            acc += (double)cosf((float)(q * ((zi - (double)z[i + 1]) * scale)));
-            ++cnt;
+    unsigned long long cnt = 0;
+    for (int y = blockIdx.x; y < e.H; y += gridDim.x) {
+        const float* __restrict__ zr = z + (long long)y * e.W;
+        const uint8_t* __restrict__ mr = mask + (long long)y * e.W;
+        const bool down = y + 1 < e.H;
+        float row = 0.0f;
+        unsigned rc = 0;
+        for (int x = threadIdx.x; x < e.W; x += blockDim.x) {
+            if (!mr[x]) continue;
+            const float zi = zr[x];
+            if (x + 1 < e.W && mr[x + 1]) {
+                row += cosf(qs * (zi - zr[x + 1]));
+                ++rc;
+            }
+            if (down && mr[x + e.W]) {
+                row += cosf(qs * (zi - zr[x + e.W]));
+                ++rc;
+            }
         }
-        if (y + 1 < e.H && mask[i + e.W]) {
-            acc += (double)cosf((float)(q * ((zi - (double)z[i + e.W]) * scale)));
-            ++cnt;
-        }
+        acc += (double)row;
+        cnt += rc;
     }
     acc = warp_sum(acc);
-    cnt = warp_sum(cnt);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     if ((threadIdx.x & 31) == 0) {
         ssum[threadIdx.x >> 5] = acc;
         scnt[threadIdx.x >> 5] = cnt;
@@ -240,11 +252,10 @@ cudaError_t launch_gap_scatter(const EntryDesc* e, const uint8_t* mask, int all_
 cudaError_t launch_sample_energy(const EntryDesc* e, const float* z, const uint8_t* mask,
                                  double scale, double q, double* part_sum,
                                  unsigned long long* part_cnt, int* nparts, cudaStream_t st) {
-    int g = grid_for((long long)e->W * e->H);
-    if (g > 1024) g = 1024;
+    const int g = e->H < 1024 ? e->H : 1024;
     *nparts = g;
     count_launches(1, st);
-    k_sample_energy<<<g, kThreads, 0, st>>>(*e, z, mask, scale, q, part_sum, part_cnt);
+    k_sample_energy<<<g, kThreads, 0, st>>>(*e, z, mask, (float)(q * scale), part_sum, part_cnt);
     return cudaGetLastError();
 }
 

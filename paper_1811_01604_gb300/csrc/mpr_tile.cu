@@ -465,7 +465,7 @@ k_tile_sweep(const TileArgs A) {
             const long long pl0 = sp[st].pl0, pl1 = sp[st].pl1;
             float2* __restrict__ dst = g3.w ? A.lat[0] : A.lat[1];
             constexpr int V = TW / 4;
-#pragma unroll 2
+#pragma unroll
             for (int i = threadIdx.x; i < 2 * TH * V; i += NT) {
                 const int c = i / (TH * V), rr = (i / V) % TH, v = i % V;
                 if (rr < rows && v < nv) {
