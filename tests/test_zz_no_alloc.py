@@ -2,7 +2,9 @@
 
 mpr_sample_energy_static serves callers that may not allocate device memory; it keeps its
 scratch in one fixed device array shared by all calls.  Two calls in a row on different
-inputs (and a repeat of the first) must each agree with e_s as mpr_init computes it.
+inputs (and a repeat of the first) must each agree with e_s as mpr_init computes it,
+within the relative 1e-6 that the parity tests allow Eq. 4 energies (mpr_init forms the
+cosine arguments in FP32, this entry point in FP64).
 """
 import numpy as np
 import pytest
@@ -42,7 +44,7 @@ def test_static_sample_energy_matches_allocating_path_on_consecutive_calls():
         cases.append((e_s, n_pairs, _allocating_e_s(z, m), _pairs(m)))
     for e_s, n_pairs, ref, ref_pairs in cases:
         assert n_pairs == ref_pairs
-        assert abs(e_s / ref - 1) < 1e-12
+        assert abs(e_s / ref - 1) < 1e-6
     assert cases[0][0] == cases[2][0]            # the shared scratch keeps no state
 
 
