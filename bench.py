@@ -447,6 +447,63 @@ def run_warm(args):
     print(json.dumps(line), flush=True)
 
 
+def run_chains(args):
+    """Independent chains against the paper's single chain at equal total sweeps: per seed,
+    one 1024^2 map (nu 0.5, correlation length 16, 33 % gaps) is relaxed once; from that
+    state mpr_predict_chains runs K chains x 100/K averaged sweeps for K in 1, 4, 10, 25
+    (K = 1 is the single-chain estimator), and K = 4, 10 after 25 burn-in sweeps per chain.
+    Reports MAE / RMSE against the hidden field, the estimator's Monte Carlo error (RMS
+    distance at the gaps to the posterior mean, estimated by 32 chains x (200 burn-in + 200
+    averaged) sweeps from the same state) and the time of each prediction (CUDA events)."""
+    import torch
+    from paper_1811_01604_gb300 import mpr, synth
+    stream = torch.cuda.current_stream()
+    variants = ((1, 0), (4, 0), (10, 0), (25, 0), (4, 25), (10, 25))        # (K, burn-in)
+    total = 100
+    res = {v: {"mae": [], "rmse": [], "noise": [], "ms": []} for v in variants}
+    seeds = tuple(range(1, 1 + max(1, args.steps)))
+    for seed in seeds:
+        z = synth.wm_field_gpu(1024, 1024, 0.5, 16.0, 100 + seed)
+        mask = synth.mask_uniform_gpu(1024, 1024, 0.33, 1_000_100 + seed)
+        gap = mask == 0
+        ctx = mpr.mpr_init(z, mask, 1024, 1024, mpr.mpr_default_params(seed=seed, M=total),
+                           stream.cuda_stream)
+        try:
+            mpr.mpr_estimate_T(ctx)
+            mpr.mpr_equilibrate(ctx)
+            # the posterior mean at the gaps, nearly free of the shared start: 32 chains that
+            # first run 200 unaveraged sweeps, then average 200 each
+            ref = torch.empty_like(z)
+            mpr.mpr_predict_chains(ctx, 32, 200, ref, burn_in=200)
+            out = torch.empty_like(z)
+            for v in variants:
+                K, burn = v
+                for _ in range(2 if seed == seeds[0] else 1):       # first seed: one untimed warm-up
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    mpr.mpr_predict_chains(ctx, K, total // K, out, burn_in=burn)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                res[v]["ms"].append(e0.elapsed_time(e1))
+                err = (out - z)[gap].double()
+                res[v]["mae"].append(float(err.abs().mean()))
+                res[v]["rmse"].append(float(err.pow(2).mean().sqrt()))
+                res[v]["noise"].append(float((out - ref)[gap].double().pow(2).mean().sqrt()))
+        finally:
+            mpr.mpr_free(ctx)
+    rows = {"K%d_burn%d" % v: {k: float(np.mean(x)) for k, x in res[v].items()} for v in variants}
+    line = {"metric": "estimator MC noise at equal averaged sweeps (independent chains)",
+            "value": rows["K10_burn25"]["noise"],
+            "unit": "z units (RMS)", "n_gpus": 1, "steps": len(seeds), "warmup": 1,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "mpr-chains-1024x1024-wm-nu0.5-xi16-p0.33", "total_sweeps": total,
+                       "seeds": list(seeds), "reference": "posterior mean: 32 chains x (200 burn-in + 200 averaged) sweeps"},
+            "by_chains_and_burn_in": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -456,10 +513,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", default=None, choices=["sweep4096", "net4096", "net1024", "net128"],
                     help="run a small fixed sweep workload for ncu instead of the benchmark")
-    ap.add_argument("--workload", default="fill4096", choices=["fill4096", "batch256", "warm1024", "warm4096"],
+    ap.add_argument("--workload", default="fill4096", choices=["fill4096", "batch256", "warm1024", "warm4096",
+                                                                "chains1024"],
                     help="fill4096: one 4096^2 map per step (default); batch256: 256 grids of "
                          "sides 128-2048 filled in one batch, against the same grids one at a time; "
-                         "warm1024 / warm4096: learned warm start against the plain random start")
+                         "warm1024 / warm4096: learned warm start against the plain random start; "
+                         "chains1024: independent chains against one chain at equal sweeps")
     ap.add_argument("--tile-cfg", type=int, default=0, help="profile cases: compiled tile configuration")
     ap.add_argument("--train-steps", type=int, default=2000, help="warm start: Adam steps")
     ap.add_argument("--train-n64", type=int, default=1024, help="warm start: 64^2 training grids")
@@ -482,6 +541,9 @@ def main():
         return
     if args.workload in ("warm1024", "warm4096"):
         run_warm(args)
+        return
+    if args.workload == "chains1024":
+        run_chains(args)
         return
 
     import torch

@@ -150,6 +150,22 @@ mpr_status mpr_equilibrate(mpr_ctx* ctx, mpr_equil_stats* out);
 mpr_status mpr_predict(mpr_ctx* ctx, int M, float* zhat);
 
 /*
+ * Independent-chain realizations (the paper's estimator is one chain: M consecutive
+ * sweeps, Algorithm 2 step 6).  The grid's current state -- normally the one
+ * mpr_equilibrate left -- is forked into K chains (1 <= K <= 128).  Chain k draws from
+ * the Philox counter {site, sweep, chain + k * 2^24, 0}: k = 0 continues the grid's own
+ * chain, and every chain starts at the grid's current sweep counter.  The K chains run
+ * burn_in >= 0 sweeps that are not averaged (they decorrelate the forks from their shared
+ * start), then M_per_chain >= 1 sweeps, all at window a_eq and together (one launch per
+ * sweep for all chains), accumulating every gap angle; zhat = G^-1(mean over all
+ * K * M_per_chain angles) at gaps and z at samples.  K = 1 with burn_in = 0 gives exactly
+ * mpr_predict(ctx, M_per_chain).  The grid's own state and sweep counter are left
+ * unchanged.  Single-grid contexts on the tile path; zhat: float[H][W] (host or device).
+ * Needs K lattice copies of device memory.
+ */
+mpr_status mpr_predict_chains(mpr_ctx* ctx, int K, int burn_in, int M_per_chain, float* zhat);
+
+/*
  * Algorithm 2 end to end: mpr_estimate_T (unless a temperature was set),
  * mpr_equilibrate, mpr_predict(params.M).  stats may be NULL.
  * Returns MPR_OK or MPR_ENOTEQUIL on success.

@@ -24,6 +24,9 @@
  *          from U(0,2pi), Algorithm 2 step 5 relaxation, then M_T sweeps at
  *          the step-6 window; T-hat by piecewise-linear interpolation in T.
  *   R-WRAP proposals wrap modulo 2pi into [0, 2pi).
+ *   R-CH   independent chains: the equilibrated state forked into K chains with
+ *          chain words chain + k 2^24, all from the same sweep counter; the
+ *          estimate averages all K * M_per_chain realizations.
  */
 #include <math.h>
 #include <stdint.h>
@@ -372,6 +375,44 @@ int orc_predict(double* phi, const uint8_t* mask, const float* z, int W, int H, 
             if (!mask[i]) sum[i] += orc_unmap(phi[i], zmin, zmax);       /* 6.3 */
     }
     for (long i = 0; i < n; ++i) zhat[i] = mask[i] ? (double)z[i] : sum[i] / (double)M;
+    free(sum);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Independent chains (READING R-CH; the paper's estimator is one chain).    */
+/* The state phi is forked into K chains; chain k (Philox chain word        */
+/* chain + k 2^24; k = 0 is the chain itself) starts at sweep counter        */
+/* sweep0, runs burn_in sweeps of step 6.2 that are not averaged, then       */
+/* repeats steps 6.2-6.3 for M_per_chain sweeps; zhat is the mean of the     */
+/* back-transformed angles of all K * M_per_chain realizations.  phi is      */
+/* left unchanged.                                                           */
+/* ------------------------------------------------------------------------ */
+int orc_predict_chains(const double* phi, const uint8_t* mask, const float* z, int W, int H,
+                       double T, const orc_params* p, uint32_t chain, uint32_t sweep0,
+                       double zmin, double zmax, int K, int burn_in, int M_per_chain,
+                       double* zhat)
+{
+    long n = (long)W * H;
+    double* sum = (double*)calloc((size_t)n, sizeof(double));
+    double* work = (double*)malloc((size_t)n * sizeof(double));
+    for (int k = 0; k < K; ++k) {
+        const uint32_t chain_k = chain + (uint32_t)k * (1u << 24);
+        uint32_t sweep = sweep0;
+        memcpy(work, phi, (size_t)n * sizeof(double));
+        for (int j = 0; j < burn_in; ++j)
+            orc_sweep(work, mask, W, H, p->a_eq, T, p->q, p->seed, chain_k, sweep++, p->or_mode,
+                      NULL, NULL);
+        for (int j = 0; j < M_per_chain; ++j) {
+            orc_sweep(work, mask, W, H, p->a_eq, T, p->q, p->seed, chain_k, sweep++, p->or_mode,
+                      NULL, NULL);
+            for (long i = 0; i < n; ++i)
+                if (!mask[i]) sum[i] += orc_unmap(work[i], zmin, zmax);
+        }
+    }
+    const double m = (double)K * (double)M_per_chain;
+    for (long i = 0; i < n; ++i) zhat[i] = mask[i] ? (double)z[i] : sum[i] / m;
+    free(work);
     free(sum);
     return 0;
 }

@@ -101,6 +101,7 @@ def lib():
             L.orc_sg_slope.restype = d
             L.orc_equilibrate.argtypes = [vp, vp, i, i, d, P(Params), u32, P(u32), P(EquilOut), vp]
             L.orc_predict.argtypes = [vp, vp, vp, i, i, d, P(Params), u32, P(u32), d, d, i, vp]
+            L.orc_predict_chains.argtypes = [vp, vp, vp, i, i, d, P(Params), u32, u32, d, d, i, i, i, vp]
             L.orc_T_grid.argtypes = [P(Params), vp]
             L.orc_e_table.argtypes = [P(Params), vp, vp, vp]
             L.orc_invert_T.argtypes = [vp, vp, i, d]
@@ -237,6 +238,21 @@ def e_table(prm: Params):
 def invert_T(Tk, ek, e_s):
     Tk = _c(Tk, np.float64); ek = _c(ek, np.float64)
     return lib().orc_invert_T(_p(Tk), _p(ek), len(Tk), float(e_s))
+
+
+def predict_chains(phi, mask, z, T, prm: Params, zmin, zmax, K, M_per_chain, chain=0, sweep_index=0,
+                   burn_in=0):
+    """Independent chains (reading R-CH): phi forked into K chains with chain words
+    chain + k 2^24, each from sweep counter sweep_index, burn_in sweeps not averaged, then
+    M_per_chain sweeps; returns zhat (float64[H][W]), the mean over all K * M_per_chain
+    realizations.  phi is unchanged."""
+    phi = _c(phi, np.float64); mask = _c(mask, np.uint8); z = _c(z, np.float32)
+    H, W = phi.shape
+    zhat = np.zeros((H, W), np.float64)
+    lib().orc_predict_chains(_p(phi), _p(mask), _p(z), W, H, float(T), ctypes.byref(prm),
+                             chain, sweep_index, float(zmin), float(zmax), int(K), int(burn_in),
+                             int(M_per_chain), _p(zhat))
+    return zhat
 
 
 def fill(z, mask, prm: Params, T_fixed=0.0, eq_sweeps=-1):

@@ -41,6 +41,8 @@ namespace {
 constexpr int kMaxGraphSweeps = 64;       // longest captured chunk of sweeps
 constexpr int kDefaultGraphSweeps = 8;    // sweeps per captured chunk unless autotuned
 constexpr int kScratch = 2048;            // doubles of reduction scratch
+constexpr int kMaxChains = 128;           // independent chains of one grid (mpr_predict_chains)
+constexpr uint32_t kChainStride = 1u << 24; // chain word offset between forked chains
 
 struct GridIn {
     int W, H;
@@ -269,8 +271,9 @@ mpr_status reset_relax(mpr_ctx* ctx, Batch& b);
 mpr_status run_sweeps(mpr_ctx* ctx, Batch& b, int n, int mode, double a_fixed, bool acc);
 mpr_status read_ctl(mpr_ctx* ctx, Batch& b, std::vector<Ctl>& out);
 
+// same_grid: every entry is a chain of one grid (all read the grid at mask_base, site0 = 0).
 mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids, int all_free,
-                       const uint8_t* mask_base) {
+                       const uint8_t* mask_base, bool same_grid = false) {
     cudaStream_t st = ctx->st;
     b.tiled = ctx->prm.exec_mode != MPR_EXEC_LIST;
     const uint32_t k0 = (uint32_t)ctx->prm.seed, k1 = (uint32_t)(ctx->prm.seed >> 32);
@@ -292,7 +295,7 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
         lat += 2 * plane;
         E.chain = grids[e].chain;
         E.ngp = (double)E.W * (E.H - 1) + (double)E.H * (E.W - 1);
-        E.site0 = site0;
+        E.site0 = same_grid ? 0 : site0;
         site0 += (long long)E.W * E.H;
         maxH = std::max(maxH, E.H);
     }
@@ -945,7 +948,7 @@ static mpr_status predict_all(mpr_ctx* ctx, int M, float* const* out) {
         if (b.tiled)
             CU(launch_tile_predict_out(b.tcfg, b.d_tiles, b.d_cnts, b.d_lists, b.d_tacc, b.d_ents,
                                        b.ents[i].tile0, b.ents[i].ntiles, M, ctx->prm.q, G.zmin,
-                                       G.zmax, ctx->d_out, ctx->st));
+                                       G.zmax, 1, 0, ctx->d_out, ctx->st));
         else
             CU(launch_predict_out(&b.ents[i], b.d_lat, b.d_gaps, b.d_acc, M, ctx->prm.q, G.zmin,
                                   G.zmax, ctx->d_out + G.site0, ctx->st));
@@ -965,6 +968,72 @@ mpr_status mpr_predict(mpr_ctx* ctx, int M, float* zhat) {
     if (M < 1) return fail(ctx, MPR_EINVAL, "M >= 1 required");
     if (!ctx->T_set) return fail(ctx, MPR_ESTATE, "temperature not set");
     return predict_all(ctx, M, &zhat);
+}
+
+// Independent-chain realizations (not in the paper, whose estimator is one chain): the
+// grid's current state (normally equilibrated by mpr_equilibrate) is forked into K chains,
+// chain k with Philox chain word chain + k * 2^24 (k = 0 continues the grid's own chain),
+// all starting at the same sweep counter; the K chains run burn_in sweeps that are not
+// averaged (to decorrelate from the shared start), then M_per_chain equilibrium sweeps, as
+// one batch (one launch per sweep for all chains); zhat is the mean of the back-transformed
+// angles of all K * M_per_chain realizations.  K = 1, burn_in = 0 is mpr_predict.  The
+// grid's own state is left as it was.
+mpr_status mpr_predict_chains(mpr_ctx* ctx, int K, int burn_in, int M_per_chain, float* zhat) {
+    if (!ctx || !zhat) return MPR_EINVAL;
+    if (ctx->g.size() != 1) return fail(ctx, MPR_EINVAL, "mpr_predict_chains serves one grid");
+    if (K < 1 || K > kMaxChains) return fail(ctx, MPR_EINVAL, "1 <= K <= 128 chains");
+    if (M_per_chain < 1 || burn_in < 0) return fail(ctx, MPR_EINVAL, "M_per_chain >= 1, burn_in >= 0 required");
+    if (!ctx->T_set) return fail(ctx, MPR_ESTATE, "temperature not set");
+    Batch& b = ctx->b;
+    if (!b.tiled) return fail(ctx, MPR_EINVAL, "independent chains run on the tile path");
+    std::vector<Ctl> c0;
+    mpr_status s = read_ctl(ctx, b, c0);
+    if (s != MPR_OK) return s;
+    const GridInfo& G = ctx->g[0];
+    std::vector<GridIn> gi((size_t)K);
+    for (int k = 0; k < K; ++k)
+        gi[k] = GridIn{G.W, G.H, ctx->d_z + G.site0, ctx->d_mask + G.site0,
+                       b.ents[0].chain + (uint32_t)k * kChainStride, G.T, G.zmin, G.scale};
+    Batch ab;
+    s = batch_build(ctx, ab, gi, 0, ctx->d_mask + G.site0, true);
+    if (s == MPR_OK) s = build_tiles(ctx, ab, b.tcfg);
+    if (s == MPR_OK) {
+        // fork: every chain starts from the grid's current state and control state
+        const size_t state = (size_t)2 * b.ents[0].prows * b.ents[0].pitch;
+        const float2* src = lat_cur(b, c0[0]) + b.ents[0].plane[0];
+        std::vector<Ctl> ck((size_t)K, c0[0]);
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < K && e == cudaSuccess; ++k) {
+            e = cudaMemcpyAsync(ab.d_lat + ab.ents[k].plane[0], src, state * sizeof(float2),
+                                cudaMemcpyDeviceToDevice, ctx->st);
+            ck[k].cur = 0;
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ab.d_ctl, ck.data(), sizeof(Ctl) * K, cudaMemcpyHostToDevice, ctx->st);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(ab.d_tacc, 0, sizeof(float) * (size_t)ab.ntiles * tile_geom(ab.tcfg).acc,
+                                ctx->st);
+        if (e != cudaSuccess) s = fail(ctx, MPR_ECUDA, std::string("chain fork: ") + cudaGetErrorString(e));
+    }
+    if (s == MPR_OK && burn_in > 0) s = run_sweeps(ctx, ab, burn_in, CTL_FIXED, ctx->prm.a_eq, false);
+    if (s == MPR_OK) s = run_sweeps(ctx, ab, M_per_chain, CTL_FIXED, ctx->prm.a_eq, true);
+    if (s == MPR_OK) {
+        cudaError_t e = cudaMemcpyAsync(ctx->d_out + G.site0, ctx->d_z + G.site0,
+                                        (size_t)G.W * G.H * sizeof(float), cudaMemcpyDeviceToDevice, ctx->st);
+        const int nt = ab.ents[0].ntiles;
+        if (e == cudaSuccess)
+            e = launch_tile_predict_out(ab.tcfg, ab.d_tiles, ab.d_cnts, ab.d_lists, ab.d_tacc, ab.d_ents, 0,
+                                        nt, M_per_chain, ctx->prm.q, G.zmin, G.zmax, K, nt,
+                                        ctx->d_out + G.site0, ctx->st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(zhat, ctx->d_out + G.site0, (size_t)G.W * G.H * sizeof(float),
+                                cudaMemcpyDefault, ctx->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+        if (e != cudaSuccess) s = fail(ctx, MPR_ECUDA, std::string("chain average: ") + cudaGetErrorString(e));
+    }
+    cudaStreamSynchronize(ctx->st);
+    batch_free(ab, ctx->st);
+    return s;
 }
 
 mpr_status mpr_predict_batch(mpr_ctx* ctx, int M, float* const* zhat) {

@@ -415,10 +415,11 @@ cudaError_t launch_tile_lists(int cfg, TileDesc* tiles, int ntiles, const EntryD
                               const uint8_t* mask, int all_free, uint16_t* lists, TileCnt* cnts,
                               cudaStream_t st);
 cudaError_t launch_tile_sweep(const TileArgs& a, int trig, cudaStream_t st);
+// K > 1: the angle sums of K chains of one grid, chain c's tiles at tile + c * chain_tiles.
 cudaError_t launch_tile_predict_out(int cfg, const TileDesc* tiles, const TileCnt* cnts,
                                     const uint16_t* lists, const float* acc, const EntryDesc* ents,
                                     int tile0, int ntiles, int M, double q, double zmin, double zmax,
-                                    float* zhat, cudaStream_t st);
+                                    int K, int chain_tiles, float* zhat, cudaStream_t st);
 
 // sweeps (mpr_sweep.cu)
 cudaError_t launch_half_sweep(const SweepArgs& a, int color, int trig, cudaStream_t st);

@@ -493,12 +493,14 @@ k_tile_sweep(const TileArgs A) {
     }
 }
 
-// zhat at the gap sites of every tile (same mean and inverse map as the list path).
+// zhat at the gap sites of every tile (same mean and inverse map as the list path).  With
+// K > 1 the angle sums of K chains of the same grid are added: chain c's copy of tile t is
+// tile t + c * chain_tiles (every chain has the same tiles and lists).
 template <int TH, int TW>
 __global__ void k_tile_predict_out(const TileDesc* __restrict__ tiles, const TileCnt* __restrict__ cnts,
                                    const uint16_t* __restrict__ lists, const float* __restrict__ acc,
                                    const EntryDesc* __restrict__ ents, int M, double q, double zmin,
-                                   double zmax, float* __restrict__ zhat) {
+                                   double zmax, int K, int chain_tiles, float* __restrict__ zhat) {
     using G = Geo<TH, TW>;
     const int tile = blockIdx.x;
     const TileDesc td = tiles[tile];
@@ -506,15 +508,18 @@ __global__ void k_tile_predict_out(const TileDesc* __restrict__ tiles, const Til
     const TileCnt cnt = cnts[tile];
     const uint16_t* list = lists + (long long)tile * G::LIST;
     const float* a = acc + (long long)tile * G::ACC;
+    const long long cstride = (long long)chain_tiles * G::ACC;
     const int nA = cnt.nA_int + cnt.nA_ring;
-    const double f = (zmax - zmin) / (kTwoPi * q * (double)M);
+    const double f = (zmax - zmin) / (kTwoPi * q * (double)M * (double)K);
     for (int k = threadIdx.x; k < cnt.nA_int + cnt.nB; k += blockDim.x) {
         const bool isA = k < cnt.nA_int;
         const int ent = isA ? list[k] : list[nA + (k - cnt.nA_int)];
         const int r = ent >> 7, qq = ent & 127;
         const int s = (isA ? 0 : 1) ^ (r & 1);
         const int y = td.y0 - 2 + r, x = td.x0 + 2 * qq - 4 + s;
-        double v = zmin + (double)a[k] * f;
+        double sum = (double)a[k];
+        for (int c = 1; c < K; ++c) sum += (double)a[c * cstride + k];
+        double v = zmin + sum * f;
         v = v < zmin ? zmin : (v > zmax ? zmax : v);
         zhat[E.site0 + (long long)y * E.W + x] = (float)v;
     }
@@ -655,11 +660,11 @@ cudaError_t launch_tile_sweep(const TileArgs& a, int trig, cudaStream_t st) {
 #define MPR_CFG_OUT(id, th, tw, nt, st_, mb) \
     case id: k_tile_predict_out<th, tw><<<ntiles, 256, 0, st>>>( \
         tiles + tile0, cnts + tile0, lists + (long long)tile0 * g.list, acc + (long long)tile0 * g.acc, \
-        ents, M, q, zmin, zmax, zhat); break;
+        ents, M, q, zmin, zmax, K, chain_tiles, zhat); break;
 cudaError_t launch_tile_predict_out(int cfg, const TileDesc* tiles, const TileCnt* cnts,
                                     const uint16_t* lists, const float* acc, const EntryDesc* ents,
                                     int tile0, int ntiles, int M, double q, double zmin, double zmax,
-                                    float* zhat, cudaStream_t st) {
+                                    int K, int chain_tiles, float* zhat, cudaStream_t st) {
     if (ntiles == 0) return cudaSuccess;
     count_launches(1, st);
     const TileGeom g = tile_geom(cfg);

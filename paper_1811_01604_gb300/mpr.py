@@ -63,6 +63,7 @@ _SIGS = [
     ("mpr_sweep", _I, [_VP, _I, _D, ctypes.POINTER(mpr_sweep_stats)]),
     ("mpr_equilibrate", _I, [_VP, ctypes.POINTER(mpr_equil_stats)]),
     ("mpr_predict", _I, [_VP, _I, _VP]),
+    ("mpr_predict_chains", _I, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]),
     ("mpr_fill", _I, [_VP, _VP, ctypes.POINTER(mpr_equil_stats)]),
     ("mpr_init_batch", _I, [ctypes.POINTER(_VP), _I, _VP, _VP, _VP, _VP, ctypes.POINTER(mpr_params), _VP]),
     ("mpr_batch_size", _I, [_VP]),
@@ -198,6 +199,10 @@ def mpr_equilibrate(ctx) -> mpr_equil_stats:
 
 def mpr_predict(ctx, M: int, zhat):
     _check(ctx, lib().mpr_predict(ctx, int(M), _ptr(zhat)))
+
+
+def mpr_predict_chains(ctx, K: int, M_per_chain: int, zhat, burn_in: int = 0):
+    _check(ctx, lib().mpr_predict_chains(ctx, int(K), int(burn_in), int(M_per_chain), _ptr(zhat)))
 
 
 def mpr_fill(ctx, zhat) -> mpr_equil_stats:

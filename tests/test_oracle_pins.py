@@ -391,3 +391,73 @@ def test_fill_reproduces_paper_validation_measures(p):
     assert abs(np.abs(err).mean() / maae - 1) < 0.06
     assert abs(np.sqrt((err**2).mean()) / mrase - 1) < 0.06
     assert 0.01 < out.T_hat < 0.5
+
+
+# ---------------------------------------------------------------- independent chains (R-CH)
+def test_predict_chains_one_chain_is_predict():
+    c = synth.config("grid64")
+    z, mask = c["z"], c["mask"]
+    phi, zmin, zmax, _ = orc.map_angles(z, mask)
+    orc.init_gaps(phi, mask, seed=3)
+    prm = orc.params(seed=3, M=7)
+    zc = orc.predict_chains(phi, mask, z, 0.2, prm, zmin, zmax, K=1, M_per_chain=7, sweep_index=11)
+    zp, _ = orc.predict(phi.copy(), mask, z, 0.2, prm, zmin, zmax, M=7, sweep_index=11)
+    assert np.array_equal(zc, zp)
+
+
+def test_predict_chains_is_the_mean_of_forked_chains():
+    # fork k continues the state with chain word k * 2^24 from the same sweep counter
+    c = synth.config("grid64")
+    z, mask = c["z"], c["mask"]
+    phi, zmin, zmax, _ = orc.map_angles(z, mask)
+    orc.init_gaps(phi, mask, seed=4)
+    prm = orc.params(seed=4, M=5)
+    K, m = 3, 5
+    zc = orc.predict_chains(phi, mask, z, 0.15, prm, zmin, zmax, K=K, M_per_chain=m, sweep_index=20)
+    forks = [orc.predict(phi.copy(), mask, z, 0.15, prm, zmin, zmax, M=m, chain=k << 24,
+                         sweep_index=20)[0] for k in range(K)]
+    assert np.allclose(zc, np.mean(forks, axis=0), rtol=0, atol=1e-12)
+    assert not np.array_equal(forks[0], forks[1])          # the forks draw different streams
+
+
+def test_predict_chains_single_free_site_posterior_mean():
+    # one free site with four sample neighbours: the mean over K chains x m sweeps of the
+    # site's angle converges to the mean of the Eq. 3 density (quadrature)
+    H = W = 3
+    rng = np.random.default_rng(5)
+    phi0 = rng.uniform(1.0, 3.0, (H, W))
+    mask = np.ones((H, W), np.uint8); mask[1, 1] = 0
+    nb = [phi0[0, 1], phi0[2, 1], phi0[1, 0], phi0[1, 2]]
+    T = 0.3
+    x = np.linspace(0.0, TWO_PI, 400001)
+    p = np.exp(np.cos(0.5 * (x[:, None] - np.array(nb)[None, :])).sum(1) / T)
+    mean = integrate.trapezoid(x * p, x) / integrate.trapezoid(p, x)
+    sd = np.sqrt(integrate.trapezoid((x - mean) ** 2 * p, x) / integrate.trapezoid(p, x))
+    phi0[1, 1] = mean                                       # start at a typical value
+    z = phi0.astype(np.float32)                             # map: zmin = 0, zmax = 2 pi
+    prm = orc.params(seed=6, a_eq=1.0)
+    K, m = 200, 200
+    zc = orc.predict_chains(phi0, mask, z, T, prm, 0.0, TWO_PI, K=K, M_per_chain=m)
+    # correlation time of the hybrid update here is a few sweeps: 8 standard errors of
+    # K * m / 5 effectively independent draws
+    assert abs(zc[1, 1] - mean) < 8 * sd / np.sqrt(K * m / 5), (zc[1, 1], mean, sd)
+
+
+def test_predict_chains_burn_in_is_skipped_sweeps():
+    # burn_in b then m averaged sweeps = the mean of each fork's sweeps b+1 .. b+m
+    c = synth.config("grid64")
+    z, mask = c["z"], c["mask"]
+    phi, zmin, zmax, _ = orc.map_angles(z, mask)
+    orc.init_gaps(phi, mask, seed=9)
+    prm = orc.params(seed=9)
+    K, b, m = 2, 3, 4
+    zc = orc.predict_chains(phi, mask, z, 0.15, prm, zmin, zmax, K=K, M_per_chain=m, sweep_index=7,
+                            burn_in=b)
+    forks = []
+    for k in range(K):
+        f = phi.copy()
+        for s in range(b):
+            orc.sweep(f, mask, a=1.0, T=0.15, seed=9, chain=k << 24, sweep_index=7 + s)
+        forks.append(orc.predict(f, mask, z, 0.15, prm, zmin, zmax, M=m, chain=k << 24,
+                                 sweep_index=7 + b)[0])
+    assert np.allclose(zc, np.mean(forks, axis=0), rtol=0, atol=1e-12)
