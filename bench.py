@@ -342,7 +342,7 @@ def run_warm(args):
     sets = [warmstart.equilibrium_states(z, m, states_per_grid=4, spacing=20, seed=20_000) for z, m in groups]
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
-    net = warmstart.WarmStartNet(seed=0)
+    net = warmstart.WarmStartNet(seed=0, stride=args.warm_stride)
     t0 = time.perf_counter()
     losses = warmstart.train(net, sets, steps=args.train_steps, batch=32, lr=1e-3, seed=0)
     torch.cuda.synchronize()
@@ -415,7 +415,8 @@ def run_warm(args):
         mpr.mpr_free(ctx)
     clk = clocks.stop()
     inf_ms = statistics.median(inf)
-    Hp, Wp = (H + 7) // 8 * 8, (W + 7) // 8 * 8
+    S = args.warm_stride
+    Hp, Wp = ((H + S - 1) // S + 7) // 8 * 8, ((W + S - 1) // S + 7) // 8 * 8      # network frame
     flops = net_flops_per_site() * Hp * Wp
     peaks, src = measured_peaks()
     peak = float(peaks.get("bf16_tflops", 1900.0))
@@ -426,6 +427,7 @@ def run_warm(args):
             "ms_per_step": statistics.mean(ms_w), "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 lattice, bf16 network", "data": "synthetic",
             "config": {"workload": wl, "W": W, "H": H, "gap_sites": P, "M": M,
+                       "net_stride": S, "net_frame": [Hp, Wp],
                        "l2": "512 MB buffer written between steps (L2 flush)",
                        "train": {"states": n_states, "steps": args.train_steps, "batch": "32 x 128^2 sites",
                                  "groups": [list(st.z.shape) for st in sets],
@@ -521,6 +523,8 @@ def main():
                          "chains1024: independent chains against one chain at equal sweeps")
     ap.add_argument("--tile-cfg", type=int, default=0, help="profile cases: compiled tile configuration")
     ap.add_argument("--train-steps", type=int, default=2000, help="warm start: Adam steps")
+    ap.add_argument("--warm-stride", type=int, default=2, choices=[1, 2],
+                    help="warm start: sites per network pixel along each axis")
     ap.add_argument("--train-n64", type=int, default=1024, help="warm start: 64^2 training grids")
     ap.add_argument("--train-n128", type=int, default=4096, help="warm start: 128^2 training crops")
     ap.add_argument("--train-n256", type=int, default=1024,

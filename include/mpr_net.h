@@ -27,7 +27,7 @@
  * Conventions: as in mpr.h.  z (float), mask (uint8, 1 = sample) and phi_target
  * (float, radians in [0, 2 pi)) are [B][H][W] device arrays (B images of one
  * shape, contiguous); zmin, zmax are B doubles (host or device).  H and W are
- * positive multiples of 8, 1 <= B <= 4096.  All work is enqueued on the stream
+ * positive multiples of 8 x stride (see mpr_net_create_strided), 1 <= B <= 4096.  All work is enqueued on the stream
  * given at creation; calls that return host values synchronise it.  A network is
  * not thread-safe.  Its activation workspace is sized for the last (B, H, W)
  * and reallocated when that changes.
@@ -48,6 +48,16 @@ typedef struct mpr_net mpr_net;
 /* A new network with He-initialised weights drawn from seed (host PRNG).
    ENOMEM / ECUDA on device failure; *net is NULL then. */
 mpr_status mpr_net_create(mpr_net** net, uint64_t seed, void* cuda_stream);
+/* The same at stride 1 or 2 (mpr_net_create is stride 1).  At stride S the network works
+   on a frame S times coarser along each axis: frame pixel (Y, X) stands for the S x S
+   block of sites (S Y + dy, S X + dx); its input channels are the block means of the
+   per-site input above, every gap site of the block takes the pixel's prediction, and
+   the training loss stays the mean over the gap SITES of 1 - cos(theta_0 - theta_t).
+   The network costs S^2 times less; the MCMC that follows refines the fine scale.
+   EINVAL for another stride. */
+mpr_status mpr_net_create_strided(mpr_net** net, uint64_t seed, int stride, void* cuda_stream);
+/* The network's stride (0 for NULL). */
+int mpr_net_stride(const mpr_net* net);
 void mpr_net_free(mpr_net* net);
 const char* mpr_net_last_error(const mpr_net* net);
 
@@ -72,7 +82,8 @@ mpr_status mpr_net_adam_step(mpr_net* net, float lr);
 mpr_status mpr_net_train_step(mpr_net* net, const float* z, const uint8_t* mask, const float* phi_target,
                               const double* zmin, const double* zmax, int B, int H, int W, float lr,
                               double* loss);
-/* Network output (u, v) per site: uv is float [B][H][W][2] (host or device). */
+/* Network output (u, v) per frame pixel: uv is float [B][H/S][W/S][2] at stride S
+   (host or device). */
 mpr_status mpr_net_forward(mpr_net* net, const float* z, const uint8_t* mask, const double* zmin,
                            const double* zmax, int B, int H, int W, float* uv);
 

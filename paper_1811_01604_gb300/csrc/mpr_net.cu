@@ -44,26 +44,41 @@ constexpr int kHeadC = 32;             // channels into the head
 constexpr int kMaxB = 4096;            // images per call
 
 // ---------------------------------------------------------------- elementwise kernels
-// Network input: image b of B, grid Hin x Win (contiguous images) inside an H x W frame
-// (H, W multiples of 8; the frame's extra sites read as missing samples).
+// Network input: image b of B, grid Hin x Win (contiguous images); the network frame is
+// H x W (multiples of 8) at stride S: frame pixel (Y, X) covers the S x S block of sites
+// (S Y + dy, S X + dx), and its channels are the block means of (cos theta, sin theta, 1)
+// over the block's sample sites (sites outside the grid read as missing samples).
 __global__ void k_input(const float* __restrict__ z, const uint8_t* __restrict__ mask, int B, int Hin, int Win,
-                        int H, int W, const double* __restrict__ zmin, const double* __restrict__ zmax,
+                        int H, int W, int S, const double* __restrict__ zmin, const double* __restrict__ zmax,
                         bf16* __restrict__ out) {
     const long long n = (long long)B * H * W;
+    const float inv = 1.0f / (float)(S * S);
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(p % W);
+        const int X = (int)(p % W);
         const long long r = p / W;
-        const int y = (int)(r % H);
+        const int Y = (int)(r % H);
         const int b = (int)(r / H);
         float c = 0.f, s = 0.f, m = 0.f;
-        if (y < Hin && x < Win) {
-            const long long i = ((long long)b * Hin + y) * Win + x;
-            if (mask[i]) {
-                // theta = q phi with q = 1/2 and phi of Eq. 1
-                const double th = 3.141592653589793 * ((double)z[i] - zmin[b]) / (zmax[b] - zmin[b]);
-                sincosf((float)th, &s, &c);
-                m = 1.f;
+        for (int dy = 0; dy < S; ++dy)
+            for (int dx = 0; dx < S; ++dx) {
+                const int y = S * Y + dy, x = S * X + dx;
+                if (y < Hin && x < Win) {
+                    const long long i = ((long long)b * Hin + y) * Win + x;
+                    if (mask[i]) {
+                        // theta = q phi with q = 1/2 and phi of Eq. 1
+                        const double th = 3.141592653589793 * ((double)z[i] - zmin[b]) / (zmax[b] - zmin[b]);
+                        float si, ci;
+                        sincosf((float)th, &si, &ci);
+                        c += ci;
+                        s += si;
+                        m += 1.f;
+                    }
+                }
             }
+        if (S > 1) {
+            c *= inv;
+            s *= inv;
+            m *= inv;
         }
         const __nv_bfloat162 cs = __floats2bfloat162_rn(c, s);      // .x = c (low half)
         const __nv_bfloat162 m0 = __floats2bfloat162_rn(m, 0.f);
@@ -174,27 +189,47 @@ __global__ void k_count_gaps(const uint8_t* __restrict__ mask, long long P, unsi
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt, c);
 }
 
-// circular loss on gap sites, mean over the batch's gap sites:
-//   L = 1 - (u c + v s) / |(u, v)|  with (c, s) = (cos, sin)(phi_target / 2);  and dL/d(u, v)
+// circular loss, mean over the batch's gap sites, at stride S: every gap site of the S x S
+// block of frame pixel p takes the direction of (u, v) = out[p]:
+//   sum over the block's gaps of 1 - cos(theta - theta_t) = n_g - (u Tc + v Ts) / |(u, v)|
+// with (Tc, Ts) the sum of the gaps' (cos, sin)(phi_target / 2) and n_g their number; and
+// dL/d(u, v).  (S = 1: one site per pixel.)  phi_target and mask are B x Hin x Win with
+// Hin = S H, Win = S W.
 __global__ void k_loss(const float* __restrict__ out, const float* __restrict__ phi_t, const uint8_t* __restrict__ mask,
-                       long long P, const unsigned long long* __restrict__ cnt, float* __restrict__ dout,
+                       int B, int H, int W, int S, const unsigned long long* __restrict__ cnt, float* __restrict__ dout,
                        double* __restrict__ loss) {
-    const unsigned long long ng = *cnt;
-    const float inv = ng ? 1.f / (float)ng : 0.f;
+    const unsigned long long ng_all = *cnt;
+    const float inv = ng_all ? 1.f / (float)ng_all : 0.f;
+    const long long P = (long long)B * H * W;
+    const int Win = S * W;
     double acc = 0.0;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        const int X = (int)(p % W);
+        const long long r = p / W;
+        const int Y = (int)(r % H);
+        const int b = (int)(r / H);
+        float tc = 0.f, ts = 0.f, ng = 0.f;
+        for (int dy = 0; dy < S; ++dy)
+            for (int dx = 0; dx < S; ++dx) {
+                const long long i = ((long long)b * (S * H) + S * Y + dy) * Win + S * X + dx;
+                if (!mask[i]) {
+                    float si, ci;
+                    sincosf(0.5f * phi_t[i], &si, &ci);
+                    tc += ci;
+                    ts += si;
+                    ng += 1.f;
+                }
+            }
         float du = 0.f, dv = 0.f;
-        if (!mask[p]) {
+        if (ng > 0.f) {
             const float2 o = reinterpret_cast<const float2*>(out)[p];
-            float s, c;
-            sincosf(0.5f * phi_t[p], &s, &c);
             const float n2 = fmaf(o.x, o.x, fmaf(o.y, o.y, 1e-12f));
             const float n = sqrtf(n2);
-            const float dot = fmaf(o.x, c, o.y * s);
-            acc += 1.0 - (double)(dot / n);
+            const float dot = fmaf(o.x, tc, o.y * ts);
+            acc += (double)ng - (double)(dot / n);
             const float n3 = n2 * n;
-            du = inv * (dot * o.x / n3 - c / n);
-            dv = inv * (dot * o.y / n3 - s / n);
+            du = inv * (dot * o.x / n3 - tc / n);
+            dv = inv * (dot * o.y / n3 - ts / n);
         }
         reinterpret_cast<float2*>(dout)[p] = make_float2(du, dv);
     }
@@ -260,10 +295,11 @@ __global__ void k_to_bf16(const float* __restrict__ a, long long n, bf16* __rest
         b[i] = __float2bfloat16(a[i]);
 }
 
-// Gap sites of image blockIdx.y (entry ents[blockIdx.y], grid Hin x Win inside the H x W
-// network frame) <- unit vector of (u, max(v, 0)), in one or both lattice buffers.
+// Gap sites of image blockIdx.y (entry ents[blockIdx.y], grid Hin x Win; network frame
+// H x W at stride S: site (y, x) takes frame pixel (y / S, x / S)) <- unit vector of
+// (u, max(v, 0)), in one or both lattice buffers.
 __global__ void k_to_lattice(const float* __restrict__ out, const uint8_t* __restrict__ mask,
-                             const mpr::EntryDesc* __restrict__ ents, int H, int W, float2* __restrict__ lat0,
+                             const mpr::EntryDesc* __restrict__ ents, int H, int W, int S, float2* __restrict__ lat0,
                              float2* __restrict__ lat1) {
     const int b = blockIdx.y;
     const mpr::EntryDesc e = ents[b];
@@ -272,7 +308,7 @@ __global__ void k_to_lattice(const float* __restrict__ out, const uint8_t* __res
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         if (mk[i]) continue;
         const int y = (int)(i / e.W), x = (int)(i - (long long)y * e.W);
-        const float2 o = reinterpret_cast<const float2*>(out)[((long long)b * H + y) * W + x];
+        const float2 o = reinterpret_cast<const float2*>(out)[((long long)b * H + y / S) * W + x / S];
         float u = o.x;
         float v = fmaxf(o.y, 1e-6f * fabsf(o.x));          // upper half circle, theta < pi
         const float r = sqrtf(u * u + v * v);
@@ -314,6 +350,7 @@ struct mpr_net {
     bool legacy = false;               // MPR_NET_CONV=mma: all convolutions on mma.sync
     int* d_err = nullptr;              // set by a tensor-core kernel whose barrier wait expired
     int adam_t = 0;
+    int stride = 1;                    // sites per frame pixel along each axis (1 or 2)
     double* d_zr = nullptr;            // zmin[kMaxB], zmax[kMaxB]
     double* d_loss = nullptr;
     unsigned long long* d_cnt = nullptr;
@@ -483,8 +520,8 @@ mpr_status input(mpr_net* net, const float* z, const uint8_t* mask, int B, int H
     NCU(cudaMemcpyAsync(net->d_zr, zmin, sizeof(double) * B, cudaMemcpyDefault, net->st));
     NCU(cudaMemcpyAsync(net->d_zr + kMaxB, zmax, sizeof(double) * B, cudaMemcpyDefault, net->st));
     const long long P0 = (long long)net->B * net->H * net->W;
-    k_input<<<grid1(P0), 256, 0, net->st>>>(z, mask, B, Hin, Win, net->H, net->W, net->d_zr, net->d_zr + kMaxB,
-                                            net->in0);
+    k_input<<<grid1(P0), 256, 0, net->st>>>(z, mask, B, Hin, Win, net->H, net->W, net->stride, net->d_zr,
+                                            net->d_zr + kMaxB, net->in0);
     mpr::count_launches(1, net->st);
     NCU(cudaGetLastError());
     return MPR_OK;
@@ -589,12 +626,14 @@ mpr_status mprnet_warmstart(mpr_net* net, const float* z, const uint8_t* mask, i
     if (B < 1 || B > kMaxB || Hin < 1 || Win < 1) return nfail(net, MPR_EINVAL, "bad warm-start batch");
     const cudaStream_t keep = net->st;
     net->st = st;
-    const int H = (Hin + 7) / 8 * 8, W = (Win + 7) / 8 * 8;
+    const int S = net->stride;
+    const int H = ((Hin + S - 1) / S + 7) / 8 * 8, W = ((Win + S - 1) / S + 7) / 8 * 8;
     mpr_status s = ensure_ws(net, B, H, W, false);
     if (s == MPR_OK) s = input(net, z, mask, B, Hin, Win, zmin, zmax);
     if (s == MPR_OK) s = forward(net);
     if (s == MPR_OK) {
-        k_to_lattice<<<dim3(grid1((long long)Hin * Win), B), 256, 0, st>>>(net->out2, mask, d_ents, H, W, lat0, lat1);
+        k_to_lattice<<<dim3(grid1((long long)Hin * Win), B), 256, 0, st>>>(net->out2, mask, d_ents, H, W, S, lat0,
+                                                                           lat1);
         mpr::count_launches(1, st);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = nfail(net, MPR_ECUDA, std::string("k_to_lattice: ") + cudaGetErrorString(e));
@@ -609,9 +648,17 @@ const char* mprnet_error(const mpr_net* net) { return net ? net->err.c_str() : "
 extern "C" {
 
 mpr_status mpr_net_create(mpr_net** out, uint64_t seed, void* cuda_stream) {
+    return mpr_net_create_strided(out, seed, 1, cuda_stream);
+}
+
+int mpr_net_stride(const mpr_net* net) { return net ? net->stride : 0; }
+
+mpr_status mpr_net_create_strided(mpr_net** out, uint64_t seed, int stride, void* cuda_stream) {
     if (!out) return MPR_EINVAL;
     *out = nullptr;
+    if (stride != 1 && stride != 2) return MPR_EINVAL;
     mpr_net* net = new mpr_net();
+    net->stride = stride;
     net->st = (cudaStream_t)cuda_stream;
     long long off = 0;
     for (int l = 0; l < 14; ++l) {
@@ -745,17 +792,20 @@ mpr_status mpr_net_zero_grads(mpr_net* net) {
 
 mpr_status mpr_net_loss_grad(mpr_net* net, const float* z, const uint8_t* mask, const float* phi_target,
                              const double* zmin, const double* zmax, int B, int H, int W, double* loss) {
-    if (!net || !z || !mask || !phi_target || !zmin || !zmax || bad_shape(B, H, W))
-        return nfail(net, MPR_EINVAL, "B in [1, 4096] and H, W positive multiples of 8 required");
-    mpr_status s = ensure_ws(net, B, H, W, true);
+    if (!net || !z || !mask || !phi_target || !zmin || !zmax || H % net->stride || W % net->stride ||
+        bad_shape(B, H / net->stride, W / net->stride))
+        return nfail(net, MPR_EINVAL, "B in [1, 4096] and H, W positive multiples of 8 x stride required");
+    const int S = net->stride, Hf = H / S, Wf = W / S;
+    mpr_status s = ensure_ws(net, B, Hf, Wf, true);
     if (s == MPR_OK) s = input(net, z, mask, B, H, W, zmin, zmax);
     if (s == MPR_OK) s = forward(net);
     if (s != MPR_OK) return s;
-    const long long P0 = (long long)B * H * W;
+    const long long P0 = (long long)B * Hf * Wf, Pin = (long long)B * H * W;
     NCU(cudaMemsetAsync(net->d_loss, 0, sizeof(double), net->st));
     NCU(cudaMemsetAsync(net->d_cnt, 0, sizeof(unsigned long long), net->st));
-    k_count_gaps<<<std::min(grid1(P0), 1024), 256, 0, net->st>>>(mask, P0, net->d_cnt);
-    k_loss<<<grid1(P0), 256, 0, net->st>>>(net->out2, phi_target, mask, P0, net->d_cnt, net->dout2, net->d_loss);
+    k_count_gaps<<<std::min(grid1(Pin), 1024), 256, 0, net->st>>>(mask, Pin, net->d_cnt);
+    k_loss<<<grid1(P0), 256, 0, net->st>>>(net->out2, phi_target, mask, B, Hf, Wf, S, net->d_cnt, net->dout2,
+                                           net->d_loss);
     mpr::count_launches(2, net->st);
     s = backward(net);
     if (s != MPR_OK) return s;
@@ -786,13 +836,15 @@ mpr_status mpr_net_train_step(mpr_net* net, const float* z, const uint8_t* mask,
 
 mpr_status mpr_net_forward(mpr_net* net, const float* z, const uint8_t* mask, const double* zmin,
                            const double* zmax, int B, int H, int W, float* uv) {
-    if (!net || !z || !mask || !zmin || !zmax || !uv || bad_shape(B, H, W))
-        return nfail(net, MPR_EINVAL, "B in [1, 4096] and H, W positive multiples of 8 required");
-    mpr_status s = ensure_ws(net, B, H, W, false);
+    if (!net || !z || !mask || !zmin || !zmax || !uv || H % net->stride || W % net->stride ||
+        bad_shape(B, H / net->stride, W / net->stride))
+        return nfail(net, MPR_EINVAL, "B in [1, 4096] and H, W positive multiples of 8 x stride required");
+    const int Hf = H / net->stride, Wf = W / net->stride;
+    mpr_status s = ensure_ws(net, B, Hf, Wf, false);
     if (s == MPR_OK) s = input(net, z, mask, B, H, W, zmin, zmax);
     if (s == MPR_OK) s = forward(net);
     if (s != MPR_OK) return s;
-    NCU(cudaMemcpyAsync(uv, net->out2, sizeof(float) * 2 * (size_t)B * H * W, cudaMemcpyDefault, net->st));
+    NCU(cudaMemcpyAsync(uv, net->out2, sizeof(float) * 2 * (size_t)B * Hf * Wf, cudaMemcpyDefault, net->st));
     return check_err(net);
 }
 

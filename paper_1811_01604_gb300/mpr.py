@@ -86,6 +86,8 @@ _SIGS = [
     ("mpr_get_state_batch", _I, [_VP, _I, _VP]),
     # include/mpr_net.h
     ("mpr_net_create", _I, [ctypes.POINTER(_VP), ctypes.c_uint64, _VP]),
+    ("mpr_net_create_strided", _I, [ctypes.POINTER(_VP), ctypes.c_uint64, ctypes.c_int, _VP]),
+    ("mpr_net_stride", ctypes.c_int, [_VP]),
     ("mpr_net_free", None, [_VP]),
     ("mpr_net_last_error", ctypes.c_char_p, [_VP]),
     ("mpr_net_num_params", ctypes.c_longlong, [_VP]),
@@ -334,10 +336,18 @@ def _f64(a):
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
 
 
-def mpr_net_create(seed: int = 0, stream=None):
+def mpr_net_create(seed: int = 0, stream=None, stride: int = 1):
     net = ctypes.c_void_p()
-    _ncheck(None, lib().mpr_net_create(ctypes.byref(net), ctypes.c_uint64(seed), _stream(stream)))
+    if stride == 1:
+        _ncheck(None, lib().mpr_net_create(ctypes.byref(net), ctypes.c_uint64(seed), _stream(stream)))
+    else:
+        _ncheck(None, lib().mpr_net_create_strided(ctypes.byref(net), ctypes.c_uint64(seed), int(stride),
+                                                   _stream(stream)))
     return net
+
+
+def mpr_net_stride(net) -> int:
+    return int(lib().mpr_net_stride(net))
 
 
 def mpr_net_free(net):

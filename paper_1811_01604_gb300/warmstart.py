@@ -133,8 +133,8 @@ def equilibrium_states(z, mask, states_per_grid: int = 4, spacing: int = 20, see
 class WarmStartNet:
     """Owner of an mpr_net handle."""
 
-    def __init__(self, seed: int = 0, stream=None):
-        self.h = mpr.mpr_net_create(seed, stream)
+    def __init__(self, seed: int = 0, stream=None, stride: int = 1):
+        self.h = mpr.mpr_net_create(seed, stream, stride=stride)
 
     def close(self):
         if self.h:
