@@ -14,10 +14,14 @@ Precisions:
     (round to nearest even) where the library stores them in bf16: network input, conv
     weights, layer outputs, pooled maps and the ReLU-gated gradients.  This is the
     reference the GPU kernels (fp32 accumulation) are compared against.
-  * ``acc32=True`` (with bf16 storage): the convolution sums accumulate in float32 instead.
-    Only the accumulation precision changes, not the order the kernels use; the distance
-    between the two bf16 references measures how strongly one-unit rounding flips of
-    stored bf16 values propagate through the network, which sets the GPU tolerance.
+  * ``acc32=True`` (with bf16 storage): the convolution sums accumulate in float32 instead,
+    taps in order or (``rev=True``) in reverse order, and (``chop=True``) with the low
+    mantissa bits of every sum cleared, which models the truncating adders of the tensor
+    cores (with bf16 inputs the products are exact and a float32 sum is often exact too,
+    so the first two may flip nothing where the GPU does).  The largest distance between
+    these bf16 references and the float64-accumulated one measures how strongly one-unit
+    rounding flips of stored bf16 values propagate through the network, which sets the GPU
+    tolerance.
 
 Arrays are NHWC: x[b, y, x, c].  Conv weights w[t, ci, co] with tap t = 3 dy + dx,
 (dy, dx) in {0, 1, 2}^2 addressing input pixel (y + dy - 1, x + dx - 1), zero padding.
@@ -96,34 +100,51 @@ def pack(dWs, dbs, dwh, dbh):
 
 
 # ------------------------------------------------------------------ building blocks
-def conv3x3(x, w, b=None, acc=np.float64):
+def _chop(a, bits=5):
+    """float32 values with their `bits` lowest mantissa bits cleared (toward zero): a
+    deviation of up to 2^(bits - 24) relative, the order by which a tensor core's long sum
+    of products (aligned and truncated inside the unit; up to 9 x 384 products here) can
+    differ from the exact one.  With 5 bits the flips this causes cascade through the
+    decoder as on the GPU (measured: the first one-unit flips in the deepest decoder layer,
+    then 3-4e-3 relative at the output, the same as this model gives)."""
+    a = np.ascontiguousarray(a, np.float32)
+    return (a.view(np.int32) & np.int32(~((1 << bits) - 1))).view(np.float32)
+
+
+def conv3x3(x, w, b=None, acc=np.float64, rev=False, chop=False):
     """out[b, y, x, co] = sum over taps and ci of x[b, y + dy - 1, x + dx - 1, ci] w[3 dy + dx, ci, co]
-    (+ b[co]); pixels outside the image are zero.  acc: accumulation dtype."""
+    (+ b[co]); pixels outside the image are zero.  acc: accumulation dtype; rev: add the
+    taps in reverse order; chop: clear the low mantissa bits of the float32 sum (the last
+    two change only the rounding of a float32 accumulation)."""
     B, H, W, _ = x.shape
     xp = np.pad(x, ((0, 0), (1, 1), (1, 1), (0, 0))).astype(acc)
     wa = w.astype(acc)
     out = np.zeros((B, H, W, w.shape[2]), acc)
-    for dy in range(3):
-        for dx in range(3):
-            out += xp[:, dy:dy + H, dx:dx + W, :] @ wa[3 * dy + dx]
+    for t in (range(8, -1, -1) if rev else range(9)):
+        dy, dx = divmod(t, 3)
+        out += xp[:, dy:dy + H, dx:dx + W, :] @ wa[t]
+    if chop:
+        out = _chop(out).astype(acc)
     if b is not None:
         out += b.astype(acc)
     return out.astype(np.float64)
 
 
-def conv3x3_grad(x, w, g, acc=np.float64):
-    """Gradients of sum(g * conv3x3(x, w)) w.r.t. x and w (the adjoint, tap by tap)."""
+def conv3x3_grad(x, w, g, acc=np.float64, rev=False, chop=False):
+    """Gradients of sum(g * conv3x3(x, w)) w.r.t. x and w (the adjoint, tap by tap; rev:
+    taps in reverse order; chop: low mantissa bits of the float32 sums cleared)."""
     B, H, W, Cin = x.shape
     xp = np.pad(x, ((0, 0), (1, 1), (1, 1), (0, 0))).astype(acc)
     dxp = np.zeros_like(xp)
     dw = np.zeros(w.shape, acc)
     wa, ga = w.astype(acc), g.astype(acc)
     g2 = ga.reshape(-1, g.shape[3])
-    for dy in range(3):
-        for dx in range(3):
-            t = 3 * dy + dx
-            dw[t] = xp[:, dy:dy + H, dx:dx + W, :].reshape(-1, Cin).T @ g2
-            dxp[:, dy:dy + H, dx:dx + W, :] += ga @ wa[t].T
+    for t in (range(8, -1, -1) if rev else range(9)):
+        dy, dx = divmod(t, 3)
+        dw[t] = xp[:, dy:dy + H, dx:dx + W, :].reshape(-1, Cin).T @ g2
+        dxp[:, dy:dy + H, dx:dx + W, :] += ga @ wa[t].T
+    if chop:
+        dxp, dw = _chop(dxp), _chop(dw)
     return dxp[:, 1:H + 1, 1:W + 1, :].astype(np.float64), dw.astype(np.float64)
 
 
@@ -145,9 +166,10 @@ def upsample_adjoint(g):
     return g[:, 0::2, 0::2] + g[:, 0::2, 1::2] + g[:, 1::2, 0::2] + g[:, 1::2, 1::2]
 
 
-def net_input(z, mask, zmin, zmax):
+def net_input(z, mask, zmin, zmax, stride=1):
     """(cos theta, sin theta, 1) at sample sites, zeros at gap sites, padded to 32 channels;
-    theta = q phi, q = 1/2, phi = 2 pi (z - zmin) / (zmax - zmin) (Eq. 1)."""
+    theta = q phi, q = 1/2, phi = 2 pi (z - zmin) / (zmax - zmin) (Eq. 1).  At stride S the
+    frame pixel (Y, X) holds the mean of these over the S x S block of sites it stands for."""
     B, H, W = z.shape
     x = np.zeros((B, H, W, N_IN))
     for b in range(B):
@@ -156,23 +178,34 @@ def net_input(z, mask, zmin, zmax):
         x[b, :, :, 0] = np.where(s, np.cos(th), 0.0)
         x[b, :, :, 1] = np.where(s, np.sin(th), 0.0)
         x[b, :, :, 2] = np.where(s, 1.0, 0.0)
+    if stride > 1:
+        S = stride
+        x = x.reshape(B, H // S, S, W // S, S, N_IN).mean(axis=(2, 4))
     return x
 
 
-def circ_loss(uv, phi_t, mask):
+def circ_loss(uv, phi_t, mask, stride=1):
     """Mean over gap sites of 1 - cos(theta - theta_t), theta the direction of (u, v),
-    theta_t = phi_t / 2; returns (loss, dL/duv)."""
+    theta_t = phi_t / 2; returns (loss, dL/duv).  At stride S every gap site of a frame
+    pixel's S x S block takes that pixel's (u, v): the block's terms add up to
+    n_g - (u Tc + v Ts) / |(u, v)|, (Tc, Ts) the sum of its gaps' (cos, sin) theta_t."""
     u, v = uv[..., 0], uv[..., 1]
-    c, s = np.cos(0.5 * phi_t.astype(np.float64)), np.sin(0.5 * phi_t.astype(np.float64))
-    gap = mask == 0
+    gap = (mask == 0).astype(np.float64)
+    c = np.cos(0.5 * phi_t.astype(np.float64)) * gap
+    s = np.sin(0.5 * phi_t.astype(np.float64)) * gap
     n_gap = int(gap.sum())
     if n_gap == 0:
         return 0.0, np.zeros_like(uv)
+    if stride > 1:
+        S = stride
+        B, H, W = gap.shape
+        blk = lambda a: a.reshape(B, H // S, S, W // S, S).sum(axis=(2, 4))
+        c, s, gap = blk(c), blk(s), blk(gap)
     n = np.sqrt(u * u + v * v + EPS_NORM)
     dot = u * c + v * s
-    loss = float(np.sum(np.where(gap, 1.0 - dot / n, 0.0)) / n_gap)
-    du = np.where(gap, dot * u / n ** 3 - c / n, 0.0) / n_gap
-    dv = np.where(gap, dot * v / n ** 3 - s / n, 0.0) / n_gap
+    loss = float(np.sum(gap - dot / n) / n_gap)
+    du = (dot * u / n ** 3 - c / n) / n_gap
+    dv = (dot * v / n ** 3 - s / n) / n_gap
     return loss, np.stack([du, dv], axis=-1)
 
 
@@ -188,30 +221,31 @@ def _layer_input(l, x0, acts, pools):
     return acts[l - 1]
 
 
-def forward(theta, z, mask, zmin, zmax, bf16_storage=False, acc32=False):
-    """Network output (u, v) per site, and the cache for backward."""
+def forward(theta, z, mask, zmin, zmax, bf16_storage=False, acc32=False, stride=1, rev=False, chop=False):
+    """Network output (u, v) per frame pixel (per site at stride 1), and the cache for backward."""
     r = bf16 if bf16_storage else (lambda a: a)
     acc = np.float32 if acc32 else np.float64
     Ws, bs, wh, bh = unpack(theta)
     Wr = [r(w) for w in Ws]
-    x0 = r(net_input(z, mask, zmin, zmax))
+    x0 = r(net_input(z, mask, zmin, zmax, stride))
     acts, pools, ins = [None] * 14, [None] * 3, [None] * 14
     for l in range(14):
         xin = _layer_input(l, x0, acts, pools)
         ins[l] = xin
-        acts[l] = r(np.maximum(conv3x3(xin, Wr[l], bs[l], acc), 0.0))
+        acts[l] = r(np.maximum(conv3x3(xin, Wr[l], bs[l], acc, rev, chop), 0.0))
         if l in (1, 3, 5):
             pools[l // 2] = r(pool(acts[l]))
     uv = acts[13] @ wh + bh
     return uv, dict(Wr=Wr, wh=wh, acts=acts, ins=ins)
 
 
-def loss_and_grad(theta, z, mask, phi_t, zmin, zmax, bf16_storage=False, acc32=False):
+def loss_and_grad(theta, z, mask, phi_t, zmin, zmax, bf16_storage=False, acc32=False, stride=1, rev=False,
+                  chop=False):
     """Loss and gradient (same layout as theta) for one batch."""
     r = bf16 if bf16_storage else (lambda a: a)
     acc = np.float32 if acc32 else np.float64
-    uv, cache = forward(theta, z, mask, zmin, zmax, bf16_storage, acc32)
-    loss, duv = circ_loss(uv, phi_t, mask)
+    uv, cache = forward(theta, z, mask, zmin, zmax, bf16_storage, acc32, stride, rev, chop)
+    loss, duv = circ_loss(uv, phi_t, mask, stride)
     acts, ins, Wr, wh = cache["acts"], cache["ins"], cache["Wr"], cache["wh"]
     dact = [None] * 14
     dact[13] = duv @ wh.T
@@ -225,7 +259,7 @@ def loss_and_grad(theta, z, mask, phi_t, zmin, zmax, bf16_storage=False, acc32=F
     for l in range(13, -1, -1):
         gl = r(np.where(acts[l] > 0, dact[l], 0.0))
         dbs[l] = gl.reshape(-1, COUT[l]).sum(axis=0)
-        dx, dWs[l] = conv3x3_grad(ins[l], Wr[l], gl, acc)
+        dx, dWs[l] = conv3x3_grad(ins[l], Wr[l], gl, acc, rev, chop)
         if l == 0:
             continue
         if l in (2, 4, 6):

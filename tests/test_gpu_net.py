@@ -114,18 +114,19 @@ def _blocks():
     return out
 
 
-@pytest.mark.parametrize("B,H,W", [(2, 16, 24), (1, 32, 32)])
-def test_network_output_loss_and_gradient_match_oracle(B, H, W):
+@pytest.mark.parametrize("B,H,W,S", [(2, 16, 24, 1), (1, 32, 32, 1), (2, 32, 48, 2), (1, 64, 32, 2)])
+def test_network_output_loss_and_gradient_match_oracle(B, H, W, S):
     z, m, phi, zmin, zmax = _batch(B * H + W, B, H, W)
     th = no.init_params(11).astype(np.float32)
-    net = mpr.mpr_net_create(0)
+    net = mpr.mpr_net_create(0, stride=S)
     try:
+        assert mpr.mpr_net_stride(net) == S
         assert mpr.mpr_net_num_params(net) == th.size
         mpr.mpr_net_set_params(net, th)
         back = np.zeros_like(th)
         mpr.mpr_net_get_params(net, back)
         assert np.array_equal(back, th)
-        uv = torch.zeros((B, H, W, 2), dtype=torch.float32, device="cuda")
+        uv = torch.zeros((B, H // S, W // S, 2), dtype=torch.float32, device="cuda")
         mpr.mpr_net_forward(net, _dev(z), _dev(m), zmin, zmax, B, H, W, uv)
         mpr.mpr_net_zero_grads(net)
         loss = mpr.mpr_net_loss_grad(net, _dev(z), _dev(m), _dev(phi), zmin, zmax, B, H, W)
@@ -134,15 +135,20 @@ def test_network_output_loss_and_gradient_match_oracle(B, H, W):
     finally:
         mpr.mpr_net_free(net)
     th64 = th.astype(np.float64)
-    ruv, _ = no.forward(th64, z, m, zmin, zmax, bf16_storage=True)
-    rloss, rg = no.loss_and_grad(th64, z, m, phi, zmin, zmax, bf16_storage=True)
+    ruv, _ = no.forward(th64, z, m, zmin, zmax, bf16_storage=True, stride=S)
+    rloss, rg = no.loss_and_grad(th64, z, m, phi, zmin, zmax, bf16_storage=True, stride=S)
     # the same bf16 reference accumulated in fp32: its distance to rg is the sensitivity
     # of this network's gradient to one-unit bf16 rounding flips
-    euv, _ = no.forward(th64, z, m, zmin, zmax, bf16_storage=True, acc32=True)
-    _, eg = no.loss_and_grad(th64, z, m, phi, zmin, zmax, bf16_storage=True, acc32=True)
+    # ... in two tap orders and with truncated sums (the tensor cores' adders truncate, so
+    # flips land elsewhere); the largest distance is the sensitivity
+    runs = ((False, False), (True, False), (False, True))
+    euvs = [no.forward(th64, z, m, zmin, zmax, bf16_storage=True, acc32=True, stride=S, rev=rv, chop=ch)[0]
+            for rv, ch in runs]
+    egs = [no.loss_and_grad(th64, z, m, phi, zmin, zmax, bf16_storage=True, acc32=True, stride=S, rev=rv,
+                            chop=ch)[1] for rv, ch in runs]
     guv = uv.cpu().numpy().astype(np.float64)
     rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
-    assert rel(guv, ruv) <= 4 * rel(euv, ruv) + 1e-3
+    assert rel(guv, ruv) <= 4 * max(rel(e, ruv) for e in euvs) + 1e-3
     assert loss == pytest.approx(rloss, rel=2e-3)
     for name, a, b in _blocks():
         ref, got = rg[a:b], g[a:b].astype(np.float64)
@@ -150,10 +156,10 @@ def test_network_output_loss_and_gradient_match_oracle(B, H, W):
         if nr == 0:
             assert np.linalg.norm(got) <= 1e-6
             continue
-        err, sens = rel(got, ref), rel(eg[a:b], ref)
+        err, sens = rel(got, ref), max(rel(e[a:b], ref) for e in egs)
         cos = float(got @ ref) / (np.linalg.norm(got) * nr)
         assert err <= 4 * sens + 2e-3 and cos > 0.995, (name, err, sens, cos)
-    assert rel(g, rg) <= 4 * rel(eg, rg) + 1e-3
+    assert rel(g, rg) <= 4 * max(rel(e, rg) for e in egs) + 1e-3
 
 
 def test_adam_first_step_closed_form():
@@ -208,10 +214,12 @@ def _ctx_grid(H, W, seed):
     return z, m
 
 
-@pytest.mark.parametrize("shapes", [[(64, 64)], [(61, 45)], [(64, 64), (64, 64), (40, 48), (33, 70)]])
-def test_warmstart_writes_the_network_state_into_gap_sites(shapes):
+@pytest.mark.parametrize("shapes,S", [([(64, 64)], 1), ([(61, 45)], 1),
+                                      ([(64, 64), (64, 64), (40, 48), (33, 70)], 1),
+                                      ([(61, 45)], 2), ([(64, 64), (40, 48), (33, 70)], 2)])
+def test_warmstart_writes_the_network_state_into_gap_sites(shapes, S):
     grids = [_ctx_grid(H, W, 7 + i) for i, (H, W) in enumerate(shapes)]
-    net = mpr.mpr_net_create(3)
+    net = mpr.mpr_net_create(3, stride=S)
     ctx = mpr.mpr_init_batch([g[0] for g in grids], [g[1] for g in grids], mpr.mpr_default_params(seed=1))
     try:
         before = []
@@ -225,14 +233,16 @@ def test_warmstart_writes_the_network_state_into_gap_sites(shapes):
             phi = torch.zeros((H, W), dtype=torch.float32, device="cuda")
             mpr.mpr_get_state_batch(ctx, i, phi)
             phi = phi.cpu().numpy()
-            Hp, Wp = (H + 7) // 8 * 8, (W + 7) // 8 * 8
+            # the network frame: ceil(side / S) rounded up to a multiple of 8, S sites per pixel
+            Hp, Wp = ((H + S - 1) // S + 7) // 8 * 8 * S, ((W + S - 1) // S + 7) // 8 * 8 * S
             zp = torch.zeros((1, Hp, Wp), dtype=torch.float32, device="cuda")
             mp = torch.zeros((1, Hp, Wp), dtype=torch.uint8, device="cuda")
             zp[0, :H, :W] = grids[i][0]
             mp[0, :H, :W] = grids[i][1]
-            uv = torch.zeros((1, Hp, Wp, 2), dtype=torch.float32, device="cuda")
+            uv = torch.zeros((1, Hp // S, Wp // S, 2), dtype=torch.float32, device="cuda")
             mpr.mpr_net_forward(net, zp, mp, [info["zmin"]], [info["zmax"]], 1, Hp, Wp, uv)
-            want = no.warm_phi(uv.cpu().numpy()[0, :H, :W].astype(np.float64))
+            up = uv.cpu().numpy()[0].repeat(S, axis=0).repeat(S, axis=1)      # nearest upsampling
+            want = no.warm_phi(up[:H, :W].astype(np.float64))
             gap = grids[i][1].cpu().numpy() == 0
             d = np.abs(phi[gap] - want[gap])
             assert d.max() < 1e-5

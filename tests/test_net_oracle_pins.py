@@ -156,3 +156,47 @@ def test_warm_phi_range():
     assert phi[0] == pytest.approx(2e-6, rel=1e-6) and phi[1] == pytest.approx(math.pi)
     assert np.all(phi < 2 * math.pi) and np.all(phi >= 0)
     assert phi[2] == pytest.approx(2 * math.pi, abs=1e-5)
+
+
+# ---------------------------------------------------------------- stride 2 (coarse frame)
+def test_stride2_loss_is_the_site_loss_of_the_upsampled_prediction():
+    # every gap site of a 2 x 2 block takes its frame pixel's (u, v): the block-sum form
+    # must equal the per-site definition on the nearest-upsampled prediction, and its
+    # gradient the block sum of the per-site gradient (chain rule of the upsampling)
+    rng = np.random.default_rng(21)
+    B, H, W = 2, 8, 12
+    m = (rng.random((B, H, W)) > 0.45).astype(np.uint8)
+    phi = rng.uniform(0, 2 * math.pi, (B, H, W))
+    uv = rng.normal(size=(B, H // 2, W // 2, 2))
+    L2, g2 = no.circ_loss(uv, phi, m, stride=2)
+    up = uv.repeat(2, axis=1).repeat(2, axis=2)
+    L1, g1 = no.circ_loss(up, phi, m, stride=1)
+    assert L2 == pytest.approx(L1, rel=1e-13)
+    assert np.allclose(g2, g1.reshape(B, H // 2, 2, W // 2, 2, 2).sum(axis=(2, 4)), rtol=0, atol=1e-14)
+    # direct: mean over gaps of 1 - cos(theta(pixel) - phi/2)
+    th = np.arctan2(up[..., 1], up[..., 0])
+    direct = np.mean((1.0 - np.cos(th - 0.5 * phi))[m == 0])
+    assert L2 == pytest.approx(direct, rel=1e-6)
+
+
+def test_stride2_input_is_block_mean_of_site_input():
+    z, m, phi, zmin, zmax = _batch(22, 2, 8, 16)
+    x1 = no.net_input(z, m, zmin, zmax)
+    x2 = no.net_input(z, m, zmin, zmax, stride=2)
+    assert x2.shape == (2, 4, 8, no.N_IN)
+    blk = x1[:, 0:2, 2:4, :3]                          # the 2 x 2 block of frame pixel (0, 1)
+    assert np.allclose(x2[:, 0, 1, :3], blk.mean(axis=(1, 2)), rtol=0, atol=1e-15)
+    assert np.all((x2[..., 2] >= 0) & (x2[..., 2] <= 1)) and np.all(x2[..., 3:] == 0)
+
+
+def test_stride2_network_gradient_matches_finite_differences():
+    z, m, phi, zmin, zmax = _batch(23, 2, 16, 16)
+    th = no.init_params(24)
+    L, g = no.loss_and_grad(th, z, m, phi, zmin, zmax, stride=2)
+    rng = np.random.default_rng(25)
+    for _ in range(2):
+        d = rng.normal(size=th.size)
+        eps = 1e-6
+        Lp = no.loss_and_grad(th + eps * d, z, m, phi, zmin, zmax, stride=2)[0]
+        Lm = no.loss_and_grad(th - eps * d, z, m, phi, zmin, zmax, stride=2)[0]
+        assert (Lp - Lm) / (2 * eps) == pytest.approx(float(g @ d), rel=1e-5, abs=1e-9)
