@@ -242,7 +242,8 @@ def profile_case(name, tile_cfg=0):
 def run_batch(args):
     """256 grids (sides log-uniform in [128, 2048], own nu, correlation length, missing
     fraction), M = 32 each: one batched fill per step, against the same grids filled one
-    at a time with the same chains and temperatures."""
+    at a time with the same chains and temperatures.  --batch-warm adds the batched fill
+    with the learned warm start (network trained first, untimed, as in the warm workloads)."""
     import torch
     from paper_1811_01604_gb300 import mpr, synth
     Mb = 32
@@ -256,11 +257,24 @@ def run_batch(args):
     gaps = [int((m == 0).sum().item()) for m in ms]
     stream = torch.cuda.current_stream()
 
-    def batched():
+    net = None
+    if args.batch_warm:
+        from paper_1811_01604_gb300 import warmstart
+        groups = warmstart.training_grids(n64=args.train_n64, n128=args.train_n128, seed=10_000,
+                                          n256=args.train_n256)
+        sets = [warmstart.equilibrium_states(z, m, states_per_grid=4, spacing=20, seed=20_000)
+                for z, m in groups]
+        net = warmstart.WarmStartNet(seed=0, stride=args.warm_stride)
+        warmstart.train(net, sets, steps=args.train_steps, batch=32, lr=1e-3, seed=0)
+        torch.cuda.synchronize()
+
+    def batched(use_net=False):
         ctx = mpr.mpr_init_batch(zs, ms, prm, stream.cuda_stream)
         try:
             mpr.mpr_estimate_T(ctx)
             tune = mpr.mpr_autotune(ctx)
+            if use_net:
+                net.warmstart(ctx)
             mpr.mpr_equilibrate(ctx)
             mpr.mpr_predict_batch(ctx, Mb, outs)
             info = [mpr.mpr_batch_info(ctx, g) for g in range(len(zs))]
@@ -283,6 +297,28 @@ def run_batch(args):
     torch.cuda.synchronize()
     batch_ms = e0.elapsed_time(e1) / args.steps
     updates = sum(P * (inf["sweeps"] + Mb) for P, inf in zip(gaps, info))
+
+    def maes():
+        return [float((o - z)[m == 0].abs().mean()) for o, z, m in zip(outs, zs, ms)]
+
+    mae_plain = maes()
+    warm = None
+    if net is not None:
+        batched(True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            info_w, _ = batched(True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        warm_ms = e0.elapsed_time(e1) / args.steps
+        mae_w = maes()
+        warm = {"ms": warm_ms, "speedup_vs_batched_plain": batch_ms / warm_ms,
+                "relax_sweeps_max": max(i["sweeps"] for i in info_w),
+                "relax_sweeps_mean": float(np.mean([i["sweeps"] for i in info_w])),
+                "mae_mean": float(np.mean(mae_w)), "mae_mean_plain": float(np.mean(mae_plain)),
+                "mae_ratio_max": float(max(a / b for a, b in zip(mae_w, mae_plain))),
+                "net_stride": args.warm_stride}
 
     def sequential():
         for g, (z, m) in enumerate(zip(zs, ms)):
@@ -315,6 +351,8 @@ def run_batch(args):
                        "note": "temperatures of the sequential runs are the batch's"},
             "sequential": {"ms": seq_ms, "value": updates / (seq_ms * 1e-3),
                            "speedup_batched": seq_ms / batch_ms}}
+    if warm:
+        line["batched_warm_start"] = warm
     print(json.dumps(line), flush=True)
 
 
@@ -525,6 +563,8 @@ def main():
     ap.add_argument("--train-steps", type=int, default=2000, help="warm start: Adam steps")
     ap.add_argument("--warm-stride", type=int, default=2, choices=[1, 2],
                     help="warm start: sites per network pixel along each axis")
+    ap.add_argument("--batch-warm", action="store_true",
+                    help="batch256: also time the batched fill with the learned warm start")
     ap.add_argument("--train-n64", type=int, default=1024, help="warm start: 64^2 training grids")
     ap.add_argument("--train-n128", type=int, default=4096, help="warm start: 128^2 training crops")
     ap.add_argument("--train-n256", type=int, default=1024,

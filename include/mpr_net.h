@@ -29,8 +29,8 @@
  * shape, contiguous); zmin, zmax are B doubles (host or device).  H and W are
  * positive multiples of 8 x stride (see mpr_net_create_strided), 1 <= B <= 4096.  All work is enqueued on the stream
  * given at creation; calls that return host values synchronise it.  A network is
- * not thread-safe.  Its activation workspace is sized for the last (B, H, W)
- * and reallocated when that changes.
+ * not thread-safe.  Its activation workspace grows to the largest B x H x W frame
+ * seen (training needs more than inference) and serves every smaller frame.
  */
 #ifndef MPR_NET_H_
 #define MPR_NET_H_

@@ -356,6 +356,7 @@ struct mpr_net {
     unsigned long long* d_cnt = nullptr;
     // activation workspace, sized for B x H x W
     int B = 0, H = 0, W = 0;
+    long long cap = 0;                 // B x H x W the workspace is sized for
     bool train = false;
     std::vector<void*> bufs;
     bf16* in0 = nullptr;
@@ -390,6 +391,7 @@ void free_ws(mpr_net* n) {
     for (void* p : n->bufs) cudaFree(p);
     n->bufs.clear();
     n->B = n->H = n->W = 0;
+    n->cap = 0;
     n->train = false;
 }
 
@@ -401,11 +403,19 @@ cudaError_t nalloc(mpr_net* n, T** p, long long count) {
     return e;
 }
 
+// Every workspace buffer scales with B x H x W (level l holds B (H >> l)(W >> l) pixels,
+// H and W multiples of 8), so buffers sized for a larger frame serve any smaller one: the
+// workspace grows only, and calls on grids of many shapes (a batch) do not reallocate.
 mpr_status ensure_ws(mpr_net* net, int B, int H, int W, bool train) {
-    if (net->B == B && net->H == H && net->W == W && (!train || net->train)) return MPR_OK;
+    const long long P0 = (long long)B * H * W;
+    if (P0 <= net->cap && (!train || net->train)) {
+        net->B = B;
+        net->H = H;
+        net->W = W;
+        return MPR_OK;
+    }
     NCU(cudaStreamSynchronize(net->st));
     free_ws(net);
-    const long long P0 = (long long)B * H * W;
     NCU(nalloc(net, &net->in0, P0 * kIn));
     for (int l = 0; l < 14; ++l) {
         const long long P = P0 >> (2 * kLevel[l]);
@@ -429,6 +439,7 @@ mpr_status ensure_ws(mpr_net* net, int B, int H, int W, bool train) {
     net->H = H;
     net->W = W;
     net->train = train;
+    net->cap = P0;
     return MPR_OK;
 }
 
