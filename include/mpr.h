@@ -49,7 +49,13 @@ typedef enum {
 } mpr_status;
 
 /* over-relaxation (Eq. 6) variants */
-enum { MPR_OR_CONSERVING = 0, MPR_OR_NONE = 2 };
+/* Over-relaxation (Eq. 6).  CONSERVING: reflection about the MPR local field, kept only
+   inside [0, 2 pi) -- the energy-conserving reading, the default.  LITERAL: the formula as
+   printed, phi' = 2 atan2(sum sin phi_j, sum cos phi_j) - phi (mod 2 pi), the q = 1
+   reflection; it does not conserve the MPR energy (its energy change is counted in the
+   tracked energy) and breaks detailed balance, and is kept for the study of that.  NONE:
+   Metropolis steps only. */
+enum { MPR_OR_CONSERVING = 0, MPR_OR_LITERAL = 1, MPR_OR_NONE = 2 };
 /* transcendental functions of the sweep kernel (Sect. 3.3.2, precision study) */
 enum { MPR_TRIG_ACCURATE = 0, MPR_TRIG_FAST = 1 };
 /* sweep kernels: AUTO (= TILE), LIST (one launch per half-sweep over gap lists, in place),
@@ -70,7 +76,7 @@ typedef struct {
     int n_fit;         /* energies in the slope fit (default 20, >= 2) */
     int i_max;         /* cap on relaxation sweeps (default 10000) */
     int M;             /* equilibrium realizations for mpr_predict's default (default 100) */
-    int or_mode;       /* MPR_OR_CONSERVING (default) or MPR_OR_NONE */
+    int or_mode;       /* MPR_OR_CONSERVING (default), MPR_OR_LITERAL or MPR_OR_NONE */
     int trig_mode;     /* MPR_TRIG_ACCURATE (default) or MPR_TRIG_FAST */
     double a_eq;       /* window factor in the equilibrium phase (paper: 1) */
     int KT;            /* temperatures in the e(T,L) table (default 16, >= 2) */

@@ -410,7 +410,7 @@ SweepArgs sweep_args(const mpr_ctx* ctx, const Batch& b, bool use_ctl_a, double 
     A.use_ctl_a = use_ctl_a ? 1 : 0;
     A.half_qd_fixed = (float)(0.5 * kTwoPi * ctx->prm.q / a_fixed);
     A.skip_stopped = skip_stopped ? 1 : 0;
-    A.or_on = ctx->prm.or_mode == MPR_OR_CONSERVING ? 1 : 0;
+    A.or_mode = ctx->prm.or_mode;
     A.rk = round_keys(ctx->prm.seed);
     return A;
 }
@@ -441,7 +441,7 @@ TileArgs tile_args(const mpr_ctx* ctx, const Batch& b, int mode, double a_fixed,
     T.use_ctl_a = relax ? 1 : 0;
     T.half_qd_fixed = (float)(0.5 * kTwoPi * p.q / a_fixed);
     T.skip_stopped = relax ? 1 : 0;
-    T.or_on = p.or_mode == MPR_OR_CONSERVING ? 1 : 0;
+    T.or_mode = p.or_mode;
     T.rk = round_keys(p.seed);
     T.mode = mode;
     T.A_targ = p.A_targ;
@@ -707,7 +707,10 @@ static mpr_status check_params(const mpr_params* p, std::string& why) {
     if (!(p->k_a > 0.0)) { why = "k_a must be > 0"; return MPR_EINVAL; }
     if (p->n_f < 1 || p->n_fit < 2 || p->i_max < 0 || p->M < 1) { why = "n_f >= 1, n_fit >= 2, i_max >= 0, M >= 1"; return MPR_EINVAL; }
     if (p->i_max > 100000000) { why = "i_max too large"; return MPR_EINVAL; }
-    if (p->or_mode != MPR_OR_CONSERVING && p->or_mode != MPR_OR_NONE) { why = "or_mode"; return MPR_EINVAL; }
+    if (p->or_mode != MPR_OR_CONSERVING && p->or_mode != MPR_OR_LITERAL && p->or_mode != MPR_OR_NONE) {
+        why = "or_mode";
+        return MPR_EINVAL;
+    }
     if (p->trig_mode != MPR_TRIG_ACCURATE && p->trig_mode != MPR_TRIG_FAST) { why = "trig_mode"; return MPR_EINVAL; }
     if (!(p->a_eq >= 1.0)) { why = "a_eq must be >= 1"; return MPR_EINVAL; }
     if (p->tile_cfg < 0 || p->tile_cfg >= tile_config_count()) { why = "tile_cfg"; return MPR_EINVAL; }

@@ -137,7 +137,7 @@ struct TileArgs {
     int use_ctl_a;
     float half_qd_fixed;
     int skip_stopped;
-    int or_on;
+    int or_mode;              // over-relaxation: OR_CONSERVING, OR_LITERAL or OR_NONE
     RoundKeys rk;             // Philox round keys of the seed
     int mode;
     double A_targ, k_a;
@@ -162,7 +162,7 @@ struct SweepArgs {
     int use_ctl_a;            // window from Ctl::a (relaxation) or fixed
     float half_qd_fixed;      // q * pi / a for the fixed window
     int skip_stopped;         // skip entries whose relaxation has ended
-    int or_on;
+    int or_mode;              // over-relaxation: OR_CONSERVING, OR_LITERAL or OR_NONE
     RoundKeys rk;             // Philox round keys of the seed
 };
 
@@ -261,23 +261,48 @@ void count_launches(unsigned long long n, cudaStream_t st);
 // ---------------------------------------------------------------- the site update
 enum { TRIG_ACCURATE = 0, TRIG_FAST = 1 };
 
+// Over-relaxation modes (the values of mpr_params::or_mode).
+enum { OR_CONSERVING = 0, OR_LITERAL = 1, OR_NONE = 2 };
+
 // One gap-site update (Algorithm 1) in unit-vector form, q = 1/2, theta = phi/2 in [0, pi).
 //   v        current (cos theta, sin theta) of the site
 //   C, S     local field: sums of the neighbours' cos/sin
+//   Fx, Fy   OR_LITERAL only: sum of the neighbours' (cos phi_j, sin phi_j) = (cos 2 theta_j,
+//            sin 2 theta_j), the field of the reflection as Eq. 6 prints it
 //   hq       half the proposal rotation, q * 2 pi (u - 1/2) / a / 2
 //   r        acceptance uniform
 //   kx       -1/T (TRIG_ACCURATE: the test uses expf) or -log2(e)/T (TRIG_FAST: ex2.approx)
-// Returns the accepted energy change (0 if rejected) and writes the new vector.  Written
-// without branches: both outcomes of each test are computed and selected.
+//   or_mode  OR_CONSERVING (reflection about the MPR field), OR_LITERAL, OR_NONE
+// Returns the energy change of the update (the reflection's, which is 0 unless OR_LITERAL,
+// plus the proposal's if accepted) and writes the new vector.  The conserving path is
+// written without branches: both outcomes of each test are computed and selected.
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 template <int TRIG>
-__device__ __forceinline__ float hybrid_update(float2& v, float C, float S, float hq, float r,
-                                               float kx, int or_on, bool& accepted) {
+__device__ __forceinline__ float hybrid_update(float2& v, float C, float S, float Fx, float Fy, float hq,
+                                               float r, float kx, int or_mode, bool& accepted) {
     float c = v.x, s = v.y;
+    float dE_or = 0.0f;
+    if (or_mode == OR_LITERAL) {
+        // Eq. 6 as printed: phi' = 2 Psi - phi (mod 2 pi), Psi the direction of (Fx, Fy);
+        // theta' = Psi - theta (mod pi).  It moves the local energy; that change is counted.
+        const float F2 = fmaf(Fx, Fx, Fy * Fy);
+        if (F2 > 1e-12f) {
+            const float inv = rsqrtf(F2);
+            const float cp = Fx * inv, sp = Fy * inv;
+            float cl = fmaf(cp, c, sp * s), sl = fmaf(sp, c, -(cp * s));
+            if (sl < 0.0f || (sl == 0.0f && cl < 0.0f)) {
+                cl = -cl;
+                sl = -sl;
+            }
+            dE_or = fmaf(c, C, s * S) - fmaf(cl, C, sl * S);     // local energy is -R cos(theta - psi)
+            c = cl;
+            s = sl;
+        }
+    }
     // R cos(theta - psi) and R sin(theta - psi), psi the direction of the field
     const float along = fmaf(c, C, s * S);
     const float perp0 = fmaf(s, C, -(c * S));
@@ -288,7 +313,7 @@ __device__ __forceinline__ float hybrid_update(float2& v, float C, float S, floa
     // reflection factor 2 (v.n)/|n|^2; a 2-ulp quotient moves the image by ~2e-7 rad
     const float f = __fdividef(2.0f * along, R2);
     const float cr = fmaf(f, C, -c), sr = fmaf(f, S, -s);
-    const bool refl = or_on && R2 > 1e-12f && (sr > 0.0f || (sr == 0.0f && cr > 0.0f));
+    const bool refl = or_mode == OR_CONSERVING && R2 > 1e-12f && (sr > 0.0f || (sr == 0.0f && cr > 0.0f));
     c = refl ? cr : c;
     s = refl ? sr : s;
     const float perp = refl ? -perp0 : perp0;     // the reflection keeps `along`, flips `perp`
@@ -318,7 +343,15 @@ __device__ __forceinline__ float hybrid_update(float2& v, float C, float S, floa
     // one Newton step back to unit length (rounding drift of reflections and rotations)
     const float g = fmaf(-0.5f, fmaf(c, c, s * s), 1.5f);
     v = make_float2(c * g, s * g);
-    return accepted ? dH : 0.0f;
+    return (accepted ? dH : 0.0f) + dE_or;
+}
+
+// The field of Eq. 6 as printed (OR_LITERAL): sum of the four neighbours' (cos 2 theta,
+// sin 2 theta) from their unit vectors (cos theta, sin theta).
+__device__ __forceinline__ void literal_field(float2 a, float2 b, float2 c, float2 d, float& Fx, float& Fy) {
+    Fx = (fmaf(a.x, a.x, -a.y * a.y) + fmaf(b.x, b.x, -b.y * b.y)) +
+         (fmaf(c.x, c.x, -c.y * c.y) + fmaf(d.x, d.x, -d.y * d.y));
+    Fy = 2.0f * ((a.x * a.y + b.x * b.y) + (c.x * c.y + d.x * d.y));
 }
 
 // The exponent scale kx of hybrid_update for a temperature given as -1/T.

@@ -46,7 +46,9 @@ k_half_sweep(const SweepArgs A, const int color) {
             const uint4 rnd = philox10(make_uint4(site, sweep, chain, 0u), A.rk);
             const float hq = (u24f(rnd.x) - 0.5f) * half_qd;
             bool accepted;
-            dE += hybrid_update<TRIG>(v, C, S, hq, u24f(rnd.y), kx, A.or_on, accepted);
+            float Fx = 0.0f, Fy = 0.0f;
+            if (A.or_mode == OR_LITERAL) literal_field(nu, nd, nl, nr, Fx, Fy);
+            dE += hybrid_update<TRIG>(v, C, S, Fx, Fy, hq, u24f(rnd.y), kx, A.or_mode, accepted);
             nacc += accepted ? 1u : 0u;
             own[k] = v;
             if (ACC) acc[g] += angle_upper(v.x, v.y);

@@ -436,7 +436,9 @@ k_tile_sweep(const TileArgs A) {
                 const uint4 rnd = philox10(make_uint4(site, sweep, chain, 0u), A.rk);
                 const float hq = (u24f(rnd.x) - 0.5f) * half_qd;
                 bool accepted;
-                const float d = hybrid_update<TRIG>(v, C, S, hq, u24f(rnd.y), kx, A.or_on, accepted);
+                float Fx = 0.0f, Fy = 0.0f;
+                if (A.or_mode == OR_LITERAL) literal_field(nu, nd, nl, nr, Fx, Fy);
+                const float d = hybrid_update<TRIG>(v, C, S, Fx, Fy, hq, u24f(rnd.y), kx, A.or_mode, accepted);
                 own[r][q] = v;
                 if (own_site) {
                     dE += d;

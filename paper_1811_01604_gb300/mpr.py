@@ -17,7 +17,7 @@ from . import build as _build
 
 MPR_OK, MPR_EINVAL, MPR_ENOMEM, MPR_ECUDA, MPR_ENODATA, MPR_ENOPAIRS, MPR_ETIMEOUT, \
     MPR_ENOTEQUIL, MPR_ESTATE = range(9)
-MPR_OR_CONSERVING, MPR_OR_NONE = 0, 2
+MPR_OR_CONSERVING, MPR_OR_LITERAL, MPR_OR_NONE = 0, 1, 2
 MPR_TRIG_ACCURATE, MPR_TRIG_FAST = 0, 1
 MPR_EXEC_AUTO, MPR_EXEC_LIST, MPR_EXEC_TILE = 0, 1, 2
 
