@@ -544,6 +544,53 @@ def run_chains(args):
     print(json.dumps(line), flush=True)
 
 
+def run_or_modes(args):
+    """Eq. 6 readings on whole fills: 1024^2 maps (nu 0.5, correlation length 16, 33 % gaps),
+    filled with the energy-conserving reflection (the library's reading), the formula as
+    printed (the q = 1 reflection) and no over-relaxation, at each grid's own T-hat; MAE /
+    RMSE against the hidden field, relaxation sweeps and time per map, over seeds."""
+    import torch
+    from paper_1811_01604_gb300 import mpr, synth
+    stream = torch.cuda.current_stream()
+    modes = (("conserving", mpr.MPR_OR_CONSERVING), ("literal", mpr.MPR_OR_LITERAL),
+             ("none", mpr.MPR_OR_NONE))
+    rows = {name: {"mae": [], "rmse": [], "sweeps": [], "ms": []} for name, _ in modes}
+    seeds = tuple(range(1, 1 + max(1, args.steps)))
+    for seed in seeds:
+        z = synth.wm_field_gpu(1024, 1024, 0.5, 16.0, 300 + seed)
+        mask = synth.mask_uniform_gpu(1024, 1024, 0.33, 1_000_300 + seed)
+        gap = mask == 0
+        out = torch.empty_like(z)
+        for name, mode in modes:
+            for _ in range(2 if seed == seeds[0] else 1):           # first seed: one untimed warm-up
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx = mpr.mpr_init(z, mask, 1024, 1024, mpr.mpr_default_params(seed=seed, or_mode=mode),
+                                   stream.cuda_stream)
+                try:
+                    mpr.mpr_estimate_T(ctx)
+                    st = mpr.mpr_equilibrate(ctx)
+                    mpr.mpr_predict(ctx, M, out)
+                finally:
+                    mpr.mpr_free(ctx)
+                e1.record(stream)
+                torch.cuda.synchronize()
+            err = (out - z)[gap].double()
+            r = rows[name]
+            r["mae"].append(float(err.abs().mean()))
+            r["rmse"].append(float(err.pow(2).mean().sqrt()))
+            r["sweeps"].append(st.sweeps)
+            r["ms"].append(e0.elapsed_time(e1))
+    summary = {name: {k: float(np.mean(v)) for k, v in r.items()} for name, r in rows.items()}
+    line = {"metric": "MAE of the fill by Eq. 6 reading", "value": summary["literal"]["mae"],
+            "unit": "z units", "n_gpus": 1, "steps": len(seeds), "warmup": 1, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "mpr-or-modes-1024x1024-wm-nu0.5-xi16-p0.33", "M": M, "seeds": list(seeds)},
+            "by_mode": summary}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -554,11 +601,12 @@ def main():
     ap.add_argument("--profile-case", default=None, choices=["sweep4096", "net4096", "net1024", "net128"],
                     help="run a small fixed sweep workload for ncu instead of the benchmark")
     ap.add_argument("--workload", default="fill4096", choices=["fill4096", "batch256", "warm1024", "warm4096",
-                                                                "chains1024"],
+                                                                "chains1024", "ormodes1024"],
                     help="fill4096: one 4096^2 map per step (default); batch256: 256 grids of "
                          "sides 128-2048 filled in one batch, against the same grids one at a time; "
                          "warm1024 / warm4096: learned warm start against the plain random start; "
-                         "chains1024: independent chains against one chain at equal sweeps")
+                         "chains1024: independent chains against one chain at equal sweeps; "
+                         "ormodes1024: fills with the Eq. 6 readings (conserving, printed, none)")
     ap.add_argument("--tile-cfg", type=int, default=0, help="profile cases: compiled tile configuration")
     ap.add_argument("--train-steps", type=int, default=2000, help="warm start: Adam steps")
     ap.add_argument("--warm-stride", type=int, default=2, choices=[1, 2],
@@ -588,6 +636,9 @@ def main():
         return
     if args.workload == "chains1024":
         run_chains(args)
+        return
+    if args.workload == "ormodes1024":
+        run_or_modes(args)
         return
 
     import torch
