@@ -116,7 +116,7 @@ class ClockSampler:
 # DRAM bytes per launch of k_tile_sweep on this grid from one ncu capture
 # (profiles/k_tile_sweep_4096.md), valid for the kernel sources with this hash only.
 TILE_TRAFFIC_BYTES = 253.8e6
-TILE_TRAFFIC_SOURCE_HASH = "5ef1a45cbc4665d7"
+TILE_TRAFFIC_SOURCE_HASH = "0dd4de56125440f5"
 
 
 def tile_kernel_hash():
@@ -548,13 +548,14 @@ def run_or_modes(args):
     """Eq. 6 readings on whole fills: 1024^2 maps (nu 0.5, correlation length 16, 33 % gaps),
     filled with the energy-conserving reflection (the library's reading), the formula as
     printed (the q = 1 reflection) and no over-relaxation, at each grid's own T-hat; MAE /
-    RMSE against the hidden field, relaxation sweeps and time per map, over seeds."""
+    RMSE against the hidden field, T-hat, relaxation sweeps, time per map and the part of it
+    spent up to T-hat (the e(T, L) table relaxes with the same reflection), over seeds."""
     import torch
     from paper_1811_01604_gb300 import mpr, synth
     stream = torch.cuda.current_stream()
     modes = (("conserving", mpr.MPR_OR_CONSERVING), ("literal", mpr.MPR_OR_LITERAL),
              ("none", mpr.MPR_OR_NONE))
-    rows = {name: {"mae": [], "rmse": [], "sweeps": [], "ms": []} for name, _ in modes}
+    rows = {name: {"mae": [], "rmse": [], "T": [], "sweeps": [], "ms": [], "ms_T": []} for name, _ in modes}
     seeds = tuple(range(1, 1 + max(1, args.steps)))
     for seed in seeds:
         z = synth.wm_field_gpu(1024, 1024, 0.5, 16.0, 300 + seed)
@@ -564,12 +565,13 @@ def run_or_modes(args):
         for name, mode in modes:
             for _ in range(2 if seed == seeds[0] else 1):           # first seed: one untimed warm-up
                 torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0, eT, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
                 e0.record(stream)
                 ctx = mpr.mpr_init(z, mask, 1024, 1024, mpr.mpr_default_params(seed=seed, or_mode=mode),
                                    stream.cuda_stream)
                 try:
-                    mpr.mpr_estimate_T(ctx)
+                    T_hat, _ = mpr.mpr_estimate_T(ctx)
+                    eT.record(stream)
                     st = mpr.mpr_equilibrate(ctx)
                     mpr.mpr_predict(ctx, M, out)
                 finally:
@@ -580,14 +582,89 @@ def run_or_modes(args):
             r = rows[name]
             r["mae"].append(float(err.abs().mean()))
             r["rmse"].append(float(err.pow(2).mean().sqrt()))
+            r["T"].append(T_hat)
             r["sweeps"].append(st.sweeps)
             r["ms"].append(e0.elapsed_time(e1))
+            r["ms_T"].append(e0.elapsed_time(eT))
     summary = {name: {k: float(np.mean(v)) for k, v in r.items()} for name, r in rows.items()}
     line = {"metric": "MAE of the fill by Eq. 6 reading", "value": summary["literal"]["mae"],
             "unit": "z units", "n_gpus": 1, "steps": len(seeds), "warmup": 1, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "mpr-or-modes-1024x1024-wm-nu0.5-xi16-p0.33", "M": M, "seeds": list(seeds)},
             "by_mode": summary}
+    print(json.dumps(line), flush=True)
+
+
+def run_dpsp(args):
+    """Single versus double precision (Sect. 4, the DP/SP time ratio against the grid side
+    for p = 33 % and 66 %): Whittle-Matern fields nu = 0.5, kappa = 0.2 (correlation length
+    5), gaps removed uniformly at random, L = 32 .. 4096.  Per grid: the whole fill (e(T, L)
+    table built afresh, T-hat, relaxation, M = 100 averaged sweeps) in FP32 (the tile
+    kernel) and in FP64 (MPR_PREC_F64, the list kernels), the time of one equilibrium sweep
+    of each (FP32 also on the list kernels, the like-for-like ratio), and the MAE of each."""
+    import torch
+    from paper_1811_01604_gb300 import mpr, synth
+    stream = torch.cuda.current_stream()
+    sides = (32, 64, 128, 256, 512, 1024, 2048, 4096)
+    variants = (("sp", dict()), ("dp", dict(precision=mpr.MPR_PREC_F64)))
+
+    def fill(z, mask, L, seed, extra):
+        out = torch.empty_like(z)
+        prm = mpr.mpr_default_params(seed=seed, **extra)
+        torch.cuda.synchronize()
+        e0, eT, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        ctx = mpr.mpr_init(z, mask, L, L, prm, stream.cuda_stream)
+        try:
+            T_hat, _ = mpr.mpr_estimate_T(ctx)
+            eT.record(stream)
+            st = mpr.mpr_equilibrate(ctx)
+            mpr.mpr_predict(ctx, M, out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        finally:
+            mpr.mpr_free(ctx)
+        # one sweep at a = 1, 10 timed after 3, on fresh contexts at T-hat (both FP32 kernels)
+        sweep_ms = {}
+        kernels = (("list", mpr.MPR_EXEC_LIST),) if extra else (("tile", mpr.MPR_EXEC_TILE),
+                                                                ("list", mpr.MPR_EXEC_LIST))
+        for name, ex in kernels:
+            c2 = mpr.mpr_init(z, mask, L, L, mpr.mpr_default_params(seed=seed, exec_mode=ex, **extra),
+                              stream.cuda_stream)
+            try:
+                mpr.mpr_set_T(c2, T_hat)
+                mpr.mpr_time_sweeps(c2, 3, 1.0)
+                sweep_ms[name] = mpr.mpr_time_sweeps(c2, 10, 1.0)
+            finally:
+                mpr.mpr_free(c2)
+        gap = mask == 0
+        mae = float((out - z)[gap].double().abs().mean())
+        return dict(T=T_hat, sweeps=st.sweeps, ms=e0.elapsed_time(e1), ms_T=e0.elapsed_time(eT),
+                    sweep_ms=sweep_ms, mae=mae)
+
+    for _, extra in variants:                                    # untimed warm-up
+        zw = synth.wm_field_gpu(64, 64, 0.5, 5.0, 1)
+        fill(zw, synth.mask_uniform_gpu(64, 64, 0.33, 2), 64, 999, extra)
+    rows = []
+    for L in sides:
+        for p in (0.33, 0.66):
+            z = synth.wm_field_gpu(L, L, 0.5, 5.0, 700 + L)
+            mask = synth.mask_uniform_gpu(L, L, p, 800 + L + int(100 * p))
+            r = {"L": L, "p": p}
+            for name, extra in variants:
+                r[name] = fill(z, mask, L, 31 + L + int(1000 * p), extra)   # own seed: no cached table
+            r["ratio_fill"] = r["dp"]["ms"] / r["sp"]["ms"]
+            r["ratio_sweep_list"] = r["dp"]["sweep_ms"]["list"] / r["sp"]["sweep_ms"]["list"]
+            r["ratio_sweep_tile"] = r["dp"]["sweep_ms"]["list"] / r["sp"]["sweep_ms"]["tile"]
+            rows.append(r)
+            print(json.dumps(r), file=sys.stderr, flush=True)
+    big = [r for r in rows if r["L"] >= 1024]
+    line = {"metric": "DP/SP time ratio of a whole fill, L >= 1024",
+            "value": float(np.mean([r["ratio_fill"] for r in big])), "unit": "ratio",
+            "n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+            "config": {"workload": "mpr-dpsp-wm-nu0.5-xi5-p0.33,0.66-L32..4096", "M": M},
+            "rows": rows}
     print(json.dumps(line), flush=True)
 
 
@@ -601,12 +678,13 @@ def main():
     ap.add_argument("--profile-case", default=None, choices=["sweep4096", "net4096", "net1024", "net128"],
                     help="run a small fixed sweep workload for ncu instead of the benchmark")
     ap.add_argument("--workload", default="fill4096", choices=["fill4096", "batch256", "warm1024", "warm4096",
-                                                                "chains1024", "ormodes1024"],
+                                                                "chains1024", "ormodes1024", "dpsp"],
                     help="fill4096: one 4096^2 map per step (default); batch256: 256 grids of "
                          "sides 128-2048 filled in one batch, against the same grids one at a time; "
                          "warm1024 / warm4096: learned warm start against the plain random start; "
                          "chains1024: independent chains against one chain at equal sweeps; "
-                         "ormodes1024: fills with the Eq. 6 readings (conserving, printed, none)")
+                         "ormodes1024: fills with the Eq. 6 readings (conserving, printed, none); "
+                         "dpsp: FP32 against FP64 fills, L = 32 .. 4096")
     ap.add_argument("--tile-cfg", type=int, default=0, help="profile cases: compiled tile configuration")
     ap.add_argument("--train-steps", type=int, default=2000, help="warm start: Adam steps")
     ap.add_argument("--warm-stride", type=int, default=2, choices=[1, 2],
@@ -639,6 +717,9 @@ def main():
         return
     if args.workload == "ormodes1024":
         run_or_modes(args)
+        return
+    if args.workload == "dpsp":
+        run_dpsp(args)
         return
 
     import torch

@@ -62,6 +62,16 @@ enum { MPR_TRIG_ACCURATE = 0, MPR_TRIG_FAST = 1 };
    TILE (one fused launch per sweep over shared-memory tiles, two lattice buffers).
    Both are replayed as CUDA graphs and give bitwise identical lattices. */
 enum { MPR_EXEC_AUTO = 0, MPR_EXEC_LIST = 1, MPR_EXEC_TILE = 2 };
+/* Arithmetic of the lattice and the sweeps (Sect. 4, the single- versus double-precision
+   comparison).  F32: unit vectors, field sums, proposal and Metropolis test in FP32 (energy
+   sums, control and table in FP64).  F64: the lattice is stored as FP64 unit vectors and
+   every step of Algorithm 1, the Eq. 4 sample energy, Eq. 2 and the equilibrium averages
+   run in FP64 (sin, cos, exp and atan2 of the CUDA math library in double), on the LIST
+   kernels only: exec_mode must be AUTO or LIST and trig_mode ACCURATE (mpr_init returns
+   MPR_EINVAL otherwise); as in any LIST context mpr_autotune returns MPR_ESTATE and
+   mpr_predict_chains MPR_EINVAL; mpr_warmstart_init returns MPR_EINVAL.  Outputs stay
+   float (mpr_get_state64 reads the FP64 angles). */
+enum { MPR_PREC_F32 = 0, MPR_PREC_F64 = 1 };
 
 /*
  * Simulation parameters (Algorithm 2, step 1.1) and the readings of what the
@@ -87,6 +97,7 @@ typedef struct {
     int exec_mode;     /* MPR_EXEC_* (default AUTO) */
     uint32_t chain;    /* realization id of this context's chain (default 0) */
     int tile_cfg;      /* compiled tile shape of the TILE kernels, 0 .. 2 (default 0; see mpr_autotune) */
+    int precision;     /* MPR_PREC_F32 (default) or MPR_PREC_F64 */
 } mpr_params;
 
 typedef struct {
@@ -232,6 +243,10 @@ mpr_status mpr_get_state(mpr_ctx* ctx, float* phi, uint32_t* sweep);
 mpr_status mpr_set_state(mpr_ctx* ctx, const float* phi, uint32_t sweep);
 /* Grid g of a batch context: its current angles phi (float[H_g][W_g], as above). */
 mpr_status mpr_get_state_batch(mpr_ctx* ctx, int g, float* phi);
+/* As mpr_get_state into double[H][W] (host or device): phi = 2 atan2(sin, cos) of the
+   stored unit vector in FP64.  In MPR_PREC_F32 contexts the FP32 vectors are widened
+   first.  sweep may be NULL. */
+mpr_status mpr_get_state64(mpr_ctx* ctx, double* phi, uint32_t* sweep);
 
 /*
  * Energy bookkeeping: H_exact recomputes Eq. 2 over all bonds; H_tracked is the

@@ -72,6 +72,7 @@ struct Batch {
     int gsweeps = kDefaultGraphSweeps;     // sweeps per captured chunk (host checks once per chunk)
     double* d_scratch = nullptr;
     double* d_H = nullptr;                 // one exact energy per entry
+    bool f64 = false;                      // lattice of double2 and d_acc of doubles (MPR_PREC_F64)
     // tile path (fused sweeps over shared-memory tiles, two lattice buffers)
     bool tiled = false;
     float2* d_lat2 = nullptr;
@@ -275,7 +276,9 @@ mpr_status read_ctl(mpr_ctx* ctx, Batch& b, std::vector<Ctl>& out);
 mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids, int all_free,
                        const uint8_t* mask_base, bool same_grid = false) {
     cudaStream_t st = ctx->st;
-    b.tiled = ctx->prm.exec_mode != MPR_EXEC_LIST;
+    b.f64 = ctx->prm.precision == MPR_PREC_F64;
+    b.tiled = ctx->prm.exec_mode != MPR_EXEC_LIST && !b.f64;
+    const size_t wide = b.f64 ? 2 : 1;     // float2 slots per lattice element, floats per average
     const uint32_t k0 = (uint32_t)ctx->prm.seed, k1 = (uint32_t)(ctx->prm.seed >> 32);
     b.n_ent = (int)grids.size();
     b.ents.assign(b.n_ent, EntryDesc{});
@@ -300,11 +303,11 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
         maxH = std::max(maxH, E.H);
     }
     b.lat_elems = lat;
-    CU(dalloc(&b.d_lat, lat, st));
-    CU(cudaMemsetAsync(b.d_lat, 0, lat * sizeof(float2), st));
+    CU(dalloc(&b.d_lat, lat * wide, st));
+    CU(cudaMemsetAsync(b.d_lat, 0, lat * wide * sizeof(float2), st));
     for (int e = 0; e < b.n_ent; ++e)
         CU(launch_pack(&b.ents[e], grids[e].z, grids[e].mask, grids[e].zmin, grids[e].scale, b.d_lat,
-                       k0, k1, all_free, st));
+                       k0, k1, all_free, b.f64, st));
     // gap lists: per-row counts, scan, scatter
     int* d_rows = nullptr;
     int* d_tot = nullptr;
@@ -332,7 +335,7 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
     }
     b.n_gaps = ng;
     CU(dalloc(&b.d_gaps, ng, st));
-    CU(dalloc(&b.d_acc, ng, st));
+    CU(dalloc(&b.d_acc, ng * wide, st));
     for (int e = 0; e < b.n_ent; ++e) {
         EntryDesc& E = b.ents[e];
         CU(cudaMemcpyAsync(d_rows, offs[e].data(), sizeof(int) * 2 * E.H, cudaMemcpyHostToDevice, st));
@@ -411,6 +414,8 @@ SweepArgs sweep_args(const mpr_ctx* ctx, const Batch& b, bool use_ctl_a, double 
     A.half_qd_fixed = (float)(0.5 * kTwoPi * ctx->prm.q / a_fixed);
     A.skip_stopped = skip_stopped ? 1 : 0;
     A.or_mode = ctx->prm.or_mode;
+    A.f64 = b.f64 ? 1 : 0;
+    A.half_qd_fixed64 = 0.5 * kTwoPi * ctx->prm.q / a_fixed;
     A.rk = round_keys(ctx->prm.seed);
     return A;
 }
@@ -539,7 +544,7 @@ mpr_status reset_tracked_energy(mpr_ctx* ctx, Batch& b) {
     mpr_status s = read_ctl(ctx, b, c);
     if (s != MPR_OK) return s;
     for (int e = 0; e < b.n_ent; ++e)
-        CU(launch_energy(&b.ents[e], lat_cur(b, c[e]), b.d_scratch, kScratch, b.d_H + e, ctx->st));
+        CU(launch_energy(&b.ents[e], lat_cur(b, c[e]), b.d_scratch, kScratch, b.d_H + e, b.f64, ctx->st));
     CU(launch_set_tracked_energy(b.d_ctl, b.d_H, b.n_ent, ctx->st));
     return MPR_OK;
 }
@@ -572,9 +577,9 @@ mpr_status reset_relax(mpr_ctx* ctx, Batch& b) {
 
 std::string table_key(const mpr_params& p, int W, int H) {
     char buf[512];
-    std::snprintf(buf, sizeof buf, "%d|%d|%llu|%.17g|%.17g|%.17g|%d|%d|%d|%d|%d|%.17g|%d|%.17g|%.17g|%d",
+    std::snprintf(buf, sizeof buf, "%d|%d|%llu|%.17g|%.17g|%.17g|%d|%d|%d|%d|%d|%.17g|%d|%.17g|%.17g|%d|%d",
                   W, H, (unsigned long long)p.seed, p.q, p.A_targ, p.k_a, p.n_f, p.n_fit, p.i_max,
-                  p.or_mode, p.trig_mode, p.a_eq, p.KT, p.T_min, p.T_max, p.M_T);
+                  p.or_mode, p.trig_mode, p.a_eq, p.KT, p.T_min, p.T_max, p.M_T, p.precision);
     return buf;
 }
 
@@ -716,6 +721,11 @@ static mpr_status check_params(const mpr_params* p, std::string& why) {
     if (p->tile_cfg < 0 || p->tile_cfg >= tile_config_count()) { why = "tile_cfg"; return MPR_EINVAL; }
     if (p->exec_mode != MPR_EXEC_AUTO && p->exec_mode != MPR_EXEC_LIST && p->exec_mode != MPR_EXEC_TILE) { why = "exec_mode"; return MPR_EINVAL; }
     if (p->KT < 2 || !(p->T_min > 0.0) || !(p->T_max > p->T_min) || p->M_T < 1 || p->T_cap < 0) { why = "table parameters"; return MPR_EINVAL; }
+    if (p->precision != MPR_PREC_F32 && p->precision != MPR_PREC_F64) { why = "precision"; return MPR_EINVAL; }
+    if (p->precision == MPR_PREC_F64 && (p->exec_mode == MPR_EXEC_TILE || p->trig_mode != MPR_TRIG_ACCURATE)) {
+        why = "MPR_PREC_F64 runs the LIST kernels with accurate transcendentals";
+        return MPR_EINVAL;
+    }
     return MPR_OK;
 }
 
@@ -805,7 +815,7 @@ static mpr_status init_grids(mpr_ctx** out, int n, const float* const* z, const 
         GridInfo& G = ctx->g[i];
         int np = 0;
         CUI(launch_sample_energy(&ctx->b.ents[i], ctx->d_z + G.site0, ctx->d_mask + G.site0, G.scale,
-                                 ctx->prm.q, d_ps, d_pc, &np, ctx->st));
+                                 ctx->prm.q, d_ps, d_pc, &np, ctx->prm.precision == MPR_PREC_F64, ctx->st));
         std::vector<double> ps(np);
         std::vector<unsigned long long> pc(np);
         CUI(cudaMemcpyAsync(ps.data(), d_ps, sizeof(double) * np, cudaMemcpyDeviceToHost, ctx->st));
@@ -941,7 +951,7 @@ static mpr_status predict_all(mpr_ctx* ctx, int M, float* const* out) {
     if (b.tiled)
         CU(cudaMemsetAsync(b.d_tacc, 0, sizeof(float) * (size_t)b.ntiles * tile_geom(b.tcfg).acc, ctx->st));
     else
-        CU(cudaMemsetAsync(b.d_acc, 0, sizeof(float) * std::max<size_t>(b.n_gaps, 1), ctx->st));
+        CU(cudaMemsetAsync(b.d_acc, 0, sizeof(float) * (b.f64 ? 2 : 1) * std::max<size_t>(b.n_gaps, 1), ctx->st));
     mpr_status s = run_sweeps(ctx, b, M, CTL_FIXED, ctx->prm.a_eq, true);
     if (s != MPR_OK) return s;
     CU(cudaMemcpyAsync(ctx->d_out, ctx->d_z, (size_t)ctx->n_sites * sizeof(float),
@@ -954,7 +964,7 @@ static mpr_status predict_all(mpr_ctx* ctx, int M, float* const* out) {
                                        G.zmax, 1, 0, ctx->d_out, ctx->st));
         else
             CU(launch_predict_out(&b.ents[i], b.d_lat, b.d_gaps, b.d_acc, M, ctx->prm.q, G.zmin,
-                                  G.zmax, ctx->d_out + G.site0, ctx->st));
+                                  G.zmax, ctx->d_out + G.site0, b.f64, ctx->st));
     }
     for (size_t i = 0; i < ctx->g.size(); ++i) {
         const GridInfo& G = ctx->g[i];
@@ -1076,6 +1086,7 @@ mpr_status mpr_fill_batch(mpr_ctx* ctx, float* const* zhat) {
 mpr_status mpr_warmstart_init(mpr_ctx* ctx, mpr_net* net) {
     if (!ctx || !net) return MPR_EINVAL;
     Batch& b = ctx->b;
+    if (b.f64) return fail(ctx, MPR_EINVAL, "the warm start writes an FP32 lattice");
     float2* lat1 = b.tiled ? b.d_lat2 : nullptr;
     const int n = (int)ctx->g.size();
     for (int i = 0; i < n;) {
@@ -1118,9 +1129,26 @@ mpr_status mpr_get_state(mpr_ctx* ctx, float* phi, uint32_t* sweep) {
     std::vector<Ctl> c;
     mpr_status s = read_ctl(ctx, ctx->b, c);
     if (s != MPR_OK) return s;
-    CU(launch_get_state(&ctx->b.ents[0], lat_cur(ctx->b, c[0]), ctx->d_out, ctx->st));
+    CU(launch_get_state(&ctx->b.ents[0], lat_cur(ctx->b, c[0]), ctx->d_out, ctx->b.f64, ctx->st));
     CU(cudaMemcpyAsync(phi, ctx->d_out, n * sizeof(float), cudaMemcpyDefault, ctx->st));
     CU(cudaStreamSynchronize(ctx->st));
+    if (sweep) *sweep = c[0].sweep;
+    return MPR_OK;
+}
+
+mpr_status mpr_get_state64(mpr_ctx* ctx, double* phi, uint32_t* sweep) {
+    if (!ctx || !phi) return MPR_EINVAL;
+    const size_t n = (size_t)ctx->g[0].W * ctx->g[0].H;
+    std::vector<Ctl> c;
+    mpr_status s = read_ctl(ctx, ctx->b, c);
+    if (s != MPR_OK) return s;
+    double* d = nullptr;
+    CU(dalloc(&d, n, ctx->st));
+    cudaError_t e = launch_get_state64(&ctx->b.ents[0], lat_cur(ctx->b, c[0]), d, ctx->b.f64, ctx->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(phi, d, n * sizeof(double), cudaMemcpyDefault, ctx->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+    dfree(d, ctx->st);
+    CU(e);
     if (sweep) *sweep = c[0].sweep;
     return MPR_OK;
 }
@@ -1131,7 +1159,7 @@ mpr_status mpr_get_state_batch(mpr_ctx* ctx, int g, float* phi) {
     std::vector<Ctl> c;
     mpr_status s = read_ctl(ctx, ctx->b, c);
     if (s != MPR_OK) return s;
-    CU(launch_get_state(&ctx->b.ents[g], lat_cur(ctx->b, c[g]), ctx->d_out + G.site0, ctx->st));
+    CU(launch_get_state(&ctx->b.ents[g], lat_cur(ctx->b, c[g]), ctx->d_out + G.site0, ctx->b.f64, ctx->st));
     CU(cudaMemcpyAsync(phi, ctx->d_out + G.site0, (size_t)G.W * G.H * sizeof(float), cudaMemcpyDefault, ctx->st));
     CU(cudaStreamSynchronize(ctx->st));
     return MPR_OK;
@@ -1144,7 +1172,7 @@ mpr_status mpr_set_state(mpr_ctx* ctx, const float* phi, uint32_t sweep) {
     mpr_status s = read_ctl(ctx, ctx->b, c);
     if (s != MPR_OK) return s;
     CU(cudaMemcpyAsync(ctx->d_out, phi, n * sizeof(float), cudaMemcpyDefault, ctx->st));
-    CU(launch_set_state(&ctx->b.ents[0], lat_cur(ctx->b, c[0]), ctx->b.d_gaps, ctx->d_out, ctx->st));
+    CU(launch_set_state(&ctx->b.ents[0], lat_cur(ctx->b, c[0]), ctx->b.d_gaps, ctx->d_out, ctx->b.f64, ctx->st));
     c[0].sweep = sweep;
     CU(cudaMemcpyAsync(ctx->b.d_ctl, c.data(), sizeof(Ctl), cudaMemcpyHostToDevice, ctx->st));
     CU(cudaStreamSynchronize(ctx->st));
@@ -1159,7 +1187,7 @@ mpr_status mpr_get_info(mpr_ctx* ctx, double* H_exact, double* H_tracked, double
     if (s != MPR_OK) return s;
     if (H_exact) {
         double* d = ctx->b.d_scratch + kScratch;
-        CU(launch_energy(&ctx->b.ents[0], lat_cur(ctx->b, c[0]), ctx->b.d_scratch, kScratch, d, ctx->st));
+        CU(launch_energy(&ctx->b.ents[0], lat_cur(ctx->b, c[0]), ctx->b.d_scratch, kScratch, d, ctx->b.f64, ctx->st));
         CU(cudaMemcpyAsync(H_exact, d, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
         CU(cudaStreamSynchronize(ctx->st));
     }

@@ -45,27 +45,38 @@ __global__ void k_minmax(const float* __restrict__ z, const uint8_t* __restrict_
 // Packs one grid into its two colour planes.  Samples get the Eq. 1 angle; gap sites
 // get phi = 2 pi u with u from the Philox stream {site, 0xFFFFFFFF, chain, 0}
 // (Algorithm 2, step 2.2).  Stored as (cos(phi/2), sin(phi/2)).
+// FP32 lattice: theta rounded to float, then sincosf; FP64 lattice: sincos of the double theta.
+// sin is clamped at 0: theta = pi rounds above pi in FP32; stay on the upper half circle.
+__device__ __forceinline__ void unit_at(double theta, float2& v) {
+    float s, co;
+    sincosf((float)theta, &s, &co);
+    v = make_float2(co, fmaxf(s, 0.0f));
+}
+__device__ __forceinline__ void unit_at(double theta, double2& v) {
+    double s, co;
+    sincos(theta, &s, &co);
+    v = make_double2(co, fmax(s, 0.0));
+}
+
+template <typename V>
 __global__ void k_pack(EntryDesc e, const float* __restrict__ z, const uint8_t* __restrict__ mask,
-                       double zmin, double scale, float2* __restrict__ lat, uint32_t key0,
+                       double zmin, double scale, V* __restrict__ lat, uint32_t key0,
                        uint32_t key1, int all_free) {
     const long long n = (long long)e.W * e.H;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(i / e.W), x = (int)(i - (long long)y * e.W);
         const int c = (x + y) & 1;
-        float theta;
+        double theta;
         if (!all_free && mask[i]) {
             const double phi = ((double)z[i] - zmin) * scale;          // Eq. 1
-            theta = (float)(0.5 * phi);
+            theta = 0.5 * phi;
         } else {
             const uint4 r = philox10(make_uint4((uint32_t)i, kInitSweep, e.chain, 0u), key0, key1);
-            theta = (float)(3.141592653589793 * (double)u24f(r.x));    // q * 2 pi u
+            theta = 3.141592653589793 * (double)u24f(r.x);             // q * 2 pi u
         }
-        float s, co;
-        sincosf(theta, &s, &co);
-        s = fmaxf(s, 0.0f);     // theta = pi rounds above pi in FP32: stay on the upper half circle
         const long long base = c ? e.plane[1] : e.plane[0];
-        lat[base + (long long)(y + 1) * e.pitch + (x >> 1) + kPadL] = make_float2(co, s);
+        unit_at(theta, lat[base + (long long)(y + 1) * e.pitch + (x >> 1) + kPadL]);
     }
 }
 
@@ -195,6 +206,49 @@ __global__ void k_sample_energy(EntryDesc e, const float* __restrict__ z,
     }
 }
 
+// Eq. 4 in FP64 (MPR_PREC_F64): the same pairs and partials, the cosine argument
+// q (z_i - z_j) 2 pi / (z_max - z_min) and every sum in double.
+__global__ void k_sample_energy64(EntryDesc e, const float* __restrict__ z,
+                                  const uint8_t* __restrict__ mask, double qs,
+                                  double* part_sum, unsigned long long* part_cnt) {
+    __shared__ double ssum[kThreads / 32];
+    __shared__ unsigned long long scnt[kThreads / 32];
+    double acc = 0.0;
+    unsigned long long cnt = 0;
+    for (int y = blockIdx.x; y < e.H; y += gridDim.x) {
+        const float* __restrict__ zr = z + (long long)y * e.W;
+        const uint8_t* __restrict__ mr = mask + (long long)y * e.W;
+        const bool down = y + 1 < e.H;
+        for (int x = threadIdx.x; x < e.W; x += blockDim.x) {
+            if (!mr[x]) continue;
+            const double zi = (double)zr[x];
+            if (x + 1 < e.W && mr[x + 1]) {
+                acc += cos(qs * (zi - (double)zr[x + 1]));
+                ++cnt;
+            }
+            if (down && mr[x + e.W]) {
+                acc += cos(qs * (zi - (double)zr[x + e.W]));
+                ++cnt;
+            }
+        }
+    }
+    acc = warp_sum(acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0) {
+        ssum[threadIdx.x >> 5] = acc;
+        scnt[threadIdx.x >> 5] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        unsigned long long c = 0;
+        for (int w = 0; w < kThreads / 32; ++w) { t += ssum[w]; c += scnt[w]; }
+        part_sum[blockIdx.x] = t;
+        part_cnt[blockIdx.x] = c;
+    }
+}
+
 __global__ void k_philox(const uint4* __restrict__ ctr, uint32_t k0, uint32_t k1,
                          uint4* __restrict__ out, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
@@ -219,10 +273,14 @@ cudaError_t launch_minmax(const float* z, const uint8_t* mask, long long n, unsi
 
 cudaError_t launch_pack(const EntryDesc* e, const float* z, const uint8_t* mask, double zmin,
                         double scale, float2* lat, uint32_t key0, uint32_t key1, int all_free,
-                        cudaStream_t st) {
+                        bool f64, cudaStream_t st) {
     count_launches(1, st);
-    k_pack<<<grid_for((long long)e->W * e->H), kThreads, 0, st>>>(*e, z, mask, zmin, scale, lat,
-                                                                   key0, key1, all_free);
+    const int g = grid_for((long long)e->W * e->H);
+    if (f64)
+        k_pack<double2><<<g, kThreads, 0, st>>>(*e, z, mask, zmin, scale, reinterpret_cast<double2*>(lat),
+                                               key0, key1, all_free);
+    else
+        k_pack<float2><<<g, kThreads, 0, st>>>(*e, z, mask, zmin, scale, lat, key0, key1, all_free);
     return cudaGetLastError();
 }
 
@@ -251,11 +309,12 @@ cudaError_t launch_gap_scatter(const EntryDesc* e, const uint8_t* mask, int all_
 
 cudaError_t launch_sample_energy(const EntryDesc* e, const float* z, const uint8_t* mask,
                                  double scale, double q, double* part_sum,
-                                 unsigned long long* part_cnt, int* nparts, cudaStream_t st) {
+                                 unsigned long long* part_cnt, int* nparts, bool f64, cudaStream_t st) {
     const int g = e->H < 1024 ? e->H : 1024;
     *nparts = g;
     count_launches(1, st);
-    k_sample_energy<<<g, kThreads, 0, st>>>(*e, z, mask, (float)(q * scale), part_sum, part_cnt);
+    if (f64) k_sample_energy64<<<g, kThreads, 0, st>>>(*e, z, mask, q * scale, part_sum, part_cnt);
+    else k_sample_energy<<<g, kThreads, 0, st>>>(*e, z, mask, (float)(q * scale), part_sum, part_cnt);
     return cudaGetLastError();
 }
 

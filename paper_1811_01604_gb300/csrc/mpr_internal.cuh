@@ -163,6 +163,8 @@ struct SweepArgs {
     float half_qd_fixed;      // q * pi / a for the fixed window
     int skip_stopped;         // skip entries whose relaxation has ended
     int or_mode;              // over-relaxation: OR_CONSERVING, OR_LITERAL or OR_NONE
+    int f64;                  // lattice of double2 and FP64 arithmetic (MPR_PREC_F64)
+    double half_qd_fixed64;   // q * pi / a for the fixed window, FP64 path
     RoundKeys rk;             // Philox round keys of the seed
 };
 
@@ -346,12 +348,76 @@ __device__ __forceinline__ float hybrid_update(float2& v, float C, float S, floa
     return (accepted ? dH : 0.0f) + dE_or;
 }
 
+// The same update in FP64 (MPR_PREC_F64): the steps and the unit-vector form above, with
+// exact division, the reflection about the field for any nonzero field, and the library's
+// double sin, cos and exp.
+//   neg_inv_T  -1/T
+__device__ __forceinline__ double hybrid_update64(double2& v, double C, double S, double Fx, double Fy,
+                                                  double hq, double r, double neg_inv_T, int or_mode,
+                                                  bool& accepted) {
+    double c = v.x, s = v.y;
+    double dE_or = 0.0;
+    if (or_mode == OR_LITERAL) {
+        const double F2 = fma(Fx, Fx, Fy * Fy);
+        if (F2 > 0.0) {
+            const double inv = 1.0 / sqrt(F2);
+            const double cp = Fx * inv, sp = Fy * inv;
+            double cl = fma(cp, c, sp * s), sl = fma(sp, c, -(cp * s));
+            if (sl < 0.0 || (sl == 0.0 && cl < 0.0)) {
+                cl = -cl;
+                sl = -sl;
+            }
+            dE_or = fma(c, C, s * S) - fma(cl, C, sl * S);
+            c = cl;
+            s = sl;
+        }
+    }
+    const double along = fma(c, C, s * S);
+    const double perp0 = fma(s, C, -(c * S));
+    const double R2 = fma(C, C, S * S);
+    bool refl = false;
+    if (or_mode == OR_CONSERVING && R2 > 0.0) {
+        const double f = 2.0 * along / R2;
+        const double cr = fma(f, C, -c), sr = fma(f, S, -s);
+        refl = sr > 0.0 || (sr == 0.0 && cr > 0.0);
+        if (refl) {
+            c = cr;
+            s = sr;
+        }
+    }
+    const double perp = refl ? -perp0 : perp0;
+    double sh, ch;
+    sincos(hq, &sh, &ch);
+    const double sn = 2.0 * sh * ch;
+    const double hh = 2.0 * sh * sh;
+    const double dH0 = fma(hh, along, sn * perp);
+    const double c20 = c - fma(c, hh, s * sn);
+    const double s20 = s - fma(s, hh, -(c * sn));
+    const bool wrap = s20 < 0.0 || (s20 == 0.0 && c20 < 0.0);
+    const double c2 = wrap ? -c20 : c20;
+    const double s2 = wrap ? -s20 : s20;
+    const double dH = wrap ? 2.0 * along - dH0 : dH0;
+    accepted = (dH <= 0.0) || (exp(dH * neg_inv_T) > r);
+    c = accepted ? c2 : c;
+    s = accepted ? s2 : s;
+    const double g = fma(-0.5, fma(c, c, s * s), 1.5);
+    v = make_double2(c * g, s * g);
+    return (accepted ? dH : 0.0) + dE_or;
+}
+
 // The field of Eq. 6 as printed (OR_LITERAL): sum of the four neighbours' (cos 2 theta,
 // sin 2 theta) from their unit vectors (cos theta, sin theta).
 __device__ __forceinline__ void literal_field(float2 a, float2 b, float2 c, float2 d, float& Fx, float& Fy) {
     Fx = (fmaf(a.x, a.x, -a.y * a.y) + fmaf(b.x, b.x, -b.y * b.y)) +
          (fmaf(c.x, c.x, -c.y * c.y) + fmaf(d.x, d.x, -d.y * d.y));
     Fy = 2.0f * ((a.x * a.y + b.x * b.y) + (c.x * c.y + d.x * d.y));
+}
+
+__device__ __forceinline__ void literal_field64(double2 a, double2 b, double2 c, double2 d, double& Fx,
+                                                double& Fy) {
+    Fx = (fma(a.x, a.x, -a.y * a.y) + fma(b.x, b.x, -b.y * b.y)) +
+         (fma(c.x, c.x, -c.y * c.y) + fma(d.x, d.x, -d.y * d.y));
+    Fy = 2.0 * ((a.x * a.y + b.x * b.y) + (c.x * c.y + d.x * d.y));
 }
 
 // The exponent scale kx of hybrid_update for a temperature given as -1/T.
@@ -420,9 +486,10 @@ __device__ __forceinline__ void control_step(Ctl& c, const EntryDesc& E, double 
 // init (mpr_init.cu)
 cudaError_t launch_minmax(const float* z, const uint8_t* mask, long long n, unsigned* keys,
                           unsigned long long* nsamples, cudaStream_t st);
+// f64: the lattice holds double2 vectors (same element offsets, twice the bytes).
 cudaError_t launch_pack(const EntryDesc* e_host, const float* z, const uint8_t* mask,
                         double zmin, double scale, float2* lat, uint32_t key0, uint32_t key1,
-                        int all_free, cudaStream_t st);
+                        int all_free, bool f64, cudaStream_t st);
 cudaError_t launch_gap_count(const EntryDesc* e_host, const uint8_t* mask, int all_free,
                              int* row_counts, cudaStream_t st);
 cudaError_t launch_scan_rows(int* row_counts, int nrows, int narrays, int* totals,
@@ -430,9 +497,10 @@ cudaError_t launch_scan_rows(int* row_counts, int nrows, int narrays, int* total
 cudaError_t launch_gap_scatter(const EntryDesc* e_host, const uint8_t* mask, int all_free,
                                const int* row_offsets, uint32_t* gaps, cudaStream_t st);
 // Eq. 4 partial sums: per block (sum of cosines, pair count) into part[block] (grid <= 1024).
+// f64: cosine arguments and row sums in FP64.
 cudaError_t launch_sample_energy(const EntryDesc* e_host, const float* z, const uint8_t* mask,
                                  double scale, double q, double* part_sum,
-                                 unsigned long long* part_cnt, int* nparts, cudaStream_t st);
+                                 unsigned long long* part_cnt, int* nparts, bool f64, cudaStream_t st);
 cudaError_t launch_philox(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, size_t n,
                           cudaStream_t st);
 
@@ -461,15 +529,18 @@ cudaError_t launch_control(Ctl* ctl, Part* const part[2], const EntryDesc* ents,
                            double* ehist, int ehist_stride, int* active, cudaStream_t st);
 // Eq. 2 of one grid: per-block partials then a fixed-order sum into *out (deterministic).
 cudaError_t launch_energy(const EntryDesc* e_host, const float2* lat, double* scratch,
-                          int scratch_len, double* out, cudaStream_t st);
+                          int scratch_len, double* out, bool f64, cudaStream_t st);
 cudaError_t launch_sum(const double* v, int n, double* out, cudaStream_t st);
 cudaError_t launch_set_tracked_energy(Ctl* ctl, const double* H, int n_ent, cudaStream_t st);
+// f64: acc holds doubles (same element offsets).
 cudaError_t launch_predict_out(const EntryDesc* e_host, const float2* lat, const uint32_t* gaps,
                                const float* acc, int M, double q, double zmin, double zmax,
-                               float* zhat, cudaStream_t st);
-cudaError_t launch_get_state(const EntryDesc* e_host, const float2* lat, float* phi,
+                               float* zhat, bool f64, cudaStream_t st);
+cudaError_t launch_get_state(const EntryDesc* e_host, const float2* lat, float* phi, bool f64,
                              cudaStream_t st);
+cudaError_t launch_get_state64(const EntryDesc* e_host, const float2* lat, double* phi, bool f64,
+                               cudaStream_t st);
 cudaError_t launch_set_state(const EntryDesc* e_host, float2* lat, const uint32_t* gaps,
-                             const float* phi, cudaStream_t st);
+                             const float* phi, bool f64, cudaStream_t st);
 
 }  // namespace mpr

@@ -77,6 +77,76 @@ k_half_sweep(const SweepArgs A, const int color) {
     }
 }
 
+// The half-sweep in FP64 (MPR_PREC_F64): the same work list, counters and partials, on a
+// lattice of double2 vectors with FP64 arithmetic throughout.
+template <bool ACC>
+__global__ void __launch_bounds__(kSweepThreads)
+k_half_sweep64(const SweepArgs A, const int color) {
+    const BlockWork w = (color ? A.work[1] : A.work[0])[blockIdx.x];
+    const EntryDesc* __restrict__ E = A.ents + w.entry;
+    const Ctl* ctl = A.ctl + w.entry;
+    if (A.skip_stopped && ctl->stop) return;
+    const double half_qd = A.use_ctl_a ? 0.5 * kTwoPi * 0.5 / ctl->a : A.half_qd_fixed64;
+    const double neg_inv_T = -1.0 / ctl->T;
+    const uint32_t sweep = ctl->sweep;
+    const int n = color ? E->ngap[1] : E->ngap[0], pitch = E->pitch, W = E->W;
+    const uint32_t chain = E->chain;
+    const long long gb = color ? E->gbase[1] : E->gbase[0];
+    const uint32_t* __restrict__ gl = A.gaps + gb;
+    double2* __restrict__ lat = reinterpret_cast<double2*>(A.lat);
+    double2* __restrict__ own = lat + (color ? E->plane[1] : E->plane[0]);
+    const double2* __restrict__ oth = lat + (color ? E->plane[0] : E->plane[1]);
+    double* __restrict__ acc = ACC ? reinterpret_cast<double*>(A.acc) + gb : nullptr;
+
+    double dE = 0.0;
+    unsigned nacc = 0;
+#pragma unroll
+    for (int it = 0; it < kSweepItems; ++it) {
+        const int g = w.first + it * kSweepThreads + (int)threadIdx.x;
+        if (g < n) {
+            const uint32_t ent = __ldg(gl + g);
+            const int y = (int)(ent >> 16), j = (int)(ent & 0xFFFFu);
+            const int s = color ^ (y & 1);
+            const long long k = (long long)(y + 1) * pitch + j + kPadL;
+            const double2 nu = oth[k - pitch], nd = oth[k + pitch];
+            const double2 nl = oth[k - 1 + s], nr = oth[k + s];
+            const double C = (nu.x + nd.x) + (nl.x + nr.x);
+            const double S = (nu.y + nd.y) + (nl.y + nr.y);
+            double2 v = own[k];
+            const uint32_t site = (uint32_t)y * (uint32_t)W + (uint32_t)(2 * j + s);
+            const uint4 rnd = philox10(make_uint4(site, sweep, chain, 0u), A.rk);
+            const double hq = ((double)u24f(rnd.x) - 0.5) * half_qd;
+            bool accepted;
+            double Fx = 0.0, Fy = 0.0;
+            if (A.or_mode == OR_LITERAL) literal_field64(nu, nd, nl, nr, Fx, Fy);
+            dE += hybrid_update64(v, C, S, Fx, Fy, hq, (double)u24f(rnd.y), neg_inv_T, A.or_mode, accepted);
+            nacc += accepted ? 1u : 0u;
+            own[k] = v;
+            if (ACC) acc[g] += atan2(v.y, v.x);
+        }
+    }
+    __shared__ double s_dE[kSweepThreads / 32];
+    __shared__ unsigned s_na[kSweepThreads / 32];
+    dE = warp_sum(dE);
+    nacc = warp_sum(nacc);
+    if ((threadIdx.x & 31) == 0) {
+        s_dE[threadIdx.x >> 5] = dE;
+        s_na[threadIdx.x >> 5] = nacc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        unsigned na = 0;
+#pragma unroll
+        for (int i = 0; i < kSweepThreads / 32; ++i) { t += s_dE[i]; na += s_na[i]; }
+        Part p;
+        p.dH = t;
+        p.nacc = na;
+        p._pad = 0;
+        (color ? A.part[1] : A.part[0])[blockIdx.x] = p;
+    }
+}
+
 // Per-sweep control, one block per entry.  The block first adds the sweep blocks'
 // partials of this entry in a fixed order (bitwise reproducible), then thread 0 runs
 //   CTL_RELAX : Algorithm 2 step 5 after one sweep (window 5.2, energy 5.3, slope 5.4, 5.5)
@@ -123,12 +193,22 @@ k_control(Ctl* ctl, Part* part0, Part* part1, const EntryDesc* __restrict__ ents
 
 // Eq. 2 over all bonds of one grid: each colour-0 site with its four colour-1 neighbours
 // (padding contributes 0).  cos(theta_i - theta_j) = c_i c_j + s_i s_j.  One partial per block.
-__global__ void k_energy(EntryDesc e, const float2* __restrict__ lat, double* part) {
+__device__ __forceinline__ double bond_sum(float2 v, float2 a, float2 b, float2 l, float2 r) {
+    return (double)fmaf(v.x, a.x, v.y * a.y) + (double)fmaf(v.x, b.x, v.y * b.y) +
+           (double)fmaf(v.x, l.x, v.y * l.y) + (double)fmaf(v.x, r.x, v.y * r.y);
+}
+__device__ __forceinline__ double bond_sum(double2 v, double2 a, double2 b, double2 l, double2 r) {
+    return fma(v.x, a.x, v.y * a.y) + fma(v.x, b.x, v.y * b.y) + fma(v.x, l.x, v.y * l.y) +
+           fma(v.x, r.x, v.y * r.y);
+}
+
+template <typename V>
+__global__ void k_energy(EntryDesc e, const V* __restrict__ lat, double* part) {
     __shared__ double sw[8];
     const int Wc = (e.W + 1) >> 1;
     const long long n = (long long)e.H * Wc;
-    const float2* p0 = lat + e.plane[0];
-    const float2* p1 = lat + e.plane[1];
+    const V* p0 = lat + e.plane[0];
+    const V* p1 = lat + e.plane[1];
     double acc = 0.0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x) {
@@ -136,10 +216,7 @@ __global__ void k_energy(EntryDesc e, const float2* __restrict__ lat, double* pa
         const int s = y & 1;                                     // colour 0: s = y & 1
         if (2 * j + s >= e.W) continue;
         const long long k = (long long)(y + 1) * e.pitch + j + kPadL;
-        const float2 v = p0[k];
-        const float2 a = p1[k - e.pitch], b = p1[k + e.pitch], l = p1[k - 1 + s], r = p1[k + s];
-        acc -= (double)fmaf(v.x, a.x, v.y * a.y) + (double)fmaf(v.x, b.x, v.y * b.y) +
-               (double)fmaf(v.x, l.x, v.y * l.y) + (double)fmaf(v.x, r.x, v.y * r.y);
+        acc -= bond_sum(p0[k], p1[k - e.pitch], p1[k + e.pitch], p1[k - 1 + s], p1[k + s]);
     }
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
@@ -172,8 +249,9 @@ __global__ void k_set_tracked_energy(Ctl* ctl, const double* H, int n_ent) {
 
 // Algorithm 2 step 7: zhat = G^-1(mean phi) at gap sites (G affine, so this equals the
 // mean of the back-transformed realizations).  Sample sites are copied beforehand.
+template <typename A>
 __global__ void k_predict_out(EntryDesc e, const uint32_t* __restrict__ gaps,
-                              const float* __restrict__ acc, int M, double q, double zmin,
+                              const A* __restrict__ acc, int M, double q, double zmin,
                               double zmax, float* __restrict__ zhat) {
     const int P = e.ngap[0] + e.ngap[1];
     const double f = (zmax - zmin) / (kTwoPi * q * (double)M);
@@ -189,20 +267,42 @@ __global__ void k_predict_out(EntryDesc e, const uint32_t* __restrict__ gaps,
     }
 }
 
-// phi = 2 theta, theta the angle of (cos, sin) in [0, pi], for every site of one grid.
-__global__ void k_get_state(EntryDesc e, const float2* __restrict__ lat, float* __restrict__ phi) {
+// phi = 2 theta, theta the angle of (cos, sin) in [0, pi], for every site of one grid:
+// FP32 vectors to float by the polynomial angle, anything to double by atan2 in FP64.
+__device__ __forceinline__ void put_angle(float2 v, float& out) { out = 2.0f * angle_upper(v.x, fmaxf(v.y, 0.0f)); }
+__device__ __forceinline__ void put_angle(float2 v, double& out) { out = 2.0 * atan2(fmax((double)v.y, 0.0), (double)v.x); }
+__device__ __forceinline__ void put_angle(double2 v, double& out) { out = 2.0 * atan2(fmax(v.y, 0.0), v.x); }
+__device__ __forceinline__ void put_angle(double2 v, float& out) {
+    double d;
+    put_angle(v, d);
+    out = (float)d;
+}
+
+template <typename V, typename O>
+__global__ void k_get_state(EntryDesc e, const V* __restrict__ lat, O* __restrict__ phi) {
     const long long n = (long long)e.W * e.H;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(i / e.W), x = (int)(i - (long long)y * e.W);
         const long long base = ((x + y) & 1) ? e.plane[1] : e.plane[0];
-        const float2 v = lat[base + (long long)(y + 1) * e.pitch + (x >> 1) + kPadL];
-        phi[i] = 2.0f * angle_upper(v.x, fmaxf(v.y, 0.0f));
+        put_angle(lat[base + (long long)(y + 1) * e.pitch + (x >> 1) + kPadL], phi[i]);
     }
 }
 
+__device__ __forceinline__ void unit_half(float phi, float2& v) {
+    float s, co;
+    sincosf(0.5f * phi, &s, &co);
+    v = make_float2(co, fmaxf(s, 0.0f));
+}
+__device__ __forceinline__ void unit_half(float phi, double2& v) {
+    double s, co;
+    sincos(0.5 * (double)phi, &s, &co);
+    v = make_double2(co, fmax(s, 0.0));
+}
+
 // Writes gap sites from phi (samples untouched).
-__global__ void k_set_state(EntryDesc e, float2* __restrict__ lat, const uint32_t* __restrict__ gaps,
+template <typename V>
+__global__ void k_set_state(EntryDesc e, V* __restrict__ lat, const uint32_t* __restrict__ gaps,
                             const float* __restrict__ phi) {
     const int P = e.ngap[0] + e.ngap[1];
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < P; g += gridDim.x * blockDim.x) {
@@ -211,11 +311,8 @@ __global__ void k_set_state(EntryDesc e, float2* __restrict__ lat, const uint32_
         const uint32_t ent = gaps[gi];
         const int y = (int)(ent >> 16), j = (int)(ent & 0xFFFFu);
         const int x = 2 * j + (c ^ (y & 1));
-        float s, co;
-        sincosf(0.5f * phi[(long long)y * e.W + x], &s, &co);
-        s = fmaxf(s, 0.0f);
         const long long base = c ? e.plane[1] : e.plane[0];
-        lat[base + (long long)(y + 1) * e.pitch + j + kPadL] = make_float2(co, s);
+        unit_half(phi[(long long)y * e.W + x], lat[base + (long long)(y + 1) * e.pitch + j + kPadL]);
     }
 }
 
@@ -232,7 +329,10 @@ cudaError_t launch_half_sweep(const SweepArgs& a, int color, int trig, cudaStrea
     if (nb == 0) return cudaSuccess;
     const bool acc = a.acc != nullptr;
     count_launches(1, st);
-    if (trig == TRIG_FAST) {
+    if (a.f64) {
+        if (acc) k_half_sweep64<true><<<nb, kSweepThreads, 0, st>>>(a, color);
+        else k_half_sweep64<false><<<nb, kSweepThreads, 0, st>>>(a, color);
+    } else if (trig == TRIG_FAST) {
         if (acc) k_half_sweep<TRIG_FAST, true><<<nb, kSweepThreads, 0, st>>>(a, color);
         else k_half_sweep<TRIG_FAST, false><<<nb, kSweepThreads, 0, st>>>(a, color);
     } else {
@@ -252,12 +352,13 @@ cudaError_t launch_control(Ctl* ctl, Part* const part[2], const EntryDesc* ents,
 }
 
 cudaError_t launch_energy(const EntryDesc* e_host, const float2* lat, double* scratch,
-                          int scratch_len, double* out, cudaStream_t st) {
+                          int scratch_len, double* out, bool f64, cudaStream_t st) {
     const long long n = (long long)e_host->H * ((e_host->W + 1) >> 1);
     int g = grid_for(n, 256);
     if (g > scratch_len) g = scratch_len;
     count_launches(1, st);
-    k_energy<<<g, 256, 0, st>>>(*e_host, lat, scratch);
+    if (f64) k_energy<double2><<<g, 256, 0, st>>>(*e_host, reinterpret_cast<const double2*>(lat), scratch);
+    else k_energy<float2><<<g, 256, 0, st>>>(*e_host, lat, scratch);
     count_launches(1, st);
     k_sum<<<1, 256, 0, st>>>(scratch, g, out);
     return cudaGetLastError();
@@ -277,27 +378,45 @@ cudaError_t launch_set_tracked_energy(Ctl* ctl, const double* H, int n_ent, cuda
 
 cudaError_t launch_predict_out(const EntryDesc* e_host, const float2*, const uint32_t* gaps,
                                const float* acc, int M, double q, double zmin, double zmax,
-                               float* zhat, cudaStream_t st) {
+                               float* zhat, bool f64, cudaStream_t st) {
     const long long P = (long long)e_host->ngap[0] + e_host->ngap[1];
     if (P == 0) return cudaSuccess;
     count_launches(1, st);
-    k_predict_out<<<grid_for(P, 256), 256, 0, st>>>(*e_host, gaps, acc, M, q, zmin, zmax, zhat);
+    const int g = grid_for(P, 256);
+    if (f64)
+        k_predict_out<double><<<g, 256, 0, st>>>(*e_host, gaps, reinterpret_cast<const double*>(acc), M, q,
+                                                 zmin, zmax, zhat);
+    else
+        k_predict_out<float><<<g, 256, 0, st>>>(*e_host, gaps, acc, M, q, zmin, zmax, zhat);
     return cudaGetLastError();
 }
 
-cudaError_t launch_get_state(const EntryDesc* e_host, const float2* lat, float* phi,
+cudaError_t launch_get_state(const EntryDesc* e_host, const float2* lat, float* phi, bool f64,
                              cudaStream_t st) {
     count_launches(1, st);
-    k_get_state<<<grid_for((long long)e_host->W * e_host->H, 256), 256, 0, st>>>(*e_host, lat, phi);
+    const int g = grid_for((long long)e_host->W * e_host->H, 256);
+    if (f64) k_get_state<double2, float><<<g, 256, 0, st>>>(*e_host, reinterpret_cast<const double2*>(lat), phi);
+    else k_get_state<float2, float><<<g, 256, 0, st>>>(*e_host, lat, phi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_state64(const EntryDesc* e_host, const float2* lat, double* phi, bool f64,
+                               cudaStream_t st) {
+    count_launches(1, st);
+    const int g = grid_for((long long)e_host->W * e_host->H, 256);
+    if (f64) k_get_state<double2, double><<<g, 256, 0, st>>>(*e_host, reinterpret_cast<const double2*>(lat), phi);
+    else k_get_state<float2, double><<<g, 256, 0, st>>>(*e_host, lat, phi);
     return cudaGetLastError();
 }
 
 cudaError_t launch_set_state(const EntryDesc* e_host, float2* lat, const uint32_t* gaps,
-                             const float* phi, cudaStream_t st) {
+                             const float* phi, bool f64, cudaStream_t st) {
     const long long P = (long long)e_host->ngap[0] + e_host->ngap[1];
     if (P == 0) return cudaSuccess;
     count_launches(1, st);
-    k_set_state<<<grid_for(P, 256), 256, 0, st>>>(*e_host, lat, gaps, phi);
+    const int g = grid_for(P, 256);
+    if (f64) k_set_state<double2><<<g, 256, 0, st>>>(*e_host, reinterpret_cast<double2*>(lat), gaps, phi);
+    else k_set_state<float2><<<g, 256, 0, st>>>(*e_host, lat, gaps, phi);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@ MPR_OK, MPR_EINVAL, MPR_ENOMEM, MPR_ECUDA, MPR_ENODATA, MPR_ENOPAIRS, MPR_ETIMEO
 MPR_OR_CONSERVING, MPR_OR_LITERAL, MPR_OR_NONE = 0, 1, 2
 MPR_TRIG_ACCURATE, MPR_TRIG_FAST = 0, 1
 MPR_EXEC_AUTO, MPR_EXEC_LIST, MPR_EXEC_TILE = 0, 1, 2
+MPR_PREC_F32, MPR_PREC_F64 = 0, 1
 
 
 class MprError(RuntimeError):
@@ -36,7 +37,7 @@ class mpr_params(ctypes.Structure):
         ("trig_mode", ctypes.c_int), ("a_eq", ctypes.c_double), ("KT", ctypes.c_int),
         ("T_min", ctypes.c_double), ("T_max", ctypes.c_double), ("T_cap", ctypes.c_int),
         ("M_T", ctypes.c_int), ("exec_mode", ctypes.c_int), ("chain", ctypes.c_uint32),
-        ("tile_cfg", ctypes.c_int),
+        ("tile_cfg", ctypes.c_int), ("precision", ctypes.c_int),
     ]
 
 
@@ -84,6 +85,7 @@ _SIGS = [
                                       ctypes.POINTER(ctypes.c_longlong), _VP]),
     ("mpr_philox", _I, [_VP, ctypes.c_uint64, _VP, ctypes.c_size_t, _VP]),
     ("mpr_get_state_batch", _I, [_VP, _I, _VP]),
+    ("mpr_get_state64", _I, [_VP, _VP, ctypes.POINTER(ctypes.c_uint32)]),
     # include/mpr_net.h
     ("mpr_net_create", _I, [ctypes.POINTER(_VP), ctypes.c_uint64, _VP]),
     ("mpr_net_create_strided", _I, [ctypes.POINTER(_VP), ctypes.c_uint64, ctypes.c_int, _VP]),
@@ -272,6 +274,12 @@ def mpr_last_error(ctx) -> str:
 def mpr_get_state(ctx, phi) -> int:
     sw = ctypes.c_uint32()
     _check(ctx, lib().mpr_get_state(ctx, _ptr(phi), ctypes.byref(sw)))
+    return sw.value
+
+
+def mpr_get_state64(ctx, phi) -> int:
+    sw = ctypes.c_uint32()
+    _check(ctx, lib().mpr_get_state64(ctx, _ptr(phi), ctypes.byref(sw)))
     return sw.value
 
 
