@@ -5,7 +5,7 @@
  * Massive Spatial Data based on the Modified Planar Rotator Model".  A grid
  * G = G_S u G_P holds sample values Z_s at the sample sites G_S; the library
  * returns estimates Z_p at the prediction (gap) sites G_P (Sect. 2.1) by
- * conditional hybrid Monte Carlo of the MPR model (Eq. 2, q = 1/2), following
+ * conditional hybrid Monte Carlo of the MPR model (Eq. 2), following
  * Algorithm 2: data-to-angle map (Eq. 1), temperature inference by specific
  * energy matching (Eqs. 4-5), relaxation with the hybrid update of Algorithm 1
  * until the energy slope test passes, M equilibrium sweeps and the inverse map.
@@ -22,7 +22,10 @@
  *  - Errors are returned as mpr_status; nothing is thrown across the ABI.
  *    mpr_last_error(ctx) gives a one-line description of the last failure.
  *  - A context is not thread-safe: use one context per host thread / stream.
- *  - Only q = 1/2 (the paper's value) is implemented by the kernels.
+ *  - The coupling q of Eq. 2 is the paper's 1/2 by default; any q in (0, 1/2] is
+ *    accepted (the paper bounds q by 1/2 and fixes it there), q < 1/2 on the LIST
+ *    kernels with the conserving or no reflection.  Angles are kept as unit vectors
+ *    (cos q phi, sin q phi), q phi in [0, 2 pi q).
  */
 #ifndef MPR_H_
 #define MPR_H_
@@ -79,7 +82,8 @@ enum { MPR_PREC_F32 = 0, MPR_PREC_F64 = 1 };
  */
 typedef struct {
     uint64_t seed;     /* Philox4x32-10 key; counter = {site, sweep, chain, 0} */
-    double q;          /* coupling of Eq. 2; must be 0.5 */
+    double q;          /* coupling of Eq. 2, in (0, 1/2] (default 1/2); q < 1/2 needs exec_mode
+                          AUTO or LIST and or_mode CONSERVING or NONE, else MPR_EINVAL */
     double A_targ;     /* target Metropolis acceptance ratio (default 0.3) */
     double k_a;        /* a(i+1) = 1 + (i+1)/k_a when A < A_targ (default 3) */
     int n_f;           /* slope test every n_f sweeps (default 5) */

@@ -277,7 +277,7 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
                        const uint8_t* mask_base, bool same_grid = false) {
     cudaStream_t st = ctx->st;
     b.f64 = ctx->prm.precision == MPR_PREC_F64;
-    b.tiled = ctx->prm.exec_mode != MPR_EXEC_LIST && !b.f64;
+    b.tiled = ctx->prm.exec_mode != MPR_EXEC_LIST && !b.f64 && ctx->prm.q == 0.5;
     const size_t wide = b.f64 ? 2 : 1;     // float2 slots per lattice element, floats per average
     const uint32_t k0 = (uint32_t)ctx->prm.seed, k1 = (uint32_t)(ctx->prm.seed >> 32);
     b.n_ent = (int)grids.size();
@@ -297,6 +297,9 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
         E.plane[1] = (long long)(lat + plane);
         lat += 2 * plane;
         E.chain = grids[e].chain;
+        E.q = ctx->prm.q;
+        E.cQ = std::cos(kTwoPi * E.q);
+        E.sQ = std::sin(kTwoPi * E.q);
         E.ngp = (double)E.W * (E.H - 1) + (double)E.H * (E.W - 1);
         E.site0 = same_grid ? 0 : site0;
         site0 += (long long)E.W * E.H;
@@ -415,6 +418,7 @@ SweepArgs sweep_args(const mpr_ctx* ctx, const Batch& b, bool use_ctl_a, double 
     A.skip_stopped = skip_stopped ? 1 : 0;
     A.or_mode = ctx->prm.or_mode;
     A.f64 = b.f64 ? 1 : 0;
+    A.genq = ctx->prm.q != 0.5 ? 1 : 0;
     A.half_qd_fixed64 = 0.5 * kTwoPi * ctx->prm.q / a_fixed;
     A.rk = round_keys(ctx->prm.seed);
     return A;
@@ -707,7 +711,11 @@ void mpr_free(mpr_ctx* ctx) {
 }
 
 static mpr_status check_params(const mpr_params* p, std::string& why) {
-    if (!(p->q == 0.5)) { why = "only q = 0.5 is implemented"; return MPR_EINVAL; }
+    if (!(p->q > 0.0 && p->q <= 0.5)) { why = "q must lie in (0, 1/2]"; return MPR_EINVAL; }
+    if (p->q != 0.5 && (p->exec_mode == MPR_EXEC_TILE || p->or_mode == MPR_OR_LITERAL)) {
+        why = "q < 1/2 runs the LIST kernels with the conserving or no reflection";
+        return MPR_EINVAL;
+    }
     if (!(p->A_targ >= 0.0 && p->A_targ <= 1.0)) { why = "A_targ must lie in [0, 1]"; return MPR_EINVAL; }
     if (!(p->k_a > 0.0)) { why = "k_a must be > 0"; return MPR_EINVAL; }
     if (p->n_f < 1 || p->n_fit < 2 || p->i_max < 0 || p->M < 1) { why = "n_f >= 1, n_fit >= 2, i_max >= 0, M >= 1"; return MPR_EINVAL; }
@@ -1087,6 +1095,7 @@ mpr_status mpr_warmstart_init(mpr_ctx* ctx, mpr_net* net) {
     if (!ctx || !net) return MPR_EINVAL;
     Batch& b = ctx->b;
     if (b.f64) return fail(ctx, MPR_EINVAL, "the warm start writes an FP32 lattice");
+    if (ctx->prm.q != 0.5) return fail(ctx, MPR_EINVAL, "the warm start writes theta = phi / 2 (q = 1/2)");
     float2* lat1 = b.tiled ? b.d_lat2 : nullptr;
     const int n = (int)ctx->g.size();
     for (int i = 0; i < n;) {

@@ -44,7 +44,7 @@ __global__ void k_minmax(const float* __restrict__ z, const uint8_t* __restrict_
 
 // Packs one grid into its two colour planes.  Samples get the Eq. 1 angle; gap sites
 // get phi = 2 pi u with u from the Philox stream {site, 0xFFFFFFFF, chain, 0}
-// (Algorithm 2, step 2.2).  Stored as (cos(phi/2), sin(phi/2)).
+// (Algorithm 2, step 2.2).  Stored as (cos(q phi), sin(q phi)).
 // FP32 lattice: theta rounded to float, then sincosf; FP64 lattice: sincos of the double theta.
 // sin is clamped at 0: theta = pi rounds above pi in FP32; stay on the upper half circle.
 __device__ __forceinline__ void unit_at(double theta, float2& v) {
@@ -70,10 +70,10 @@ __global__ void k_pack(EntryDesc e, const float* __restrict__ z, const uint8_t* 
         double theta;
         if (!all_free && mask[i]) {
             const double phi = ((double)z[i] - zmin) * scale;          // Eq. 1
-            theta = 0.5 * phi;
+            theta = e.q * phi;
         } else {
             const uint4 r = philox10(make_uint4((uint32_t)i, kInitSweep, e.chain, 0u), key0, key1);
-            theta = 3.141592653589793 * (double)u24f(r.x);             // q * 2 pi u
+            theta = kTwoPi * e.q * (double)u24f(r.x);                  // q * 2 pi u
         }
         const long long base = c ? e.plane[1] : e.plane[0];
         unit_at(theta, lat[base + (long long)(y + 1) * e.pitch + (x >> 1) + kPadL]);

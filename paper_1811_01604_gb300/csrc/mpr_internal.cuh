@@ -46,6 +46,8 @@ struct EntryDesc {            // immutable during a run
     int ntiles;               // number of tiles of this entry
     int prows;                // rows allocated per plane: max(H + 2, tallest tile box)
     int _pad2;
+    double q;                 // coupling of Eq. 2: theta = q phi in [0, 2 pi q)
+    double cQ, sQ;            // cos and sin of Q = 2 pi q, the end of the range of theta
 };
 
 struct Ctl {                  // mutable per-entry control state (Algorithm 2)
@@ -164,6 +166,7 @@ struct SweepArgs {
     int skip_stopped;         // skip entries whose relaxation has ended
     int or_mode;              // over-relaxation: OR_CONSERVING, OR_LITERAL or OR_NONE
     int f64;                  // lattice of double2 and FP64 arithmetic (MPR_PREC_F64)
+    int genq;                 // q < 1/2: the arc tests and turns of hybrid_update<., true>
     double half_qd_fixed64;   // q * pi / a for the fixed window, FP64 path
     RoundKeys rk;             // Philox round keys of the seed
 };
@@ -266,7 +269,7 @@ enum { TRIG_ACCURATE = 0, TRIG_FAST = 1 };
 // Over-relaxation modes (the values of mpr_params::or_mode).
 enum { OR_CONSERVING = 0, OR_LITERAL = 1, OR_NONE = 2 };
 
-// One gap-site update (Algorithm 1) in unit-vector form, q = 1/2, theta = phi/2 in [0, pi).
+// One gap-site update (Algorithm 1) in unit-vector form, theta = q phi (q = 1/2: in [0, pi)).
 //   v        current (cos theta, sin theta) of the site
 //   C, S     local field: sums of the neighbours' cos/sin
 //   Fx, Fy   OR_LITERAL only: sum of the neighbours' (cos phi_j, sin phi_j) = (cos 2 theta_j,
@@ -283,9 +286,24 @@ __device__ __forceinline__ float ex2_approx(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-template <int TRIG>
+// theta of (c, s) in [0, Q), Q = 2 pi q <= pi: on the upper half circle (theta = 0
+// included) and before (cQ, sQ), i.e. sin(Q - theta) > 0.
+__device__ __forceinline__ bool in_arc(float c, float s, float cQ, float sQ) {
+    return (s > 0.0f || (s == 0.0f && c > 0.0f)) && (s == 0.0f || fmaf(sQ, c, -(cQ * s)) > 0.0f);
+}
+__device__ __forceinline__ bool in_arc(double c, double s, double cQ, double sQ) {
+    return (s > 0.0 || (s == 0.0 && c > 0.0)) && (s == 0.0 || fma(sQ, c, -(cQ * s)) > 0.0);
+}
+
+// GQ (q < 1/2): theta lives on the arc [0, Q); the reflection is kept only inside it, and
+// the proposal's modulo 2 pi in phi is a turn by -Q above the arc or +Q below it (the step
+// is at most pi q / a <= Q / 2, so one turn lands inside); dH is then taken from the new
+// vector.  Without GQ (q = 1/2, Q = pi) the arc is the upper half circle and the turn a
+// negation, written out below without the general tests.
+template <int TRIG, bool GQ = false>
 __device__ __forceinline__ float hybrid_update(float2& v, float C, float S, float Fx, float Fy, float hq,
-                                               float r, float kx, int or_mode, bool& accepted) {
+                                               float r, float kx, int or_mode, bool& accepted,
+                                               float cQ = -1.0f, float sQ = 0.0f) {
     float c = v.x, s = v.y;
     float dE_or = 0.0f;
     if (or_mode == OR_LITERAL) {
@@ -315,7 +333,8 @@ __device__ __forceinline__ float hybrid_update(float2& v, float C, float S, floa
     // reflection factor 2 (v.n)/|n|^2; a 2-ulp quotient moves the image by ~2e-7 rad
     const float f = __fdividef(2.0f * along, R2);
     const float cr = fmaf(f, C, -c), sr = fmaf(f, S, -s);
-    const bool refl = or_mode == OR_CONSERVING && R2 > 1e-12f && (sr > 0.0f || (sr == 0.0f && cr > 0.0f));
+    const bool refl = or_mode == OR_CONSERVING && R2 > 1e-12f &&
+                      (GQ ? in_arc(cr, sr, cQ, sQ) : (sr > 0.0f || (sr == 0.0f && cr > 0.0f)));
     c = refl ? cr : c;
     s = refl ? sr : s;
     const float perp = refl ? -perp0 : perp0;     // the reflection keeps `along`, flips `perp`
@@ -332,11 +351,21 @@ __device__ __forceinline__ float hybrid_update(float2& v, float C, float S, floa
     const float dH0 = fmaf(hh, along, sn * perp);
     const float c20 = c - fmaf(c, hh, s * sn);
     const float s20 = s - fmaf(s, hh, -(c * sn));
-    // modulo 2 pi in phi is a half turn in theta: negate the vector, dH -> 2 along - dH
-    const bool wrap = s20 < 0.0f || (s20 == 0.0f && c20 < 0.0f);
-    const float c2 = wrap ? -c20 : c20;
-    const float s2 = wrap ? -s20 : s20;
-    const float dH = wrap ? 2.0f * along - dH0 : dH0;
+    float c2, s2, dH;
+    if (GQ) {
+        const bool inside = in_arc(c20, s20, cQ, sQ);
+        const bool below = !inside && s20 < 0.0f && c20 > 0.0f;
+        const float sb = below ? sQ : -sQ;                     // sin of the turn +-Q
+        c2 = inside ? c20 : fmaf(c20, cQ, -(s20 * sb));
+        s2 = inside ? s20 : fmaf(c20, sb, s20 * cQ);
+        dH = inside ? dH0 : along - fmaf(c2, C, s2 * S);
+    } else {
+        // modulo 2 pi in phi is a half turn in theta: negate the vector, dH -> 2 along - dH
+        const bool wrap = s20 < 0.0f || (s20 == 0.0f && c20 < 0.0f);
+        c2 = wrap ? -c20 : c20;
+        s2 = wrap ? -s20 : s20;
+        dH = wrap ? 2.0f * along - dH0 : dH0;
+    }
     // steps 5-6: accept if min(1, exp(-dH/T)) > r
     const float ap = (TRIG == TRIG_FAST) ? ex2_approx(dH * kx) : expf(dH * kx);
     accepted = (dH <= 0.0f) || (ap > r);
@@ -352,9 +381,10 @@ __device__ __forceinline__ float hybrid_update(float2& v, float C, float S, floa
 // exact division, the reflection about the field for any nonzero field, and the library's
 // double sin, cos and exp.
 //   neg_inv_T  -1/T
+template <bool GQ = false>
 __device__ __forceinline__ double hybrid_update64(double2& v, double C, double S, double Fx, double Fy,
                                                   double hq, double r, double neg_inv_T, int or_mode,
-                                                  bool& accepted) {
+                                                  bool& accepted, double cQ = -1.0, double sQ = 0.0) {
     double c = v.x, s = v.y;
     double dE_or = 0.0;
     if (or_mode == OR_LITERAL) {
@@ -379,7 +409,7 @@ __device__ __forceinline__ double hybrid_update64(double2& v, double C, double S
     if (or_mode == OR_CONSERVING && R2 > 0.0) {
         const double f = 2.0 * along / R2;
         const double cr = fma(f, C, -c), sr = fma(f, S, -s);
-        refl = sr > 0.0 || (sr == 0.0 && cr > 0.0);
+        refl = GQ ? in_arc(cr, sr, cQ, sQ) : (sr > 0.0 || (sr == 0.0 && cr > 0.0));
         if (refl) {
             c = cr;
             s = sr;
@@ -393,10 +423,20 @@ __device__ __forceinline__ double hybrid_update64(double2& v, double C, double S
     const double dH0 = fma(hh, along, sn * perp);
     const double c20 = c - fma(c, hh, s * sn);
     const double s20 = s - fma(s, hh, -(c * sn));
-    const bool wrap = s20 < 0.0 || (s20 == 0.0 && c20 < 0.0);
-    const double c2 = wrap ? -c20 : c20;
-    const double s2 = wrap ? -s20 : s20;
-    const double dH = wrap ? 2.0 * along - dH0 : dH0;
+    double c2, s2, dH;
+    if (GQ) {
+        const bool inside = in_arc(c20, s20, cQ, sQ);
+        const bool below = !inside && s20 < 0.0 && c20 > 0.0;
+        const double sb = below ? sQ : -sQ;
+        c2 = inside ? c20 : fma(c20, cQ, -(s20 * sb));
+        s2 = inside ? s20 : fma(c20, sb, s20 * cQ);
+        dH = inside ? dH0 : along - fma(c2, C, s2 * S);
+    } else {
+        const bool wrap = s20 < 0.0 || (s20 == 0.0 && c20 < 0.0);
+        c2 = wrap ? -c20 : c20;
+        s2 = wrap ? -s20 : s20;
+        dH = wrap ? 2.0 * along - dH0 : dH0;
+    }
     accepted = (dH <= 0.0) || (exp(dH * neg_inv_T) > r);
     c = accepted ? c2 : c;
     s = accepted ? s2 : s;

@@ -9,14 +9,15 @@ namespace {
 
 // Half-sweep: every gap site of one colour (all entries), Algorithm 1.
 // Blocks come from a work list (entry, first gap) so that grids of any size share a launch.
-template <int TRIG, bool ACC>
+template <int TRIG, bool ACC, bool GQ>
 __global__ void __launch_bounds__(kSweepThreads)
 k_half_sweep(const SweepArgs A, const int color) {
     const BlockWork w = (color ? A.work[1] : A.work[0])[blockIdx.x];
     const EntryDesc* __restrict__ E = A.ents + w.entry;
     const Ctl* ctl = A.ctl + w.entry;
     if (A.skip_stopped && ctl->stop) return;
-    const float half_qd = A.use_ctl_a ? (float)(0.5 * kTwoPi * 0.5 / ctl->a) : A.half_qd_fixed;
+    const float half_qd = A.use_ctl_a ? (float)(0.5 * kTwoPi * E->q / ctl->a) : A.half_qd_fixed;
+    const float cQ = (float)E->cQ, sQ = (float)E->sQ;
     const float kx = accept_scale<TRIG>((float)(-1.0 / ctl->T));
     const uint32_t sweep = ctl->sweep;
     const int n = color ? E->ngap[1] : E->ngap[0], pitch = E->pitch, W = E->W;
@@ -48,7 +49,7 @@ k_half_sweep(const SweepArgs A, const int color) {
             bool accepted;
             float Fx = 0.0f, Fy = 0.0f;
             if (A.or_mode == OR_LITERAL) literal_field(nu, nd, nl, nr, Fx, Fy);
-            dE += hybrid_update<TRIG>(v, C, S, Fx, Fy, hq, u24f(rnd.y), kx, A.or_mode, accepted);
+            dE += hybrid_update<TRIG, GQ>(v, C, S, Fx, Fy, hq, u24f(rnd.y), kx, A.or_mode, accepted, cQ, sQ);
             nacc += accepted ? 1u : 0u;
             own[k] = v;
             if (ACC) acc[g] += angle_upper(v.x, v.y);
@@ -79,14 +80,15 @@ k_half_sweep(const SweepArgs A, const int color) {
 
 // The half-sweep in FP64 (MPR_PREC_F64): the same work list, counters and partials, on a
 // lattice of double2 vectors with FP64 arithmetic throughout.
-template <bool ACC>
+template <bool ACC, bool GQ>
 __global__ void __launch_bounds__(kSweepThreads)
 k_half_sweep64(const SweepArgs A, const int color) {
     const BlockWork w = (color ? A.work[1] : A.work[0])[blockIdx.x];
     const EntryDesc* __restrict__ E = A.ents + w.entry;
     const Ctl* ctl = A.ctl + w.entry;
     if (A.skip_stopped && ctl->stop) return;
-    const double half_qd = A.use_ctl_a ? 0.5 * kTwoPi * 0.5 / ctl->a : A.half_qd_fixed64;
+    const double half_qd = A.use_ctl_a ? 0.5 * kTwoPi * E->q / ctl->a : A.half_qd_fixed64;
+    const double cQ = E->cQ, sQ = E->sQ;
     const double neg_inv_T = -1.0 / ctl->T;
     const uint32_t sweep = ctl->sweep;
     const int n = color ? E->ngap[1] : E->ngap[0], pitch = E->pitch, W = E->W;
@@ -119,7 +121,8 @@ k_half_sweep64(const SweepArgs A, const int color) {
             bool accepted;
             double Fx = 0.0, Fy = 0.0;
             if (A.or_mode == OR_LITERAL) literal_field64(nu, nd, nl, nr, Fx, Fy);
-            dE += hybrid_update64(v, C, S, Fx, Fy, hq, (double)u24f(rnd.y), neg_inv_T, A.or_mode, accepted);
+            dE += hybrid_update64<GQ>(v, C, S, Fx, Fy, hq, (double)u24f(rnd.y), neg_inv_T, A.or_mode, accepted,
+                                      cQ, sQ);
             nacc += accepted ? 1u : 0u;
             own[k] = v;
             if (ACC) acc[g] += atan2(v.y, v.x);
@@ -269,34 +272,41 @@ __global__ void k_predict_out(EntryDesc e, const uint32_t* __restrict__ gaps,
 
 // phi = 2 theta, theta the angle of (cos, sin) in [0, pi], for every site of one grid:
 // FP32 vectors to float by the polynomial angle, anything to double by atan2 in FP64.
-__device__ __forceinline__ void put_angle(float2 v, float& out) { out = 2.0f * angle_upper(v.x, fmaxf(v.y, 0.0f)); }
-__device__ __forceinline__ void put_angle(float2 v, double& out) { out = 2.0 * atan2(fmax((double)v.y, 0.0), (double)v.x); }
-__device__ __forceinline__ void put_angle(double2 v, double& out) { out = 2.0 * atan2(fmax(v.y, 0.0), v.x); }
-__device__ __forceinline__ void put_angle(double2 v, float& out) {
+// phi = theta / q (inv_q = 1/q; 2 exactly for q = 1/2).
+__device__ __forceinline__ void put_angle(float2 v, double inv_q, float& out) {
+    out = (float)inv_q * angle_upper(v.x, fmaxf(v.y, 0.0f));
+}
+__device__ __forceinline__ void put_angle(float2 v, double inv_q, double& out) {
+    out = inv_q * atan2(fmax((double)v.y, 0.0), (double)v.x);
+}
+__device__ __forceinline__ void put_angle(double2 v, double inv_q, double& out) { out = inv_q * atan2(fmax(v.y, 0.0), v.x); }
+__device__ __forceinline__ void put_angle(double2 v, double inv_q, float& out) {
     double d;
-    put_angle(v, d);
+    put_angle(v, inv_q, d);
     out = (float)d;
 }
 
 template <typename V, typename O>
 __global__ void k_get_state(EntryDesc e, const V* __restrict__ lat, O* __restrict__ phi) {
     const long long n = (long long)e.W * e.H;
+    const double inv_q = 1.0 / e.q;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(i / e.W), x = (int)(i - (long long)y * e.W);
         const long long base = ((x + y) & 1) ? e.plane[1] : e.plane[0];
-        put_angle(lat[base + (long long)(y + 1) * e.pitch + (x >> 1) + kPadL], phi[i]);
+        put_angle(lat[base + (long long)(y + 1) * e.pitch + (x >> 1) + kPadL], inv_q, phi[i]);
     }
 }
 
-__device__ __forceinline__ void unit_half(float phi, float2& v) {
+// (cos theta, sin theta) of theta = q phi.
+__device__ __forceinline__ void unit_q(float phi, double q, float2& v) {
     float s, co;
-    sincosf(0.5f * phi, &s, &co);
+    sincosf((float)q * phi, &s, &co);
     v = make_float2(co, fmaxf(s, 0.0f));
 }
-__device__ __forceinline__ void unit_half(float phi, double2& v) {
+__device__ __forceinline__ void unit_q(float phi, double q, double2& v) {
     double s, co;
-    sincos(0.5 * (double)phi, &s, &co);
+    sincos(q * (double)phi, &s, &co);
     v = make_double2(co, fmax(s, 0.0));
 }
 
@@ -312,7 +322,7 @@ __global__ void k_set_state(EntryDesc e, V* __restrict__ lat, const uint32_t* __
         const int y = (int)(ent >> 16), j = (int)(ent & 0xFFFFu);
         const int x = 2 * j + (c ^ (y & 1));
         const long long base = c ? e.plane[1] : e.plane[0];
-        unit_half(phi[(long long)y * e.W + x], lat[base + (long long)(y + 1) * e.pitch + j + kPadL]);
+        unit_q(phi[(long long)y * e.W + x], e.q, lat[base + (long long)(y + 1) * e.pitch + j + kPadL]);
     }
 }
 
@@ -329,15 +339,29 @@ cudaError_t launch_half_sweep(const SweepArgs& a, int color, int trig, cudaStrea
     if (nb == 0) return cudaSuccess;
     const bool acc = a.acc != nullptr;
     count_launches(1, st);
+    const dim3 g(nb), b(kSweepThreads);
     if (a.f64) {
-        if (acc) k_half_sweep64<true><<<nb, kSweepThreads, 0, st>>>(a, color);
-        else k_half_sweep64<false><<<nb, kSweepThreads, 0, st>>>(a, color);
+        if (a.genq) {
+            if (acc) k_half_sweep64<true, true><<<g, b, 0, st>>>(a, color);
+            else k_half_sweep64<false, true><<<g, b, 0, st>>>(a, color);
+        } else {
+            if (acc) k_half_sweep64<true, false><<<g, b, 0, st>>>(a, color);
+            else k_half_sweep64<false, false><<<g, b, 0, st>>>(a, color);
+        }
+    } else if (a.genq) {
+        if (trig == TRIG_FAST) {
+            if (acc) k_half_sweep<TRIG_FAST, true, true><<<g, b, 0, st>>>(a, color);
+            else k_half_sweep<TRIG_FAST, false, true><<<g, b, 0, st>>>(a, color);
+        } else {
+            if (acc) k_half_sweep<TRIG_ACCURATE, true, true><<<g, b, 0, st>>>(a, color);
+            else k_half_sweep<TRIG_ACCURATE, false, true><<<g, b, 0, st>>>(a, color);
+        }
     } else if (trig == TRIG_FAST) {
-        if (acc) k_half_sweep<TRIG_FAST, true><<<nb, kSweepThreads, 0, st>>>(a, color);
-        else k_half_sweep<TRIG_FAST, false><<<nb, kSweepThreads, 0, st>>>(a, color);
+        if (acc) k_half_sweep<TRIG_FAST, true, false><<<g, b, 0, st>>>(a, color);
+        else k_half_sweep<TRIG_FAST, false, false><<<g, b, 0, st>>>(a, color);
     } else {
-        if (acc) k_half_sweep<TRIG_ACCURATE, true><<<nb, kSweepThreads, 0, st>>>(a, color);
-        else k_half_sweep<TRIG_ACCURATE, false><<<nb, kSweepThreads, 0, st>>>(a, color);
+        if (acc) k_half_sweep<TRIG_ACCURATE, true, false><<<g, b, 0, st>>>(a, color);
+        else k_half_sweep<TRIG_ACCURATE, false, false><<<g, b, 0, st>>>(a, color);
     }
     return cudaGetLastError();
 }

@@ -52,7 +52,13 @@ def test_init_rejects_bad_arguments_before_touching_the_device():
         ctx = ctypes.c_void_p()
         st = mpr.lib().mpr_init(ctypes.byref(ctx), mpr._ptr(z), mpr._ptr(m), W, H, None, None)
         assert st == mpr.MPR_EINVAL and not ctx.value
-    bad = mpr.mpr_default_params(q=0.25)
-    ctx = ctypes.c_void_p()
-    st = mpr.lib().mpr_init(ctypes.byref(ctx), mpr._ptr(z), mpr._ptr(m), 4, 4, ctypes.byref(bad), None)
-    assert st == mpr.MPR_EINVAL
+    # q outside (0, 1/2]; q < 1/2 with the tile kernels or the printed reflection
+    for bad in (mpr.mpr_default_params(q=0.75), mpr.mpr_default_params(q=0.0),
+                mpr.mpr_default_params(q=0.25, exec_mode=mpr.MPR_EXEC_TILE),
+                mpr.mpr_default_params(q=0.25, or_mode=mpr.MPR_OR_LITERAL),
+                mpr.mpr_default_params(precision=mpr.MPR_PREC_F64, exec_mode=mpr.MPR_EXEC_TILE),
+                mpr.mpr_default_params(precision=mpr.MPR_PREC_F64, trig_mode=mpr.MPR_TRIG_FAST),
+                mpr.mpr_default_params(precision=3)):
+        ctx = ctypes.c_void_p()
+        st = mpr.lib().mpr_init(ctypes.byref(ctx), mpr._ptr(z), mpr._ptr(m), 4, 4, ctypes.byref(bad), None)
+        assert st == mpr.MPR_EINVAL and not ctx.value
