@@ -54,8 +54,10 @@ def test_q_trajectory_f64_matches_oracle(q, or_mode):
         info = mpr.mpr_get_info(ctx)
     finally:
         mpr.mpr_free(ctx)
-    # phi stays in [0, 2 pi): the arc of theta = q phi is never left
-    assert (got >= 0).all() and (got < TWO_PI).all()
+    # gap angles stay in [0, 2 pi): the arc of theta = q phi is never left (samples lie in
+    # [0, 2 pi], the maximum mapping to 2 pi by Eq. 1)
+    assert (got[gap] >= 0).all() and (got[gap] < TWO_PI).all()
+    assert (got >= 0).all() and (got <= TWO_PI + 1e-12).all()
     e_orc = orc.energy(phi, q=q)
     assert abs(info["H_exact"] / e_orc - 1) < 1e-12
     assert abs(info["H_tracked"] / e_orc - 1) < 1e-11
@@ -77,7 +79,7 @@ def test_q_single_sweep_f32_parity_and_energy(q):
         for it in range(60):
             a = (1.0, 3.0, 12.0)[it % 3]
             sw = mpr.mpr_get_state(ctx, phi)
-            assert (phi >= 0).all() and (phi < TWO_PI + 1e-5).all()
+            assert (phi >= 0).all() and (phi <= TWO_PI + 1e-5).all()
             ref = phi.astype(np.float64)
             orc.sweep(ref, mask, a=a, T=T, q=q, seed=seed, sweep_index=sw)
             mpr.mpr_sweep(ctx, 1, a)
