@@ -1,5 +1,5 @@
-"""Couplings q < 1/2 (Eq. 2 bounds q by 1/2; the paper fixes q = 1/2 and notes that q could
-be learned): the list kernels keep theta = q phi on the arc [0, 2 pi q), reflect only
+"""Couplings q < 1/2 (Eq. 2 bounds q by 1/2; the paper fixes q = 1/2 and leaves fitting q
+to data open): the list kernels keep theta = q phi on the arc [0, 2 pi q), reflect only
 inside it and turn proposals that leave it by -+2 pi q (the modulo 2 pi of phi).
 
   * FP64 (MPR_PREC_F64): trajectories equal to the FP64 oracle's over 200 sweeps
