@@ -1,0 +1,115 @@
+"""Parity at the full 4096 x 4096 size of the timed workload (nu = 1, correlation length 32,
+50 % disk and random gaps), in the launch configuration the bench times: the tile kernel
+in the configuration the autotuner picks for this grid, accurate and fast transcendentals.
+
+The oracle runs whole 4096^2 sweeps (about 2 s each), so every one of the 8.4 M gap sites
+is compared, not a sample:
+  * single sweeps from the GPU's own state: |d phi| <= 1e-5 rad where the decisions agree,
+    at most 1e-6 of the decisions flipped (+1), samples bitwise frozen;
+  * the tracked energy equals Eq. 2 recomputed by the oracle (relative 1e-6);
+  * two averaged sweeps (Algorithm 2 steps 6-7) from the same state: zhat equal to the
+    oracle's within 1e-4 of the data range except at sites a flipped decision reached
+    (each flip moves its own site and can move its four neighbours in the next sweep).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle.oracle as orc
+from paper_1811_01604_gb300 import mpr, synth
+
+pytestmark = pytest.mark.gpu
+TWO_PI = 2 * math.pi
+
+
+def _circ(a, b):
+    d = np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64)) % TWO_PI
+    return np.minimum(d, TWO_PI - d)
+
+
+@pytest.fixture(scope="module")
+def grid4096():
+    c = synth.config("grid4096")
+    return c["z"], c["mask"]
+
+
+@pytest.fixture(scope="module")
+def tuned(grid4096):
+    """T-hat and the autotuned tile configuration of the grid (as in the bench)."""
+    z, mask = grid4096
+    H, W = z.shape
+    ctx = mpr.mpr_init(z, mask, W, H, mpr.mpr_default_params(seed=1))
+    try:
+        T, _ = mpr.mpr_estimate_T(ctx)
+        tune = mpr.mpr_autotune(ctx)
+    finally:
+        mpr.mpr_free(ctx)
+    return T, tune["tile_cfg"]
+
+
+@pytest.mark.parametrize("trig", [mpr.MPR_TRIG_ACCURATE, mpr.MPR_TRIG_FAST])
+def test_fullsize_single_sweeps_match_oracle(grid4096, tuned, trig):
+    z, mask = grid4096
+    H, W = z.shape
+    T, cfg = tuned
+    gap = mask == 0
+    seed = 1
+    ctx = mpr.mpr_init(z, mask, W, H, mpr.mpr_default_params(seed=seed, trig_mode=trig, tile_cfg=cfg))
+    flips = n = 0
+    worst = 0.0
+    try:
+        mpr.mpr_set_T(ctx, T)
+        mpr.mpr_sweep(ctx, 20, 4.0)                     # away from the uniform random start
+        phi = np.zeros((H, W), np.float32)
+        for a in ((1.0, 8.0) if trig == mpr.MPR_TRIG_ACCURATE else (8.0,)):
+            sw = mpr.mpr_get_state(ctx, phi)
+            ref = phi.astype(np.float64)
+            orc.sweep(ref, mask, a=a, T=T, seed=seed, chain=0, sweep_index=sw)
+            mpr.mpr_sweep(ctx, 1, a)
+            got = np.zeros_like(phi)
+            assert mpr.mpr_get_state(ctx, got) == sw + 1
+            d = _circ(got[gap], ref[gap])
+            bad = d > 1e-5
+            flips += int(bad.sum())
+            n += int(gap.sum())
+            if (~bad).any():
+                worst = max(worst, float(d[~bad].max()))
+            assert np.array_equal(got[~gap], phi[~gap])
+        info = mpr.mpr_get_info(ctx)
+    finally:
+        mpr.mpr_free(ctx)
+    assert n > 8_000_000
+    assert worst <= 1e-5
+    assert flips <= 1e-6 * n + 1, (flips, n)
+    e_ref = orc.energy(got.astype(np.float64))
+    assert abs(info["H_exact"] / e_ref - 1) < 1e-6
+    assert abs(info["H_tracked"] / e_ref - 1) < 1e-6
+
+
+def test_fullsize_averaging_matches_oracle(grid4096, tuned):
+    z, mask = grid4096
+    H, W = z.shape
+    T, cfg = tuned
+    gap = mask == 0
+    seed, M = 1, 2
+    ctx = mpr.mpr_init(z, mask, W, H, mpr.mpr_default_params(seed=seed, tile_cfg=cfg))
+    zhat = np.zeros((H, W), np.float32)
+    try:
+        mpr.mpr_set_T(ctx, T)
+        mpr.mpr_sweep(ctx, 20, 4.0)
+        phi = np.zeros((H, W), np.float32)
+        sw = mpr.mpr_get_state(ctx, phi)
+        mpr.mpr_predict(ctx, M, zhat)
+        info = mpr.mpr_get_info(ctx)
+    finally:
+        mpr.mpr_free(ctx)
+    ref = phi.astype(np.float64)
+    ref_z, _ = orc.predict(ref, mask, z, T, orc.params(seed=seed), info["zmin"], info["zmax"], M,
+                           chain=0, sweep_index=sw)
+    assert (zhat[~gap] == z[~gap]).all()
+    d = np.abs(zhat.astype(np.float64) - ref_z)[gap]
+    off = int((d > 1e-4 * (info["zmax"] - info["zmin"])).sum())
+    # at most ~1e-6 flips per decision and sweep, each reaching its site and four neighbours
+    assert off <= 5 * (2e-6 * gap.sum() + 1), off
+    assert np.median(d) < 1e-5 * (info["zmax"] - info["zmin"])
