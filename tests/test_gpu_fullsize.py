@@ -79,6 +79,8 @@ def test_fullsize_single_sweeps_match_oracle(grid4096, tuned, trig):
         info = mpr.mpr_get_info(ctx)
     finally:
         mpr.mpr_free(ctx)
+    print(f"trig {trig}, tile configuration {cfg}: {flips} flipped of {n} decisions, "
+          f"max |d phi| elsewhere {worst:.2e} rad")
     assert n > 8_000_000
     assert worst <= 1e-5
     assert flips <= 1e-6 * n + 1, (flips, n)
@@ -110,6 +112,8 @@ def test_fullsize_averaging_matches_oracle(grid4096, tuned):
     assert (zhat[~gap] == z[~gap]).all()
     d = np.abs(zhat.astype(np.float64) - ref_z)[gap]
     off = int((d > 1e-4 * (info["zmax"] - info["zmin"])).sum())
+    print(f"zhat: {off} of {int(gap.sum())} gap sites off by more than 1e-4 of the range, "
+          f"median |d zhat| {np.median(d):.2e}")
     # at most ~1e-6 flips per decision and sweep, each reaching its site and four neighbours
     assert off <= 5 * (2e-6 * gap.sum() + 1), off
     assert np.median(d) < 1e-5 * (info["zmax"] - info["zmin"])
