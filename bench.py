@@ -190,7 +190,9 @@ def profile_case(name, tile_cfg=0):
     """sweep4096: 4096^2 bench grid, T = 0.05, 24 sweeps at a = 8 (about 50 sweep launches).
     net4096: two warm-start forward passes (untrained network) on the 4096^2 bench grid.
     net128: two training steps of the warm-start network on a batch of 32 128^2 grids.
-    net1024: two warm-start forward passes (untrained network) on a 1024^2 grid."""
+    net1024: two warm-start forward passes (untrained network) on a 1024^2 grid.
+    sweep64_4096: the 4096^2 bench grid in FP64 (MPR_PREC_F64, list kernels), T = 0.05,
+    3 sweeps at a = 8 (6 half-sweep launches)."""
     import torch
     from paper_1811_01604_gb300 import mpr
     if name == "net128":
@@ -219,7 +221,8 @@ def profile_case(name, tile_cfg=0):
         H, W = z_np.shape
         z = torch.from_numpy(z_np).cuda()
         mask = torch.from_numpy(m_np).cuda()
-    ctx = mpr.mpr_init(z, mask, W, H, mpr.mpr_default_params(seed=1, tile_cfg=tile_cfg))
+    extra = dict(precision=mpr.MPR_PREC_F64) if name == "sweep64_4096" else dict(tile_cfg=tile_cfg)
+    ctx = mpr.mpr_init(z, mask, W, H, mpr.mpr_default_params(seed=1, **extra))
     try:
         if name in ("net4096", "net1024"):
             net = mpr.mpr_net_create(0)
@@ -232,7 +235,7 @@ def profile_case(name, tile_cfg=0):
             print(f"profile case {name}: done")
             return
         mpr.mpr_set_T(ctx, 0.05)
-        st = mpr.mpr_sweep(ctx, 24, 8.0)
+        st = mpr.mpr_sweep(ctx, 3 if name == "sweep64_4096" else 24, 8.0)
         torch.cuda.synchronize()
     finally:
         mpr.mpr_free(ctx)
@@ -675,7 +678,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mpr", choices=["mpr", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-case", default=None, choices=["sweep4096", "net4096", "net1024", "net128"],
+    ap.add_argument("--profile-case", default=None, choices=["sweep4096", "net4096", "net1024", "net128", "sweep64_4096"],
                     help="run a small fixed sweep workload for ncu instead of the benchmark")
     ap.add_argument("--workload", default="fill4096", choices=["fill4096", "batch256", "warm1024", "warm4096",
                                                                 "chains1024", "ormodes1024", "dpsp"],
