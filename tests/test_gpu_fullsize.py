@@ -5,7 +5,11 @@ in the configuration the autotuner picks for this grid, accurate and fast transc
 The oracle runs whole 4096^2 sweeps (about 2 s each), so every one of the 8.4 M gap sites
 is compared, not a sample:
   * single sweeps from the GPU's own state: |d phi| <= 1e-5 rad where the decisions agree,
-    at most 1e-6 of the decisions flipped (+1), samples bitwise frozen;
+    at most 1e-6 of the decisions flipped (+1) with the accurate transcendentals (the
+    default), 2e-6 (+1) with the fast ones, samples bitwise frozen.  At this grid's low
+    T-hat (about 1e-3) an energy error is magnified 1000 times in exp(-dH/T); the fast
+    mode's larger angle error (up to 3e-6 rad against 1.6e-6) flipped 9 of 8.4 M
+    decisions where the accurate mode flipped 2 of 16.8 M;
   * the tracked energy equals Eq. 2 recomputed by the oracle (relative 1e-6);
   * two averaged sweeps (Algorithm 2 steps 6-7) from the same state: zhat equal to the
     oracle's within 1e-4 of the data range except at sites a flipped decision reached
@@ -83,7 +87,8 @@ def test_fullsize_single_sweeps_match_oracle(grid4096, tuned, trig):
           f"max |d phi| elsewhere {worst:.2e} rad")
     assert n > 8_000_000
     assert worst <= 1e-5
-    assert flips <= 1e-6 * n + 1, (flips, n)
+    rate = 1e-6 if trig == mpr.MPR_TRIG_ACCURATE else 2e-6
+    assert flips <= rate * n + 1, (flips, n)
     e_ref = orc.energy(got.astype(np.float64))
     assert abs(info["H_exact"] / e_ref - 1) < 1e-6
     assert abs(info["H_tracked"] / e_ref - 1) < 1e-6
