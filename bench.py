@@ -113,10 +113,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
-# DRAM bytes per launch of k_tile_sweep on this grid from one ncu capture
-# (profiles/k_tile_sweep_4096.md), valid for the kernel sources with this hash only.
-TILE_TRAFFIC_BYTES = 253.8e6
-TILE_TRAFFIC_SOURCE_HASH = "0dd4de56125440f5"
+# DRAM bytes per launch of k_tile_sweep on this grid, per compiled tile configuration, from
+# one ncu capture each (profiles/k_tile_sweep_4096.md), valid for the kernel sources with
+# this hash only.
+TILE_TRAFFIC_BYTES = {0: 251.3e6, 1: 259.4e6, 2: 244.4e6}
+TILE_TRAFFIC_SOURCE_HASH = "b4e747d5adbf3c22"
 
 
 def tile_kernel_hash():
@@ -850,8 +851,9 @@ def main():
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm,
-                         "traffic": TILE_TRAFFIC_BYTES if tile_kernel_hash() == TILE_TRAFFIC_SOURCE_HASH else None,
-                         "kernel": "k_tile_sweep", "ms_per_launch": sweep_ms,
+                         "traffic": (TILE_TRAFFIC_BYTES.get(tune["tile_cfg"])
+                                     if tile_kernel_hash() == TILE_TRAFFIC_SOURCE_HASH else None),
+                         "kernel": "k_tile_sweep", "tile_cfg": tune["tile_cfg"], "ms_per_launch": sweep_ms,
                          "ms_per_launch_fast": sweep_ms_fast,
                          "peak_source": f"{peak_src} hbm_gbs",
                          "bytes_per_launch": bytes_per_launch},
