@@ -225,9 +225,10 @@ mpr_status mpr_batch_info(mpr_ctx* ctx, int g, double* T, double* e_s, int* swee
  * Autotuner of the TILE kernels: times a few sweeps of every compiled tile shape on the
  * context's own grids (starting from a snapshot of the state, which is restored, so the
  * chains are not advanced), keeps the fastest, and sets the number of sweeps per captured
- * CUDA graph so that the host's once-per-graph check costs about a quarter of the sweeping
- * time.  Needs a temperature.  Outputs (may be NULL): chosen tile configuration, sweeps
- * per graph, time of one sweep in ms.
+ * chunk (the relaxation runs as a device-side loop over chunks, checking once per chunk
+ * whether any grid is still relaxing) to about 60 us of sweeping, at least 4 and at most
+ * 64.  Needs a temperature.  Outputs (may be NULL): chosen tile configuration, sweeps per
+ * chunk, time of one sweep in ms.
  */
 mpr_status mpr_autotune(mpr_ctx* ctx, int* tile_cfg, int* graph_sweeps, double* ms_per_sweep);
 

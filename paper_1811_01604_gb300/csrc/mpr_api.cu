@@ -69,7 +69,8 @@ struct Batch {
     double* d_ehist = nullptr;
     int ehist_stride = 0;
     int* d_active = nullptr;               // one counter per sweep of a captured chunk
-    int gsweeps = kDefaultGraphSweeps;     // sweeps per captured chunk (host checks once per chunk)
+    int* d_chunks = nullptr;               // chunks run by the device-side relaxation loop
+    int gsweeps = kDefaultGraphSweeps;     // sweeps per captured chunk (loop condition once per chunk)
     double* d_scratch = nullptr;
     double* d_H = nullptr;                 // one exact energy per entry
     bool f64 = false;                      // lattice of double2 and d_acc of doubles (MPR_PREC_F64)
@@ -204,6 +205,7 @@ void batch_free(Batch& b, cudaStream_t st) {
     dfree(b.d_ctl, st);
     dfree(b.d_ehist, st);
     dfree(b.d_active, st);
+    dfree(b.d_chunks, st);
     dfree(b.d_scratch, st);
     dfree(b.d_H, st);
     dfree(b.d_lat2, st);
@@ -393,6 +395,7 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
     CU(dalloc(&b.d_ehist, (size_t)b.n_ent * b.ehist_stride, st));
     CU(cudaMemsetAsync(b.d_ehist, 0, sizeof(double) * (size_t)b.n_ent * b.ehist_stride, st));
     CU(dalloc(&b.d_active, kMaxGraphSweeps, st));
+    CU(dalloc(&b.d_chunks, 1, st));
     CU(dalloc(&b.d_scratch, kScratch + 8, st));
     CU(dalloc(&b.d_H, (size_t)b.n_ent, st));
     CU(cudaStreamSynchronize(st));
@@ -486,14 +489,72 @@ mpr_status enqueue_sweeps(mpr_ctx* ctx, Batch& b, cudaStream_t s, int n, int mod
     return MPR_OK;
 }
 
-// Runs n sweeps through a cached CUDA graph of b.gsweeps sweeps (plus a tail).
+// The condition of the device-side relaxation loop, run after each chunk of S sweeps:
+// continue while any grid is still relaxing (the control step of the chunk's last sweep
+// counted them) and fewer than cap chunks have run.  Every grid stops by itself within
+// i_max sweeps and cap covers that, so the loop ends even if a count went wrong.
+__global__ void k_relax_loop_cond(cudaGraphConditionalHandle h, const int* __restrict__ active_last,
+                                  int* __restrict__ chunks, int cap) {
+    const int n = *chunks + 1;
+    *chunks = n;
+    cudaGraphSetConditional(h, (*active_last > 0 && n < cap) ? 1u : 0u);
+}
+
+// Relaxation graph: a WHILE node whose body is one chunk of S sweeps followed by the loop
+// condition, so the whole relaxation runs without a host round trip per chunk.
+mpr_status build_relax_graph(mpr_ctx* ctx, Batch& b, int S, int cap, double a_fixed, bool acc,
+                             cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    CU(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    mpr_status s = MPR_OK;
+    if (e == cudaSuccess) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(ctx->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            s = enqueue_sweeps(ctx, b, ctx->cap, S, CTL_RELAX, a_fixed, acc, true);
+            if (s == MPR_OK) {
+                k_relax_loop_cond<<<1, 1, 0, ctx->cap>>>(h, b.d_active + (S - 1), b.d_chunks, cap);
+                e = cudaGetLastError();
+            }
+            cudaGraph_t captured = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(ctx->cap, &captured);
+            if (e == cudaSuccess) e = ce;
+        }
+    }
+    if (s == MPR_OK && e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (s != MPR_OK) return s;
+    CU(e);
+    return MPR_OK;
+}
+
+// Runs n sweeps through a cached CUDA graph of b.gsweeps sweeps (plus a tail); relaxation
+// (n ignored) through the device-side loop of build_relax_graph.
 mpr_status run_sweeps(mpr_ctx* ctx, Batch& b, int n, int mode, double a_fixed, bool acc) {
     const int S = b.gsweeps;
     const bool relax = mode == CTL_RELAX;
     if (n <= 0 && !relax) return MPR_OK;
     auto key = std::make_tuple(mode, acc ? 1 : 0, S, ctx->prm.trig_mode, (float)a_fixed);
     cudaGraphExec_t exec = nullptr;
-    if (n >= S || relax) {
+    const int cap_chunks = (int)std::min<long long>((long long)ctx->prm.i_max / S + 4, 1LL << 30);
+    if (relax) {
+        auto it = b.graphs.find(key);
+        if (it == b.graphs.end()) {
+            const mpr_status s = build_relax_graph(ctx, b, S, cap_chunks, a_fixed, acc, &exec);
+            if (s != MPR_OK) return s;
+            b.graphs[key] = exec;
+        } else {
+            exec = it->second;
+        }
+    } else if (n >= S) {
         auto it = b.graphs.find(key);
         if (it == b.graphs.end()) {
             CU(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
@@ -514,18 +575,21 @@ mpr_status run_sweeps(mpr_ctx* ctx, Batch& b, int n, int mode, double a_fixed, b
         }
     }
     if (relax) {
-        // replay until no entry is still relaxing (each entry stops itself on the slope
-        // test or on i_max; the cap below only guards against a logic error)
-        const long long cap_chunks = (long long)ctx->prm.i_max / S + 4;
-        for (long long ch = 0;; ++ch) {
-            if (ch > cap_chunks)
-                return fail(ctx, MPR_ETIMEOUT, "relaxation did not stop within i_max sweeps");
-            CU(cudaGraphLaunch(exec, ctx->st));
-            count_launches((b.tiled ? 1ull : 3ull) * S, nullptr);
-            CU(cudaMemcpyAsync(ctx->h_active, b.d_active + (S - 1), sizeof(int),
-                               cudaMemcpyDeviceToHost, ctx->st));
-            CU(cudaStreamSynchronize(ctx->st));
-            if (*ctx->h_active == 0) break;
+        // chunks until no entry is still relaxing (each stops itself on the slope test or
+        // on i_max), decided on the device; the host reads the chunk count once at the end
+        CU(cudaMemsetAsync(b.d_chunks, 0, sizeof(int), ctx->st));
+        CU(cudaGraphLaunch(exec, ctx->st));
+        CU(cudaMemcpyAsync(ctx->h_active, b.d_chunks, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+        CU(cudaStreamSynchronize(ctx->st));
+        const int chunks = *ctx->h_active;
+        count_launches((unsigned long long)chunks * ((b.tiled ? 1ull : 3ull) * S + 1ull), nullptr);
+        if (chunks >= cap_chunks) {
+            // the cap ends the loop only if some grid was still relaxing after i_max sweeps
+            std::vector<Ctl> c;
+            const mpr_status rs = read_ctl(ctx, b, c);
+            if (rs != MPR_OK) return rs;
+            for (const Ctl& x : c)
+                if (!x.stop) return fail(ctx, MPR_ETIMEOUT, "relaxation did not stop within i_max sweeps");
         }
         return MPR_OK;
     }
@@ -1210,9 +1274,7 @@ mpr_status mpr_get_info(mpr_ctx* ctx, double* H_exact, double* H_tracked, double
 
 // Autotuner: times a few sweeps of every compiled tile configuration on the context's own
 // grids (from a snapshot of the state, restored afterwards, so the chain is unchanged),
-// keeps the fastest, and sizes the captured chunk of sweeps so that the host's once-per-
-// chunk check (a graph launch, a 4-byte read and a synchronisation, also measured) costs
-// about a quarter of the chunk's sweeping time.
+// keeps the fastest, and sizes the captured chunk of sweeps from its time.
 mpr_status mpr_autotune(mpr_ctx* ctx, int* tile_cfg, int* graph_sweeps, double* ms_per_sweep) {
     if (!ctx) return MPR_EINVAL;
     Batch& b = ctx->b;
@@ -1251,22 +1313,10 @@ mpr_status mpr_autotune(mpr_ctx* ctx, int* tile_cfg, int* graph_sweeps, double* 
         s = build_tiles(ctx, b, best);
         if (s != MPR_OK) return s;
     }
-    // cost of the host's check of one chunk: an empty graph launch, a 4-byte read, a sync
-    cudaGraph_t eg = nullptr;
-    cudaGraphExec_t ex = nullptr;
-    CU(cudaGraphCreate(&eg, 0));
-    CU(cudaGraphInstantiate(&ex, eg, 0));
-    auto t0 = std::chrono::steady_clock::now();
-    for (int i = 0; i < 20; ++i) {
-        CU(cudaGraphLaunch(ex, ctx->st));
-        CU(cudaMemcpyAsync(ctx->h_active, b.d_active, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
-        CU(cudaStreamSynchronize(ctx->st));
-    }
-    const double check_ms =
-        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() / 20.0;
-    cudaGraphExecDestroy(ex);
-    cudaGraphDestroy(eg);
-    int S = (int)std::lround(4.0 * check_ms / std::max(best_ms, 1e-6));
+    // sweeps per chunk of the device-side relaxation loop: at least ~60 us of sweeping per
+    // chunk, so that the chunk's condition launch (a few us) costs under ~5 %; more only
+    // adds empty launches after the last grid has stopped
+    int S = (int)std::lround(0.06 / std::max(best_ms, 1e-6));
     S = std::min(kMaxGraphSweeps, std::max(4, S));
     if (S != b.gsweeps) {
         for (auto& kv : b.graphs) cudaGraphExecDestroy(kv.second);
