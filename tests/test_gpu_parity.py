@@ -341,3 +341,31 @@ def test_pooled_memory_reuse_and_release():
     mpr.mpr_release_memory()
     assert np.array_equal(states(), first)
     mpr.mpr_release_memory()
+
+
+@pytest.mark.parametrize("exec_mode", EXEC)
+@pytest.mark.parametrize("i_max", [0, 1, 5, 9])
+def test_relaxation_loop_stops_at_i_max(exec_mode, i_max):
+    # Algorithm 2 step 5 ends after sweep i = i_max + 1 when the slope test has not passed
+    # (n_fit larger than the run: the slope stays at its initial -1); the device-side loop
+    # runs chunks of several sweeps, so it must stop within one chunk and leave the counters
+    # exactly where the oracle's loop leaves them
+    c = synth.config("grid64")
+    z, mask = c["z"], c["mask"]
+    ctx = make_ctx(z, mask, seed=4, i_max=i_max, n_fit=10**6, exec_mode=exec_mode)
+    try:
+        mpr.mpr_set_T(ctx, 0.2)
+        st = mpr.mpr_equilibrate(ctx)
+        phi = np.zeros(z.shape, np.float32)
+        sw = mpr.mpr_get_state(ctx, phi)
+        mpr.mpr_sweep(ctx, 3, 1.0)                     # the context stays usable
+        sw2 = mpr.mpr_get_state(ctx, phi)
+    finally:
+        mpr.mpr_free(ctx)
+    ref = orc.map_angles(z, mask)[0]
+    orc.init_gaps(ref, mask, 4)
+    out, sw_ref, _ = orc.equilibrate(ref, mask, 0.2, orc.params(seed=4, i_max=i_max, n_fit=10**6))
+    assert st.sweeps == out.sweeps == i_max + 1
+    assert st.converged == 0
+    assert st.a == out.a
+    assert sw == sw_ref and sw2 == sw + 3
