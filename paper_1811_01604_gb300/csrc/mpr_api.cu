@@ -261,6 +261,13 @@ mpr_status build_tiles(mpr_ctx* ctx, Batch& b, int cfg) {
     CU(cudaMemsetAsync(b.d_ticket, 0, sizeof(unsigned) * b.n_ent, st));
     CU(launch_tile_lists(cfg, b.d_tiles, b.ntiles, b.d_ents, b.mask_base, b.all_free, b.d_lists,
                          b.d_cnts, st));
+    // heaviest tiles first (the counts are known now), then the lists again in that order
+    CU(cudaMemcpyAsync(tiles.data(), b.d_tiles, tiles.size() * sizeof(TileDesc), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    order_tiles_by_work(tiles.data(), b.ents.data(), b.n_ent);
+    CU(cudaMemcpyAsync(b.d_tiles, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, st));
+    CU(launch_tile_lists(cfg, b.d_tiles, b.ntiles, b.d_ents, b.mask_base, b.all_free, b.d_lists,
+                         b.d_cnts, st));
     CU(make_tile_maps(cfg, b.ents.data(), b.n_ent, b.d_lat, b.d_lat2, b.d_maps, st));
     tile_sweep_blocks(cfg);               // kernel attributes are set outside any capture
     CU(cudaGetLastError());

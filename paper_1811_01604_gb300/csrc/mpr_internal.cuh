@@ -556,6 +556,8 @@ cudaError_t launch_tile_lists(int cfg, TileDesc* tiles, int ntiles, const EntryD
                               const uint8_t* mask, int all_free, uint16_t* lists, TileCnt* cnts,
                               cudaStream_t st);
 cudaError_t launch_tile_sweep(const TileArgs& a, int trig, cudaStream_t st);
+// Host: sorts each grid's tiles (with their gap counts filled in) by descending work.
+void order_tiles_by_work(TileDesc* tiles, const EntryDesc* ents, int n_ent);
 // K > 1: the angle sums of K chains of one grid, chain c's tiles at tile + c * chain_tiles.
 cudaError_t launch_tile_predict_out(int cfg, const TileDesc* tiles, const TileCnt* cnts,
                                     const uint16_t* lists, const float* acc, const EntryDesc* ents,

@@ -529,6 +529,21 @@ __global__ void k_tile_predict_out(const TileDesc* __restrict__ tiles, const Til
 
 }  // namespace
 
+// Heaviest tiles first.  The persistent blocks take tiles in index order, so with each
+// grid's tiles sorted by descending gap count the last tiles handed out are the lightest
+// and the blocks finish close together (cloud-like gaps make some tiles several times
+// heavier than others).  Stable, so equal tiles keep raster order; per grid, so a grid's
+// tiles stay contiguous.  Every update depends only on its neighbours and its counter, so
+// the order changes no result.
+void order_tiles_by_work(TileDesc* tiles, const EntryDesc* ents, int n_ent) {
+    for (int e = 0; e < n_ent; ++e) {
+        TileDesc* t0 = tiles + ents[e].tile0;
+        std::stable_sort(t0, t0 + ents[e].ntiles, [](const TileDesc& a, const TileDesc& b) {
+            return a.nA_int + a.nA_ring + a.nB > b.nA_int + b.nA_ring + b.nB;
+        });
+    }
+}
+
 // ---------------------------------------------------------------- compiled configurations
 // The tile shapes the library is built with; the autotuner picks one per batch.
 //   id  TH  TW  threads  stages  blocks/SM register budget
