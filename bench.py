@@ -116,8 +116,8 @@ class ClockSampler:
 # DRAM bytes per launch of k_tile_sweep on this grid, per compiled tile configuration, from
 # one ncu capture each (profiles/k_tile_sweep_4096.md), valid for the kernel sources with
 # this hash only.
-TILE_TRAFFIC_BYTES = {0: 251.3e6, 1: 259.4e6, 2: 244.4e6}
-TILE_TRAFFIC_SOURCE_HASH = "b4e747d5adbf3c22"
+TILE_TRAFFIC_BYTES = {0: 296.6e6, 1: 338.7e6, 2: 288.6e6}
+TILE_TRAFFIC_SOURCE_HASH = "0af182705d745df9"
 
 
 def tile_kernel_hash():
