@@ -159,7 +159,10 @@ mpr_status mpr_sweep(mpr_ctx* ctx, int n, double a, mpr_sweep_stats* out);
  * Algorithm 2 step 5 from the current state: i = 0, k = -1, a = 1; sweep while
  * k < 0 and i <= i_max, with the window update of step 5.2 and the slope test of
  * step 5.4 (least-squares slope of the last n_fit specific energies, every n_f
- * sweeps once i >= n_fit).  Returns MPR_ENOTEQUIL if it stopped on i_max.
+ * sweeps once i >= n_fit).  Returns MPR_ENOTEQUIL if it stopped on i_max.  The loop runs
+ * on the device (a CUDA graph whose conditional node repeats chunks of sweeps while any
+ * grid is still relaxing, at most i_max / chunk + 4 chunks); the host waits once, at the
+ * end.  Sweeps of a chunk that start after a grid has stopped leave it unchanged.
  */
 mpr_status mpr_equilibrate(mpr_ctx* ctx, mpr_equil_stats* out);
 
