@@ -8,8 +8,10 @@ differences do not grow: two oracle runs whose start differs by 1e-15 rad stay w
 lattice at T = 1).  So no Metropolis decision flips and the chains coincide: the whole
 fill -- Eq. 4, the e(T, L) table, T-hat, the relaxation with its window and slope test,
 the M averaged sweeps -- must agree to rounding.  The printed reflection (Eq. 6 as
-printed, q = 1) is chaotic (the same 1e-15 start separates completely within 50 sweeps
-at T = 0.3), so its trajectory is compared over a short run at low T only.
+printed, q = 1) amplifies rounding (the same 1e-15 start separates completely within 50
+sweeps on an all-free lattice at T = 0.3, and with the 64 x 64 grid's samples grows to
+1e-7 rad in 300 sweeps at T = 0.3, completely at T = 1), so its trajectory is compared
+over a short run at low T only.
 """
 import math
 

@@ -488,3 +488,44 @@ def test_predict_chains_burn_in_is_skipped_sweeps():
         forks.append(orc.predict(f, mask, z, 0.15, prm, zmin, zmax, M=m, chain=k << 24,
                                  sweep_index=7 + b)[0])
     assert np.allclose(zc, np.mean(forks, axis=0), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("or_mode,T,sweeps,bound", [
+    (orc.OR_CONSERVING, 0.3, 200, 1e-12),
+    (orc.OR_NONE, 0.3, 200, 1e-12),
+])
+def test_rounding_differences_do_not_grow(or_mode, T, sweeps, bound):
+    # Two runs whose gap angles start 1e-15 rad apart (rounding-sized) stay within ~1e-13
+    # rad: the reflection about the field and the proposal rotation are isometries, so
+    # differences are carried, not amplified.  This is what lets an FP64 implementation
+    # of the same steps follow this oracle's trajectory to rounding.
+    c = synth.config("grid64")
+    z, mask = c["z"], c["mask"]
+    gap = mask == 0
+    phi, _, _, _ = orc.map_angles(z, mask)
+    orc.init_gaps(phi, mask, 13)
+    rng = np.random.default_rng(0)
+    p2 = phi.copy()
+    p2[gap] = (p2[gap] + rng.uniform(-1e-15, 1e-15, int(gap.sum())) * (p2[gap] + 1)) % TWO_PI
+    for s in range(sweeps):
+        a = 1.0 + s / 3.0 if s < 30 else 1.0
+        orc.sweep(phi, mask, a, T, seed=13, sweep_index=s, or_mode=or_mode)
+        orc.sweep(p2, mask, a, T, seed=13, sweep_index=s, or_mode=or_mode)
+    d = np.abs(phi - p2)[gap] % TWO_PI
+    assert np.minimum(d, TWO_PI - d).max() < bound
+
+
+def test_printed_reflection_amplifies_rounding():
+    # Eq. 6 as printed (the q = 1 reflection) is chaotic: on an all-free 64 x 64 lattice at
+    # T = 0.3 the same 1e-15 start separates the two runs completely within 100 sweeps
+    mask = np.zeros((64, 64), np.uint8)
+    phi = np.zeros((64, 64))
+    orc.init_gaps(phi, mask, 7)
+    rng = np.random.default_rng(0)
+    p2 = (phi + rng.uniform(-1e-15, 1e-15, phi.shape) * (phi + 1)) % TWO_PI
+    for s in range(100):
+        a = 1.0 + s / 3.0 if s < 30 else 1.0
+        orc.sweep(phi, mask, a, 0.3, seed=3, sweep_index=s, or_mode=orc.OR_LITERAL)
+        orc.sweep(p2, mask, a, 0.3, seed=3, sweep_index=s, or_mode=orc.OR_LITERAL)
+    d = np.abs(phi - p2) % TWO_PI
+    assert np.minimum(d, TWO_PI - d).max() > 1e-3
