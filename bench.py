@@ -117,7 +117,7 @@ class ClockSampler:
 # one ncu capture each (profiles/k_tile_sweep_4096.md), valid for the kernel sources with
 # this hash only.
 TILE_TRAFFIC_BYTES = {0: 296.6e6, 1: 338.7e6, 2: 288.6e6}
-TILE_TRAFFIC_SOURCE_HASH = "0af182705d745df9"
+TILE_TRAFFIC_SOURCE_HASH = "5cdc904b05e94b9a"
 
 
 def tile_kernel_hash():

@@ -130,19 +130,6 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         ::"r"(smem_addr(dst)), "l"((unsigned long long)src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
 }
-// Bulk copy of `bytes` (a multiple of 16) from shared to global memory, tracked by the
-// issuing thread's bulk-async group.
-__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_t bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
-                 ::"l"((unsigned long long)gdst), "r"(smem_addr(ssrc)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-// Waits until this thread's bulk stores have read their shared-memory source.
-__device__ __forceinline__ void bulk_wait_read() {
-    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-}
-// Waits until this thread's bulk stores are complete.
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 // Orders this thread's generic-proxy shared-memory writes before later async-proxy reads.
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -164,15 +151,6 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ bool mbar_wait_try(uint64_t* bar, uint32_t parity) {
     for (uint32_t i = 0; i < 3000u; ++i)
         if (mbar_try(bar, parity)) return true;
-    return false;
-}
-// Bounded wait: gives up after ~0.3 s (2^24 polls with a 20 ns pause) and reports false.
-// (Polling measured faster here than the hardware-suspended try_wait.)
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (uint32_t i = 0; i < (1u << 24); ++i) {
-        if (mbar_test(bar, parity)) return true;
-        __nanosleep(20);
-    }
     return false;
 }
 
