@@ -27,6 +27,13 @@
  *   R-CH   independent chains: the equilibrated state forked into K chains with
  *          chain words chain + k 2^24, all from the same sweep counter; the
  *          estimate averages all K * M_per_chain realizations.
+ *   R-Q    couplings q in (0, 1/2] (Eq. 2 bounds q by 1/2): every step is written
+ *          for a general q; the reflection is kept only inside [0, 2pi).
+ *
+ * Parity unpinned: the default values of the run-length parameters (A_targ,
+ * k_a, n_f, n_fit, i_max, M) and of the table (K_T, T range, lattice size,
+ * M_T).  The paper defers them to earlier work; they change how long the
+ * chains run, not the law they sample, and no closed form fixes them.
  */
 #include <math.h>
 #include <stdint.h>
