@@ -6,10 +6,12 @@
 // owns the device memory through its own pool or budget and forbids cudaMalloc/cudaFree
 // from libraries, or latency-critical loops where an allocation or a free would stall or
 // synchronise the device.  Every word of scratch memory it needs lives in one file-scope
-// device array, reserved when the library is loaded and kept on each GPU until the process
-// exits.  The caller passes device-resident inputs and host outputs.
+// device array, reserved on a GPU when the library's device code is loaded there (with
+// CUDA's lazy module loading, at the library's first use on that device) and kept until
+// the process exits.  The caller passes device-resident inputs and host outputs.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
 
 #include "../../include/mpr.h"
@@ -121,22 +123,26 @@ __global__ void k_static_finish(int H, unsigned char* s) {
     h->e_s = c ? -t / (double)c : 0.0;
 }
 
-// Device address of the scratch, looked up once per device.
+// Device address of the scratch, looked up once per device.  Two host threads making
+// their first call on one device may both look it up; they store the same address, and the
+// atomic slots make that a benign race rather than a data race.
 constexpr int kMaxDevices = 64;
-unsigned char* g_scratch_ptr[kMaxDevices] = {nullptr};
+std::atomic<unsigned char*> g_scratch_ptr[kMaxDevices];
 
 cudaError_t scratch_for_current_device(unsigned char** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (!g_scratch_ptr[dev]) {
+    unsigned char* ptr = g_scratch_ptr[dev].load(std::memory_order_relaxed);
+    if (!ptr) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+        ptr = static_cast<unsigned char*>(p);
+        g_scratch_ptr[dev].store(ptr, std::memory_order_relaxed);
     }
-    *out = g_scratch_ptr[dev];
+    *out = ptr;
     return cudaSuccess;
 }
 
@@ -145,7 +151,8 @@ cudaError_t scratch_for_current_device(unsigned char** out) {
 extern "C" mpr_status mpr_sample_energy_static(const float* z, const uint8_t* mask, int W, int H,
                                                double q, double* e_s, long long* n_pairs,
                                                void* cuda_stream) {
-    if (!z || !mask || !e_s || !n_pairs || W < 1 || H < 1 || !(q > 0.0)) return MPR_EINVAL;
+    // the same coupling range as mpr_init: q in (0, 1/2]
+    if (!z || !mask || !e_s || !n_pairs || W < 1 || H < 1 || !(q > 0.0 && q <= 0.5)) return MPR_EINVAL;
     if (H > MPR_STATIC_MAX_ROWS) return MPR_EINVAL;       // more rows than scratch slots
     cudaStream_t st = (cudaStream_t)cuda_stream;
     unsigned char* s = nullptr;

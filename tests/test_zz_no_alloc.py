@@ -55,6 +55,10 @@ def test_static_sample_energy_limits_and_errors():
     with pytest.raises(mpr.MprError) as e:
         mpr.mpr_sample_energy_static(z, m, 4, 4)            # constant data: Eq. 1 undefined
     assert e.value.status == mpr.MPR_ENODATA
+    zr = torch.arange(16, dtype=torch.float32, device="cuda").reshape(4, 4)
+    with pytest.raises(mpr.MprError) as e:
+        mpr.mpr_sample_energy_static(zr, m, 4, 4, 0.6)      # q outside (0, 1/2], as mpr_init
+    assert e.value.status == mpr.MPR_EINVAL
     big = torch.zeros(1, dtype=torch.float32, device="cuda")
     with pytest.raises(mpr.MprError) as e:
         mpr.mpr_sample_energy_static(big, big, 1, 16385)    # more rows than the scratch holds
