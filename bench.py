@@ -113,11 +113,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
-# DRAM bytes per launch of k_tile_sweep on this grid, per compiled tile configuration, from
-# one ncu capture each (profiles/k_tile_sweep_4096.md), valid for the kernel sources with
-# this hash only.
-TILE_TRAFFIC_BYTES = {0: 296.6e6, 1: 338.7e6, 2: 288.6e6}
-TILE_TRAFFIC_SOURCE_HASH = "5cdc904b05e94b9a"
+# DRAM bytes per sweep of k_tile_sweep on this grid (dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture of the profile case sweep4096, divided by its 24
+# sweeps), per compiled tile configuration; valid for the kernel sources with this hash only.
+TILE_TRAFFIC_PER_SWEEP = {}
+TILE_TRAFFIC_SOURCE_HASH = ""
 
 
 def tile_kernel_hash():
@@ -129,6 +129,15 @@ def tile_kernel_hash():
     return h.hexdigest()[:16]
 
 
+# Arithmetic of one gap-site update counted for the ALU roof: about 60 FP32 and 70 integer
+# operations (Philox4x32-10, the reflection, the proposal and the Metropolis test), the
+# per-update figure of the method's operation count; the unit-vector lattice replaces the
+# neighbours' transcendentals by plain arithmetic, so the MUFU roof (about 5 per update) is
+# far below both others.
+ALU_OPS_PER_UPDATE = 130
+LANES_PER_SM = 128                 # 4 schedulers x 32 lanes issue one operation each per clock
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -138,19 +147,37 @@ def measured_peaks():
 
 
 def cpu_baseline(z, mask, T):
-    """The FP64 oracle, single-threaded, on a 1024 x 1024 crop of the same workload."""
+    """The FP64 oracle on 512 x 512 crops of the same workload (fixed T-hat, slope-test
+    relaxation + M sweeps): once on one core, then one crop per host core on as many
+    threads (the C oracle runs outside the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
     import oracle.oracle as orc
-    c = 1024
-    zc = np.ascontiguousarray(z[:c, :c])
-    mc = np.ascontiguousarray(mask[:c, :c])
+    c = 512
+    crops = []
+    for i in range(max(1, os.cpu_count() or 1)):
+        y0, x0 = (i // 8) * c % (z.shape[0] - c + 1), (i % 8) * c % (z.shape[1] - c + 1)
+        crops.append((np.ascontiguousarray(z[y0:y0 + c, x0:x0 + c]),
+                      np.ascontiguousarray(mask[y0:y0 + c, x0:x0 + c])))
     prm = orc.params(seed=0, M=M)
+
+    def one(zm):
+        _, _, out = orc.fill(zm[0], zm[1], prm, T_fixed=T)
+        return out.n_gap * (out.eq.sweeps + M)
+
     t0 = time.perf_counter()
-    _, _, out = orc.fill(zc, mc, prm, T_fixed=T)
-    dt = time.perf_counter() - t0
-    updates = out.n_gap * (out.eq.sweeps + M)
-    return {"value": updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"1024x1024 crop of the step's grid, fixed T-hat, slope-test relaxation "
-                      f"({out.eq.sweeps} sweeps) + M={M}, {updates} site-updates in {dt:.1f} s"}
+    u1 = one(crops[0])
+    t1 = time.perf_counter() - t0
+    cores = len(crops)
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        un = sum(ex.map(one, crops))
+    tn = time.perf_counter() - t0
+    return {"value": u1 / t1, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"512x512 crop of the step's grid, fixed T-hat, slope-test relaxation + "
+                      f"M={M}: {u1} site-updates in {t1:.1f} s on one core",
+            "all_cores": {"value": un / tn, "unit": UNIT, "cores": cores,
+                          "sample": f"{cores} different 512x512 crops on {cores} threads "
+                                    f"(host cores: {os.cpu_count()}): {un} site-updates in {tn:.1f} s"}}
 
 
 def run_reference(args, rank):
@@ -188,7 +215,11 @@ def run_reference(args, rank):
 
 
 def profile_case(name, tile_cfg=0):
-    """sweep4096: 4096^2 bench grid, T = 0.05, 24 sweeps at a = 8 (about 50 sweep launches).
+    """sweep4096: 4096^2 bench grid, T = 0.05, 24 sweeps at a = 8 (one launch of the
+    persistent sweep kernel; a few set-up kernels before it).
+    copy4096: a plain device copy of the bytes a ping-pong sweep of the 4096^2 grid moves
+    (both unit-vector lattice buffers, 2 x 134 MB read, 2 x 134 MB written), timed with
+    CUDA events: the memory floor of a sweep that rewrites its whole lattice.
     net4096: two warm-start forward passes (untrained network) on the 4096^2 bench grid.
     net128: two training steps of the warm-start network on a batch of 32 128^2 grids.
     net1024: two warm-start forward passes (untrained network) on a 1024^2 grid.
@@ -196,6 +227,22 @@ def profile_case(name, tile_cfg=0):
     3 sweeps at a = 8 (6 half-sweep launches)."""
     import torch
     from paper_1811_01604_gb300 import mpr
+    if name == "copy4096":
+        n = 2 * 2 * 4096 * 4096                     # float2 elements of two lattice buffers
+        src = torch.ones(2 * n, dtype=torch.float32, device="cuda")
+        dst = torch.empty_like(src)
+        ms = []
+        for _ in range(23):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            dst.copy_(src)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = statistics.median(ms[3:])
+        print(json.dumps({"profile_case": name, "bytes_read": 4 * 2 * n, "bytes_written": 4 * 2 * n,
+                          "median_ms": t, "GB_per_s": 2 * 4 * 2 * n / (t * 1e-3) / 1e9}))
+        return
     if name == "net128":
         B, S = 32, 128
         g = torch.Generator(device="cuda")
@@ -679,7 +726,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mpr", choices=["mpr", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-case", default=None, choices=["sweep4096", "net4096", "net1024", "net128", "sweep64_4096"],
+    ap.add_argument("--profile-case", default=None,
+                    choices=["sweep4096", "copy4096", "net4096", "net1024", "net128", "sweep64_4096"],
                     help="run a small fixed sweep workload for ncu instead of the benchmark")
     ap.add_argument("--workload", default="fill4096", choices=["fill4096", "batch256", "warm1024", "warm4096",
                                                                 "chains1024", "ormodes1024", "dpsp"],
@@ -748,23 +796,24 @@ def main():
     prm = mpr.mpr_default_params(seed=1 + rank, M=M)
     stream = torch.cuda.current_stream(dev)
 
-    def one_fill(zi, mi, out):
-        ctx = mpr.mpr_init(zi, mi, W, H, prm, stream.cuda_stream)
+    N = H * W
+    P = int(m_np.size - m_np.sum())                     # gap sites (host work, outside every timed region)
+
+    def one_fill(zi, mi, out, p=prm):
+        ctx = mpr.mpr_init(zi, mi, W, H, p, stream.cuda_stream)
         try:
             T, _ = mpr.mpr_estimate_T(ctx)
             st = mpr.mpr_equilibrate(ctx)
             mpr.mpr_predict(ctx, M, out)
-            P = int(m_np.size - m_np.sum())
         finally:
             mpr.mpr_free(ctx)
         return P * (st.sweeps + M), st, T
 
-    # warm-up (the first one builds and caches the e(T, L) table); the library's autotuner
-    # then picks the tile configuration for this grid shape, used by every later fill
-    t_tab = time.perf_counter()
+    # warm-up (the first one loads the library's kernels and builds and caches the e(T, L)
+    # table of this shape); the library's autotuner then picks the tile configuration for
+    # this grid shape, used by every later fill
     one_fill(z, mask, zhat)
     torch.cuda.synchronize()
-    table_s = time.perf_counter() - t_tab
     ctx = mpr.mpr_init(z, mask, W, H, prm, stream.cuda_stream)
     try:
         mpr.mpr_estimate_T(ctx)
@@ -774,6 +823,18 @@ def main():
     prm.tile_cfg = tune["tile_cfg"]
     for _ in range(max(0, args.warmup - 1)):
         one_fill(z, mask, zhat)
+
+    # a first map of a new shape pays for its e(T, L) table: a fill with a seed whose table
+    # is not cached yet (the table depends on the seed), timed alone
+    cold_prm = mpr.mpr_default_params(seed=1_000_001 + rank, M=M, tile_cfg=prm.tile_cfg)
+    flush.zero_()
+    torch.cuda.synchronize()
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    one_fill(z, mask, zhat, cold_prm)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    cold_ms = c0.elapsed_time(c1)
 
     def timed(zi, mi, out):
         total_ms, updates, launches, sweeps = 0.0, 0, 0, []
@@ -798,36 +859,41 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     torch.cuda.profiler.start()        # an ncu run with --profile-from-start off sees these steps
+    mpr.mpr_sweep_timing_start()       # CUDA events around every sweep-kernel launch of the steps
     dev_ms, dev_updates, launches, sweeps, T = timed(z, mask, zhat)
+    swt = mpr.mpr_sweep_timing_read(stop=True)
     torch.cuda.profiler.stop()
     e2e_ms, e2e_updates, _, _, _ = timed(z_h, m_h, zhat_h)
     clk = clocks.stop()
 
-    # dominant kernel: fused sweep launches timed with CUDA events on the context stream
-    ctx = mpr.mpr_init(z, mask, W, H, prm, stream.cuda_stream)
-    try:
-        mpr.mpr_set_T(ctx, T)
-        mpr.mpr_sweep(ctx, 50, 8.0)
-        sweep_ms = mpr.mpr_time_sweeps(ctx, 20, 8.0)
-    finally:
-        mpr.mpr_free(ctx)
-    # the same sweep with the fast transcendentals (__sincosf, ex2.approx), for reference
+    # the same sweeps with the fast transcendentals (__sincosf, ex2.approx), for reference
     ctx = mpr.mpr_init(z, mask, W, H, mpr.mpr_default_params(seed=1 + rank, M=M, trig_mode=mpr.MPR_TRIG_FAST,
                                                              tile_cfg=prm.tile_cfg), stream.cuda_stream)
     try:
         mpr.mpr_set_T(ctx, T)
-        mpr.mpr_sweep(ctx, 50, 8.0)
-        sweep_ms_fast = mpr.mpr_time_sweeps(ctx, 20, 8.0)
+        mpr.mpr_sweep(ctx, 20, 1.0)
+        sweep_ms_fast = mpr.mpr_time_sweeps(ctx, 100, 1.0)
     finally:
         mpr.mpr_free(ctx)
-    N = H * W
-    P = int(m_np.size - m_np.sum())
-    # algorithmic bytes of one sweep: read every site's vector once (8 B), write every gap
-    # site once (8 B) and read its 2-byte list entry
-    bytes_per_launch = 8 * N + 10 * P
+    # roofline of the dominant kernel (the persistent sweep kernel: one launch per phase of
+    # a fill), from the CUDA-event durations of its launches in the timed steps.  Algorithmic
+    # bytes of one sweep: every site's angle read once (4 B) plus the gap sites' angles
+    # read and written (8 B) plus the mask bits (N / 4 B); the unit-vector lattice's own
+    # bytes are 8 B per site read and 10 B per gap site (vector written, list entry read).
     peaks, peak_src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = bytes_per_launch / (sweep_ms * 1e-3) / 1e9
+    k_ms = swt["ms"]
+    k_launches = max(1, swt["launches"])
+    bytes_alg = 4.25 * swt["site_sweeps"] + 8.0 * swt["gap_updates"]
+    bytes_uv = 8.0 * swt["site_sweeps"] + 10.0 * swt["gap_updates"]
+    achieved = bytes_alg / (k_ms * 1e-3) / 1e9 if k_ms > 0 else 0.0
+    sweeps_total = swt["site_sweeps"] / N
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = sms * LANES_PER_SM * sm_mhz * 1e6                 # lane operations / s
+    alu_achieved = ALU_OPS_PER_UPDATE * swt["gap_updates"] / (k_ms * 1e-3) if k_ms > 0 else 0.0
+    traffic_sweep = (TILE_TRAFFIC_PER_SWEEP.get(tune["tile_cfg"])
+                     if tile_kernel_hash() == TILE_TRAFFIC_SOURCE_HASH else None)
 
     (dev_ms, e2e_ms), (dev_updates, e2e_updates) = reduce_over_ranks(
         [dev_ms, e2e_ms], [dev_updates, e2e_updates], dist, dev)
@@ -841,9 +907,11 @@ def main():
             "config": {"workload": WORKLOAD, "W": W, "H": H, "gap_sites": P, "M": M,
                        "relax_sweeps": sweeps, "T_hat": T,
                        "s_per_map": dev_ms * 1e-3 / args.steps,
-                       "T_table": f"built once per shape during warm-up ({table_s:.2f} s incl. one fill)",
+                       "cold_s_per_map": cold_ms * 1e-3,
+                       "T_table": "cached per lattice shape and sampler parameters; every timed step "
+                                  "reuses it, cold_s_per_map includes building it",
                        "tile_cfg": tune["tile_cfg"], "autotune_ms_per_sweep": tune["ms_per_sweep"],
-                       "trig": "accurate (Taylor sincos, expf); fast-trig sweep in roofline.ms_per_launch_fast",
+                       "trig": "accurate (Taylor sincos, expf); fast-trig sweep in roofline.ms_per_sweep_fast",
                        "l2": "512 MB buffer written between steps (L2 flush)",
                        "parallelism": f"replicas{world}"},
             "e2e": {"value": e2e_updates / (e2e_ms * 1e-3), "unit": UNIT,
@@ -851,12 +919,23 @@ def main():
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm,
-                         "traffic": (TILE_TRAFFIC_BYTES.get(tune["tile_cfg"])
-                                     if tile_kernel_hash() == TILE_TRAFFIC_SOURCE_HASH else None),
-                         "kernel": "k_tile_sweep", "tile_cfg": tune["tile_cfg"], "ms_per_launch": sweep_ms,
-                         "ms_per_launch_fast": sweep_ms_fast,
+                         "traffic": (traffic_sweep * sweeps_total / k_launches) if traffic_sweep else None,
+                         "kernel": "k_tile_sweep", "tile_cfg": tune["tile_cfg"],
+                         "launches": swt["launches"], "ms_per_launch": k_ms / k_launches,
+                         "bytes_per_launch": bytes_alg / k_launches,
+                         "bytes_model": "(4 + 8p) N + N/4 per sweep",
+                         "sweeps_per_launch": sweeps_total / k_launches,
+                         "ms_per_sweep": k_ms / sweeps_total if sweeps_total else None,
+                         "ms_per_sweep_fast": sweep_ms_fast,
                          "peak_source": f"{peak_src} hbm_gbs",
-                         "bytes_per_launch": bytes_per_launch},
+                         "frac_unit_vector_bytes": bytes_uv / (k_ms * 1e-3) / 1e9 / hbm if k_ms > 0 else None,
+                         "traffic_per_sweep": traffic_sweep,
+                         "alu": {"ops_per_update": ALU_OPS_PER_UPDATE, "sms": sms,
+                                 "lanes_per_sm": LANES_PER_SM, "sm_mhz": sm_mhz,
+                                 "peak_ops": alu_peak, "achieved_ops": alu_achieved},
+                         "frac_alu": alu_achieved / alu_peak,
+                         "binding": "alu" if ALU_OPS_PER_UPDATE * swt["gap_updates"] / alu_peak
+                                    > bytes_alg / (hbm * 1e9) else "hbm"},
             "clocks": clk,
         }
         if not args.no_cpu_baseline and world == 1:

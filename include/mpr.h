@@ -160,16 +160,22 @@ mpr_status mpr_sweep(mpr_ctx* ctx, int n, double a, mpr_sweep_stats* out);
  * k < 0 and i <= i_max, with the window update of step 5.2 and the slope test of
  * step 5.4 (least-squares slope of the last n_fit specific energies, every n_f
  * sweeps once i >= n_fit).  Returns MPR_ENOTEQUIL if it stopped on i_max.  The loop runs
- * on the device (a CUDA graph whose conditional node repeats chunks of sweeps while any
- * grid is still relaxing, at most i_max / chunk + 4 chunks); the host waits once, at the
- * end.  Sweeps of a chunk that start after a grid has stopped leave it unchanged.
+ * on the device; the host waits once, at the end.  TILE kernels: the whole loop is one
+ * launch of the persistent sweep kernel, in which the block that completes a sweep's tiles
+ * runs the grid's control step and the next sweep's tiles start once it has published its
+ * window (every wait bounded: MPR_ETIMEOUT if one expires); the launch ends when every grid
+ * has stopped.  LIST kernels: a CUDA graph whose conditional node repeats chunks of sweeps
+ * while any grid is still relaxing (at most i_max / chunk + 4 chunks); sweeps of a chunk
+ * that start after a grid has stopped leave it unchanged.
  */
 mpr_status mpr_equilibrate(mpr_ctx* ctx, mpr_equil_stats* out);
 
 /*
  * Algorithm 2 steps 6-7: M >= 1 sweeps at window a_eq, accumulating every gap
  * angle, then zhat = G^-1(mean angle) at gaps and zhat = z at samples.
- * zhat: float[H][W] (host or device).
+ * zhat: float[H][W] (host or device).  TILE kernels: the M sweeps are one launch, in which
+ * a tile starts its next sweep as soon as it and its eight neighbouring tiles have finished
+ * the previous one, so consecutive sweeps overlap.
  */
 mpr_status mpr_predict(mpr_ctx* ctx, int M, float* zhat);
 
@@ -227,11 +233,10 @@ mpr_status mpr_batch_info(mpr_ctx* ctx, int g, double* T, double* e_s, int* swee
 /*
  * Autotuner of the TILE kernels: times a few sweeps of every compiled tile shape on the
  * context's own grids (starting from a snapshot of the state, which is restored, so the
- * chains are not advanced), keeps the fastest, and sets the number of sweeps per captured
- * chunk (the relaxation runs as a device-side loop over chunks, checking once per chunk
- * whether any grid is still relaxing) to about 60 us of sweeping, at least 4 and at most
- * 64.  Needs a temperature.  Outputs (may be NULL): chosen tile configuration, sweeps per
- * chunk, time of one sweep in ms.
+ * chains are not advanced), keeps the fastest, and sizes the chunk of sweeps of the LIST
+ * kernels' captured graphs to about 60 us of sweeping, at least 4 and at most 64.  Needs a
+ * temperature.  Outputs (may be NULL): chosen tile configuration, that chunk size, time of
+ * one sweep in ms.
  */
 mpr_status mpr_autotune(mpr_ctx* ctx, int* tile_cfg, int* graph_sweeps, double* ms_per_sweep);
 
@@ -266,9 +271,9 @@ mpr_status mpr_get_info(mpr_ctx* ctx, double* H_exact, double* H_tracked, double
 
 /*
  * Benchmark support: enqueues n sweeps at window a >= 1 (the kernels of the context's
- * exec_mode, launched directly, no graph), times them with CUDA events on the context
- * stream and returns the mean duration of one sweep in milliseconds.  Advances the state
- * and the sweep counter like mpr_sweep.
+ * exec_mode, launched directly, no graph: one launch of n sweeps on the TILE kernels),
+ * times them with CUDA events on the context stream and returns the mean duration of one
+ * sweep in milliseconds.  Advances the state and the sweep counter like mpr_sweep.
  */
 mpr_status mpr_time_sweeps(mpr_ctx* ctx, int n, double a, double* ms_per_sweep);
 
@@ -277,6 +282,31 @@ mpr_status mpr_time_sweeps(mpr_ctx* ctx, int n, double a, double* ms_per_sweep);
  * (direct launches plus the kernels of every replayed CUDA graph).
  */
 uint64_t mpr_kernel_launches(void);
+
+/*
+ * Benchmark support: timing of the TILE sweep kernel.  mpr_sweep_timing_start() resets
+ * the process-wide record and enables it: from then on every launch of the sweep kernel
+ * (every phase of mpr_equilibrate, mpr_predict, mpr_sweep, ...) is bracketed by CUDA events
+ * on its context's stream, and the library adds up, after the call's own synchronisation,
+ * the launches' durations (ms), their number, and the sweeps they performed as
+ * sum over grids of (sweeps x sites) and (sweeps x gap sites).  mpr_sweep_timing_read
+ * reports the record (any pointer may be NULL) and, if stop != 0, disables it.  The
+ * relaxation's sweeps are counted from the grids' sweep counters, which costs one extra
+ * read of the control state per phase while enabled.
+ */
+void mpr_sweep_timing_start(void);
+void mpr_sweep_timing_read(int stop, double* ms, uint64_t* launches, double* site_sweeps,
+                           double* gap_updates);
+
+/*
+ * Test support for the bounded waits of the TILE sweep kernel (process-wide, applies to
+ * launches made after the call).  ns: limit of every wait between blocks in nanoseconds
+ * (0 = the default, 4 s).  stall != 0: block 0 of every sweep launch first waits for a flag
+ * that nothing sets, so that the wait expires after ns: the launch sets its error flag,
+ * every block leaves after its copies have landed, and the call returns MPR_ETIMEOUT with
+ * the GPU still usable (the context's state is then unreliable: free it).
+ */
+void mpr_debug_wait_limit(uint64_t ns, int stall);
 
 /*
  * Memory of released contexts.  Contexts take their device memory from a stream-ordered
@@ -302,10 +332,13 @@ mpr_status mpr_release_memory(void);
  * synchronises the stream).  H may not exceed MPR_STATIC_MAX_ROWS (MPR_EINVAL otherwise).
  *
  * It allocates nothing and calls no allocating routine.  Its scratch is one fixed
- * device array of about 256 KB (16 bytes per row plus a 256-byte header), reserved on
- * every GPU where the library is loaded and held until the process exits.  The first
- * call on each device looks up that array's device address (cudaGetSymbolAddress, with
- * the device current); make that first call before any stream capture.  Every call
+ * device array of about 256 KB (16 bytes per row plus a 256-byte header), held until the
+ * process exits.  The array is reserved on a GPU when the library's device code is loaded
+ * there; under CUDA's lazy module loading (the default) that happens at the library's
+ * first use on that device, so a caller that must not see any allocation makes one call
+ * (or any other library call) on each device at start-up.  The first call on each device
+ * also looks up that array's device address (cudaGetSymbolAddress, with the device
+ * current); make that first call before any stream capture.  Every call
  * shares the one array: calls whose work overlaps on the GPU (other streams, other host
  * threads) race and must be serialised by the caller.  Each call clears the fields it
  * accumulates into before use, so one call's leftovers never reach the next.

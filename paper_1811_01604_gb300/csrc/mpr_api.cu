@@ -77,13 +77,16 @@ struct Batch {
     // tile path (fused sweeps over shared-memory tiles, two lattice buffers)
     bool tiled = false;
     float2* d_lat2 = nullptr;
-    TileDesc* d_tiles = nullptr;
+    TileDesc* d_tiles = nullptr;           // raster order per grid (index = TileDesc::t)
+    TileDesc* d_tiles_ord = nullptr;       // the same, each grid's heaviest first (relaxation order)
+    unsigned* d_tdone = nullptr;           // per tile: sweeps completed
+    int* d_live = nullptr;                 // grids still relaxing during a relaxation launch
     int ntiles = 0;
     TileCnt* d_cnts = nullptr;
     uint16_t* d_lists = nullptr;
     float* d_tacc = nullptr;
-    unsigned long long* d_gsum = nullptr;   // per grid: fixed-point energy change, acceptance count
-    unsigned* d_sched = nullptr;            // tile counter of the persistent sweep
+    unsigned long long* d_gsum = nullptr;   // per grid and slot: fixed-point energy change, acceptance count
+    unsigned* d_sched = nullptr;            // item counter, blocks-out counter, a flag nothing sets
     unsigned* d_ticket = nullptr;
     CUtensorMap* d_maps = nullptr;
     int* d_err = nullptr;
@@ -210,6 +213,9 @@ void batch_free(Batch& b, cudaStream_t st) {
     dfree(b.d_H, st);
     dfree(b.d_lat2, st);
     dfree(b.d_tiles, st);
+    dfree(b.d_tiles_ord, st);
+    dfree(b.d_tdone, st);
+    dfree(b.d_live, st);
     dfree(b.d_cnts, st);
     dfree(b.d_lists, st);
     dfree(b.d_tacc, st);
@@ -222,20 +228,23 @@ void batch_free(Batch& b, cudaStream_t st) {
 }
 
 // (Re)builds the tile tables of a batch for compiled configuration cfg: tile
-// descriptors, gap lists, per-tile accumulators and partials, tickets, tensor maps.
+// descriptors (raster order, and each grid's heaviest first), gap lists, per-tile
+// accumulators and completion counters, per-grid totals and tickets, tensor maps.
 mpr_status build_tiles(mpr_ctx* ctx, Batch& b, int cfg) {
     cudaStream_t st = ctx->st;
     if (cfg < 0 || cfg >= tile_config_count()) return fail(ctx, MPR_EINVAL, "tile configuration");
     const TileGeom g = tile_geom(cfg);
     dfree(b.d_tiles, st);
+    dfree(b.d_tiles_ord, st);
+    dfree(b.d_tdone, st);
     dfree(b.d_cnts, st);
     dfree(b.d_lists, st);
     dfree(b.d_tacc, st);
     dfree(b.d_gsum, st);
     dfree(b.d_sched, st);
     dfree(b.d_ticket, st);
-    b.d_tiles = nullptr; b.d_cnts = nullptr; b.d_lists = nullptr; b.d_tacc = nullptr;
-    b.d_gsum = nullptr; b.d_sched = nullptr; b.d_ticket = nullptr;
+    b.d_tiles = nullptr; b.d_tiles_ord = nullptr; b.d_tdone = nullptr; b.d_cnts = nullptr;
+    b.d_lists = nullptr; b.d_tacc = nullptr; b.d_gsum = nullptr; b.d_sched = nullptr; b.d_ticket = nullptr;
     for (auto& kv : b.graphs) cudaGraphExecDestroy(kv.second);
     b.graphs.clear();
     std::vector<TileDesc> tiles;          // per grid ceil(H/th) x ceil(W/tw), row-major
@@ -243,36 +252,45 @@ mpr_status build_tiles(mpr_ctx* ctx, Batch& b, int cfg) {
         EntryDesc& E = b.ents[e];
         E.tile0 = (int)tiles.size();
         for (int y0 = 0; y0 < E.H; y0 += g.th)
-            for (int x0 = 0; x0 < E.W; x0 += g.tw) tiles.push_back(TileDesc{e, y0, x0, 0, 0, 0, {0, 0}});
+            for (int x0 = 0; x0 < E.W; x0 += g.tw)
+                tiles.push_back(TileDesc{e, y0, x0, 0, 0, 0, (int)tiles.size(), 0});
         E.ntiles = (int)tiles.size() - E.tile0;
     }
     CU(cudaMemcpyAsync(b.d_ents, b.ents.data(), b.n_ent * sizeof(EntryDesc), cudaMemcpyHostToDevice, st));
     b.ntiles = (int)tiles.size();
     CU(dalloc(&b.d_tiles, tiles.size(), st));
     CU(cudaMemcpyAsync(b.d_tiles, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, st));
+    CU(dalloc(&b.d_tiles_ord, tiles.size(), st));
+    CU(dalloc(&b.d_tdone, tiles.size(), st));
     CU(dalloc(&b.d_cnts, tiles.size(), st));
     CU(dalloc(&b.d_lists, tiles.size() * (size_t)g.list, st));
     CU(dalloc(&b.d_tacc, tiles.size() * (size_t)g.acc, st));
-    CU(dalloc(&b.d_gsum, (size_t)2 * b.n_ent, st));
-    CU(cudaMemsetAsync(b.d_gsum, 0, sizeof(unsigned long long) * 2 * b.n_ent, st));
-    CU(dalloc(&b.d_sched, 2, st));
-    CU(cudaMemsetAsync(b.d_sched, 0, sizeof(unsigned) * 2, st));
-    CU(dalloc(&b.d_ticket, (size_t)b.n_ent, st));
-    CU(cudaMemsetAsync(b.d_ticket, 0, sizeof(unsigned) * b.n_ent, st));
+    CU(dalloc(&b.d_gsum, (size_t)2 * kSlots * b.n_ent, st));
+    CU(cudaMemsetAsync(b.d_gsum, 0, sizeof(unsigned long long) * 2 * kSlots * b.n_ent, st));
+    CU(dalloc(&b.d_sched, 3, st));
+    CU(cudaMemsetAsync(b.d_sched, 0, sizeof(unsigned) * 3, st));
+    CU(dalloc(&b.d_ticket, (size_t)kSlots * b.n_ent, st));
+    CU(cudaMemsetAsync(b.d_ticket, 0, sizeof(unsigned) * kSlots * b.n_ent, st));
     CU(launch_tile_lists(cfg, b.d_tiles, b.ntiles, b.d_ents, b.mask_base, b.all_free, b.d_lists,
                          b.d_cnts, st));
-    // heaviest tiles first (the counts are known now), then the lists again in that order
-    CU(cudaMemcpyAsync(tiles.data(), b.d_tiles, tiles.size() * sizeof(TileDesc), cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    order_tiles_by_work(tiles.data(), b.ents.data(), b.n_ent);
-    CU(cudaMemcpyAsync(b.d_tiles, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, st));
-    CU(launch_tile_lists(cfg, b.d_tiles, b.ntiles, b.d_ents, b.mask_base, b.all_free, b.d_lists,
-                         b.d_cnts, st));
+    // the relaxation's order (heaviest tiles first), from the counts just listed
+    unsigned* d_hist = nullptr;
+    CU(dalloc(&d_hist, (size_t)256 * b.n_ent, st));
+    CU(launch_tile_order(b.d_tiles, b.ntiles, b.d_ents, b.n_ent, cfg, d_hist, b.d_tiles_ord, st));
+    dfree(d_hist, st);
+    if (b.d_ctl) CU(launch_tile_sync(b.d_tiles, b.ntiles, b.d_ctl, b.n_ent, b.d_tdone, st));
     CU(make_tile_maps(cfg, b.ents.data(), b.n_ent, b.d_lat, b.d_lat2, b.d_maps, st));
     tile_sweep_blocks(cfg);               // kernel attributes are set outside any capture
     CU(cudaGetLastError());
-    CU(cudaStreamSynchronize(st));
     b.tcfg = cfg;
+    return MPR_OK;
+}
+
+// After the host changed the control state: every tile's completion counter and every
+// grid's launch base follow the grids' sweep counters.
+mpr_status sync_tiles(mpr_ctx* ctx, Batch& b) {
+    if (!b.tiled) return MPR_OK;
+    CU(launch_tile_sync(b.d_tiles, b.ntiles, b.d_ctl, b.n_ent, b.d_tdone, ctx->st));
     return MPR_OK;
 }
 
@@ -382,6 +400,7 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
         CU(dalloc(&b.d_maps, (size_t)2 * b.n_ent, st));
         CU(dalloc(&b.d_err, 1, st));
         CU(cudaMemsetAsync(b.d_err, 0, sizeof(int), st));
+        CU(dalloc(&b.d_live, 1, st));
         b.mask_base = mask_base;
         b.all_free = all_free;
         const mpr_status ts = build_tiles(ctx, b, ctx->prm.tile_cfg);
@@ -393,11 +412,15 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
         ctl[e].T = grids[e].T;
         ctl[e].a = 1.0;
         ctl[e].k = -1.0;
-        ctl[e].half_qd = (float)(0.5 * kTwoPi * 0.5 / 1.0);
+        ctl[e].half_qd = (float)(0.5 * kTwoPi * b.ents[e].q / 1.0);
         ctl[e].neg_inv_T = grids[e].T > 0.0 ? (float)(-1.0 / grids[e].T) : 0.0f;
     }
     CU(dalloc(&b.d_ctl, b.n_ent, st));
     CU(cudaMemcpyAsync(b.d_ctl, ctl.data(), b.n_ent * sizeof(Ctl), cudaMemcpyHostToDevice, st));
+    {
+        const mpr_status ss = sync_tiles(ctx, b);
+        if (ss != MPR_OK) return ss;
+    }
     b.ehist_stride = ctx->prm.i_max + 2;
     CU(dalloc(&b.d_ehist, (size_t)b.n_ent * b.ehist_stride, st));
     CU(cudaMemsetAsync(b.d_ehist, 0, sizeof(double) * (size_t)b.n_ent * b.ehist_stride, st));
@@ -434,8 +457,24 @@ SweepArgs sweep_args(const mpr_ctx* ctx, const Batch& b, bool use_ctl_a, double 
     return A;
 }
 
-// Enqueues n sweeps (A, B, control) on stream s.
-TileArgs tile_args(const mpr_ctx* ctx, const Batch& b, int mode, double a_fixed, bool acc) {
+// Limit of the tile kernels' waits between blocks, and the test switch that makes one
+// wait expire (process-wide; mpr_debug_wait_limit).
+std::atomic<unsigned long long> g_wait_ns{4000000000ull};
+std::atomic<int> g_stall{0};
+
+// Timing of the sweep kernel (mpr_sweep_timing_start / _read): CUDA events around every
+// tile-path sweep launch, on the context's stream, while enabled.
+struct SweepTiming {
+    std::mutex mu;
+    bool on = false;
+    double ms = 0.0;
+    unsigned long long launches = 0;
+    double site_sweeps = 0.0;    // sum over grids of sweeps x sites
+    double gap_updates = 0.0;    // sum over grids of sweeps x gap sites
+};
+SweepTiming g_timing;
+
+TileArgs tile_args(const mpr_ctx* ctx, const Batch& b, int mode, double a_fixed, bool acc, int nsweeps) {
     const mpr_params& p = ctx->prm;
     const bool relax = mode == CTL_RELAX;
     TileArgs T;
@@ -445,21 +484,23 @@ TileArgs tile_args(const mpr_ctx* ctx, const Batch& b, int mode, double a_fixed,
     T.lat[1] = b.d_lat2;
     T.maps = b.d_maps;
     T.err = b.d_err;
-    T.tiles = b.d_tiles;
-    T.cnts = b.d_cnts;
+    T.desc = relax ? b.d_tiles_ord : b.d_tiles;
     T.lists = b.d_lists;
     T.acc = acc ? b.d_tacc : nullptr;
     T.ctl = b.d_ctl;
     T.gsum = b.d_gsum;
     T.ticket = b.d_ticket;
     T.sched = b.d_sched;
+    T.tdone = b.d_tdone;
+    T.live = b.d_live;
     T.ehist = b.d_ehist;
     T.ehist_stride = b.ehist_stride;
     T.ntiles = b.ntiles;
+    T.n_ent = b.n_ent;
+    T.nsweeps = nsweeps;
     T.cfg = b.tcfg;
-    T.use_ctl_a = relax ? 1 : 0;
+    T.relax = relax ? 1 : 0;
     T.half_qd_fixed = (float)(0.5 * kTwoPi * p.q / a_fixed);
-    T.skip_stopped = relax ? 1 : 0;
     T.or_mode = p.or_mode;
     T.rk = round_keys(p.seed);
     T.mode = mode;
@@ -468,8 +509,26 @@ TileArgs tile_args(const mpr_ctx* ctx, const Batch& b, int mode, double a_fixed,
     T.n_f = p.n_f;
     T.n_fit = p.n_fit;
     T.i_max = p.i_max;
-    T.active = nullptr;
+    T.wait_ns = g_wait_ns.load();
+    T.stall = g_stall.load();
     return T;
+}
+
+// Sweeps per launch of the tile kernel (work items are counted in 32 bits).
+int tile_launch_cap(const Batch& b) {
+    const long long room = ((1LL << 31) - 65536LL) / std::max(1, b.ntiles);
+    return (int)std::max(1LL, std::min<long long>(room, 1LL << 30));
+}
+
+// One launch of n tile sweeps on stream s, timed with CUDA events while the sweep timing
+// is enabled (*ev_ms gets the launch's duration after the caller synchronised s).
+mpr_status launch_tile_phase(mpr_ctx* ctx, Batch& b, cudaStream_t s, int n, int mode, double a_fixed,
+                             bool acc, cudaEvent_t ev[2]) {
+    const TileArgs T = tile_args(ctx, b, mode, a_fixed, acc, n);
+    if (ev) CU(cudaEventRecord(ev[0], s));
+    CU(launch_tile_sweep(T, ctx->prm.trig_mode, s));
+    if (ev) CU(cudaEventRecord(ev[1], s));
+    return MPR_OK;
 }
 
 mpr_status enqueue_sweeps(mpr_ctx* ctx, Batch& b, cudaStream_t s, int n, int mode, double a_fixed,
@@ -477,15 +536,17 @@ mpr_status enqueue_sweeps(mpr_ctx* ctx, Batch& b, cudaStream_t s, int n, int mod
     const bool relax = mode == CTL_RELAX;
     const SweepArgs A = sweep_args(ctx, b, relax, a_fixed, relax, acc);
     const mpr_params& p = ctx->prm;
-    if (count_active) CU(cudaMemsetAsync(b.d_active, 0, sizeof(int) * b.gsweeps, s));
     if (b.tiled) {
-        TileArgs T = tile_args(ctx, b, mode, a_fixed, acc);
-        for (int i = 0; i < n; ++i) {
-            T.active = count_active ? b.d_active + (i % b.gsweeps) : nullptr;
-            CU(launch_tile_sweep(T, p.trig_mode, s));
+        const int cap = tile_launch_cap(b);
+        for (int done = 0; done < n;) {
+            const int k = std::min(cap, n - done);
+            const mpr_status ls = launch_tile_phase(ctx, b, s, k, mode, a_fixed, acc, nullptr);
+            if (ls != MPR_OK) return ls;
+            done += k;
         }
         return MPR_OK;
     }
+    if (count_active) CU(cudaMemsetAsync(b.d_active, 0, sizeof(int) * b.gsweeps, s));
     for (int i = 0; i < n; ++i) {
         CU(launch_half_sweep(A, 0, p.trig_mode, s));
         CU(launch_half_sweep(A, 1, p.trig_mode, s));
@@ -543,9 +604,13 @@ mpr_status build_relax_graph(mpr_ctx* ctx, Batch& b, int S, int cap, double a_fi
     return MPR_OK;
 }
 
-// Runs n sweeps through a cached CUDA graph of b.gsweeps sweeps (plus a tail); relaxation
-// (n ignored) through the device-side loop of build_relax_graph.
+// List path: runs n sweeps through a cached CUDA graph of b.gsweeps sweeps (plus a tail);
+// relaxation (n ignored) through the device-side loop of build_relax_graph.  The tile path
+// runs each phase as one persistent launch (run_tile_sweeps).
+mpr_status run_tile_sweeps(mpr_ctx* ctx, Batch& b, int n, int mode, double a_fixed, bool acc);
+
 mpr_status run_sweeps(mpr_ctx* ctx, Batch& b, int n, int mode, double a_fixed, bool acc) {
+    if (b.tiled) return run_tile_sweeps(ctx, b, n, mode, a_fixed, acc);
     const int S = b.gsweeps;
     const bool relax = mode == CTL_RELAX;
     if (n <= 0 && !relax) return MPR_OK;
@@ -608,6 +673,71 @@ mpr_status run_sweeps(mpr_ctx* ctx, Batch& b, int n, int mode, double a_fixed, b
     return enqueue_sweeps(ctx, b, ctx->st, n - done, mode, a_fixed, acc, false);
 }
 
+// Tile path: a whole phase is one launch of the persistent sweep kernel.  The relaxation
+// is one launch of up to i_max + 1 sweeps that ends as soon as every grid has stopped (the
+// control steps count down the grids still relaxing); a fixed-window phase of n sweeps is
+// one launch.  (More launches only if a phase has more sweeps than one launch can count.)
+// The host then reads the error flag, and the count of grids still relaxing, once.
+mpr_status run_tile_sweeps(mpr_ctx* ctx, Batch& b, int n, int mode, double a_fixed, bool acc) {
+    const bool relax = mode == CTL_RELAX;
+    if (!relax && n <= 0) return MPR_OK;
+    const int cap = tile_launch_cap(b);
+    const long long total = relax ? (long long)ctx->prm.i_max + 1 : (long long)n;
+    bool timing = false;
+    {
+        std::lock_guard<std::mutex> lk(g_timing.mu);
+        timing = g_timing.on;
+    }
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (timing) {
+        CU(cudaEventCreate(&ev[0]));
+        CU(cudaEventCreate(&ev[1]));
+    }
+    std::vector<Ctl> c0;
+    if (timing && relax) {
+        const mpr_status rs = read_ctl(ctx, b, c0);
+        if (rs != MPR_OK) return rs;
+    }
+    if (relax) CU(launch_count_live(b.d_ctl, b.n_ent, b.d_live, ctx->st));
+    mpr_status s = MPR_OK;
+    long long done = 0;
+    while (s == MPR_OK && done < total) {
+        const int k = (int)std::min<long long>(cap, total - done);
+        s = launch_tile_phase(ctx, b, ctx->st, k, mode, a_fixed, acc, timing ? ev : nullptr);
+        if (s != MPR_OK) break;
+        done += k;
+        int* h = ctx->h_active;
+        cudaError_t e = cudaMemcpyAsync(h, b.d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st);
+        if (e == cudaSuccess && relax) e = cudaMemcpyAsync(h + 1, b.d_live, sizeof(int), cudaMemcpyDeviceToHost, ctx->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+        if (e != cudaSuccess) { s = fail(ctx, MPR_ECUDA, std::string("tile sweeps: ") + cudaGetErrorString(e)); break; }
+        if (timing) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            double site_sweeps = 0.0, gap_updates = 0.0;
+            std::vector<Ctl> c1;
+            if (relax) s = read_ctl(ctx, b, c1);
+            for (int g = 0; g < b.n_ent && s == MPR_OK; ++g) {
+                const double sw = relax ? (double)(c1[g].sweep - c0[g].sweep) : (double)k;
+                site_sweeps += sw * (double)b.ents[g].W * (double)b.ents[g].H;
+                gap_updates += sw * (double)b.ents[g].P;
+            }
+            if (relax && s == MPR_OK) c0 = c1;
+            std::lock_guard<std::mutex> lk(g_timing.mu);
+            g_timing.ms += ms;
+            g_timing.launches += 1;
+            g_timing.site_sweeps += site_sweeps;
+            g_timing.gap_updates += gap_updates;
+        }
+        if (h[0]) { s = fail(ctx, MPR_ETIMEOUT, "a bounded wait of the sweep kernel expired"); break; }
+        if (relax && h[1] <= 0) break;
+        if (relax && done >= total) s = fail(ctx, MPR_ETIMEOUT, "relaxation did not stop within i_max sweeps");
+    }
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    if (ev[1]) cudaEventDestroy(ev[1]);
+    return s;
+}
+
 // Recomputes Eq. 2 for every entry and makes it the tracked energy.
 mpr_status read_ctl(mpr_ctx* ctx, Batch& b, std::vector<Ctl>& out);
 
@@ -644,7 +774,7 @@ mpr_status reset_relax(mpr_ctx* ctx, Batch& b) {
         c[e].converged = 0;
         c[e].esum = 0.0;
         c[e].nsamp = 0;
-        c[e].half_qd = (float)(0.5 * kTwoPi * 0.5 / 1.0);
+        c[e].half_qd = (float)(0.5 * kTwoPi * b.ents[e].q / 1.0);
     }
     CU(cudaMemcpyAsync(b.d_ctl, c.data(), sizeof(Ctl) * b.n_ent, cudaMemcpyHostToDevice, ctx->st));
     return reset_tracked_energy(ctx, b);
@@ -1099,9 +1229,12 @@ mpr_status mpr_predict_chains(mpr_ctx* ctx, int K, int burn_in, int M_per_chain,
             e = cudaMemcpyAsync(ab.d_lat + ab.ents[k].plane[0], src, state * sizeof(float2),
                                 cudaMemcpyDeviceToDevice, ctx->st);
             ck[k].cur = 0;
+            ck[k].cur_base = 0;
+            ck[k].sweep_base = ck[k].sweep;
         }
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(ab.d_ctl, ck.data(), sizeof(Ctl) * K, cudaMemcpyHostToDevice, ctx->st);
+        if (e == cudaSuccess && sync_tiles(ctx, ab) != MPR_OK) e = cudaErrorUnknown;
         if (e == cudaSuccess)
             e = cudaMemsetAsync(ab.d_tacc, 0, sizeof(float) * (size_t)ab.ntiles * tile_geom(ab.tcfg).acc,
                                 ctx->st);
@@ -1254,7 +1387,11 @@ mpr_status mpr_set_state(mpr_ctx* ctx, const float* phi, uint32_t sweep) {
     CU(cudaMemcpyAsync(ctx->d_out, phi, n * sizeof(float), cudaMemcpyDefault, ctx->st));
     CU(launch_set_state(&ctx->b.ents[0], lat_cur(ctx->b, c[0]), ctx->b.d_gaps, ctx->d_out, ctx->b.f64, ctx->st));
     c[0].sweep = sweep;
+    c[0].sweep_base = sweep;
+    c[0].cur_base = c[0].cur;
     CU(cudaMemcpyAsync(ctx->b.d_ctl, c.data(), sizeof(Ctl), cudaMemcpyHostToDevice, ctx->st));
+    s = sync_tiles(ctx, ctx->b);
+    if (s != MPR_OK) return s;
     CU(cudaStreamSynchronize(ctx->st));
     return MPR_OK;
 }
@@ -1311,6 +1448,8 @@ mpr_status mpr_autotune(mpr_ctx* ctx, int* tile_cfg, int* graph_sweeps, double* 
         CU(cudaMemcpyAsync(b.d_lat, snap0, bytes, cudaMemcpyDeviceToDevice, ctx->st));
         CU(cudaMemcpyAsync(b.d_lat2, snap1, bytes, cudaMemcpyDeviceToDevice, ctx->st));
         CU(cudaMemcpyAsync(b.d_ctl, c0.data(), sizeof(Ctl) * c0.size(), cudaMemcpyHostToDevice, ctx->st));
+        s = sync_tiles(ctx, b);
+        if (s != MPR_OK) return s;
         CU(cudaStreamSynchronize(ctx->st));
     }
     dfree(snap0, ctx->st);
@@ -1320,9 +1459,9 @@ mpr_status mpr_autotune(mpr_ctx* ctx, int* tile_cfg, int* graph_sweeps, double* 
         s = build_tiles(ctx, b, best);
         if (s != MPR_OK) return s;
     }
-    // sweeps per chunk of the device-side relaxation loop: at least ~60 us of sweeping per
-    // chunk, so that the chunk's condition launch (a few us) costs under ~5 %; more only
-    // adds empty launches after the last grid has stopped
+    // sweeps per captured chunk of the list path's graphs (the tile path runs each phase as
+    // one launch): at least ~60 us of sweeping per chunk, so that the chunk's condition
+    // launch (a few us) costs under ~5 %
     int S = (int)std::lround(0.06 / std::max(best_ms, 1e-6));
     S = std::min(kMaxGraphSweeps, std::max(4, S));
     if (S != b.gsweeps) {
@@ -1355,6 +1494,30 @@ mpr_status mpr_time_sweeps(mpr_ctx* ctx, int n, double a, double* ms_per_sweep) 
     cudaEventDestroy(e1);
     *ms_per_sweep = (double)ms / (double)n;
     return MPR_OK;
+}
+
+void mpr_debug_wait_limit(uint64_t ns, int stall) {
+    g_wait_ns = ns ? (unsigned long long)ns : 4000000000ull;
+    g_stall = stall ? 1 : 0;
+}
+
+void mpr_sweep_timing_start(void) {
+    std::lock_guard<std::mutex> lk(g_timing.mu);
+    g_timing.on = true;
+    g_timing.ms = 0.0;
+    g_timing.launches = 0;
+    g_timing.site_sweeps = 0.0;
+    g_timing.gap_updates = 0.0;
+}
+
+void mpr_sweep_timing_read(int stop, double* ms, uint64_t* launches, double* site_sweeps,
+                           double* gap_updates) {
+    std::lock_guard<std::mutex> lk(g_timing.mu);
+    if (ms) *ms = g_timing.ms;
+    if (launches) *launches = g_timing.launches;
+    if (site_sweeps) *site_sweeps = g_timing.site_sweeps;
+    if (gap_updates) *gap_updates = g_timing.gap_updates;
+    if (stop) g_timing.on = false;
 }
 
 mpr_status mpr_release_memory(void) {

@@ -60,12 +60,19 @@ struct Ctl {                  // mutable per-entry control state (Algorithm 2)
     int i;                    // relaxation counter
     int stop;                 // relaxation finished (or nothing to do)
     int converged;
-    uint32_t sweep;           // global sweep counter (Philox counter word 1)
     int nsamp;
     int status;               // 0, or a device-side error code
     int cur;                  // tile path: which of the two lattice buffers holds the state
     float half_qd;            // q * pi / a as float (proposal half-angle scale)
     float neg_inv_T;          // -1/T as float
+    // tile path: sweep counter and buffer at the start of the current multi-sweep launch
+    // (sweep s of a launch has counter sweep_base + s and reads buffer cur_base ^ (s & 1));
+    // written by the host with every change of `sweep` and by the last block of a launch
+    uint32_t sweep_base;
+    int cur_base;
+    // global sweep counter (Philox counter word 1); alone in the last 8-byte word, since
+    // the tile path publishes it last, with release semantics, after the other fields
+    uint32_t sweep;
     int _pad1;
 };
 
@@ -91,7 +98,8 @@ struct TileDesc {             // one tile: its grid, origin, and gap-list counts
     int nA_int;               // colour A inside the tile
     int nA_ring;              // colour A on the one-site ring
     int nB;                   // colour B inside the tile
-    int _pad[2];
+    int t;                    // the tile's own index (its lists and accumulators)
+    int _pad;
 };
 
 struct TileCnt {              // gap sites listed for one tile
@@ -119,32 +127,37 @@ inline RoundKeys round_keys(uint64_t seed) {
     return rk;
 }
 
+constexpr int kSlots = 8;     // per grid: ring of per-sweep totals and tickets (tile path)
+
 struct TileArgs {
     const EntryDesc* ents;
-    float2* lat[2];           // the two lattice buffers (Ctl::cur selects the source)
+    float2* lat[2];           // the two lattice buffers (sweep s reads cur_base ^ (s & 1))
     const CUtensorMap* maps;  // per entry: maps of buffer 0 and buffer 1 (64-byte aligned)
     int* err;                 // set to 1 if a bounded wait gave up
-    const TileDesc* tiles;
-    const TileCnt* cnts;
-    const uint16_t* lists;
+    const TileDesc* desc;     // tiles in the order they are handed out (TileDesc::t = index)
+    const uint16_t* lists;    // per tile index: its gap list slot
     float* acc;               // per-tile accumulators, or nullptr
     Ctl* ctl;
-    unsigned long long* gsum; // per grid: energy change (fixed point, 2^-28) and acceptance count
-    unsigned* ticket;         // one per grid, zero between sweeps
-    unsigned* sched;          // tile counter and blocks-done counter, zero between launches
+    unsigned long long* gsum; // per grid and slot: energy change (fixed point, 2^-28), acceptance count
+    unsigned* ticket;         // per grid and slot: tiles done, zero between uses
+    unsigned* sched;          // work-item counter and blocks-done counter, zero between launches
+    unsigned* tdone;          // per tile index: sweeps completed (absolute counter)
+    int* live;                // relaxation: grids still relaxing
     double* ehist;
     int ehist_stride;
     int ntiles;
+    int n_ent;
+    int nsweeps;              // sweeps of this launch
     int cfg;                  // compiled tile configuration
-    int use_ctl_a;
+    int relax;                // Algorithm 2 step 5 (window from Ctl, grids stop) or a fixed window
     float half_qd_fixed;
-    int skip_stopped;
     int or_mode;              // over-relaxation: OR_CONSERVING, OR_LITERAL or OR_NONE
     RoundKeys rk;             // Philox round keys of the seed
     int mode;
     double A_targ, k_a;
     int n_f, n_fit, i_max;
-    int* active;
+    unsigned long long wait_ns;   // limit of every inter-block wait
+    int stall;                // test support: block 0 first waits on a flag that nothing sets
 };
 
 struct BlockWork {            // one sweep block: entry and first gap index of its chunk
@@ -482,7 +495,7 @@ __device__ __forceinline__ void control_step(Ctl& c, const EntryDesc& E, double 
         const double A = E.P ? (double)na / (double)E.P : 0.0;
         if (A < A_targ) {                                                  // 5.2
             c.a = 1.0 + (double)(c.i + 1) / k_a;
-            c.half_qd = (float)(0.5 * kTwoPi * 0.5 / c.a);
+            c.half_qd = (float)(0.5 * kTwoPi * E.q / c.a);
         }
         const double en = c.H / E.ngp;                                     // 5.3
         eh[c.i + 1] = en;
@@ -556,8 +569,16 @@ cudaError_t launch_tile_lists(int cfg, TileDesc* tiles, int ntiles, const EntryD
                               const uint8_t* mask, int all_free, uint16_t* lists, TileCnt* cnts,
                               cudaStream_t st);
 cudaError_t launch_tile_sweep(const TileArgs& a, int trig, cudaStream_t st);
-// Host: sorts each grid's tiles (with their gap counts filled in) by descending work.
-void order_tiles_by_work(TileDesc* tiles, const EntryDesc* ents, int n_ent);
+// ord <- the tiles of every grid, heaviest first (grids contiguous, in entry order); hist:
+// n_ent * 256 unsigned of scratch.  Needs the gap counts of every tile filled in.
+cudaError_t launch_tile_order(const TileDesc* tiles, int ntiles, const EntryDesc* ents, int n_ent,
+                              int cfg, unsigned* hist, TileDesc* ord, cudaStream_t st);
+// tdone[t] <- the sweep counter of tile t's grid; and every grid's launch base <- its
+// current sweep counter and buffer
+cudaError_t launch_tile_sync(const TileDesc* tiles, int ntiles, Ctl* ctl, int n_ent, unsigned* tdone,
+                             cudaStream_t st);
+// *live <- number of grids whose relaxation has not stopped
+cudaError_t launch_count_live(const Ctl* ctl, int n_ent, int* live, cudaStream_t st);
 // K > 1: the angle sums of K chains of one grid, chain c's tiles at tile + c * chain_tiles.
 cudaError_t launch_tile_predict_out(int cfg, const TileDesc* tiles, const TileCnt* cnts,
                                     const uint16_t* lists, const float* acc, const EntryDesc* ents,

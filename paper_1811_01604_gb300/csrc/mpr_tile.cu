@@ -1,25 +1,28 @@
-// mpr_tile.cu -- fused full sweep over shared-memory tiles with halos.
+// mpr_tile.cu -- fused sweeps over shared-memory tiles with halos, many sweeps per launch.
 //
-// One block owns a TH x TW tile of one grid.  It copies the tile plus a halo of two
-// sites of both colour planes from the current lattice buffer into shared memory,
-// updates colour A (Algorithm 1) on the tile and on a one-site ring around it, then
-// colour B on the tile, and writes the tile's interior to the other lattice buffer.
-// The ring updates duplicate what the neighbouring tiles compute for their own interior:
-// every update is a deterministic function of its neighbours and of its Philox counter
-// {site, sweep, chain, 0}, so the duplicates are bitwise identical and each tile's B
-// pass sees exactly the post-A values of a whole-grid half-sweep.  Reading one buffer
-// and writing the other keeps every tile's halo at the pre-sweep state.
+// One work item is one sweep of one TH x TW tile of one grid.  The block that runs it
+// copies the tile plus a halo of two sites of both colour planes from the sweep's source
+// lattice buffer into shared memory, updates colour A (Algorithm 1) on the tile and on a
+// one-site ring around it, then colour B on the tile, and writes the tile's interior to
+// the other lattice buffer.  The ring updates duplicate what the neighbouring tiles compute
+// for their own interior: every update is a deterministic function of its neighbours and
+// of its Philox counter {site, sweep, chain, 0}, so the duplicates are bitwise identical
+// and each tile's B pass sees exactly the post-A values of a whole-grid half-sweep.
+// Reading one buffer and writing the other keeps every tile's halo at the pre-sweep state;
+// consecutive sweeps alternate the buffers.
 //
 // Per tile, the gap sites are listed once at set-up (u16 (r << 7) | q in the tile's
 // local region coordinates): colour-A sites inside the tile, then colour-A sites on the
 // ring, then colour-B sites inside the tile, contiguous in a 16-byte aligned slot that is
-// copied into shared memory together with the region.  Accumulators for the equilibrium average
-// use the same order (A interior, then B).
+// copied into shared memory together with the region.  Accumulators for the equilibrium
+// average use the same order (A interior, then B).
 //
-// The sweep's accepted energy change and acceptance count are reduced per tile; the
-// last tile of a grid to finish (atomic ticket) adds the tiles' partials in tile order
-// and runs the Algorithm 2 control step for that grid in place, so no separate control
-// launch is needed and the sums are bitwise reproducible.
+// The sweep's accepted energy change and acceptance count go into per-grid, per-sweep
+// 64-bit fixed-point totals, whose sum does not depend on the order in which tiles finish;
+// the block that completes a sweep's tiles of a grid (atomic ticket) runs the Algorithm 2
+// control step for that grid in place, so no separate control launch is needed and the
+// results are bitwise reproducible.  A whole phase of Algorithm 2 (the relaxation, or the
+// M equilibrium sweeps) is one launch (k_tile_sweep).
 #include <algorithm>
 #include <vector>
 
@@ -154,15 +157,95 @@ __device__ __forceinline__ bool mbar_wait_try(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
-// Per-tile parameters staged in shared memory by the issuing thread, in 16-byte groups
+// ---------------------------------------------------------------- waits between blocks
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+    return (int)ld_relaxed(reinterpret_cast<const unsigned*>(p));
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// with a preceding relaxed load that observed a release store: acquire
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+// orders this thread's generic-proxy global accesses with its later async-proxy (TMA) ones
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// One thread spins until ready() holds.  It gives up, with the launch's error flag set,
+// as soon as another block has set the flag or once the wait outlives A.wait_ns.
+template <class F>
+__device__ __forceinline__ bool bounded_wait(const TileArgs& A, F ready) {
+    if (ready()) return true;
+    const unsigned long long t0 = gtimer();
+    for (unsigned k = 1;; ++k) {
+        if (ready()) return true;
+        if ((k & 7u) == 0u) {
+            if (ld_relaxed(A.err) != 0) return false;
+            if (gtimer() - t0 > A.wait_ns) {
+                atomicExch(A.err, 1);
+                return false;
+            }
+        }
+    }
+}
+
+// Control state in 8-byte words through L2 (other blocks rewrite it during a launch).
+static_assert(sizeof(Ctl) % 8 == 0 && offsetof(Ctl, sweep) % 8 == 0 &&
+                  offsetof(Ctl, sweep) + 8 == sizeof(Ctl),
+              "the sweep counter is published alone, last");
+__device__ __forceinline__ Ctl ctl_load(const Ctl* p) {
+    Ctl c;
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(p);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&c);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(Ctl) / 8); ++i) dst[i] = __ldcg(src + i);
+    return c;
+}
+// Every field but the sweep counter, then the counter with release semantics: a block
+// that acquires the new counter sees the whole control step.
+__device__ __forceinline__ void ctl_publish(Ctl* p, const Ctl& c) {
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(p);
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&c);
+#pragma unroll
+    for (int i = 0; i < (int)(offsetof(Ctl, sweep) / 8); ++i) __stcg(dst + i, src[i]);
+    st_release(&p->sweep, c.sweep);
+}
+
+// Per-item parameters staged in shared memory by the issuing thread, in 16-byte groups
 // so that each thread picks up what it needs with a few vector loads.
 struct __align__(16) TileParams {
-    int t, y0, x0, W;                     // tile, origin, grid width
+    int t, y0, x0, W;                     // tile (-1: no item), origin, grid width
     uint32_t chain, sweep;                // Philox counter words 2 and 1
     float half_qd, neg_inv_T;             // proposal half-angle scale, -1/T
     int nA_int, nA_ring, nB, e;           // list counts, grid
     int ntiles, H, pitch, cur;            // grid's tile count and height, row pitch, source buffer
     long long pl0, pl1;                   // plane offsets of the grid in the lattice buffers
+};
+
+// What the issuing thread keeps of the grid of the last item it looked at (constant
+// during a launch).
+struct GridCache {
+    int e, W, H, pitch;
+    int tile0, tpr, ntr, ntiles;          // first tile, tiles per row and per column, count
+    uint32_t chain, sweep_base;
+    int cur_base;
+    float neg_inv_T;
+    long long pl0, pl1;
 };
 
 // Energy changes are summed across the tiles of a grid in 64-bit fixed point (2^-28 units):
@@ -172,147 +255,195 @@ struct __align__(16) TileParams {
 constexpr float kFixScale = 268435456.0f;             // 2^28
 constexpr double kFixUnit = 1.0 / 268435456.0;
 
-// Thread 0 of a block, after a barrier that follows every warp's flush for grid e: n more
-// tiles of e are done (release/acquire through the fences around the ticket).  The block
-// completing e's tiles runs e's control step from the fixed-point totals and clears them.
-__device__ __forceinline__ void tile_ticket(const TileArgs& A, int e, int n) {
+// Thread 0 of a block, after a barrier that follows every warp's flush of the block's
+// totals for grid e at sweep sig: n more tiles of that sweep are done.  The block that
+// completes the sweep's tiles runs the grid's Algorithm 2 control step from the totals --
+// after the control step of sweep sig - 1, which a fixed-window launch may still be
+// running -- and publishes it.
+__device__ void tile_ticket(const TileArgs& A, int e, uint32_t sig, int n) {
+    const int slot = e * kSlots + (int)(sig & (uint32_t)(kSlots - 1));
     __threadfence();
-    const unsigned prev = atomicAdd(A.ticket + e, (unsigned)n);
-    if (prev + (unsigned)n == (unsigned)A.ents[e].ntiles) {
-        __threadfence();
-        const long long f = (long long)atomicExch(A.gsum + 2 * e, 0ull);
-        const unsigned long long nacc_e = atomicExch(A.gsum + 2 * e + 1, 0ull);
-        Ctl c = A.ctl[e];
-        control_step(c, A.ents[e], (double)f * kFixUnit, nacc_e, A.mode, A.A_targ, A.k_a, A.n_f,
-                     A.n_fit, A.i_max, A.ehist + (long long)e * A.ehist_stride, 1);
-        A.ctl[e] = c;
-        A.ticket[e] = 0u;
-        if (A.active && !c.stop) atomicAdd(A.active, 1);
-    }
+    const unsigned prev = atomicAdd(A.ticket + slot, (unsigned)n);
+    if (prev + (unsigned)n != (unsigned)A.ents[e].ntiles) return;
+    __threadfence();
+    Ctl* cp = A.ctl + e;
+    if (!bounded_wait(A, [&] { return ld_acquire(&cp->sweep) == sig; })) return;
+    const long long f = (long long)atomicExch(A.gsum + 2 * slot, 0ull);
+    const unsigned long long na = atomicExch(A.gsum + 2 * slot + 1, 0ull);
+    atomicExch(A.ticket + slot, 0u);
+    Ctl c = ctl_load(cp);
+    control_step(c, A.ents[e], (double)f * kFixUnit, na, A.mode, A.A_targ, A.k_a, A.n_f, A.n_fit,
+                 A.i_max, A.ehist + (long long)e * A.ehist_stride, 1);
+    ctl_publish(cp, c);
+    if (A.relax && c.stop) atomicSub(A.live, 1);
 }
 
-// Persistent fused sweep.  Blocks take tiles from a global counter (the last block to
-// leave resets it for the next launch), so faster blocks take more tiles and no block
-// idles while others finish.  Thread 0 stages a tile: a TMA box of both colour planes
-// plus the bulk-copied gap list, completing on the stage's mbarrier.  With two stages the
-// next tile is staged as soon as the current one is in shared memory, a whole tile
-// ahead; with one stage, after the previous tile has been written back.
-// Each thread keeps its energy change (fixed point) and acceptance count summed over the
-// block's tiles of one grid; when the block moves on to another grid or runs out of
-// tiles, the warps add them to the grid's totals and thread 0 adds the block's tile count
-// to the grid's ticket.  The block that completes a grid's tiles runs the grid's
-// Algorithm 2 control step from the totals.
-// The interior rows of both planes go back to the other lattice buffer as 16-byte
-// stores, which frees the stage at once.
-template <int TH, int TW, int TRIG, bool ACC, int NT, int STAGES, int MB>
+// Persistent fused sweeps: A.nsweeps sweeps of every tile of every grid in one launch.
+// Work item w is sweep s = w / ntiles of tile A.desc[w % ntiles]; blocks take items from a
+// global counter in increasing order (the last block to leave resets it), so faster blocks
+// take more items.  An item starts once what it reads is final:
+//  * relaxation (Algorithm 2 step 5): sweep s of a grid needs the window that the control
+//    step of sweep s - 1 chose, and runs only if that step did not end the relaxation, so
+//    its items wait for that control step (which follows every tile of sweep s - 1);
+//  * fixed window: tile t at sweep s needs the interiors of t and its 8 neighbours after
+//    sweep s - 1 (its halo is two sites wide), and writes the buffer those tiles read at
+//    sweep s - 1, so it waits for the 9 tiles' completion counters to pass s - 1; sweeps
+//    overlap wherever the tiles allow.
+// Items are taken in increasing order and depend only on items before them, so the
+// smallest unfinished item can always run: the launch cannot deadlock, whatever the
+// number of resident blocks.  Every wait is bounded (A.wait_ns); an expired wait sets the
+// error flag and every block leaves after its copies have landed.
+// Thread 0 stages an item: a TMA box of both colour planes plus the bulk-copied gap list,
+// completing on the block's mbarrier.  Each thread keeps its energy change (fixed point)
+// and acceptance count summed over the block's consecutive items of one grid and sweep;
+// before the block moves on to another grid or sweep, the warps add them to that sweep's
+// slot of the grid's totals and thread 0 adds the block's tile count to the slot's
+// ticket.  The block that completes a sweep's tiles runs the grid's control step.
+// The interior rows of both planes go back to the other lattice buffer as 16-byte stores.
+template <int TH, int TW, int TRIG, bool ACC, int NT, int MB>
 __global__ void __launch_bounds__(NT, MB)
 k_tile_sweep(const TileArgs A) {
-    static_assert(STAGES == 1 || STAGES == 2, "one or two stages");
     static_assert(TW % 8 == 0, "write-back in 16-byte vectors");
     using G = Geo<TH, TW>;
     extern __shared__ __align__(128) unsigned char dsm[];
-    float2(*stage)[2][G::RH][G::RW] = reinterpret_cast<float2(*)[2][G::RH][G::RW]>(dsm);
-    uint16_t(*slist)[G::LIST] =
-        reinterpret_cast<uint16_t(*)[G::LIST]>(dsm + STAGES * 2 * G::RH * G::RW * sizeof(float2));
-    __shared__ TileParams sp[STAGES];
-    __shared__ __align__(8) uint64_t bar[STAGES];
-    __shared__ int s_fail;
-    __shared__ TileParams cp_;                                 // thread 0's grid cache
-    __shared__ const CUtensorMap* cmap;
-    __shared__ int cstop;
+    float2(*sm)[G::RH][G::RW] = reinterpret_cast<float2(*)[G::RH][G::RW]>(dsm);
+    uint16_t* list = reinterpret_cast<uint16_t*>(dsm + 2 * G::RH * G::RW * sizeof(float2));
+    __shared__ TileParams sp;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(16) TileDesc dnext;
+    __shared__ GridCache gc;
+    __shared__ int s_fail, s_flush, s_ke, s_kn, s_last;
+    __shared__ uint32_t s_ksig;
+    __shared__ unsigned s_w0, s_w1;
+    __shared__ long long s_fx[NT];
+    __shared__ unsigned s_nat[NT];
     constexpr uint32_t kBytes = 2u * G::RH * G::RW * sizeof(float2);
     const int lane = threadIdx.x & 31;
+    const unsigned ntiles = (unsigned)A.ntiles;
+    const unsigned nitems = (unsigned)A.nsweeps * ntiles;
 
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < STAGES; ++i) mbar_init(&bar[i], 1);
-        fence_barrier_init();
-        s_fail = 0;
-    }
-    __syncthreads();
-
-    // Thread 0 only: tile indices come from the counter two tiles ahead and descriptors
-    // one tile ahead (an asynchronous copy into shared memory), so that staging a tile
-    // never waits on the counter or on a global load; the parameters of the grid being
-    // staged are reloaded only when the grid changes (tiles are taken in increasing
-    // order and a grid's tiles are contiguous; they are constant during a launch).
-    int ce = -1, i0 = A.ntiles, i1 = A.ntiles;
-    __shared__ __align__(16) TileDesc dnext;
-    auto fetch_desc = [&](int i) {
-        const TileDesc* src = A.tiles + i;
+    // thread 0 only: item s_w0 is next (its descriptor is on its way into dnext), s_w1 the
+    // one after (taken from the counter an item ahead, so staging never waits on it)
+    auto fetch_desc = [&](unsigned w) {
+        const TileDesc* src = A.desc + (w % ntiles);
         asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(&dnext)), "l"(src) : "memory");
         asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(&dnext) + 16u),
                      "l"(reinterpret_cast<const char*>(src) + 16) : "memory");
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    if (threadIdx.x == 0) {
-        i0 = (int)atomicAdd(A.sched, 1u);
-        i1 = (int)atomicAdd(A.sched, 1u);
-        if (i0 < A.ntiles) fetch_desc(i0);
-    }
-    auto load_entry = [&](int e) {
+    auto load_grid = [&](int e) {
         const EntryDesc& E = A.ents[e];
-        const Ctl& c = A.ctl[e];
-        cp_.W = E.W;
-        cp_.H = E.H;
-        cp_.chain = E.chain;
-        cp_.sweep = c.sweep;
-        cp_.half_qd = A.use_ctl_a ? c.half_qd : A.half_qd_fixed;
-        cp_.neg_inv_T = c.neg_inv_T;
-        cp_.e = e;
-        cp_.ntiles = E.ntiles;
-        cp_.pl0 = E.plane[0];
-        cp_.pl1 = E.plane[1];
-        cp_.pitch = E.pitch;
-        cp_.cur = c.cur;
-        cstop = A.skip_stopped ? c.stop : 0;
-        cmap = A.maps + 2 * e + c.cur;
-        ce = e;
+        const Ctl* cp = A.ctl + e;
+        gc.e = e;
+        gc.W = E.W;
+        gc.H = E.H;
+        gc.pitch = E.pitch;
+        gc.tile0 = E.tile0;
+        gc.tpr = (E.W + TW - 1) / TW;
+        gc.ntr = (E.H + TH - 1) / TH;
+        gc.ntiles = E.ntiles;
+        gc.chain = E.chain;
+        gc.pl0 = E.plane[0];
+        gc.pl1 = E.plane[1];
+        gc.sweep_base = __ldcg(&cp->sweep_base);
+        gc.cur_base = __ldcg(&cp->cur_base);
+        gc.neg_inv_T = __ldcg(&cp->neg_inv_T);
     };
-    // stages the next tile whose grid is still relaxing into stage st, or marks the stage
-    // empty (t = ntiles) when the counter is exhausted
-    auto issue = [&](int st) {
-        TileParams& P = sp[st];
+    // stages the next item to run into sp, or sets sp.t = -1 when there is none (all items
+    // taken, every grid's relaxation ended, or an expired wait)
+    auto issue = [&]() {
         for (;;) {
-            if (i0 >= A.ntiles) { P.t = A.ntiles; return; }
-            asm volatile("cp.async.wait_all;" ::: "memory");          // the descriptor of i0
+            const unsigned w = s_w0;
+            if (w >= nitems) { sp.t = -1; return; }
+            asm volatile("cp.async.wait_all;" ::: "memory");          // the descriptor of w
             const TileDesc d = dnext;
-            const int cur_t = i0;
-            i0 = i1;                                                  // taken a tile ago
-            if (i0 < A.ntiles) fetch_desc(i0);
-            i1 = (int)atomicAdd(A.sched, 1u);                         // needed two tiles from now
-            if (d.entry != ce) load_entry(d.entry);
-            if (!cstop) {
-                cp_.t = cur_t;
-                cp_.y0 = d.y0;
-                cp_.x0 = d.x0;
-                cp_.nA_int = d.nA_int;
-                cp_.nA_ring = d.nA_ring;
-                cp_.nB = d.nB;
-                P = cp_;
-                const uint32_t lbytes = ((uint32_t)(d.nA_int + d.nA_ring + d.nB) * 2u + 15u) & ~15u;
-                mbar_expect_tx(&bar[st], kBytes + lbytes);
-                tma_load_3d(&stage[st][0][0][0], cmap, &bar[st], d.x0 >> 1, d.y0 - 1, 0);
-                if (lbytes)
-                    bulk_load(&slist[st][0], A.lists + (long long)cur_t * G::LIST, lbytes, &bar[st]);
-                return;
+            const unsigned wn = s_w1;
+            s_w0 = wn;
+            if (wn < nitems) fetch_desc(wn);
+            s_w1 = atomicAdd(A.sched, 1u);
+            const int e = d.entry;
+            if (e != gc.e) load_grid(e);
+            const unsigned s = w / ntiles;
+            const uint32_t sig = gc.sweep_base + s;
+            Ctl* cp = A.ctl + e;
+            float half_qd = A.half_qd_fixed;
+            bool ok = true;
+            if (A.relax) {
+                // ready once the control step of sweep sig - 1 is published, or the grid's
+                // relaxation (or every grid's) has ended; the loads of one poll go out together
+                int stop = 0, live = 1;
+                ok = bounded_wait(A, [&] {
+                    const unsigned cs = ld_relaxed(&cp->sweep);
+                    stop = ld_relaxed(&cp->stop);
+                    live = ld_relaxed(A.live);
+                    return (int)(cs - sig) >= 0 || stop != 0 || live <= 0;
+                });
+                fence_acq_rel();
+                if (ok && live <= 0) { sp.t = -1; return; }           // every grid has stopped
+                if (ok && ld_relaxed(&cp->stop)) continue;            // this grid has stopped
+                half_qd = __uint_as_float(ld_relaxed(reinterpret_cast<const unsigned*>(&cp->half_qd)));
+            } else if (s > 0) {
+                // the halo: tile t and its 8 neighbours have finished sweep sig - 1; and the
+                // slot of sweep sig was emptied by the control step of sweep sig - kSlots
+                const int i = d.t - gc.tile0, ty = i / gc.tpr, tx = i - ty * gc.tpr;
+                const uint32_t slot_free = sig - (uint32_t)(kSlots - 1);
+                ok = bounded_wait(A, [&] {
+                    unsigned v[9];
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) {
+                        const int yy = ty + k / 3 - 1, xx = tx + k % 3 - 1;
+                        v[k] = (yy >= 0 && yy < gc.ntr && xx >= 0 && xx < gc.tpr)
+                                   ? ld_relaxed(A.tdone + gc.tile0 + yy * gc.tpr + xx) : sig;
+                    }
+                    const unsigned cs = s >= (unsigned)(kSlots - 1) ? ld_relaxed(&cp->sweep) : slot_free;
+                    bool r = (int)(cs - slot_free) >= 0;
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) r = r && (int)(v[k] - sig) >= 0;
+                    return r;
+                });
+                fence_acq_rel();
             }
+            if (!ok) { sp.t = -1; return; }
+            const int cur = gc.cur_base ^ (int)(s & 1u);
+            fence_proxy_async_global();                               // writes of other blocks before the copy
+            TileParams P;
+            P.t = d.t;
+            P.y0 = d.y0;
+            P.x0 = d.x0;
+            P.W = gc.W;
+            P.chain = gc.chain;
+            P.sweep = sig;
+            P.half_qd = half_qd;
+            P.neg_inv_T = gc.neg_inv_T;
+            P.nA_int = d.nA_int;
+            P.nA_ring = d.nA_ring;
+            P.nB = d.nB;
+            P.e = e;
+            P.ntiles = gc.ntiles;
+            P.H = gc.H;
+            P.pitch = gc.pitch;
+            P.cur = cur;
+            P.pl0 = gc.pl0;
+            P.pl1 = gc.pl1;
+            sp = P;
+            const uint32_t lbytes = ((uint32_t)(d.nA_int + d.nA_ring + d.nB) * 2u + 15u) & ~15u;
+            mbar_expect_tx(&bar, kBytes + lbytes);
+            tma_load_3d(&sm[0][0][0], A.maps + 2 * e + cur, &bar, d.x0 >> 1, d.y0 - 1, 0);
+            if (lbytes) bulk_load(list, A.lists + (long long)d.t * G::LIST, lbytes, &bar);
+            return;
         }
     };
-
-    // each thread's totals over the block's tiles of grid s_acc_e (kept in shared memory)
-    __shared__ long long s_fx[NT];
-    __shared__ unsigned s_nat[NT];
-    __shared__ int s_acc_e, ntile_e, pend_e, pend_n;         // thread 0 writes; ticket bookkeeping
-    s_fx[threadIdx.x] = 0;
-    s_nat[threadIdx.x] = 0u;
-    if (threadIdx.x == 0) {
-        s_acc_e = -1;
-        ntile_e = 0;
-        pend_e = -1;
-        pend_n = 0;
-    }
-    __syncthreads();
-    auto flush_partials = [&](int e) {
+    // thread 0, after an item of grid e at sweep sig: does the next item belong to another
+    // grid or sweep (or is there none)?  Then the block hands in its totals first.
+    auto next_differs = [&](int e, uint32_t sig) {
+        const unsigned w = s_w0;
+        if (w >= nitems) return true;
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        const int ne = dnext.entry;
+        if (ne != gc.e) load_grid(ne);
+        return ne != e || gc.sweep_base + w / ntiles != sig;
+    };
+    auto flush_partials = [&](int e, uint32_t sig) {
         long long w = s_fx[threadIdx.x];
         unsigned long long wn = s_nat[threadIdx.x];
 #pragma unroll
@@ -321,66 +452,79 @@ k_tile_sweep(const TileArgs A) {
             wn += __shfl_xor_sync(0xffffffffu, wn, o);
         }
         if (lane == 0) {
-            if (w) atomicAdd(A.gsum + 2 * e, (unsigned long long)w);
-            if (wn) atomicAdd(A.gsum + 2 * e + 1, wn);
+            const int slot = e * kSlots + (int)(sig & (uint32_t)(kSlots - 1));
+            if (w) atomicAdd(A.gsum + 2 * slot, (unsigned long long)w);
+            if (wn) atomicAdd(A.gsum + 2 * slot + 1, wn);
         }
         s_fx[threadIdx.x] = 0;
         s_nat[threadIdx.x] = 0u;
     };
-    // thread 0, after a barrier that follows every warp's flush for grid e: n more tiles of
-    // e are done; the block completing e's tiles runs e's control step
-    auto take_ticket = [&](int e, int n) { tile_ticket(A, e, n); };
 
-    if (threadIdx.x == 0) issue(0);
+    if (threadIdx.x == 0) {
+        // test support: a wait that must expire (before block 0 takes any item, so that it
+        // happens whatever the order in which the blocks start)
+        if (A.stall && blockIdx.x == 0) (void)bounded_wait(A, [&] { return ld_relaxed(A.sched + 2) != 0u; });
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+        s_fail = 0;
+        s_flush = 0;
+        s_ke = -1;
+        s_kn = 0;
+        gc.e = -1;
+        s_w0 = atomicAdd(A.sched, 1u);
+        s_w1 = atomicAdd(A.sched, 1u);
+        if (s_w0 < nitems) fetch_desc(s_w0);
+    }
+    s_fx[threadIdx.x] = 0;
+    s_nat[threadIdx.x] = 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) issue();
+
     for (int it = 0;; ++it) {
-        const int st = STAGES == 1 ? 0 : (it & 1);
-        const uint32_t parity = (uint32_t)(STAGES == 1 ? it : (it >> 1)) & 1u;
-        if (STAGES == 1 && it > 0) {
-            __syncthreads();                                      // B0: the write-back has read the stage
-            if (threadIdx.x == 0) issue(0);
+        const uint32_t parity = (uint32_t)it & 1u;
+        if (it > 0) {
+            __syncthreads();                                      // B0: write-back and flushes issued
+            if (threadIdx.x == 0) {
+                // the previous item is done: its tile's interior after sweep sp.sweep is in
+                // the other buffer, and the tile no longer reads its source buffer
+                __threadfence();
+                st_release(A.tdone + sp.t, sp.sweep + 1u);
+                if (s_flush) {
+                    tile_ticket(A, s_ke, s_ksig, s_kn);
+                    s_ke = -1;
+                    s_kn = 0;
+                }
+                issue();
+            }
         }
-        // the previous grid's ticket (its flushes were ordered by the last B2/B3), while the
-        // copy is in flight
-        if (threadIdx.x == 0 && pend_e >= 0) {
-            take_ticket(pend_e, pend_n);
-            pend_e = -1;
-        }
-        if (threadIdx.x == 0 && sp[st].t < A.ntiles && !mbar_wait_try(&bar[st], parity)) {
+        if (threadIdx.x == 0 && sp.t >= 0 && !mbar_wait_try(&bar, parity)) {
             atomicExch(A.err, 1);
             s_fail = 1;
         }
-        __syncthreads();                                          // B1: the tile is in stage st
-        const int4 g0 = *reinterpret_cast<const int4*>(&sp[st].t);
+        __syncthreads();                                          // B1: the tile is in shared memory
+        const int4 g0 = *reinterpret_cast<const int4*>(&sp.t);
         const int t = g0.x;
-        if (t >= A.ntiles) break;
+        if (t < 0) break;
         if (s_fail) {
             // give the late copy a second bounded wait to land before the block's shared
             // memory goes away (no other copy is in flight at B1), then leave
-            if (threadIdx.x == 0) (void)mbar_wait_try(&bar[st], parity);
+            if (threadIdx.x == 0) (void)mbar_wait_try(&bar, parity);
             break;
         }
-        (void)mbar_test(&bar[st], parity);                        // each thread acquires the copy
-        // stage st ^ 1 was written back before B1: stage the next tile into it now
-        if (STAGES == 2 && threadIdx.x == 0) issue(st ^ 1);
+        (void)mbar_test(&bar, parity);                            // each thread acquires the copy
         const int y0 = g0.y, x0 = g0.z, W = g0.w;
-        const int4 g1 = *reinterpret_cast<const int4*>(&sp[st].chain);
-        const int4 g2 = *reinterpret_cast<const int4*>(&sp[st].nA_int);
+        const int4 g1 = *reinterpret_cast<const int4*>(&sp.chain);
+        const int4 g2 = *reinterpret_cast<const int4*>(&sp.nA_int);
         const uint32_t chain = (uint32_t)g1.x, sweep = (uint32_t)g1.y;
         const float half_qd = __int_as_float(g1.z), kx = accept_scale<TRIG>(__int_as_float(g1.w));
         const int nA_int = g2.x, nA = g2.x + g2.y, nB = g2.z, e = g2.w;
-        float2(*sm)[G::RH][G::RW] = stage[st];
-        const uint16_t* list = slist[st];
         float* __restrict__ acc = ACC ? A.acc + (long long)t * G::ACC : nullptr;
-        {
-            const int acc_e = s_acc_e;                        // rewritten only after B2
-            if (e != acc_e) {                                 // the block moves on to grid e
-                if (acc_e >= 0) flush_partials(acc_e);
-                if (threadIdx.x == 0) {
-                    pend_e = acc_e;
-                    pend_n = ntile_e;
-                    ntile_e = 0;
-                }
+        if (threadIdx.x == 0) {
+            if (s_ke < 0) {
+                s_ke = e;
+                s_ksig = sweep;
             }
+            ++s_kn;
         }
 
         // colour A on the tile and its ring, then colour B on the tile
@@ -398,9 +542,9 @@ k_tile_sweep(const TileArgs A) {
                 const bool own_site = pass || k < nA_int;
                 const int aidx = pass ? nA_int + k : k;
                 // the running angle sum is loaded first, so that its latency hides behind
-                // the update
+                // the update (from L2: another block may have written it in this launch)
                 float acc_old = 0.0f;
-                if (ACC && own_site) acc_old = acc[aidx];
+                if (ACC && own_site) acc_old = __ldcg(acc + aidx);
                 const int ent = lst[k];
                 const int r = ent >> 7, q = ent & 127;
                 const int s = c ^ (r & 1);
@@ -421,28 +565,25 @@ k_tile_sweep(const TileArgs A) {
                 if (own_site) {
                     dE += d;
                     nacc += accepted ? 1u : 0u;
-                    if (ACC) acc[aidx] = acc_old + angle_upper(v.x, v.y);
+                    if (ACC) __stcg(acc + aidx, acc_old + angle_upper(v.x, v.y));
                 }
             }
-            if (pass == 0) {
-                __syncthreads();                          // B2: colour A done (and any flush)
-                if (threadIdx.x == 0) s_acc_e = e;
-            }
+            if (pass == 0) __syncthreads();               // B2: colour A done
         }
         // the tile's energy change in fixed point: deterministic whatever the tile order
         s_fx[threadIdx.x] += __float2ll_rn(dE * kFixScale);
         s_nat[threadIdx.x] += nacc;
-        if (threadIdx.x == 0) ++ntile_e;
-        fence_proxy_async_smem();                     // this thread's stage writes before the next copy into it
-        __syncthreads();                              // B3: colour B done
-        const int4 g3 = *reinterpret_cast<const int4*>(&sp[st].ntiles);
+        if (threadIdx.x == 0) s_flush = next_differs(e, sweep) ? 1 : 0;
+        fence_proxy_async_smem();                         // this thread's stage writes before the next copy into it
+        __syncthreads();                                  // B3: colour B done
+        const int4 g3 = *reinterpret_cast<const int4*>(&sp.ntiles);
         // interior rows of both colours to the other buffer (samples included), 16 bytes
         // per thread and step, one warp per row; rows and columns beyond the grid skipped
         {
             const int rows = min(TH, g3.y - y0);
             const int pc = (x0 >> 1) + 2;
             const int nv = (min(TW / 2, g3.z - pc) & ~1) >> 1;        // 16-byte vectors per row
-            const long long pl0 = sp[st].pl0, pl1 = sp[st].pl1;
+            const long long pl0 = sp.pl0, pl1 = sp.pl1;
             float2* __restrict__ dst = g3.w ? A.lat[0] : A.lat[1];
             constexpr int V = TW / 4;
 #pragma unroll
@@ -455,22 +596,94 @@ k_tile_sweep(const TileArgs A) {
                 }
             }
         }
+        fence_proxy_async_global();                       // the write-back before later copies of it
+        if (s_flush) flush_partials(e, sweep);
     }
-    // leave: hand in the last grid's totals and tiles, then the last block out resets the
-    // tile counter for the next launch (every block has stopped taking tiles by the time
-    // it counts itself out)
-    const int acc_e = s_acc_e;
-    if (acc_e >= 0) flush_partials(acc_e);
+    // an error or the end of the relaxation can leave totals that were not handed in
     __syncthreads();
-    if (threadIdx.x == 0 && acc_e >= 0) take_ticket(acc_e, ntile_e);
+    {
+        const int ke = s_ke;
+        if (ke >= 0 && s_kn > 0) {
+            flush_partials(ke, s_ksig);
+            __syncthreads();
+            if (threadIdx.x == 0) tile_ticket(A, ke, s_ksig, s_kn);
+        }
+    }
+    // leave: the last block out resets the counters for the next launch and records every
+    // grid's sweep counter and buffer as the next launch's base (every block has stopped
+    // taking items, and every control step has run, by the time it counts itself out)
     if (threadIdx.x == 0) {
         asm volatile("cp.async.wait_all;" ::: "memory");
         __threadfence();
-        if (atomicAdd(A.sched + 1, 1u) == gridDim.x - 1u) {
+        s_last = atomicAdd(A.sched + 1, 1u) == gridDim.x - 1u ? 1 : 0;
+        if (s_last) __threadfence();
+    }
+    __syncthreads();
+    if (s_last) {
+        for (int e = threadIdx.x; e < A.n_ent; e += NT) {
+            Ctl* cp = A.ctl + e;
+            cp->sweep_base = ld_relaxed(&cp->sweep);
+            cp->cur_base = ld_relaxed(&cp->cur);
+        }
+        if (threadIdx.x == 0) {
             atomicExch(A.sched, 0u);
             atomicExch(A.sched + 1, 0u);
         }
     }
+}
+
+// Tile order of the relaxation: each grid's tiles heaviest first, in 256 buckets of the
+// listed gap count (the order inside a bucket is arbitrary: every update depends only on
+// its neighbours and its counter, and the totals are order-independent, so no result
+// depends on it).  Handing out the heavy tiles first makes a sweep's tail out of light
+// tiles, which matters where every sweep waits for the previous one's control step.
+__device__ __forceinline__ int work_bucket(const TileDesc& d, int maxw) {
+    const int w = d.nA_int + d.nA_ring + d.nB;
+    return 255 - min(255, (int)((long long)w * 256 / (maxw + 1)));
+}
+__global__ void k_tile_hist(const TileDesc* __restrict__ tiles, int ntiles, int maxw, unsigned* hist) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const TileDesc d = tiles[t];
+    atomicAdd(hist + d.entry * 256 + work_bucket(d, maxw), 1u);
+}
+__global__ void k_tile_scan(unsigned* hist, const EntryDesc* __restrict__ ents, int n_ent) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_ent) return;
+    unsigned run = (unsigned)ents[e].tile0;
+    for (int b = 0; b < 256; ++b) {
+        const unsigned c = hist[e * 256 + b];
+        hist[e * 256 + b] = run;
+        run += c;
+    }
+}
+__global__ void k_tile_scatter(const TileDesc* __restrict__ tiles, int ntiles, int maxw, unsigned* hist,
+                               TileDesc* __restrict__ ord) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const TileDesc d = tiles[t];
+    ord[atomicAdd(hist + d.entry * 256 + work_bucket(d, maxw), 1u)] = d;
+}
+
+__global__ void k_tile_sync(const TileDesc* __restrict__ tiles, int ntiles, Ctl* ctl, int n_ent,
+                            unsigned* __restrict__ tdone) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ntiles) tdone[i] = ctl[tiles[i].entry].sweep;
+    if (i < n_ent) {
+        ctl[i].sweep_base = ctl[i].sweep;
+        ctl[i].cur_base = ctl[i].cur;
+    }
+}
+
+__global__ void k_count_live(const Ctl* __restrict__ ctl, int n_ent, int* live) {
+    __shared__ int n;
+    if (threadIdx.x == 0) n = 0;
+    __syncthreads();
+    int m = 0;
+    for (int e = threadIdx.x; e < n_ent; e += blockDim.x) m += ctl[e].stop ? 0 : 1;
+    if (m) atomicAdd(&n, m);
+    __syncthreads();
+    if (threadIdx.x == 0) *live = n;
 }
 
 // zhat at the gap sites of every tile (same mean and inverse map as the list path).  With
@@ -507,39 +720,24 @@ __global__ void k_tile_predict_out(const TileDesc* __restrict__ tiles, const Til
 
 }  // namespace
 
-// Heaviest tiles first.  The persistent blocks take tiles in index order, so with each
-// grid's tiles sorted by descending gap count the last tiles handed out are the lightest
-// and the blocks finish close together (cloud-like gaps make some tiles several times
-// heavier than others).  Stable, so equal tiles keep raster order; per grid, so a grid's
-// tiles stay contiguous.  Every update depends only on its neighbours and its counter, so
-// the order changes no result.
-void order_tiles_by_work(TileDesc* tiles, const EntryDesc* ents, int n_ent) {
-    for (int e = 0; e < n_ent; ++e) {
-        TileDesc* t0 = tiles + ents[e].tile0;
-        std::stable_sort(t0, t0 + ents[e].ntiles, [](const TileDesc& a, const TileDesc& b) {
-            return a.nA_int + a.nA_ring + a.nB > b.nA_int + b.nA_ring + b.nB;
-        });
-    }
-}
-
 // ---------------------------------------------------------------- compiled configurations
 // The tile shapes the library is built with; the autotuner picks one per batch.
-//   id  TH  TW  threads  stages  blocks/SM register budget
-//    0  16 128     128       1    8
-//    1  32  64     128       1    8
-//    2  32 128     256       1    4
+//   id  TH  TW  threads  blocks/SM register budget
+//    0  16 128     128    8
+//    1  32  64     128    8
+//    2  32 128     256    4
 #define MPR_TILE_CONFIGS(X) \
-    X(0, 16, 128, 128, 1, 8)  \
-    X(1, 32, 64, 128, 1, 8)   \
-    X(2, 32, 128, 256, 1, 4)
+    X(0, 16, 128, 128, 8)  \
+    X(1, 32, 64, 128, 8)   \
+    X(2, 32, 128, 256, 4)
 
-template <int TH, int TW, int NT, int ST>
+template <int TH, int TW>
 struct Cfg {
     using G = Geo<TH, TW>;
-    static constexpr int SMEM = ST * 2 * G::RH * G::RW * 8 + ST * G::LIST * 2;
+    static constexpr int SMEM = 2 * G::RH * G::RW * 8 + G::LIST * 2;
 };
 
-#define MPR_CFG_GEOM(id, th, tw, nt, st, mb) \
+#define MPR_CFG_GEOM(id, th, tw, nt, mb) \
     case id: g = TileGeom{th, tw, Geo<th, tw>::RH, Geo<th, tw>::RW, Geo<th, tw>::LIST, Geo<th, tw>::ACC, nt}; break;
 TileGeom tile_geom(int cfg) {
     TileGeom g{0, 0, 0, 0, 0, 0, 0};
@@ -589,27 +787,27 @@ cudaError_t make_tile_maps(int cfg, const EntryDesc* ents, int n_ent, float2* la
 // than the default 48 KB) and returns the persistent grid size of configuration cfg:
 // blocks per SM at its footprint times the SMs.  Called from set-up code, never under
 // stream capture.
-template <int TH, int TW, int NT, int ST, int MB>
+template <int TH, int TW, int NT, int MB>
 int blocks_for() {
-    constexpr int sm = Cfg<TH, TW, NT, ST>::SMEM;
-    cudaFuncSetAttribute(k_tile_sweep<TH, TW, TRIG_ACCURATE, true, NT, ST, MB>,
+    constexpr int sm = Cfg<TH, TW>::SMEM;
+    cudaFuncSetAttribute(k_tile_sweep<TH, TW, TRIG_ACCURATE, true, NT, MB>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_tile_sweep<TH, TW, TRIG_ACCURATE, false, NT, ST, MB>,
+    cudaFuncSetAttribute(k_tile_sweep<TH, TW, TRIG_ACCURATE, false, NT, MB>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_tile_sweep<TH, TW, TRIG_FAST, true, NT, ST, MB>,
+    cudaFuncSetAttribute(k_tile_sweep<TH, TW, TRIG_FAST, true, NT, MB>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_tile_sweep<TH, TW, TRIG_FAST, false, NT, ST, MB>,
+    cudaFuncSetAttribute(k_tile_sweep<TH, TW, TRIG_FAST, false, NT, MB>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per, k_tile_sweep<TH, TW, TRIG_ACCURATE, true, NT, ST, MB>, NT, sm);
+        &per, k_tile_sweep<TH, TW, TRIG_ACCURATE, true, NT, MB>, NT, sm);
     return std::max(1, sms * std::max(1, per));
 }
 
-#define MPR_CFG_BLOCKS(id, th, tw, nt, st, mb) \
-    case id: blocks[id] = blocks_for<th, tw, nt, st, mb>(); break;
+#define MPR_CFG_BLOCKS(id, th, tw, nt, mb) \
+    case id: blocks[id] = blocks_for<th, tw, nt, mb>(); break;
 int tile_sweep_blocks(int cfg) {
     static int blocks[8] = {0};
     if (cfg < 0 || cfg >= tile_config_count()) return 0;
@@ -619,7 +817,7 @@ int tile_sweep_blocks(int cfg) {
     return blocks[cfg];
 }
 
-#define MPR_CFG_LISTS(id, th, tw, nt, st, mb) \
+#define MPR_CFG_LISTS(id, th, tw, nt, mb) \
     case id: k_tile_lists<th, tw><<<(ntiles * 32 + 127) / 128, 128, 0, st_>>>(tiles, ntiles, ents, mask, all_free, lists, cnts); break;
 cudaError_t launch_tile_lists(int cfg, TileDesc* tiles, int ntiles, const EntryDesc* ents,
                               const uint8_t* mask, int all_free, uint16_t* lists, TileCnt* cnts,
@@ -630,29 +828,62 @@ cudaError_t launch_tile_lists(int cfg, TileDesc* tiles, int ntiles, const EntryD
     return cudaGetLastError();
 }
 
-template <int TH, int TW, int NT, int ST, int MB>
+template <int TH, int TW, int NT, int MB>
 void sweep_for(const TileArgs& a, int trig, cudaStream_t st) {
-    constexpr int sm = Cfg<TH, TW, NT, ST>::SMEM;
-    const int nb = std::min(a.ntiles, tile_sweep_blocks(a.cfg));
+    constexpr int sm = Cfg<TH, TW>::SMEM;
+    // persistent: at most the resident blocks, and no more than the launch's items
+    const long long items = (long long)a.ntiles * a.nsweeps;
+    const int nb = (int)std::min<long long>(items, tile_sweep_blocks(a.cfg));
     const bool acc = a.acc != nullptr;
     if (trig == TRIG_FAST) {
-        if (acc) k_tile_sweep<TH, TW, TRIG_FAST, true, NT, ST, MB><<<nb, NT, sm, st>>>(a);
-        else k_tile_sweep<TH, TW, TRIG_FAST, false, NT, ST, MB><<<nb, NT, sm, st>>>(a);
+        if (acc) k_tile_sweep<TH, TW, TRIG_FAST, true, NT, MB><<<nb, NT, sm, st>>>(a);
+        else k_tile_sweep<TH, TW, TRIG_FAST, false, NT, MB><<<nb, NT, sm, st>>>(a);
     } else {
-        if (acc) k_tile_sweep<TH, TW, TRIG_ACCURATE, true, NT, ST, MB><<<nb, NT, sm, st>>>(a);
-        else k_tile_sweep<TH, TW, TRIG_ACCURATE, false, NT, ST, MB><<<nb, NT, sm, st>>>(a);
+        if (acc) k_tile_sweep<TH, TW, TRIG_ACCURATE, true, NT, MB><<<nb, NT, sm, st>>>(a);
+        else k_tile_sweep<TH, TW, TRIG_ACCURATE, false, NT, MB><<<nb, NT, sm, st>>>(a);
     }
 }
-#define MPR_CFG_SWEEP(id, th, tw, nt, st_, mb) \
-    case id: sweep_for<th, tw, nt, st_, mb>(a, trig, st); break;
+#define MPR_CFG_SWEEP(id, th, tw, nt, mb) \
+    case id: sweep_for<th, tw, nt, mb>(a, trig, st); break;
 cudaError_t launch_tile_sweep(const TileArgs& a, int trig, cudaStream_t st) {
-    if (a.ntiles == 0) return cudaSuccess;
+    if (a.ntiles == 0 || a.nsweeps <= 0) return cudaSuccess;
+    // items are counted in 32 bits, with room for the blocks' claims past the end
+    if ((long long)a.ntiles * a.nsweeps + 4LL * tile_sweep_blocks(a.cfg) >= (1LL << 32))
+        return cudaErrorInvalidValue;
     count_launches(1, st);
     switch (a.cfg) { MPR_TILE_CONFIGS(MPR_CFG_SWEEP) default: return cudaErrorInvalidValue; }
     return cudaGetLastError();
 }
 
-#define MPR_CFG_OUT(id, th, tw, nt, st_, mb) \
+cudaError_t launch_tile_order(const TileDesc* tiles, int ntiles, const EntryDesc* ents, int n_ent,
+                              int cfg, unsigned* hist, TileDesc* ord, cudaStream_t st) {
+    if (ntiles == 0) return cudaSuccess;
+    const int maxw = tile_geom(cfg).list;
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned) * 256 * (size_t)n_ent, st);
+    if (e != cudaSuccess) return e;
+    count_launches(3, st);
+    k_tile_hist<<<(ntiles + 255) / 256, 256, 0, st>>>(tiles, ntiles, maxw, hist);
+    k_tile_scan<<<(n_ent + 127) / 128, 128, 0, st>>>(hist, ents, n_ent);
+    k_tile_scatter<<<(ntiles + 255) / 256, 256, 0, st>>>(tiles, ntiles, maxw, hist, ord);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_sync(const TileDesc* tiles, int ntiles, Ctl* ctl, int n_ent, unsigned* tdone,
+                             cudaStream_t st) {
+    const int n = std::max(ntiles, n_ent);
+    if (n == 0) return cudaSuccess;
+    count_launches(1, st);
+    k_tile_sync<<<(n + 255) / 256, 256, 0, st>>>(tiles, ntiles, ctl, n_ent, tdone);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_live(const Ctl* ctl, int n_ent, int* live, cudaStream_t st) {
+    count_launches(1, st);
+    k_count_live<<<1, 256, 0, st>>>(ctl, n_ent, live);
+    return cudaGetLastError();
+}
+
+#define MPR_CFG_OUT(id, th, tw, nt, mb) \
     case id: k_tile_predict_out<th, tw><<<ntiles, 256, 0, st>>>( \
         tiles + tile0, cnts + tile0, lists + (long long)tile0 * g.list, acc + (long long)tile0 * g.acc, \
         ents, M, q, zmin, zmax, K, chain_tiles, zhat); break;

@@ -80,6 +80,10 @@ _SIGS = [
     ("mpr_get_info", _I, [_VP] + [ctypes.POINTER(_D)] * 6),
     ("mpr_time_sweeps", _I, [_VP, _I, _D, ctypes.POINTER(_D)]),
     ("mpr_kernel_launches", ctypes.c_uint64, []),
+    ("mpr_sweep_timing_start", None, []),
+    ("mpr_sweep_timing_read", None, [_I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_uint64),
+                                     ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    ("mpr_debug_wait_limit", None, [ctypes.c_uint64, _I]),
     ("mpr_release_memory", _I, []),
     ("mpr_sample_energy_static", _I, [_VP, _VP, _I, _I, _D, ctypes.POINTER(_D),
                                       ctypes.POINTER(ctypes.c_longlong), _VP]),
@@ -313,6 +317,24 @@ def mpr_sample_energy_static(z, mask, W: int, H: int, q: float = 0.5, stream=Non
 
 def mpr_kernel_launches() -> int:
     return int(lib().mpr_kernel_launches())
+
+
+def mpr_sweep_timing_start() -> None:
+    """Enables (and resets) the library's CUDA-event timing of every sweep-kernel launch."""
+    lib().mpr_sweep_timing_start()
+
+
+def mpr_sweep_timing_read(stop: bool = True) -> dict:
+    """The sweep-kernel timing record: total ms, launches, sweeps x sites, sweeps x gap sites."""
+    ms, n, ss, gu = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_double(), ctypes.c_double()
+    lib().mpr_sweep_timing_read(1 if stop else 0, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(ss),
+                                ctypes.byref(gu))
+    return dict(ms=ms.value, launches=int(n.value), site_sweeps=ss.value, gap_updates=gu.value)
+
+
+def mpr_debug_wait_limit(ns: int = 0, stall: bool = False) -> None:
+    """Test support: limit of the sweep kernel's waits (0 = default) and the expiring wait."""
+    lib().mpr_debug_wait_limit(int(ns), 1 if stall else 0)
 
 
 def mpr_release_memory():
