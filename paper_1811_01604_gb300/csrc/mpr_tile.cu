@@ -312,8 +312,8 @@ k_tile_sweep(const TileArgs A) {
     __shared__ __align__(8) uint64_t bar;
     __shared__ __align__(16) TileDesc dnext;
     __shared__ GridCache gc;
-    __shared__ int s_fail, s_flush, s_ke, s_kn, s_last;
-    __shared__ uint32_t s_ksig;
+    __shared__ int s_fail, s_flush, s_ke, s_kn, s_last, s_pub_t;
+    __shared__ uint32_t s_ksig, s_pub_sig;
     __shared__ unsigned s_w0, s_w1;
     __shared__ long long s_fx[NT];
     __shared__ unsigned s_nat[NT];
@@ -349,6 +349,16 @@ k_tile_sweep(const TileArgs A) {
         gc.cur_base = __ldcg(&cp->cur_base);
         gc.neg_inv_T = __ldcg(&cp->neg_inv_T);
     };
+    // thread 0, fixed window: publishes that the last item's tile has finished its sweep (its
+    // interior is in the other buffer and it no longer reads its source buffer).  Deferred
+    // until after the next copy has been issued, unless that copy must wait for a tile.
+    auto publish = [&]() {
+        if (s_pub_t >= 0) {
+            __threadfence();
+            st_release(A.tdone + s_pub_t, s_pub_sig);
+            s_pub_t = -1;
+        }
+    };
     // stages the next item to run into sp, or sets sp.t = -1 when there is none (all items
     // taken, every grid's relaxation ended, or an expired wait)
     auto issue = [&]() {
@@ -369,14 +379,19 @@ k_tile_sweep(const TileArgs A) {
             float half_qd = A.half_qd_fixed;
             bool ok = true;
             if (A.relax) {
-                // ready once the control step of sweep sig - 1 is published, or the grid's
-                // relaxation (or every grid's) has ended; the loads of one poll go out together
-                int stop = 0, live = 1;
+                // ready once the control step of sweep sig - 1 is published (every block polls
+                // the same word, so gently), or the grid's relaxation (or every grid's) has
+                // ended, which is looked at every 8th poll
+                int live = 1;
+                unsigned polls = 0;
                 ok = bounded_wait(A, [&] {
-                    const unsigned cs = ld_relaxed(&cp->sweep);
-                    stop = ld_relaxed(&cp->stop);
-                    live = ld_relaxed(A.live);
-                    return (int)(cs - sig) >= 0 || stop != 0 || live <= 0;
+                    if ((int)(ld_relaxed(&cp->sweep) - sig) >= 0) return true;
+                    if ((++polls & 7u) == 0u) {
+                        live = ld_relaxed(A.live);
+                        if (live <= 0 || ld_relaxed(&cp->stop) != 0) return true;
+                    }
+                    __nanosleep(64);
+                    return false;
                 });
                 fence_acq_rel();
                 if (ok && live <= 0) { sp.t = -1; return; }           // every grid has stopped
@@ -387,7 +402,7 @@ k_tile_sweep(const TileArgs A) {
                 // slot of sweep sig was emptied by the control step of sweep sig - kSlots
                 const int i = d.t - gc.tile0, ty = i / gc.tpr, tx = i - ty * gc.tpr;
                 const uint32_t slot_free = sig - (uint32_t)(kSlots - 1);
-                ok = bounded_wait(A, [&] {
+                auto ready = [&] {
                     unsigned v[9];
 #pragma unroll
                     for (int k = 0; k < 9; ++k) {
@@ -400,7 +415,15 @@ k_tile_sweep(const TileArgs A) {
 #pragma unroll
                     for (int k = 0; k < 9; ++k) r = r && (int)(v[k] - sig) >= 0;
                     return r;
-                });
+                };
+                if (!ready()) {
+                    publish();                  // this block's last tile may be one of the nine
+                    ok = bounded_wait(A, [&] {
+                        if (ready()) return true;
+                        __nanosleep(32);
+                        return false;
+                    });
+                }
                 fence_acq_rel();
             }
             if (!ok) { sp.t = -1; return; }
@@ -470,6 +493,7 @@ k_tile_sweep(const TileArgs A) {
         s_flush = 0;
         s_ke = -1;
         s_kn = 0;
+        s_pub_t = -1;
         gc.e = -1;
         s_w0 = atomicAdd(A.sched, 1u);
         s_w1 = atomicAdd(A.sched, 1u);
@@ -485,16 +509,20 @@ k_tile_sweep(const TileArgs A) {
         if (it > 0) {
             __syncthreads();                                      // B0: write-back and flushes issued
             if (threadIdx.x == 0) {
-                // the previous item is done: its tile's interior after sweep sp.sweep is in
-                // the other buffer, and the tile no longer reads its source buffer
-                __threadfence();
-                st_release(A.tdone + sp.t, sp.sweep + 1u);
+                // the previous item is done (a relaxation's items wait for control steps,
+                // not for tiles: their counters are set when the launch ends)
+                if (!A.relax) {
+                    s_pub_t = sp.t;
+                    s_pub_sig = sp.sweep + 1u;
+                }
                 if (s_flush) {
+                    publish();
                     tile_ticket(A, s_ke, s_ksig, s_kn);
                     s_ke = -1;
                     s_kn = 0;
                 }
                 issue();
+                publish();
             }
         }
         if (threadIdx.x == 0 && sp.t >= 0 && !mbar_wait_try(&bar, parity)) {
@@ -596,7 +624,6 @@ k_tile_sweep(const TileArgs A) {
                 }
             }
         }
-        fence_proxy_async_global();                       // the write-back before later copies of it
         if (s_flush) flush_partials(e, sweep);
     }
     // an error or the end of the relaxation can leave totals that were not handed in
@@ -625,6 +652,11 @@ k_tile_sweep(const TileArgs A) {
             cp->sweep_base = ld_relaxed(&cp->sweep);
             cp->cur_base = ld_relaxed(&cp->cur);
         }
+        if (A.relax)
+            for (int j = threadIdx.x; j < A.ntiles; j += NT) {
+                const TileDesc& d = A.desc[j];
+                A.tdone[d.t] = ld_relaxed(&A.ctl[d.entry].sweep);
+            }
         if (threadIdx.x == 0) {
             atomicExch(A.sched, 0u);
             atomicExch(A.sched + 1, 0u);
