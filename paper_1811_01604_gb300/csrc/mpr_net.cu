@@ -88,22 +88,6 @@ __global__ void k_input(const float* __restrict__ z, const uint8_t* __restrict__
     }
 }
 
-__global__ void k_pool(const bf16* __restrict__ in, int B, int H, int W, int C, bf16* __restrict__ out) {
-    const int Ho = H / 2, Wo = W / 2;
-    const long long n = (long long)B * Ho * Wo * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        long long q = i / C;
-        const int x = (int)(q % Wo); q /= Wo;
-        const int y = (int)(q % Ho);
-        const int b = (int)(q / Ho);
-        const bf16* s = in + (((long long)b * H + 2 * y) * W + 2 * x) * C + c;
-        const float v = __bfloat162float(s[0]) + __bfloat162float(s[C]) + __bfloat162float(s[(long long)W * C]) +
-                        __bfloat162float(s[(long long)W * C + C]);
-        out[i] = __float2bfloat16(0.25f * v);
-    }
-}
-
 // dIn (H x W) += dOut (H/2 x W/2) / 4 on each 2x2 block
 __global__ void k_pool_bwd(const float* __restrict__ dout, int B, int H, int W, int C, float* __restrict__ din) {
     const long long n = (long long)B * H * W * C;
@@ -146,18 +130,6 @@ __global__ void k_bias_grad(const bf16* __restrict__ g, long long P, int C, floa
     for (long long p = blockIdx.x * 8 + (threadIdx.x >> 5); p < P; p += (long long)gridDim.x * 8)
         s += __bfloat162float(g[p * C + c]);
     atomicAdd(db + c, s);
-}
-
-// W'[t][co][ci] = W[8 - t][ci][co]: weights of the transposed (data-gradient) convolution
-__global__ void k_flip(const bf16* __restrict__ w, int Cin, int Cout, bf16* __restrict__ wf) {
-    const long long n = 9LL * Cin * Cout;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int ci = (int)(i % Cin);
-        const long long r = i / Cin;
-        const int co = (int)(r % Cout);
-        const int t = (int)(r / Cout);
-        wf[i] = w[((long long)(8 - t) * Cin + ci) * Cout + co];
-    }
 }
 
 // 1x1 head: out[p][o] = sum_c act[p][c] wh[c][o] + bh[o], o in {0, 1}
@@ -343,11 +315,9 @@ struct mpr_net {
     float* m = nullptr;                // Adam moments
     float* v = nullptr;
     bf16* wb = nullptr;                // bf16 copy of the parameters (conv weights are read from it)
-    bf16* wflip = nullptr;             // flipped weights of one layer (backward, legacy kernel)
     bf16* wt = nullptr;                // K-major weights of the tensor-core kernels: forward
     bf16* wtb = nullptr;               //   and data-gradient, per layer at wt_off / wtb_off
     long long wt_off[14] = {0}, wtb_off[14] = {0};
-    bool legacy = false;               // MPR_NET_CONV=mma: all convolutions on mma.sync
     int* d_err = nullptr;              // set by a tensor-core kernel whose barrier wait expired
     int adam_t = 0;
     int stride = 1;                    // sites per frame pixel along each axis (1 or 2)
@@ -428,8 +398,7 @@ mpr_status ensure_ws(mpr_net* net, int B, int H, int W, bool train) {
         if (train) NCU(nalloc(net, &net->dpool[i], P * kCout[2 * i + 1]));
     }
     NCU(nalloc(net, &net->out2, P0 * 2));
-    if (!net->legacy)
-        for (int i = 0; i < 3; ++i) NCU(nalloc(net, &net->cat[i], (P0 >> (2 * i)) * kCatC[i]));
+    for (int i = 0; i < 3; ++i) NCU(nalloc(net, &net->cat[i], (P0 >> (2 * i)) * kCatC[i]));
     if (train) {
         NCU(nalloc(net, &net->dout2, P0 * 2));
         NCU(nalloc(net, &net->dup, P0 * 64));       // largest: level 0, 64 upsampled channels
@@ -445,7 +414,6 @@ mpr_status ensure_ws(mpr_net* net, int B, int H, int W, bool train) {
 
 // K-major copies of the current bf16 weights for the tensor-core kernels
 mpr_status refresh_wt(mpr_net* net) {
-    if (net->legacy) return MPR_OK;
     for (int l = 0; l < 14; ++l) {
         NCU(mprnet::tc_weights(net->wb + net->off_w[l], kCin[l], kCout[l], 0, net->wt + net->wt_off[l], net->st));
         NCU(mprnet::tc_weights(net->wb + net->off_w[l], kCin[l], kCout[l], 1, net->wtb + net->wtb_off[l], net->st));
@@ -454,15 +422,11 @@ mpr_status refresh_wt(mpr_net* net) {
     return MPR_OK;
 }
 
-// One convolution: tensor cores (TMA-fed, weights from the K-major copy) or the legacy
-// kernel.  On the tensor-core path the decoder inputs are the concatenation buffers, which
-// the layers producing their parts also write (A_l as is, the lower level upsampled).
+// One convolution on the tensor cores (TMA-fed, weights from the K-major copy).  The
+// decoder inputs are the concatenation buffers, which the layers producing their parts
+// also write (A_l as is, the lower level upsampled); 2 x 2 pooling is fused into the
+// epilogue of the layer it follows.
 mpr_status conv(mpr_net* net, ConvArgs& a, int l, bool dgrad) {
-    if (net->legacy) {
-        NCU(mprnet::conv3x3(a, net->st));
-        mpr::count_launches(1, net->st);
-        return MPR_OK;
-    }
     mprnet::TcConv c;
     std::memset(&c, 0, sizeof c);
     c.B = a.B; c.H = a.H; c.W = a.W;
@@ -555,11 +519,6 @@ mpr_status forward(mpr_net* net) {
         a.out_bf16 = net->act[l];
         const mpr_status cs = conv(net, a, l, false);
         if (cs != MPR_OK) return cs;
-        if (net->legacy && (l == 1 || l == 3 || l == 5)) {   // fused into the convolution otherwise
-            k_pool<<<grid1((long long)B * (Hl / 2) * (Wl / 2) * kCout[l]), 256, 0, st>>>(net->act[l], B, Hl, Wl,
-                                                                                     kCout[l], net->pool[l / 2]);
-            mpr::count_launches(1, st);
-        }
     }
     const long long P0 = (long long)B * H * W;
     k_head<<<grid1(P0), 256, 0, st>>>(net->act[13], P0, net->w + net->off_wh, net->w + net->off_bh, net->out2);
@@ -584,16 +543,11 @@ mpr_status backward(mpr_net* net) {
         NCU(mprnet::conv3x3_wgrad(layer_in(net, l), B, Hl, Wl, Cin, net->gb, Cout, net->g + net->off_w[l], st));
         mpr::count_launches(3, st);
         if (l == 0) break;                                    // no gradient w.r.t. the network input
-        if (net->legacy) {
-            k_flip<<<grid1(9LL * Cin * Cout), 256, 0, st>>>(net->wb + net->off_w[l], Cin, Cout, net->wflip);
-            mpr::count_launches(1, st);
-        }
         ConvArgs a;
         std::memset(&a, 0, sizeof a);
         a.in = ConvIn{net->gb, Cout, nullptr, 0, 0};
         a.B = B; a.H = Hl; a.W = Wl;
         a.Cin = Cout;
-        a.w = net->wflip;
         a.Cout = Cin;
         if (l == 2 || l == 4 || l == 6) {                      // input = pool(A)
             a.out_f32 = {net->dpool[l / 2 - 1], Cin, nullptr, 0, 0};
@@ -690,10 +644,6 @@ mpr_status mpr_net_create_strided(mpr_net** out, uint64_t seed, int stride, void
         net->wtb_off[l] = owtb;
         owtb += (long long)kCin[l] * 9 * mprnet::tc_layer_kt(kCout[l], kCin[l]);
     }
-    {
-        const char* env = std::getenv("MPR_NET_CONV");
-        net->legacy = env && std::string(env) == "mma";
-    }
     std::vector<float> h((size_t)off, 0.f);
     std::mt19937_64 rng(seed);
     for (int l = 0; l < 14; ++l) {                 // He initialisation (3 used input channels at l = 0)
@@ -713,7 +663,6 @@ mpr_status mpr_net_create_strided(mpr_net** out, uint64_t seed, int stride, void
               cudaMalloc((void**)&net->m, sizeof(float) * off) == cudaSuccess &&
               cudaMalloc((void**)&net->v, sizeof(float) * off) == cudaSuccess &&
               cudaMalloc((void**)&net->wb, sizeof(bf16) * off) == cudaSuccess &&
-              cudaMalloc((void**)&net->wflip, sizeof(bf16) * 9 * 256 * 256) == cudaSuccess &&
               cudaMalloc((void**)&net->d_zr, sizeof(double) * 2 * kMaxB) == cudaSuccess &&
               cudaMalloc((void**)&net->d_loss, sizeof(double)) == cudaSuccess &&
               cudaMalloc((void**)&net->d_cnt, sizeof(unsigned long long)) == cudaSuccess &&
@@ -752,7 +701,6 @@ void mpr_net_free(mpr_net* net) {
     cudaFree(net->m);
     cudaFree(net->v);
     cudaFree(net->wb);
-    cudaFree(net->wflip);
     cudaFree(net->d_zr);
     cudaFree(net->d_loss);
     cudaFree(net->d_cnt);
@@ -857,6 +805,42 @@ mpr_status mpr_net_forward(mpr_net* net, const float* z, const uint8_t* mask, co
     if (s != MPR_OK) return s;
     NCU(cudaMemcpyAsync(uv, net->out2, sizeof(float) * 2 * (size_t)B * Hf * Wf, cudaMemcpyDefault, net->st));
     return check_err(net);
+}
+
+// Test support: a copy of one of the network's internal tensors (layer-by-layer checks).
+mpr_status mpr_net_tensor(mpr_net* net, int kind, int index, void* out, long long count) {
+    if (!net || !out) return MPR_EINVAL;
+    const long long P0 = (long long)net->B * net->H * net->W;
+    const void* src = nullptr;
+    size_t elem = 0;
+    long long n = 0;
+    switch (kind) {
+        case MPR_NET_T_INPUT:
+            src = net->in0; elem = sizeof(bf16); n = P0 * kIn;
+            break;
+        case MPR_NET_T_ACT:
+            if (index < 0 || index >= 14) break;
+            src = net->act[index]; elem = sizeof(bf16); n = (P0 >> (2 * kLevel[index])) * kCout[index];
+            break;
+        case MPR_NET_T_POOL:
+            if (index < 0 || index >= 3) break;
+            src = net->pool[index]; elem = sizeof(bf16); n = (P0 >> (2 * (index + 1))) * kCout[2 * index + 1];
+            break;
+        case MPR_NET_T_DACT:
+            if (index < 0 || index >= 14 || !net->train) break;
+            src = net->dact[index]; elem = sizeof(float); n = (P0 >> (2 * kLevel[index])) * kCout[index];
+            break;
+        case MPR_NET_T_OUT:
+            src = net->out2; elem = sizeof(float); n = P0 * 2;
+            break;
+        default:
+            break;
+    }
+    if (!src || P0 == 0) return nfail(net, MPR_ESTATE, "no such tensor after the last call");
+    if (count != n) return nfail(net, MPR_EINVAL, "element count of the tensor differs");
+    NCU(cudaMemcpyAsync(out, src, (size_t)n * elem, cudaMemcpyDefault, net->st));
+    NCU(cudaStreamSynchronize(net->st));
+    return MPR_OK;
 }
 
 // Test support: the library's own convolution kernels on caller buffers.

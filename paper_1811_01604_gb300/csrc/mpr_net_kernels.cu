@@ -1,5 +1,5 @@
-// mpr_net_kernels.cu -- implicit-GEMM 3x3 convolutions on the tensor cores (mma.sync,
-// bf16 inputs, fp32 accumulation) for the warm-start network.
+// mpr_net_kernels.cu -- the weight gradient of the warm-start network's 3x3 convolutions
+// (a reduction over pixels on mma.sync, bf16 inputs, fp32 accumulation).
 #include "mpr_net_kernels.cuh"
 
 namespace mprnet {
@@ -56,138 +56,6 @@ __device__ __forceinline__ const bf16* in_ptr(const ConvIn& in, int b, int y, in
         return in.src1 + (((long long)b * Hh + (y >> 1)) * Wh + (x >> 1)) * in.C1 + c1;
     }
     return in.src1 + (((long long)b * H + y) * W + x) * in.C1 + c1;
-}
-
-constexpr int BM = 128;               // pixels per block
-constexpr int BK = 32;                // reduction chunk (one tap, 32 channels)
-constexpr int APAD = BK + 8;          // smem row stride of the A tile (bf16), breaks bank conflicts
-
-// Implicit-GEMM convolution.  8 warps: 4 along M (32 pixels each) x 2 along N (BN/2 each).
-template <int BN>
-__global__ void __launch_bounds__(256) k_conv3x3(const ConvArgs a) {
-    constexpr int BPAD = BN + 8;
-    constexpr int WN = BN / 2;        // warp tile along N
-    constexpr int NT = WN / 8;        // n8 tiles per warp
-    __shared__ __align__(16) bf16 As[2][BM][APAD];
-    __shared__ __align__(16) bf16 Bs[2][BK][BPAD];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp & 3, wn = warp >> 2;
-    const long long P = (long long)a.B * a.H * a.W;
-    const long long p0 = (long long)blockIdx.x * BM;
-    const int n0 = blockIdx.y * BN;
-    const int HW = a.H * a.W;
-
-    // each thread loads 2 A chunks (pixel row, 16-byte piece) per stage
-    int ab[2], ay[2], ax[2], arow[2], apiece[2];
-    bool aval[2];
-    for (int i = 0; i < 2; ++i) {
-        const int idx = tid + i * 256;                  // 0..511: 128 rows x 4 pieces
-        arow[i] = idx >> 2;
-        apiece[i] = idx & 3;
-        const long long p = p0 + arow[i];
-        aval[i] = p < P;
-        const long long pp = aval[i] ? p : 0;
-        ab[i] = (int)(pp / HW);
-        const int r = (int)(pp - (long long)ab[i] * HW);
-        ay[i] = r / a.W;
-        ax[i] = r - ay[i] * a.W;
-    }
-    const int kchunks = 9 * (a.Cin / BK);
-    auto load = [&](int kc, int s) {
-        const int tap = kc / (a.Cin / BK);
-        const int c0 = (kc - tap * (a.Cin / BK)) * BK;
-        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-        for (int i = 0; i < 2; ++i) {
-            int bytes = 0;
-            const bf16* src = in_ptr(a.in, ab[i], ay[i] + dy, ax[i] + dx, a.H, a.W, c0 + apiece[i] * 8, &bytes);
-            if (!aval[i]) bytes = 0;
-            cp16(&As[s][arow[i]][apiece[i] * 8], src, bytes);
-        }
-        // B tile: BK rows of BN columns
-        constexpr int BCH = BK * BN / 8;                 // 16-byte chunks
-        for (int idx = tid; idx < BCH; idx += 256) {
-            const int r = idx / (BN / 8), c8 = idx - r * (BN / 8);
-            const int k = tap * a.Cin + c0 + r;
-            const int n = n0 + c8 * 8;
-            const bool ok = n < a.Cout;
-            cp16(&Bs[s][r][c8 * 8], a.w + (long long)k * a.Cout + (ok ? n : 0), ok ? 16 : 0);
-        }
-    };
-
-    float acc[2][NT][4];
-    for (int i = 0; i < 2; ++i)
-        for (int j = 0; j < NT; ++j)
-            for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
-
-    load(0, 0);
-    cp_commit();
-    for (int kc = 0; kc < kchunks; ++kc) {
-        const int s = kc & 1;
-        if (kc + 1 < kchunks) load(kc + 1, s ^ 1);
-        cp_commit();
-        cp_wait<1>();
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            uint32_t af[2][4];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int row = wm * 32 + i * 16 + (lane & 15);
-                const int col = kk + (lane >> 4) * 8;
-                ldsm_x4(af[i][0], af[i][1], af[i][2], af[i][3], &As[s][row][col]);
-            }
-#pragma unroll
-            for (int j = 0; j < NT; j += 2) {
-                // two n8 tiles per x4.trans: lanes 0-7 k rows 0-7, 8-15 k rows 8-15 of tile j;
-                // 16-23 / 24-31 the same rows of tile j + 1
-                const int krow = kk + (lane & 7) + ((lane >> 3) & 1) * 8;
-                const int ncol = wn * WN + j * 8 + (lane >> 4) * 8;
-                uint32_t b0, b1, b2, b3;
-                if (j + 1 < NT) {
-                    ldsm_x4_t(b0, b1, b2, b3, &Bs[s][krow][ncol]);
-                } else {
-                    ldsm_x2_t(b0, b1, &Bs[s][kk + (lane & 7) + ((lane >> 3) & 1) * 8][wn * WN + j * 8]);
-                    b2 = b3 = 0u;
-                }
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    mma16816(acc[i][j], af[i][0], af[i][1], af[i][2], af[i][3], b0, b1);
-                    if (j + 1 < NT) mma16816(acc[i][j + 1], af[i][0], af[i][1], af[i][2], af[i][3], b2, b3);
-                }
-            }
-        }
-        __syncthreads();
-    }
-    cp_wait<0>();
-
-    // epilogue: thread holds rows g, g + 8 and columns 2t, 2t + 1 of each m16n8 tile
-    const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const long long p = p0 + wm * 32 + i * 16 + h * 8 + g;
-            if (p >= P) continue;
-#pragma unroll
-            for (int j = 0; j < NT; ++j) {
-                const int n = n0 + wn * WN + j * 8 + 2 * t;
-                if (n >= a.Cout) continue;
-                float v0 = acc[i][j][2 * h], v1 = acc[i][j][2 * h + 1];
-                if (a.out_bf16) {
-                    if (a.bias) { v0 += a.bias[n]; v1 += a.bias[n + 1]; }
-                    if (a.relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
-                    *reinterpret_cast<__nv_bfloat162*>(a.out_bf16 + p * a.Cout + n) = __floats2bfloat162_rn(v0, v1);
-                } else {
-                    const ConvOutF32& o = a.out_f32;
-                    float* dst;
-                    if (n < o.C0) dst = o.dst0 + p * o.C0 + n;
-                    else dst = o.dst1 + p * o.C1 + (n - o.C0);
-                    if (o.accumulate) { v0 += dst[0]; v1 += dst[1]; }
-                    dst[0] = v0;
-                    dst[1] = v1;
-                }
-            }
-        }
 }
 
 // Weight gradient: block tile 64 (k = tap * Cin + ci) x 64 (co), reduction over a chunk of
@@ -291,18 +159,6 @@ __global__ void __launch_bounds__(256) k_conv3x3_wgrad(const ConvIn in, int B, i
 }
 
 }  // namespace
-
-cudaError_t conv3x3(const ConvArgs& a, cudaStream_t st) {
-    const long long P = (long long)a.B * a.H * a.W;
-    const dim3 grid((unsigned)((P + BM - 1) / BM), (unsigned)((a.Cout + 63) / 64));
-    if (a.Cout % 64 == 0) {
-        k_conv3x3<64><<<grid, 256, 0, st>>>(a);
-    } else {
-        const dim3 g2((unsigned)((P + BM - 1) / BM), (unsigned)((a.Cout + 31) / 32));
-        k_conv3x3<32><<<g2, 256, 0, st>>>(a);
-    }
-    return cudaGetLastError();
-}
 
 cudaError_t conv3x3_wgrad(const ConvIn& in, int B, int H, int W, int Cin, const bf16* g, int Cout,
                           float* dW, cudaStream_t st) {

@@ -2,7 +2,9 @@
 //
 // Activations are NHWC bf16, weights [tap = 3 ky + kx][C_in][C_out] bf16 (C_out contiguous),
 // gradients fp32.  Every 3x3 convolution (stride 1, zero padding 1) is an implicit GEMM
-// over M = pixels, N = output channels, K = 9 C_in, computed with mma.sync m16n8k16
+// over M = pixels, N = output channels, K = 9 C_in.  Forward and data-gradient convolutions
+// run on the 5th-generation tensor cores (tcgen05, TMA-fed; conv3x3_tma); the weight
+// gradient (training only) is a reduction over pixels computed with mma.sync m16n8k16
 // (bf16 x bf16 -> fp32) on fragments loaded by ldmatrix from cp.async-filled shared memory.
 #pragma once
 
@@ -46,8 +48,6 @@ struct ConvArgs {
     bf16* out_bf16;              // forward output [B][H][W][Cout]
     ConvOutF32 out_f32;          // backward output (used when out_bf16 is null)
 };
-
-cudaError_t conv3x3(const ConvArgs& a, cudaStream_t st);
 
 // dW[tap][ci][co] += sum_p in(p + tap)[ci] * g[p][co] over all pixels (in: ConvIn with the
 // forward layer's input, g: bf16 [B][H][W][Cout]).  dW fp32, accumulated with atomics.
