@@ -94,6 +94,22 @@ mpr_status mpr_net_forward(mpr_net* net, const float* z, const uint8_t* mask, co
    mpr_fill.  EINVAL for NULL arguments. */
 mpr_status mpr_warmstart_init(mpr_ctx* ctx, mpr_net* net);
 
+/* Test support (layer-by-layer checks): copies one internal tensor of the network, as the
+   last mpr_net_forward / mpr_net_loss_grad call left it, to out (host or device), count
+   elements; returns after the copy.  kind, index and layout (frame H x W = the call's grid
+   divided by the stride; level l of a layer: H >> l x W >> l):
+     MPR_NET_T_INPUT  the input, bf16 [B][H][W][32] (index ignored)
+     MPR_NET_T_ACT    output of convolution index (0..13, ReLU applied), bf16 [B][Hl][Wl][C_out]
+     MPR_NET_T_POOL   2 x 2 average of the output of convolution 2 index + 1 (index 0..2),
+                      bf16 [B][H >> (index + 1)][W >> (index + 1)][C_out of that convolution]
+     MPR_NET_T_DACT   loss gradient w.r.t. the output of convolution index, before the ReLU
+                      gate, fp32 [B][Hl][Wl][C_out] (after mpr_net_loss_grad only)
+     MPR_NET_T_OUT    head output (u, v), fp32 [B][H][W][2] (index ignored)
+   MPR_EINVAL if count is not the tensor's element count, MPR_ESTATE if the tensor does not
+   exist after the last call.  No counterpart in the paper (the network is this library's). */
+enum { MPR_NET_T_INPUT = 0, MPR_NET_T_ACT = 1, MPR_NET_T_POOL = 2, MPR_NET_T_DACT = 3, MPR_NET_T_OUT = 4 };
+mpr_status mpr_net_tensor(mpr_net* net, int kind, int index, void* out, long long count);
+
 /* Test support: one 3x3 convolution (zero padding 1) of the network on caller
    device buffers.  in: bf16 [B][H][W][Cin], w: bf16 [9][Cin][Cout], bias: fp32
    [Cout] or NULL, out: bf16 [B][H][W][Cout] = relu?(conv(in) + bias).  Cin, Cout

@@ -12,16 +12,9 @@ Precisions:
     scipy's correlate2d in the CPU tests);
   * ``bf16_storage=True``: the same arithmetic in float64, with values rounded to bf16
     (round to nearest even) where the library stores them in bf16: network input, conv
-    weights, layer outputs, pooled maps and the ReLU-gated gradients.  This is the
-    reference the GPU kernels (fp32 accumulation) are compared against.
-  * ``acc32=True`` (with bf16 storage): the convolution sums accumulate in float32 instead,
-    taps in order or (``rev=True``) in reverse order, and (``chop=True``) with the low
-    mantissa bits of every sum cleared, which models the truncating adders of the tensor
-    cores (with bf16 inputs the products are exact and a float32 sum is often exact too,
-    so the first two may flip nothing where the GPU does).  The largest distance between
-    these bf16 references and the float64-accumulated one measures how strongly one-unit
-    rounding flips of stored bf16 values propagate through the network, which sets the GPU
-    tolerance.
+    weights, layer outputs, pooled maps and the ReLU-gated gradients.
+The GPU tests apply the building blocks below (conv3x3, conv3x3_grad, pool, upsample and
+their adjoints, circ_loss) to the kernels' own inputs of each step, layer by layer.
 
 Arrays are NHWC: x[b, y, x, c].  Conv weights w[t, ci, co] with tap t = 3 dy + dx,
 (dy, dx) in {0, 1, 2}^2 addressing input pixel (y + dy - 1, x + dx - 1), zero padding.
@@ -100,52 +93,34 @@ def pack(dWs, dbs, dwh, dbh):
 
 
 # ------------------------------------------------------------------ building blocks
-def _chop(a, bits=5):
-    """float32 values with their `bits` lowest mantissa bits cleared (toward zero): a
-    deviation of up to 2^(bits - 24) relative, the order by which a tensor core's long sum
-    of products (aligned and truncated inside the unit; up to 9 x 384 products here) can
-    differ from the exact one.  With 5 bits the flips this causes cascade through the
-    decoder as on the GPU (measured: the first one-unit flips in the deepest decoder layer,
-    then 3-4e-3 relative at the output, the same as this model gives)."""
-    a = np.ascontiguousarray(a, np.float32)
-    return (a.view(np.int32) & np.int32(~((1 << bits) - 1))).view(np.float32)
-
-
-def conv3x3(x, w, b=None, acc=np.float64, rev=False, chop=False):
+def conv3x3(x, w, b=None):
     """out[b, y, x, co] = sum over taps and ci of x[b, y + dy - 1, x + dx - 1, ci] w[3 dy + dx, ci, co]
-    (+ b[co]); pixels outside the image are zero.  acc: accumulation dtype; rev: add the
-    taps in reverse order; chop: clear the low mantissa bits of the float32 sum (the last
-    two change only the rounding of a float32 accumulation)."""
+    (+ b[co]); pixels outside the image are zero.  Float64."""
     B, H, W, _ = x.shape
-    xp = np.pad(x, ((0, 0), (1, 1), (1, 1), (0, 0))).astype(acc)
-    wa = w.astype(acc)
-    out = np.zeros((B, H, W, w.shape[2]), acc)
-    for t in (range(8, -1, -1) if rev else range(9)):
+    xp = np.pad(x, ((0, 0), (1, 1), (1, 1), (0, 0))).astype(np.float64)
+    wa = w.astype(np.float64)
+    out = np.zeros((B, H, W, w.shape[2]))
+    for t in range(9):
         dy, dx = divmod(t, 3)
         out += xp[:, dy:dy + H, dx:dx + W, :] @ wa[t]
-    if chop:
-        out = _chop(out).astype(acc)
     if b is not None:
-        out += b.astype(acc)
-    return out.astype(np.float64)
+        out += b.astype(np.float64)
+    return out
 
 
-def conv3x3_grad(x, w, g, acc=np.float64, rev=False, chop=False):
-    """Gradients of sum(g * conv3x3(x, w)) w.r.t. x and w (the adjoint, tap by tap; rev:
-    taps in reverse order; chop: low mantissa bits of the float32 sums cleared)."""
+def conv3x3_grad(x, w, g):
+    """Gradients of sum(g * conv3x3(x, w)) w.r.t. x and w (the adjoint, tap by tap).  Float64."""
     B, H, W, Cin = x.shape
-    xp = np.pad(x, ((0, 0), (1, 1), (1, 1), (0, 0))).astype(acc)
+    xp = np.pad(x, ((0, 0), (1, 1), (1, 1), (0, 0))).astype(np.float64)
     dxp = np.zeros_like(xp)
-    dw = np.zeros(w.shape, acc)
-    wa, ga = w.astype(acc), g.astype(acc)
+    dw = np.zeros(w.shape)
+    wa, ga = w.astype(np.float64), g.astype(np.float64)
     g2 = ga.reshape(-1, g.shape[3])
-    for t in (range(8, -1, -1) if rev else range(9)):
+    for t in range(9):
         dy, dx = divmod(t, 3)
         dw[t] = xp[:, dy:dy + H, dx:dx + W, :].reshape(-1, Cin).T @ g2
         dxp[:, dy:dy + H, dx:dx + W, :] += ga @ wa[t].T
-    if chop:
-        dxp, dw = _chop(dxp), _chop(dw)
-    return dxp[:, 1:H + 1, 1:W + 1, :].astype(np.float64), dw.astype(np.float64)
+    return dxp[:, 1:H + 1, 1:W + 1, :], dw
 
 
 def pool(x):
@@ -221,10 +196,9 @@ def _layer_input(l, x0, acts, pools):
     return acts[l - 1]
 
 
-def forward(theta, z, mask, zmin, zmax, bf16_storage=False, acc32=False, stride=1, rev=False, chop=False):
+def forward(theta, z, mask, zmin, zmax, bf16_storage=False, stride=1):
     """Network output (u, v) per frame pixel (per site at stride 1), and the cache for backward."""
     r = bf16 if bf16_storage else (lambda a: a)
-    acc = np.float32 if acc32 else np.float64
     Ws, bs, wh, bh = unpack(theta)
     Wr = [r(w) for w in Ws]
     x0 = r(net_input(z, mask, zmin, zmax, stride))
@@ -232,19 +206,17 @@ def forward(theta, z, mask, zmin, zmax, bf16_storage=False, acc32=False, stride=
     for l in range(14):
         xin = _layer_input(l, x0, acts, pools)
         ins[l] = xin
-        acts[l] = r(np.maximum(conv3x3(xin, Wr[l], bs[l], acc, rev, chop), 0.0))
+        acts[l] = r(np.maximum(conv3x3(xin, Wr[l], bs[l]), 0.0))
         if l in (1, 3, 5):
             pools[l // 2] = r(pool(acts[l]))
     uv = acts[13] @ wh + bh
     return uv, dict(Wr=Wr, wh=wh, acts=acts, ins=ins)
 
 
-def loss_and_grad(theta, z, mask, phi_t, zmin, zmax, bf16_storage=False, acc32=False, stride=1, rev=False,
-                  chop=False):
+def loss_and_grad(theta, z, mask, phi_t, zmin, zmax, bf16_storage=False, stride=1):
     """Loss and gradient (same layout as theta) for one batch."""
     r = bf16 if bf16_storage else (lambda a: a)
-    acc = np.float32 if acc32 else np.float64
-    uv, cache = forward(theta, z, mask, zmin, zmax, bf16_storage, acc32, stride, rev, chop)
+    uv, cache = forward(theta, z, mask, zmin, zmax, bf16_storage, stride)
     loss, duv = circ_loss(uv, phi_t, mask, stride)
     acts, ins, Wr, wh = cache["acts"], cache["ins"], cache["Wr"], cache["wh"]
     dact = [None] * 14
@@ -259,7 +231,7 @@ def loss_and_grad(theta, z, mask, phi_t, zmin, zmax, bf16_storage=False, acc32=F
     for l in range(13, -1, -1):
         gl = r(np.where(acts[l] > 0, dact[l], 0.0))
         dbs[l] = gl.reshape(-1, COUT[l]).sum(axis=0)
-        dx, dWs[l] = conv3x3_grad(ins[l], Wr[l], gl, acc, rev, chop)
+        dx, dWs[l] = conv3x3_grad(ins[l], Wr[l], gl)
         if l == 0:
             continue
         if l in (2, 4, 6):

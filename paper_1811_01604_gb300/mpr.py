@@ -21,6 +21,7 @@ MPR_OR_CONSERVING, MPR_OR_LITERAL, MPR_OR_NONE = 0, 1, 2
 MPR_TRIG_ACCURATE, MPR_TRIG_FAST = 0, 1
 MPR_EXEC_AUTO, MPR_EXEC_LIST, MPR_EXEC_TILE = 0, 1, 2
 MPR_PREC_F32, MPR_PREC_F64 = 0, 1
+MPR_NET_T_INPUT, MPR_NET_T_ACT, MPR_NET_T_POOL, MPR_NET_T_DACT, MPR_NET_T_OUT = 0, 1, 2, 3, 4
 
 
 class MprError(RuntimeError):
@@ -94,6 +95,7 @@ _SIGS = [
     ("mpr_net_create", _I, [ctypes.POINTER(_VP), ctypes.c_uint64, _VP]),
     ("mpr_net_create_strided", _I, [ctypes.POINTER(_VP), ctypes.c_uint64, ctypes.c_int, _VP]),
     ("mpr_net_stride", ctypes.c_int, [_VP]),
+    ("mpr_net_tensor", _I, [_VP, _I, _I, _VP, ctypes.c_longlong]),
     ("mpr_net_free", None, [_VP]),
     ("mpr_net_last_error", ctypes.c_char_p, [_VP]),
     ("mpr_net_num_params", ctypes.c_longlong, [_VP]),
@@ -378,6 +380,13 @@ def mpr_net_create(seed: int = 0, stream=None, stride: int = 1):
 
 def mpr_net_stride(net) -> int:
     return int(lib().mpr_net_stride(net))
+
+
+def mpr_net_tensor(net, kind: int, index: int, out) -> None:
+    """Copies an internal tensor of the network (MPR_NET_T_*) into out (numpy array or tensor
+    with exactly the tensor's element count; bf16 tensors as uint16 / int16 bit patterns)."""
+    n = int(out.numel()) if hasattr(out, "numel") else int(out.size)
+    _ncheck(net, lib().mpr_net_tensor(net, int(kind), int(index), _ptr(out), n))
 
 
 def mpr_net_free(net):

@@ -1,17 +1,16 @@
 """Warm-start network on the GPU against the FP64 oracle (oracle/net_oracle.py): single
-convolutions (forward, data and weight gradients), the whole network's output, loss and
-gradient, the Adam step, training progress and the warm-start write into a context.
+convolutions (forward, data and weight gradients), every layer of the whole network's
+forward and backward pass, the Adam step, training progress and the warm-start write into
+a context.
 
 Tolerances.  The kernels multiply bf16 values exactly and accumulate in fp32; the oracle
-uses the same bf16 values and accumulates in fp64, rounding to bf16 where the kernels
-store bf16.  A stored bf16 value can therefore differ by one bf16 unit (at most 2^-7 of
-its magnitude) where the fp32 sum lies within its rounding error of a bf16 rounding
-boundary; everything else differs by fp32 accumulation error (about 1e-6 relative).  In
-a single convolution that bounds the error directly.  Through the whole network such
-flips cascade (deep layers end up with a large share of values one unit apart), so the
-whole-network tolerance is measured, not assumed: the oracle is re-run with fp32
-accumulation, and the GPU must be within 4x that run's distance to the fp64-accumulated
-reference (plus a small floor).
+uses the same bf16 values and accumulates in fp64.  A value the kernels store in bf16 can
+therefore differ from the exact one by half a bf16 unit (round to nearest) plus the fp32
+accumulation error, and an fp32 value by the accumulation error alone.  The whole network
+is checked step by step: each layer's output, pooled map, gradient and weight gradient is
+compared element by element with the oracle applied to the kernels' own inputs of that step
+(read back with mpr_net_tensor), so rounding differences never accumulate across layers and
+every element is held to the single-step bound.
 """
 import math
 
@@ -114,10 +113,78 @@ def _blocks():
     return out
 
 
+# Element-wise check of one tensor.  got: the kernels' values; exact: the value the oracle
+# computes in FP64 from the kernels' own inputs of that step; absum: the sum of the absolute
+# values of the terms behind each element.  A kernel value may differ from the exact one by
+# its FP32 accumulation error (at most REL_ACC of absum: products of bf16 values are exact in
+# FP32, and the sums of a few thousand terms carry a relative rounding error far below 2^-16)
+# plus, for values stored in bf16, half a bf16 unit of the larger of the two (round to
+# nearest).  Returns the number of elements outside that bound.
+REL_ACC = 2.0 ** -16
+
+
+def _half_ulp_bf16(a):
+    e = np.floor(np.log2(np.maximum(np.abs(a), 1e-300)))
+    return np.where(a == 0, 0.0, 2.0 ** (e - 8))
+
+
+def _outside(got, exact, absum, bf16_out):
+    got = np.asarray(got, np.float64)
+    allowed = REL_ACC * absum + 1e-30
+    if bf16_out:
+        allowed = allowed + _half_ulp_bf16(np.maximum(np.abs(got), np.abs(exact)))
+    return int((np.abs(got - exact) > allowed).sum())
+
+
+def _loss_grad_terms(uv, phi, mask, S):
+    """Magnitudes of the two terms of dL/du and dL/dv (circ_loss), |dot u| / n^3 + |Tc| / n
+    and |dot v| / n^3 + |Ts| / n over the gap count: the FP32 kernel forms their
+    difference, so its rounding error scales with them, not with the (cancelling) result."""
+    B, H, W = mask.shape
+    gap = (mask == 0).astype(np.float64)
+    c = np.cos(0.5 * phi.astype(np.float64)) * gap
+    sn = np.sin(0.5 * phi.astype(np.float64)) * gap
+    blk = lambda a: a.reshape(B, H // S, S, W // S, S).sum(axis=(2, 4))
+    c, sn = blk(c), blk(sn)
+    u, v = uv[..., 0], uv[..., 1]
+    n = np.sqrt(u * u + v * v + no.EPS_NORM)
+    dot = np.abs(u * c + v * sn)
+    ng = max(1.0, gap.sum())
+    return np.stack([(dot * np.abs(u) / n ** 3 + np.abs(c) / n) / ng,
+                     (dot * np.abs(v) / n ** 3 + np.abs(sn) / n) / ng], axis=-1)
+
+
+def _gpu_tensors(net, B, Hf, Wf):
+    """The network's internal tensors after mpr_net_loss_grad, as float64 arrays."""
+    def bf(kind, i, shape):
+        t = np.zeros(shape, np.uint16)
+        mpr.mpr_net_tensor(net, kind, i, t)
+        return no.from_bf16_bits(t)
+
+    def f32(kind, i, shape):
+        t = np.zeros(shape, np.float32)
+        mpr.mpr_net_tensor(net, kind, i, t)
+        return t.astype(np.float64)
+
+    lv = lambda l: (B, Hf >> no.LEVEL[l], Wf >> no.LEVEL[l], no.COUT[l])
+    x0 = bf(mpr.MPR_NET_T_INPUT, 0, (B, Hf, Wf, no.N_IN))
+    acts = [bf(mpr.MPR_NET_T_ACT, l, lv(l)) for l in range(14)]
+    pools = [bf(mpr.MPR_NET_T_POOL, i, (B, Hf >> (i + 1), Wf >> (i + 1), no.COUT[2 * i + 1])) for i in range(3)]
+    dacts = [f32(mpr.MPR_NET_T_DACT, l, lv(l)) for l in range(14)]
+    uv = f32(mpr.MPR_NET_T_OUT, 0, (B, Hf, Wf, 2))
+    return x0, acts, pools, dacts, uv
+
+
 @pytest.mark.parametrize("B,H,W,S", [(2, 16, 24, 1), (1, 32, 32, 1), (2, 32, 48, 2), (1, 64, 32, 2)])
-def test_network_output_loss_and_gradient_match_oracle(B, H, W, S):
+def test_network_layer_by_layer_matches_oracle(B, H, W, S):
+    # Every step of the forward and backward pass is checked element by element against the
+    # FP64 oracle applied to the kernels' own inputs of that step (their stored bf16
+    # activations, pooled maps and FP32 gradients), so one step's rounding never becomes the
+    # next step's reference: each tensor is held to the bound of a single step (_outside)
+    # and no element may fall outside it.
     z, m, phi, zmin, zmax = _batch(B * H + W, B, H, W)
     th = no.init_params(11).astype(np.float32)
+    Hf, Wf = H // S, W // S
     net = mpr.mpr_net_create(0, stride=S)
     try:
         assert mpr.mpr_net_stride(net) == S
@@ -126,40 +193,87 @@ def test_network_output_loss_and_gradient_match_oracle(B, H, W, S):
         back = np.zeros_like(th)
         mpr.mpr_net_get_params(net, back)
         assert np.array_equal(back, th)
-        uv = torch.zeros((B, H // S, W // S, 2), dtype=torch.float32, device="cuda")
-        mpr.mpr_net_forward(net, _dev(z), _dev(m), zmin, zmax, B, H, W, uv)
         mpr.mpr_net_zero_grads(net)
         loss = mpr.mpr_net_loss_grad(net, _dev(z), _dev(m), _dev(phi), zmin, zmax, B, H, W)
         g = np.zeros_like(th)
         mpr.mpr_net_get_grads(net, g)
+        x0, acts, pools, dacts, uv = _gpu_tensors(net, B, Hf, Wf)
     finally:
         mpr.mpr_net_free(net)
-    th64 = th.astype(np.float64)
-    ruv, _ = no.forward(th64, z, m, zmin, zmax, bf16_storage=True, stride=S)
-    rloss, rg = no.loss_and_grad(th64, z, m, phi, zmin, zmax, bf16_storage=True, stride=S)
-    # the same bf16 reference accumulated in fp32: its distance to rg is the sensitivity
-    # of this network's gradient to one-unit bf16 rounding flips
-    # ... in two tap orders and with truncated sums (the tensor cores' adders truncate, so
-    # flips land elsewhere); the largest distance is the sensitivity
-    runs = ((False, False), (True, False), (False, True))
-    euvs = [no.forward(th64, z, m, zmin, zmax, bf16_storage=True, acc32=True, stride=S, rev=rv, chop=ch)[0]
-            for rv, ch in runs]
-    egs = [no.loss_and_grad(th64, z, m, phi, zmin, zmax, bf16_storage=True, acc32=True, stride=S, rev=rv,
-                            chop=ch)[1] for rv, ch in runs]
-    guv = uv.cpu().numpy().astype(np.float64)
-    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
-    assert rel(guv, ruv) <= 4 * max(rel(e, ruv) for e in euvs) + 1e-3
-    assert loss == pytest.approx(rloss, rel=2e-3)
-    for name, a, b in _blocks():
-        ref, got = rg[a:b], g[a:b].astype(np.float64)
-        nr = np.linalg.norm(ref)
-        if nr == 0:
-            assert np.linalg.norm(got) <= 1e-6
+    Ws, bs, wh, bh = no.unpack(th.astype(np.float64))
+    Wr = [no.bf16(w) for w in Ws]
+    bad = {}
+
+    # input encoding: cos, sin of the Eq. 1 half angle and the sample indicator, block means
+    # at stride S, in bf16 (the kernel evaluates them in FP32: slack 1e-6 of the value)
+    ref = no.net_input(z, m, zmin, zmax, S)
+    bad["input"] = _outside(x0, ref, 1e-6 / REL_ACC * np.abs(ref) + 1e-6 / REL_ACC, True)
+
+    def layer_in(l):
+        if l == 0:
+            return x0
+        if l in (2, 4, 6):
+            return pools[l // 2 - 1]
+        if l in (8, 10, 12):
+            skip = {8: 5, 10: 3, 12: 1}[l]
+            return np.concatenate([acts[skip], no.upsample(acts[l - 1])], axis=3)
+        return acts[l - 1]
+
+    # forward: each convolution (+ bias, ReLU) and each pooled map from the stored inputs
+    for l in range(14):
+        xin = layer_in(l)
+        exact = np.maximum(no.conv3x3(xin, Wr[l], bs[l]), 0.0)
+        absum = no.conv3x3(np.abs(xin), np.abs(Wr[l]), np.abs(bs[l]))
+        bad[f"act{l}"] = _outside(acts[l], exact, absum, True)
+    for i in range(3):
+        a = acts[2 * i + 1]
+        bad[f"pool{i}"] = _outside(pools[i], no.pool(a), no.pool(np.abs(a)), True)
+    # head (FP32) and loss
+    bad["head"] = _outside(uv, acts[13] @ wh + bh, np.abs(acts[13]) @ np.abs(wh) + np.abs(bh), False)
+    rloss, duv = no.circ_loss(uv, phi, m, S)
+    assert loss == pytest.approx(rloss, rel=1e-5, abs=1e-9)
+
+    # backward: the head's gradients and the gradient w.r.t. the last activation; the loss
+    # gradient is a difference of two terms in FP32 (relative rounding 1e-5 of their size,
+    # with the FP32 sine and cosine of the targets)
+    conv, owh, obh, _ = no.layout()
+    dterm = 1e-5 / REL_ACC * _loss_grad_terms(uv, phi, m, S)
+    bad["dact13"] = _outside(dacts[13], duv @ wh.T, dterm @ np.abs(wh.T), False)
+    bad["dWh"] = _outside(g[owh:obh].reshape(no.HEAD_C, 2),
+                          acts[13].reshape(-1, no.HEAD_C).T @ duv.reshape(-1, 2),
+                          np.abs(acts[13]).reshape(-1, no.HEAD_C).T @ dterm.reshape(-1, 2), False)
+    bad["dbh"] = _outside(g[obh:obh + 2], duv.reshape(-1, 2).sum(0), dterm.reshape(-1, 2).sum(0), False)
+    # every convolution: weight and bias gradients from the stored gated gradient, and the
+    # data gradient it sends to the layers below (added up where a tensor feeds two layers)
+    dx_to = [np.zeros_like(a) for a in acts]
+    dx_abs = [np.zeros_like(a) for a in acts]
+    for l in range(13, -1, -1):
+        gl = no.bf16(np.where(acts[l] > 0, dacts[l], 0.0))        # the kernels' gated bf16 gradient
+        xin = layer_in(l)
+        dx, dW = no.conv3x3_grad(xin, Wr[l], gl)
+        ax, aW = no.conv3x3_grad(np.abs(xin), np.abs(Wr[l]), np.abs(gl))
+        ow, ob = conv[l]
+        bad[f"dW{l}"] = _outside(g[ow:ob].reshape(dW.shape), dW, aW, False)
+        bad[f"db{l}"] = _outside(g[ob:ob + no.COUT[l]], gl.reshape(-1, no.COUT[l]).sum(0),
+                                 np.abs(gl).reshape(-1, no.COUT[l]).sum(0), False)
+        if l == 0:
             continue
-        err, sens = rel(got, ref), max(rel(e[a:b], ref) for e in egs)
-        cos = float(got @ ref) / (np.linalg.norm(got) * nr)
-        assert err <= 4 * sens + 2e-3 and cos > 0.995, (name, err, sens, cos)
-    assert rel(g, rg) <= 4 * max(rel(e, rg) for e in egs) + 1e-3
+        if l in (2, 4, 6):
+            dx_to[l - 1] += no.pool_adjoint(dx)
+            dx_abs[l - 1] += no.pool_adjoint(ax)
+        elif l in (8, 10, 12):
+            skip = {8: 5, 10: 3, 12: 1}[l]
+            cs = no.COUT[skip]
+            dx_to[skip] += dx[..., :cs]
+            dx_abs[skip] += ax[..., :cs]
+            dx_to[l - 1] += no.upsample_adjoint(dx[..., cs:])
+            dx_abs[l - 1] += no.upsample_adjoint(ax[..., cs:])
+        else:
+            dx_to[l - 1] += dx
+            dx_abs[l - 1] += ax
+    for l in range(13):
+        bad[f"dact{l}"] = _outside(dacts[l], dx_to[l], dx_abs[l], False)
+    assert not any(bad.values()), {k: v for k, v in bad.items() if v}
 
 
 def test_adam_first_step_closed_form():
