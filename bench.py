@@ -646,6 +646,72 @@ def run_or_modes(args):
     print(json.dumps(line), flush=True)
 
 
+def run_config2(args):
+    """The 1024^2 workloads: Whittle-Matern fields (nu = 0.5 and 2.5, correlation length 16,
+    Gaussian and pointwise lognormal), 33 % and 66 % of the sites removed at random; each
+    filled by the whole method (T-hat from the e(T, L) table, relaxation with the slope
+    test, M = 100) -- one JSON line per grid with MAE, RMSE and correlation against the
+    hidden field at the gap sites, and site-updates/s and ms per map (CUDA events, device-
+    resident inputs, L2 flushed before each fill, the table built in the warm-up)."""
+    import torch
+    from paper_1811_01604_gb300 import mpr, synth
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    Lc = 1024
+    for nu in (0.5, 2.5):
+        for kind in ("gauss", "lognormal"):
+            for p in (0.33, 0.66):
+                seed = 1 if nu == 0.5 else 2
+                z_np = synth.wm_field(Lc, nu, 16.0, seed=seed)
+                if kind == "lognormal":
+                    z_np = synth.lognormal(z_np).astype(np.float32)
+                m_np = synth.mask_uniform(Lc, Lc, p, seed=1_000_000 + seed + int(100 * p))
+                z = torch.from_numpy(np.ascontiguousarray(z_np, np.float32)).cuda()
+                mask = torch.from_numpy(np.ascontiguousarray(m_np, np.uint8)).cuda()
+                gap = mask == 0
+                P = int(gap.sum().item())
+                out = torch.empty_like(z)
+                prm = mpr.mpr_default_params(seed=1, M=M)
+
+                def fill():
+                    ctx = mpr.mpr_init(z, mask, Lc, Lc, prm, stream.cuda_stream)
+                    try:
+                        T, _ = mpr.mpr_estimate_T(ctx)
+                        st = mpr.mpr_equilibrate(ctx)
+                        mpr.mpr_predict(ctx, M, out)
+                    finally:
+                        mpr.mpr_free(ctx)
+                    return T, st.sweeps
+
+                for _ in range(max(1, args.warmup)):
+                    fill()
+                ms, sw = [], []
+                for _ in range(args.steps):
+                    flush.zero_()
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    T, n = fill()
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                    sw.append(n)
+                zt, zh = z[gap].double(), out[gap].double()
+                err = zh - zt
+                corr = float(torch.corrcoef(torch.stack([zh, zt]))[0, 1])
+                updates = sum(P * (n + M) for n in sw)
+                line = {"metric": METRIC, "value": updates / (sum(ms) * 1e-3), "unit": UNIT, "n_gpus": 1,
+                        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms),
+                        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                        "data": "synthetic",
+                        "config": {"workload": f"mpr-fill-1024x1024-wm-nu{nu}-xi16-{kind}-p{p}", "M": M,
+                                   "gap_sites": P, "T_hat": T, "relax_sweeps": sw,
+                                   "l2": "512 MB buffer written between fills (L2 flush)"},
+                        "mae": float(err.abs().mean()), "rmse": float(err.pow(2).mean().sqrt()),
+                        "corr": corr}
+                print(json.dumps(line), flush=True)
+
+
 def run_dpsp(args):
     """Single versus double precision (Sect. 4, the DP/SP time ratio against the grid side
     for p = 33 % and 66 %): Whittle-Matern fields nu = 0.5, kappa = 0.2 (correlation length
@@ -729,9 +795,11 @@ def main():
     ap.add_argument("--profile-case", default=None,
                     choices=["sweep4096", "copy4096", "net4096", "net1024", "net128", "sweep64_4096"],
                     help="run a small fixed sweep workload for ncu instead of the benchmark")
-    ap.add_argument("--workload", default="fill4096", choices=["fill4096", "batch256", "warm1024", "warm4096",
-                                                                "chains1024", "ormodes1024", "dpsp"],
-                    help="fill4096: one 4096^2 map per step (default); batch256: 256 grids of "
+    ap.add_argument("--workload", default="fill4096", choices=["fill4096", "config1024", "batch256", "warm1024",
+                                                                "warm4096", "chains1024", "ormodes1024", "dpsp"],
+                    help="fill4096: one 4096^2 map per step (default); config1024: the eight 1024^2 "
+                         "grids (nu 0.5 / 2.5, Gaussian / lognormal, 33 / 66 %% gaps), one line each; "
+                         "batch256: 256 grids of "
                          "sides 128-2048 filled in one batch, against the same grids one at a time; "
                          "warm1024 / warm4096: learned warm start against the plain random start; "
                          "chains1024: independent chains against one chain at equal sweeps; "
@@ -772,6 +840,9 @@ def main():
         return
     if args.workload == "dpsp":
         run_dpsp(args)
+        return
+    if args.workload == "config1024":
+        run_config2(args)
         return
 
     import torch
