@@ -350,6 +350,68 @@ mpr_status mpr_sample_energy_static(const float* z, const uint8_t* mask, int W, 
                                     double* e_s, long long* n_pairs, void* cuda_stream);
 
 /*
+ * Row strips of one grid (several processes, one GPU each, fill one grid too large for one
+ * GPU; no counterpart in the paper, whose single GPU sweeps the whole checkerboard of
+ * Sect. 3.3).  The grid's rows are cut into bands, one per process.  A strip's context
+ * holds the block of rows [row0, row0 + Hb) of the W x H_global grid: its own rows, plus
+ * one row of the strip above (when row0 > 0) and one of the strip below (when
+ * row0 + Hb < H_global), which it never updates and which the caller refreshes from their
+ * owners after every half-sweep (mpr_strip_row).  row0 must be even (so every strip but
+ * the first begins at an odd grid row): the block's colours are then the grid's, and the
+ * Philox site index of block site (y, x) is (row0 + y) W + x, so the strips together make
+ * exactly the updates of a single context on the whole grid.  Strip contexts run the LIST
+ * kernels (exec_mode AUTO or LIST).  Reductions across strips (sums, minimum, maximum)
+ * are the caller's (e.g. torch.distributed).  The order of one fill:
+ *   mpr_strip_extremes on every strip -> global z_min, z_max (Eq. 1) -> mpr_strip_init;
+ *   mpr_strip_pairs -> e_s = -sum / count over all strips (Eq. 4) -> mpr_strip_temperature;
+ *   exchange the boundary rows; mpr_strip_energy and mpr_strip_gaps summed ->
+ *   mpr_strip_begin(phase 0); per sweep: for colour 0, 1: mpr_strip_half_sweep, exchange;
+ *   sum the totals; mpr_strip_control (until *stop);
+ *   mpr_strip_begin(phase 1); M sweeps as above with phase 1; mpr_strip_predict.
+ * z, mask: float / uint8 [Hb][W] of the block (device memory for mpr_strip_extremes, host
+ * or device for mpr_strip_init); the gap sites of the other strips' rows are not read.
+ */
+/* Minimum, maximum and number of the samples in the strip's own rows: out[3] (host). */
+mpr_status mpr_strip_extremes(const float* z, const uint8_t* mask, int W, int Hb, int row0, int H_global,
+                              double* out, void* cuda_stream);
+/* A strip's context, with the whole grid's Eq. 1 extremes.  EINVAL for an odd row0, a block
+   outside the grid or one without an own row, the TILE kernels, or a grid of 2^31 sites or
+   more; ENODATA unless zmax > zmin. */
+mpr_status mpr_strip_init(mpr_ctx** ctx, const float* z, const uint8_t* mask, int W, int Hb, int row0,
+                          int H_global, double zmin, double zmax, const mpr_params* params, void* cuda_stream);
+/* Eq. 4 terms of the strip's sample pairs (those whose upper or left site is its own): the
+   sum of cos(q (phi_i - phi_j)) and the pair count. */
+mpr_status mpr_strip_pairs(mpr_ctx* ctx, double* sum_cos, double* n_pairs);
+/* T-hat of the whole grid's e_s, from the e(T, L) table of the whole grid's shape (every
+   strip computes the same value); sets the context's temperature. */
+mpr_status mpr_strip_temperature(mpr_ctx* ctx, double e_s, double* T_hat);
+/* Eq. 2 over the bonds of the strip's colour-0 sites (every bond has one colour-0 end): the
+   strips' values add up to the grid's energy.  The neighbouring rows must be current. */
+mpr_status mpr_strip_energy(mpr_ctx* ctx, double* H_part);
+/* Gap sites of the strip's own rows (-1 for another context). */
+long long mpr_strip_gaps(const mpr_ctx* ctx);
+/* phase 0: Algorithm 2 steps 2.1-2.4 with the grid's energy H_total and gap count P_total;
+   phase 1: the equilibrium angle sums start at zero (step 6). */
+mpr_status mpr_strip_begin(mpr_ctx* ctx, int phase, double H_total, double P_total);
+/* Algorithm 1 on the strip's gap sites of one colour (phase 0: at the relaxation's window;
+   phase 1: at a_eq, adding every angle to the sums).  totals: double[2] of device memory;
+   colour 0 sets, colour 1 adds, the strip's accepted energy change and acceptance count. */
+mpr_status mpr_strip_half_sweep(mpr_ctx* ctx, int color, int phase, double* totals);
+/* One control step (phase 0: Algorithm 2 step 5.2-5.5; phase 1: the energy bookkeeping and
+   sweep counter of a fixed-window sweep) from totals summed over every strip (device
+   double[2]), with the whole grid's gap and bond counts.  stop (host, may be NULL: no
+   synchronisation): the relaxation has ended. */
+mpr_status mpr_strip_control(mpr_ctx* ctx, const double* totals, int phase, int* stop);
+/* Boundary rows, both colours: which = 0 copies the first own row to buf, 1 the last own
+   row; 2 copies buf into the row of the strip above, 3 into the row of the strip below.
+   buf (host or device) holds mpr_strip_row_bytes(ctx) bytes; enqueued on the stream. */
+size_t mpr_strip_row_bytes(const mpr_ctx* ctx);
+mpr_status mpr_strip_row(mpr_ctx* ctx, int which, void* buf);
+/* Step 7 for the strip: zhat float[Hb][W] of the block (host or device); its own rows hold
+   the estimates (gap sites) and the data (samples). */
+mpr_status mpr_strip_predict(mpr_ctx* ctx, int M, float* zhat);
+
+/*
  * Test support: Philox4x32-10 on the device.  ctr: uint32[n][4], out: uint32[n][4]
  * (host or device), key = (seed lo, seed hi).
  */

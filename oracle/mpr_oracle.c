@@ -240,13 +240,13 @@ enum { ORC_F_REFLECTED = 1, ORC_F_WRAPPED = 2, ORC_F_ACCEPTED = 4, ORC_F_VISITED
 /* ------------------------------------------------------------------------ */
 static int update_site(double* phi, int W, int H, int x, int y, double a, double T, double q,
                        uint64_t seed, uint32_t chain, uint32_t sweep, int or_mode,
-                       double* margin)
+                       double* margin, uint32_t site_off)
 {
     long i = (long)y * W + x;
     double nb[4];
     int nnb = gather_nb(phi, W, H, x, y, nb);
     double u, r;
-    site_randoms(seed, (uint32_t)i, sweep, chain, &u, &r);
+    site_randoms(seed, (uint32_t)i + site_off, sweep, chain, &u, &r);
     int flags = ORC_F_VISITED;
 
     double p1 = orc_over_relax(phi[i], nb, nnb, q, or_mode);          /* step 1 */
@@ -281,12 +281,54 @@ long orc_sweep(double* phi, const uint8_t* mask, int W, int H, double a, double 
                 long i = (long)y * W + x;
                 if (mask[i]) continue;                 /* samples stay frozen */
                 double m = 0.0;
-                int f = update_site(phi, W, H, x, y, a, T, q, seed, chain, sweep, or_mode, &m);
+                int f = update_site(phi, W, H, x, y, a, T, q, seed, chain, sweep, or_mode, &m, 0u);
                 if (f & ORC_F_ACCEPTED) ++nacc;
                 if (flags) flags[i] = (uint8_t)f;
                 if (margins) margins[i] = m;
             }
     return nacc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Row strips of one grid: the checkerboard of Sect. 3.3 cut into bands of   */
+/* rows.  A block holds rows [row0, row0 + Hb) of a W-wide grid: rows        */
+/* [y_a, y_b) of the block are the strip's own, the rows beside them (other  */
+/* strips' rows) serve as neighbours only, and the block's first and last    */
+/* rows are the grid's edges where the block has no row beyond them.         */
+/* ------------------------------------------------------------------------ */
+
+/* Algorithm 1 on the gap sites of colour `color` ((x + row0 + y) & 1, the grid's colour) in
+ * rows [y_a, y_b) of a block: the same updates orc_sweep makes to these sites in the whole
+ * grid, with the grid's Philox site index (row0 + y) W + x.  Returns the accepted proposals. */
+long orc_sweep_rows(double* phi, const uint8_t* mask, int W, int Hb, int row0, int y_a, int y_b,
+                    int color, double a, double T, double q, uint64_t seed, uint32_t chain,
+                    uint32_t sweep, int or_mode)
+{
+    long nacc = 0;
+    for (int y = y_a; y < y_b; ++y)
+        for (int x = 0; x < W; ++x) {
+            if (((x + row0 + y) & 1) != color) continue;
+            long i = (long)y * W + x;
+            if (mask[i]) continue;
+            int f = update_site(phi, W, Hb, x, y, a, T, q, seed, chain, sweep, or_mode, NULL,
+                                (uint32_t)row0 * (uint32_t)W);
+            if (f & ORC_F_ACCEPTED) ++nacc;
+        }
+    return nacc;
+}
+
+/* Eq. 2 over the bonds whose upper or left end lies in rows [y_a, y_b) of a block (each
+ * bond of the grid belongs to exactly one strip this way). */
+double orc_energy_rows(const double* phi, int W, int Hb, int y_a, int y_b, double q)
+{
+    double E = 0.0;
+    for (int y = y_a; y < y_b; ++y)
+        for (int x = 0; x < W; ++x) {
+            long i = (long)y * W + x;
+            if (x + 1 < W) E -= cos(q * (phi[i] - phi[i + 1]));
+            if (y + 1 < Hb) E -= cos(q * (phi[i] - phi[i + W]));
+        }
+    return E;
 }
 
 /* Algorithm 2 step 2.2: gap angles drawn from U(0, 2pi). */
@@ -322,6 +364,28 @@ typedef struct {
     double e_last;   /* specific energy after the last sweep */
 } orc_equil_out;
 
+/* State of the Algorithm 2 step 5 loop: counter i, slope k, window a, last acceptance A,
+ * history of e (e[0] before the first sweep, >= i_max + 2 values). */
+typedef struct {
+    int i;
+    double k, a, A;
+    double* e;
+} orc_relax;
+
+/* Steps 5.2-5.5 after one sweep in which nacc of the P gap sites accepted their proposal,
+ * e_next being the specific energy after it.  Returns 1 while the loop goes on (k < 0 and
+ * i <= i_max), 0 when it ends. */
+int orc_relax_step(orc_relax* s, long nacc, long P, double e_next, const orc_params* p)
+{
+    s->A = (double)nacc / (double)P;
+    if (s->A < p->A_targ) s->a = 1.0 + (double)(s->i + 1) / p->k_a;   /* 5.2 */
+    s->e[s->i + 1] = e_next;                                           /* 5.3 */
+    if (s->i >= p->n_fit && s->i % p->n_f == 0)
+        s->k = orc_sg_slope(&s->e[s->i + 2 - p->n_fit], p->n_fit);     /* 5.4 */
+    s->i += 1;                                                         /* 5.5 */
+    return s->k < 0.0 && s->i <= p->i_max;
+}
+
 static long count_gaps(const uint8_t* mask, long n)
 {
     long p = 0;
@@ -342,23 +406,21 @@ int orc_equilibrate(double* phi, const uint8_t* mask, int W, int H, double T,
     double ngp = (double)orc_n_gp(W, H);
     int cap = p->i_max + 2;
     double* e = ehist ? ehist : (double*)calloc((size_t)cap, sizeof(double));
-    int i = 0;                       /* step 2.1 */
-    double k = -1.0;                 /* step 2.3 */
-    double a = 1.0;                  /* step 2.4 */
-    double A = 0.0;
+    orc_relax s;
+    s.i = 0;                         /* step 2.1 */
+    s.k = -1.0;                      /* step 2.3 */
+    s.a = 1.0;                       /* step 2.4 */
+    s.A = 0.0;
+    s.e = e;
     e[0] = orc_energy(phi, W, H, p->q) / ngp;
-    while (k < 0.0 && i <= p->i_max && P > 0) {
-        long nacc = orc_sweep(phi, mask, W, H, a, T, p->q, p->seed, chain, (*sweep)++,
+    int go = P > 0 && s.i <= p->i_max;
+    while (go) {
+        long nacc = orc_sweep(phi, mask, W, H, s.a, T, p->q, p->seed, chain, (*sweep)++,
                               p->or_mode, NULL, NULL);                  /* 5.1 */
-        A = (double)nacc / (double)P;
-        if (A < p->A_targ) a = 1.0 + (double)(i + 1) / p->k_a;         /* 5.2 */
-        e[i + 1] = orc_energy(phi, W, H, p->q) / ngp;                  /* 5.3 */
-        if (i >= p->n_fit && i % p->n_f == 0)
-            k = orc_sg_slope(&e[i + 2 - p->n_fit], p->n_fit);          /* 5.4 */
-        i += 1;                                                         /* 5.5 */
+        go = orc_relax_step(&s, nacc, P, orc_energy(phi, W, H, p->q) / ngp, p);
     }
     if (out) {
-        out->sweeps = i; out->a = a; out->k = k; out->A_last = A; out->e_last = e[i];
+        out->sweeps = s.i; out->a = s.a; out->k = s.k; out->A_last = s.A; out->e_last = e[s.i];
     }
     if (!ehist) free(e);
     return 0;

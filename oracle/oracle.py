@@ -55,6 +55,12 @@ class EquilOut(ctypes.Structure):
                 ("A_last", ctypes.c_double), ("e_last", ctypes.c_double)]
 
 
+class RelaxState(ctypes.Structure):
+    """Mirror of ``orc_relax``: the Algorithm 2 step 5 loop state (e: history buffer)."""
+    _fields_ = [("i", ctypes.c_int), ("k", ctypes.c_double), ("a", ctypes.c_double),
+                ("A", ctypes.c_double), ("e", ctypes.c_void_p)]
+
+
 class FillOut(ctypes.Structure):
     _fields_ = [("zmin", ctypes.c_double), ("zmax", ctypes.c_double), ("e_s", ctypes.c_double),
                 ("T_hat", ctypes.c_double), ("n_sp", ctypes.c_longlong), ("n_gap", ctypes.c_long),
@@ -96,6 +102,12 @@ def lib():
             L.orc_over_relax.restype = d
             L.orc_sweep.argtypes = [vp, vp, i, i, d, d, d, u64, u32, u32, i, vp, vp]
             L.orc_sweep.restype = ctypes.c_long
+            L.orc_sweep_rows.argtypes = [vp, vp, i, i, i, i, i, i, d, d, d, u64, u32, u32, i]
+            L.orc_sweep_rows.restype = ctypes.c_long
+            L.orc_energy_rows.argtypes = [vp, i, i, i, i, d]
+            L.orc_energy_rows.restype = d
+            L.orc_relax_step.argtypes = [P(RelaxState), ctypes.c_long, ctypes.c_long, d, P(Params)]
+            L.orc_relax_step.restype = i
             L.orc_init_gaps.argtypes = [vp, vp, i, i, u64, u32]
             L.orc_sg_slope.argtypes = [vp, i]
             L.orc_sg_slope.restype = d
@@ -143,6 +155,37 @@ def map_angles(z, mask):
 
 def unmap(phi, zmin, zmax):
     return lib().orc_unmap(float(phi), float(zmin), float(zmax))
+
+
+def sweep_rows(phi, mask, row0, y_a, y_b, color, a, T, q=0.5, seed=0, chain=0, sweep_index=0,
+               or_mode=OR_CONSERVING):
+    """Algorithm 1 on the colour-`color` gap sites of rows [y_a, y_b) of a block holding rows
+    [row0, row0 + Hb) of a grid (in place); returns the accepted proposals."""
+    assert phi.dtype == np.float64 and phi.flags.c_contiguous
+    mask = _c(mask, np.uint8); Hb, W = phi.shape
+    return lib().orc_sweep_rows(_p(phi), _p(mask), W, Hb, row0, y_a, y_b, color, a, T, q, seed,
+                                chain, sweep_index, or_mode)
+
+
+def energy_rows(phi, y_a, y_b, q=0.5):
+    """Eq. 2 over the bonds whose upper or left end lies in rows [y_a, y_b) of the block."""
+    phi = _c(phi, np.float64); Hb, W = phi.shape
+    return lib().orc_energy_rows(_p(phi), W, Hb, y_a, y_b, q)
+
+
+class Relax:
+    """The Algorithm 2 step 5 loop driven from outside (one step per sweep)."""
+
+    def __init__(self, prm: Params, e0: float):
+        self.prm = prm
+        self.hist = np.zeros(prm.i_max + 2, np.float64)
+        self.hist[0] = e0
+        self.s = RelaxState(i=0, k=-1.0, a=1.0, A=0.0, e=self.hist.ctypes.data)
+
+    def step(self, nacc: int, P: int, e_next: float) -> bool:
+        """Steps 5.2-5.5; False once the loop ends."""
+        return bool(lib().orc_relax_step(ctypes.byref(self.s), int(nacc), int(P), float(e_next),
+                                         ctypes.byref(self.prm)))
 
 
 def sample_energy(phi, mask, q=0.5):

@@ -51,6 +51,7 @@ struct GridIn {
     uint32_t chain;
     double T;
     double zmin, scale;
+    uint32_t site_off = 0; // Philox site offset (a block of rows of a larger grid)
 };
 
 struct Batch {
@@ -108,8 +109,18 @@ struct GridInfo {                          // host view of one grid of a context
     double T = 0;
 };
 
+struct StripInfo {                         // a context that holds one row strip of a larger grid
+    bool on = false;
+    int row0 = 0, H_global = 0;            // grid row of the block's row 0, grid height
+    int h0 = 0, h1 = 0;                    // rows of other strips above / below the own rows
+    double pair_sum = 0, pair_cnt = 0;     // Eq. 4 terms of the own sample pairs
+    double P_total = 0;                    // gap sites of the whole grid
+};
+
 struct mpr_ctx {
     cudaStream_t st = nullptr;
+    StripInfo strip;
+    int* d_stop = nullptr;                 // row strips: the control step's stop flag
     cudaStream_t cap = nullptr;            // private stream for graph capture
     mpr_params prm{};
     std::vector<GridInfo> g;               // one per grid
@@ -324,6 +335,7 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
         E.plane[1] = (long long)(lat + plane);
         lat += 2 * plane;
         E.chain = grids[e].chain;
+        E.site_off = grids[e].site_off;
         E.q = ctx->prm.q;
         E.cQ = std::cos(kTwoPi * E.q);
         E.sQ = std::sin(kTwoPi * E.q);
@@ -906,6 +918,7 @@ void mpr_free(mpr_ctx* ctx) {
     dfree(ctx->d_z, ctx->st);
     dfree(ctx->d_mask, ctx->st);
     dfree(ctx->d_out, ctx->st);
+    dfree(ctx->d_stop, ctx->st);
     if (ctx->h_active) cudaFreeHost(ctx->h_active);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
     delete ctx;
@@ -1076,16 +1089,13 @@ mpr_status mpr_set_T(mpr_ctx* ctx, double T) {
     return set_T_all(ctx, std::vector<double>(ctx->g.size(), T));
 }
 
-mpr_status mpr_estimate_T(mpr_ctx* ctx, double* T_hat, double* e_s) {
-    if (!ctx) return MPR_EINVAL;
+// T-hat of e_s from the e(T, L) tables of the given lattice shapes (built, all together, for
+// the shapes not cached yet).
+static mpr_status temperatures_for(mpr_ctx* ctx, const std::vector<std::pair<int, int>>& shapes,
+                                   const std::vector<double>& e_s, std::vector<double>& T) {
     const mpr_params& p = ctx->prm;
-    const bool batch = ctx->g.size() > 1;
-    for (const GridInfo& G : ctx->g)
-        if (G.n_sp == 0) return fail(ctx, MPR_ENOPAIRS, "no nearest-neighbour sample pairs");
-    // tables for every lattice shape not cached yet, built together
     std::vector<std::pair<int, int>> need;
-    for (const GridInfo& G : ctx->g) {
-        const auto sh = table_shape(p, G.W, G.H, batch);
+    for (const auto& sh : shapes) {
         std::lock_guard<std::mutex> lk(g_table_mu);
         if (!g_tables.count(table_key(p, sh.first, sh.second)) &&
             std::find(need.begin(), need.end(), sh) == need.end())
@@ -1099,17 +1109,35 @@ mpr_status mpr_estimate_T(mpr_ctx* ctx, double* T_hat, double* e_s) {
         for (size_t i = 0; i < need.size(); ++i)
             g_tables[table_key(p, need[i].first, need[i].second)] = std::make_pair(Tk[i], ek[i]);
     }
-    std::vector<double> T(ctx->g.size());
-    for (size_t i = 0; i < ctx->g.size(); ++i) {
-        const auto sh = table_shape(p, ctx->g[i].W, ctx->g[i].H, batch);
+    T.resize(shapes.size());
+    for (size_t i = 0; i < shapes.size(); ++i) {
         std::pair<std::vector<double>, std::vector<double>> tab;
         {
             std::lock_guard<std::mutex> lk(g_table_mu);
-            tab = g_tables[table_key(p, sh.first, sh.second)];
+            tab = g_tables[table_key(p, shapes[i].first, shapes[i].second)];
         }
-        T[i] = invert_T(tab.first, tab.second, ctx->g[i].e_s);
+        T[i] = invert_T(tab.first, tab.second, e_s[i]);
     }
-    mpr_status s = set_T_all(ctx, T);
+    return MPR_OK;
+}
+
+mpr_status mpr_estimate_T(mpr_ctx* ctx, double* T_hat, double* e_s) {
+    if (!ctx) return MPR_EINVAL;
+    const mpr_params& p = ctx->prm;
+    const bool batch = ctx->g.size() > 1;
+    if (ctx->strip.on) return fail(ctx, MPR_ESTATE, "a row strip takes its temperature from mpr_strip_temperature");
+    for (const GridInfo& G : ctx->g)
+        if (G.n_sp == 0) return fail(ctx, MPR_ENOPAIRS, "no nearest-neighbour sample pairs");
+    std::vector<std::pair<int, int>> shapes;
+    std::vector<double> es;
+    for (const GridInfo& G : ctx->g) {
+        shapes.push_back(table_shape(p, G.W, G.H, batch));
+        es.push_back(G.e_s);
+    }
+    std::vector<double> T;
+    mpr_status s = temperatures_for(ctx, shapes, es, T);
+    if (s != MPR_OK) return s;
+    s = set_T_all(ctx, T);
     if (s != MPR_OK) return s;
     if (T_hat) *T_hat = T[0];
     if (e_s) *e_s = ctx->g[0].e_s;
@@ -1546,6 +1574,281 @@ mpr_status mpr_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, size_t 
     dfree(d_in, st);
     dfree(d_out, st);
     return s;
+}
+
+// ---------------------------------------------------------------- row strips of one grid
+// A grid too large for one GPU is cut into bands of rows, one per process (the checkerboard
+// of Sect. 3.3 cut by rows).  A strip's context holds the block of rows [row0, row0 + Hb)
+// of the W x H_global grid: its own rows and, where another strip continues the grid, the
+// one row of that strip above (h0 = 1) and below (h1 = 1), frozen in the block and
+// refreshed from its owner after every half-sweep.  row0 is even, so the block's colours
+// are the grid's, and the Philox site index of block site (y, x) is (row0 + y) W + x: the
+// strips together draw exactly the random numbers of the whole grid.
+
+static bool strip_geometry(int W, int Hb, int row0, int H_global, int* h0, int* h1) {
+    if (W < 1 || Hb < 1 || row0 < 0 || (row0 & 1) || H_global < 1 || H_global > 65535 ||
+        row0 + Hb > H_global || (W + 1) / 2 > 65535 || (long long)W * H_global >= (1LL << 31))
+        return false;
+    *h0 = row0 > 0 ? 1 : 0;
+    *h1 = row0 + Hb < H_global ? 1 : 0;
+    return Hb >= *h0 + *h1 + 1;
+}
+
+static double unkey_value(unsigned k) {
+    const unsigned b = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+    float f;
+    std::memcpy(&f, &b, sizeof f);
+    return (double)f;
+}
+
+mpr_status mpr_strip_extremes(const float* z, const uint8_t* mask, int W, int Hb, int row0, int H_global,
+                              double* out, void* cuda_stream) {
+    int h0 = 0, h1 = 0;
+    if (!z || !mask || !out || !strip_geometry(W, Hb, row0, H_global, &h0, &h1)) return MPR_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    unsigned* d_keys = nullptr;
+    unsigned long long* d_ns = nullptr;
+    if (dalloc(&d_keys, 2, st) != cudaSuccess) return MPR_ENOMEM;
+    if (dalloc(&d_ns, 1, st) != cudaSuccess) { dfree(d_keys, st); return MPR_ENOMEM; }
+    unsigned keys[2] = {0u, 0u};
+    unsigned long long ns = 0;
+    const long long off = (long long)h0 * W;
+    cudaError_t e = cudaMemsetAsync(d_keys, 0xFF, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_keys + 1, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_ns, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = launch_minmax(z + off, mask + off, (long long)(Hb - h0 - h1) * W, d_keys, d_ns, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(keys, d_keys, sizeof keys, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ns, d_ns, sizeof ns, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dfree(d_keys, st);
+    dfree(d_ns, st);
+    if (e != cudaSuccess) { cudaGetLastError(); return MPR_ECUDA; }
+    out[0] = ns ? unkey_value(keys[0]) : INFINITY;
+    out[1] = ns ? unkey_value(keys[1]) : -INFINITY;
+    out[2] = (double)ns;
+    return MPR_OK;
+}
+
+mpr_status mpr_strip_init(mpr_ctx** out, const float* z, const uint8_t* mask, int W, int Hb, int row0,
+                          int H_global, double zmin, double zmax, const mpr_params* params, void* cuda_stream) {
+    if (!out) return MPR_EINVAL;
+    *out = nullptr;
+    int h0 = 0, h1 = 0;
+    if (!z || !mask || !strip_geometry(W, Hb, row0, H_global, &h0, &h1)) return MPR_EINVAL;
+    if (!(zmax > zmin) || !std::isfinite(zmin) || !std::isfinite(zmax)) return MPR_ENODATA;
+    mpr_ctx* ctx = new mpr_ctx();
+    if (params) ctx->prm = *params; else mpr_default_params(&ctx->prm);
+    std::string why;
+    if (ctx->prm.exec_mode == MPR_EXEC_TILE || check_params(&ctx->prm, why) != MPR_OK) {
+        delete ctx;
+        return MPR_EINVAL;
+    }
+    ctx->prm.exec_mode = MPR_EXEC_LIST;              // the half-sweep kernels carry the site offset
+    ctx->st = (cudaStream_t)cuda_stream;
+    ctx->g.resize(1);
+    GridInfo& G = ctx->g[0];
+    G.W = W;
+    G.H = Hb;
+    G.site0 = 0;
+    G.zmin = zmin;
+    G.zmax = zmax;
+    G.scale = kTwoPi / (zmax - zmin);
+    ctx->n_sites = (long long)W * Hb;
+    auto bail = [&](mpr_status s) { mpr_free(ctx); return s; };
+#define CUS(call) do { if ((call) != cudaSuccess) { cudaGetLastError(); return bail(MPR_ECUDA); } } while (0)
+    CUS(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
+    CUS(cudaMallocHost((void**)&ctx->h_active, sizeof(int) * 4));
+    const size_t N = (size_t)ctx->n_sites;
+    if (dalloc(&ctx->d_z, N, ctx->st) != cudaSuccess || dalloc(&ctx->d_mask, N, ctx->st) != cudaSuccess ||
+        dalloc(&ctx->d_out, N, ctx->st) != cudaSuccess || dalloc(&ctx->d_stop, 1, ctx->st) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(MPR_ENOMEM);
+    }
+    CUS(cudaMemcpyAsync(ctx->d_z, z, N * sizeof(float), cudaMemcpyDefault, ctx->st));
+    CUS(cudaMemcpyAsync(ctx->d_mask, mask, N, cudaMemcpyDefault, ctx->st));
+    // Eq. 4 terms of the strip's own sample pairs (a pair belongs to the strip of its upper
+    // or left site), before the neighbouring strips' rows are frozen in the mask copy
+    {
+        EntryDesc t{};
+        t.W = W;
+        t.H = Hb - h0;
+        double* d_ps = nullptr;
+        unsigned long long* d_pc = nullptr;
+        CUS(dalloc(&d_ps, 1024, ctx->st));
+        CUS(dalloc(&d_pc, 1024, ctx->st));
+        int np = 0;
+        const long long off = (long long)h0 * W;
+        CUS(launch_sample_energy(&t, ctx->d_z + off, ctx->d_mask + off, G.scale, ctx->prm.q, d_ps, d_pc, &np,
+                                 ctx->prm.precision == MPR_PREC_F64, ctx->st, Hb - h0 - h1));
+        std::vector<double> ps(np);
+        std::vector<unsigned long long> pc(np);
+        CUS(cudaMemcpyAsync(ps.data(), d_ps, sizeof(double) * np, cudaMemcpyDeviceToHost, ctx->st));
+        CUS(cudaMemcpyAsync(pc.data(), d_pc, sizeof(unsigned long long) * np, cudaMemcpyDeviceToHost, ctx->st));
+        CUS(cudaStreamSynchronize(ctx->st));
+        dfree(d_ps, ctx->st);
+        dfree(d_pc, ctx->st);
+        for (int k = 0; k < np; ++k) {
+            ctx->strip.pair_sum += ps[k];
+            ctx->strip.pair_cnt += (double)pc[k];
+        }
+    }
+    // the neighbouring strips' rows: never updated here (their values come from their owners)
+    if (h0) CUS(cudaMemsetAsync(ctx->d_mask, 1, (size_t)W, ctx->st));
+    if (h1) CUS(cudaMemsetAsync(ctx->d_mask + (size_t)(Hb - 1) * W, 1, (size_t)W, ctx->st));
+#undef CUS
+    GridIn gi{W, Hb, ctx->d_z, ctx->d_mask, ctx->prm.chain, 0.0, zmin, G.scale};
+    gi.site_off = (uint32_t)row0 * (uint32_t)W;
+    const mpr_status bs = batch_build(ctx, ctx->b, std::vector<GridIn>{gi}, 0, ctx->d_mask);
+    if (bs != MPR_OK) return bail(bs);
+    ctx->strip.on = true;
+    ctx->strip.row0 = row0;
+    ctx->strip.H_global = H_global;
+    ctx->strip.h0 = h0;
+    ctx->strip.h1 = h1;
+    *out = ctx;
+    return MPR_OK;
+}
+
+static mpr_status strip_ctx(mpr_ctx* ctx) {
+    if (!ctx) return MPR_EINVAL;
+    if (!ctx->strip.on) return fail(ctx, MPR_ESTATE, "not a row-strip context (mpr_strip_init)");
+    return MPR_OK;
+}
+
+mpr_status mpr_strip_pairs(mpr_ctx* ctx, double* sum_cos, double* n_pairs) {
+    const mpr_status s = strip_ctx(ctx);
+    if (s != MPR_OK) return s;
+    if (sum_cos) *sum_cos = ctx->strip.pair_sum;
+    if (n_pairs) *n_pairs = ctx->strip.pair_cnt;
+    return MPR_OK;
+}
+
+mpr_status mpr_strip_temperature(mpr_ctx* ctx, double e_s, double* T_hat) {
+    mpr_status s = strip_ctx(ctx);
+    if (s != MPR_OK) return s;
+    if (!std::isfinite(e_s)) return fail(ctx, MPR_EINVAL, "e_s must be finite");
+    std::vector<double> T;
+    s = temperatures_for(ctx, {table_shape(ctx->prm, ctx->g[0].W, ctx->strip.H_global, false)}, {e_s}, T);
+    if (s == MPR_OK) s = set_T_all(ctx, T);
+    if (s != MPR_OK) return s;
+    ctx->g[0].e_s = e_s;
+    if (T_hat) *T_hat = T[0];
+    return MPR_OK;
+}
+
+mpr_status mpr_strip_energy(mpr_ctx* ctx, double* H_part) {
+    mpr_status s = strip_ctx(ctx);
+    if (s != MPR_OK) return s;
+    if (!H_part) return MPR_EINVAL;
+    double* d = ctx->b.d_scratch + kScratch;
+    CU(launch_energy(&ctx->b.ents[0], ctx->b.d_lat, ctx->b.d_scratch, kScratch, d, ctx->b.f64, ctx->st,
+                     ctx->strip.h0, ctx->g[0].H - ctx->strip.h1));
+    CU(cudaMemcpyAsync(H_part, d, sizeof(double), cudaMemcpyDefault, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    return MPR_OK;
+}
+
+long long mpr_strip_gaps(const mpr_ctx* ctx) {
+    return ctx && ctx->strip.on ? (long long)ctx->b.ents[0].P : -1;
+}
+
+mpr_status mpr_strip_begin(mpr_ctx* ctx, int phase, double H_total, double P_total) {
+    mpr_status s = strip_ctx(ctx);
+    if (s != MPR_OK) return s;
+    if (!ctx->T_set) return fail(ctx, MPR_ESTATE, "temperature not set");
+    if (phase != 0 && phase != 1) return fail(ctx, MPR_EINVAL, "phase 0 (relaxation) or 1 (equilibrium)");
+    if (!(P_total >= 0.0) || P_total >= 2147483648.0) return fail(ctx, MPR_EINVAL, "0 <= P_total < 2^31");
+    Batch& b = ctx->b;
+    ctx->strip.P_total = P_total;
+    std::vector<Ctl> c;
+    s = read_ctl(ctx, b, c);
+    if (s != MPR_OK) return s;
+    if (phase == 0) {                        // Algorithm 2 steps 2.1, 2.3, 2.4, and the energy of the grid
+        c[0].i = 0;
+        c[0].k = -1.0;
+        c[0].a = 1.0;
+        c[0].stop = P_total > 0.0 ? 0 : 1;
+        c[0].converged = 0;
+        c[0].esum = 0.0;
+        c[0].nsamp = 0;
+        c[0].half_qd = (float)(0.5 * kTwoPi * b.ents[0].q / 1.0);
+        c[0].H = H_total;
+        CU(cudaMemcpyAsync(b.d_ctl, c.data(), sizeof(Ctl), cudaMemcpyHostToDevice, ctx->st));
+    } else {                                 // step 6: the angle sums start at zero
+        CU(cudaMemsetAsync(b.d_acc, 0, sizeof(float) * (b.f64 ? 2 : 1) * std::max<size_t>(b.n_gaps, 1), ctx->st));
+    }
+    CU(cudaStreamSynchronize(ctx->st));
+    return MPR_OK;
+}
+
+mpr_status mpr_strip_half_sweep(mpr_ctx* ctx, int color, int phase, double* totals) {
+    mpr_status s = strip_ctx(ctx);
+    if (s != MPR_OK) return s;
+    if ((color != 0 && color != 1) || (phase != 0 && phase != 1) || !totals)
+        return fail(ctx, MPR_EINVAL, "color 0 or 1, phase 0 or 1, totals required");
+    Batch& b = ctx->b;
+    const bool relax = phase == 0;
+    const SweepArgs A = sweep_args(ctx, b, relax, ctx->prm.a_eq, relax, !relax);
+    CU(launch_half_sweep(A, color, ctx->prm.trig_mode, ctx->st));
+    CU(launch_strip_partials(b.d_part[color], b.nblk[color], color, totals, ctx->st));
+    return MPR_OK;
+}
+
+mpr_status mpr_strip_control(mpr_ctx* ctx, const double* totals, int phase, int* stop) {
+    mpr_status s = strip_ctx(ctx);
+    if (s != MPR_OK) return s;
+    if ((phase != 0 && phase != 1) || !totals) return fail(ctx, MPR_EINVAL, "phase 0 or 1, totals required");
+    Batch& b = ctx->b;
+    const mpr_params& p = ctx->prm;
+    const double W = ctx->g[0].W, Hg = ctx->strip.H_global;
+    const double ngp = W * (Hg - 1.0) + Hg * (W - 1.0);
+    CU(launch_strip_control(b.d_ctl, &b.ents[0], ctx->strip.P_total, ngp, totals, phase == 0 ? CTL_RELAX : CTL_FIXED,
+                            p.A_targ, p.k_a, p.n_f, p.n_fit, p.i_max, b.d_ehist, ctx->d_stop, ctx->st));
+    if (stop) {
+        CU(cudaMemcpyAsync(ctx->h_active, ctx->d_stop, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+        CU(cudaStreamSynchronize(ctx->st));
+        *stop = phase == 0 ? ctx->h_active[0] : 0;
+    }
+    return MPR_OK;
+}
+
+size_t mpr_strip_row_bytes(const mpr_ctx* ctx) {
+    if (!ctx || !ctx->strip.on) return 0;
+    return (size_t)2 * ctx->b.ents[0].pitch * (ctx->b.f64 ? sizeof(double2) : sizeof(float2));
+}
+
+mpr_status mpr_strip_row(mpr_ctx* ctx, int which, void* buf) {
+    mpr_status s = strip_ctx(ctx);
+    if (s != MPR_OK) return s;
+    if (!buf || which < 0 || which > 3) return fail(ctx, MPR_EINVAL, "which in 0..3 and a buffer required");
+    const int Hb = ctx->g[0].H, h0 = ctx->strip.h0, h1 = ctx->strip.h1;
+    if ((which == 2 && !h0) || (which == 3 && !h1)) return fail(ctx, MPR_EINVAL, "no neighbouring strip there");
+    const int y = which == 0 ? h0 : which == 1 ? Hb - 1 - h1 : which == 2 ? 0 : Hb - 1;
+    const EntryDesc& E = ctx->b.ents[0];
+    const size_t el = ctx->b.f64 ? sizeof(double2) : sizeof(float2);
+    const size_t wide = ctx->b.f64 ? 2 : 1;
+    const size_t row = (size_t)E.pitch * el;
+    for (int c = 0; c < 2; ++c) {
+        char* lat = reinterpret_cast<char*>(ctx->b.d_lat + (size_t)(E.plane[c] + (long long)(y + 1) * E.pitch) * wide);
+        char* other = static_cast<char*>(buf) + (size_t)c * row;
+        if (which <= 1) CU(cudaMemcpyAsync(other, lat, row, cudaMemcpyDefault, ctx->st));
+        else CU(cudaMemcpyAsync(lat, other, row, cudaMemcpyDefault, ctx->st));
+    }
+    return MPR_OK;
+}
+
+mpr_status mpr_strip_predict(mpr_ctx* ctx, int M, float* zhat) {
+    mpr_status s = strip_ctx(ctx);
+    if (s != MPR_OK) return s;
+    if (!zhat || M < 1) return fail(ctx, MPR_EINVAL, "M >= 1 and zhat required");
+    Batch& b = ctx->b;
+    const GridInfo& G = ctx->g[0];
+    CU(cudaMemcpyAsync(ctx->d_out, ctx->d_z, (size_t)ctx->n_sites * sizeof(float), cudaMemcpyDeviceToDevice, ctx->st));
+    CU(launch_predict_out(&b.ents[0], b.d_lat, b.d_gaps, b.d_acc, M, ctx->prm.q, G.zmin, G.zmax, ctx->d_out, b.f64,
+                          ctx->st));
+    CU(cudaMemcpyAsync(zhat, ctx->d_out, (size_t)ctx->n_sites * sizeof(float), cudaMemcpyDefault, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    return MPR_OK;
 }
 
 }  // extern "C"

@@ -72,7 +72,7 @@ __global__ void k_pack(EntryDesc e, const float* __restrict__ z, const uint8_t* 
             const double phi = ((double)z[i] - zmin) * scale;          // Eq. 1
             theta = e.q * phi;
         } else {
-            const uint4 r = philox10(make_uint4((uint32_t)i, kInitSweep, e.chain, 0u), key0, key1);
+            const uint4 r = philox10(make_uint4((uint32_t)i + e.site_off, kInitSweep, e.chain, 0u), key0, key1);
             theta = kTwoPi * e.q * (double)u24f(r.x);                  // q * 2 pi u
         }
         const long long base = c ? e.plane[1] : e.plane[0];
@@ -158,7 +158,7 @@ __global__ void k_gap_scatter(EntryDesc e, const uint8_t* __restrict__ mask, int
 // Each block writes its partial sums; they are added in block order afterwards.
 __global__ void k_sample_energy(EntryDesc e, const float* __restrict__ z,
                                 const uint8_t* __restrict__ mask, float qs,
-                                double* part_sum, unsigned long long* part_cnt) {
+                                double* part_sum, unsigned long long* part_cnt, int y_end) {
     // Eq. 4 pairs (each unordered sample pair once: right and down neighbours), rows
     // block-strided and columns thread-strided (no index division).  The cosine argument
     // q (z_i - z_j) 2 pi / (z_max - z_min) is formed in FP32 (one rounding of the scale,
@@ -168,7 +168,7 @@ __global__ void k_sample_energy(EntryDesc e, const float* __restrict__ z,
     __shared__ unsigned long long scnt[kThreads / 32];
     double acc = 0.0;
     unsigned long long cnt = 0;
-    for (int y = blockIdx.x; y < e.H; y += gridDim.x) {
+    for (int y = blockIdx.x; y < y_end; y += gridDim.x) {
         const float* __restrict__ zr = z + (long long)y * e.W;
         const uint8_t* __restrict__ mr = mask + (long long)y * e.W;
         const bool down = y + 1 < e.H;
@@ -210,12 +210,12 @@ __global__ void k_sample_energy(EntryDesc e, const float* __restrict__ z,
 // q (z_i - z_j) 2 pi / (z_max - z_min) and every sum in double.
 __global__ void k_sample_energy64(EntryDesc e, const float* __restrict__ z,
                                   const uint8_t* __restrict__ mask, double qs,
-                                  double* part_sum, unsigned long long* part_cnt) {
+                                  double* part_sum, unsigned long long* part_cnt, int y_end) {
     __shared__ double ssum[kThreads / 32];
     __shared__ unsigned long long scnt[kThreads / 32];
     double acc = 0.0;
     unsigned long long cnt = 0;
-    for (int y = blockIdx.x; y < e.H; y += gridDim.x) {
+    for (int y = blockIdx.x; y < y_end; y += gridDim.x) {
         const float* __restrict__ zr = z + (long long)y * e.W;
         const uint8_t* __restrict__ mr = mask + (long long)y * e.W;
         const bool down = y + 1 < e.H;
@@ -309,12 +309,14 @@ cudaError_t launch_gap_scatter(const EntryDesc* e, const uint8_t* mask, int all_
 
 cudaError_t launch_sample_energy(const EntryDesc* e, const float* z, const uint8_t* mask,
                                  double scale, double q, double* part_sum,
-                                 unsigned long long* part_cnt, int* nparts, bool f64, cudaStream_t st) {
-    const int g = e->H < 1024 ? e->H : 1024;
+                                 unsigned long long* part_cnt, int* nparts, bool f64, cudaStream_t st,
+                                 int y_end) {
+    if (y_end < 0 || y_end > e->H) y_end = e->H;
+    const int g = y_end < 1 ? 1 : (y_end < 1024 ? y_end : 1024);
     *nparts = g;
     count_launches(1, st);
-    if (f64) k_sample_energy64<<<g, kThreads, 0, st>>>(*e, z, mask, q * scale, part_sum, part_cnt);
-    else k_sample_energy<<<g, kThreads, 0, st>>>(*e, z, mask, (float)(q * scale), part_sum, part_cnt);
+    if (f64) k_sample_energy64<<<g, kThreads, 0, st>>>(*e, z, mask, q * scale, part_sum, part_cnt, y_end);
+    else k_sample_energy<<<g, kThreads, 0, st>>>(*e, z, mask, (float)(q * scale), part_sum, part_cnt, y_end);
     return cudaGetLastError();
 }
 

@@ -32,7 +32,8 @@ constexpr uint32_t kInitSweep = 0xFFFFFFFFu;      // Philox sweep word of the in
 enum { CTL_RELAX = 0, CTL_FIXED = 1, CTL_SAMPLE = 2 };
 
 struct EntryDesc {            // immutable during a run
-    int W, H, pitch, _pad0;
+    int W, H, pitch;
+    uint32_t site_off;        // added to the Philox site index (a block of rows of a larger grid)
     long long plane[2];       // float2 offset of plane c's padded origin
     long long gbase[2];       // offset of colour c's gap list
     int ngap[2];
@@ -551,9 +552,12 @@ cudaError_t launch_gap_scatter(const EntryDesc* e_host, const uint8_t* mask, int
                                const int* row_offsets, uint32_t* gaps, cudaStream_t st);
 // Eq. 4 partial sums: per block (sum of cosines, pair count) into part[block] (grid <= 1024).
 // f64: cosine arguments and row sums in FP64.
+// y_end: only pairs whose upper or left site lies in rows [0, y_end) (a strip's own rows;
+// e_host->H otherwise).
 cudaError_t launch_sample_energy(const EntryDesc* e_host, const float* z, const uint8_t* mask,
                                  double scale, double q, double* part_sum,
-                                 unsigned long long* part_cnt, int* nparts, bool f64, cudaStream_t st);
+                                 unsigned long long* part_cnt, int* nparts, bool f64, cudaStream_t st,
+                                 int y_end = -1);
 cudaError_t launch_philox(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, size_t n,
                           cudaStream_t st);
 
@@ -591,8 +595,19 @@ cudaError_t launch_control(Ctl* ctl, Part* const part[2], const EntryDesc* ents,
                            int mode, double A_targ, double k_a, int n_f, int n_fit, int i_max,
                            double* ehist, int ehist_stride, int* active, cudaStream_t st);
 // Eq. 2 of one grid: per-block partials then a fixed-order sum into *out (deterministic).
+// [y_a, y_b): only the bonds of the colour-0 sites of these rows (every bond has one
+// colour-0 end); the whole grid by default.
 cudaError_t launch_energy(const EntryDesc* e_host, const float2* lat, double* scratch,
-                          int scratch_len, double* out, bool f64, cudaStream_t st);
+                          int scratch_len, double* out, bool f64, cudaStream_t st, int y_a = 0,
+                          int y_b = -1);
+// Row strips: out[0] (color 0: =, color 1: +=) the colour's accepted energy change, out[1]
+// its acceptance count, summed over the half-sweep blocks in block order.
+cudaError_t launch_strip_partials(const Part* part, int nblk, int color, double* out, cudaStream_t st);
+// Row strips: one control step of entry 0 from the totals {dH, n_acc} of all strips, with
+// the whole grid's gap count P and bond count ngp; *stop_dev <- the relaxation has ended.
+cudaError_t launch_strip_control(Ctl* ctl, const EntryDesc* e_host, double P, double ngp, const double* tot,
+                                 int mode, double A_targ, double k_a, int n_f, int n_fit, int i_max,
+                                 double* ehist, int* stop_dev, cudaStream_t st);
 cudaError_t launch_sum(const double* v, int n, double* out, cudaStream_t st);
 cudaError_t launch_set_tracked_energy(Ctl* ctl, const double* H, int n_ent, cudaStream_t st);
 // f64: acc holds doubles (same element offsets).

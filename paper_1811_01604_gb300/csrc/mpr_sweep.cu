@@ -21,7 +21,7 @@ k_half_sweep(const SweepArgs A, const int color) {
     const float kx = accept_scale<TRIG>((float)(-1.0 / ctl->T));
     const uint32_t sweep = ctl->sweep;
     const int n = color ? E->ngap[1] : E->ngap[0], pitch = E->pitch, W = E->W;
-    const uint32_t chain = E->chain;
+    const uint32_t chain = E->chain, site_off = E->site_off;
     const long long gb = color ? E->gbase[1] : E->gbase[0];
     const uint32_t* __restrict__ gl = A.gaps + gb;
     float2* __restrict__ own = A.lat + (color ? E->plane[1] : E->plane[0]);
@@ -43,7 +43,7 @@ k_half_sweep(const SweepArgs A, const int color) {
             const float C = (nu.x + nd.x) + (nl.x + nr.x);
             const float S = (nu.y + nd.y) + (nl.y + nr.y);
             float2 v = own[k];
-            const uint32_t site = (uint32_t)y * (uint32_t)W + (uint32_t)(2 * j + s);
+            const uint32_t site = (uint32_t)y * (uint32_t)W + (uint32_t)(2 * j + s) + site_off;
             const uint4 rnd = philox10(make_uint4(site, sweep, chain, 0u), A.rk);
             const float hq = (u24f(rnd.x) - 0.5f) * half_qd;
             bool accepted;
@@ -92,7 +92,7 @@ k_half_sweep64(const SweepArgs A, const int color) {
     const double neg_inv_T = -1.0 / ctl->T;
     const uint32_t sweep = ctl->sweep;
     const int n = color ? E->ngap[1] : E->ngap[0], pitch = E->pitch, W = E->W;
-    const uint32_t chain = E->chain;
+    const uint32_t chain = E->chain, site_off = E->site_off;
     const long long gb = color ? E->gbase[1] : E->gbase[0];
     const uint32_t* __restrict__ gl = A.gaps + gb;
     double2* __restrict__ lat = reinterpret_cast<double2*>(A.lat);
@@ -115,7 +115,7 @@ k_half_sweep64(const SweepArgs A, const int color) {
             const double C = (nu.x + nd.x) + (nl.x + nr.x);
             const double S = (nu.y + nd.y) + (nl.y + nr.y);
             double2 v = own[k];
-            const uint32_t site = (uint32_t)y * (uint32_t)W + (uint32_t)(2 * j + s);
+            const uint32_t site = (uint32_t)y * (uint32_t)W + (uint32_t)(2 * j + s) + site_off;
             const uint4 rnd = philox10(make_uint4(site, sweep, chain, 0u), A.rk);
             const double hq = ((double)u24f(rnd.x) - 0.5) * half_qd;
             bool accepted;
@@ -206,16 +206,16 @@ __device__ __forceinline__ double bond_sum(double2 v, double2 a, double2 b, doub
 }
 
 template <typename V>
-__global__ void k_energy(EntryDesc e, const V* __restrict__ lat, double* part) {
+__global__ void k_energy(EntryDesc e, const V* __restrict__ lat, double* part, int y_a, int y_b) {
     __shared__ double sw[8];
     const int Wc = (e.W + 1) >> 1;
-    const long long n = (long long)e.H * Wc;
+    const long long n = (long long)(y_b - y_a) * Wc;
     const V* p0 = lat + e.plane[0];
     const V* p1 = lat + e.plane[1];
     double acc = 0.0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(t / Wc), j = (int)(t - (long long)y * Wc);
+        const int yr = (int)(t / Wc), j = (int)(t - (long long)yr * Wc), y = y_a + yr;
         const int s = y & 1;                                     // colour 0: s = y & 1
         if (2 * j + s >= e.W) continue;
         const long long k = (long long)(y + 1) * e.pitch + j + kPadL;
@@ -248,6 +248,29 @@ __global__ void k_sum(const double* __restrict__ v, int n, double* out) {
 __global__ void k_set_tracked_energy(Ctl* ctl, const double* H, int n_ent) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e < n_ent) ctl[e].H = H[e];
+}
+
+// Row strips: the half-sweep blocks' energy changes and acceptance counts of one colour,
+// added in block order (one thread: the order is fixed).
+__global__ void k_strip_partials(const Part* __restrict__ part, int nblk, int color, double* out) {
+    double dH = 0.0, na = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+        dH += part[b].dH;
+        na += (double)part[b].nacc;
+    }
+    out[0] = color ? out[0] + dH : dH;
+    out[1] = color ? out[1] + na : na;
+}
+
+// Row strips: one control step from the totals of every strip; e carries the whole grid's
+// gap count and bond count.
+__global__ void k_strip_control(Ctl* ctl, EntryDesc e, const double* __restrict__ tot, int mode,
+                                double A_targ, double k_a, int n_f, int n_fit, int i_max, double* ehist,
+                                int* stop) {
+    Ctl c = ctl[0];
+    control_step(c, e, tot[0], (unsigned long long)tot[1], mode, A_targ, k_a, n_f, n_fit, i_max, ehist, 0);
+    ctl[0] = c;
+    if (stop) *stop = c.stop;
 }
 
 // Algorithm 2 step 7: zhat = G^-1(mean phi) at gap sites (G affine, so this equals the
@@ -376,15 +399,35 @@ cudaError_t launch_control(Ctl* ctl, Part* const part[2], const EntryDesc* ents,
 }
 
 cudaError_t launch_energy(const EntryDesc* e_host, const float2* lat, double* scratch,
-                          int scratch_len, double* out, bool f64, cudaStream_t st) {
-    const long long n = (long long)e_host->H * ((e_host->W + 1) >> 1);
-    int g = grid_for(n, 256);
+                          int scratch_len, double* out, bool f64, cudaStream_t st, int y_a, int y_b) {
+    if (y_b < 0 || y_b > e_host->H) y_b = e_host->H;
+    if (y_a < 0) y_a = 0;
+    if (y_a > y_b) y_a = y_b;
+    const long long n = (long long)(y_b - y_a) * ((e_host->W + 1) >> 1);
+    int g = grid_for(n > 0 ? n : 1, 256);
     if (g > scratch_len) g = scratch_len;
     count_launches(1, st);
-    if (f64) k_energy<double2><<<g, 256, 0, st>>>(*e_host, reinterpret_cast<const double2*>(lat), scratch);
-    else k_energy<float2><<<g, 256, 0, st>>>(*e_host, lat, scratch);
+    if (f64) k_energy<double2><<<g, 256, 0, st>>>(*e_host, reinterpret_cast<const double2*>(lat), scratch, y_a, y_b);
+    else k_energy<float2><<<g, 256, 0, st>>>(*e_host, lat, scratch, y_a, y_b);
     count_launches(1, st);
     k_sum<<<1, 256, 0, st>>>(scratch, g, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_strip_partials(const Part* part, int nblk, int color, double* out, cudaStream_t st) {
+    count_launches(1, st);
+    k_strip_partials<<<1, 1, 0, st>>>(part, nblk, color, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_strip_control(Ctl* ctl, const EntryDesc* e_host, double P, double ngp, const double* tot,
+                                 int mode, double A_targ, double k_a, int n_f, int n_fit, int i_max,
+                                 double* ehist, int* stop_dev, cudaStream_t st) {
+    EntryDesc e = *e_host;
+    e.P = (int)P;
+    e.ngp = ngp;
+    count_launches(1, st);
+    k_strip_control<<<1, 1, 0, st>>>(ctl, e, tot, mode, A_targ, k_a, n_f, n_fit, i_max, ehist, stop_dev);
     return cudaGetLastError();
 }
 

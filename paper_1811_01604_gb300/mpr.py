@@ -89,6 +89,19 @@ _SIGS = [
     ("mpr_sample_energy_static", _I, [_VP, _VP, _I, _I, _D, ctypes.POINTER(_D),
                                       ctypes.POINTER(ctypes.c_longlong), _VP]),
     ("mpr_philox", _I, [_VP, ctypes.c_uint64, _VP, ctypes.c_size_t, _VP]),
+    ("mpr_strip_extremes", _I, [_VP, _VP, _I, _I, _I, _I, ctypes.POINTER(_D), _VP]),
+    ("mpr_strip_init", _I, [ctypes.POINTER(_VP), _VP, _VP, _I, _I, _I, _I, _D, _D, ctypes.POINTER(mpr_params),
+                            _VP]),
+    ("mpr_strip_pairs", _I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    ("mpr_strip_temperature", _I, [_VP, _D, ctypes.POINTER(_D)]),
+    ("mpr_strip_energy", _I, [_VP, ctypes.POINTER(_D)]),
+    ("mpr_strip_gaps", ctypes.c_longlong, [_VP]),
+    ("mpr_strip_begin", _I, [_VP, _I, _D, _D]),
+    ("mpr_strip_half_sweep", _I, [_VP, _I, _I, _VP]),
+    ("mpr_strip_control", _I, [_VP, _VP, _I, ctypes.POINTER(_I)]),
+    ("mpr_strip_row_bytes", ctypes.c_size_t, [_VP]),
+    ("mpr_strip_row", _I, [_VP, _I, _VP]),
+    ("mpr_strip_predict", _I, [_VP, _I, _VP]),
     ("mpr_get_state_batch", _I, [_VP, _I, _VP]),
     ("mpr_get_state64", _I, [_VP, _VP, ctypes.POINTER(ctypes.c_uint32)]),
     # include/mpr_net.h
@@ -315,6 +328,76 @@ def mpr_sample_energy_static(z, mask, W: int, H: int, q: float = 0.5, stream=Non
     if st != MPR_OK:
         raise MprError(st, lib().mpr_status_string(st).decode())
     return e.value, n.value
+
+
+# ---------------------------------------------------------------- row strips of one grid
+def mpr_strip_extremes(z, mask, W: int, Hb: int, row0: int, H_global: int, stream=None):
+    """(zmin, zmax, n_samples) of the strip's own rows (device buffers)."""
+    out = (ctypes.c_double * 3)()
+    st = lib().mpr_strip_extremes(_ptr(z), _ptr(mask), int(W), int(Hb), int(row0), int(H_global), out,
+                                  _stream(stream))
+    if st != MPR_OK:
+        raise MprError(st, lib().mpr_status_string(st).decode())
+    return out[0], out[1], int(out[2])
+
+
+def mpr_strip_init(z, mask, W: int, Hb: int, row0: int, H_global: int, zmin: float, zmax: float,
+                   params: mpr_params | None = None, stream=None):
+    ctx = ctypes.c_void_p()
+    st = lib().mpr_strip_init(ctypes.byref(ctx), _ptr(z), _ptr(mask), int(W), int(Hb), int(row0), int(H_global),
+                              float(zmin), float(zmax), ctypes.byref(params) if params is not None else None,
+                              _stream(stream))
+    if st != MPR_OK:
+        raise MprError(st, lib().mpr_status_string(st).decode())
+    return ctx
+
+
+def mpr_strip_pairs(ctx):
+    s, n = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().mpr_strip_pairs(ctx, ctypes.byref(s), ctypes.byref(n)))
+    return s.value, n.value
+
+
+def mpr_strip_temperature(ctx, e_s: float) -> float:
+    T = ctypes.c_double()
+    _check(ctx, lib().mpr_strip_temperature(ctx, float(e_s), ctypes.byref(T)))
+    return T.value
+
+
+def mpr_strip_energy(ctx) -> float:
+    H = ctypes.c_double()
+    _check(ctx, lib().mpr_strip_energy(ctx, ctypes.byref(H)))
+    return H.value
+
+
+def mpr_strip_gaps(ctx) -> int:
+    return int(lib().mpr_strip_gaps(ctx))
+
+
+def mpr_strip_begin(ctx, phase: int, H_total: float = 0.0, P_total: float = 0.0):
+    _check(ctx, lib().mpr_strip_begin(ctx, int(phase), float(H_total), float(P_total)))
+
+
+def mpr_strip_half_sweep(ctx, color: int, phase: int, totals):
+    _check(ctx, lib().mpr_strip_half_sweep(ctx, int(color), int(phase), _ptr(totals)))
+
+
+def mpr_strip_control(ctx, totals, phase: int, want_stop: bool = True):
+    stop = ctypes.c_int(0)
+    _check(ctx, lib().mpr_strip_control(ctx, _ptr(totals), int(phase), ctypes.byref(stop) if want_stop else None))
+    return bool(stop.value)
+
+
+def mpr_strip_row_bytes(ctx) -> int:
+    return int(lib().mpr_strip_row_bytes(ctx))
+
+
+def mpr_strip_row(ctx, which: int, buf):
+    _check(ctx, lib().mpr_strip_row(ctx, int(which), _ptr(buf)))
+
+
+def mpr_strip_predict(ctx, M: int, zhat):
+    _check(ctx, lib().mpr_strip_predict(ctx, int(M), _ptr(zhat)))
 
 
 def mpr_kernel_launches() -> int:
