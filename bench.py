@@ -113,11 +113,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
-# DRAM bytes per sweep of k_tile_sweep on this grid (dram__bytes_read.sum +
-# dram__bytes_write.sum of one ncu capture of the profile case sweep4096, divided by its 24
-# sweeps), per compiled tile configuration; valid for the kernel sources with this hash only.
-TILE_TRAFFIC_PER_SWEEP = {}
-TILE_TRAFFIC_SOURCE_HASH = ""
+# DRAM bytes per sweep of k_tile_sweep on this grid, per compiled tile configuration and
+# phase: dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the profile case
+# fill4096 (the relaxation launch, 201 sweeps, and the accumulating launch, 100 sweeps),
+# divided by the launch's sweeps; valid for the kernel sources with this hash only.
+TILE_TRAFFIC_PER_SWEEP = {2: {"relax": 66.239127e9 / 201, "acc": 35.691708e9 / 100}}
+TILE_TRAFFIC_SOURCE_HASH = "bc38498c637af18e"
 
 
 def tile_kernel_hash():
@@ -217,9 +218,12 @@ def run_reference(args, rank):
 def profile_case(name, tile_cfg=0):
     """sweep4096: 4096^2 bench grid, T = 0.05, 24 sweeps at a = 8 (one launch of the
     persistent sweep kernel; a few set-up kernels before it).
+    fill4096: the 4096^2 bench grid at its T-hat (set directly: no table build): the
+    relaxation (one launch of the sweep kernel) and M = 100 accumulating sweeps (one
+    launch), as in a timed step.
     copy4096: a plain device copy of the bytes a ping-pong sweep of the 4096^2 grid moves
-    (both unit-vector lattice buffers, 2 x 134 MB read, 2 x 134 MB written), timed with
-    CUDA events: the memory floor of a sweep that rewrites its whole lattice.
+    (one unit-vector lattice buffer of 134 MB read, one written), timed with CUDA events:
+    the memory floor of a sweep that rewrites its whole lattice.
     net4096: two warm-start forward passes (untrained network) on the 4096^2 bench grid.
     net128: two training steps of the warm-start network on a batch of 32 128^2 grids.
     net1024: two warm-start forward passes (untrained network) on a 1024^2 grid.
@@ -228,7 +232,7 @@ def profile_case(name, tile_cfg=0):
     import torch
     from paper_1811_01604_gb300 import mpr
     if name == "copy4096":
-        n = 2 * 2 * 4096 * 4096                     # float2 elements of two lattice buffers
+        n = 4096 * 4096                             # float2 elements of one lattice buffer (2 planes)
         src = torch.ones(2 * n, dtype=torch.float32, device="cuda")
         dst = torch.empty_like(src)
         ms = []
@@ -240,8 +244,8 @@ def profile_case(name, tile_cfg=0):
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
         t = statistics.median(ms[3:])
-        print(json.dumps({"profile_case": name, "bytes_read": 4 * 2 * n, "bytes_written": 4 * 2 * n,
-                          "median_ms": t, "GB_per_s": 2 * 4 * 2 * n / (t * 1e-3) / 1e9}))
+        print(json.dumps({"profile_case": name, "bytes_read": 8 * n, "bytes_written": 8 * n,
+                          "median_ms": t, "GB_per_s": 2 * 8 * n / (t * 1e-3) / 1e9}))
         return
     if name == "net128":
         B, S = 32, 128
@@ -281,6 +285,14 @@ def profile_case(name, tile_cfg=0):
             finally:
                 mpr.mpr_net_free(net)
             print(f"profile case {name}: done")
+            return
+        if name == "fill4096":
+            mpr.mpr_set_T(ctx, 9.869677377227477e-4)
+            eq = mpr.mpr_equilibrate(ctx)
+            out = torch.empty_like(z)
+            mpr.mpr_predict(ctx, M, out)
+            torch.cuda.synchronize()
+            print(f"profile case {name}: relaxation {eq.sweeps} sweeps, then {M}")
             return
         mpr.mpr_set_T(ctx, 0.05)
         st = mpr.mpr_sweep(ctx, 3 if name == "sweep64_4096" else 24, 8.0)
@@ -793,7 +805,8 @@ def main():
     ap.add_argument("--impl", default="mpr", choices=["mpr", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", default=None,
-                    choices=["sweep4096", "copy4096", "net4096", "net1024", "net128", "sweep64_4096"],
+                    choices=["sweep4096", "fill4096", "copy4096", "net4096", "net1024", "net128",
+                             "sweep64_4096"],
                     help="run a small fixed sweep workload for ncu instead of the benchmark")
     ap.add_argument("--workload", default="fill4096", choices=["fill4096", "config1024", "batch256", "warm1024",
                                                                 "warm4096", "chains1024", "ormodes1024", "dpsp"],
@@ -963,8 +976,9 @@ def main():
     sm_mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = sms * LANES_PER_SM * sm_mhz * 1e6                 # lane operations / s
     alu_achieved = ALU_OPS_PER_UPDATE * swt["gap_updates"] / (k_ms * 1e-3) if k_ms > 0 else 0.0
-    traffic_sweep = (TILE_TRAFFIC_PER_SWEEP.get(tune["tile_cfg"])
-                     if tile_kernel_hash() == TILE_TRAFFIC_SOURCE_HASH else None)
+    tr = TILE_TRAFFIC_PER_SWEEP.get(tune["tile_cfg"]) if tile_kernel_hash() == TILE_TRAFFIC_SOURCE_HASH else None
+    # per launch of the timed steps: each step is one relaxation launch and one of M sweeps
+    traffic_launch = ((sum(sweeps) * tr["relax"] + args.steps * M * tr["acc"]) / k_launches) if tr else None
 
     (dev_ms, e2e_ms), (dev_updates, e2e_updates) = reduce_over_ranks(
         [dev_ms, e2e_ms], [dev_updates, e2e_updates], dist, dev)
@@ -990,7 +1004,7 @@ def main():
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm,
-                         "traffic": (traffic_sweep * sweeps_total / k_launches) if traffic_sweep else None,
+                         "traffic": traffic_launch,
                          "kernel": "k_tile_sweep", "tile_cfg": tune["tile_cfg"],
                          "launches": swt["launches"], "ms_per_launch": k_ms / k_launches,
                          "bytes_per_launch": bytes_alg / k_launches,
@@ -1000,7 +1014,7 @@ def main():
                          "ms_per_sweep_fast": sweep_ms_fast,
                          "peak_source": f"{peak_src} hbm_gbs",
                          "frac_unit_vector_bytes": bytes_uv / (k_ms * 1e-3) / 1e9 / hbm if k_ms > 0 else None,
-                         "traffic_per_sweep": traffic_sweep,
+                         "traffic_per_sweep": ({"relax": tr["relax"], "acc": tr["acc"]} if tr else None),
                          "alu": {"ops_per_update": ALU_OPS_PER_UPDATE, "sms": sms,
                                  "lanes_per_sm": LANES_PER_SM, "sm_mhz": sm_mhz,
                                  "peak_ops": alu_peak, "achieved_ops": alu_achieved},
