@@ -246,6 +246,8 @@ struct GridCache {
     int cur_base;
     float neg_inv_T;
     long long pl0, pl1;
+    int stopped;                          // its relaxation has ended (seen in this launch)
+    unsigned skips;                       // items of stopped grids skipped by this block
 };
 
 // Energy changes are summed across the tiles of a grid in 64-bit fixed point (2^-28 units):
@@ -348,6 +350,7 @@ k_tile_sweep(const TileArgs A) {
         gc.sweep_base = __ldcg(&cp->sweep_base);
         gc.cur_base = __ldcg(&cp->cur_base);
         gc.neg_inv_T = __ldcg(&cp->neg_inv_T);
+        gc.stopped = A.relax ? ld_relaxed(&cp->stop) : 0;     // stays set once set
     };
     // thread 0, fixed window: publishes that the last item's tile has finished its sweep (its
     // interior is in the other buffer and it no longer reads its source buffer).  Deferred
@@ -379,6 +382,11 @@ k_tile_sweep(const TileArgs A) {
             float half_qd = A.half_qd_fixed;
             bool ok = true;
             if (A.relax) {
+                if (gc.stopped) {                                     // this grid has stopped
+                    // and every grid? (looked at every 16th skipped item)
+                    if ((++gc.skips & 15u) == 0u && ld_relaxed(A.live) <= 0) { sp.t = -1; return; }
+                    continue;
+                }
                 // ready once the control step of sweep sig - 1 is published (every block polls
                 // the same word, so gently), or the grid's relaxation (or every grid's) has
                 // ended, which is looked at every 8th poll
@@ -395,7 +403,10 @@ k_tile_sweep(const TileArgs A) {
                 });
                 fence_acq_rel();
                 if (ok && live <= 0) { sp.t = -1; return; }           // every grid has stopped
-                if (ok && ld_relaxed(&cp->stop)) continue;            // this grid has stopped
+                if (ok && ld_relaxed(&cp->stop)) {                    // this grid has stopped
+                    gc.stopped = 1;
+                    continue;
+                }
                 half_qd = __uint_as_float(ld_relaxed(reinterpret_cast<const unsigned*>(&cp->half_qd)));
             } else if (s > 0) {
                 // the halo: tile t and its 8 neighbours have finished sweep sig - 1; and the
@@ -495,6 +506,7 @@ k_tile_sweep(const TileArgs A) {
         s_kn = 0;
         s_pub_t = -1;
         gc.e = -1;
+        gc.skips = 0u;
         s_w0 = atomicAdd(A.sched, 1u);
         s_w1 = atomicAdd(A.sched, 1u);
         if (s_w0 < nitems) fetch_desc(s_w0);
