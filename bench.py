@@ -115,10 +115,10 @@ class ClockSampler:
 
 # DRAM bytes per sweep of k_tile_sweep on this grid, per compiled tile configuration and
 # phase: dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the profile case
-# fill4096 (the relaxation launch, 201 sweeps, and the accumulating launch, 100 sweeps),
+# fill4096 (the relaxation launch, 241 sweeps, and the accumulating launch, 100 sweeps),
 # divided by the launch's sweeps; valid for the kernel sources with this hash only.
-TILE_TRAFFIC_PER_SWEEP = {2: {"relax": 66.239127e9 / 201, "acc": 35.691708e9 / 100}}
-TILE_TRAFFIC_SOURCE_HASH = "bc38498c637af18e"
+TILE_TRAFFIC_PER_SWEEP = {2: {"relax": 79.430174e9 / 241, "acc": 35.685410e9 / 100}}
+TILE_TRAFFIC_SOURCE_HASH = "f9b05abc94d3a6f0"
 
 
 def tile_kernel_hash():
@@ -331,11 +331,21 @@ def run_batch(args):
         warmstart.train(net, sets, steps=args.train_steps, batch=32, lr=1e-3, seed=0)
         torch.cuda.synchronize()
 
+    # the tile shape is chosen once, by the autotuner in the first (untimed) fill, and
+    # passed in the parameters of every later fill, as for the single map
+    tuned = {}
+
     def batched(use_net=False):
         ctx = mpr.mpr_init_batch(zs, ms, prm, stream.cuda_stream)
         try:
             mpr.mpr_estimate_T(ctx)
-            tune = mpr.mpr_autotune(ctx)
+            if not tuned:
+                t0 = time.perf_counter()
+                tuned.update(mpr.mpr_autotune(ctx))
+                torch.cuda.synchronize()
+                tuned["autotune_s"] = time.perf_counter() - t0
+                prm.tile_cfg = tuned["tile_cfg"]
+            tune = tuned
             if use_net:
                 net.warmstart(ctx)
             mpr.mpr_equilibrate(ctx)
@@ -386,7 +396,8 @@ def run_batch(args):
     def sequential():
         for g, (z, m) in enumerate(zip(zs, ms)):
             H, W = z.shape
-            ctx = mpr.mpr_init(z, m, W, H, mpr.mpr_default_params(seed=4, M=Mb, chain=g),
+            ctx = mpr.mpr_init(z, m, W, H, mpr.mpr_default_params(seed=4, M=Mb, chain=g,
+                                                                  tile_cfg=prm.tile_cfg),
                                stream.cuda_stream)
             try:
                 mpr.mpr_set_T(ctx, info[g]["T"])

@@ -322,7 +322,6 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
     b.ents.assign(b.n_ent, EntryDesc{});
     size_t lat = 0;
     long long site0 = 0;
-    int maxH = 1;
     for (int e = 0; e < b.n_ent; ++e) {
         EntryDesc& E = b.ents[e];
         E.W = grids[e].W;
@@ -342,7 +341,6 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
         E.ngp = (double)E.W * (E.H - 1) + (double)E.H * (E.W - 1);
         E.site0 = same_grid ? 0 : site0;
         site0 += (long long)E.W * E.H;
-        maxH = std::max(maxH, E.H);
     }
     b.lat_elems = lat;
     CU(dalloc(&b.d_lat, lat * wide, st));
@@ -350,40 +348,37 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
     for (int e = 0; e < b.n_ent; ++e)
         CU(launch_pack(&b.ents[e], grids[e].z, grids[e].mask, grids[e].zmin, grids[e].scale, b.d_lat,
                        k0, k1, all_free, b.f64, st));
-    // gap lists: per-row counts, scan, scatter
+    // gap lists: per-row counts of both colours (2 H ints per entry, all entries in one
+    // buffer), scanned in place into row offsets; one read-back of the totals sizes the gap
+    // buffer, then every entry's list is scattered from its own offsets
+    std::vector<size_t> roff((size_t)b.n_ent + 1, 0);
+    for (int e = 0; e < b.n_ent; ++e) roff[e + 1] = roff[e] + (size_t)2 * b.ents[e].H;
     int* d_rows = nullptr;
     int* d_tot = nullptr;
-    CU(dalloc(&d_rows, (size_t)2 * maxH, st));
-    CU(dalloc(&d_tot, 2, st));
-    std::vector<std::vector<int>> row_off(b.n_ent);
+    CU(dalloc(&d_rows, roff[b.n_ent], st));
+    CU(dalloc(&d_tot, (size_t)2 * b.n_ent, st));
+    for (int e = 0; e < b.n_ent; ++e) {
+        CU(launch_gap_count(&b.ents[e], grids[e].mask, all_free, d_rows + roff[e], st));
+        CU(launch_scan_rows(d_rows + roff[e], b.ents[e].H, 2, d_tot + 2 * e, st));
+    }
+    std::vector<int> tot((size_t)2 * b.n_ent);
+    CU(cudaMemcpyAsync(tot.data(), d_tot, sizeof(int) * tot.size(), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
     size_t ng = 0;
-    std::vector<int> tot(2);
-    // counts first (so the gap buffer can be sized), one entry at a time
-    std::vector<std::vector<int>> offs(b.n_ent);
     for (int e = 0; e < b.n_ent; ++e) {
         EntryDesc& E = b.ents[e];
-        CU(launch_gap_count(&E, grids[e].mask, all_free, d_rows, st));
-        CU(launch_scan_rows(d_rows, E.H, 2, d_tot, st));
-        offs[e].resize((size_t)2 * E.H);
-        CU(cudaMemcpyAsync(offs[e].data(), d_rows, sizeof(int) * 2 * E.H, cudaMemcpyDeviceToHost, st));
-        CU(cudaMemcpyAsync(tot.data(), d_tot, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
-        CU(cudaStreamSynchronize(st));
-        E.ngap[0] = tot[0];
-        E.ngap[1] = tot[1];
-        E.P = tot[0] + tot[1];
+        E.ngap[0] = tot[2 * e];
+        E.ngap[1] = tot[2 * e + 1];
+        E.P = E.ngap[0] + E.ngap[1];
         E.gbase[0] = (long long)ng;
-        E.gbase[1] = (long long)(ng + tot[0]);
+        E.gbase[1] = (long long)(ng + E.ngap[0]);
         ng += (size_t)E.P;
     }
     b.n_gaps = ng;
     CU(dalloc(&b.d_gaps, ng, st));
     CU(dalloc(&b.d_acc, ng * wide, st));
-    for (int e = 0; e < b.n_ent; ++e) {
-        EntryDesc& E = b.ents[e];
-        CU(cudaMemcpyAsync(d_rows, offs[e].data(), sizeof(int) * 2 * E.H, cudaMemcpyHostToDevice, st));
-        CU(launch_gap_scatter(&E, grids[e].mask, all_free, d_rows, b.d_gaps, st));
-        CU(cudaStreamSynchronize(st));
-    }
+    for (int e = 0; e < b.n_ent; ++e)
+        CU(launch_gap_scatter(&b.ents[e], grids[e].mask, all_free, d_rows + roff[e], b.d_gaps, st));
     dfree(d_rows, st);
     dfree(d_tot, st);
     // sweep work lists
@@ -991,15 +986,16 @@ static mpr_status init_grids(mpr_ctx** out, int n, const float* const* z, const 
     unsigned long long* d_ns = nullptr;
     CUI(dalloc(&d_keys, (size_t)2 * n, ctx->st));
     CUI(dalloc(&d_ns, (size_t)n, ctx->st));
-    for (int i = 0; i < n; ++i) {
-        CUI(cudaMemsetAsync(d_keys + 2 * i, 0xFF, sizeof(unsigned), ctx->st));
-        CUI(cudaMemsetAsync(d_keys + 2 * i + 1, 0, sizeof(unsigned), ctx->st));
+    std::vector<unsigned> keys((size_t)2 * n);
+    for (int i = 0; i < n; ++i) {                 // identities of the min / max keys
+        keys[2 * i] = 0xFFFFFFFFu;
+        keys[2 * i + 1] = 0u;
     }
+    CUI(cudaMemcpyAsync(d_keys, keys.data(), sizeof(unsigned) * 2 * n, cudaMemcpyHostToDevice, ctx->st));
     CUI(cudaMemsetAsync(d_ns, 0, sizeof(unsigned long long) * n, ctx->st));
     for (int i = 0; i < n; ++i)
         CUI(launch_minmax(ctx->d_z + ctx->g[i].site0, ctx->d_mask + ctx->g[i].site0,
                           (long long)W[i] * H[i], d_keys + 2 * i, d_ns + i, ctx->st));
-    std::vector<unsigned> keys((size_t)2 * n);
     std::vector<unsigned long long> ns((size_t)n);
     CUI(cudaMemcpyAsync(keys.data(), d_keys, sizeof(unsigned) * 2 * n, cudaMemcpyDeviceToHost, ctx->st));
     CUI(cudaMemcpyAsync(ns.data(), d_ns, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, ctx->st));
@@ -1028,29 +1024,37 @@ static mpr_status init_grids(mpr_ctx** out, int n, const float* const* z, const 
         const mpr_status bs = batch_build(ctx, ctx->b, gi, 0, ctx->d_mask);
         if (bs != MPR_OK) return bail(bs);
     }
-    // Eq. 4, per grid (per-block partials added in block order on the host)
+    // Eq. 4, per grid: each grid's per-block partials in its own slots of one buffer (one
+    // block per row, at most 1024), read back once and added in block order on the host
+    std::vector<size_t> poff((size_t)n + 1, 0);
+    for (int i = 0; i < n; ++i) poff[i + 1] = poff[i] + (size_t)std::min(std::max(H[i], 1), 1024);
     double* d_ps = nullptr;
     unsigned long long* d_pc = nullptr;
-    CUI(dalloc(&d_ps, 1024, ctx->st));
-    CUI(dalloc(&d_pc, 1024, ctx->st));
+    CUI(dalloc(&d_ps, poff[n], ctx->st));
+    CUI(dalloc(&d_pc, poff[n], ctx->st));
     for (int i = 0; i < n; ++i) {
         GridInfo& G = ctx->g[i];
         int np = 0;
         CUI(launch_sample_energy(&ctx->b.ents[i], ctx->d_z + G.site0, ctx->d_mask + G.site0, G.scale,
-                                 ctx->prm.q, d_ps, d_pc, &np, ctx->prm.precision == MPR_PREC_F64, ctx->st));
-        std::vector<double> ps(np);
-        std::vector<unsigned long long> pc(np);
-        CUI(cudaMemcpyAsync(ps.data(), d_ps, sizeof(double) * np, cudaMemcpyDeviceToHost, ctx->st));
-        CUI(cudaMemcpyAsync(pc.data(), d_pc, sizeof(unsigned long long) * np, cudaMemcpyDeviceToHost, ctx->st));
-        CUI(cudaStreamSynchronize(ctx->st));
+                                 ctx->prm.q, d_ps + poff[i], d_pc + poff[i], &np,
+                                 ctx->prm.precision == MPR_PREC_F64, ctx->st));
+        if ((size_t)np != poff[i + 1] - poff[i]) return bail(MPR_ECUDA);
+    }
+    std::vector<double> ps(poff[n]);
+    std::vector<unsigned long long> pc(poff[n]);
+    CUI(cudaMemcpyAsync(ps.data(), d_ps, sizeof(double) * poff[n], cudaMemcpyDeviceToHost, ctx->st));
+    CUI(cudaMemcpyAsync(pc.data(), d_pc, sizeof(unsigned long long) * poff[n], cudaMemcpyDeviceToHost, ctx->st));
+    CUI(cudaStreamSynchronize(ctx->st));
+    dfree(d_ps, ctx->st);
+    dfree(d_pc, ctx->st);
+    for (int i = 0; i < n; ++i) {
+        GridInfo& G = ctx->g[i];
         double sum = 0.0;
         unsigned long long cnt = 0;
-        for (int k = 0; k < np; ++k) { sum += ps[k]; cnt += pc[k]; }
+        for (size_t k = poff[i]; k < poff[i + 1]; ++k) { sum += ps[k]; cnt += pc[k]; }
         G.n_sp = (long long)cnt;
         G.e_s = cnt ? -sum / (double)cnt : 0.0;
     }
-    dfree(d_ps, ctx->st);
-    dfree(d_pc, ctx->st);
 #undef CUI
     *out = ctx;
     return MPR_OK;
@@ -1193,15 +1197,22 @@ static mpr_status predict_all(mpr_ctx* ctx, int M, float* const* out) {
     if (s != MPR_OK) return s;
     CU(cudaMemcpyAsync(ctx->d_out, ctx->d_z, (size_t)ctx->n_sites * sizeof(float),
                        cudaMemcpyDeviceToDevice, ctx->st));
-    for (size_t i = 0; i < ctx->g.size(); ++i) {
-        const GridInfo& G = ctx->g[i];
-        if (b.tiled)
-            CU(launch_tile_predict_out(b.tcfg, b.d_tiles, b.d_cnts, b.d_lists, b.d_tacc, b.d_ents,
-                                       b.ents[i].tile0, b.ents[i].ntiles, M, ctx->prm.q, G.zmin,
-                                       G.zmax, 1, 0, ctx->d_out, ctx->st));
-        else
+    if (b.tiled) {
+        // one launch over the tiles of every grid, each grid's (z_min, z_max) from zr
+        std::vector<double2> zr(ctx->g.size());
+        for (size_t i = 0; i < ctx->g.size(); ++i) zr[i] = make_double2(ctx->g[i].zmin, ctx->g[i].zmax);
+        double2* d_zr = nullptr;
+        CU(dalloc(&d_zr, zr.size(), ctx->st));
+        CU(cudaMemcpyAsync(d_zr, zr.data(), sizeof(double2) * zr.size(), cudaMemcpyHostToDevice, ctx->st));
+        CU(launch_tile_predict_out(b.tcfg, b.d_tiles, b.d_cnts, b.d_lists, b.d_tacc, b.d_ents, 0, b.ntiles, M,
+                                   ctx->prm.q, 0.0, 0.0, d_zr, 1, 0, ctx->d_out, ctx->st));
+        dfree(d_zr, ctx->st);
+    } else {
+        for (size_t i = 0; i < ctx->g.size(); ++i) {
+            const GridInfo& G = ctx->g[i];
             CU(launch_predict_out(&b.ents[i], b.d_lat, b.d_gaps, b.d_acc, M, ctx->prm.q, G.zmin,
                                   G.zmax, ctx->d_out + G.site0, b.f64, ctx->st));
+        }
     }
     for (size_t i = 0; i < ctx->g.size(); ++i) {
         const GridInfo& G = ctx->g[i];
@@ -1276,7 +1287,7 @@ mpr_status mpr_predict_chains(mpr_ctx* ctx, int K, int burn_in, int M_per_chain,
         const int nt = ab.ents[0].ntiles;
         if (e == cudaSuccess)
             e = launch_tile_predict_out(ab.tcfg, ab.d_tiles, ab.d_cnts, ab.d_lists, ab.d_tacc, ab.d_ents, 0,
-                                        nt, M_per_chain, ctx->prm.q, G.zmin, G.zmax, K, nt,
+                                        nt, M_per_chain, ctx->prm.q, G.zmin, G.zmax, nullptr, K, nt,
                                         ctx->d_out + G.site0, ctx->st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(zhat, ctx->d_out + G.site0, (size_t)G.W * G.H * sizeof(float),

@@ -584,10 +584,11 @@ cudaError_t launch_tile_sync(const TileDesc* tiles, int ntiles, Ctl* ctl, int n_
 // *live <- number of grids whose relaxation has not stopped
 cudaError_t launch_count_live(const Ctl* ctl, int n_ent, int* live, cudaStream_t st);
 // K > 1: the angle sums of K chains of one grid, chain c's tiles at tile + c * chain_tiles.
+// zr (device, one (z_min, z_max) per entry) replaces zmin, zmax when not null.
 cudaError_t launch_tile_predict_out(int cfg, const TileDesc* tiles, const TileCnt* cnts,
                                     const uint16_t* lists, const float* acc, const EntryDesc* ents,
                                     int tile0, int ntiles, int M, double q, double zmin, double zmax,
-                                    int K, int chain_tiles, float* zhat, cudaStream_t st);
+                                    const double2* zr, int K, int chain_tiles, float* zhat, cudaStream_t st);
 
 // sweeps (mpr_sweep.cu)
 cudaError_t launch_half_sweep(const SweepArgs& a, int color, int trig, cudaStream_t st);

@@ -248,6 +248,8 @@ struct GridCache {
     long long pl0, pl1;
     int stopped;                          // its relaxation has ended (seen in this launch)
     unsigned skips;                       // items of stopped grids skipped by this block
+    uint32_t seen;                        // a sweep counter of the grid this thread acquired
+    float seen_hqd;                       // relaxation: the window of sweep `seen`
 };
 
 // Energy changes are summed across the tiles of a grid in 64-bit fixed point (2^-28 units):
@@ -316,7 +318,8 @@ k_tile_sweep(const TileArgs A) {
     __shared__ GridCache gc;
     __shared__ int s_fail, s_flush, s_ke, s_kn, s_last, s_pub_t;
     __shared__ uint32_t s_ksig, s_pub_sig;
-    __shared__ unsigned s_w0, s_w1;
+    __shared__ unsigned s_w0;
+    unsigned w1 = 0u;                     // thread 0: the item after s_w0 (an atomic in flight)
     __shared__ long long s_fx[NT];
     __shared__ unsigned s_nat[NT];
     constexpr uint32_t kBytes = 2u * G::RH * G::RW * sizeof(float2);
@@ -324,8 +327,9 @@ k_tile_sweep(const TileArgs A) {
     const unsigned ntiles = (unsigned)A.ntiles;
     const unsigned nitems = (unsigned)A.nsweeps * ntiles;
 
-    // thread 0 only: item s_w0 is next (its descriptor is on its way into dnext), s_w1 the
-    // one after (taken from the counter an item ahead, so staging never waits on it)
+    // thread 0 only: item s_w0 is next (its descriptor is on its way into dnext), w1 the
+    // one after (taken from the counter an item ahead and kept in a register, so staging
+    // never waits on the atomic)
     auto fetch_desc = [&](unsigned w) {
         const TileDesc* src = A.desc + (w % ntiles);
         asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(&dnext)), "l"(src) : "memory");
@@ -351,6 +355,8 @@ k_tile_sweep(const TileArgs A) {
         gc.cur_base = __ldcg(&cp->cur_base);
         gc.neg_inv_T = __ldcg(&cp->neg_inv_T);
         gc.stopped = A.relax ? ld_relaxed(&cp->stop) : 0;     // stays set once set
+        gc.seen = gc.sweep_base;
+        gc.seen_hqd = -1.0f;                                  // none yet
     };
     // thread 0, fixed window: publishes that the last item's tile has finished its sweep (its
     // interior is in the other buffer and it no longer reads its source buffer).  Deferred
@@ -370,10 +376,10 @@ k_tile_sweep(const TileArgs A) {
             if (w >= nitems) { sp.t = -1; return; }
             asm volatile("cp.async.wait_all;" ::: "memory");          // the descriptor of w
             const TileDesc d = dnext;
-            const unsigned wn = s_w1;
+            const unsigned wn = w1;
             s_w0 = wn;
             if (wn < nitems) fetch_desc(wn);
-            s_w1 = atomicAdd(A.sched, 1u);
+            w1 = atomicAdd(A.sched, 1u);
             const int e = d.entry;
             if (e != gc.e) load_grid(e);
             const unsigned s = w / ntiles;
@@ -387,30 +393,42 @@ k_tile_sweep(const TileArgs A) {
                     if ((++gc.skips & 15u) == 0u && ld_relaxed(A.live) <= 0) { sp.t = -1; return; }
                     continue;
                 }
-                // ready once the control step of sweep sig - 1 is published (every block polls
-                // the same word, so gently), or the grid's relaxation (or every grid's) has
-                // ended, which is looked at every 8th poll
-                int live = 1;
-                unsigned polls = 0;
-                ok = bounded_wait(A, [&] {
-                    if ((int)(ld_relaxed(&cp->sweep) - sig) >= 0) return true;
-                    if ((++polls & 7u) == 0u) {
-                        live = ld_relaxed(A.live);
-                        if (live <= 0 || ld_relaxed(&cp->stop) != 0) return true;
+                if (sig == gc.seen && gc.seen_hqd > 0.0f) {
+                    // this thread already acquired the control step of sweep sig - 1 (and it
+                    // did not end the relaxation): nothing to wait for or load again
+                    half_qd = gc.seen_hqd;
+                } else {
+                    // ready once the control step of sweep sig - 1 is published (every
+                    // block polls the same word, so gently), or the grid's relaxation (or
+                    // every grid's) has ended, which is looked at every 8th poll
+                    int live = 1;
+                    unsigned polls = 0;
+                    ok = bounded_wait(A, [&] {
+                        if ((int)(ld_relaxed(&cp->sweep) - sig) >= 0) return true;
+                        if ((++polls & 7u) == 0u) {
+                            live = ld_relaxed(A.live);
+                            if (live <= 0 || ld_relaxed(&cp->stop) != 0) return true;
+                        }
+                        __nanosleep(64);
+                        return false;
+                    });
+                    fence_acq_rel();
+                    if (ok && live <= 0) { sp.t = -1; return; }       // every grid has stopped
+                    if (ok && ld_relaxed(&cp->stop)) {                // this grid has stopped
+                        gc.stopped = 1;
+                        continue;
                     }
-                    __nanosleep(64);
-                    return false;
-                });
-                fence_acq_rel();
-                if (ok && live <= 0) { sp.t = -1; return; }           // every grid has stopped
-                if (ok && ld_relaxed(&cp->stop)) {                    // this grid has stopped
-                    gc.stopped = 1;
-                    continue;
+                    half_qd = __uint_as_float(ld_relaxed(reinterpret_cast<const unsigned*>(&cp->half_qd)));
+                    if (ok) {                                         // kept for the sweep's other tiles
+                        gc.seen = sig;
+                        gc.seen_hqd = half_qd;
+                    }
                 }
-                half_qd = __uint_as_float(ld_relaxed(reinterpret_cast<const unsigned*>(&cp->half_qd)));
-            } else if (s > 0) {
+            } else if (s > 0 && (int)(gc.seen - sig) < 0) {
                 // the halo: tile t and its 8 neighbours have finished sweep sig - 1; and the
-                // slot of sweep sig was emptied by the control step of sweep sig - kSlots
+                // slot of sweep sig was emptied by the control step of sweep sig - kSlots.
+                // (Nothing to wait for once this thread has acquired a sweep counter >= sig:
+                // the control step of sweep sig - 1 follows every tile of that sweep.)
                 const int i = d.t - gc.tile0, ty = i / gc.tpr, tx = i - ty * gc.tpr;
                 const uint32_t slot_free = sig - (uint32_t)(kSlots - 1);
                 auto ready = [&] {
@@ -421,7 +439,8 @@ k_tile_sweep(const TileArgs A) {
                         v[k] = (yy >= 0 && yy < gc.ntr && xx >= 0 && xx < gc.tpr)
                                    ? ld_relaxed(A.tdone + gc.tile0 + yy * gc.tpr + xx) : sig;
                     }
-                    const unsigned cs = s >= (unsigned)(kSlots - 1) ? ld_relaxed(&cp->sweep) : slot_free;
+                    const unsigned cs = ld_relaxed(&cp->sweep);
+                    if ((int)(cs - gc.seen) > 0) gc.seen = cs;        // acquired by the fence below
                     bool r = (int)(cs - slot_free) >= 0;
 #pragma unroll
                     for (int k = 0; k < 9; ++k) r = r && (int)(v[k] - sig) >= 0;
@@ -508,7 +527,7 @@ k_tile_sweep(const TileArgs A) {
         gc.e = -1;
         gc.skips = 0u;
         s_w0 = atomicAdd(A.sched, 1u);
-        s_w1 = atomicAdd(A.sched, 1u);
+        w1 = atomicAdd(A.sched, 1u);
         if (s_w0 < nitems) fetch_desc(s_w0);
     }
     s_fx[threadIdx.x] = 0;
@@ -732,17 +751,23 @@ __global__ void k_count_live(const Ctl* __restrict__ ctl, int n_ent, int* live) 
 
 // zhat at the gap sites of every tile (same mean and inverse map as the list path).  With
 // K > 1 the angle sums of K chains of the same grid are added: chain c's copy of tile t is
-// tile t + c * chain_tiles (every chain has the same tiles and lists).
+// tile t + c * chain_tiles (every chain has the same tiles and lists).  zr, when given, holds
+// each entry's (z_min, z_max), so that one launch serves the tiles of many grids.
 template <int TH, int TW>
 __global__ void k_tile_predict_out(const TileDesc* __restrict__ tiles, const TileCnt* __restrict__ cnts,
                                    const uint16_t* __restrict__ lists, const float* __restrict__ acc,
                                    const EntryDesc* __restrict__ ents, int M, double q, double zmin,
-                                   double zmax, int K, int chain_tiles, float* __restrict__ zhat) {
+                                   double zmax, const double2* __restrict__ zr, int K, int chain_tiles,
+                                   float* __restrict__ zhat) {
     using G = Geo<TH, TW>;
     const int tile = blockIdx.x;
     const TileDesc td = tiles[tile];
     const EntryDesc E = ents[td.entry];
     const TileCnt cnt = cnts[tile];
+    if (zr) {
+        zmin = zr[td.entry].x;
+        zmax = zr[td.entry].y;
+    }
     const uint16_t* list = lists + (long long)tile * G::LIST;
     const float* a = acc + (long long)tile * G::ACC;
     const long long cstride = (long long)chain_tiles * G::ACC;
@@ -930,11 +955,11 @@ cudaError_t launch_count_live(const Ctl* ctl, int n_ent, int* live, cudaStream_t
 #define MPR_CFG_OUT(id, th, tw, nt, mb) \
     case id: k_tile_predict_out<th, tw><<<ntiles, 256, 0, st>>>( \
         tiles + tile0, cnts + tile0, lists + (long long)tile0 * g.list, acc + (long long)tile0 * g.acc, \
-        ents, M, q, zmin, zmax, K, chain_tiles, zhat); break;
+        ents, M, q, zmin, zmax, zr, K, chain_tiles, zhat); break;
 cudaError_t launch_tile_predict_out(int cfg, const TileDesc* tiles, const TileCnt* cnts,
                                     const uint16_t* lists, const float* acc, const EntryDesc* ents,
                                     int tile0, int ntiles, int M, double q, double zmin, double zmax,
-                                    int K, int chain_tiles, float* zhat, cudaStream_t st) {
+                                    const double2* zr, int K, int chain_tiles, float* zhat, cudaStream_t st) {
     if (ntiles == 0) return cudaSuccess;
     count_launches(1, st);
     const TileGeom g = tile_geom(cfg);
