@@ -423,6 +423,7 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
         ctl[e].neg_inv_T = grids[e].T > 0.0 ? (float)(-1.0 / grids[e].T) : 0.0f;
     }
     CU(dalloc(&b.d_ctl, b.n_ent, st));
+    for (auto& cc : ctl) ctl_set_go(cc);
     CU(cudaMemcpyAsync(b.d_ctl, ctl.data(), b.n_ent * sizeof(Ctl), cudaMemcpyHostToDevice, st));
     {
         const mpr_status ss = sync_tiles(ctx, b);
@@ -559,7 +560,7 @@ mpr_status enqueue_sweeps(mpr_ctx* ctx, Batch& b, cudaStream_t s, int n, int mod
         CU(launch_half_sweep(A, 1, p.trig_mode, s));
         CU(launch_control(b.d_ctl, b.d_part, b.d_ents, b.n_ent, mode, p.A_targ, p.k_a, p.n_f,
                           p.n_fit, p.i_max, b.d_ehist, b.ehist_stride,
-                          count_active ? b.d_active + (i % b.gsweeps) : nullptr, s));
+                          count_active ? b.d_active + (i % b.gsweeps) : nullptr, b.f64, s));
     }
     return MPR_OK;
 }
@@ -783,6 +784,7 @@ mpr_status reset_relax(mpr_ctx* ctx, Batch& b) {
         c[e].nsamp = 0;
         c[e].half_qd = (float)(0.5 * kTwoPi * b.ents[e].q / 1.0);
     }
+    for (auto& cc : c) ctl_set_go(cc);
     CU(cudaMemcpyAsync(b.d_ctl, c.data(), sizeof(Ctl) * b.n_ent, cudaMemcpyHostToDevice, ctx->st));
     return reset_tracked_energy(ctx, b);
 }
@@ -1081,6 +1083,7 @@ static mpr_status set_T_all(mpr_ctx* ctx, const std::vector<double>& T) {
         c[i].neg_inv_T = (float)(-1.0 / T[i]);
         ctx->g[i].T = T[i];
     }
+    for (auto& cc : c) ctl_set_go(cc);
     CU(cudaMemcpyAsync(ctx->b.d_ctl, c.data(), sizeof(Ctl) * c.size(), cudaMemcpyHostToDevice, ctx->st));
     CU(cudaStreamSynchronize(ctx->st));
     ctx->T_set = true;
@@ -1271,6 +1274,7 @@ mpr_status mpr_predict_chains(mpr_ctx* ctx, int K, int burn_in, int M_per_chain,
             ck[k].cur_base = 0;
             ck[k].sweep_base = ck[k].sweep;
         }
+        for (auto& cc : ck) ctl_set_go(cc);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(ab.d_ctl, ck.data(), sizeof(Ctl) * K, cudaMemcpyHostToDevice, ctx->st);
         if (e == cudaSuccess && sync_tiles(ctx, ab) != MPR_OK) e = cudaErrorUnknown;
@@ -1428,6 +1432,7 @@ mpr_status mpr_set_state(mpr_ctx* ctx, const float* phi, uint32_t sweep) {
     c[0].sweep = sweep;
     c[0].sweep_base = sweep;
     c[0].cur_base = c[0].cur;
+    for (auto& cc : c) ctl_set_go(cc);
     CU(cudaMemcpyAsync(ctx->b.d_ctl, c.data(), sizeof(Ctl), cudaMemcpyHostToDevice, ctx->st));
     s = sync_tiles(ctx, ctx->b);
     if (s != MPR_OK) return s;
@@ -1486,6 +1491,7 @@ mpr_status mpr_autotune(mpr_ctx* ctx, int* tile_cfg, int* graph_sweeps, double* 
         if (s == MPR_OK && ms < best_ms) { best_ms = ms; best = cfg; }
         CU(cudaMemcpyAsync(b.d_lat, snap0, bytes, cudaMemcpyDeviceToDevice, ctx->st));
         CU(cudaMemcpyAsync(b.d_lat2, snap1, bytes, cudaMemcpyDeviceToDevice, ctx->st));
+        for (auto& cc : c0) ctl_set_go(cc);
         CU(cudaMemcpyAsync(b.d_ctl, c0.data(), sizeof(Ctl) * c0.size(), cudaMemcpyHostToDevice, ctx->st));
         s = sync_tiles(ctx, b);
         if (s != MPR_OK) return s;
@@ -1784,6 +1790,7 @@ mpr_status mpr_strip_begin(mpr_ctx* ctx, int phase, double H_total, double P_tot
         c[0].nsamp = 0;
         c[0].half_qd = (float)(0.5 * kTwoPi * b.ents[0].q / 1.0);
         c[0].H = H_total;
+        for (auto& cc : c) ctl_set_go(cc);
         CU(cudaMemcpyAsync(b.d_ctl, c.data(), sizeof(Ctl), cudaMemcpyHostToDevice, ctx->st));
     } else {                                 // step 6: the angle sums start at zero
         CU(cudaMemsetAsync(b.d_acc, 0, sizeof(float) * (b.f64 ? 2 : 1) * std::max<size_t>(b.n_gaps, 1), ctx->st));
@@ -1801,7 +1808,7 @@ mpr_status mpr_strip_half_sweep(mpr_ctx* ctx, int color, int phase, double* tota
     const bool relax = phase == 0;
     const SweepArgs A = sweep_args(ctx, b, relax, ctx->prm.a_eq, relax, !relax);
     CU(launch_half_sweep(A, color, ctx->prm.trig_mode, ctx->st));
-    CU(launch_strip_partials(b.d_part[color], b.nblk[color], color, totals, ctx->st));
+    CU(launch_strip_partials(b.d_part[color], b.nblk[color], color, totals, b.f64, ctx->st));
     return MPR_OK;
 }
 

@@ -71,14 +71,19 @@ struct Ctl {                  // mutable per-entry control state (Algorithm 2)
     // written by the host with every change of `sweep` and by the last block of a launch
     uint32_t sweep_base;
     int cur_base;
-    // global sweep counter (Philox counter word 1); alone in the last 8-byte word, since
-    // the tile path publishes it last, with release semantics, after the other fields
+    // global sweep counter (Philox counter word 1) and, in the same 8-byte word, the
+    // window of that sweep, or -1 once the relaxation has stopped (ctl_set_go): the tile
+    // path publishes this word last, with release semantics, after the other fields, so a
+    // block learns with one load whether sweep `sweep` runs and with which window
     uint32_t sweep;
-    int _pad1;
+    float go_hqd;
 };
 
+// Keeps go_hqd in step with half_qd and stop (after every change of either).
+__host__ __device__ inline void ctl_set_go(Ctl& c) { c.go_hqd = c.stop ? -1.0f : c.half_qd; }
+
 struct Part {                 // one sweep block's energy change and acceptance count
-    double dH;
+    double dH;                // FP32 paths: a whole number of kDEUnit (exactly representable)
     unsigned nacc;
     unsigned _pad;
 };
@@ -215,6 +220,21 @@ __device__ __forceinline__ uint4 philox10(uint4 c, const RoundKeys& rk) {
 }
 
 __device__ __forceinline__ float u24f(uint32_t x) { return (float)(x >> 8) * 0x1p-24f; }
+
+// The FP32 paths add energy changes in fixed point: each site's change is rounded to a
+// whole number of kDEUnit = 2^-17 where it is computed, and those integers are summed.
+// Integer sums are exact and associative, so a sweep's total is the same whichever
+// kernel, tile shape, thread count or strip decomposition produced it.  The rounding is
+// one FP32 addition: for |d| < 32, d + 96 lies in [64, 128), where FP32 numbers are spaced
+// 2^-17 apart, so the sum is d rounded to nearest (even) and its bit pattern minus that of
+// 96 is the rounded value in units.  |dH| <= 16 per update (8 from the proposal, 8 more
+// from the printed reflection), so one site is below 2^21 units and 511 sites fit in a
+// 32-bit partial.
+constexpr double kDEUnit = 1.0 / 131072.0;
+constexpr int kDEMaxSites32 = 511;
+__device__ __forceinline__ int de_fixed(float d) { return __float_as_int(__fadd_rn(d, 96.0f)) - 0x42C00000; }
+// a total held as a double (a whole number of units below 2^53) back to its integer
+__device__ __forceinline__ long long de_units(double d) { return __double2ll_rn(d * 131072.0); }
 
 // sin and cos of |x| <= pi/4 by their Taylor series (coefficients 1/n!), to degree 9
 // and 10: truncation error below 2e-9, far under FP32 rounding.
@@ -503,14 +523,31 @@ __device__ __forceinline__ void control_step(Ctl& c, const EntryDesc& E, double 
         if (c.i >= n_fit && c.i % n_f == 0) {                              // 5.4
             const double* w = eh + (c.i + 2 - n_fit);
             const double tbar = 0.5 * (double)(n_fit - 1);
+            // least-squares slope of the last n_fit values; the history is read in chunks
+            // of 8 independent loads and added in index order
             double ebar = 0.0;
-            for (int t = 0; t < n_fit; ++t) ebar += w[t];
+            for (int t0 = 0; t0 < n_fit; t0 += 8) {
+                double v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = t0 + j < n_fit ? w[t0 + j] : 0.0;
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (t0 + j < n_fit) ebar += v[j];
+            }
             ebar /= (double)n_fit;
             double num = 0.0, den = 0.0;
-            for (int t = 0; t < n_fit; ++t) {
-                const double dt = (double)t - tbar;
-                num += dt * (w[t] - ebar);
-                den += dt * dt;
+            for (int t0 = 0; t0 < n_fit; t0 += 8) {
+                double v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = t0 + j < n_fit ? w[t0 + j] : 0.0;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (t0 + j < n_fit) {
+                        const double dt = (double)(t0 + j) - tbar;
+                        num += dt * (v[j] - ebar);
+                        den += dt * dt;
+                    }
+                }
             }
             c.k = num / den;
         }
@@ -523,6 +560,7 @@ __device__ __forceinline__ void control_step(Ctl& c, const EntryDesc& E, double 
             c.stop = 1;
             c.converged = c.k >= 0.0 ? 1 : 0;
         }
+        ctl_set_go(c);
         return;
     }
     c.H += dH;
@@ -534,6 +572,7 @@ __device__ __forceinline__ void control_step(Ctl& c, const EntryDesc& E, double 
     }
     c.sweep += 1u;
     if (flip_cur) c.cur ^= 1;
+    ctl_set_go(c);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -594,7 +633,7 @@ cudaError_t launch_tile_predict_out(int cfg, const TileDesc* tiles, const TileCn
 cudaError_t launch_half_sweep(const SweepArgs& a, int color, int trig, cudaStream_t st);
 cudaError_t launch_control(Ctl* ctl, Part* const part[2], const EntryDesc* ents, int n_ent,
                            int mode, double A_targ, double k_a, int n_f, int n_fit, int i_max,
-                           double* ehist, int ehist_stride, int* active, cudaStream_t st);
+                           double* ehist, int ehist_stride, int* active, bool f64, cudaStream_t st);
 // Eq. 2 of one grid: per-block partials then a fixed-order sum into *out (deterministic).
 // [y_a, y_b): only the bonds of the colour-0 sites of these rows (every bond has one
 // colour-0 end); the whole grid by default.
@@ -602,8 +641,10 @@ cudaError_t launch_energy(const EntryDesc* e_host, const float2* lat, double* sc
                           int scratch_len, double* out, bool f64, cudaStream_t st, int y_a = 0,
                           int y_b = -1);
 // Row strips: out[0] (color 0: =, color 1: +=) the colour's accepted energy change, out[1]
-// its acceptance count, summed over the half-sweep blocks in block order.
-cudaError_t launch_strip_partials(const Part* part, int nblk, int color, double* out, cudaStream_t st);
+// its acceptance count, summed over the half-sweep blocks in block order (FP32 partials as
+// exact integer sums of kDEUnit).
+cudaError_t launch_strip_partials(const Part* part, int nblk, int color, double* out, bool f64,
+                                  cudaStream_t st);
 // Row strips: one control step of entry 0 from the totals {dH, n_acc} of all strips, with
 // the whole grid's gap count P and bond count ngp; *stop_dev <- the relaxation has ended.
 cudaError_t launch_strip_control(Ctl* ctl, const EntryDesc* e_host, double P, double ngp, const double* tot,

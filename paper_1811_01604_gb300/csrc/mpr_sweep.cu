@@ -28,7 +28,8 @@ k_half_sweep(const SweepArgs A, const int color) {
     const float2* __restrict__ oth = A.lat + (color ? E->plane[0] : E->plane[1]);
     float* __restrict__ acc = ACC ? A.acc + gb : nullptr;
 
-    float dE = 0.0f;
+    static_assert(kSweepItems <= kDEMaxSites32, "32-bit energy partial");
+    int dE = 0;                                   // fixed point, whole kDEUnit per site
     unsigned nacc = 0;
 #pragma unroll
     for (int it = 0; it < kSweepItems; ++it) {
@@ -49,29 +50,32 @@ k_half_sweep(const SweepArgs A, const int color) {
             bool accepted;
             float Fx = 0.0f, Fy = 0.0f;
             if (A.or_mode == OR_LITERAL) literal_field(nu, nd, nl, nr, Fx, Fy);
-            dE += hybrid_update<TRIG, GQ>(v, C, S, Fx, Fy, hq, u24f(rnd.y), kx, A.or_mode, accepted, cQ, sQ);
+            dE += de_fixed(hybrid_update<TRIG, GQ>(v, C, S, Fx, Fy, hq, u24f(rnd.y), kx, A.or_mode, accepted,
+                                                   cQ, sQ));
             nacc += accepted ? 1u : 0u;
             own[k] = v;
             if (ACC) acc[g] += angle_upper(v.x, v.y);
         }
     }
-    // energy change and acceptance count: warp shuffle, then a fixed-order block sum
-    __shared__ float s_dE[kSweepThreads / 32];
+    // energy change (exact integer sums) and acceptance count of the block
+    __shared__ long long s_dE[kSweepThreads / 32];
     __shared__ unsigned s_na[kSweepThreads / 32];
-    dE = warp_sum(dE);
+    long long dEw = dE;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dEw += __shfl_xor_sync(0xffffffffu, dEw, o);
     nacc = warp_sum(nacc);
     if ((threadIdx.x & 31) == 0) {
-        s_dE[threadIdx.x >> 5] = dE;
+        s_dE[threadIdx.x >> 5] = dEw;
         s_na[threadIdx.x >> 5] = nacc;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
+        long long t = 0;
         unsigned na = 0;
 #pragma unroll
-        for (int i = 0; i < kSweepThreads / 32; ++i) { t += (double)s_dE[i]; na += s_na[i]; }
+        for (int i = 0; i < kSweepThreads / 32; ++i) { t += s_dE[i]; na += s_na[i]; }
         Part p;
-        p.dH = t;
+        p.dH = (double)t * kDEUnit;
         p.nacc = na;
         p._pad = 0;
         (color ? A.part[1] : A.part[0])[blockIdx.x] = p;
@@ -159,33 +163,41 @@ constexpr int kCtlThreads = 128;
 __global__ void __launch_bounds__(kCtlThreads)
 k_control(Ctl* ctl, Part* part0, Part* part1, const EntryDesc* __restrict__ ents, int mode,
           double A_targ, double k_a, int n_f, int n_fit, int i_max, double* ehist,
-          int ehist_stride, int* active) {
+          int ehist_stride, int* active, int f64_parts) {
     __shared__ double s_dH[kCtlThreads];
     __shared__ unsigned long long s_na[kCtlThreads];
+    __shared__ long long s_fx[kCtlThreads];
     const int e = blockIdx.x;
     const EntryDesc E = ents[e];
+    // FP32 partials are whole numbers of kDEUnit: added as integers (exact); FP64 ones as
+    // doubles in a fixed order
+    const bool fixed = !f64_parts;
     double dH = 0.0;
+    long long fx = 0;
     unsigned long long na = 0;
     for (int c = 0; c < 2; ++c) {
         const Part* p = c ? part1 + E.blk0[1] : part0 + E.blk0[0];
         const int nb = c ? E.nblk[1] : E.nblk[0];
         for (int b = threadIdx.x; b < nb; b += kCtlThreads) {
-            dH += p[b].dH;
+            if (fixed) fx += de_units(p[b].dH);
+            else dH += p[b].dH;
             na += p[b].nacc;
         }
     }
+    s_fx[threadIdx.x] = fx;
     s_dH[threadIdx.x] = dH;
     s_na[threadIdx.x] = na;
     __syncthreads();
     for (int o = kCtlThreads / 2; o > 0; o >>= 1) {
         if ((int)threadIdx.x < o) {
             s_dH[threadIdx.x] += s_dH[threadIdx.x + o];
+            s_fx[threadIdx.x] += s_fx[threadIdx.x + o];
             s_na[threadIdx.x] += s_na[threadIdx.x + o];
         }
         __syncthreads();
     }
     if (threadIdx.x != 0) return;
-    dH = s_dH[0];
+    dH = fixed ? (double)s_fx[0] * kDEUnit : s_dH[0];
     na = s_na[0];
     Ctl c = ctl[e];
     control_step(c, E, dH, na, mode, A_targ, k_a, n_f, n_fit, i_max,
@@ -252,12 +264,16 @@ __global__ void k_set_tracked_energy(Ctl* ctl, const double* H, int n_ent) {
 
 // Row strips: the half-sweep blocks' energy changes and acceptance counts of one colour,
 // added in block order (one thread: the order is fixed).
-__global__ void k_strip_partials(const Part* __restrict__ part, int nblk, int color, double* out) {
+__global__ void k_strip_partials(const Part* __restrict__ part, int nblk, int color, double* out,
+                                 int f64_parts) {
     double dH = 0.0, na = 0.0;
+    long long fx = 0;                                       // FP32: exact integer sum
     for (int b = 0; b < nblk; ++b) {
-        dH += part[b].dH;
+        if (f64_parts) dH += part[b].dH;
+        else fx += de_units(part[b].dH);
         na += (double)part[b].nacc;
     }
+    if (!f64_parts) dH = (double)fx * kDEUnit;
     out[0] = color ? out[0] + dH : dH;
     out[1] = color ? out[1] + na : na;
 }
@@ -391,10 +407,10 @@ cudaError_t launch_half_sweep(const SweepArgs& a, int color, int trig, cudaStrea
 
 cudaError_t launch_control(Ctl* ctl, Part* const part[2], const EntryDesc* ents, int n_ent,
                            int mode, double A_targ, double k_a, int n_f, int n_fit, int i_max,
-                           double* ehist, int ehist_stride, int* active, cudaStream_t st) {
+                           double* ehist, int ehist_stride, int* active, bool f64, cudaStream_t st) {
     count_launches(1, st);
     k_control<<<n_ent, kCtlThreads, 0, st>>>(ctl, part[0], part[1], ents, mode, A_targ, k_a, n_f,
-                                             n_fit, i_max, ehist, ehist_stride, active);
+                                             n_fit, i_max, ehist, ehist_stride, active, f64 ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -414,9 +430,10 @@ cudaError_t launch_energy(const EntryDesc* e_host, const float2* lat, double* sc
     return cudaGetLastError();
 }
 
-cudaError_t launch_strip_partials(const Part* part, int nblk, int color, double* out, cudaStream_t st) {
+cudaError_t launch_strip_partials(const Part* part, int nblk, int color, double* out, bool f64,
+                                  cudaStream_t st) {
     count_launches(1, st);
-    k_strip_partials<<<1, 1, 0, st>>>(part, nblk, color, out);
+    k_strip_partials<<<1, 1, 0, st>>>(part, nblk, color, out, f64 ? 1 : 0);
     return cudaGetLastError();
 }
 

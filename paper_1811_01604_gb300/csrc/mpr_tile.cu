@@ -179,6 +179,14 @@ __device__ __forceinline__ int ld_relaxed(const int* p) {
 __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 // with a preceding relaxed load that observed a release store: acquire
 __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 // orders this thread's generic-proxy global accesses with its later async-proxy (TMA) ones
@@ -206,8 +214,9 @@ __device__ __forceinline__ bool bounded_wait(const TileArgs& A, F ready) {
 
 // Control state in 8-byte words through L2 (other blocks rewrite it during a launch).
 static_assert(sizeof(Ctl) % 8 == 0 && offsetof(Ctl, sweep) % 8 == 0 &&
+                  offsetof(Ctl, go_hqd) == offsetof(Ctl, sweep) + 4 &&
                   offsetof(Ctl, sweep) + 8 == sizeof(Ctl),
-              "the sweep counter is published alone, last");
+              "the sweep counter and its window are published as one word, last");
 __device__ __forceinline__ Ctl ctl_load(const Ctl* p) {
     Ctl c;
     const unsigned long long* src = reinterpret_cast<const unsigned long long*>(p);
@@ -216,14 +225,24 @@ __device__ __forceinline__ Ctl ctl_load(const Ctl* p) {
     for (int i = 0; i < (int)(sizeof(Ctl) / 8); ++i) dst[i] = __ldcg(src + i);
     return c;
 }
-// Every field but the sweep counter, then the counter with release semantics: a block
-// that acquires the new counter sees the whole control step.
+// Every field but the last word, then the word {sweep, go_hqd} with release semantics: a
+// block that acquires the new counter sees the whole control step.
 __device__ __forceinline__ void ctl_publish(Ctl* p, const Ctl& c) {
     unsigned long long* dst = reinterpret_cast<unsigned long long*>(p);
     const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&c);
+    constexpr int kLast = (int)(offsetof(Ctl, sweep) / 8);
 #pragma unroll
-    for (int i = 0; i < (int)(offsetof(Ctl, sweep) / 8); ++i) __stcg(dst + i, src[i]);
-    st_release(&p->sweep, c.sweep);
+    for (int i = 0; i < kLast; ++i) __stcg(dst + i, src[i]);
+    st_release(dst + kLast, src[kLast]);
+}
+// The published word {sweep, go_hqd} of a grid, in one load.
+struct CtlGo {
+    uint32_t sweep;
+    float go_hqd;
+};
+__device__ __forceinline__ CtlGo ctl_go(const Ctl* p) {
+    const unsigned long long v = ld_relaxed(reinterpret_cast<const unsigned long long*>(&p->sweep));
+    return CtlGo{(uint32_t)v, __uint_as_float((uint32_t)(v >> 32))};
 }
 
 // Per-item parameters staged in shared memory by the issuing thread, in 16-byte groups
@@ -252,13 +271,6 @@ struct GridCache {
     float seen_hqd;                       // relaxation: the window of sweep `seen`
 };
 
-// Energy changes are summed across the tiles of a grid in 64-bit fixed point (2^-28 units):
-// integer addition is associative, so the total does not depend on which block updated
-// which tile or in which order.  |dH| <= 8 per site keeps any grid of < 2^31 sites far
-// from overflow.
-constexpr float kFixScale = 268435456.0f;             // 2^28
-constexpr double kFixUnit = 1.0 / 268435456.0;
-
 // Thread 0 of a block, after a barrier that follows every warp's flush of the block's
 // totals for grid e at sweep sig: n more tiles of that sweep are done.  The block that
 // completes the sweep's tiles runs the grid's Algorithm 2 control step from the totals --
@@ -271,12 +283,14 @@ __device__ void tile_ticket(const TileArgs& A, int e, uint32_t sig, int n) {
     if (prev + (unsigned)n != (unsigned)A.ents[e].ntiles) return;
     __threadfence();
     Ctl* cp = A.ctl + e;
-    if (!bounded_wait(A, [&] { return ld_acquire(&cp->sweep) == sig; })) return;
+    // a fixed-window launch may still be running the control step of sweep sig - 1; in the
+    // relaxation this thread acquired it before staging the sweep's tiles
+    if (!A.relax && !bounded_wait(A, [&] { return ld_acquire(&cp->sweep) == sig; })) return;
+    Ctl c = ctl_load(cp);                                     // in flight with the exchanges
     const long long f = (long long)atomicExch(A.gsum + 2 * slot, 0ull);
     const unsigned long long na = atomicExch(A.gsum + 2 * slot + 1, 0ull);
     atomicExch(A.ticket + slot, 0u);
-    Ctl c = ctl_load(cp);
-    control_step(c, A.ents[e], (double)f * kFixUnit, na, A.mode, A.A_targ, A.k_a, A.n_f, A.n_fit,
+    control_step(c, A.ents[e], (double)f * kDEUnit, na, A.mode, A.A_targ, A.k_a, A.n_f, A.n_fit,
                  A.i_max, A.ehist + (long long)e * A.ehist_stride, 1);
     ctl_publish(cp, c);
     if (A.relax && c.stop) atomicSub(A.live, 1);
@@ -398,27 +412,22 @@ k_tile_sweep(const TileArgs A) {
                     // did not end the relaxation): nothing to wait for or load again
                     half_qd = gc.seen_hqd;
                 } else {
-                    // ready once the control step of sweep sig - 1 is published (every
-                    // block polls the same word, so gently), or the grid's relaxation (or
-                    // every grid's) has ended, which is looked at every 8th poll
-                    int live = 1;
-                    unsigned polls = 0;
+                    // ready once the control step of sweep sig - 1 is published, or the
+                    // grid's relaxation has ended: one word says both, and the window
+                    // (every block polls the same word, so gently)
+                    CtlGo g{0u, 0.0f};
                     ok = bounded_wait(A, [&] {
-                        if ((int)(ld_relaxed(&cp->sweep) - sig) >= 0) return true;
-                        if ((++polls & 7u) == 0u) {
-                            live = ld_relaxed(A.live);
-                            if (live <= 0 || ld_relaxed(&cp->stop) != 0) return true;
-                        }
+                        g = ctl_go(cp);
+                        if ((int)(g.sweep - sig) >= 0 || g.go_hqd < 0.0f) return true;
                         __nanosleep(64);
                         return false;
                     });
                     fence_acq_rel();
-                    if (ok && live <= 0) { sp.t = -1; return; }       // every grid has stopped
-                    if (ok && ld_relaxed(&cp->stop)) {                // this grid has stopped
+                    if (ok && g.go_hqd < 0.0f) {                      // this grid has stopped
                         gc.stopped = 1;
                         continue;
                     }
-                    half_qd = __uint_as_float(ld_relaxed(reinterpret_cast<const unsigned*>(&cp->half_qd)));
+                    half_qd = g.go_hqd;
                     if (ok) {                                         // kept for the sweep's other tiles
                         gc.seen = sig;
                         gc.seen_hqd = half_qd;
@@ -586,8 +595,10 @@ k_tile_sweep(const TileArgs A) {
             ++s_kn;
         }
 
-        // colour A on the tile and its ring, then colour B on the tile
-        float dE = 0.0f;
+        // colour A on the tile and its ring, then colour B on the tile; energy changes in
+        // fixed point per site, summed in 32 bits (at most kDEMaxSites32 sites a thread)
+        static_assert((G::LIST + NT - 1) / NT <= kDEMaxSites32, "32-bit energy partial");
+        int dE = 0;
         unsigned nacc = 0;
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
@@ -622,15 +633,14 @@ k_tile_sweep(const TileArgs A) {
                 const float d = hybrid_update<TRIG>(v, C, S, Fx, Fy, hq, u24f(rnd.y), kx, A.or_mode, accepted);
                 own[r][q] = v;
                 if (own_site) {
-                    dE += d;
+                    dE += de_fixed(d);
                     nacc += accepted ? 1u : 0u;
                     if (ACC) __stcg(acc + aidx, acc_old + angle_upper(v.x, v.y));
                 }
             }
             if (pass == 0) __syncthreads();               // B2: colour A done
         }
-        // the tile's energy change in fixed point: deterministic whatever the tile order
-        s_fx[threadIdx.x] += __float2ll_rn(dE * kFixScale);
+        s_fx[threadIdx.x] += dE;
         s_nat[threadIdx.x] += nacc;
         if (threadIdx.x == 0) s_flush = next_differs(e, sweep) ? 1 : 0;
         fence_proxy_async_smem();                         // this thread's stage writes before the next copy into it
