@@ -17,9 +17,13 @@
  *   R-ES   sample specific energy: each unordered sample pair counted once.
  *   R-NGP  N_GP = W(H-1) + H(W-1); H sums over all nearest-neighbour bonds.
  *   R-SG   SG slope = least-squares linear slope of the last n_fit energies.
- *   R-RNG  Philox4x32-10 counter {site, sweep, chain, 0}, key = 64-bit seed;
- *          u = (x0 >> 8) 2^-24 (proposal), r = (x1 >> 8) 2^-24 (acceptance);
- *          initial gap angles use sweep = 0xFFFFFFFF.
+ *   R-RNG  Philox4x32-10, key = 64-bit seed.  In a sweep, site (x, y) of colour
+ *          k = (x + y) & 1 draws from the counter {y ceil(W/4) + floor(x/4),
+ *          sweep, chain, k}: of the four columns 4 floor(x/4) .. +3 of row y two
+ *          sites have colour k; the one with floor(x/2) even takes words
+ *          (o0, o1), the other (o2, o3); u = (first >> 8) 2^-24 is the
+ *          proposal uniform, r = (second >> 8) 2^-24 the acceptance uniform.
+ *          Initial gap angles: counter {y W + x, 0xFFFFFFFF, chain, 0}, o0.
  *   R-TAB  e(T,L): K_T log-spaced temperatures, all-free lattices started
  *          from U(0,2pi), Algorithm 2 step 5 relaxation, then M_T sweeps at
  *          the step-6 window; T-hat by piecewise-linear interpolation in T.
@@ -98,15 +102,30 @@ void orc_philox_batch(const uint32_t* ctr, uint64_t seed, uint32_t* out, long n)
 /* 24-bit uniform in [0,1): exactly representable in FP32 and FP64. */
 static double u24(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
 
-static void site_randoms(uint64_t seed, uint32_t site, uint32_t sweep, uint32_t chain,
+/* READING R-RNG: the two uniforms of a sweep's update of site (x, y) (y counted in the
+ * whole grid) of a W-wide grid. */
+static void site_randoms(uint64_t seed, int W, int x, int y, uint32_t sweep, uint32_t chain,
                          double* u, double* r)
 {
-    uint32_t ctr[4] = { site, sweep, chain, 0u };
+    const uint32_t quads = (uint32_t)((W + 3) / 4);
+    const uint32_t color = (uint32_t)((x + y) & 1);
+    uint32_t ctr[4] = { (uint32_t)y * quads + (uint32_t)(x / 4), sweep, chain, color };
     uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
     uint32_t o[4];
     orc_philox4x32_10(ctr, key, o);
-    *u = u24(o[0]);
-    *r = u24(o[1]);
+    const int second = (x / 2) & 1;
+    *u = u24(o[second ? 2 : 0]);
+    *r = u24(o[second ? 3 : 1]);
+}
+
+/* Initial gap angle uniform of site index i (READING R-RNG). */
+static double init_uniform(uint64_t seed, uint32_t i, uint32_t chain)
+{
+    uint32_t ctr[4] = { i, 0xFFFFFFFFu, chain, 0u };
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t o[4];
+    orc_philox4x32_10(ctr, key, o);
+    return u24(o[0]);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -240,13 +259,13 @@ enum { ORC_F_REFLECTED = 1, ORC_F_WRAPPED = 2, ORC_F_ACCEPTED = 4, ORC_F_VISITED
 /* ------------------------------------------------------------------------ */
 static int update_site(double* phi, int W, int H, int x, int y, double a, double T, double q,
                        uint64_t seed, uint32_t chain, uint32_t sweep, int or_mode,
-                       double* margin, uint32_t site_off)
+                       double* margin, int row0)
 {
     long i = (long)y * W + x;
     double nb[4];
     int nnb = gather_nb(phi, W, H, x, y, nb);
     double u, r;
-    site_randoms(seed, (uint32_t)i + site_off, sweep, chain, &u, &r);
+    site_randoms(seed, W, x, row0 + y, sweep, chain, &u, &r);
     int flags = ORC_F_VISITED;
 
     double p1 = orc_over_relax(phi[i], nb, nnb, q, or_mode);          /* step 1 */
@@ -281,7 +300,7 @@ long orc_sweep(double* phi, const uint8_t* mask, int W, int H, double a, double 
                 long i = (long)y * W + x;
                 if (mask[i]) continue;                 /* samples stay frozen */
                 double m = 0.0;
-                int f = update_site(phi, W, H, x, y, a, T, q, seed, chain, sweep, or_mode, &m, 0u);
+                int f = update_site(phi, W, H, x, y, a, T, q, seed, chain, sweep, or_mode, &m, 0);
                 if (f & ORC_F_ACCEPTED) ++nacc;
                 if (flags) flags[i] = (uint8_t)f;
                 if (margins) margins[i] = m;
@@ -299,7 +318,7 @@ long orc_sweep(double* phi, const uint8_t* mask, int W, int H, double a, double 
 
 /* Algorithm 1 on the gap sites of colour `color` ((x + row0 + y) & 1, the grid's colour) in
  * rows [y_a, y_b) of a block: the same updates orc_sweep makes to these sites in the whole
- * grid, with the grid's Philox site index (row0 + y) W + x.  Returns the accepted proposals. */
+ * grid, with the grid's Philox counters (row row0 + y).  Returns the accepted proposals. */
 long orc_sweep_rows(double* phi, const uint8_t* mask, int W, int Hb, int row0, int y_a, int y_b,
                     int color, double a, double T, double q, uint64_t seed, uint32_t chain,
                     uint32_t sweep, int or_mode)
@@ -310,8 +329,7 @@ long orc_sweep_rows(double* phi, const uint8_t* mask, int W, int Hb, int row0, i
             if (((x + row0 + y) & 1) != color) continue;
             long i = (long)y * W + x;
             if (mask[i]) continue;
-            int f = update_site(phi, W, Hb, x, y, a, T, q, seed, chain, sweep, or_mode, NULL,
-                                (uint32_t)row0 * (uint32_t)W);
+            int f = update_site(phi, W, Hb, x, y, a, T, q, seed, chain, sweep, or_mode, NULL, row0);
             if (f & ORC_F_ACCEPTED) ++nacc;
         }
     return nacc;
@@ -336,9 +354,7 @@ void orc_init_gaps(double* phi, const uint8_t* mask, int W, int H, uint64_t seed
 {
     for (long i = 0; i < (long)W * H; ++i) {
         if (mask[i]) continue;
-        double u, r;
-        site_randoms(seed, (uint32_t)i, 0xFFFFFFFFu, chain, &u, &r);
-        phi[i] = ORC_TWO_PI * u;
+        phi[i] = ORC_TWO_PI * init_uniform(seed, (uint32_t)i, chain);
     }
 }
 

@@ -51,7 +51,7 @@ struct GridIn {
     uint32_t chain;
     double T;
     double zmin, scale;
-    uint32_t site_off = 0; // Philox site offset (a block of rows of a larger grid)
+    uint32_t row_off = 0;  // rows of a larger grid above this block (Philox counters)
 };
 
 struct Batch {
@@ -334,7 +334,7 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
         E.plane[1] = (long long)(lat + plane);
         lat += 2 * plane;
         E.chain = grids[e].chain;
-        E.site_off = grids[e].site_off;
+        E.row_off = grids[e].row_off;
         E.q = ctx->prm.q;
         E.cQ = std::cos(kTwoPi * E.q);
         E.sQ = std::sin(kTwoPi * E.q);
@@ -1714,7 +1714,7 @@ mpr_status mpr_strip_init(mpr_ctx** out, const float* z, const uint8_t* mask, in
     if (h1) CUS(cudaMemsetAsync(ctx->d_mask + (size_t)(Hb - 1) * W, 1, (size_t)W, ctx->st));
 #undef CUS
     GridIn gi{W, Hb, ctx->d_z, ctx->d_mask, ctx->prm.chain, 0.0, zmin, G.scale};
-    gi.site_off = (uint32_t)row0 * (uint32_t)W;
+    gi.row_off = (uint32_t)row0;
     const mpr_status bs = batch_build(ctx, ctx->b, std::vector<GridIn>{gi}, 0, ctx->d_mask);
     if (bs != MPR_OK) return bail(bs);
     ctx->strip.on = true;

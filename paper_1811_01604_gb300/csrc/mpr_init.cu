@@ -72,7 +72,8 @@ __global__ void k_pack(EntryDesc e, const float* __restrict__ z, const uint8_t* 
             const double phi = ((double)z[i] - zmin) * scale;          // Eq. 1
             theta = e.q * phi;
         } else {
-            const uint4 r = philox10(make_uint4((uint32_t)i + e.site_off, kInitSweep, e.chain, 0u), key0, key1);
+            const uint32_t site = (uint32_t)i + e.row_off * (uint32_t)e.W;   // in the whole grid
+            const uint4 r = philox10(make_uint4(site, kInitSweep, e.chain, 0u), key0, key1);
             theta = kTwoPi * e.q * (double)u24f(r.x);                  // q * 2 pi u
         }
         const long long base = c ? e.plane[1] : e.plane[0];

@@ -33,7 +33,7 @@ enum { CTL_RELAX = 0, CTL_FIXED = 1, CTL_SAMPLE = 2 };
 
 struct EntryDesc {            // immutable during a run
     int W, H, pitch;
-    uint32_t site_off;        // added to the Philox site index (a block of rows of a larger grid)
+    uint32_t row_off;         // rows of a larger grid above this block (its Philox counters)
     long long plane[2];       // float2 offset of plane c's padded origin
     long long gbase[2];       // offset of colour c's gap list
     int ngap[2];
@@ -98,20 +98,27 @@ struct TileGeom {
     int nt;                   // threads per block
 };
 
+// A tile's gap list has three parts: colour A inside the tile, colour A on the one-site
+// ring around it, colour B inside the tile.  An entry is a pair of plane columns of one
+// region row; the interior parts list the pairs whose two sites are both gaps first ("full":
+// two updates from one Philox block), then the pairs with one gap site; the ring part has
+// one entry per site.
 struct TileDesc {             // one tile: its grid, origin, and gap-list counts (set-up)
     int entry;
     int y0, x0;
-    int nA_int;               // colour A inside the tile
-    int nA_ring;              // colour A on the one-site ring
-    int nB;                   // colour B inside the tile
+    int nA_int;               // entries: colour A inside the tile
+    int nA_ring;              // entries: colour A on the one-site ring
+    int nB;                   // entries: colour B inside the tile
     int t;                    // the tile's own index (its lists and accumulators)
-    int _pad;
+    int nfull;                // full pairs: colour A in bits 0-15, colour B in bits 16-31
 };
 
-struct TileCnt {              // gap sites listed for one tile
-    uint16_t nA_int;          // colour A inside the tile
-    uint16_t nA_ring;         // colour A on the one-site ring around it
-    uint16_t nB;              // colour B inside the tile
+struct TileCnt {              // entries listed for one tile (as in TileDesc)
+    uint16_t nA_int;
+    uint16_t nA_ring;
+    uint16_t nB;
+    uint16_t nA_full;
+    uint16_t nB_full;
     uint16_t _pad;
 };
 
@@ -220,6 +227,14 @@ __device__ __forceinline__ uint4 philox10(uint4 c, const RoundKeys& rk) {
 }
 
 __device__ __forceinline__ float u24f(uint32_t x) { return (float)(x >> 8) * 0x1p-24f; }
+
+// Random numbers of a sweep's site update: Philox4x32-10 at the counter
+// {y ceil(W/4) + floor(x/4), sweep, chain, colour}.  Of the four columns 4 floor(x/4) .. +3
+// of row y, two sites have the colour; the one with floor(x/2) even takes words (0, 1), the
+// other words (2, 3): proposal uniform first, acceptance uniform second.
+__device__ __forceinline__ uint32_t quad_index(int W, int y, int x) {
+    return (uint32_t)y * (uint32_t)((W + 3) >> 2) + (uint32_t)(x >> 2);
+}
 
 // The FP32 paths add energy changes in fixed point: each site's change is rounded to a
 // whole number of kDEUnit = 2^-17 where it is computed, and those integers are summed.

@@ -21,7 +21,8 @@ k_half_sweep(const SweepArgs A, const int color) {
     const float kx = accept_scale<TRIG>((float)(-1.0 / ctl->T));
     const uint32_t sweep = ctl->sweep;
     const int n = color ? E->ngap[1] : E->ngap[0], pitch = E->pitch, W = E->W;
-    const uint32_t chain = E->chain, site_off = E->site_off;
+    const uint32_t chain = E->chain;
+    const int row_off = (int)E->row_off;
     const long long gb = color ? E->gbase[1] : E->gbase[0];
     const uint32_t* __restrict__ gl = A.gaps + gb;
     float2* __restrict__ own = A.lat + (color ? E->plane[1] : E->plane[0]);
@@ -44,13 +45,15 @@ k_half_sweep(const SweepArgs A, const int color) {
             const float C = (nu.x + nd.x) + (nl.x + nr.x);
             const float S = (nu.y + nd.y) + (nl.y + nr.y);
             float2 v = own[k];
-            const uint32_t site = (uint32_t)y * (uint32_t)W + (uint32_t)(2 * j + s) + site_off;
-            const uint4 rnd = philox10(make_uint4(site, sweep, chain, 0u), A.rk);
-            const float hq = (u24f(rnd.x) - 0.5f) * half_qd;
+            const uint4 rnd = philox10(make_uint4(quad_index(W, y + row_off, 2 * j + s), sweep, chain,
+                                                  (uint32_t)color), A.rk);
+            const bool second = (j & 1) != 0;                    // floor(x / 2) odd
+            const float hq = (u24f(second ? rnd.z : rnd.x) - 0.5f) * half_qd;
+            const float ur = u24f(second ? rnd.w : rnd.y);
             bool accepted;
             float Fx = 0.0f, Fy = 0.0f;
             if (A.or_mode == OR_LITERAL) literal_field(nu, nd, nl, nr, Fx, Fy);
-            dE += de_fixed(hybrid_update<TRIG, GQ>(v, C, S, Fx, Fy, hq, u24f(rnd.y), kx, A.or_mode, accepted,
+            dE += de_fixed(hybrid_update<TRIG, GQ>(v, C, S, Fx, Fy, hq, ur, kx, A.or_mode, accepted,
                                                    cQ, sQ));
             nacc += accepted ? 1u : 0u;
             own[k] = v;
@@ -96,7 +99,8 @@ k_half_sweep64(const SweepArgs A, const int color) {
     const double neg_inv_T = -1.0 / ctl->T;
     const uint32_t sweep = ctl->sweep;
     const int n = color ? E->ngap[1] : E->ngap[0], pitch = E->pitch, W = E->W;
-    const uint32_t chain = E->chain, site_off = E->site_off;
+    const uint32_t chain = E->chain;
+    const int row_off = (int)E->row_off;
     const long long gb = color ? E->gbase[1] : E->gbase[0];
     const uint32_t* __restrict__ gl = A.gaps + gb;
     double2* __restrict__ lat = reinterpret_cast<double2*>(A.lat);
@@ -119,13 +123,15 @@ k_half_sweep64(const SweepArgs A, const int color) {
             const double C = (nu.x + nd.x) + (nl.x + nr.x);
             const double S = (nu.y + nd.y) + (nl.y + nr.y);
             double2 v = own[k];
-            const uint32_t site = (uint32_t)y * (uint32_t)W + (uint32_t)(2 * j + s) + site_off;
-            const uint4 rnd = philox10(make_uint4(site, sweep, chain, 0u), A.rk);
-            const double hq = ((double)u24f(rnd.x) - 0.5) * half_qd;
+            const uint4 rnd = philox10(make_uint4(quad_index(W, y + row_off, 2 * j + s), sweep, chain,
+                                                  (uint32_t)color), A.rk);
+            const bool second = (j & 1) != 0;                    // floor(x / 2) odd
+            const double hq = ((double)u24f(second ? rnd.z : rnd.x) - 0.5) * half_qd;
+            const double ur = (double)u24f(second ? rnd.w : rnd.y);
             bool accepted;
             double Fx = 0.0, Fy = 0.0;
             if (A.or_mode == OR_LITERAL) literal_field64(nu, nd, nl, nr, Fx, Fy);
-            dE += hybrid_update64<GQ>(v, C, S, Fx, Fy, hq, (double)u24f(rnd.y), neg_inv_T, A.or_mode, accepted,
+            dE += hybrid_update64<GQ>(v, C, S, Fx, Fy, hq, ur, neg_inv_T, A.or_mode, accepted,
                                       cQ, sQ);
             nacc += accepted ? 1u : 0u;
             own[k] = v;

@@ -37,18 +37,29 @@ template <int TH, int TW>
 struct Geo {
     static constexpr int RH = TH + 4;                 // region rows (halo 2)
     static constexpr int RW = TW / 2 + 4;             // region plane columns
-    static constexpr int CAPA = ((TH + 2) * (TW + 2) + 1) / 2;
-    static constexpr int CAPB = TH * TW / 2;
+    static constexpr int RP = RW / 2;                 // region plane column pairs
+    // pairs of plane columns (2 qp, 2 qp + 1) holding gap sites: colour A inside the tile
+    // and on its ring, colour B inside the tile
+    static constexpr int CAPA = TH * TW / 4 + TH + TW + 2;
+    static constexpr int CAPB = TH * TW / 4;
     static constexpr int LIST = (CAPA + CAPB + 7) / 8 * 8;   // u16 entries per tile (16-byte slots)
-    static constexpr int ACC = TH * TW;               // accumulator floats per tile
-    static_assert(TH % 2 == 0 && TW % 4 == 0, "tile origin parity and 16-byte alignment");
-    static_assert(RW <= 128 && RH <= 512, "entry encoding");
+    static constexpr int ACC = TH * TW;               // accumulator floats per tile: 2 per pair
+    static_assert(TH % 2 == 0 && TW % 8 == 0, "tile origin parity, quads of columns, 16-byte stores");
+    static_assert(RH <= 64 && RP <= 64, "entry encoding (r << 8) | (qp << 2) | members");
 
     static_assert(RW * 8 % 16 == 0, "TMA box rows must be a multiple of 16 bytes");
     static_assert((2 * RH * RW * 8) % 128 == 0, "list slots stay 16-byte aligned");
 };
 
-// Lists the gap sites of each tile (one warp per tile), row-major in region coordinates.
+// Lists the gap sites of each tile (one warp per tile) in region coordinates, by pairs of
+// plane columns: entry (r << 8) | (qp << 2) | members, where bit m of `members` marks
+// plane column q = 2 qp + m of region row r as a gap site of the part's kind.  The two
+// sites of a pair have the same colour and lie in one quad of grid columns (the tile origin
+// is a multiple of 4), so they share one Philox block.  The interior parts list their full
+// pairs (both bits) first, then the pairs with only site 0, then those with only site 1, so
+// that the warps of a block take entries of one kind together; the ring part has one entry
+// per site.  A pair never mixes interior and
+// ring sites (the interior starts on an even plane column and spans an even number of them).
 template <int TH, int TW>
 __global__ void k_tile_lists(TileDesc* __restrict__ tiles, int ntiles,
                              const EntryDesc* __restrict__ ents, const uint8_t* __restrict__ mask,
@@ -61,45 +72,61 @@ __global__ void k_tile_lists(TileDesc* __restrict__ tiles, int ntiles,
     const uint8_t* m = mask ? mask + E.site0 : nullptr;
     uint16_t* out = lists + (long long)t * G::LIST;
     const unsigned lt = (1u << lane) - 1u;
-    int counts[3] = {0, 0, 0};
-    // list 0: colour A, interior; list 1: colour A, ring; list 2: colour B, interior
-    for (int which = 0; which < 3; ++which) {
-        const int c = which == 2 ? 1 : 0;
-        int n = 0;
-        uint16_t* dst = out + (which == 0 ? 0 : which == 1 ? counts[0] : counts[0] + counts[1]);
-        for (int base = 0; base < G::RH * G::RW; base += 32) {
-            const int idx = base + lane;
-            bool take = false;
-            int r = 0, q = 0;
-            if (idx < G::RH * G::RW) {
-                r = idx / G::RW;
-                q = idx - r * G::RW;
-                const int y = td.y0 - 2 + r;
-                const int s = c ^ (r & 1);
-                const int x = td.x0 + 2 * q - 4 + s;
-                const bool in_grid = y >= 0 && y < E.H && x >= 0 && x < E.W;
-                const bool interior = y >= td.y0 && y < td.y0 + TH && x >= td.x0 && x < td.x0 + TW;
-                const bool ring = !interior && y >= td.y0 - 1 && y <= td.y0 + TH && x >= td.x0 - 1 &&
-                                  x <= td.x0 + TW;
-                const bool gap = in_grid && (all_free || !m[(long long)y * E.W + x]);
-                take = gap && (which == 1 ? ring : interior);
+    int n = 0;                                  // entries written so far
+    int counts[3] = {0, 0, 0}, full[2] = {0, 0};
+    // part 0: colour A, interior; part 1: colour A, ring; part 2: colour B, interior; each in
+    // three rounds: full pairs, pairs of site 0 only, pairs of site 1 only
+    for (int part = 0; part < 3; ++part) {
+        const int c = part == 2 ? 1 : 0;
+        const int n0 = n;
+        for (int round = 0; round < 3; ++round) {
+            if (round == 1 && part != 1) full[part >> 1] = n - n0;
+            for (int base = 0; base < G::RH * G::RP; base += 32) {
+                const int idx = base + lane;
+                unsigned members = 0u;
+                int r = 0, qp = 0;
+                if (idx < G::RH * G::RP) {
+                    r = idx / G::RP;
+                    qp = idx - r * G::RP;
+                    const int y = td.y0 - 2 + r;
+                    const int s = c ^ (r & 1);
+#pragma unroll
+                    for (int mm = 0; mm < 2; ++mm) {
+                        const int x = td.x0 + 2 * (2 * qp + mm) - 4 + s;
+                        const bool in_grid = y >= 0 && y < E.H && x >= 0 && x < E.W;
+                        const bool interior = y >= td.y0 && y < td.y0 + TH && x >= td.x0 && x < td.x0 + TW;
+                        const bool ring = !interior && y >= td.y0 - 1 && y <= td.y0 + TH && x >= td.x0 - 1 &&
+                                          x <= td.x0 + TW;
+                        const bool gap = in_grid && (all_free || !m[(long long)y * E.W + x]);
+                        if (gap && (part == 1 ? ring : interior)) members |= 1u << mm;
+                    }
+                }
+                // interior: full pairs, then pairs of site 0 only, then of site 1 only; ring:
+                // one entry per site (sites 0, then sites 1)
+                unsigned emit;
+                if (part == 1) emit = round < 2 ? members & (1u << round) : 0u;
+                else emit = members == (round == 0 ? 3u : round == 1 ? 1u : 2u) ? members : 0u;
+                const bool take = emit != 0u;
+                const unsigned b = __ballot_sync(0xffffffffu, take);
+                if (take) out[n + __popc(b & lt)] = (uint16_t)((r << 8) | (qp << 2) | (int)emit);
+                n += __popc(b);
             }
-            const unsigned b = __ballot_sync(0xffffffffu, take);
-            if (take) dst[n + __popc(b & lt)] = (uint16_t)((r << 7) | q);
-            n += __popc(b);
         }
-        counts[which] = n;
+        counts[part] = n - n0;
     }
     if (lane == 0) {
         TileCnt c;
         c.nA_int = (uint16_t)counts[0];
         c.nA_ring = (uint16_t)counts[1];
         c.nB = (uint16_t)counts[2];
+        c.nA_full = (uint16_t)full[0];
+        c.nB_full = (uint16_t)full[1];
         c._pad = 0;
         cnts[t] = c;
         tiles[t].nA_int = counts[0];
         tiles[t].nA_ring = counts[1];
         tiles[t].nB = counts[2];
+        tiles[t].nfull = full[0] | (full[1] << 16);
     }
 }
 
@@ -252,7 +279,7 @@ struct __align__(16) TileParams {
     uint32_t chain, sweep;                // Philox counter words 2 and 1
     float half_qd, neg_inv_T;             // proposal half-angle scale, -1/T
     int nA_int, nA_ring, nB, e;           // list counts, grid
-    int ntiles, H, pitch, cur;            // grid's tile count and height, row pitch, source buffer
+    int nfull, H, pitch, cur;             // full pairs (A | B << 16), grid height, row pitch, source buffer
     long long pl0, pl1;                   // plane offsets of the grid in the lattice buffers
 };
 
@@ -481,7 +508,7 @@ k_tile_sweep(const TileArgs A) {
             P.nA_ring = d.nA_ring;
             P.nB = d.nB;
             P.e = e;
-            P.ntiles = gc.ntiles;
+            P.nfull = d.nfull;
             P.H = gc.H;
             P.pitch = gc.pitch;
             P.cur = cur;
@@ -597,46 +624,66 @@ k_tile_sweep(const TileArgs A) {
 
         // colour A on the tile and its ring, then colour B on the tile; energy changes in
         // fixed point per site, summed in 32 bits (at most kDEMaxSites32 sites a thread)
-        static_assert((G::LIST + NT - 1) / NT <= kDEMaxSites32, "32-bit energy partial");
+        static_assert(2 * ((G::LIST + NT - 1) / NT) <= kDEMaxSites32, "32-bit energy partial");
         int dE = 0;
         unsigned nacc = 0;
+        const int nfull = *reinterpret_cast<const int*>(&sp.nfull);
+        const uint32_t quads = (uint32_t)((W + 3) >> 2), quad0 = (uint32_t)(x0 >> 2) - 1u;
+        const int sitesA = (nfull & 0xFFFF) + nA_int;     // accumulator slots of colour A
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
             const int c = pass;                           // colour being updated
             const int n = pass ? nB : nA;
+            const int nf = pass ? (nfull >> 16) : (nfull & 0xFFFF);
             const uint16_t* lst = pass ? list + nA : list;
+            float* __restrict__ pacc = ACC ? acc + (pass ? sitesA : 0) : nullptr;
             float2(*own)[G::RW] = sm[c];
             float2(*oth)[G::RW] = sm[c ^ 1];
-            for (int k = threadIdx.x; k < n; k += NT) {
-                // the ring belongs to other tiles: its sites count nowhere
-                const bool own_site = pass || k < nA_int;
-                const int aidx = pass ? nA_int + k : k;
+            // Algorithm 1 on plane column q of region row r with the pair's uniforms (ru:
+            // proposal, ra: acceptance); own: an interior site (its energy change and
+            // acceptance count, and its running angle sum in slot aidx)
+            auto update = [&](int r, int q, uint32_t ru, uint32_t ra, bool own_site, int aidx) {
                 // the running angle sum is loaded first, so that its latency hides behind
                 // the update (from L2: another block may have written it in this launch)
                 float acc_old = 0.0f;
-                if (ACC && own_site) acc_old = __ldcg(acc + aidx);
-                const int ent = lst[k];
-                const int r = ent >> 7, q = ent & 127;
+                if (ACC && own_site) acc_old = __ldcg(pacc + aidx);
                 const int s = c ^ (r & 1);
                 const float2 nu = oth[r - 1][q], nd = oth[r + 1][q];
                 const float2 nl = oth[r][q - 1 + s], nr = oth[r][q + s];
                 const float C = (nu.x + nd.x) + (nl.x + nr.x);
                 const float S = (nu.y + nd.y) + (nl.y + nr.y);
                 float2 v = own[r][q];
-                const int y = y0 - 2 + r, x = x0 + 2 * q - 4 + s;
-                const uint32_t site = (uint32_t)y * (uint32_t)W + (uint32_t)x;
-                const uint4 rnd = philox10(make_uint4(site, sweep, chain, 0u), A.rk);
-                const float hq = (u24f(rnd.x) - 0.5f) * half_qd;
+                const float hq = (u24f(ru) - 0.5f) * half_qd;
                 bool accepted;
                 float Fx = 0.0f, Fy = 0.0f;
                 if (A.or_mode == OR_LITERAL) literal_field(nu, nd, nl, nr, Fx, Fy);
-                const float d = hybrid_update<TRIG>(v, C, S, Fx, Fy, hq, u24f(rnd.y), kx, A.or_mode, accepted);
+                const float d = hybrid_update<TRIG>(v, C, S, Fx, Fy, hq, u24f(ra), kx, A.or_mode, accepted);
                 own[r][q] = v;
                 if (own_site) {
                     dE += de_fixed(d);
                     nacc += accepted ? 1u : 0u;
-                    if (ACC) __stcg(acc + aidx, acc_old + angle_upper(v.x, v.y));
+                    if (ACC) __stcg(pacc + aidx, acc_old + angle_upper(v.x, v.y));
                 }
+            };
+            // the pair's Philox block: counter {quad, sweep, chain, colour}
+            auto block = [&](int r, int qp) {
+                const uint32_t quad = (uint32_t)(y0 - 2 + r) * quads + quad0 + (uint32_t)qp;
+                return philox10(make_uint4(quad, sweep, chain, (uint32_t)c), A.rk);
+            };
+            // pairs of two gap sites: both updates from one block (interior sites only)
+            for (int k = threadIdx.x; k < nf; k += NT) {
+                const int ent = lst[k];
+                const int r = ent >> 8, qp = (ent >> 2) & 63;
+                const uint4 rnd = block(r, qp);
+                update(r, 2 * qp, rnd.x, rnd.y, true, 2 * k);
+                update(r, 2 * qp + 1, rnd.z, rnd.w, true, 2 * k + 1);
+            }
+            // single sites: the ring belongs to other tiles, its sites count nowhere
+            for (int k = nf + threadIdx.x; k < n; k += NT) {
+                const int ent = lst[k];
+                const int r = ent >> 8, qp = (ent >> 2) & 63, mm = (ent >> 1) & 1;
+                const uint4 rnd = block(r, qp);
+                update(r, 2 * qp + mm, mm ? rnd.z : rnd.x, mm ? rnd.w : rnd.y, pass || k < nA_int, nf + k);
             }
             if (pass == 0) __syncthreads();               // B2: colour A done
         }
@@ -645,7 +692,7 @@ k_tile_sweep(const TileArgs A) {
         if (threadIdx.x == 0) s_flush = next_differs(e, sweep) ? 1 : 0;
         fence_proxy_async_smem();                         // this thread's stage writes before the next copy into it
         __syncthreads();                                  // B3: colour B done
-        const int4 g3 = *reinterpret_cast<const int4*>(&sp.ntiles);
+        const int4 g3 = *reinterpret_cast<const int4*>(&sp.nfull);
         // interior rows of both colours to the other buffer (samples included), 16 bytes
         // per thread and step, one warp per row; rows and columns beyond the grid skipped
         {
@@ -711,7 +758,8 @@ k_tile_sweep(const TileArgs A) {
 // depends on it).  Handing out the heavy tiles first makes a sweep's tail out of light
 // tiles, which matters where every sweep waits for the previous one's control step.
 __device__ __forceinline__ int work_bucket(const TileDesc& d, int maxw) {
-    const int w = d.nA_int + d.nA_ring + d.nB;
+    // site updates: one per entry, two for a full pair
+    const int w = d.nA_int + d.nA_ring + d.nB + (d.nfull & 0xFFFF) + (d.nfull >> 16);
     return 255 - min(255, (int)((long long)w * 256 / (maxw + 1)));
 }
 __global__ void k_tile_hist(const TileDesc* __restrict__ tiles, int ntiles, int maxw, unsigned* hist) {
@@ -783,17 +831,28 @@ __global__ void k_tile_predict_out(const TileDesc* __restrict__ tiles, const Til
     const long long cstride = (long long)chain_tiles * G::ACC;
     const int nA = cnt.nA_int + cnt.nA_ring;
     const double f = (zmax - zmin) / (kTwoPi * q * (double)M * (double)K);
+    // interior entries of both colours (as in the sweep: full pairs in slots 2k, 2k + 1,
+    // single sites of part p in slot nf_p + k, colour B after colour A's slots)
+    const int sitesA = cnt.nA_full + cnt.nA_int;
     for (int k = threadIdx.x; k < cnt.nA_int + cnt.nB; k += blockDim.x) {
         const bool isA = k < cnt.nA_int;
-        const int ent = isA ? list[k] : list[nA + (k - cnt.nA_int)];
-        const int r = ent >> 7, qq = ent & 127;
+        const int kk = isA ? k : k - cnt.nA_int;           // entry within its part
+        const int nf = isA ? cnt.nA_full : cnt.nB_full;
+        const int ent = isA ? list[k] : list[nA + kk];
+        const int r = ent >> 8, qp = (ent >> 2) & 63;
         const int s = (isA ? 0 : 1) ^ (r & 1);
-        const int y = td.y0 - 2 + r, x = td.x0 + 2 * qq - 4 + s;
-        double sum = (double)a[k];
-        for (int c = 1; c < K; ++c) sum += (double)a[c * cstride + k];
-        double v = zmin + sum * f;
-        v = v < zmin ? zmin : (v > zmax ? zmax : v);
-        zhat[E.site0 + (long long)y * E.W + x] = (float)v;
+        const int y = td.y0 - 2 + r;
+        const int base = isA ? 0 : sitesA;
+        for (int mm = 0; mm < 2; ++mm) {
+            if (!((ent >> mm) & 1)) continue;
+            const int slot = base + (kk < nf ? 2 * kk + mm : nf + kk);
+            const int x = td.x0 + 2 * (2 * qp + mm) - 4 + s;
+            double sum = (double)a[slot];
+            for (int c = 1; c < K; ++c) sum += (double)a[c * cstride + slot];
+            double v = zmin + sum * f;
+            v = v < zmin ? zmin : (v > zmax ? zmax : v);
+            zhat[E.site0 + (long long)y * E.W + x] = (float)v;
+        }
     }
 }
 
@@ -937,7 +996,7 @@ cudaError_t launch_tile_sweep(const TileArgs& a, int trig, cudaStream_t st) {
 cudaError_t launch_tile_order(const TileDesc* tiles, int ntiles, const EntryDesc* ents, int n_ent,
                               int cfg, unsigned* hist, TileDesc* ord, cudaStream_t st) {
     if (ntiles == 0) return cudaSuccess;
-    const int maxw = tile_geom(cfg).list;
+    const int maxw = 2 * tile_geom(cfg).list;
     cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned) * 256 * (size_t)n_ent, st);
     if (e != cudaSuccess) return e;
     count_launches(3, st);
