@@ -115,10 +115,10 @@ class ClockSampler:
 
 # DRAM bytes per sweep of k_tile_sweep on this grid, per compiled tile configuration and
 # phase: dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the profile case
-# fill4096 (the relaxation launch, 241 sweeps, and the accumulating launch, 100 sweeps),
+# fill4096 (the relaxation launch, 261 sweeps, and the accumulating launch, 100 sweeps),
 # divided by the launch's sweeps; valid for the kernel sources with this hash only.
-TILE_TRAFFIC_PER_SWEEP = {2: {"relax": 79.430174e9 / 241, "acc": 35.685410e9 / 100}}
-TILE_TRAFFIC_SOURCE_HASH = "f9b05abc94d3a6f0"
+TILE_TRAFFIC_PER_SWEEP = {2: {"relax": 84.142302e9 / 261, "acc": 35.097969e9 / 100}}
+TILE_TRAFFIC_SOURCE_HASH = "b45613700ab352cc"
 
 
 def tile_kernel_hash():
