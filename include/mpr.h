@@ -81,7 +81,9 @@ enum { MPR_PREC_F32 = 0, MPR_PREC_F64 = 1 };
  * paper leaves open.  Fill with mpr_default_params() and override.
  */
 typedef struct {
-    uint64_t seed;     /* Philox4x32-10 key; counter = {site, sweep, chain, 0} */
+    uint64_t seed;     /* Philox4x32-10 key; a sweep's update of site (x, y) of colour
+                          k = (x + y) & 1 uses the counter {y ceil(W/4) + floor(x/4), sweep,
+                          chain, k}, words 0-1 if floor(x/2) is even, else 2-3 */
     double q;          /* coupling of Eq. 2, in (0, 1/2] (default 1/2); q < 1/2 needs exec_mode
                           AUTO or LIST and or_mode CONSERVING or NONE, else MPR_EINVAL */
     double A_targ;     /* target Metropolis acceptance ratio (default 0.3) */
@@ -183,8 +185,8 @@ mpr_status mpr_predict(mpr_ctx* ctx, int M, float* zhat);
  * Independent-chain realizations (the paper's estimator is one chain: M consecutive
  * sweeps, Algorithm 2 step 6).  The grid's current state -- normally the one
  * mpr_equilibrate left -- is forked into K chains (1 <= K <= 128).  Chain k draws from
- * the Philox counter {site, sweep, chain + k * 2^24, 0}: k = 0 continues the grid's own
- * chain, and every chain starts at the grid's current sweep counter.  The K chains run
+ * the grid's Philox counters with chain word chain + k * 2^24: k = 0 continues the grid's
+ * own chain, and every chain starts at the grid's current sweep counter.  The K chains run
  * burn_in >= 0 sweeps that are not averaged (they decorrelate the forks from their shared
  * start), then M_per_chain >= 1 sweeps, all at window a_eq and together (one launch per
  * sweep for all chains), accumulating every gap angle; zhat = G^-1(mean over all
@@ -358,10 +360,10 @@ mpr_status mpr_sample_energy_static(const float* z, const uint8_t* mask, int W, 
  * row0 + Hb < H_global), which it never updates and which the caller refreshes from their
  * owners after every half-sweep (mpr_strip_row).  row0 must be even (so every strip but
  * the first begins at an odd grid row): the block's colours are then the grid's, and the
- * Philox site index of block site (y, x) is (row0 + y) W + x, so the strips together make
- * exactly the updates of a single context on the whole grid.  Strip contexts run the LIST
- * kernels (exec_mode AUTO or LIST).  Reductions across strips (sums, minimum, maximum)
- * are the caller's (e.g. torch.distributed).  The order of one fill:
+ * Philox counters of block site (y, x) are those of grid site (x, row0 + y), so the
+ * strips together make exactly the updates of a single context on the whole grid.  Strip
+ * contexts run the LIST kernels (exec_mode AUTO or LIST).  Reductions across strips (sums,
+ * minimum, maximum) are the caller's (e.g. torch.distributed).  The order of one fill:
  *   mpr_strip_extremes on every strip -> global z_min, z_max (Eq. 1) -> mpr_strip_init;
  *   mpr_strip_pairs -> e_s = -sum / count over all strips (Eq. 4) -> mpr_strip_temperature;
  *   exchange the boundary rows; mpr_strip_energy and mpr_strip_gaps summed ->

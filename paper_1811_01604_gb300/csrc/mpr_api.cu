@@ -1660,7 +1660,7 @@ mpr_status mpr_strip_init(mpr_ctx** out, const float* z, const uint8_t* mask, in
         delete ctx;
         return MPR_EINVAL;
     }
-    ctx->prm.exec_mode = MPR_EXEC_LIST;              // the half-sweep kernels carry the site offset
+    ctx->prm.exec_mode = MPR_EXEC_LIST;              // the half-sweep kernels carry the row offset
     ctx->st = (cudaStream_t)cuda_stream;
     ctx->g.resize(1);
     GridInfo& G = ctx->g[0];

@@ -86,7 +86,7 @@ def test_strip_arguments_are_checked():
     with pytest.raises(mpr.MprError) as e:                    # odd first row of the block
         mpr.mpr_strip_init(z[1:20].contiguous(), mask[1:20].contiguous(), W, 19, 1, H, 0.0, 1.0)
     assert e.value.status == mpr.MPR_EINVAL
-    with pytest.raises(mpr.MprError) as e:                    # the tile kernels carry no site offset
+    with pytest.raises(mpr.MprError) as e:                    # the tile kernels carry no row offset
         mpr.mpr_strip_init(z[:20].contiguous(), mask[:20].contiguous(), W, 20, 0, H, 0.0, 1.0,
                            mpr.mpr_default_params(exec_mode=mpr.MPR_EXEC_TILE))
     assert e.value.status == mpr.MPR_EINVAL
