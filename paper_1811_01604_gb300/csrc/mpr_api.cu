@@ -205,6 +205,32 @@ void dfree(void* p, cudaStream_t st) {
     if (p) cudaFreeAsync(p, st);
 }
 
+// Pinned host slots of 4 ints for the contexts' small read-backs, cut from arenas that
+// live as long as the process: building and freeing contexts in a serving loop then
+// allocates and frees no pinned memory.
+constexpr int kPinSlotInts = 4, kPinSlotsPerArena = 256;
+std::mutex g_pin_mu;
+std::vector<int*> g_pin_free;
+
+cudaError_t pinned_slot(int** out) {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (g_pin_free.empty()) {
+        int* arena = nullptr;
+        const cudaError_t e = cudaMallocHost((void**)&arena, sizeof(int) * kPinSlotInts * kPinSlotsPerArena);
+        if (e != cudaSuccess) return e;
+        for (int i = kPinSlotsPerArena - 1; i >= 0; --i) g_pin_free.push_back(arena + i * kPinSlotInts);
+    }
+    *out = g_pin_free.back();
+    g_pin_free.pop_back();
+    return cudaSuccess;
+}
+
+void release_pinned_slot(int* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(p);
+}
+
 void batch_free(Batch& b, cudaStream_t st) {
     for (auto& kv : b.graphs) cudaGraphExecDestroy(kv.second);
     b.graphs.clear();
@@ -578,8 +604,15 @@ __global__ void k_relax_loop_cond(cudaGraphConditionalHandle h, const int* __res
 
 // Relaxation graph: a WHILE node whose body is one chunk of S sweeps followed by the loop
 // condition, so the whole relaxation runs without a host round trip per chunk.
+// The stream the list path captures its graphs on, created on first use.
+cudaError_t capture_stream(mpr_ctx* ctx) {
+    if (ctx->cap) return cudaSuccess;
+    return cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking);
+}
+
 mpr_status build_relax_graph(mpr_ctx* ctx, Batch& b, int S, int cap, double a_fixed, bool acc,
                              cudaGraphExec_t* out) {
+    CU(capture_stream(ctx));
     cudaGraph_t g = nullptr;
     CU(cudaGraphCreate(&g, 0));
     cudaGraphConditionalHandle h;
@@ -637,6 +670,7 @@ mpr_status run_sweeps(mpr_ctx* ctx, Batch& b, int n, int mode, double a_fixed, b
     } else if (n >= S) {
         auto it = b.graphs.find(key);
         if (it == b.graphs.end()) {
+            CU(capture_stream(ctx));
             CU(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
             mpr_status s = enqueue_sweeps(ctx, b, ctx->cap, S, mode, a_fixed, acc, relax);
             cudaGraph_t g = nullptr;
@@ -916,7 +950,7 @@ void mpr_free(mpr_ctx* ctx) {
     dfree(ctx->d_mask, ctx->st);
     dfree(ctx->d_out, ctx->st);
     dfree(ctx->d_stop, ctx->st);
-    if (ctx->h_active) cudaFreeHost(ctx->h_active);
+    release_pinned_slot(ctx->h_active);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
     delete ctx;
 }
@@ -973,8 +1007,7 @@ static mpr_status init_grids(mpr_ctx** out, int n, const float* const* z, const 
     ctx->n_sites = site0;
     auto bail = [&](mpr_status s) { mpr_free(ctx); return s; };
 #define CUI(call) do { if ((call) != cudaSuccess) { cudaGetLastError(); return bail(MPR_ECUDA); } } while (0)
-    CUI(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
-    CUI(cudaMallocHost((void**)&ctx->h_active, sizeof(int) * 4));
+    CUI(pinned_slot(&ctx->h_active));
     const size_t N = (size_t)site0;
     if (dalloc(&ctx->d_z, N, ctx->st) != cudaSuccess || dalloc(&ctx->d_mask, N, ctx->st) != cudaSuccess ||
         dalloc(&ctx->d_out, N, ctx->st) != cudaSuccess) { cudaGetLastError(); return bail(MPR_ENOMEM); }
@@ -1673,8 +1706,7 @@ mpr_status mpr_strip_init(mpr_ctx** out, const float* z, const uint8_t* mask, in
     ctx->n_sites = (long long)W * Hb;
     auto bail = [&](mpr_status s) { mpr_free(ctx); return s; };
 #define CUS(call) do { if ((call) != cudaSuccess) { cudaGetLastError(); return bail(MPR_ECUDA); } } while (0)
-    CUS(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
-    CUS(cudaMallocHost((void**)&ctx->h_active, sizeof(int) * 4));
+    CUS(pinned_slot(&ctx->h_active));
     const size_t N = (size_t)ctx->n_sites;
     if (dalloc(&ctx->d_z, N, ctx->st) != cudaSuccess || dalloc(&ctx->d_mask, N, ctx->st) != cudaSuccess ||
         dalloc(&ctx->d_out, N, ctx->st) != cudaSuccess || dalloc(&ctx->d_stop, 1, ctx->st) != cudaSuccess) {
