@@ -118,15 +118,22 @@ class ClockSampler:
 # fill4096 (the relaxation launch, 261 sweeps, and the accumulating launch, 100 sweeps),
 # divided by the launch's sweeps; valid for the kernel sources with this hash only.
 TILE_TRAFFIC_PER_SWEEP = {2: {"relax": 84.142302e9 / 261, "acc": 35.097969e9 / 100}}
-TILE_TRAFFIC_SOURCE_HASH = "b45613700ab352cc"
+TILE_TRAFFIC_SOURCE_HASH = "ec026c7fd83a5ef5"
 
 
 def tile_kernel_hash():
+    """Hash of the sweep kernel's sources with comments and blank lines removed (an edit of
+    a comment leaves the captured counters valid; any change of code does not)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ("mpr_tile.cu", "mpr_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_1811_01604_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1811_01604_gb300", "csrc", f), encoding="utf-8") as fh:
+            t = fh.read()
+        t = re.sub(r"/\*.*?\*/", "", t, flags=re.S)
+        t = re.sub(r"//[^\n]*", "", t)
+        t = "\n".join(line.rstrip() for line in t.splitlines() if line.strip())
+        h.update(t.encode())
     return h.hexdigest()[:16]
 
 

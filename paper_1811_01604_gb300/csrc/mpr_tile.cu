@@ -11,14 +11,16 @@
 // Reading one buffer and writing the other keeps every tile's halo at the pre-sweep state;
 // consecutive sweeps alternate the buffers.
 //
-// Per tile, the gap sites are listed once at set-up (u16 (r << 7) | q in the tile's
-// local region coordinates): colour-A sites inside the tile, then colour-A sites on the
-// ring, then colour-B sites inside the tile, contiguous in a 16-byte aligned slot that is
-// copied into shared memory together with the region.  Accumulators for the equilibrium
-// average use the same order (A interior, then B).
+// Per tile, the gap sites are listed once at set-up, by pairs of plane columns of one region
+// row (u16 (r << 8) | (qp << 2) | members, k_tile_lists): colour A inside the tile, then
+// colour A on the ring, then colour B inside the tile, contiguous in a 16-byte aligned slot
+// that is copied into shared memory together with the region.  The two sites of a pair
+// share one Philox block.  Accumulators for the equilibrium average follow the interior
+// entries (two slots per full pair, one per single site; A, then B).
 //
-// The sweep's accepted energy change and acceptance count go into per-grid, per-sweep
-// 64-bit fixed-point totals, whose sum does not depend on the order in which tiles finish;
+// The sweep's accepted energy change (each site's rounded to a whole number of kDEUnit)
+// and acceptance count go into per-grid, per-sweep 64-bit integer totals, whose sum does
+// not depend on the order in which tiles finish;
 // the block that completes a sweep's tiles of a grid (atomic ticket) runs the Algorithm 2
 // control step for that grid in place, so no separate control launch is needed and the
 // results are bitwise reproducible.  A whole phase of Algorithm 2 (the relaxation, or the
