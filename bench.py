@@ -965,6 +965,8 @@ def main():
     dev_ms, dev_updates, launches, sweeps, T = timed(z, mask, zhat)
     swt = mpr.mpr_sweep_timing_read(stop=True)
     torch.cuda.profiler.stop()
+    one_fill(z_h, m_h, zhat_h)         # untimed: the first fill from these host buffers
+    torch.cuda.synchronize()
     e2e_ms, e2e_updates, _, _, _ = timed(z_h, m_h, zhat_h)
     clk = clocks.stop()
 
