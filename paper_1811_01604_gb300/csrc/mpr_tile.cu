@@ -307,10 +307,10 @@ struct GridCache {
 // running -- and publishes it.
 __device__ void tile_ticket(const TileArgs& A, int e, uint32_t sig, int n) {
     const int slot = e * kSlots + (int)(sig & (uint32_t)(kSlots - 1));
-    __threadfence();
+    fence_acq_rel();                          // the block's flushes (after a barrier) before the ticket
     const unsigned prev = atomicAdd(A.ticket + slot, (unsigned)n);
     if (prev + (unsigned)n != (unsigned)A.ents[e].ntiles) return;
-    __threadfence();
+    fence_acq_rel();                          // every block's flushes before the totals are read
     Ctl* cp = A.ctl + e;
     // a fixed-window launch may still be running the control step of sweep sig - 1; in the
     // relaxation this thread acquired it before staging the sweep's tiles
@@ -406,7 +406,8 @@ k_tile_sweep(const TileArgs A) {
     // until after the next copy has been issued, unless that copy must wait for a tile.
     auto publish = [&]() {
         if (s_pub_t >= 0) {
-            __threadfence();
+            // the release is cumulative: it covers the block's write-back stores, ordered
+            // before it by the barrier that precedes this call
             st_release(A.tdone + s_pub_t, s_pub_sig);
             s_pub_t = -1;
         }
