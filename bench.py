@@ -117,8 +117,8 @@ class ClockSampler:
 # phase: dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the profile case
 # fill4096 (the relaxation launch, 261 sweeps, and the accumulating launch, 100 sweeps),
 # divided by the launch's sweeps; valid for the kernel sources with this hash only.
-TILE_TRAFFIC_PER_SWEEP = {2: {"relax": 84.142302e9 / 261, "acc": 35.097969e9 / 100}}
-TILE_TRAFFIC_SOURCE_HASH = "ec026c7fd83a5ef5"
+TILE_TRAFFIC_PER_SWEEP = {2: {"relax": (48.008025e9 + 36.123540e9) / 261, "acc": (18.342899e9 + 16.763545e9) / 100}}
+TILE_TRAFFIC_SOURCE_HASH = "878316a791d95d98"
 
 
 def tile_kernel_hash():
@@ -996,6 +996,7 @@ def main():
     sm_mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = sms * LANES_PER_SM * sm_mhz * 1e6                 # lane operations / s
     alu_achieved = ALU_OPS_PER_UPDATE * swt["gap_updates"] / (k_ms * 1e-3) if k_ms > 0 else 0.0
+    binding = "alu" if ALU_OPS_PER_UPDATE * swt["gap_updates"] / alu_peak > bytes_alg / (hbm * 1e9) else "hbm"
     tr = TILE_TRAFFIC_PER_SWEEP.get(tune["tile_cfg"]) if tile_kernel_hash() == TILE_TRAFFIC_SOURCE_HASH else None
     # per launch of the timed steps: each step is one relaxation launch and one of M sweeps
     traffic_launch = ((sum(sweeps) * tr["relax"] + args.steps * M * tr["acc"]) / k_launches) if tr else None
@@ -1022,9 +1023,15 @@ def main():
             "e2e": {"value": e2e_updates / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": N * 5, "d2h_bytes_per_step": N * 4},
             "gpu_launches": int(launches),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm,
+            # the binding roof of the algorithmic counts (the larger of the two times, the
+            # fraction of the roofline model: max(bytes / BW, ops / ALU peak) / time)
+            "roofline": {"bound": binding,
+                         "achieved": alu_achieved * 1e-12 if binding == "alu" else achieved,
+                         "peak": alu_peak * 1e-12 if binding == "alu" else hbm,
+                         "unit": "Top/s" if binding == "alu" else "GB/s",
+                         "frac": alu_achieved / alu_peak if binding == "alu" else achieved / hbm,
                          "traffic": traffic_launch,
+                         "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm},
                          "kernel": "k_tile_sweep", "tile_cfg": tune["tile_cfg"],
                          "launches": swt["launches"], "ms_per_launch": k_ms / k_launches,
                          "bytes_per_launch": bytes_alg / k_launches,
@@ -1039,8 +1046,7 @@ def main():
                                  "lanes_per_sm": LANES_PER_SM, "sm_mhz": sm_mhz,
                                  "peak_ops": alu_peak, "achieved_ops": alu_achieved},
                          "frac_alu": alu_achieved / alu_peak,
-                         "binding": "alu" if ALU_OPS_PER_UPDATE * swt["gap_updates"] / alu_peak
-                                    > bytes_alg / (hbm * 1e9) else "hbm"},
+                         "binding": binding},
             "clocks": clk,
         }
         if not args.no_cpu_baseline and world == 1:
