@@ -117,8 +117,8 @@ class ClockSampler:
 # phase: dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the profile case
 # fill4096 (the relaxation launch, 261 sweeps, and the accumulating launch, 100 sweeps),
 # divided by the launch's sweeps; valid for the kernel sources with this hash only.
-TILE_TRAFFIC_PER_SWEEP = {2: {"relax": (48.008025e9 + 36.123540e9) / 261, "acc": (18.342899e9 + 16.763545e9) / 100}}
-TILE_TRAFFIC_SOURCE_HASH = "878316a791d95d98"
+TILE_TRAFFIC_PER_SWEEP = {2: {"relax": (48.007567e9 + 36.125274e9) / 261, "acc": (18.342268e9 + 16.763504e9) / 100}}
+TILE_TRAFFIC_SOURCE_HASH = "609e9af40e2168f0"
 
 
 def tile_kernel_hash():
@@ -222,6 +222,66 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def trace_phases(z, mask, W, H, T, tile_cfg):
+    """Per-item timestamps of the sweep kernel (mpr_debug_trace) over one fill at a fixed T:
+    the relaxation launch and the M accumulating sweeps.  Per phase: median per item of the
+    wait for its inputs, the tile copy, the update of both colours and the write-back; the
+    fraction of block time spent updating; the time per sweep; in the relaxation, the
+    Algorithm 2 control step's serial gap (from the sweep's last update to the ticket that
+    completes it, the control step, and from its publication to the next sweep's first
+    copy landing); and how a mid-relaxation sweep's tiles fall on the SMs."""
+    import torch
+    from paper_1811_01604_gb300 import mpr
+    g = mpr.mpr_default_params(seed=1, M=M, tile_cfg=tile_cfg)
+    ctx = mpr.mpr_init(z, mask, W, H, g)
+    out = {}
+    try:
+        mpr.mpr_set_T(ctx, T)
+        th, tw = {0: (16, 128), 1: (32, 64), 2: (32, 128)}[tile_cfg]
+        ntiles = -(-H // th) * -(-W // tw)
+        buf = torch.zeros(ntiles * 10002 * 6 + 8192, dtype=torch.int64, device="cuda")
+        K = (buf.numel() - 8192) // 6
+        for phase in ("relax", "acc"):
+            buf.zero_()
+            mpr.mpr_debug_trace(buf)
+            if phase == "relax":
+                S = mpr.mpr_equilibrate(ctx).sweeps
+            else:
+                S = M
+                mpr.mpr_predict(ctx, M, torch.empty_like(z))
+            torch.cuda.synchronize()
+            mpr.mpr_debug_trace(None)
+            it = buf[: ntiles * S * 6].cpu().numpy().astype(np.int64).reshape(S, ntiles, 6)
+            ctl = buf[K * 6:].cpu().numpy().astype(np.int64).reshape(-1, 2)
+            ok = it[:, :, 1] > 0
+            t = [it[:, :, k][ok] for k in range(5)]
+            d = lambda a, b: float(np.median(b - a)) / 1e3
+            last = np.where(ok, it[:, :, 3], 0).max(axis=1)
+            r = {"sweeps": S, "items": int(ok.sum()),
+                 "us_wait": d(t[0], t[1]), "us_copy": d(t[1], t[2]), "us_update": d(t[2], t[3]),
+                 "us_writeback": float(np.median((t[4] - t[3])[t[4] > 0])) / 1e3,
+                 "us_per_sweep": float(np.median(np.diff(last))) / 1e3}
+            nb = int((it[:, :, 5][ok] & 0xFFFFFFFF).max()) + 1
+            r["blocks"] = nb
+            r["update_share_of_block_time"] = float((t[3] - t[2]).sum() / (nb * (t[3].max() - t[0].min())))
+            if phase == "relax":
+                tix = np.sort(ctl[:, 0][ctl[:, 0] > 0])
+                pub = np.sort(ctl[:, 1][ctl[:, 1] > 0])
+                n = min(len(pub), S) - 1
+                first = np.where(ok, it[:, :, 2], np.iinfo(np.int64).max).min(axis=1)
+                r["us_last_update_to_ticket"] = float(np.median(tix[:n] - last[:n])) / 1e3
+                r["us_control_step"] = float(np.median(pub[:n] - tix[:n])) / 1e3
+                r["us_publish_to_first_copy_landed"] = float(np.median(first[1:n + 1] - pub[:n])) / 1e3
+                sm = (it[S // 2, :, 5] >> 32)[ok[S // 2]]
+                cnt = np.bincount(sm.astype(np.int64), minlength=torch.cuda.get_device_properties(0).multi_processor_count)
+                r["mid_sweep_tiles_per_sm"] = {"max": int(cnt.max()), "idle_sms": int((cnt == 0).sum()),
+                                               "histogram": np.bincount(cnt).tolist()}
+            out[phase] = r
+    finally:
+        mpr.mpr_free(ctx)
+    return out
+
+
 def profile_case(name, tile_cfg=0):
     """sweep4096: 4096^2 bench grid, T = 0.05, 24 sweeps at a = 8 (one launch of the
     persistent sweep kernel; a few set-up kernels before it).
@@ -269,6 +329,27 @@ def profile_case(name, tile_cfg=0):
         finally:
             mpr.mpr_net_free(net)
         print(f"profile case {name}: done")
+        return
+    if name in ("trace4096", "trace1024"):
+        if name == "trace4096":
+            z_np, m_np = make_inputs(0)
+            T = 9.869677377227477e-4
+        else:
+            from paper_1811_01604_gb300 import synth
+            z_np = synth.wm_field(1024, 0.5, 16.0, seed=1)
+            m_np = synth.mask_uniform(1024, 1024, 0.33, seed=1_000_034)
+            T = None
+        z = torch.from_numpy(np.ascontiguousarray(z_np, np.float32)).cuda()
+        mask = torch.from_numpy(np.ascontiguousarray(m_np, np.uint8)).cuda()
+        H, W = z.shape
+        if T is None:
+            ctx = mpr.mpr_init(z, mask, W, H, mpr.mpr_default_params(seed=1, M=M))
+            try:
+                T, _ = mpr.mpr_estimate_T(ctx)
+            finally:
+                mpr.mpr_free(ctx)
+        print(json.dumps({"profile_case": name, "tile_cfg": tile_cfg, "T": T,
+                          **trace_phases(z, mask, W, H, T, tile_cfg)}))
         return
     if name == "net1024":
         from paper_1811_01604_gb300 import synth
@@ -688,6 +769,7 @@ def run_config2(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     Lc = 1024
+    tile_cfg = None                    # chosen once by the autotuner, untimed, on the first grid
     for nu in (0.5, 2.5):
         for kind in ("gauss", "lognormal"):
             for p in (0.33, 0.66):
@@ -701,7 +783,14 @@ def run_config2(args):
                 gap = mask == 0
                 P = int(gap.sum().item())
                 out = torch.empty_like(z)
-                prm = mpr.mpr_default_params(seed=1, M=M)
+                if tile_cfg is None:
+                    ctx = mpr.mpr_init(z, mask, Lc, Lc, mpr.mpr_default_params(seed=1, M=M), stream.cuda_stream)
+                    try:
+                        mpr.mpr_estimate_T(ctx)
+                        tile_cfg = mpr.mpr_autotune(ctx)["tile_cfg"]
+                    finally:
+                        mpr.mpr_free(ctx)
+                prm = mpr.mpr_default_params(seed=1, M=M, tile_cfg=tile_cfg)
 
                 def fill():
                     ctx = mpr.mpr_init(z, mask, Lc, Lc, prm, stream.cuda_stream)
@@ -735,6 +824,7 @@ def run_config2(args):
                         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                         "data": "synthetic",
                         "config": {"workload": f"mpr-fill-1024x1024-wm-nu{nu}-xi16-{kind}-p{p}", "M": M,
+                                   "tile_cfg": tile_cfg,
                                    "gap_sites": P, "T_hat": T, "relax_sweeps": sw,
                                    "l2": "512 MB buffer written between fills (L2 flush)"},
                         "mae": float(err.abs().mean()), "rmse": float(err.pow(2).mean().sqrt()),
@@ -824,7 +914,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", default=None,
                     choices=["sweep4096", "fill4096", "copy4096", "net4096", "net1024", "net128",
-                             "sweep64_4096"],
+                             "sweep64_4096", "trace4096", "trace1024"],
                     help="run a small fixed sweep workload for ncu instead of the benchmark")
     ap.add_argument("--workload", default="fill4096", choices=["fill4096", "config1024", "batch256", "warm1024",
                                                                 "warm4096", "chains1024", "ormodes1024", "dpsp"],

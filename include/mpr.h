@@ -311,6 +311,23 @@ void mpr_sweep_timing_read(int stop, double* ms, uint64_t* launches, double* sit
 void mpr_debug_wait_limit(uint64_t ns, int stall);
 
 /*
+ * Benchmark support: where the TILE sweep kernel's time goes (process-wide, applies to
+ * launches made after the call; not for concurrent use by several host threads).
+ * buf: device memory of `words` 64-bit words, cleared by the caller, or NULL to stop.
+ * Thread 0 of every block writes %globaltimer (ns) stamps into it: for the work item w of
+ * a launch (w = sweep within the launch x tiles + position in the launch's tile order),
+ * words 6w .. 6w + 5 are: item taken (before any wait), copy issued, copy landed, both
+ * colours updated, write-back issued, and blockIdx.x | SM id << 32; items beyond
+ * K = (words - 8192) / 6 are not stamped.  The 8192 words after item K - 1 hold, for the
+ * Algorithm 2 control step of sweep counter c, words 2 (c mod 4096) and + 1: the ticket that
+ * completed the sweep's tiles, and the control step published.  While a buffer is set,
+ * launches with accurate transcendentals run a separately compiled copy of the sweep
+ * kernel that writes the stamps (MPR_TRIG_FAST launches stamp nothing); results do not
+ * change.  words < 8192 disables the trace.
+ */
+void mpr_debug_trace(uint64_t* buf, uint64_t words);
+
+/*
  * Memory of released contexts.  Contexts take their device memory from a stream-ordered
  * pool per device owned by the library, which keeps what mpr_free releases so that the
  * next context of a similar size allocates without going back to the driver (no

@@ -495,6 +495,9 @@ SweepArgs sweep_args(const mpr_ctx* ctx, const Batch& b, bool use_ctl_a, double 
 // wait expire (process-wide; mpr_debug_wait_limit).
 std::atomic<unsigned long long> g_wait_ns{4000000000ull};
 std::atomic<int> g_stall{0};
+// Timestamp buffer of the sweep kernel (mpr_debug_trace): device words, their count.
+std::atomic<unsigned long long*> g_trace{nullptr};
+std::atomic<unsigned long long> g_trace_words{0};
 
 // Timing of the sweep kernel (mpr_sweep_timing_start / _read): CUDA events around every
 // tile-path sweep launch, on the context's stream, while enabled.
@@ -545,6 +548,11 @@ TileArgs tile_args(const mpr_ctx* ctx, const Batch& b, int mode, double a_fixed,
     T.i_max = p.i_max;
     T.wait_ns = g_wait_ns.load();
     T.stall = g_stall.load();
+    const unsigned long long words = g_trace_words.load();
+    if (g_trace.load() && words >= 2ull * kTraceCtl) {
+        T.trace = g_trace.load();
+        T.trace_items = (words - 2ull * kTraceCtl) / kTraceWords;
+    }
     return T;
 }
 
@@ -1572,6 +1580,11 @@ mpr_status mpr_time_sweeps(mpr_ctx* ctx, int n, double a, double* ms_per_sweep) 
     cudaEventDestroy(e1);
     *ms_per_sweep = (double)ms / (double)n;
     return MPR_OK;
+}
+
+void mpr_debug_trace(uint64_t* buf, uint64_t words) {
+    g_trace_words = buf ? (unsigned long long)words : 0ull;
+    g_trace = buf ? reinterpret_cast<unsigned long long*>(buf) : nullptr;
 }
 
 void mpr_debug_wait_limit(uint64_t ns, int stall) {

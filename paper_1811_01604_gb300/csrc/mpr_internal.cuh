@@ -171,7 +171,11 @@ struct TileArgs {
     int n_f, n_fit, i_max;
     unsigned long long wait_ns;   // limit of every inter-block wait
     int stall;                // test support: block 0 first waits on a flag that nothing sets
+    unsigned long long* trace;        // bench support: per-item timestamps (mpr_debug_trace), or nullptr
+    unsigned long long trace_items;   // items the trace holds before its control-step area
 };
+constexpr int kTraceWords = 6;        // per work item of the trace
+constexpr int kTraceCtl = 4096;       // control steps of the trace (by sweep counter modulo this)
 
 struct BlockWork {            // one sweep block: entry and first gap index of its chunk
     int entry;

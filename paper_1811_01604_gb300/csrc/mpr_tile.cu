@@ -192,6 +192,27 @@ __device__ __forceinline__ unsigned long long gtimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+// Bench support (mpr_debug_trace): thread 0 stamps the phases of its work items and the
+// control steps with the global timer, when the launch carries a trace buffer.  The item
+// stamps are compiled into a separate instantiation of the sweep kernel (TRACE), which
+// runs only while a trace buffer is set: in the kernel that runs otherwise they cost
+// about 1.5 % of a sweep.
+__device__ __forceinline__ void trace_item(const TileArgs& A, unsigned w, int k) {
+    if (A.trace && w < A.trace_items) A.trace[(unsigned long long)w * kTraceWords + k] = gtimer();
+}
+__device__ __forceinline__ void trace_block(const TileArgs& A, unsigned w) {
+    if (A.trace && w < A.trace_items) {
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        A.trace[(unsigned long long)w * kTraceWords + 5] =
+            (unsigned long long)blockIdx.x | ((unsigned long long)smid << 32);
+    }
+}
+__device__ __forceinline__ void trace_ctl(const TileArgs& A, uint32_t sig, int k) {
+    if (A.trace)
+        A.trace[A.trace_items * kTraceWords + 2ull * (sig % (uint32_t)kTraceCtl) + (unsigned)k] = gtimer();
+}
+
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -305,11 +326,13 @@ struct GridCache {
 // completes the sweep's tiles runs the grid's Algorithm 2 control step from the totals --
 // after the control step of sweep sig - 1, which a fixed-window launch may still be
 // running -- and publishes it.
+template <bool TRACE>
 __device__ void tile_ticket(const TileArgs& A, int e, uint32_t sig, int n) {
     const int slot = e * kSlots + (int)(sig & (uint32_t)(kSlots - 1));
     fence_acq_rel();                          // the block's flushes (after a barrier) before the ticket
     const unsigned prev = atomicAdd(A.ticket + slot, (unsigned)n);
     if (prev + (unsigned)n != (unsigned)A.ents[e].ntiles) return;
+    if (TRACE) trace_ctl(A, sig, 0);
     fence_acq_rel();                          // every block's flushes before the totals are read
     Ctl* cp = A.ctl + e;
     // a fixed-window launch may still be running the control step of sweep sig - 1; in the
@@ -322,6 +345,7 @@ __device__ void tile_ticket(const TileArgs& A, int e, uint32_t sig, int n) {
     control_step(c, A.ents[e], (double)f * kDEUnit, na, A.mode, A.A_targ, A.k_a, A.n_f, A.n_fit,
                  A.i_max, A.ehist + (long long)e * A.ehist_stride, 1);
     ctl_publish(cp, c);
+    if (TRACE) trace_ctl(A, sig, 1);
     if (A.relax && c.stop) atomicSub(A.live, 1);
 }
 
@@ -347,7 +371,7 @@ __device__ void tile_ticket(const TileArgs& A, int e, uint32_t sig, int n) {
 // slot of the grid's totals and thread 0 adds the block's tile count to the slot's
 // ticket.  The block that completes a sweep's tiles runs the grid's control step.
 // The interior rows of both planes go back to the other lattice buffer as 16-byte stores.
-template <int TH, int TW, int TRIG, bool ACC, int NT, int MB>
+template <int TH, int TW, int TRIG, bool ACC, int NT, int MB, bool TRACE = false>
 __global__ void __launch_bounds__(NT, MB)
 k_tile_sweep(const TileArgs A) {
     static_assert(TW % 8 == 0, "write-back in 16-byte vectors");
@@ -362,6 +386,7 @@ k_tile_sweep(const TileArgs A) {
     __shared__ int s_fail, s_flush, s_ke, s_kn, s_last, s_pub_t;
     __shared__ uint32_t s_ksig, s_pub_sig;
     __shared__ unsigned s_w0;
+    __shared__ unsigned s_wcur;           // the staged item (trace)
     unsigned w1 = 0u;                     // thread 0: the item after s_w0 (an atomic in flight)
     __shared__ long long s_fx[NT];
     __shared__ unsigned s_nat[NT];
@@ -418,6 +443,7 @@ k_tile_sweep(const TileArgs A) {
         for (;;) {
             const unsigned w = s_w0;
             if (w >= nitems) { sp.t = -1; return; }
+            if (TRACE) trace_item(A, w, 0);
             asm volatile("cp.async.wait_all;" ::: "memory");          // the descriptor of w
             const TileDesc d = dnext;
             const unsigned wn = w1;
@@ -518,6 +544,11 @@ k_tile_sweep(const TileArgs A) {
             P.pl0 = gc.pl0;
             P.pl1 = gc.pl1;
             sp = P;
+            if (TRACE) {
+                s_wcur = w;
+                trace_item(A, w, 1);
+                trace_block(A, w);
+            }
             const uint32_t lbytes = ((uint32_t)(d.nA_int + d.nA_ring + d.nB) * 2u + 15u) & ~15u;
             mbar_expect_tx(&bar, kBytes + lbytes);
             tma_load_3d(&sm[0][0][0], A.maps + 2 * e + cur, &bar, d.x0 >> 1, d.y0 - 1, 0);
@@ -579,6 +610,7 @@ k_tile_sweep(const TileArgs A) {
         if (it > 0) {
             __syncthreads();                                      // B0: write-back and flushes issued
             if (threadIdx.x == 0) {
+                if (TRACE) trace_item(A, s_wcur, 4);
                 // the previous item is done (a relaxation's items wait for control steps,
                 // not for tiles: their counters are set when the launch ends)
                 if (!A.relax) {
@@ -587,7 +619,7 @@ k_tile_sweep(const TileArgs A) {
                 }
                 if (s_flush) {
                     publish();
-                    tile_ticket(A, s_ke, s_ksig, s_kn);
+                    tile_ticket<TRACE>(A, s_ke, s_ksig, s_kn);
                     s_ke = -1;
                     s_kn = 0;
                 }
@@ -610,6 +642,7 @@ k_tile_sweep(const TileArgs A) {
             break;
         }
         (void)mbar_test(&bar, parity);                            // each thread acquires the copy
+        if (TRACE && threadIdx.x == 0) trace_item(A, s_wcur, 2);
         const int y0 = g0.y, x0 = g0.z, W = g0.w;
         const int4 g1 = *reinterpret_cast<const int4*>(&sp.chain);
         const int4 g2 = *reinterpret_cast<const int4*>(&sp.nA_int);
@@ -695,6 +728,7 @@ k_tile_sweep(const TileArgs A) {
         if (threadIdx.x == 0) s_flush = next_differs(e, sweep) ? 1 : 0;
         fence_proxy_async_smem();                         // this thread's stage writes before the next copy into it
         __syncthreads();                                  // B3: colour B done
+        if (TRACE && threadIdx.x == 0) trace_item(A, s_wcur, 3);
         const int4 g3 = *reinterpret_cast<const int4*>(&sp.nfull);
         // interior rows of both colours to the other buffer (samples included), 16 bytes
         // per thread and step, one warp per row; rows and columns beyond the grid skipped
@@ -724,7 +758,7 @@ k_tile_sweep(const TileArgs A) {
         if (ke >= 0 && s_kn > 0) {
             flush_partials(ke, s_ksig);
             __syncthreads();
-            if (threadIdx.x == 0) tile_ticket(A, ke, s_ksig, s_kn);
+            if (threadIdx.x == 0) tile_ticket<TRACE>(A, ke, s_ksig, s_kn);
         }
     }
     // leave: the last block out resets the counters for the next launch and records every
@@ -939,6 +973,10 @@ int blocks_for() {
                          cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_tile_sweep<TH, TW, TRIG_FAST, false, NT, MB>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_tile_sweep<TH, TW, TRIG_ACCURATE, true, NT, MB, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_tile_sweep<TH, TW, TRIG_ACCURATE, false, NT, MB, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -969,14 +1007,35 @@ cudaError_t launch_tile_lists(int cfg, TileDesc* tiles, int ntiles, const EntryD
     return cudaGetLastError();
 }
 
+// Streaming multiprocessors of the current device (looked up once, like the block counts).
+int device_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0, n = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        sms = std::max(1, n);
+    }
+    return sms;
+}
+
 template <int TH, int TW, int NT, int MB>
 void sweep_for(const TileArgs& a, int trig, cudaStream_t st) {
     constexpr int sm = Cfg<TH, TW>::SMEM;
-    // persistent: at most the resident blocks, and no more than the launch's items
+    // persistent: at most the resident blocks, and no more than the launch's items.  With
+    // fewer tiles per sweep than resident blocks, at most as many blocks per SM as a sweep
+    // has tiles per SM (rounded up): blocks take items in order, so with the full grid the
+    // tiles of one sweep land on a random subset of the blocks and pile up to 4 on some
+    // SMs while others idle, and a sweep lasts as long as its most crowded SM.
     const long long items = (long long)a.ntiles * a.nsweeps;
-    const int nb = (int)std::min<long long>(items, tile_sweep_blocks(a.cfg));
+    const int sms = device_sms();
+    const int per_sweep = sms * std::max(1, (a.ntiles + sms - 1) / sms);
+    const int nb = (int)std::min<long long>(items, std::min(per_sweep, tile_sweep_blocks(a.cfg)));
     const bool acc = a.acc != nullptr;
-    if (trig == TRIG_FAST) {
+    if (a.trace && trig == TRIG_ACCURATE) {            // bench support: the stamped kernel
+        if (acc) k_tile_sweep<TH, TW, TRIG_ACCURATE, true, NT, MB, true><<<nb, NT, sm, st>>>(a);
+        else k_tile_sweep<TH, TW, TRIG_ACCURATE, false, NT, MB, true><<<nb, NT, sm, st>>>(a);
+    } else if (trig == TRIG_FAST) {
         if (acc) k_tile_sweep<TH, TW, TRIG_FAST, true, NT, MB><<<nb, NT, sm, st>>>(a);
         else k_tile_sweep<TH, TW, TRIG_FAST, false, NT, MB><<<nb, NT, sm, st>>>(a);
     } else {

@@ -85,6 +85,7 @@ _SIGS = [
     ("mpr_sweep_timing_read", None, [_I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_uint64),
                                      ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     ("mpr_debug_wait_limit", None, [ctypes.c_uint64, _I]),
+    ("mpr_debug_trace", None, [_VP, ctypes.c_uint64]),
     ("mpr_release_memory", _I, []),
     ("mpr_sample_energy_static", _I, [_VP, _VP, _I, _I, _D, ctypes.POINTER(_D),
                                       ctypes.POINTER(ctypes.c_longlong), _VP]),
@@ -415,6 +416,15 @@ def mpr_sweep_timing_read(stop: bool = True) -> dict:
     lib().mpr_sweep_timing_read(1 if stop else 0, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(ss),
                                 ctypes.byref(gu))
     return dict(ms=ms.value, launches=int(n.value), site_sweeps=ss.value, gap_updates=gu.value)
+
+
+def mpr_debug_trace(buf=None) -> None:
+    """Bench support: per-item timestamps of the sweep kernel into a cleared int64 CUDA
+    tensor (None stops); the layout is in include/mpr.h."""
+    if buf is None:
+        lib().mpr_debug_trace(None, 0)
+    else:
+        lib().mpr_debug_trace(_ptr(buf), int(buf.numel()))
 
 
 def mpr_debug_wait_limit(ns: int = 0, stall: bool = False) -> None:

@@ -189,3 +189,42 @@ def test_expired_wait_returns_timeout_and_gpu_stays_usable(phase):
     # the device and the library are fine: a fresh context gives the same state as before
     after = reference()
     assert np.array_equal(before.view(np.uint32), after.view(np.uint32))
+
+
+def test_trace_stamps_every_item_and_changes_nothing():
+    # the bench's timestamps (mpr_debug_trace): every work item of a fixed-window launch is
+    # stamped in order (taken, copy issued, copy landed, updated, written back), every
+    # control step has its ticket before its publication, and the lattice is bitwise what
+    # the same sweeps give without the trace
+    import torch
+    z, mask = _grid(290, 1530, 31)
+    ntiles = 10 * 12                                   # 32 x 128 tiles
+    states = []
+    for traced in (False, True):
+        ctx = _ctx(z, mask, seed=5, tile_cfg=2)
+        try:
+            mpr.mpr_set_T(ctx, 0.07)
+            buf = torch.zeros(ntiles * 12 * 6 + 8192, dtype=torch.int64, device="cuda")
+            if traced:
+                mpr.mpr_debug_trace(buf)
+            try:
+                mpr.mpr_sweep(ctx, 12, 1.0)
+                torch.cuda.synchronize()
+            finally:
+                mpr.mpr_debug_trace(None)
+            states.append(_state(ctx, z.shape)[0])
+        finally:
+            mpr.mpr_free(ctx)
+    assert np.array_equal(states[0].view(np.uint32), states[1].view(np.uint32))
+    t = buf.cpu().numpy().astype(np.int64)
+    it = t[: ntiles * 12 * 6].reshape(-1, 6)
+    assert np.all(it[:, :4] > 0)
+    assert np.all(np.diff(it[:, :4], axis=1) >= 0)
+    done = it[:, 4] > 0
+    assert done.sum() >= len(it) - 152 * 8             # all but each block's last item
+    assert np.all(it[done, 4] >= it[done, 3])
+    blocks = it[:, 5] & 0xFFFFFFFF
+    assert blocks.max() < 152 * 8
+    ctl = t[ntiles * 12 * 6:].reshape(-1, 2)
+    ctl = ctl[ctl[:, 0] > 0]
+    assert len(ctl) == 12 and np.all(ctl[:, 1] >= ctl[:, 0])
