@@ -438,7 +438,7 @@ def run_batch(args):
                 net.warmstart(ctx)
             mpr.mpr_equilibrate(ctx)
             mpr.mpr_predict_batch(ctx, Mb, outs)
-            info = [mpr.mpr_batch_info(ctx, g) for g in range(len(zs))]
+            info = mpr.mpr_batch_info_all(ctx)
         finally:
             mpr.mpr_free(ctx)
         return info, tune

@@ -232,6 +232,12 @@ mpr_status mpr_fill_batch(mpr_ctx* ctx, float* const* zhat);
 mpr_status mpr_batch_info(mpr_ctx* ctx, int g, double* T, double* e_s, int* sweeps, int* converged,
                           double* zmin, double* zmax);
 
+/* The same for all n grids of the batch in one read of the control state (one host
+   synchronisation instead of one per grid): each non-NULL pointer is an array of n = the
+   batch size.  EINVAL if n differs from the batch size. */
+mpr_status mpr_batch_info_all(mpr_ctx* ctx, int n, double* T, double* e_s, int* sweeps, int* converged,
+                              double* zmin, double* zmax);
+
 /*
  * Autotuner of the TILE kernels: times a few sweeps of every compiled tile shape on the
  * context's own grids (starting from a snapshot of the state, which is restored, so the

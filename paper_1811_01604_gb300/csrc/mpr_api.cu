@@ -41,6 +41,7 @@ namespace {
 constexpr int kMaxGraphSweeps = 64;       // longest captured chunk of sweeps
 constexpr int kDefaultGraphSweeps = 8;    // sweeps per captured chunk unless autotuned
 constexpr int kScratch = 2048;            // doubles of reduction scratch
+constexpr int kFan = 8;                   // auxiliary streams of a batch's per-grid set-up work
 constexpr int kMaxChains = 128;           // independent chains of one grid (mpr_predict_chains)
 constexpr uint32_t kChainStride = 1u << 24; // chain word offset between forked chains
 
@@ -73,6 +74,7 @@ struct Batch {
     int* d_chunks = nullptr;               // chunks run by the device-side relaxation loop
     int gsweeps = kDefaultGraphSweeps;     // sweeps per captured chunk (loop condition once per chunk)
     double* d_scratch = nullptr;
+    int nscratch = 1;                      // reduction scratch slots (one per auxiliary stream of the fan)
     double* d_H = nullptr;                 // one exact energy per entry
     bool f64 = false;                      // lattice of double2 and d_acc of doubles (MPR_PREC_F64)
     // tile path (fused sweeps over shared-memory tiles, two lattice buffers)
@@ -132,6 +134,9 @@ struct mpr_ctx {
     Batch b;
     int* h_active = nullptr;               // pinned
     std::string err;
+    int nfan = 0;                          // auxiliary streams in use (batches of 2 or more grids)
+    cudaStream_t fan[kFan] = {};
+    cudaEvent_t fan_ev[kFan + 1] = {};     // one per auxiliary stream, and the fork
 };
 
 namespace {
@@ -211,6 +216,50 @@ void dfree(void* p, cudaStream_t st) {
 constexpr int kPinSlotInts = 4, kPinSlotsPerArena = 256;
 std::mutex g_pin_mu;
 std::vector<int*> g_pin_free;
+
+// A batch's per-grid set-up work (input copies and small kernels, one grid each) goes
+// round-robin over up to kFan auxiliary streams that first wait for the context's stream;
+// the context's stream then waits for all of them.  The grids' small launches run side by
+// side instead of one after another.  A single grid keeps everything on the context's
+// stream.  Streams and events are made on first use and released by mpr_free.
+cudaError_t fan_begin(mpr_ctx* ctx, int n) {
+    if (n < 2 && !ctx->nfan) return cudaSuccess;
+    if (!ctx->nfan) {
+        const int k = std::min(kFan, n);
+        cudaError_t e = cudaEventCreateWithFlags(&ctx->fan_ev[kFan], cudaEventDisableTiming);
+        for (int i = 0; i < k && e == cudaSuccess; ++i) {
+            e = cudaStreamCreateWithFlags(&ctx->fan[i], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fan_ev[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) ctx->nfan = i + 1;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaEventRecord(ctx->fan_ev[kFan], ctx->st);
+    for (int i = 0; i < ctx->nfan && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(ctx->fan[i], ctx->fan_ev[kFan], 0);
+    return e;
+}
+cudaStream_t fan_stream(const mpr_ctx* ctx, int i) { return ctx->nfan ? ctx->fan[i % ctx->nfan] : ctx->st; }
+cudaError_t fan_end(mpr_ctx* ctx) {
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < ctx->nfan && e == cudaSuccess; ++i) {
+        e = cudaEventRecord(ctx->fan_ev[i], ctx->fan[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->st, ctx->fan_ev[i], 0);
+    }
+    return e;
+}
+void fan_release(mpr_ctx* ctx) {
+    for (int i = 0; i < ctx->nfan; ++i) {
+        cudaStreamDestroy(ctx->fan[i]);
+        cudaEventDestroy(ctx->fan_ev[i]);
+    }
+    if (ctx->fan_ev[kFan]) cudaEventDestroy(ctx->fan_ev[kFan]);
+    ctx->nfan = 0;
+}
+// Reduction scratch slot k of a batch (k < nscratch): kScratch doubles each; slot 0 is
+// followed by 8 doubles of single results, then slots 1, 2, ...
+double* fan_scratch(const Batch& b, int k) {
+    return k == 0 ? b.d_scratch : b.d_scratch + kScratch + 8 + (size_t)(k - 1) * kScratch;
+}
 
 cudaError_t pinned_slot(int** out) {
     std::lock_guard<std::mutex> lk(g_pin_mu);
@@ -371,22 +420,25 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
     b.lat_elems = lat;
     CU(dalloc(&b.d_lat, lat * wide, st));
     CU(cudaMemsetAsync(b.d_lat, 0, lat * wide * sizeof(float2), st));
-    for (int e = 0; e < b.n_ent; ++e)
-        CU(launch_pack(&b.ents[e], grids[e].z, grids[e].mask, grids[e].zmin, grids[e].scale, b.d_lat,
-                       k0, k1, all_free, b.f64, st));
     // gap lists: per-row counts of both colours (2 H ints per entry, all entries in one
     // buffer), scanned in place into row offsets; one read-back of the totals sizes the gap
-    // buffer, then every entry's list is scattered from its own offsets
+    // buffer, then every entry's list is scattered from its own offsets.  Each entry's
+    // pack, counts and scan on one stream of the batch's fan.
     std::vector<size_t> roff((size_t)b.n_ent + 1, 0);
     for (int e = 0; e < b.n_ent; ++e) roff[e + 1] = roff[e] + (size_t)2 * b.ents[e].H;
     int* d_rows = nullptr;
     int* d_tot = nullptr;
     CU(dalloc(&d_rows, roff[b.n_ent], st));
     CU(dalloc(&d_tot, (size_t)2 * b.n_ent, st));
+    CU(fan_begin(ctx, b.n_ent));
     for (int e = 0; e < b.n_ent; ++e) {
-        CU(launch_gap_count(&b.ents[e], grids[e].mask, all_free, d_rows + roff[e], st));
-        CU(launch_scan_rows(d_rows + roff[e], b.ents[e].H, 2, d_tot + 2 * e, st));
+        const cudaStream_t se = fan_stream(ctx, e);
+        CU(launch_pack(&b.ents[e], grids[e].z, grids[e].mask, grids[e].zmin, grids[e].scale, b.d_lat,
+                       k0, k1, all_free, b.f64, se));
+        CU(launch_gap_count(&b.ents[e], grids[e].mask, all_free, d_rows + roff[e], se));
+        CU(launch_scan_rows(d_rows + roff[e], b.ents[e].H, 2, d_tot + 2 * e, se));
     }
+    CU(fan_end(ctx));
     std::vector<int> tot((size_t)2 * b.n_ent);
     CU(cudaMemcpyAsync(tot.data(), d_tot, sizeof(int) * tot.size(), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
@@ -403,8 +455,11 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
     b.n_gaps = ng;
     CU(dalloc(&b.d_gaps, ng, st));
     CU(dalloc(&b.d_acc, ng * wide, st));
+    CU(fan_begin(ctx, b.n_ent));
     for (int e = 0; e < b.n_ent; ++e)
-        CU(launch_gap_scatter(&b.ents[e], grids[e].mask, all_free, d_rows + roff[e], b.d_gaps, st));
+        CU(launch_gap_scatter(&b.ents[e], grids[e].mask, all_free, d_rows + roff[e], b.d_gaps,
+                              fan_stream(ctx, e)));
+    CU(fan_end(ctx));
     dfree(d_rows, st);
     dfree(d_tot, st);
     // sweep work lists
@@ -460,7 +515,8 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
     CU(cudaMemsetAsync(b.d_ehist, 0, sizeof(double) * (size_t)b.n_ent * b.ehist_stride, st));
     CU(dalloc(&b.d_active, kMaxGraphSweeps, st));
     CU(dalloc(&b.d_chunks, 1, st));
-    CU(dalloc(&b.d_scratch, kScratch + 8, st));
+    b.nscratch = std::max(1, ctx->nfan);
+    CU(dalloc(&b.d_scratch, kScratch + 8 + (size_t)(b.nscratch - 1) * kScratch, st));
     CU(dalloc(&b.d_H, (size_t)b.n_ent, st));
     CU(cudaStreamSynchronize(st));
     return MPR_OK;
@@ -798,8 +854,17 @@ mpr_status reset_tracked_energy(mpr_ctx* ctx, Batch& b) {
     std::vector<Ctl> c;
     mpr_status s = read_ctl(ctx, b, c);
     if (s != MPR_OK) return s;
-    for (int e = 0; e < b.n_ent; ++e)
-        CU(launch_energy(&b.ents[e], lat_cur(b, c[e]), b.d_scratch, kScratch, b.d_H + e, b.f64, ctx->st));
+    // on the fan only where this batch has a scratch slot per auxiliary stream
+    if (b.n_ent >= 2 && ctx->nfan > 0 && b.nscratch == ctx->nfan) {
+        CU(fan_begin(ctx, b.n_ent));
+        for (int e = 0; e < b.n_ent; ++e)
+            CU(launch_energy(&b.ents[e], lat_cur(b, c[e]), fan_scratch(b, e % ctx->nfan), kScratch,
+                             b.d_H + e, b.f64, fan_stream(ctx, e)));
+        CU(fan_end(ctx));
+    } else {
+        for (int e = 0; e < b.n_ent; ++e)
+            CU(launch_energy(&b.ents[e], lat_cur(b, c[e]), b.d_scratch, kScratch, b.d_H + e, b.f64, ctx->st));
+    }
     CU(launch_set_tracked_energy(b.d_ctl, b.d_H, b.n_ent, ctx->st));
     return MPR_OK;
 }
@@ -953,6 +1018,7 @@ void mpr_free(mpr_ctx* ctx) {
     // the work already enqueued finishes before its buffers and graphs go (the frees are
     // stream-ordered on the caller's stream)
     cudaStreamSynchronize(ctx->st);
+    for (int i = 0; i < ctx->nfan; ++i) cudaStreamSynchronize(ctx->fan[i]);   // an early return may leave work there
     batch_free(ctx->b, ctx->st);
     dfree(ctx->d_z, ctx->st);
     dfree(ctx->d_mask, ctx->st);
@@ -960,6 +1026,7 @@ void mpr_free(mpr_ctx* ctx) {
     dfree(ctx->d_stop, ctx->st);
     release_pinned_slot(ctx->h_active);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    fan_release(ctx);
     delete ctx;
 }
 
@@ -1019,12 +1086,8 @@ static mpr_status init_grids(mpr_ctx** out, int n, const float* const* z, const 
     const size_t N = (size_t)site0;
     if (dalloc(&ctx->d_z, N, ctx->st) != cudaSuccess || dalloc(&ctx->d_mask, N, ctx->st) != cudaSuccess ||
         dalloc(&ctx->d_out, N, ctx->st) != cudaSuccess) { cudaGetLastError(); return bail(MPR_ENOMEM); }
-    for (int i = 0; i < n; ++i) {
-        const size_t ni = (size_t)W[i] * H[i];
-        CUI(cudaMemcpyAsync(ctx->d_z + ctx->g[i].site0, z[i], ni * sizeof(float), cudaMemcpyDefault, ctx->st));
-        CUI(cudaMemcpyAsync(ctx->d_mask + ctx->g[i].site0, mask[i], ni, cudaMemcpyDefault, ctx->st));
-    }
-    // Eq. 1 extremes, per grid
+    // Eq. 1 extremes, per grid (each grid's input copies and extremes on one stream of the
+    // batch's fan)
     unsigned* d_keys = nullptr;
     unsigned long long* d_ns = nullptr;
     CUI(dalloc(&d_keys, (size_t)2 * n, ctx->st));
@@ -1036,9 +1099,16 @@ static mpr_status init_grids(mpr_ctx** out, int n, const float* const* z, const 
     }
     CUI(cudaMemcpyAsync(d_keys, keys.data(), sizeof(unsigned) * 2 * n, cudaMemcpyHostToDevice, ctx->st));
     CUI(cudaMemsetAsync(d_ns, 0, sizeof(unsigned long long) * n, ctx->st));
-    for (int i = 0; i < n; ++i)
+    CUI(fan_begin(ctx, n));
+    for (int i = 0; i < n; ++i) {
+        const size_t ni = (size_t)W[i] * H[i];
+        const cudaStream_t si = fan_stream(ctx, i);
+        CUI(cudaMemcpyAsync(ctx->d_z + ctx->g[i].site0, z[i], ni * sizeof(float), cudaMemcpyDefault, si));
+        CUI(cudaMemcpyAsync(ctx->d_mask + ctx->g[i].site0, mask[i], ni, cudaMemcpyDefault, si));
         CUI(launch_minmax(ctx->d_z + ctx->g[i].site0, ctx->d_mask + ctx->g[i].site0,
-                          (long long)W[i] * H[i], d_keys + 2 * i, d_ns + i, ctx->st));
+                          (long long)W[i] * H[i], d_keys + 2 * i, d_ns + i, si));
+    }
+    CUI(fan_end(ctx));
     std::vector<unsigned long long> ns((size_t)n);
     CUI(cudaMemcpyAsync(keys.data(), d_keys, sizeof(unsigned) * 2 * n, cudaMemcpyDeviceToHost, ctx->st));
     CUI(cudaMemcpyAsync(ns.data(), d_ns, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, ctx->st));
@@ -1075,14 +1145,16 @@ static mpr_status init_grids(mpr_ctx** out, int n, const float* const* z, const 
     unsigned long long* d_pc = nullptr;
     CUI(dalloc(&d_ps, poff[n], ctx->st));
     CUI(dalloc(&d_pc, poff[n], ctx->st));
+    CUI(fan_begin(ctx, n));
     for (int i = 0; i < n; ++i) {
         GridInfo& G = ctx->g[i];
         int np = 0;
         CUI(launch_sample_energy(&ctx->b.ents[i], ctx->d_z + G.site0, ctx->d_mask + G.site0, G.scale,
                                  ctx->prm.q, d_ps + poff[i], d_pc + poff[i], &np,
-                                 ctx->prm.precision == MPR_PREC_F64, ctx->st));
+                                 ctx->prm.precision == MPR_PREC_F64, fan_stream(ctx, i)));
         if ((size_t)np != poff[i + 1] - poff[i]) return bail(MPR_ECUDA);
     }
+    CUI(fan_end(ctx));
     std::vector<double> ps(poff[n]);
     std::vector<unsigned long long> pc(poff[n]);
     CUI(cudaMemcpyAsync(ps.data(), d_ps, sizeof(double) * poff[n], cudaMemcpyDeviceToHost, ctx->st));
@@ -1258,11 +1330,13 @@ static mpr_status predict_all(mpr_ctx* ctx, int M, float* const* out) {
                                   G.zmax, ctx->d_out + G.site0, b.f64, ctx->st));
         }
     }
+    CU(fan_begin(ctx, (int)ctx->g.size()));
     for (size_t i = 0; i < ctx->g.size(); ++i) {
         const GridInfo& G = ctx->g[i];
         CU(cudaMemcpyAsync(out[i], ctx->d_out + G.site0, (size_t)G.W * G.H * sizeof(float),
-                           cudaMemcpyDefault, ctx->st));
+                           cudaMemcpyDefault, fan_stream(ctx, (int)i)));
     }
+    CU(fan_end(ctx));
     CU(cudaStreamSynchronize(ctx->st));
     return MPR_OK;
 }
@@ -1417,6 +1491,24 @@ mpr_status mpr_batch_info(mpr_ctx* ctx, int g, double* T, double* e_s, int* swee
     if (converged) *converged = c[g].converged;
     if (zmin) *zmin = G.zmin;
     if (zmax) *zmax = G.zmax;
+    return MPR_OK;
+}
+
+mpr_status mpr_batch_info_all(mpr_ctx* ctx, int n, double* T, double* e_s, int* sweeps, int* converged,
+                              double* zmin, double* zmax) {
+    if (!ctx || n != (int)ctx->g.size()) return MPR_EINVAL;
+    std::vector<Ctl> c;
+    mpr_status s = read_ctl(ctx, ctx->b, c);
+    if (s != MPR_OK) return s;
+    for (int g = 0; g < n; ++g) {
+        const GridInfo& G = ctx->g[g];
+        if (T) T[g] = G.T;
+        if (e_s) e_s[g] = G.e_s;
+        if (sweeps) sweeps[g] = c[g].i;
+        if (converged) converged[g] = c[g].converged;
+        if (zmin) zmin[g] = G.zmin;
+        if (zmax) zmax[g] = G.zmax;
+    }
     return MPR_OK;
 }
 

@@ -73,6 +73,7 @@ _SIGS = [
     ("mpr_fill_batch", _I, [_VP, _VP]),
     ("mpr_batch_info", _I, [_VP, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I),
                             ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    ("mpr_batch_info_all", _I, [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("mpr_autotune", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     ("mpr_free", None, [_VP]),
     ("mpr_last_error", ctypes.c_char_p, [_VP]),
@@ -274,6 +275,17 @@ def mpr_batch_info(ctx, g: int) -> dict:
                                      ctypes.byref(cv), ctypes.byref(zmin), ctypes.byref(zmax)))
     return dict(T=T.value, e_s=es.value, sweeps=sw.value, converged=cv.value, zmin=zmin.value,
                 zmax=zmax.value)
+
+
+def mpr_batch_info_all(ctx) -> list:
+    """mpr_batch_info of every grid of the batch, in one read of the control state."""
+    n = mpr_batch_size(ctx)
+    T, es, zmin, zmax = (np.zeros(n, np.float64) for _ in range(4))
+    sw, cv = np.zeros(n, np.int32), np.zeros(n, np.int32)
+    _check(ctx, lib().mpr_batch_info_all(ctx, n, T.ctypes.data, es.ctypes.data, sw.ctypes.data, cv.ctypes.data,
+                                         zmin.ctypes.data, zmax.ctypes.data))
+    return [dict(T=float(T[g]), e_s=float(es[g]), sweeps=int(sw[g]), converged=int(cv[g]), zmin=float(zmin[g]),
+                 zmax=float(zmax[g])) for g in range(n)]
 
 
 def mpr_autotune(ctx) -> dict:

@@ -109,6 +109,7 @@ def test_batch_fill_quality_and_per_grid_temperatures():
         outs = [np.zeros_like(z) for z in zs]
         mpr.mpr_fill_batch(ctx, outs)
         info = [mpr.mpr_batch_info(ctx, i) for i in range(len(zs))]
+        assert mpr.mpr_batch_info_all(ctx) == info          # one read of every grid's state
     finally:
         mpr.mpr_free(ctx)
     for z, m, o, inf in zip(zs, ms, outs, info):
