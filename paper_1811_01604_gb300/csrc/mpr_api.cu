@@ -430,15 +430,33 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
     int* d_tot = nullptr;
     CU(dalloc(&d_rows, roff[b.n_ent], st));
     CU(dalloc(&d_tot, (size_t)2 * b.n_ent, st));
-    CU(fan_begin(ctx, b.n_ent));
-    for (int e = 0; e < b.n_ent; ++e) {
-        const cudaStream_t se = fan_stream(ctx, e);
-        CU(launch_pack(&b.ents[e], grids[e].z, grids[e].mask, grids[e].zmin, grids[e].scale, b.d_lat,
-                       k0, k1, all_free, b.f64, se));
-        CU(launch_gap_count(&b.ents[e], grids[e].mask, all_free, d_rows + roff[e], se));
-        CU(launch_scan_rows(d_rows + roff[e], b.ents[e].H, 2, d_tot + 2 * e, se));
+    // several entries: each step one launch for all of them, from a table of set-up
+    // records and an early copy of the entry table (layout fields; the gap counts follow)
+    SetupRec* d_recs = nullptr;
+    long long max_sites = 0;
+    int max_rows = 0;
+    CU(dalloc(&b.d_ents, b.n_ent, st));
+    if (b.n_ent > 1) {
+        std::vector<SetupRec> recs((size_t)b.n_ent);
+        for (int e = 0; e < b.n_ent; ++e) {
+            const EntryDesc& E = b.ents[e];
+            recs[e] = SetupRec{grids[e].z, grids[e].mask, grids[e].zmin, grids[e].scale, (long long)E.W * E.H,
+                               (int)roff[e], 0, 0};
+            max_sites = std::max(max_sites, recs[e].n);
+            max_rows = std::max(max_rows, E.H);
+        }
+        CU(dalloc(&d_recs, (size_t)b.n_ent, st));
+        CU(cudaMemcpyAsync(d_recs, recs.data(), sizeof(SetupRec) * b.n_ent, cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(b.d_ents, b.ents.data(), b.n_ent * sizeof(EntryDesc), cudaMemcpyHostToDevice, st));
+        CU(launch_pack_batch(b.d_ents, d_recs, b.n_ent, max_sites, b.d_lat, k0, k1, all_free, b.f64, st));
+        CU(launch_gap_count_batch(b.d_ents, d_recs, b.n_ent, max_rows, all_free, d_rows, st));
+        CU(launch_scan_rows_batch(b.d_ents, d_recs, b.n_ent, d_rows, d_tot, st));
+    } else {
+        CU(launch_pack(&b.ents[0], grids[0].z, grids[0].mask, grids[0].zmin, grids[0].scale, b.d_lat,
+                       k0, k1, all_free, b.f64, st));
+        CU(launch_gap_count(&b.ents[0], grids[0].mask, all_free, d_rows, st));
+        CU(launch_scan_rows(d_rows, b.ents[0].H, 2, d_tot, st));
     }
-    CU(fan_end(ctx));
     std::vector<int> tot((size_t)2 * b.n_ent);
     CU(cudaMemcpyAsync(tot.data(), d_tot, sizeof(int) * tot.size(), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
@@ -455,13 +473,16 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
     b.n_gaps = ng;
     CU(dalloc(&b.d_gaps, ng, st));
     CU(dalloc(&b.d_acc, ng * wide, st));
-    CU(fan_begin(ctx, b.n_ent));
-    for (int e = 0; e < b.n_ent; ++e)
-        CU(launch_gap_scatter(&b.ents[e], grids[e].mask, all_free, d_rows + roff[e], b.d_gaps,
-                              fan_stream(ctx, e)));
-    CU(fan_end(ctx));
+    if (b.n_ent > 1) {
+        // the gap bases are in the host table now
+        CU(cudaMemcpyAsync(b.d_ents, b.ents.data(), b.n_ent * sizeof(EntryDesc), cudaMemcpyHostToDevice, st));
+        CU(launch_gap_scatter_batch(b.d_ents, d_recs, b.n_ent, max_rows, all_free, d_rows, b.d_gaps, st));
+    } else {
+        CU(launch_gap_scatter(&b.ents[0], grids[0].mask, all_free, d_rows, b.d_gaps, st));
+    }
     dfree(d_rows, st);
     dfree(d_tot, st);
+    dfree(d_recs, st);
     // sweep work lists
     const int chunk = kSweepThreads * kSweepItems;
     for (int c = 0; c < 2; ++c) {
@@ -480,7 +501,6 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
             CU(cudaMemcpyAsync(b.d_work[c], w.data(), w.size() * sizeof(BlockWork),
                                cudaMemcpyHostToDevice, st));
     }
-    CU(dalloc(&b.d_ents, b.n_ent, st));
     CU(cudaMemcpyAsync(b.d_ents, b.ents.data(), b.n_ent * sizeof(EntryDesc), cudaMemcpyHostToDevice, st));
     if (b.tiled) {
         CU(dalloc(&b.d_lat2, lat, st));
@@ -1099,16 +1119,31 @@ static mpr_status init_grids(mpr_ctx** out, int n, const float* const* z, const 
     }
     CUI(cudaMemcpyAsync(d_keys, keys.data(), sizeof(unsigned) * 2 * n, cudaMemcpyHostToDevice, ctx->st));
     CUI(cudaMemsetAsync(d_ns, 0, sizeof(unsigned long long) * n, ctx->st));
+    // set-up records of the grids (several grids: each step is one launch for all of them)
+    std::vector<SetupRec> recs((size_t)n);
+    long long max_sites = 0;
+    for (int i = 0; i < n; ++i) {
+        recs[i] = SetupRec{ctx->d_z + ctx->g[i].site0, ctx->d_mask + ctx->g[i].site0, 0.0, 0.0,
+                           (long long)W[i] * H[i], 0, 0, 0};
+        max_sites = std::max(max_sites, recs[i].n);
+    }
+    SetupRec* d_recs = nullptr;
+    if (n > 1) {
+        CUI(dalloc(&d_recs, (size_t)n, ctx->st));
+        CUI(cudaMemcpyAsync(d_recs, recs.data(), sizeof(SetupRec) * n, cudaMemcpyHostToDevice, ctx->st));
+    }
     CUI(fan_begin(ctx, n));
     for (int i = 0; i < n; ++i) {
         const size_t ni = (size_t)W[i] * H[i];
         const cudaStream_t si = fan_stream(ctx, i);
         CUI(cudaMemcpyAsync(ctx->d_z + ctx->g[i].site0, z[i], ni * sizeof(float), cudaMemcpyDefault, si));
         CUI(cudaMemcpyAsync(ctx->d_mask + ctx->g[i].site0, mask[i], ni, cudaMemcpyDefault, si));
-        CUI(launch_minmax(ctx->d_z + ctx->g[i].site0, ctx->d_mask + ctx->g[i].site0,
-                          (long long)W[i] * H[i], d_keys + 2 * i, d_ns + i, si));
+        if (n == 1)
+            CUI(launch_minmax(ctx->d_z + ctx->g[i].site0, ctx->d_mask + ctx->g[i].site0,
+                              (long long)W[i] * H[i], d_keys + 2 * i, d_ns + i, si));
     }
     CUI(fan_end(ctx));
+    if (n > 1) CUI(launch_minmax_batch(d_recs, n, max_sites, d_keys, d_ns, ctx->st));
     std::vector<unsigned long long> ns((size_t)n);
     CUI(cudaMemcpyAsync(keys.data(), d_keys, sizeof(unsigned) * 2 * n, cudaMemcpyDeviceToHost, ctx->st));
     CUI(cudaMemcpyAsync(ns.data(), d_ns, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, ctx->st));
@@ -1145,16 +1180,24 @@ static mpr_status init_grids(mpr_ctx** out, int n, const float* const* z, const 
     unsigned long long* d_pc = nullptr;
     CUI(dalloc(&d_ps, poff[n], ctx->st));
     CUI(dalloc(&d_pc, poff[n], ctx->st));
-    CUI(fan_begin(ctx, n));
-    for (int i = 0; i < n; ++i) {
-        GridInfo& G = ctx->g[i];
+    if (n == 1) {
+        GridInfo& G = ctx->g[0];
         int np = 0;
-        CUI(launch_sample_energy(&ctx->b.ents[i], ctx->d_z + G.site0, ctx->d_mask + G.site0, G.scale,
-                                 ctx->prm.q, d_ps + poff[i], d_pc + poff[i], &np,
-                                 ctx->prm.precision == MPR_PREC_F64, fan_stream(ctx, i)));
-        if ((size_t)np != poff[i + 1] - poff[i]) return bail(MPR_ECUDA);
+        CUI(launch_sample_energy(&ctx->b.ents[0], ctx->d_z + G.site0, ctx->d_mask + G.site0, G.scale,
+                                 ctx->prm.q, d_ps, d_pc, &np, ctx->prm.precision == MPR_PREC_F64, ctx->st));
+        if ((size_t)np != poff[1]) return bail(MPR_ECUDA);
+    } else {
+        int max_parts = 0;
+        for (int i = 0; i < n; ++i) {
+            recs[i].scale = ctx->g[i].scale;
+            recs[i].poff = (int)poff[i];
+            recs[i].nparts = (int)(poff[i + 1] - poff[i]);
+            max_parts = std::max(max_parts, recs[i].nparts);
+        }
+        CUI(cudaMemcpyAsync(d_recs, recs.data(), sizeof(SetupRec) * n, cudaMemcpyHostToDevice, ctx->st));
+        CUI(launch_sample_energy_batch(ctx->b.d_ents, d_recs, n, max_parts, ctx->prm.q, d_ps, d_pc,
+                                       ctx->prm.precision == MPR_PREC_F64, ctx->st));
     }
-    CUI(fan_end(ctx));
     std::vector<double> ps(poff[n]);
     std::vector<unsigned long long> pc(poff[n]);
     CUI(cudaMemcpyAsync(ps.data(), d_ps, sizeof(double) * poff[n], cudaMemcpyDeviceToHost, ctx->st));
@@ -1162,6 +1205,7 @@ static mpr_status init_grids(mpr_ctx** out, int n, const float* const* z, const 
     CUI(cudaStreamSynchronize(ctx->st));
     dfree(d_ps, ctx->st);
     dfree(d_pc, ctx->st);
+    dfree(d_recs, ctx->st);
     for (int i = 0; i < n; ++i) {
         GridInfo& G = ctx->g[i];
         double sum = 0.0;

@@ -1,6 +1,8 @@
 // mpr_init.cu -- set-up kernels: Eq. 1 map, lattice packing, gap lists, Eq. 4.
 //
 // These run once per grid (Algorithm 2, steps 2-4.1); the hot path is in mpr_sweep.cu.
+#include <algorithm>
+
 #include "mpr_internal.cuh"
 
 namespace mpr {
@@ -14,12 +16,13 @@ __device__ __forceinline__ unsigned float_key(float f) {
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
 
-// z_min, z_max and the number of samples over one grid (Eq. 1 needs the extremes).
-__global__ void k_minmax(const float* __restrict__ z, const uint8_t* __restrict__ mask,
-                         long long n, unsigned* keys, unsigned long long* nsamples) {
+// z_min, z_max and the number of samples over one grid (Eq. 1 needs the extremes); block
+// bid of nb (integer keys and counts: any partition gives the same result).
+__device__ __forceinline__ void minmax_body(const float* __restrict__ z, const uint8_t* __restrict__ mask,
+                                            long long n, unsigned* keys, unsigned long long* nsamples,
+                                            int bid, int nb) {
     unsigned kmin = 0xFFFFFFFFu, kmax = 0u, cnt = 0u;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
+    for (long long i = bid * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)nb * blockDim.x) {
         if (mask[i]) {
             const unsigned k = float_key(z[i]);
             kmin = min(kmin, k);
@@ -41,6 +44,14 @@ __global__ void k_minmax(const float* __restrict__ z, const uint8_t* __restrict_
         }
     }
 }
+__global__ void k_minmax(const float* __restrict__ z, const uint8_t* __restrict__ mask,
+                         long long n, unsigned* keys, unsigned long long* nsamples) {
+    minmax_body(z, mask, n, keys, nsamples, blockIdx.x, gridDim.x);
+}
+__global__ void k_minmax_batch(const SetupRec* __restrict__ recs, unsigned* keys, unsigned long long* nsamples) {
+    const SetupRec& r = recs[blockIdx.y];
+    minmax_body(r.z, r.mask, r.n, keys + 2 * blockIdx.y, nsamples + blockIdx.y, blockIdx.x, gridDim.x);
+}
 
 // Packs one grid into its two colour planes.  Samples get the Eq. 1 angle; gap sites
 // get phi = 2 pi u with u from the Philox stream {site, 0xFFFFFFFF, chain, 0}
@@ -59,12 +70,12 @@ __device__ __forceinline__ void unit_at(double theta, double2& v) {
 }
 
 template <typename V>
-__global__ void k_pack(EntryDesc e, const float* __restrict__ z, const uint8_t* __restrict__ mask,
-                       double zmin, double scale, V* __restrict__ lat, uint32_t key0,
-                       uint32_t key1, int all_free) {
+__device__ __forceinline__ void pack_body(const EntryDesc& e, const float* __restrict__ z,
+                                          const uint8_t* __restrict__ mask, double zmin, double scale,
+                                          V* __restrict__ lat, uint32_t key0, uint32_t key1, int all_free,
+                                          int bid, int nb) {
     const long long n = (long long)e.W * e.H;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
+    for (long long i = bid * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)nb * blockDim.x) {
         const int y = (int)(i / e.W), x = (int)(i - (long long)y * e.W);
         const int c = (x + y) & 1;
         double theta;
@@ -80,10 +91,23 @@ __global__ void k_pack(EntryDesc e, const float* __restrict__ z, const uint8_t* 
         unit_at(theta, lat[base + (long long)(y + 1) * e.pitch + (x >> 1) + kPadL]);
     }
 }
+template <typename V>
+__global__ void k_pack(EntryDesc e, const float* __restrict__ z, const uint8_t* __restrict__ mask,
+                       double zmin, double scale, V* __restrict__ lat, uint32_t key0,
+                       uint32_t key1, int all_free) {
+    pack_body(e, z, mask, zmin, scale, lat, key0, key1, all_free, blockIdx.x, gridDim.x);
+}
+template <typename V>
+__global__ void k_pack_batch(const EntryDesc* __restrict__ ents, const SetupRec* __restrict__ recs,
+                             V* __restrict__ lat, uint32_t key0, uint32_t key1, int all_free) {
+    const EntryDesc e = ents[blockIdx.y];
+    const SetupRec& r = recs[blockIdx.y];
+    pack_body(e, r.z, r.mask, r.zmin, r.scale, lat, key0, key1, all_free, blockIdx.x, gridDim.x);
+}
 
 // Number of gap sites of each colour in each row: row_counts[c * H + y].  One warp per row.
-__global__ void k_gap_count(EntryDesc e, const uint8_t* __restrict__ mask, int all_free,
-                            int* __restrict__ row_counts) {
+__device__ __forceinline__ void gap_count_body(const EntryDesc& e, const uint8_t* __restrict__ mask,
+                                               int all_free, int* __restrict__ row_counts) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= e.H) return;
     const int y = warp;
@@ -102,12 +126,20 @@ __global__ void k_gap_count(EntryDesc e, const uint8_t* __restrict__ mask, int a
         row_counts[e.H + y] = cnt[1];
     }
 }
+__global__ void k_gap_count(EntryDesc e, const uint8_t* __restrict__ mask, int all_free,
+                            int* __restrict__ row_counts) {
+    gap_count_body(e, mask, all_free, row_counts);
+}
+__global__ void k_gap_count_batch(const EntryDesc* __restrict__ ents, const SetupRec* __restrict__ recs,
+                                  int all_free, int* __restrict__ row_counts) {
+    const EntryDesc e = ents[blockIdx.y];
+    gap_count_body(e, recs[blockIdx.y].mask, all_free, row_counts + recs[blockIdx.y].roff);
+}
 
 // In-place exclusive scan of narrays consecutive arrays of nrows ints (one block each);
 // totals[a] receives the sum of array a.
-__global__ void k_scan_rows(int* __restrict__ v, int nrows, int* __restrict__ totals) {
+__device__ __forceinline__ void scan_body(int* __restrict__ a, int nrows, int* __restrict__ total) {
     __shared__ int part[1024];
-    int* a = v + (long long)blockIdx.x * nrows;
     const int t = threadIdx.x, nt = blockDim.x;
     const int chunk = (nrows + nt - 1) / nt;
     const int b = min(nrows, t * chunk), e = min(nrows, b + chunk);
@@ -127,12 +159,22 @@ __global__ void k_scan_rows(int* __restrict__ v, int nrows, int* __restrict__ to
         a[i] = run;
         run += c;
     }
-    if (t == nt - 1) totals[blockIdx.x] = part[t];
+    if (t == nt - 1) *total = part[t];
+}
+__global__ void k_scan_rows(int* __restrict__ v, int nrows, int* __restrict__ totals) {
+    scan_body(v + (long long)blockIdx.x * nrows, nrows, totals + blockIdx.x);
+}
+// array 2 i + c of the batch: colour c of grid i
+__global__ void k_scan_rows_batch(const EntryDesc* __restrict__ ents, const SetupRec* __restrict__ recs,
+                                  int* __restrict__ v, int* __restrict__ totals) {
+    const int i = blockIdx.x >> 1, c = blockIdx.x & 1, H = ents[i].H;
+    scan_body(v + recs[i].roff + (long long)c * H, H, totals + blockIdx.x);
 }
 
 // Writes the gap lists, row-major, as (y << 16) | j.  One warp per row.
-__global__ void k_gap_scatter(EntryDesc e, const uint8_t* __restrict__ mask, int all_free,
-                              const int* __restrict__ row_off, uint32_t* __restrict__ gaps) {
+__device__ __forceinline__ void gap_scatter_body(const EntryDesc& e, const uint8_t* __restrict__ mask,
+                                                 int all_free, const int* __restrict__ row_off,
+                                                 uint32_t* __restrict__ gaps) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= e.H) return;
     const int y = warp;
@@ -153,13 +195,23 @@ __global__ void k_gap_scatter(EntryDesc e, const uint8_t* __restrict__ mask, int
         pos1 += __popc(b & ~even);
     }
 }
+__global__ void k_gap_scatter(EntryDesc e, const uint8_t* __restrict__ mask, int all_free,
+                              const int* __restrict__ row_off, uint32_t* __restrict__ gaps) {
+    gap_scatter_body(e, mask, all_free, row_off, gaps);
+}
+__global__ void k_gap_scatter_batch(const EntryDesc* __restrict__ ents, const SetupRec* __restrict__ recs,
+                                    int all_free, const int* __restrict__ row_off, uint32_t* __restrict__ gaps) {
+    const EntryDesc e = ents[blockIdx.y];
+    gap_scatter_body(e, recs[blockIdx.y].mask, all_free, row_off + recs[blockIdx.y].roff, gaps);
+}
 
 // Eq. 4: sum over nearest-neighbour sample pairs (each once: right and down partner) of
 // cos(q (phi_i - phi_j)), with phi_i - phi_j = (z_i - z_j) * 2pi / (z_max - z_min).
 // Each block writes its partial sums; they are added in block order afterwards.
-__global__ void k_sample_energy(EntryDesc e, const float* __restrict__ z,
-                                const uint8_t* __restrict__ mask, float qs,
-                                double* part_sum, unsigned long long* part_cnt, int y_end) {
+__device__ __forceinline__ void sample_energy_body(const EntryDesc& e, const float* __restrict__ z,
+                                                   const uint8_t* __restrict__ mask, float qs,
+                                                   double* part_sum, unsigned long long* part_cnt, int y_end,
+                                                   int bid, int nb) {
     // Eq. 4 pairs (each unordered sample pair once: right and down neighbours), rows
     // block-strided and columns thread-strided (no index division).  The cosine argument
     // q (z_i - z_j) 2 pi / (z_max - z_min) is formed in FP32 (one rounding of the scale,
@@ -169,7 +221,7 @@ __global__ void k_sample_energy(EntryDesc e, const float* __restrict__ z,
     __shared__ unsigned long long scnt[kThreads / 32];
     double acc = 0.0;
     unsigned long long cnt = 0;
-    for (int y = blockIdx.x; y < y_end; y += gridDim.x) {
+    for (int y = bid; y < y_end; y += nb) {
         const float* __restrict__ zr = z + (long long)y * e.W;
         const uint8_t* __restrict__ mr = mask + (long long)y * e.W;
         const bool down = y + 1 < e.H;
@@ -202,21 +254,37 @@ __global__ void k_sample_energy(EntryDesc e, const float* __restrict__ z,
         double t = 0.0;
         unsigned long long c = 0;
         for (int w = 0; w < kThreads / 32; ++w) { t += ssum[w]; c += scnt[w]; }
-        part_sum[blockIdx.x] = t;
-        part_cnt[blockIdx.x] = c;
+        part_sum[bid] = t;
+        part_cnt[bid] = c;
     }
+}
+__global__ void k_sample_energy(EntryDesc e, const float* __restrict__ z,
+                                const uint8_t* __restrict__ mask, float qs,
+                                double* part_sum, unsigned long long* part_cnt, int y_end) {
+    sample_energy_body(e, z, mask, qs, part_sum, part_cnt, y_end, blockIdx.x, gridDim.x);
+}
+// grid i: its own partial count (blocks beyond it return), the same rows per block as the
+// single-grid launch
+__global__ void k_sample_energy_batch(const EntryDesc* __restrict__ ents, const SetupRec* __restrict__ recs,
+                                      double q, double* part_sum, unsigned long long* part_cnt) {
+    const SetupRec& r = recs[blockIdx.y];
+    if ((int)blockIdx.x >= r.nparts) return;
+    const EntryDesc e = ents[blockIdx.y];
+    sample_energy_body(e, r.z, r.mask, (float)(q * r.scale), part_sum + r.poff, part_cnt + r.poff, e.H,
+                       blockIdx.x, r.nparts);
 }
 
 // Eq. 4 in FP64 (MPR_PREC_F64): the same pairs and partials, the cosine argument
 // q (z_i - z_j) 2 pi / (z_max - z_min) and every sum in double.
-__global__ void k_sample_energy64(EntryDesc e, const float* __restrict__ z,
-                                  const uint8_t* __restrict__ mask, double qs,
-                                  double* part_sum, unsigned long long* part_cnt, int y_end) {
+__device__ __forceinline__ void sample_energy64_body(const EntryDesc& e, const float* __restrict__ z,
+                                                     const uint8_t* __restrict__ mask, double qs,
+                                                     double* part_sum, unsigned long long* part_cnt, int y_end,
+                                                     int bid, int nb) {
     __shared__ double ssum[kThreads / 32];
     __shared__ unsigned long long scnt[kThreads / 32];
     double acc = 0.0;
     unsigned long long cnt = 0;
-    for (int y = blockIdx.x; y < y_end; y += gridDim.x) {
+    for (int y = bid; y < y_end; y += nb) {
         const float* __restrict__ zr = z + (long long)y * e.W;
         const uint8_t* __restrict__ mr = mask + (long long)y * e.W;
         const bool down = y + 1 < e.H;
@@ -245,9 +313,22 @@ __global__ void k_sample_energy64(EntryDesc e, const float* __restrict__ z,
         double t = 0.0;
         unsigned long long c = 0;
         for (int w = 0; w < kThreads / 32; ++w) { t += ssum[w]; c += scnt[w]; }
-        part_sum[blockIdx.x] = t;
-        part_cnt[blockIdx.x] = c;
+        part_sum[bid] = t;
+        part_cnt[bid] = c;
     }
+}
+__global__ void k_sample_energy64(EntryDesc e, const float* __restrict__ z,
+                                  const uint8_t* __restrict__ mask, double qs,
+                                  double* part_sum, unsigned long long* part_cnt, int y_end) {
+    sample_energy64_body(e, z, mask, qs, part_sum, part_cnt, y_end, blockIdx.x, gridDim.x);
+}
+__global__ void k_sample_energy64_batch(const EntryDesc* __restrict__ ents, const SetupRec* __restrict__ recs,
+                                        double q, double* part_sum, unsigned long long* part_cnt) {
+    const SetupRec& r = recs[blockIdx.y];
+    if ((int)blockIdx.x >= r.nparts) return;
+    const EntryDesc e = ents[blockIdx.y];
+    sample_energy64_body(e, r.z, r.mask, q * r.scale, part_sum + r.poff, part_cnt + r.poff, e.H,
+                         blockIdx.x, r.nparts);
 }
 
 __global__ void k_philox(const uint4* __restrict__ ctr, uint32_t k0, uint32_t k1,
@@ -318,6 +399,64 @@ cudaError_t launch_sample_energy(const EntryDesc* e, const float* z, const uint8
     count_launches(1, st);
     if (f64) k_sample_energy64<<<g, kThreads, 0, st>>>(*e, z, mask, q * scale, part_sum, part_cnt, y_end);
     else k_sample_energy<<<g, kThreads, 0, st>>>(*e, z, mask, (float)(q * scale), part_sum, part_cnt, y_end);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_minmax_batch(const SetupRec* recs, int n, long long max_sites, unsigned* keys,
+                                unsigned long long* nsamples, cudaStream_t st) {
+    if (n < 1) return cudaSuccess;
+    count_launches(1, st);
+    k_minmax_batch<<<dim3(std::min(grid_for(max_sites), 608), n), kThreads, 0, st>>>(recs, keys, nsamples);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_batch(const EntryDesc* ents, const SetupRec* recs, int n, long long max_sites,
+                              float2* lat, uint32_t key0, uint32_t key1, int all_free, bool f64,
+                              cudaStream_t st) {
+    if (n < 1) return cudaSuccess;
+    count_launches(1, st);
+    const dim3 g(std::min(grid_for(max_sites), 608), n);
+    if (f64)
+        k_pack_batch<double2><<<g, kThreads, 0, st>>>(ents, recs, reinterpret_cast<double2*>(lat), key0, key1,
+                                                      all_free);
+    else
+        k_pack_batch<float2><<<g, kThreads, 0, st>>>(ents, recs, lat, key0, key1, all_free);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gap_count_batch(const EntryDesc* ents, const SetupRec* recs, int n, int max_rows,
+                                   int all_free, int* row_counts, cudaStream_t st) {
+    if (n < 1) return cudaSuccess;
+    count_launches(1, st);
+    k_gap_count_batch<<<dim3((max_rows * 32 + kThreads - 1) / kThreads, n), kThreads, 0, st>>>(ents, recs, all_free,
+                                                                                               row_counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_rows_batch(const EntryDesc* ents, const SetupRec* recs, int n, int* row_counts,
+                                   int* totals, cudaStream_t st) {
+    if (n < 1) return cudaSuccess;
+    count_launches(1, st);
+    k_scan_rows_batch<<<2 * n, 1024, 0, st>>>(ents, recs, row_counts, totals);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gap_scatter_batch(const EntryDesc* ents, const SetupRec* recs, int n, int max_rows,
+                                     int all_free, const int* row_offsets, uint32_t* gaps, cudaStream_t st) {
+    if (n < 1) return cudaSuccess;
+    count_launches(1, st);
+    k_gap_scatter_batch<<<dim3((max_rows * 32 + kThreads - 1) / kThreads, n), kThreads, 0, st>>>(
+        ents, recs, all_free, row_offsets, gaps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_energy_batch(const EntryDesc* ents, const SetupRec* recs, int n, int max_parts,
+                                       double q, double* part_sum, unsigned long long* part_cnt, bool f64,
+                                       cudaStream_t st) {
+    if (n < 1 || max_parts < 1) return cudaSuccess;
+    count_launches(1, st);
+    if (f64) k_sample_energy64_batch<<<dim3(max_parts, n), kThreads, 0, st>>>(ents, recs, q, part_sum, part_cnt);
+    else k_sample_energy_batch<<<dim3(max_parts, n), kThreads, 0, st>>>(ents, recs, q, part_sum, part_cnt);
     return cudaGetLastError();
 }
 

@@ -619,6 +619,33 @@ cudaError_t launch_sample_energy(const EntryDesc* e_host, const float* z, const 
 cudaError_t launch_philox(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, size_t n,
                           cudaStream_t st);
 
+// The same set-up steps for every grid of a batch in one launch each (grid i of the launch
+// = blockIdx.y): a device table of SetupRec (and of the batch's EntryDesc where the step
+// needs the lattice layout).  Per grid the work and its partition are those of the
+// single-grid launchers above, so the results are the same bit for bit.
+struct SetupRec {
+    const float* z;           // the grid's data (device; null for all-free lattices)
+    const uint8_t* mask;      // 1 = sample (device; null for all-free lattices)
+    double zmin, scale;       // Eq. 1
+    long long n;              // sites
+    int roff;                 // first of its 2 H row counts (gap lists)
+    int poff, nparts;         // its Eq. 4 partials: first, count
+};
+cudaError_t launch_minmax_batch(const SetupRec* recs, int n, long long max_sites, unsigned* keys,
+                                unsigned long long* nsamples, cudaStream_t st);
+cudaError_t launch_pack_batch(const EntryDesc* ents, const SetupRec* recs, int n, long long max_sites,
+                              float2* lat, uint32_t key0, uint32_t key1, int all_free, bool f64,
+                              cudaStream_t st);
+cudaError_t launch_gap_count_batch(const EntryDesc* ents, const SetupRec* recs, int n, int max_rows,
+                                   int all_free, int* row_counts, cudaStream_t st);
+cudaError_t launch_scan_rows_batch(const EntryDesc* ents, const SetupRec* recs, int n, int* row_counts,
+                                   int* totals, cudaStream_t st);
+cudaError_t launch_gap_scatter_batch(const EntryDesc* ents, const SetupRec* recs, int n, int max_rows,
+                                     int all_free, const int* row_offsets, uint32_t* gaps, cudaStream_t st);
+cudaError_t launch_sample_energy_batch(const EntryDesc* ents, const SetupRec* recs, int n, int max_parts,
+                                       double q, double* part_sum, unsigned long long* part_cnt, bool f64,
+                                       cudaStream_t st);
+
 // tile path (mpr_tile.cu)
 TileGeom tile_geom(int cfg);
 int tile_config_count();
