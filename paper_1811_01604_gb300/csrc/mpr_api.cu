@@ -74,7 +74,6 @@ struct Batch {
     int* d_chunks = nullptr;               // chunks run by the device-side relaxation loop
     int gsweeps = kDefaultGraphSweeps;     // sweeps per captured chunk (loop condition once per chunk)
     double* d_scratch = nullptr;
-    int nscratch = 1;                      // reduction scratch slots (one per auxiliary stream of the fan)
     double* d_H = nullptr;                 // one exact energy per entry
     bool f64 = false;                      // lattice of double2 and d_acc of doubles (MPR_PREC_F64)
     // tile path (fused sweeps over shared-memory tiles, two lattice buffers)
@@ -217,11 +216,11 @@ constexpr int kPinSlotInts = 4, kPinSlotsPerArena = 256;
 std::mutex g_pin_mu;
 std::vector<int*> g_pin_free;
 
-// A batch's per-grid set-up work (input copies and small kernels, one grid each) goes
-// round-robin over up to kFan auxiliary streams that first wait for the context's stream;
-// the context's stream then waits for all of them.  The grids' small launches run side by
-// side instead of one after another.  A single grid keeps everything on the context's
-// stream.  Streams and events are made on first use and released by mpr_free.
+// A batch's per-grid copies (inputs in, estimates out) go round-robin over up to kFan
+// auxiliary streams that first wait for the context's stream; the context's stream then
+// waits for all of them, so the grids' copies overlap instead of queueing one after
+// another.  A single grid keeps everything on the context's stream.  Streams and events
+// are made on first use and released by mpr_free.
 cudaError_t fan_begin(mpr_ctx* ctx, int n) {
     if (n < 2 && !ctx->nfan) return cudaSuccess;
     if (!ctx->nfan) {
@@ -254,11 +253,6 @@ void fan_release(mpr_ctx* ctx) {
     }
     if (ctx->fan_ev[kFan]) cudaEventDestroy(ctx->fan_ev[kFan]);
     ctx->nfan = 0;
-}
-// Reduction scratch slot k of a batch (k < nscratch): kScratch doubles each; slot 0 is
-// followed by 8 doubles of single results, then slots 1, 2, ...
-double* fan_scratch(const Batch& b, int k) {
-    return k == 0 ? b.d_scratch : b.d_scratch + kScratch + 8 + (size_t)(k - 1) * kScratch;
 }
 
 cudaError_t pinned_slot(int** out) {
@@ -535,8 +529,7 @@ mpr_status batch_build(mpr_ctx* ctx, Batch& b, const std::vector<GridIn>& grids,
     CU(cudaMemsetAsync(b.d_ehist, 0, sizeof(double) * (size_t)b.n_ent * b.ehist_stride, st));
     CU(dalloc(&b.d_active, kMaxGraphSweeps, st));
     CU(dalloc(&b.d_chunks, 1, st));
-    b.nscratch = std::max(1, ctx->nfan);
-    CU(dalloc(&b.d_scratch, kScratch + 8 + (size_t)(b.nscratch - 1) * kScratch, st));
+    CU(dalloc(&b.d_scratch, kScratch + 8, st));
     CU(dalloc(&b.d_H, (size_t)b.n_ent, st));
     CU(cudaStreamSynchronize(st));
     return MPR_OK;
@@ -874,16 +867,20 @@ mpr_status reset_tracked_energy(mpr_ctx* ctx, Batch& b) {
     std::vector<Ctl> c;
     mpr_status s = read_ctl(ctx, b, c);
     if (s != MPR_OK) return s;
-    // on the fan only where this batch has a scratch slot per auxiliary stream
-    if (b.n_ent >= 2 && ctx->nfan > 0 && b.nscratch == ctx->nfan) {
-        CU(fan_begin(ctx, b.n_ent));
-        for (int e = 0; e < b.n_ent; ++e)
-            CU(launch_energy(&b.ents[e], lat_cur(b, c[e]), fan_scratch(b, e % ctx->nfan), kScratch,
-                             b.d_H + e, b.f64, fan_stream(ctx, e)));
-        CU(fan_end(ctx));
+    if (b.n_ent >= 2) {
+        // every grid in one launch (each with the single-grid launch's blocks and order)
+        int max_w = 1, max_h = 1;
+        for (const EntryDesc& E : b.ents) {
+            max_w = std::max(max_w, E.W);
+            max_h = std::max(max_h, E.H);
+        }
+        double* d_part = nullptr;
+        CU(dalloc(&d_part, (size_t)b.n_ent * kScratch, ctx->st));
+        CU(launch_energy_batch(b.d_ents, b.n_ent, max_w, max_h, b.d_lat, b.d_lat2, b.d_ctl, b.tiled ? 1 : 0,
+                               d_part, kScratch, b.d_H, b.f64, ctx->st));
+        dfree(d_part, ctx->st);
     } else {
-        for (int e = 0; e < b.n_ent; ++e)
-            CU(launch_energy(&b.ents[e], lat_cur(b, c[e]), b.d_scratch, kScratch, b.d_H + e, b.f64, ctx->st));
+        CU(launch_energy(&b.ents[0], lat_cur(b, c[0]), b.d_scratch, kScratch, b.d_H, b.f64, ctx->st));
     }
     CU(launch_set_tracked_energy(b.d_ctl, b.d_H, b.n_ent, ctx->st));
     return MPR_OK;

@@ -686,6 +686,12 @@ cudaError_t launch_control(Ctl* ctl, Part* const part[2], const EntryDesc* ents,
 cudaError_t launch_energy(const EntryDesc* e_host, const float2* lat, double* scratch,
                           int scratch_len, double* out, bool f64, cudaStream_t st, int y_a = 0,
                           int y_b = -1);
+// The same for every grid of a batch in two launches: grid i reads lattice buffer 1 where
+// tiled and ctl[i].cur are set, else buffer 0; its partials go to scratch + i scratch_len
+// (the single-grid launch's blocks and order), its H to out[i].
+cudaError_t launch_energy_batch(const EntryDesc* ents, int n, int max_cols, int max_rows, const float2* lat0,
+                                const float2* lat1, const Ctl* ctl, int tiled, double* scratch,
+                                int scratch_len, double* out, bool f64, cudaStream_t st);
 // Row strips: out[0] (color 0: =, color 1: +=) the colour's accepted energy change, out[1]
 // its acceptance count, summed over the half-sweep blocks in block order (FP32 partials as
 // exact integer sums of kDEUnit).

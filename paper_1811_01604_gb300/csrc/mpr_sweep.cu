@@ -224,15 +224,15 @@ __device__ __forceinline__ double bond_sum(double2 v, double2 a, double2 b, doub
 }
 
 template <typename V>
-__global__ void k_energy(EntryDesc e, const V* __restrict__ lat, double* part, int y_a, int y_b) {
+__device__ __forceinline__ void energy_body(const EntryDesc& e, const V* __restrict__ lat, double* part, int y_a,
+                                            int y_b, int bid, int nb) {
     __shared__ double sw[8];
     const int Wc = (e.W + 1) >> 1;
     const long long n = (long long)(y_b - y_a) * Wc;
     const V* p0 = lat + e.plane[0];
     const V* p1 = lat + e.plane[1];
     double acc = 0.0;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-         t += (long long)gridDim.x * blockDim.x) {
+    for (long long t = bid * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)nb * blockDim.x) {
         const int yr = (int)(t / Wc), j = (int)(t - (long long)yr * Wc), y = y_a + yr;
         const int s = y & 1;                                     // colour 0: s = y & 1
         if (2 * j + s >= e.W) continue;
@@ -245,12 +245,35 @@ __global__ void k_energy(EntryDesc e, const V* __restrict__ lat, double* part, i
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sw[w];
-        part[blockIdx.x] = t;
+        part[bid] = t;
     }
+}
+template <typename V>
+__global__ void k_energy(EntryDesc e, const V* __restrict__ lat, double* part, int y_a, int y_b) {
+    energy_body(e, lat, part, y_a, y_b, blockIdx.x, gridDim.x);
+}
+
+// Blocks of the energy launch of a grid of W x H sites (the single-grid launch's count).
+__host__ __device__ __forceinline__ int energy_blocks(int W, int H, int scratch_len) {
+    const long long n = (long long)H * ((W + 1) >> 1);
+    long long b = (n + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < 1) b = 1;
+    return (int)(b < scratch_len ? b : scratch_len);
+}
+template <typename V>
+__global__ void k_energy_batch(const EntryDesc* __restrict__ ents, const V* __restrict__ lat0,
+                               const V* __restrict__ lat1, const Ctl* __restrict__ ctl, int tiled, double* scratch,
+                               int scratch_len) {
+    const EntryDesc e = ents[blockIdx.y];
+    const int nb = energy_blocks(e.W, e.H, scratch_len);
+    if ((int)blockIdx.x >= nb) return;
+    const V* lat = (tiled && ctl[blockIdx.y].cur) ? lat1 : lat0;
+    energy_body(e, lat, scratch + (long long)blockIdx.y * scratch_len, 0, e.H, blockIdx.x, nb);
 }
 
 // Fixed-order sum of n doubles (one block).
-__global__ void k_sum(const double* __restrict__ v, int n, double* out) {
+__device__ __forceinline__ void sum_body(const double* __restrict__ v, int n, double* out) {
     __shared__ double s[256];
     double t = 0.0;
     for (int i = threadIdx.x; i < n; i += 256) t += v[i];
@@ -261,6 +284,12 @@ __global__ void k_sum(const double* __restrict__ v, int n, double* out) {
         __syncthreads();
     }
     if (threadIdx.x == 0) *out = s[0];
+}
+__global__ void k_sum(const double* __restrict__ v, int n, double* out) { sum_body(v, n, out); }
+__global__ void k_sum_batch(const EntryDesc* __restrict__ ents, const double* __restrict__ v, int scratch_len,
+                            double* out) {
+    const EntryDesc& e = ents[blockIdx.x];
+    sum_body(v + (long long)blockIdx.x * scratch_len, energy_blocks(e.W, e.H, scratch_len), out + blockIdx.x);
 }
 
 __global__ void k_set_tracked_energy(Ctl* ctl, const double* H, int n_ent) {
@@ -433,6 +462,22 @@ cudaError_t launch_energy(const EntryDesc* e_host, const float2* lat, double* sc
     else k_energy<float2><<<g, 256, 0, st>>>(*e_host, lat, scratch, y_a, y_b);
     count_launches(1, st);
     k_sum<<<1, 256, 0, st>>>(scratch, g, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_batch(const EntryDesc* ents, int n, int max_cols, int max_rows, const float2* lat0,
+                                const float2* lat1, const Ctl* ctl, int tiled, double* scratch,
+                                int scratch_len, double* out, bool f64, cudaStream_t st) {
+    if (n < 1) return cudaSuccess;
+    const dim3 g(energy_blocks(max_cols, max_rows, scratch_len), n);
+    count_launches(2, st);
+    if (f64)
+        k_energy_batch<double2><<<g, 256, 0, st>>>(ents, reinterpret_cast<const double2*>(lat0),
+                                                   reinterpret_cast<const double2*>(lat1), ctl, tiled, scratch,
+                                                   scratch_len);
+    else
+        k_energy_batch<float2><<<g, 256, 0, st>>>(ents, lat0, lat1, ctl, tiled, scratch, scratch_len);
+    k_sum_batch<<<n, 256, 0, st>>>(ents, scratch, scratch_len, out);
     return cudaGetLastError();
 }
 
