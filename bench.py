@@ -295,7 +295,11 @@ def profile_case(name, tile_cfg=0):
     net128: two training steps of the warm-start network on a batch of 32 128^2 grids.
     net1024: two warm-start forward passes (untrained network) on a 1024^2 grid.
     sweep64_4096: the 4096^2 bench grid in FP64 (MPR_PREC_F64, list kernels), T = 0.05,
-    3 sweeps at a = 8 (6 half-sweep launches)."""
+    3 sweeps at a = 8 (6 half-sweep launches).
+    trace4096, trace1024: per-item timestamps of the sweep kernel over one fill
+    (trace_phases).
+    hostlink: the host<->device bandwidth of the end-to-end line's copies (pinned host
+    memory; torch copies, which are cudaMemcpyAsync)."""
     import torch
     from paper_1811_01604_gb300 import mpr
     if name == "copy4096":
@@ -313,6 +317,28 @@ def profile_case(name, tile_cfg=0):
         t = statistics.median(ms[3:])
         print(json.dumps({"profile_case": name, "bytes_read": 8 * n, "bytes_written": 8 * n,
                           "median_ms": t, "GB_per_s": 2 * 8 * n / (t * 1e-3) / 1e9}))
+        return
+    if name == "hostlink":
+        # the end-to-end line's copies: 83.9 MB from pinned host memory to the device (the
+        # 4096^2 grid's data and mask) and 67.1 MB back (its estimates), timed with CUDA events
+        out = {"profile_case": name}
+        for what, nbytes in (("h2d", 5 * 4096 * 4096), ("d2h", 4 * 4096 * 4096)):
+            h = torch.ones(nbytes, dtype=torch.uint8).pin_memory()
+            d = torch.ones(nbytes, dtype=torch.uint8, device="cuda")
+            ms = []
+            for _ in range(13):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                if what == "h2d":
+                    d.copy_(h, non_blocking=True)
+                else:
+                    h.copy_(d, non_blocking=True)
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            t = statistics.median(ms[3:])
+            out[what] = {"bytes": nbytes, "median_ms": t, "GB_per_s": nbytes / (t * 1e-3) / 1e9}
+        print(json.dumps(out))
         return
     if name == "net128":
         B, S = 32, 128
@@ -914,7 +940,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", default=None,
                     choices=["sweep4096", "fill4096", "copy4096", "net4096", "net1024", "net128",
-                             "sweep64_4096", "trace4096", "trace1024"],
+                             "sweep64_4096", "trace4096", "trace1024", "hostlink"],
                     help="run a small fixed sweep workload for ncu instead of the benchmark")
     ap.add_argument("--workload", default="fill4096", choices=["fill4096", "config1024", "batch256", "warm1024",
                                                                 "warm4096", "chains1024", "ormodes1024", "dpsp"],
