@@ -18,27 +18,33 @@ def _grids():
     return out
 
 
-def _single(z, m, chain, T, sweeps, M, **kw):
+def _single(z, m, chain, T, sweeps, M, with_info=False, **kw):
     H, W = z.shape
     ctx = mpr.mpr_init(z, m, W, H, mpr.mpr_default_params(seed=5, chain=chain, **kw))
     try:
+        info = mpr.mpr_batch_info(ctx, 0)
         mpr.mpr_set_T(ctx, T)
         mpr.mpr_sweep(ctx, sweeps, 3.0)
         zh = np.zeros_like(z)
         mpr.mpr_predict(ctx, M, zh)
-        return zh
+        return (zh, info) if with_info else zh
     finally:
         mpr.mpr_free(ctx)
 
 
-@pytest.mark.parametrize("exec_mode", [mpr.MPR_EXEC_TILE, mpr.MPR_EXEC_LIST])
-def test_batch_reproduces_separate_runs_bitwise(exec_mode):
+@pytest.mark.parametrize("exec_mode,prec", [(mpr.MPR_EXEC_TILE, mpr.MPR_PREC_F32), (mpr.MPR_EXEC_LIST, mpr.MPR_PREC_F32),
+                                            (mpr.MPR_EXEC_LIST, mpr.MPR_PREC_F64)])
+def test_batch_reproduces_separate_runs_bitwise(exec_mode, prec):
+    # the batch's set-up runs each step once for all grids (Eq. 1 extremes, pack, gap
+    # lists, Eq. 4 partials, Eq. 2 energies), a single grid's set-up one grid at a time:
+    # the same e_s, extremes and estimates bit for bit, in FP32 and FP64 lattices
     g = _grids()
     T, sweeps, M = 0.09, 11, 7
     ctx = mpr.mpr_init_batch([z for z, _ in g], [m for _, m in g],
-                             mpr.mpr_default_params(seed=5, chain=0, exec_mode=exec_mode))
+                             mpr.mpr_default_params(seed=5, chain=0, exec_mode=exec_mode, precision=prec))
     try:
         assert mpr.mpr_batch_size(ctx) == len(g)
+        info = mpr.mpr_batch_info_all(ctx)
         mpr.mpr_set_T(ctx, T)
         mpr.mpr_sweep(ctx, sweeps, 3.0)
         outs = [np.zeros_like(z) for z, _ in g]
@@ -46,8 +52,10 @@ def test_batch_reproduces_separate_runs_bitwise(exec_mode):
     finally:
         mpr.mpr_free(ctx)
     for i, (z, m) in enumerate(g):
-        ref = _single(z, m, i, T, sweeps, M, exec_mode=exec_mode)
+        ref, ref_info = _single(z, m, i, T, sweeps, M, with_info=True, exec_mode=exec_mode, precision=prec)
         assert np.array_equal(outs[i].view(np.uint32), ref.view(np.uint32)), i
+        for k in ("e_s", "zmin", "zmax"):
+            assert info[i][k] == ref_info[k], (i, k)
 
 
 def test_batch_relaxation_stops_per_grid_like_separate_runs():
