@@ -954,7 +954,7 @@ def main():
                          "dpsp: FP32 against FP64 fills, L = 32 .. 4096")
     ap.add_argument("--tile-cfg", type=int, default=0, help="profile cases: compiled tile configuration")
     ap.add_argument("--train-steps", type=int, default=2000, help="warm start: Adam steps")
-    ap.add_argument("--warm-stride", type=int, default=4, choices=[1, 2, 4],
+    ap.add_argument("--warm-stride", type=int, default=4, choices=[1, 2, 4, 8],
                     help="warm start: sites per network pixel along each axis")
     ap.add_argument("--batch-warm", action="store_true",
                     help="batch256: also time the batched fill with the learned warm start")

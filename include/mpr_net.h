@@ -48,7 +48,7 @@ typedef struct mpr_net mpr_net;
 /* A new network with He-initialised weights drawn from seed (host PRNG).
    ENOMEM / ECUDA on device failure; *net is NULL then. */
 mpr_status mpr_net_create(mpr_net** net, uint64_t seed, void* cuda_stream);
-/* The same at stride 1, 2 or 4 (mpr_net_create is stride 1).  At stride S the network works
+/* The same at stride 1, 2, 4 or 8 (mpr_net_create is stride 1).  At stride S the network works
    on a frame S times coarser along each axis: frame pixel (Y, X) stands for the S x S
    block of sites (S Y + dy, S X + dx); its input channels are the block means of the
    per-site input above, every gap site of the block takes the pixel's prediction, and

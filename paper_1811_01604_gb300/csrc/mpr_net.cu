@@ -320,7 +320,7 @@ struct mpr_net {
     long long wt_off[14] = {0}, wtb_off[14] = {0};
     int* d_err = nullptr;              // set by a tensor-core kernel whose barrier wait expired
     int adam_t = 0;
-    int stride = 1;                    // sites per frame pixel along each axis (1, 2 or 4)
+    int stride = 1;                    // sites per frame pixel along each axis (1, 2, 4 or 8)
     double* d_zr = nullptr;            // zmin[kMaxB], zmax[kMaxB]
     double* d_loss = nullptr;
     unsigned long long* d_cnt = nullptr;
@@ -621,7 +621,7 @@ int mpr_net_stride(const mpr_net* net) { return net ? net->stride : 0; }
 mpr_status mpr_net_create_strided(mpr_net** out, uint64_t seed, int stride, void* cuda_stream) {
     if (!out) return MPR_EINVAL;
     *out = nullptr;
-    if (stride != 1 && stride != 2 && stride != 4) return MPR_EINVAL;
+    if (stride != 1 && stride != 2 && stride != 4 && stride != 8) return MPR_EINVAL;
     mpr_net* net = new mpr_net();
     net->stride = stride;
     net->st = (cudaStream_t)cuda_stream;

@@ -176,7 +176,7 @@ def _gpu_tensors(net, B, Hf, Wf):
 
 
 @pytest.mark.parametrize("B,H,W,S", [(2, 16, 24, 1), (1, 32, 32, 1), (2, 32, 48, 2), (1, 64, 32, 2),
-                                     (2, 64, 32, 4)])
+                                     (2, 64, 32, 4), (1, 64, 64, 8)])
 def test_network_layer_by_layer_matches_oracle(B, H, W, S):
     # Every step of the forward and backward pass is checked element by element against the
     # FP64 oracle applied to the kernels' own inputs of that step (their stored bf16
@@ -332,7 +332,7 @@ def _ctx_grid(H, W, seed):
 @pytest.mark.parametrize("shapes,S", [([(64, 64)], 1), ([(61, 45)], 1),
                                       ([(64, 64), (64, 64), (40, 48), (33, 70)], 1),
                                       ([(61, 45)], 2), ([(64, 64), (40, 48), (33, 70)], 2),
-                                      ([(61, 45), (64, 64)], 4)])
+                                      ([(61, 45), (64, 64)], 4), ([(61, 45), (64, 70)], 8)])
 def test_warmstart_writes_the_network_state_into_gap_sites(shapes, S):
     grids = [_ctx_grid(H, W, 7 + i) for i, (H, W) in enumerate(shapes)]
     net = mpr.mpr_net_create(3, stride=S)
