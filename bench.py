@@ -222,14 +222,46 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def trace_summary(it, ctl, relax, n_sms):
+    """Where a phase's time goes, from the sweep kernel's timestamps (mpr_debug_trace).
+    it: int64 [sweeps][tiles][6] item stamps in ns (taken, copy issued, copy landed, both
+    colours updated, written back; block | SM << 32), zero where an item was not run;
+    ctl: int64 [k][2] control-step stamps (ticket that completed a sweep, published), zero
+    where unused.  Per item medians (us) of the wait for its inputs, the copy, the update
+    and the write-back; the fraction of block time spent updating; the time per sweep; for
+    a relaxation (relax), the serial gap of the Algorithm 2 control step (last update to
+    the ticket, the control step, its publication to the next sweep's first copy landing)
+    and how a mid-relaxation sweep's tiles fall on the n_sms SMs."""
+    S = it.shape[0]
+    ok = it[:, :, 1] > 0
+    t = [it[:, :, k][ok] for k in range(5)]
+    d = lambda a, b: float(np.median(b - a)) / 1e3
+    last = np.where(ok, it[:, :, 3], 0).max(axis=1)
+    r = {"sweeps": S, "items": int(ok.sum()),
+         "us_wait": d(t[0], t[1]), "us_copy": d(t[1], t[2]), "us_update": d(t[2], t[3]),
+         "us_writeback": float(np.median((t[4] - t[3])[t[4] > 0])) / 1e3,
+         "us_per_sweep": float(np.median(np.diff(last))) / 1e3}
+    nb = int((it[:, :, 5][ok] & 0xFFFFFFFF).max()) + 1
+    r["blocks"] = nb
+    r["update_share_of_block_time"] = float((t[3] - t[2]).sum() / (nb * (t[3].max() - t[0].min())))
+    if relax:
+        tix = np.sort(ctl[:, 0][ctl[:, 0] > 0])
+        pub = np.sort(ctl[:, 1][ctl[:, 1] > 0])
+        n = min(len(pub), S) - 1
+        first = np.where(ok, it[:, :, 2], np.iinfo(np.int64).max).min(axis=1)
+        r["us_last_update_to_ticket"] = float(np.median(tix[:n] - last[:n])) / 1e3
+        r["us_control_step"] = float(np.median(pub[:n] - tix[:n])) / 1e3
+        r["us_publish_to_first_copy_landed"] = float(np.median(first[1:n + 1] - pub[:n])) / 1e3
+        sm = (it[S // 2, :, 5] >> 32)[ok[S // 2]]
+        cnt = np.bincount(sm.astype(np.int64), minlength=n_sms)
+        r["mid_sweep_tiles_per_sm"] = {"max": int(cnt.max()), "idle_sms": int((cnt == 0).sum()),
+                                       "histogram": np.bincount(cnt).tolist()}
+    return r
+
+
 def trace_phases(z, mask, W, H, T, tile_cfg):
-    """Per-item timestamps of the sweep kernel (mpr_debug_trace) over one fill at a fixed T:
-    the relaxation launch and the M accumulating sweeps.  Per phase: median per item of the
-    wait for its inputs, the tile copy, the update of both colours and the write-back; the
-    fraction of block time spent updating; the time per sweep; in the relaxation, the
-    Algorithm 2 control step's serial gap (from the sweep's last update to the ticket that
-    completes it, the control step, and from its publication to the next sweep's first
-    copy landing); and how a mid-relaxation sweep's tiles fall on the SMs."""
+    """trace_summary of the relaxation launch and the M accumulating sweeps of one fill at
+    a fixed T (mpr_debug_trace)."""
     import torch
     from paper_1811_01604_gb300 import mpr
     g = mpr.mpr_default_params(seed=1, M=M, tile_cfg=tile_cfg)
@@ -253,30 +285,8 @@ def trace_phases(z, mask, W, H, T, tile_cfg):
             mpr.mpr_debug_trace(None)
             it = buf[: ntiles * S * 6].cpu().numpy().astype(np.int64).reshape(S, ntiles, 6)
             ctl = buf[K * 6:].cpu().numpy().astype(np.int64).reshape(-1, 2)
-            ok = it[:, :, 1] > 0
-            t = [it[:, :, k][ok] for k in range(5)]
-            d = lambda a, b: float(np.median(b - a)) / 1e3
-            last = np.where(ok, it[:, :, 3], 0).max(axis=1)
-            r = {"sweeps": S, "items": int(ok.sum()),
-                 "us_wait": d(t[0], t[1]), "us_copy": d(t[1], t[2]), "us_update": d(t[2], t[3]),
-                 "us_writeback": float(np.median((t[4] - t[3])[t[4] > 0])) / 1e3,
-                 "us_per_sweep": float(np.median(np.diff(last))) / 1e3}
-            nb = int((it[:, :, 5][ok] & 0xFFFFFFFF).max()) + 1
-            r["blocks"] = nb
-            r["update_share_of_block_time"] = float((t[3] - t[2]).sum() / (nb * (t[3].max() - t[0].min())))
-            if phase == "relax":
-                tix = np.sort(ctl[:, 0][ctl[:, 0] > 0])
-                pub = np.sort(ctl[:, 1][ctl[:, 1] > 0])
-                n = min(len(pub), S) - 1
-                first = np.where(ok, it[:, :, 2], np.iinfo(np.int64).max).min(axis=1)
-                r["us_last_update_to_ticket"] = float(np.median(tix[:n] - last[:n])) / 1e3
-                r["us_control_step"] = float(np.median(pub[:n] - tix[:n])) / 1e3
-                r["us_publish_to_first_copy_landed"] = float(np.median(first[1:n + 1] - pub[:n])) / 1e3
-                sm = (it[S // 2, :, 5] >> 32)[ok[S // 2]]
-                cnt = np.bincount(sm.astype(np.int64), minlength=torch.cuda.get_device_properties(0).multi_processor_count)
-                r["mid_sweep_tiles_per_sm"] = {"max": int(cnt.max()), "idle_sms": int((cnt == 0).sum()),
-                                               "histogram": np.bincount(cnt).tolist()}
-            out[phase] = r
+            out[phase] = trace_summary(it, ctl, phase == "relax",
+                                       torch.cuda.get_device_properties(0).multi_processor_count)
     finally:
         mpr.mpr_free(ctx)
     return out
