@@ -117,8 +117,8 @@ class ClockSampler:
 # phase: dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the profile case
 # fill4096 (the relaxation launch, 261 sweeps, and the accumulating launch, 100 sweeps),
 # divided by the launch's sweeps; valid for the kernel sources with this hash only.
-TILE_TRAFFIC_PER_SWEEP = {2: {"relax": (48.007567e9 + 36.125274e9) / 261, "acc": (18.342268e9 + 16.763504e9) / 100}}
-TILE_TRAFFIC_SOURCE_HASH = "609e9af40e2168f0"
+TILE_TRAFFIC_PER_SWEEP = {2: {"relax": (48.008288e9 + 36.125516e9) / 261, "acc": (18.341778e9 + 16.763368e9) / 100}}
+TILE_TRAFFIC_SOURCE_HASH = "61db15acd72b83d5"
 
 
 def tile_kernel_hash():
